@@ -1,0 +1,69 @@
+"""Seeded input generators: laws of Section 3.2 and the workload substitutions."""
+import numpy as np
+
+from paper_2403_03571_gb300 import synth
+
+
+def test_deterministic():
+    a = synth.make_instance(3, 50, 8, 123)
+    b = synth.make_instance(3, 50, 8, 123)
+    for f in ("x", "A", "v"):
+        assert np.array_equal(getattr(a, f), getattr(b, f))
+
+
+def test_2d_anisotropy_law():
+    A = synth.aniso_2d_lognormal(synth.rng(1), 20000, 0.3)
+    assert np.allclose(A, np.transpose(A, (0, 2, 1)))
+    assert np.allclose(np.linalg.det(A), 1.0, atol=1e-12)
+    ev = np.linalg.eigvalsh(A)
+    assert np.all(ev > 0)
+    # eigenvalues are a and 1/a with ln a ~ N(0, 0.3^2): ln(max eig) = |ln a|
+    la = np.log(ev[:, 1])
+    assert abs(np.mean(la) - 0.3 * np.sqrt(2 / np.pi)) < 0.01
+
+
+def test_3d_anisotropy_law():
+    A = synth.aniso_3d_lognormal(synth.rng(2), 20000, 0.3)
+    assert np.allclose(A, np.transpose(A, (0, 2, 1)))
+    assert np.allclose(np.linalg.det(A), 1.0, atol=1e-12)
+    assert np.all(np.linalg.eigvalsh(A) > 0)
+    # Haar-uniform rotations: E[Q] = 0 and E[Q_00^2] = 1/3
+    Q = synth.uniform_rotations(synth.rng(3), 50000)
+    assert np.allclose(np.einsum("nij,nkj->nik", Q, Q), np.eye(3), atol=1e-12)
+    assert np.allclose(np.linalg.det(Q), 1.0)
+    assert np.abs(Q.mean(axis=0)).max() < 0.01
+    assert abs(np.mean(Q[:, 0, 0] ** 2) - 1 / 3) < 0.01
+
+
+def test_alpha_law_2d():
+    A = synth.aniso_2d_alpha(synth.rng(4), 5000, 0.7)
+    ev = np.linalg.eigvalsh(A)
+    assert np.allclose(ev[:, 0] * ev[:, 1], 1.0)
+    # minor axis a_hat in (0.3, 1): eigenvalues a_hat^2 and a_hat^-2
+    a_hat = np.sqrt(ev[:, 0])
+    assert a_hat.min() >= 0.3 - 1e-12 and a_hat.max() <= 1.0 + 1e-12
+    assert np.allclose(synth.aniso_2d_alpha(synth.rng(4), 10, 0.0), np.eye(2))
+
+
+def test_volumes():
+    v = synth.volumes_lognormal(synth.rng(5), 1000, 0.5)
+    assert abs(v.sum() - 1.0) < 1e-12 and np.all(v > 0)
+    lv = np.log(v)
+    assert abs(lv.std() - 0.5) < 0.05
+    assert np.allclose(synth.volumes_equal(20), 1 / 20)
+
+
+def test_rejection_distance():
+    for dim, n in ((2, 400), (3, 600)):
+        x = synth.seeds_with_rejection(synth.rng(6), n, dim, 0.2)
+        d = np.sqrt(((x[:, None] - x[None]) ** 2).sum(-1)) + np.eye(n) * 10
+        assert d.min() > 0.2 * n ** (-1.0 / dim)
+        assert x.min() >= 0 and x.max() <= 1
+
+
+def test_workloads_shapes():
+    w0 = synth.workload_2d_20()
+    assert w0.x.shape == (20, 2) and w0.grid.res == (256, 256)
+    assert np.allclose(w0.v, 1 / 20)
+    w1 = synth.workload_3d_1000(m=16)
+    assert w1.x.shape == (1000, 3) and abs(w1.v.sum() - 1) < 1e-12
