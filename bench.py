@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the APD generator hot path on GB300.
+
+One step = one complete anisotropic power diagram generated by Algorithm 3 of
+arXiv 2403.03571 on the 3D workload (1000 seeds, lognormal volumes,
+quaternion anisotropy, 256^3 voxels): a weight solve to 1% volume error
+(Algorithm 2), five Lloyd moves each followed by a warm-started solve.  Every
+evaluation of the dual runs the scoring kernel (Algorithm 1 fused with the
+moment reduction), the FP64 near-tie rescoring, and eqs. (2.7)-(2.8).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (builder, Lloyd rounds)
+    "3d_n1000_256cube_lloyd5": ("workload_3d_1000", 5),
+    "2d_n20_256sq": ("workload_2d_20", 0),
+}
+DEFAULT_WORKLOAD = "3d_n1000_256cube_lloyd5"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def make_instance(name, rank):
+    from paper_2403_03571_gb300 import synth
+    builder, rounds = WORKLOADS[name]
+    return getattr(synth, builder)(instance=rank), rounds
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+
+def oracle_sample_eval(inst, frac_den=16, threads=0, seed=7):
+    """Time one oracle evaluation of the dual on a 1/frac_den random pixel sample."""
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(seed))
+    J = inst.grid.num_pixels
+    ids = np.sort(rng.choice(J, size=J // frac_den, replace=False))
+    w = np.zeros(inst.n)
+    t0 = time.perf_counter()
+    oracle.assign_ids(inst.grid, inst.x, inst.A, w, ids, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return dt, ids.shape[0] * inst.n, J * inst.n
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, evals_per_apd):
+    """The oracle on the host cores: each step times one evaluation on a pixel sample,
+    scaled to the full grid and to the evaluations one APD needs."""
+    import oracle
+    oracle.lib()
+    inst, rounds = make_instance(args.workload, 0)
+    frac = 16 if inst.grid.dim == 3 else 1
+    for _ in range(max(0, args.warmup)):
+        oracle_sample_eval(inst, frac_den=frac * 4)
+    times = []
+    pairs_s = []
+    for k in range(args.steps):
+        dt, pairs, full_pairs = oracle_sample_eval(inst, frac_den=frac, seed=100 + k)
+        t_eval = dt * full_pairs / pairs
+        times.append(t_eval * evals_per_apd)
+        pairs_s.append(pairs / dt)
+    ms = 1000.0 * statistics.mean(times)
+    val = 1.0 / statistics.mean(times)
+    cores = oracle.max_threads()
+    sample = (f"one FP64 evaluation (Algorithm 1 + moments) on a random 1/{frac} pixel sample "
+              f"({inst.grid.num_pixels // frac} of {inst.grid.num_pixels} pixels x {inst.n} seeds) per "
+              f"step, scaled to the full grid and to {evals_per_apd} evaluations per APD "
+              f"(the GPU run's count)")
+    return {
+        "impl": "reference", "metric": metric_name(args.workload), "value": val, "unit": "APD/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args.workload, inst, rounds),
+        "pair_evals_per_s": statistics.mean(pairs_s),
+        "cpu_baseline": {"value": val, "unit": "APD/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "APD/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def metric_name(workload):
+    return "APD solves/s to 1% volume error and pixel-seed evals/s, plain FP32 path"
+
+
+def config_dict(workload, inst, rounds):
+    return {"workload": workload, "dim": inst.grid.dim, "seeds": inst.n,
+            "grid": list(inst.grid.res), "eps": 0.01, "lloyd_rounds": rounds,
+            "solves_per_apd": rounds + 1, "precision": "fp32 scoring, fp64 near-tie rescoring",
+            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz, sms):
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2403_03571_gb300 import build, capi
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    capi.load()
+    dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    inst, rounds = make_instance(args.workload, rank)
+    dim, n, J = inst.grid.dim, inst.n, inst.grid.num_pixels
+    x0 = torch.from_numpy(inst.x).to(dev)
+    A = torch.from_numpy(inst.A).to(dev)
+    v = torch.from_numpy(inst.v).to(dev)
+    w0 = torch.zeros(n, dtype=torch.float64, device=dev)
+    x_out = torch.empty_like(x0)
+    w_out = torch.empty_like(w0)
+    ws = capi.Workspace(dim, n, J)
+    opts = capi.solve_opts(eps=0.01)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(xin, win):
+        if rounds > 0:
+            rc, info = capi.apd_lloyd(inst.grid, xin, A, win, v, rounds, x_out, w_out, ws, opts)
+        else:
+            rc, info = capi.apd_solve_weights(inst.grid, xin, A, win, v, w_out, ws, opts)
+        if rc not in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE):
+            raise RuntimeError(f"solve did not converge: {info.as_dict()}")
+        return info
+
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(step(x0, w0))
+    torch.cuda.synchronize()
+    ws.profile_read()
+    ws.profile(True)
+    clk = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    total_ms = 0.0
+    timed_infos = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        timed_infos.append(step(x0, w0))
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    assign_ms, assign_launches, assign_pairs, kernel_launches = ws.profile_read()
+    ws.profile(False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    max_ms = float(t.item())
+
+    # end to end through the public API: inputs from pinned host memory, result read back
+    hx = torch.from_numpy(inst.x).pin_memory()
+    hA = torch.from_numpy(inst.A).pin_memory()
+    hv = torch.from_numpy(inst.v).pin_memory()
+    hw = torch.zeros(n, dtype=torch.float64).pin_memory()
+    hxo = torch.empty_like(hx).pin_memory()
+    hwo = torch.empty_like(hw).pin_memory()
+    h2d = sum(tt.numel() * tt.element_size() for tt in (hx, hA, hv, hw))
+    d2h = hxo.numel() * hxo.element_size() + hwo.numel() * hwo.element_size()
+    e2e_ms = 0.0
+    for _ in range(args.e2e_steps):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dx = hx.to(dev, non_blocking=True)
+        dA = hA.to(dev, non_blocking=True)
+        dv = hv.to(dev, non_blocking=True)
+        dw = hw.to(dev, non_blocking=True)
+        if rounds > 0:
+            capi.apd_lloyd(inst.grid, dx, dA, dw, dv, rounds, x_out, w_out, ws, opts)
+        else:
+            capi.apd_solve_weights(inst.grid, dx, dA, dw, dv, w_out, ws, opts)
+        hxo.copy_(x_out, non_blocking=True)
+        hwo.copy_(w_out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = world * args.e2e_steps / (float(te.item()) / 1000.0)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    evals = [i.evaluations for i in timed_infos]
+    rescored = sum(i.rescored_fp64 for i in timed_infos)
+    pairs_total = sum(i.evaluations for i in timed_infos) * J * n
+    value = world * args.steps / (max_ms / 1000.0)
+    peaks, peak_src = load_peaks()
+    sm_mhz_nominal = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = fp32_peak_tflops(sm_mhz_nominal, sms)
+    F = 10 if dim == 3 else 6
+    per_launch_ms = assign_ms / max(1, assign_launches)
+    pairs_per_launch = assign_pairs / max(1, assign_launches)
+    achieved = pairs_per_launch * 2 * F / (per_launch_ms / 1000.0) / 1e12
+    out = {
+        "metric": metric_name(args.workload),
+        "value": value,
+        "unit": "APD/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": max_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32/f64",
+        "data": "synthetic",
+        "config": config_dict(args.workload, inst, rounds),
+        "pair_evals_per_s": pairs_total / (max_ms / 1000.0),
+        "assign_kernel_pair_evals_per_s": pairs_per_launch / (per_launch_ms / 1000.0),
+        "evaluations_per_apd": statistics.mean(evals),
+        "rescored_fp64_fraction": rescored / max(1, sum(i.evaluations for i in timed_infos) * J),
+        "roofline": {
+            "bound": "alu",
+            "kernel": "assign_fp32_kernel<%d>" % dim,
+            "achieved": achieved,
+            "peak": fp32_peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak,
+            "traffic": None,
+            "work_per_pair_flops": 2 * F,
+            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz_nominal:.0f} MHz "
+                           f"(max SM clock from MEASURED_PEAKS.json, {peak_src})",
+            "launch_ms": per_launch_ms,
+            "launches": assign_launches,
+        },
+        "e2e": {"value": e2e_val, "unit": "APD/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": kernel_launches,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "wall_s_timed": wall,
+    }
+    if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
+        ref_args = argparse.Namespace(**vars(args))
+        ref_args.steps, ref_args.warmup = 1, 0
+        ref = run_reference(ref_args, int(round(statistics.mean(evals))))
+        out["cpu_baseline"] = ref["cpu_baseline"]
+        out["cpu_baseline"]["pair_evals_per_s"] = ref["pair_evals_per_s"]
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        # evaluations per APD measured on the GPU are not known here: use the
+        # count this workload needed in the committed GPU profile run
+        evals = int(os.environ.get("APD_EVALS_PER_APD", "400"))
+        print(json.dumps(run_reference(args, evals)))
+        return 0
+    out = run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * apd.h -- C ABI of the GB300 (sm_103a) anisotropic power diagram library.
+ *
+ * An anisotropic power diagram (APD) of seeds x_i in R^D (D = 2 or 3) with
+ * symmetric positive-definite anisotropy matrices A_i and weights w_i splits
+ * the box Omega = [lo, hi] into cells
+ *     L_i = { y : |y - x_i|^2_{A_i} - w_i <= |y - x_k|^2_{A_k} - w_k for all k }
+ * (eq. (2.1) of Buze, Feydy, Roper, Sedighiani, Bourne, "Anisotropic power
+ * diagrams for polycrystal modelling", arXiv 2403.03571).  The library works
+ * on the regular pixel/voxel discretisation of Section 2.3 (eq. (2.6)):
+ *     h_d = (hi_d - lo_d) / res_d,   pixel k has centre y_k = lo + (k + 1/2) h,
+ *     linear pixel id j = k_0 + res_0 * (k_1 + res_1 * k_2)  (first axis fastest),
+ *     J = prod_d res_d pixels of measure |P| = prod_d h_d.
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller, contiguous,
+ *     row-major, 8-byte aligned, seed ids 0-based.  The library never frees or
+ *     retains them past the call (stream-ordered calls read them on the stream).
+ *   - x: double [n][dim]; A: double [n][dim][dim] (symmetric positive definite;
+ *     the scoring uses (A + A^T)/2); w: double [n]; v: double [n].
+ *   - A workspace (apd_workspace_create) owns all scratch memory; the compute
+ *     calls allocate nothing.  One workspace per concurrently used stream.
+ *   - Calls marked "stream-ordered" enqueue work on `stream` and return; their
+ *     return value covers argument validation and launch errors only.  Errors
+ *     found on the device (non-finite input, an A that is not SPD, a wait that
+ *     timed out) are latched in the workspace and returned by the next
+ *     apd_workspace_status() or host-synchronous call.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Return values are the apd_status codes below.
+ */
+#ifndef APD_H
+#define APD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *apd_stream_t; /* same type as cudaStream_t */
+
+enum apd_status {
+    APD_OK = 0,
+    APD_NOT_CONVERGED = 1,       /* evaluation cap hit; outputs hold the best iterate */
+    APD_WARN_TOL_INFEASIBLE = 2, /* |P| > eps min_i v_i / 2^D (eq. (2.10)); solve still ran */
+    APD_ERR_ARG = -1,            /* null pointer, bad size, bad grid, bad volumes, non-finite input */
+    APD_ERR_NOT_SPD = -2,        /* some (A_i + A_i^T)/2 is not positive definite */
+    APD_ERR_CUDA = -3,           /* a CUDA runtime call or launch failed */
+    APD_ERR_WORKSPACE = -4,      /* workspace too small for this call, or wrong dimension */
+    APD_ERR_TIMEOUT = -5,        /* a bounded device-side wait ran out; kernel returned early */
+    APD_ERR_UNSUPPORTED = -6     /* precision or option not available in this build */
+};
+
+/* Regular grid on the box [lo, hi] (eq. (2.6)); entries beyond dim are ignored. */
+typedef struct {
+    int32_t dim;     /* 2 or 3 */
+    int32_t res[3];  /* pixels per axis, >= 1 each; J = prod res < 2^31 */
+    double lo[3];
+    double hi[3];    /* hi_d > lo_d, finite */
+} apd_grid;
+
+/* Generators (X, W, Lambda) of eq. (2.1): n seeds, device pointers. */
+typedef struct {
+    int32_t n;
+    const double *x; /* [n][dim] */
+    const double *A; /* [n][dim][dim] */
+    const double *w; /* [n] */
+} apd_seeds;
+
+/* Arithmetic of the scoring stage (Algorithm 1).  Every precision returns the
+ * same labels: candidates are rescored exactly (FP32, then FP64 for near ties
+ * with the reference arithmetic of the cost matrix). */
+typedef enum {
+    APD_FP32 = 0,    /* CUDA-core FP32 scoring of the expanded quadratic */
+    APD_TC_BF16 = 1, /* tcgen05 BF16 contraction of [y (x) y, y, 1] . phi_i, FP32 accumulate */
+    APD_TC_TF32 = 2  /* tcgen05 TF32 contraction, FP32 accumulate */
+} apd_precision;
+
+typedef struct apd_workspace apd_workspace;
+
+/* Moments layout: per seed K = 1 + dim + dim (dim + 1) / 2 int64 words:
+ *   [0]            m_i  = #{ j : H_j = i }
+ *   [1 .. dim]     S1_i = sum_{H_j = i} u_j      with u = 2k + 1 (odd pixel coordinates,
+ *                                               y = lo + u h / 2)
+ *   [dim+1 .. K-1] S2_i = sum_{H_j = i} u_j u_j^T, upper triangle row by row
+ *                  (2D: 00 01 11; 3D: 00 01 02 11 12 22). */
+#define APD_MOMENT_WIDTH(dim) (1 + (dim) + (dim) * ((dim) + 1) / 2)
+
+/* Allocate device scratch for grids of up to max_j pixels and up to max_n
+ * seeds of dimension dim, on the current CUDA device.  *ws receives the handle.
+ * Errors: APD_ERR_ARG (null ws, dim not 2/3, max_n < 1, max_j < 1),
+ * APD_ERR_CUDA (allocation failed; *ws is set to NULL). */
+int apd_workspace_create(apd_workspace **ws, int32_t dim, int32_t max_n, int64_t max_j);
+
+/* Free a workspace (NULL is ignored).  The caller makes sure no work that
+ * uses it is still in flight. */
+void apd_workspace_destroy(apd_workspace *ws);
+
+/* Synchronise `stream`, return and clear the device-side status latched by the
+ * stream-ordered calls (APD_OK, APD_ERR_ARG, APD_ERR_NOT_SPD, APD_ERR_TIMEOUT),
+ * or APD_ERR_CUDA if the synchronisation itself failed. */
+int apd_workspace_status(apd_workspace *ws, apd_stream_t stream);
+
+/* Per-evaluation counters of the last scoring pass on this workspace
+ * (host-synchronous: synchronises `stream`).  rescored_fp64 = pixels whose FP32
+ * best/second-best gap was inside the rounding bound and were rescored in FP64. */
+typedef struct {
+    int64_t pixels;
+    int64_t pairs;          /* pixels * n */
+    int64_t rescored_fp64;
+} apd_eval_stats;
+int apd_last_stats(apd_workspace *ws, apd_eval_stats *out, apd_stream_t stream);
+
+/* Algorithm 1 (pixel method): labels[j] = H_j = argmin_i C_ij with
+ * C_ij = |y_j - x_i|^2_{A_i} - w_i; the lowest index wins exact ties.
+ * labels: int32 device [J].  Stream-ordered.
+ * Errors: APD_ERR_ARG, APD_ERR_WORKSPACE, APD_ERR_UNSUPPORTED, APD_ERR_CUDA. */
+int apd_assign(const apd_grid *grid, const apd_seeds *seeds, apd_precision precision,
+               int32_t *labels, apd_workspace *ws, apd_stream_t stream);
+
+/* Algorithm 1 fused with the per-cell reduction: moments int64 device
+ * [n][APD_MOMENT_WIDTH(dim)] (layout above), exact integers, overwritten.
+ * Stream-ordered.  Errors as apd_assign. */
+int apd_cell_moments(const apd_grid *grid, const apd_seeds *seeds, apd_precision precision,
+                     int64_t *moments, apd_workspace *ws, apd_stream_t stream);
+
+/* Discrete dual of eq. (2.7) and its approximate gradient eq. (2.8):
+ *   g~(W)   = sum_i ((v_i - m_i |P|) w_i + sum_{H_j=i} |P| |y_j - x_i|^2_{A_i})
+ *   grad_i  = v_i - m_i |P|
+ *   max_rel_err = max_i |grad_i| / v_i      (stop quantity of Algorithm 2)
+ * g, max_rel_err: double device [1]; grad: double device [n] (may be NULL).
+ * v: target volumes, v_i > 0.  Stream-ordered. */
+int apd_dual_value_grad(const apd_grid *grid, const apd_seeds *seeds, const double *v,
+                        apd_precision precision, double *g, double *grad, double *max_rel_err,
+                        apd_workspace *ws, apd_stream_t stream);
+
+/* Options of the weight solve (Algorithm 2) and the Lloyd loop (Algorithm 3). */
+typedef struct {
+    double eps;              /* relative volume tolerance, stop when max_i |v_i - m_i|P||/v_i < eps */
+    int32_t max_evals;       /* cap on dual evaluations per solve */
+    int32_t history;         /* L-BFGS memory (1..32) */
+    apd_precision precision; /* scoring arithmetic */
+    int32_t check_volumes;   /* nonzero: reject v unless v_i > 0 and |sum v - |Omega|| <= 1e-9 |Omega| */
+} apd_solve_opts;
+
+/* Fill *opts with the defaults: eps 0.01, max_evals 1000, history 10, APD_FP32, check_volumes 1. */
+void apd_solve_opts_default(apd_solve_opts *opts);
+
+typedef struct {
+    int32_t status;        /* final status of the call */
+    int32_t iterations;    /* accepted L-BFGS steps (summed over solves for apd_lloyd) */
+    int32_t evaluations;   /* dual evaluations */
+    int32_t solves;        /* Algorithm 2 runs */
+    double max_rel_err;    /* at the returned weights */
+    double g;              /* g~ at the returned weights */
+    int64_t rescored_fp64; /* pixels rescored in FP64, summed over evaluations */
+    double seconds;        /* wall time of the call */
+} apd_solve_info;
+
+/* Algorithm 2: maximise g~ by L-BFGS from W0 = seeds->w until
+ * max_i |v_i - m_i |P|| / v_i < eps.  w_out: double device [n] (may alias
+ * seeds->w).  info: host pointer (may be NULL).  Host-synchronous: returns
+ * APD_OK, APD_NOT_CONVERGED (w_out = best iterate), APD_WARN_TOL_INFEASIBLE
+ * (converged although eq. (2.10) fails for this grid) or an error. */
+int apd_solve_weights(const apd_grid *grid, const apd_seeds *seeds, const double *v,
+                      double *w_out, const apd_solve_opts *opts, apd_solve_info *info,
+                      apd_workspace *ws, apd_stream_t stream);
+
+/* One round of Algorithm 3: solve the weights from W0 = seeds->w at X = seeds->x,
+ * then move every seed to the discrete centroid of its cell
+ *   x_i <- sum_{H_j=i} |P| y_j / (m_i |P|)   (empty cells keep x_i),
+ * writing x_out [n][dim] and w_out [n] (the solved weights, the warm start of
+ * the next round).  x_out may alias seeds->x.  Host-synchronous; status as
+ * apd_solve_weights. */
+int apd_lloyd_step(const apd_grid *grid, const apd_seeds *seeds, const double *v,
+                   double *x_out, double *w_out, const apd_solve_opts *opts,
+                   apd_solve_info *info, apd_workspace *ws, apd_stream_t stream);
+
+/* Algorithm 3 in full: `rounds` calls of apd_lloyd_step followed by a final
+ * apd_solve_weights, from X0 = seeds->x and W0 = seeds->w.  Host-synchronous. */
+int apd_lloyd(const apd_grid *grid, const apd_seeds *seeds, const double *v, int32_t rounds,
+              double *x_out, double *w_out, const apd_solve_opts *opts, apd_solve_info *info,
+              apd_workspace *ws, apd_stream_t stream);
+
+/* Kernel timing for benchmarks: when enabled, the library records a CUDA event
+ * pair on the caller's stream around every launch of the scoring kernel
+ * (Algorithm 1 fused with the moments).  apd_profile_read synchronises those
+ * events and returns (and resets) the summed kernel time in milliseconds, the
+ * number of scoring launches, the pixel-seed pairs they scored, and the number
+ * of kernels of any kind this workspace launched since the last read.
+ * Host-synchronous. */
+int apd_profile_enable(apd_workspace *ws, int32_t enable);
+int apd_profile_read(apd_workspace *ws, double *assign_ms, int64_t *launches, int64_t *pairs,
+                     int64_t *kernel_launches);
+
+/* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
+ * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).
+ * Returns M >= 1, or -1 for invalid arguments. */
+int64_t apd_choose_resolution(int32_t dim, double v_min, double eps, double domain_measure);
+
+/* Static text for a status code. */
+const char *apd_status_string(int status);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t apd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APD_H */

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libapd.so (include/apd.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Functions keep the C names; array arguments are
+torch CUDA tensors (device memory) and streams are torch CUDA streams.
+Loading fails loudly when the library is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libapd.so")
+
+APD_OK = 0
+APD_NOT_CONVERGED = 1
+APD_WARN_TOL_INFEASIBLE = 2
+APD_ERR_ARG = -1
+APD_ERR_NOT_SPD = -2
+APD_ERR_CUDA = -3
+APD_ERR_WORKSPACE = -4
+APD_ERR_TIMEOUT = -5
+APD_ERR_UNSUPPORTED = -6
+
+APD_FP32 = 0
+APD_TC_BF16 = 1
+APD_TC_TF32 = 2
+
+# every symbol include/apd.h declares
+EXPORTED = (
+    "apd_workspace_create", "apd_workspace_destroy", "apd_workspace_status", "apd_last_stats",
+    "apd_assign", "apd_cell_moments", "apd_dual_value_grad", "apd_solve_opts_default",
+    "apd_solve_weights", "apd_lloyd_step", "apd_lloyd", "apd_choose_resolution",
+    "apd_status_string", "apd_version", "apd_profile_enable", "apd_profile_read",
+)
+
+
+class ApdGrid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("res", ctypes.c_int32 * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class ApdSeeds(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("x", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("w", ctypes.c_void_p)]
+
+
+class ApdEvalStats(ctypes.Structure):
+    _fields_ = [("pixels", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("rescored_fp64", ctypes.c_int64)]
+
+
+class ApdSolveOpts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("max_evals", ctypes.c_int32),
+                ("history", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("check_volumes", ctypes.c_int32)]
+
+
+class ApdSolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("evaluations", ctypes.c_int32), ("solves", ctypes.c_int32),
+                ("max_rel_err", ctypes.c_double), ("g", ctypes.c_double),
+                ("rescored_fp64", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ApdError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: status {code} ({status_string(code)})")
+
+
+_lib = None
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+
+
+def load(path: Optional[str] = None):
+    """Load libapd.so (built by ``paper_2403_03571_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libapd.so not found at {path}; run paper_2403_03571_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    L.apd_workspace_create.argtypes = [_P(_vp), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+    L.apd_workspace_destroy.argtypes = [_vp]
+    L.apd_workspace_destroy.restype = None
+    L.apd_workspace_status.argtypes = [_vp, _vp]
+    L.apd_last_stats.argtypes = [_vp, _P(ApdEvalStats), _vp]
+    L.apd_assign.argtypes = [_P(ApdGrid), _P(ApdSeeds), ctypes.c_int32, _vp, _vp, _vp]
+    L.apd_cell_moments.argtypes = [_P(ApdGrid), _P(ApdSeeds), ctypes.c_int32, _vp, _vp, _vp]
+    L.apd_dual_value_grad.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, ctypes.c_int32, _vp, _vp, _vp,
+                                      _vp, _vp]
+    L.apd_solve_opts_default.argtypes = [_P(ApdSolveOpts)]
+    L.apd_solve_opts_default.restype = None
+    L.apd_solve_weights.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _P(ApdSolveOpts),
+                                    _P(ApdSolveInfo), _vp, _vp]
+    L.apd_lloyd_step.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _vp, _P(ApdSolveOpts),
+                                 _P(ApdSolveInfo), _vp, _vp]
+    L.apd_lloyd.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, ctypes.c_int32, _vp, _vp,
+                            _P(ApdSolveOpts), _P(ApdSolveInfo), _vp, _vp]
+    L.apd_choose_resolution.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double]
+    L.apd_choose_resolution.restype = ctypes.c_int64
+    L.apd_status_string.argtypes = [ctypes.c_int]
+    L.apd_status_string.restype = ctypes.c_char_p
+    L.apd_version.restype = ctypes.c_int32
+    L.apd_profile_enable.argtypes = [_vp, ctypes.c_int32]
+    L.apd_profile_read.argtypes = [_vp, _P(ctypes.c_double), _P(ctypes.c_int64), _P(ctypes.c_int64),
+                                   _P(ctypes.c_int64)]
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return load().apd_status_string(int(code)).decode()
+
+
+def make_grid(grid) -> ApdGrid:
+    """ApdGrid from an object with dim, res, lo, hi (e.g. synth.Grid)."""
+    g = ApdGrid()
+    g.dim = grid.dim
+    for d in range(3):
+        g.res[d] = grid.res[d] if d < grid.dim else 1
+        g.lo[d] = grid.lo[d] if d < grid.dim else 0.0
+        g.hi[d] = grid.hi[d] if d < grid.dim else 1.0
+    return g
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("arrays must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_seeds(x, A, w) -> ApdSeeds:
+    s = ApdSeeds()
+    s.n = int(x.shape[0])
+    s.x, s.A, s.w = _ptr(x).value, _ptr(A).value, _ptr(w).value
+    return s
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc, what, ok=(APD_OK,)):
+    if rc not in ok:
+        raise ApdError(rc, what)
+    return rc
+
+
+class Workspace:
+    """Owns an apd_workspace (device scratch for one stream)."""
+
+    def __init__(self, dim: int, max_n: int, max_j: int):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.apd_workspace_create(ctypes.byref(h), dim, int(max_n), int(max_j)),
+               "apd_workspace_create")
+        self.handle = h
+        self.dim, self.max_n, self.max_j = dim, max_n, max_j
+
+    def close(self):
+        if self.handle:
+            load().apd_workspace_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None) -> int:
+        return load().apd_workspace_status(self.handle, _stream(stream))
+
+    def profile(self, enable: bool = True):
+        _check(load().apd_profile_enable(self.handle, int(bool(enable))), "apd_profile_enable")
+
+    def profile_read(self):
+        """(summed scoring-kernel ms, scoring launches, pairs, all kernel launches) since
+        the last read."""
+        ms, n, pairs, kl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().apd_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n),
+                                       ctypes.byref(pairs), ctypes.byref(kl)), "apd_profile_read")
+        return ms.value, n.value, pairs.value, kl.value
+
+    def last_stats(self, stream=None) -> ApdEvalStats:
+        st = ApdEvalStats()
+        _check(load().apd_last_stats(self.handle, ctypes.byref(st), _stream(stream)), "apd_last_stats")
+        return st
+
+
+def apd_assign(grid, x, A, w, labels, ws: Workspace, precision=APD_FP32, stream=None):
+    g, s = make_grid(grid), make_seeds(x, A, w)
+    return _check(load().apd_assign(ctypes.byref(g), ctypes.byref(s), precision, _ptr(labels),
+                                    ws.handle, _stream(stream)), "apd_assign")
+
+
+def apd_cell_moments(grid, x, A, w, moments, ws: Workspace, precision=APD_FP32, stream=None):
+    g, s = make_grid(grid), make_seeds(x, A, w)
+    return _check(load().apd_cell_moments(ctypes.byref(g), ctypes.byref(s), precision, _ptr(moments),
+                                          ws.handle, _stream(stream)), "apd_cell_moments")
+
+
+def apd_dual_value_grad(grid, x, A, w, v, g_out, grad, err_out, ws: Workspace, precision=APD_FP32,
+                        stream=None):
+    g, s = make_grid(grid), make_seeds(x, A, w)
+    return _check(load().apd_dual_value_grad(ctypes.byref(g), ctypes.byref(s), _ptr(v), precision,
+                                             _ptr(g_out), _ptr(grad), _ptr(err_out), ws.handle,
+                                             _stream(stream)), "apd_dual_value_grad")
+
+
+def solve_opts(eps=0.01, max_evals=1000, history=10, precision=APD_FP32, check_volumes=1):
+    o = ApdSolveOpts()
+    load().apd_solve_opts_default(ctypes.byref(o))
+    o.eps, o.max_evals, o.history, o.precision, o.check_volumes = (
+        eps, max_evals, history, precision, check_volumes)
+    return o
+
+
+_SOLVE_OK = (APD_OK, APD_NOT_CONVERGED, APD_WARN_TOL_INFEASIBLE)
+
+
+def apd_solve_weights(grid, x, A, w0, v, w_out, ws: Workspace, opts=None, stream=None):
+    g, s = make_grid(grid), make_seeds(x, A, w0)
+    info = ApdSolveInfo()
+    opts = opts or solve_opts()
+    rc = load().apd_solve_weights(ctypes.byref(g), ctypes.byref(s), _ptr(v), _ptr(w_out),
+                                  ctypes.byref(opts), ctypes.byref(info), ws.handle, _stream(stream))
+    _check(rc, "apd_solve_weights", _SOLVE_OK)
+    return rc, info
+
+
+def apd_lloyd_step(grid, x, A, w0, v, x_out, w_out, ws: Workspace, opts=None, stream=None):
+    g, s = make_grid(grid), make_seeds(x, A, w0)
+    info = ApdSolveInfo()
+    opts = opts or solve_opts()
+    rc = load().apd_lloyd_step(ctypes.byref(g), ctypes.byref(s), _ptr(v), _ptr(x_out), _ptr(w_out),
+                               ctypes.byref(opts), ctypes.byref(info), ws.handle, _stream(stream))
+    _check(rc, "apd_lloyd_step", _SOLVE_OK)
+    return rc, info
+
+
+def apd_lloyd(grid, x0, A, w0, v, rounds, x_out, w_out, ws: Workspace, opts=None, stream=None):
+    g, s = make_grid(grid), make_seeds(x0, A, w0)
+    info = ApdSolveInfo()
+    opts = opts or solve_opts()
+    rc = load().apd_lloyd(ctypes.byref(g), ctypes.byref(s), _ptr(v), int(rounds), _ptr(x_out),
+                          _ptr(w_out), ctypes.byref(opts), ctypes.byref(info), ws.handle,
+                          _stream(stream))
+    _check(rc, "apd_lloyd", _SOLVE_OK)
+    return rc, info
+
+
+def apd_choose_resolution(dim, v_min, eps=0.01, domain_measure=1.0) -> int:
+    return int(load().apd_choose_resolution(dim, v_min, eps, domain_measure))

@@ -1,0 +1,705 @@
+// Host side of the C ABI declared in include/apd.h: argument validation,
+// workspace management, the stream-ordered evaluation sequence (Algorithm 1 +
+// moments + eqs. (2.7)-(2.8)), the L-BFGS weight solve of Algorithm 2 and the
+// Lloyd loop of Algorithm 3.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <utility>
+
+#include "apd_internal.cuh"
+
+struct apd_workspace {
+    apd::Workspace w;
+};
+
+using namespace apd;
+
+namespace {
+
+constexpr int kHistCap = 32;
+
+int map_bits(int bits) {
+    if (bits & ST_NOT_SPD) return APD_ERR_NOT_SPD;
+    if (bits & (ST_NONFINITE | ST_BAD_VOLUME)) return APD_ERR_ARG;
+    if (bits & ST_TIMEOUT) return APD_ERR_TIMEOUT;
+    if (bits & ST_BAD_LABEL) return APD_ERR_CUDA;
+    return APD_OK;
+}
+
+int validate_grid(const apd_grid *gr, GridDev &g) {
+    if (!gr) return APD_ERR_ARG;
+    if (gr->dim != 2 && gr->dim != 3) return APD_ERR_ARG;
+    std::memset(&g, 0, sizeof g);
+    g.dim = gr->dim;
+    long long J = 1;
+    double cell = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        if (d < gr->dim) {
+            if (gr->res[d] < 1) return APD_ERR_ARG;
+            if (!std::isfinite(gr->lo[d]) || !std::isfinite(gr->hi[d]) || !(gr->hi[d] > gr->lo[d]))
+                return APD_ERR_ARG;
+            g.res[d] = gr->res[d];
+            g.lo[d] = gr->lo[d];
+            g.h[d] = (gr->hi[d] - gr->lo[d]) / (double)gr->res[d];
+            g.h32[d] = (float)g.h[d];
+            J *= gr->res[d];
+            cell *= g.h[d];
+            if (J >= (1ll << 31)) return APD_ERR_ARG;
+        } else {
+            g.res[d] = 1;
+            g.lo[d] = 0.0;
+            g.h[d] = 1.0;
+            g.h32[d] = 1.f;
+        }
+    }
+    g.J = J;
+    g.cell = cell;
+    return APD_OK;
+}
+
+double domain_measure(const apd_grid *gr) {
+    double m = 1.0;
+    for (int d = 0; d < gr->dim; ++d) m *= gr->hi[d] - gr->lo[d];
+    return m;
+}
+
+int validate_seeds(const apd_seeds *s) {
+    if (!s || s->n < 1 || !s->x || !s->A || !s->w) return APD_ERR_ARG;
+    return APD_OK;
+}
+
+int check_ws(const apd_workspace *ws, const GridDev &g, int n) {
+    if (!ws) return APD_ERR_ARG;
+    if (ws->w.dim != g.dim || n > ws->w.max_n || g.J > ws->w.max_j) return APD_ERR_WORKSPACE;
+    return APD_OK;
+}
+
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? APD_OK : APD_ERR_CUDA; }
+
+#define APD_TRY(expr)                  \
+    do {                               \
+        int _rc = (expr);              \
+        if (_rc != APD_OK) return _rc; \
+    } while (0)
+
+// Algorithm 1 + moments (+ FP64 rescoring of near ties) on `st`.
+int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, const double *w,
+                   apd_precision prec, Workspace &ws, int32_t *labels, unsigned long long *mom,
+                   cudaStream_t st) {
+    if (prec != APD_FP32) return APD_ERR_UNSUPPORTED;
+    const size_t K = (size_t)moment_width(g.dim);
+    APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
+    APD_TRY(cuda_ok(launch_eval_reset(ws, st)));
+    APD_TRY(cuda_ok(launch_seed_prep(g, n, x, A, w, ws, st)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ws.profiling) {
+        while (ws.ev.size() < ws.ev_used + 2) {
+            cudaEvent_t e;
+            APD_TRY(cuda_ok(cudaEventCreate(&e)));
+            ws.ev.push_back(e);
+        }
+        e0 = ws.ev[ws.ev_used];
+        e1 = ws.ev[ws.ev_used + 1];
+        ws.ev_used += 2;
+        ws.prof_pairs += g.J * (long long)n;
+        APD_TRY(cuda_ok(cudaEventRecord(e0, st)));
+    }
+    APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
+    if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
+    APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
+    ws.kernel_launches += 4;
+    ws.last_pixels = g.J;
+    ws.last_pairs = g.J * (long long)n;
+    return APD_OK;
+}
+
+int take_status(Workspace &ws, cudaStream_t st) {
+    int bits = 0;
+    APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+    APD_TRY(cuda_ok(cudaMemcpy(&bits, &ws.sc->status, sizeof(int), cudaMemcpyDeviceToHost)));
+    if (bits) APD_TRY(cuda_ok(cudaMemset(&ws.sc->status, 0, sizeof(int))));
+    return map_bits(bits);
+}
+
+// ----------------------------------------------------------------------------
+// Algorithm 2: L-BFGS on f(W) = -g~(W) with a strong-Wolfe line search
+// (Nocedal & Wright, Algorithms 3.5/3.6, cubic interpolation), stopping at the
+// first evaluation with max_i |v_i - m_i |P|| / v_i < eps.
+// ----------------------------------------------------------------------------
+struct Solver {
+    GridDev g;
+    int n;
+    const double *x, *A, *v;
+    Workspace &ws;
+    apd_precision prec;
+    cudaStream_t st;
+    double eps;
+    int max_evals;
+    int history;
+    bool check_volumes;
+    double measure;
+
+    int evals = 0, iters = 0;
+    long long rescored = 0;
+    double best_err = INFINITY, best_g = 0.0;
+    double last_g = 0.0, last_err = INFINITY;
+    const double *last_point = nullptr;  // device pointer evaluated last
+    bool last_is_best = false;
+    bool first = true;
+
+    Solver(Workspace &w) : ws(w) {}
+
+    // Evaluate at Wp; gf_out receives grad f = -(v - |P| m); pdir (nullable) for <grad f, p>.
+    int eval(const double *Wp, double *gf_out, const double *pdir, double &f, double &dphi,
+             double &err) {
+        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, st));
+        APD_TRY(cuda_ok(launch_dual(g, n, x, A, Wp, v, pdir, ws.moments, ws, nullptr, ws.grad, gf_out,
+                                    nullptr, st)));
+        ws.kernel_launches += 1;
+        APD_TRY(cuda_ok(cudaMemcpyAsync(ws.sc_host, ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st)));
+        APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+        ++evals;
+        const DevScalars &h = *ws.sc_host;
+        rescored += h.flag_count;
+        if (h.status) {
+            const int rc = map_bits(h.status);
+            cudaMemset(&ws.sc->status, 0, sizeof(int));
+            return rc;
+        }
+        if (first) {
+            first = false;
+            if (check_volumes) {
+                if (!(h.min_v > 0.0) || std::fabs(h.sum_v - measure) > 1e-9 * measure) return APD_ERR_ARG;
+            }
+        }
+        f = -h.g;
+        dphi = h.dot_gp;
+        err = h.max_rel_err;
+        last_g = h.g;
+        last_err = err;
+        last_point = Wp;
+        last_is_best = false;
+        if (err < best_err) {
+            best_err = err;
+            best_g = h.g;
+            APD_TRY(cuda_ok(cudaMemcpyAsync(ws.Wbest, Wp, (size_t)n * sizeof(double),
+                                            cudaMemcpyDeviceToDevice, st)));
+            last_is_best = true;
+        }
+        return APD_OK;
+    }
+
+    enum LsResult { LS_ACCEPT, LS_CONVERGED, LS_FAIL, LS_BUDGET };
+
+    // phi(t) = f(W + t p); on LS_ACCEPT ws.Wt / ws.gft hold the accepted point.
+    int line_search(double f0, double dphi0, double t_init, LsResult &res, double &f_acc) {
+        const double c1 = 1e-4, c2 = 0.9;
+        double t_prev = 0.0, phi_prev = f0, dphi_prev = dphi0;
+        double t = t_init;
+        double best_t = 0.0, best_phi = f0;
+        double cur_t = -1.0;  // t at which Wt/gft were last evaluated
+        auto evaluate = [&](double tt, double &phi, double &dphi, double &err) -> int {
+            APD_TRY(cuda_ok(launch_axpy(n, ws.W, tt, ws.p, ws.Wt, st)));
+            ws.kernel_launches += 1;
+            APD_TRY(eval(ws.Wt, ws.gft, ws.p, phi, dphi, err));
+            cur_t = tt;
+            return APD_OK;
+        };
+        auto accept = [&](double tt, double phi) -> int {
+            if (cur_t != tt) {
+                double p2, d2, e2;
+                APD_TRY(evaluate(tt, p2, d2, e2));
+                if (e2 < eps) {
+                    res = LS_CONVERGED;
+                    return APD_OK;
+                }
+                phi = p2;
+            }
+            res = LS_ACCEPT;
+            f_acc = phi;
+            return APD_OK;
+        };
+        auto zoom = [&](double lo, double plo, double dlo, double hi, double phi_hi,
+                        double dhi) -> int {
+            for (int it = 0; it < 20; ++it) {
+                if (evals >= max_evals) {
+                    res = LS_BUDGET;
+                    return APD_OK;
+                }
+                const double a = std::min(lo, hi), b = std::max(lo, hi), w = b - a;
+                double tt;
+                const double d1 = dlo + dhi - 3.0 * (plo - phi_hi) / (lo - hi);
+                const double disc = d1 * d1 - dlo * dhi;
+                if (disc >= 0.0 && std::isfinite(disc)) {
+                    const double d2 = std::copysign(std::sqrt(disc), hi - lo);
+                    const double den = dhi - dlo + 2.0 * d2;
+                    tt = den != 0.0 ? hi - (hi - lo) * (dhi + d2 - d1) / den : 0.5 * (a + b);
+                } else {
+                    tt = 0.5 * (a + b);
+                }
+                if (!std::isfinite(tt) || tt < a + 0.1 * w || tt > b - 0.1 * w) tt = 0.5 * (a + b);
+                double phi, dphi, err;
+                APD_TRY(evaluate(tt, phi, dphi, err));
+                if (err < eps) {
+                    res = LS_CONVERGED;
+                    return APD_OK;
+                }
+                if (phi > f0 + c1 * tt * dphi0 || phi >= plo) {
+                    hi = tt;
+                    phi_hi = phi;
+                    dhi = dphi;
+                } else {
+                    if (phi < best_phi) {
+                        best_phi = phi;
+                        best_t = tt;
+                    }
+                    if (std::fabs(dphi) <= -c2 * dphi0) return accept(tt, phi);
+                    if (dphi * (hi - lo) >= 0.0) {
+                        hi = lo;
+                        phi_hi = plo;
+                        dhi = dlo;
+                    }
+                    lo = tt;
+                    plo = phi;
+                    dlo = dphi;
+                }
+                if (std::fabs(hi - lo) <= 1e-14 * std::max(1.0, std::fabs(lo))) break;
+            }
+            if (best_t > 0.0) return accept(best_t, best_phi);
+            res = LS_FAIL;
+            return APD_OK;
+        };
+        for (int i = 0; i < 30; ++i) {
+            if (evals >= max_evals) {
+                res = LS_BUDGET;
+                return APD_OK;
+            }
+            double phi, dphi, err;
+            APD_TRY(evaluate(t, phi, dphi, err));
+            if (err < eps) {
+                res = LS_CONVERGED;
+                return APD_OK;
+            }
+            if (phi > f0 + c1 * t * dphi0 || (i > 0 && phi >= phi_prev))
+                return zoom(t_prev, phi_prev, dphi_prev, t, phi, dphi);
+            if (phi < best_phi) {
+                best_phi = phi;
+                best_t = t;
+            }
+            if (std::fabs(dphi) <= -c2 * dphi0) return accept(t, phi);
+            if (dphi >= 0.0) return zoom(t, phi, dphi, t_prev, phi_prev, dphi_prev);
+            t_prev = t;
+            phi_prev = phi;
+            dphi_prev = dphi;
+            t = std::min(4.0 * t, 1e12);
+        }
+        if (best_t > 0.0) return accept(best_t, best_phi);
+        res = LS_FAIL;
+        return APD_OK;
+    }
+
+    // Runs the solve from W0 (device, n); returns status.  On exit ws.Wbest
+    // (or the converged point, copied to out) holds the weights.
+    int run(const double *W0, double *out, bool &converged) {
+        converged = false;
+        APD_TRY(cuda_ok(cudaMemcpyAsync(ws.W, W0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st)));
+        double f0, d0, err0;
+        APD_TRY(eval(ws.W, ws.gf, nullptr, f0, d0, err0));
+        if (err0 < eps) {
+            converged = true;
+            return cuda_ok(cudaMemcpyAsync(out, ws.W, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+        int hist = 0, newest = kHistCap - 1;
+        double gamma = 1.0;
+        int fails = 0;
+        while (evals < max_evals) {
+            APD_TRY(cuda_ok(launch_lbfgs_direction(n, hist, newest, kHistCap, gamma, ws, st)));
+            ws.kernel_launches += 1;
+            APD_TRY(cuda_ok(cudaMemcpyAsync(ws.sc_host, ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st)));
+            APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+            double gp0 = ws.sc_host->gp0;
+            if (!(gp0 < 0.0)) {
+                if (hist == 0) break;
+                hist = 0;
+                gamma = 1.0;
+                continue;
+            }
+            double t0 = 1.0;
+            if (hist == 0) {
+                // first step (or after a reset): p = -grad f; take t0 ~ 1 / H_ii with the
+                // cell-volume sensitivity H_ii ~ D V^(1 - 2/D) of a cell of volume V = |Omega| / n
+                const double V = measure / (double)n;
+                t0 = 0.5 * std::pow(V, 2.0 / g.dim - 1.0) / g.dim;
+            }
+            LsResult res;
+            double f_acc = f0;
+            APD_TRY(line_search(f0, gp0, t0, res, f_acc));
+            if (res == LS_CONVERGED) {
+                converged = true;
+                ++iters;
+                return cuda_ok(cudaMemcpyAsync(out, ws.Wt, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            if (res == LS_BUDGET) break;
+            if (res == LS_FAIL) {
+                if (hist == 0 || ++fails > 3) break;
+                hist = 0;
+                gamma = 1.0;
+                continue;
+            }
+            fails = 0;
+            ++iters;
+            const int slot = (newest + 1) % kHistCap;
+            APD_TRY(cuda_ok(launch_lbfgs_push(n, slot, ws, st)));
+            ws.kernel_launches += 1;
+            APD_TRY(cuda_ok(cudaMemcpyAsync(ws.sc_host, ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st)));
+            APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+            const double sy = ws.sc_host->sy, yy = ws.sc_host->yy, ss = ws.sc_host->ss;
+            if (sy > 1e-12 * std::sqrt(ss * yy) && yy > 0.0) {
+                newest = slot;
+                hist = std::min(hist + 1, history);
+                gamma = sy / yy;
+            }
+            std::swap(ws.W, ws.Wt);
+            std::swap(ws.gf, ws.gft);
+            f0 = f_acc;
+        }
+        return cuda_ok(cudaMemcpyAsync(out, ws.Wbest, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+};
+
+int solve_impl(const GridDev &g, const apd_grid *grid, int n, const double *x, const double *A,
+               const double *w0, const double *v, double *w_out, const apd_solve_opts &o,
+               apd_solve_info &info, Workspace &ws, cudaStream_t st, bool need_moments_at_out) {
+    Solver s(ws);
+    s.g = g;
+    s.n = n;
+    s.x = x;
+    s.A = A;
+    s.v = v;
+    s.prec = o.precision;
+    s.st = st;
+    s.eps = o.eps;
+    s.max_evals = o.max_evals;
+    s.history = std::max(1, std::min(o.history, kHistCap));
+    s.check_volumes = o.check_volumes != 0;
+    s.measure = domain_measure(grid);
+    bool conv = false;
+    int rc = s.run(w0, w_out, conv);
+    info.evaluations += s.evals;
+    info.iterations += s.iters;
+    info.rescored_fp64 += s.rescored;
+    info.solves += 1;
+    if (rc != APD_OK) return rc;
+    if (conv) {
+        info.max_rel_err = s.last_err;
+        info.g = s.last_g;
+    } else {
+        info.max_rel_err = s.best_err;
+        info.g = s.best_g;
+        if (need_moments_at_out) {
+            // re-evaluate so that the workspace moments belong to the returned weights
+            double f, d, e;
+            APD_TRY(s.eval(w_out, ws.gf, nullptr, f, d, e));
+        }
+    }
+    if (!conv) return APD_NOT_CONVERGED;
+    const double vmin = ws.sc_host->min_v;
+    if (g.cell > o.eps * vmin / std::pow(2.0, g.dim)) return APD_WARN_TOL_INFEASIBLE;
+    return APD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t apd_version(void) { return 100; }
+
+const char *apd_status_string(int status) {
+    switch (status) {
+        case APD_OK: return "ok";
+        case APD_NOT_CONVERGED: return "not converged: evaluation cap reached";
+        case APD_WARN_TOL_INFEASIBLE: return "converged, but the grid is coarser than eq. (2.10) asks";
+        case APD_ERR_ARG: return "invalid argument";
+        case APD_ERR_NOT_SPD: return "an anisotropy matrix is not symmetric positive definite";
+        case APD_ERR_CUDA: return "CUDA error";
+        case APD_ERR_WORKSPACE: return "workspace too small or of another dimension";
+        case APD_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case APD_ERR_UNSUPPORTED: return "unsupported precision or option";
+        default: return "unknown status";
+    }
+}
+
+void apd_solve_opts_default(apd_solve_opts *o) {
+    if (!o) return;
+    o->eps = 0.01;
+    o->max_evals = 1000;
+    o->history = 10;
+    o->precision = APD_FP32;
+    o->check_volumes = 1;
+}
+
+int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_t max_j) {
+    if (!out) return APD_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || max_n < 1 || max_j < 1 || max_j >= (1ll << 31)) return APD_ERR_ARG;
+    apd_workspace *ws = new (std::nothrow) apd_workspace();
+    if (!ws) return APD_ERR_CUDA;
+    Workspace &w = ws->w;
+    w.dim = dim;
+    w.max_n = max_n;
+    w.max_j = max_j;
+    cudaGetDevice(&w.device);
+    w.n_pad_max = ((max_n + kChunk - 1) / kChunk) * kChunk;
+    w.hist_cap = kHistCap;
+    const size_t K = (size_t)moment_width(dim);
+    const size_t nb = (size_t)((max_n + 255) / 256);
+    bool ok = true;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
+    };
+    alloc((void **)&w.recs, (size_t)w.n_pad_max * sizeof(SeedRec));
+    alloc((void **)&w.moments, (size_t)max_n * K * sizeof(unsigned long long));
+    alloc((void **)&w.flags, (size_t)max_j * sizeof(uint32_t));
+    alloc((void **)&w.sc, sizeof(DevScalars));
+    alloc((void **)&w.part, nb * 5 * sizeof(double));
+    alloc((void **)&w.grad, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.W, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.Wt, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.p, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.gf, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.gft, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.Wbest, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.S, (size_t)kHistCap * max_n * sizeof(double));
+    alloc((void **)&w.Y, (size_t)kHistCap * max_n * sizeof(double));
+    alloc((void **)&w.alpha, kHistCap * sizeof(double));
+    alloc((void **)&w.rho, kHistCap * sizeof(double));
+    alloc((void **)&w.X, (size_t)max_n * dim * sizeof(double));
+    alloc((void **)&w.vbuf, (size_t)max_n * sizeof(double));
+    if (ok && cudaMallocHost((void **)&w.sc_host, sizeof(DevScalars)) != cudaSuccess) ok = false;
+    if (ok && cudaMemset(w.sc, 0, sizeof(DevScalars)) != cudaSuccess) ok = false;
+    if (ok && cudaMemset(w.recs, 0, (size_t)w.n_pad_max * sizeof(SeedRec)) != cudaSuccess) ok = false;
+    if (ok && cudaDeviceSynchronize() != cudaSuccess) ok = false;
+    if (!ok) {
+        apd_workspace_destroy(ws);
+        return APD_ERR_CUDA;
+    }
+    *out = ws;
+    return APD_OK;
+}
+
+void apd_workspace_destroy(apd_workspace *ws) {
+    if (!ws) return;
+    Workspace &w = ws->w;
+    for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
+    void *ptrs[] = {w.recs, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+                    w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (w.sc_host) cudaFreeHost(w.sc_host);
+    delete ws;
+}
+
+int apd_profile_enable(apd_workspace *ws, int32_t enable) {
+    if (!ws) return APD_ERR_ARG;
+    ws->w.profiling = enable != 0;
+    return APD_OK;
+}
+
+int apd_profile_read(apd_workspace *ws, double *assign_ms, int64_t *launches, int64_t *pairs,
+                     int64_t *kernel_launches) {
+    if (!ws || !assign_ms || !launches || !pairs || !kernel_launches) return APD_ERR_ARG;
+    Workspace &w = ws->w;
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < w.ev_used; k += 2) {
+        APD_TRY(cuda_ok(cudaEventSynchronize(w.ev[k + 1])));
+        float ms = 0.f;
+        APD_TRY(cuda_ok(cudaEventElapsedTime(&ms, w.ev[k], w.ev[k + 1])));
+        total += ms;
+    }
+    *assign_ms = total;
+    *launches = (int64_t)(w.ev_used / 2);
+    *pairs = w.prof_pairs;
+    *kernel_launches = w.kernel_launches;
+    w.ev_used = 0;
+    w.prof_pairs = 0;
+    w.kernel_launches = 0;
+    return APD_OK;
+}
+
+int apd_workspace_status(apd_workspace *ws, apd_stream_t stream) {
+    if (!ws) return APD_ERR_ARG;
+    return take_status(ws->w, (cudaStream_t)stream);
+}
+
+int apd_last_stats(apd_workspace *ws, apd_eval_stats *out, apd_stream_t stream) {
+    if (!ws || !out) return APD_ERR_ARG;
+    unsigned int fc = 0;
+    APD_TRY(cuda_ok(cudaStreamSynchronize((cudaStream_t)stream)));
+    APD_TRY(cuda_ok(cudaMemcpy(&fc, &ws->w.sc->flag_count, sizeof fc, cudaMemcpyDeviceToHost)));
+    out->pixels = ws->w.last_pixels;
+    out->pairs = ws->w.last_pairs;
+    out->rescored_fp64 = fc;
+    return APD_OK;
+}
+
+int apd_assign(const apd_grid *grid, const apd_seeds *seeds, apd_precision precision, int32_t *labels,
+               apd_workspace *ws, apd_stream_t stream) {
+    GridDev g;
+    APD_TRY(validate_grid(grid, g));
+    APD_TRY(validate_seeds(seeds));
+    if (!labels) return APD_ERR_ARG;
+    APD_TRY(check_ws(ws, g, seeds->n));
+    return enqueue_assign(g, seeds->n, seeds->x, seeds->A, seeds->w, precision, ws->w, labels,
+                          ws->w.moments, (cudaStream_t)stream);
+}
+
+int apd_cell_moments(const apd_grid *grid, const apd_seeds *seeds, apd_precision precision,
+                     int64_t *moments, apd_workspace *ws, apd_stream_t stream) {
+    GridDev g;
+    APD_TRY(validate_grid(grid, g));
+    APD_TRY(validate_seeds(seeds));
+    if (!moments) return APD_ERR_ARG;
+    APD_TRY(check_ws(ws, g, seeds->n));
+    return enqueue_assign(g, seeds->n, seeds->x, seeds->A, seeds->w, precision, ws->w, nullptr,
+                          reinterpret_cast<unsigned long long *>(moments), (cudaStream_t)stream);
+}
+
+int apd_dual_value_grad(const apd_grid *grid, const apd_seeds *seeds, const double *v,
+                        apd_precision precision, double *g_out, double *grad, double *max_rel_err,
+                        apd_workspace *ws, apd_stream_t stream) {
+    GridDev g;
+    APD_TRY(validate_grid(grid, g));
+    APD_TRY(validate_seeds(seeds));
+    if (!v || !g_out || !max_rel_err) return APD_ERR_ARG;
+    APD_TRY(check_ws(ws, g, seeds->n));
+    cudaStream_t st = (cudaStream_t)stream;
+    APD_TRY(enqueue_assign(g, seeds->n, seeds->x, seeds->A, seeds->w, precision, ws->w, nullptr,
+                           ws->w.moments, st));
+    ws->w.kernel_launches += 1;
+    return cuda_ok(launch_dual(g, seeds->n, seeds->x, seeds->A, seeds->w, v, nullptr, ws->w.moments,
+                               ws->w, g_out, grad, nullptr, max_rel_err, st));
+}
+
+static int solve_entry(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
+                       const apd_solve_opts *opts, GridDev &g, apd_solve_opts &o, apd_workspace *ws,
+                       cudaStream_t st) {
+    APD_TRY(validate_grid(grid, g));
+    APD_TRY(validate_seeds(seeds));
+    if (!v || !w_out) return APD_ERR_ARG;
+    APD_TRY(check_ws(ws, g, seeds->n));
+    if (opts) o = *opts;
+    else apd_solve_opts_default(&o);
+    if (!(o.eps > 0.0) || o.max_evals < 1 || o.history < 1) return APD_ERR_ARG;
+    if (o.precision != APD_FP32) return APD_ERR_UNSUPPORTED;
+    // a status latched by earlier stream-ordered calls is reported first
+    return take_status(ws->w, st);
+}
+
+int apd_solve_weights(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
+                      const apd_solve_opts *opts, apd_solve_info *info, apd_workspace *ws,
+                      apd_stream_t stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    apd_solve_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    GridDev g;
+    apd_solve_opts o;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st);
+    if (rc == APD_OK)
+        rc = solve_impl(g, grid, seeds->n, seeds->x, seeds->A, seeds->w, v, w_out, o, inf, ws->w, st, false);
+    if (rc >= 0) cudaStreamSynchronize(st);
+    inf.status = rc;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
+static int lloyd_round(const GridDev &g, const apd_grid *grid, int n, const double *x, const double *A,
+                       const double *w0, const double *v, double *x_out, double *w_out,
+                       const apd_solve_opts &o, apd_solve_info &inf, Workspace &ws, cudaStream_t st,
+                       int &worst) {
+    int rc = solve_impl(g, grid, n, x, A, w0, v, w_out, o, inf, ws, st, true);
+    if (rc < 0) return rc;
+    if (rc > worst) worst = rc;
+    // the workspace moments belong to (x, w_out): move seeds to the discrete centroids
+    ws.kernel_launches += 1;
+    return cuda_ok(launch_centroids(g, n, x, ws.moments, x_out, st));
+}
+
+int apd_lloyd_step(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *x_out,
+                   double *w_out, const apd_solve_opts *opts, apd_solve_info *info,
+                   apd_workspace *ws, apd_stream_t stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    apd_solve_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    GridDev g;
+    apd_solve_opts o;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st);
+    if (rc == APD_OK && !x_out) rc = APD_ERR_ARG;
+    int worst = APD_OK;
+    if (rc == APD_OK) {
+        rc = lloyd_round(g, grid, seeds->n, seeds->x, seeds->A, seeds->w, v, x_out, w_out, o, inf, ws->w,
+                         st, worst);
+        if (rc == APD_OK) rc = worst;
+    }
+    if (rc >= 0) cudaStreamSynchronize(st);
+    inf.status = rc;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
+int apd_lloyd(const apd_grid *grid, const apd_seeds *seeds, const double *v, int32_t rounds,
+              double *x_out, double *w_out, const apd_solve_opts *opts, apd_solve_info *info,
+              apd_workspace *ws, apd_stream_t stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    apd_solve_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    GridDev g;
+    apd_solve_opts o;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st);
+    if (rc == APD_OK && (!x_out || rounds < 0)) rc = APD_ERR_ARG;
+    int worst = APD_OK;
+    if (rc == APD_OK) {
+        const int n = seeds->n;
+        if (x_out != seeds->x)
+            rc = cuda_ok(cudaMemcpyAsync(x_out, seeds->x, (size_t)n * g.dim * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+        if (rc == APD_OK && w_out != seeds->w)
+            rc = cuda_ok(cudaMemcpyAsync(w_out, seeds->w, (size_t)n * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+        for (int k = 0; rc == APD_OK && k < rounds; ++k)
+            rc = lloyd_round(g, grid, n, x_out, seeds->A, w_out, v, x_out, w_out, o, inf, ws->w, st, worst);
+        if (rc == APD_OK) {
+            rc = solve_impl(g, grid, n, x_out, seeds->A, w_out, v, w_out, o, inf, ws->w, st, false);
+            if (rc >= 0 && rc > worst) worst = rc;
+            if (rc >= 0) rc = worst;
+        }
+    }
+    if (rc >= 0) cudaStreamSynchronize(st);
+    inf.status = rc;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
+int64_t apd_choose_resolution(int32_t dim, double v_min, double eps, double domain_measure_) {
+    if ((dim != 2 && dim != 3) || !(v_min > 0.0) || !(eps > 0.0) || !(domain_measure_ > 0.0) ||
+        !std::isfinite(v_min) || !std::isfinite(domain_measure_))
+        return -1;
+    const double bound = eps * v_min / std::pow(2.0, dim);
+    const double t = domain_measure_ / bound;
+    int64_t m = (int64_t)std::ceil(std::pow(t, 1.0 / dim) - 1e-9);
+    if (m < 1) m = 1;
+    auto fits = [&](int64_t mm) { return domain_measure_ / std::pow((double)mm, dim) <= bound * (1.0 + 1e-12); };
+    while (!fits(m)) ++m;
+    while (m > 1 && fits(m - 1)) --m;
+    return m;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Internal declarations shared by the CUDA translation units of libapd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/apd.h"
+
+namespace apd {
+
+// ----------------------------------------------------------------------------
+// device status bits (latched in DevScalars::status, mapped to apd_status)
+// ----------------------------------------------------------------------------
+enum : int {
+    ST_NONFINITE = 1,   // non-finite x, A or w
+    ST_NOT_SPD = 2,     // (A + A^T)/2 not positive definite
+    ST_TIMEOUT = 4,     // a bounded mbarrier wait ran out
+    ST_BAD_VOLUME = 8,  // v_i <= 0 or non-finite
+    ST_BAD_LABEL = 16,  // internal: a label outside [0, n)
+};
+
+// Seed record streamed into shared memory by the scoring kernels: the FP64
+// position and weight (recentred per tile in FP64, then rounded) and the FP32
+// symmetric part of A (upper triangle: 2D 00 01 11, 3D 00 01 02 11 12 22).
+struct __align__(16) SeedRec {
+    double x[3];
+    double w;
+    float a[6];
+    float pad[2];
+};
+static_assert(sizeof(SeedRec) == 64, "SeedRec must be 64 bytes");
+
+constexpr int kChunk = 256;         // seeds per shared-memory chunk (= scoring CTA size)
+constexpr int kGroup = 32;          // seeds per packed-index group (5 low mantissa bits)
+
+// Small block of device scalars owned by the workspace.
+struct DevScalars {
+    int status;
+    unsigned int flag_count;            // pixels queued for FP64 rescoring in the last pass
+    unsigned long long wref_key;        // ordered-key max of w
+    unsigned long long lam_abs_bits;    // max_i ||sym A_i||_F  (non-negative double bits)
+    unsigned long long lam_min_bits;    // min_i lower bound of lambda_min(sym A_i)
+    double g;                           // dual value
+    double max_rel_err;
+    double dot_gp;                      // <grad f, p> at the last evaluation
+    double sum_v;
+    double min_v;
+    double sy, yy, ss;                  // L-BFGS curvature pair products
+    double gp0;                         // <grad f, p> at the start of a line search
+    unsigned int dual_done;             // block counter of the two-phase dual reduction
+    unsigned int pad0;
+    long long rescored_total;
+};
+
+// Workspace (host struct; device pointers inside).
+struct Workspace {
+    int dim = 0;
+    int max_n = 0;
+    int64_t max_j = 0;
+    int device = 0;
+    int n_pad_max = 0;
+    SeedRec *recs = nullptr;            // [n_pad_max]
+    unsigned long long *moments = nullptr;  // [max_n * K]
+    uint32_t *flags = nullptr;          // [max_j]
+    DevScalars *sc = nullptr;           // device
+    DevScalars *sc_host = nullptr;      // pinned host mirror
+    double *part = nullptr;             // [2 * max_blocks] dual partial sums
+    double *grad = nullptr;             // [max_n] gradient of g~ of the last evaluation
+    // L-BFGS / Lloyd state
+    int hist_cap = 0;
+    double *W = nullptr, *Wt = nullptr, *p = nullptr, *gf = nullptr, *gft = nullptr;
+    double *Wbest = nullptr;
+    double *S = nullptr, *Y = nullptr;  // [hist_cap][max_n]
+    double *alpha = nullptr;            // [hist_cap]
+    double *rho = nullptr;              // [hist_cap]
+    double *X = nullptr;                // [max_n * dim] seed positions for Lloyd
+    double *vbuf = nullptr;             // [max_n]
+    int64_t last_pixels = 0, last_pairs = 0;
+    // optional kernel timing (event pairs around scoring launches)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;  // 2 per recorded launch
+    size_t ev_used = 0;
+    int64_t prof_pairs = 0;
+    int64_t kernel_launches = 0;  // every kernel launched with this workspace
+};
+
+// Grid description passed by value to kernels.
+struct GridDev {
+    int dim;
+    int res[3];
+    double lo[3];
+    double h[3];
+    float h32[3];
+    double cell;  // |P|
+    long long J;
+};
+
+// ----------------------------------------------------------------------------
+// ordered keys for atomic max/min of doubles
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// ----------------------------------------------------------------------------
+// mbarrier + bulk async copy (TMA, non-tensor form), all waits bounded
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared, completion signalled on `bar` (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: returns false (and latches ST_TIMEOUT) after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status,
+                                                  uint32_t limit = (1u << 24)) {
+    for (uint32_t it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(status, ST_TIMEOUT);
+    return false;
+}
+
+// ----------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ----------------------------------------------------------------------------
+constexpr int moment_width(int dim) { return 1 + dim + dim * (dim + 1) / 2; }
+
+// zero the per-evaluation counters and statistics in sc
+cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st);
+// seed records (FP64 x, w; FP32 symmetric A) + stats (max w, max ||A||_F, min lambda bound)
+cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const double *A,
+                             const double *w, Workspace &ws, cudaStream_t st);
+// FP32 scoring fused with the moments; queues near ties; labels optional.
+cudaError_t launch_assign_fp32(const GridDev &g, int n, Workspace &ws, int32_t *labels,
+                               unsigned long long *moments, cudaStream_t st);
+// FP64 rescoring of the queued pixels (labels optional, moments updated).
+cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,
+                                const double *w, Workspace &ws, int32_t *labels,
+                                unsigned long long *moments, cudaStream_t st);
+// dual value / gradient from the moments (outputs optional; scalars also into ws.sc)
+cudaError_t launch_dual(const GridDev &g, int n, const double *x, const double *A, const double *w,
+                        const double *v, const double *p_dir, const unsigned long long *moments,
+                        Workspace &ws, double *g_out, double *grad_out, double *gf_out,
+                        double *err_out, cudaStream_t st);
+// discrete centroids from the moments (empty cells keep x)
+cudaError_t launch_centroids(const GridDev &g, int n, const double *x,
+                             const unsigned long long *moments, double *x_out, cudaStream_t st);
+// L-BFGS helpers
+cudaError_t launch_axpy(int n, const double *a, double t, const double *b, double *out,
+                        cudaStream_t st);
+cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma,
+                                   Workspace &ws, cudaStream_t st);
+cudaError_t launch_lbfgs_push(int n, int slot, Workspace &ws, cudaStream_t st);
+
+}  // namespace apd

@@ -1,0 +1,69 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+symbol include/apd.h declares; host-only entry points and argument checks that
+return before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2403_03571_gb300 import build, capi
+from conftest import ROOT, golden_rows
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.load()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "apd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(apd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(capi.EXPORTED)
+
+
+def test_version_and_strings(lib):
+    assert lib.apd_version() >= 100
+    for code in (0, 1, 2, -1, -2, -3, -4, -5, -6):
+        assert len(capi.status_string(code)) > 0
+
+
+def test_choose_resolution_matches_eq_2_10(lib):
+    for d, n, eps, m in golden_rows("choice_of_m_example.txt"):
+        assert capi.apd_choose_resolution(int(d), 1.0 / int(n), float(eps), 1.0) == int(m)
+    for d in (2, 3):
+        for vmin in (1e-3, 3.7e-4, 2e-5, 0.05):
+            assert capi.apd_choose_resolution(d, vmin, 0.01, 1.0) == oracle.resolution_practical(d, vmin, 0.01)
+    assert capi.apd_choose_resolution(4, 0.1, 0.01, 1.0) == -1
+    assert capi.apd_choose_resolution(2, 0.0, 0.01, 1.0) == -1
+
+
+def test_argument_errors_before_cuda(lib):
+    g = capi.ApdGrid()
+    g.dim = 4
+    s = capi.ApdSeeds()
+    s.n = 3
+    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, None, None, None) == capi.APD_ERR_ARG
+    g.dim = 2
+    g.res[0], g.res[1] = 8, 0
+    g.hi[0], g.hi[1] = 1.0, 1.0
+    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, None, None, None) == capi.APD_ERR_ARG
+    g.res[1] = 8
+    # seeds with null pointers
+    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, ctypes.c_void_p(16), None,
+                          None) == capi.APD_ERR_ARG
+    h = ctypes.c_void_p()
+    assert lib.apd_workspace_create(ctypes.byref(h), 5, 10, 100) == capi.APD_ERR_ARG
+    assert lib.apd_workspace_create(ctypes.byref(h), 2, 0, 100) == capi.APD_ERR_ARG
+    assert lib.apd_workspace_create(None, 2, 10, 100) == capi.APD_ERR_ARG
+    lib.apd_workspace_destroy(None)

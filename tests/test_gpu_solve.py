@@ -1,0 +1,96 @@
+"""Weight solve (Algorithm 2) and Lloyd (Algorithm 3) through the C ABI, judged
+by the FP64 oracle: at the weights the GPU returns, the oracle's own
+evaluation must meet the stop rule max_i |v_i - m_i|P|| / v_i < eps; centroids
+must equal the oracle's discrete centroids at the GPU's (X, W)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_03571_gb300 import synth
+from _gpu import dev, host, instance_tensors, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    require_gpu()
+    from paper_2403_03571_gb300 import capi as c
+    return c
+
+
+def _solve(capi, inst, eps=0.01, ws=None):
+    x, A, w, v = instance_tensors(inst)
+    ws = ws or capi.Workspace(inst.grid.dim, inst.n, inst.grid.num_pixels)
+    w_out = torch.zeros(inst.n, dtype=torch.float64, device="cuda")
+    rc, info = capi.apd_solve_weights(inst.grid, x, A, w, v, w_out, ws, capi.solve_opts(eps=eps))
+    return rc, info, host(w_out)
+
+
+def test_solve_2d_20_seeds_256(capi):
+    inst = synth.workload_2d_20()
+    rc, info, W = _solve(capi, inst)
+    assert rc == capi.APD_OK, info.as_dict()
+    _, _, err = oracle.dual(inst.grid, inst.x, inst.A, W, inst.v)
+    assert err < 0.01
+    assert abs(info.max_rel_err - err) <= 1e-12
+    assert info.evaluations < 200
+
+
+@pytest.mark.parametrize("dim,n,m,seed", [(2, 150, 200, 3), (3, 120, 48, 4)])
+def test_solve_multiphase(capi, dim, n, m, seed):
+    inst = synth.make_instance(dim, n, m, seed)
+    rc, info, W = _solve(capi, inst)
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+    g_w, _, err = oracle.dual(inst.grid, inst.x, inst.A, W, inst.v)
+    assert err < 0.01
+    g_0, _, _ = oracle.dual(inst.grid, inst.x, inst.A, np.zeros(n), inst.v)
+    assert g_w >= g_0
+
+
+def test_lloyd_step_centroids(capi):
+    inst = synth.make_instance(2, 60, 128, 5)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(2, 60, inst.grid.num_pixels)
+    x_out = torch.zeros_like(x)
+    w_out = torch.zeros_like(w)
+    rc, info = capi.apd_lloyd_step(inst.grid, x, A, w, v, x_out, w_out, ws)
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE)
+    W = host(w_out)
+    lab = oracle.assign(inst.grid, inst.x, inst.A, W)
+    ref = oracle.centroids(inst.grid, inst.x, lab)
+    np.testing.assert_allclose(host(x_out), ref, rtol=0, atol=1e-12)
+    _, _, err = oracle.dual(inst.grid, inst.x, inst.A, W, inst.v)
+    assert err < 0.01
+
+
+def test_lloyd_full(capi):
+    inst = synth.make_instance(2, 40, 128, 6)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(2, 40, inst.grid.num_pixels)
+    x_out = torch.zeros_like(x)
+    w_out = torch.zeros_like(w)
+    rc, info = capi.apd_lloyd(inst.grid, x, A, w, v, 3, x_out, w_out, ws)
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+    assert info.solves == 4
+    X, W = host(x_out), host(w_out)
+    _, _, err = oracle.dual(inst.grid, X, inst.A, W, inst.v)
+    assert err < 0.01
+    # X after round k is the centroid of the previous round's diagram: one more
+    # oracle centroid step from (X, W) moves the seeds by less than a cell radius
+    lab = oracle.assign(inst.grid, X, inst.A, W)
+    C = oracle.centroids(inst.grid, X, lab)
+    assert np.max(np.abs(C - X)) < 0.5 * 40 ** -0.5
+
+
+def test_not_converged_reports_best(capi):
+    inst = synth.make_instance(2, 80, 128, 7)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(2, 80, inst.grid.num_pixels)
+    w_out = torch.zeros_like(w)
+    rc, info = capi.apd_solve_weights(inst.grid, x, A, w, v, w_out, ws,
+                                      capi.solve_opts(eps=1e-9, max_evals=15))
+    assert rc == capi.APD_NOT_CONVERGED
+    assert info.evaluations <= 16
+    _, _, err = oracle.dual(inst.grid, inst.x, inst.A, host(w_out), inst.v)
+    assert abs(err - info.max_rel_err) <= 1e-12
