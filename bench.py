@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--mode", default="apd", choices=["apd", "assign"],
+                    help="apd: the full benchmark; assign: only repeated scoring+moments calls "
+                         "(apd_cell_moments) at zero weights, for kernel profiling")
     return ap.parse_args()
 
 
@@ -367,8 +370,41 @@ def run_ours(args):
     return out
 
 
+def run_assign_only(args):
+    """Repeated apd_cell_moments on the workload (inputs resident): one scoring launch,
+    one rescoring launch and three small kernels per call."""
+    import torch
+    from paper_2403_03571_gb300 import build, capi
+    build.build()
+    capi.load()
+    inst, _ = make_instance(args.workload, 0)
+    dim, n, J = inst.grid.dim, inst.n, inst.grid.num_pixels
+    x = torch.from_numpy(inst.x).cuda()
+    A = torch.from_numpy(inst.A).cuda()
+    g = np.random.Generator(np.random.PCG64(5))
+    w = torch.from_numpy(0.3 * g.standard_normal(n) * n ** (-2.0 / dim)).cuda()
+    mom = torch.zeros((n, 1 + dim + dim * (dim + 1) // 2), dtype=torch.int64, device="cuda")
+    ws = capi.Workspace(dim, n, J)
+    for _ in range(args.warmup):
+        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws)
+    torch.cuda.synchronize()
+    ws.profile_read()
+    ws.profile(True)
+    for _ in range(args.steps):
+        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws)
+    assert ws.status() == capi.APD_OK
+    ms, launches, pairs, _ = ws.profile_read()
+    st = ws.last_stats()
+    print(json.dumps({"mode": "assign", "workload": args.workload, "launch_ms": ms / max(1, launches),
+                      "pairs_per_s": pairs / (ms / 1000.0), "rescored_fp64": st.rescored_fp64,
+                      "pixels": st.pixels}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "assign":
+        return run_assign_only(args)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:

@@ -387,35 +387,101 @@ __device__ __forceinline__ double cost64(const double *y, const double *__restri
     return __dsub_rn(q, wi);
 }
 
+// Rescoring of a queued pixel, one warp per pixel, lanes over seeds.
+// Pass 1: FP32 direct-form cost of every seed with y - x formed from FP32
+// high/low splits (error <= 2u |y - x|), and a per-seed rounding bound
+//     E_k = 16 u (sum_ab |A_ab| |d_a| |d_b| + |w'_k| + |C_k|),
+// covering the roundings of d, A, the two 3-term dot products, w' and the final
+// subtraction (about 11 u of them) and the FP64 reference's own error.  The
+// threshold is min_k (C_k + E_k).  Pass 2: every seed with C_k - E_k <= threshold
+// is recomputed in FP64 with the reference arithmetic; the smallest FP64 cost
+// wins, ties to the lowest index.  Any seed left out has an exact cost above the
+// exact minimum by more than the FP64 rounding, so the result equals the FP64
+// argmin over all seeds.
+template <int D>
+__device__ __forceinline__ void cost32_bound(const SeedRec32 &r, const float (&yh)[3], const float (&yl)[3],
+                                             float wrh, float wrl, float &c, float &E) {
+    float d[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) d[a] = (yh[a] - r.xh[a]) + (yl[a] - r.xl[a]);
+    float q, qa;
+    if (D == 3) {
+        const float A00 = r.a[0], A01 = r.a[1], A02 = r.a[2], A11 = r.a[3], A12 = r.a[4], A22 = r.a[5];
+        const float t0 = fmaf(A02, d[2], fmaf(A01, d[1], A00 * d[0]));
+        const float t1 = fmaf(A12, d[2], fmaf(A11, d[1], A01 * d[0]));
+        const float t2 = fmaf(A22, d[2], fmaf(A12, d[1], A02 * d[0]));
+        q = fmaf(d[2], t2, fmaf(d[1], t1, d[0] * t0));
+        const float e0 = fabsf(d[0]), e1 = fabsf(d[1]), e2 = fabsf(d[2]);
+        const float s0 = fmaf(fabsf(A02), e2, fmaf(fabsf(A01), e1, fabsf(A00) * e0));
+        const float s1 = fmaf(fabsf(A12), e2, fmaf(fabsf(A11), e1, fabsf(A01) * e0));
+        const float s2 = fmaf(fabsf(A22), e2, fmaf(fabsf(A12), e1, fabsf(A02) * e0));
+        qa = fmaf(e2, s2, fmaf(e1, s1, e0 * s0));
+    } else {
+        const float A00 = r.a[0], A01 = r.a[1], A11 = r.a[2];
+        const float t0 = fmaf(A01, d[1], A00 * d[0]);
+        const float t1 = fmaf(A11, d[1], A01 * d[0]);
+        q = fmaf(d[1], t1, d[0] * t0);
+        const float e0 = fabsf(d[0]), e1 = fabsf(d[1]);
+        const float s0 = fmaf(fabsf(A01), e1, fabsf(A00) * e0);
+        const float s1 = fmaf(fabsf(A11), e1, fabsf(A01) * e0);
+        qa = fmaf(e1, s1, e0 * s0);
+    }
+    const float wp = (r.wh - wrh) + (r.wl - wrl);
+    c = q - wp;
+    E = 16.f * 5.9604644775390625e-8f * (qa + fabsf(wp) + fabsf(c)) + 1e-37f;
+}
+
 template <int D>
 __global__ void __launch_bounds__(256)
-    rescore_fp64_kernel(const GridDev g, const int n, const double *__restrict__ x,
-                        const double *__restrict__ A, const double *__restrict__ w,
-                        const uint32_t *__restrict__ flags, DevScalars *__restrict__ sc,
-                        unsigned long long *__restrict__ gmom, int32_t *__restrict__ labels) {
+    rescore_kernel(const GridDev g, const int n, const double *__restrict__ x,
+                   const double *__restrict__ A, const double *__restrict__ w,
+                   const SeedRec32 *__restrict__ r32, const uint32_t *__restrict__ flags,
+                   DevScalars *__restrict__ sc, unsigned long long *__restrict__ gmom,
+                   int32_t *__restrict__ labels) {
     constexpr int K = moment_width(D);
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const unsigned count = sc->flag_count;
-    if (warp == 0 && lane == 0 && count) atomicAdd((unsigned long long *)&sc->rescored_total, (unsigned long long)count);
+    if (warp == 0 && lane == 0 && count)
+        atomicAdd((unsigned long long *)&sc->rescored_total, (unsigned long long)count);
+    const double wref = dkey_inv(sc->wref_key);
+    float wrh, wrl;
+    wrh = (float)wref;
+    wrl = (float)(wref - (double)wrh);
     for (unsigned it = warp; it < count; it += nwarps) {
         const long long j = (long long)flags[it];
         int k[3] = {0, 0, 0};
-        long long r = j;
+        long long rr = j;
         double y[D];
+        float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            k[a] = (int)(r % g.res[a]);
-            r /= g.res[a];
+            k[a] = (int)(rr % g.res[a]);
+            rr /= g.res[a];
             y[a] = __dadd_rn(g.lo[a], __dmul_rn((double)k[a] + 0.5, g.h[a]));
+            yh[a] = (float)y[a];
+            yl[a] = (float)(y[a] - (double)yh[a]);
         }
+        // pass 1: threshold = min over seeds of (C + E)
+        float thr = __int_as_float(0x7f800000);
+        for (int s = lane; s < n; s += 32) {
+            float c, E;
+            cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
+            thr = fminf(thr, c + E);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) thr = fminf(thr, __shfl_xor_sync(0xffffffffu, thr, off));
+        // pass 2: FP64 reference cost of the candidates
         double best = __longlong_as_double(0x7ff0000000000000ll);
         int bi = 0x7fffffff;
         for (int s = lane; s < n; s += 32) {
-            const double c = cost64<D>(y, x + (size_t)s * D, A + (size_t)s * D * D, w[s]);
-            if (c < best) {
-                best = c;
+            float c, E;
+            cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
+            if (!(c - E <= thr)) continue;
+            const double c64 = cost64<D>(y, x + (size_t)s * D, A + (size_t)s * D * D, w[s]);
+            if (c64 < best) {
+                best = c64;
                 bi = s;
             }
         }
@@ -431,21 +497,21 @@ __global__ void __launch_bounds__(256)
         if (lane == 0) {
             if (bi < 0 || bi >= n) {
                 atomicOr(&sc->status, ST_BAD_LABEL);
-                continue;
+            } else {
+                if (labels) labels[j] = bi;
+                unsigned long long u[3];
+#pragma unroll
+                for (int a = 0; a < D; ++a) u[a] = 2ull * (unsigned long long)k[a] + 1ull;
+                unsigned long long *o = gmom + (size_t)bi * K;
+                atomicAdd(&o[0], 1ull);
+#pragma unroll
+                for (int a = 0; a < D; ++a) atomicAdd(&o[1 + a], u[a]);
+                int e = 1 + D;
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+#pragma unroll
+                    for (int b = a; b < D; ++b) atomicAdd(&o[e++], u[a] * u[b]);
             }
-            if (labels) labels[j] = bi;
-            unsigned long long u[3];
-#pragma unroll
-            for (int a = 0; a < D; ++a) u[a] = 2ull * (unsigned long long)k[a] + 1ull;
-            unsigned long long *o = gmom + (size_t)bi * K;
-            atomicAdd(&o[0], 1ull);
-#pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(&o[1 + a], u[a]);
-            int e = 1 + D;
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int b = a; b < D; ++b) atomicAdd(&o[e++], u[a] * u[b]);
         }
     }
 }
@@ -487,9 +553,9 @@ cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const 
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ws.device);
     const int blocks = dev_sms * 2;
     if (g.dim == 3)
-        rescore_fp64_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.flags, ws.sc, moments, labels);
+        rescore_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.sc, moments, labels);
     else
-        rescore_fp64_kernel<2><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.flags, ws.sc, moments, labels);
+        rescore_kernel<2><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.sc, moments, labels);
     return cudaGetLastError();
 }
 

@@ -461,6 +461,7 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
         if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
     };
     alloc((void **)&w.recs, (size_t)w.n_pad_max * sizeof(SeedRec));
+    alloc((void **)&w.recs32, (size_t)w.n_pad_max * sizeof(SeedRec32));
     alloc((void **)&w.moments, (size_t)max_n * K * sizeof(unsigned long long));
     alloc((void **)&w.flags, (size_t)max_j * sizeof(uint32_t));
     alloc((void **)&w.sc, sizeof(DevScalars));
@@ -494,7 +495,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -32,6 +32,16 @@ struct __align__(16) SeedRec {
 };
 static_assert(sizeof(SeedRec) == 64, "SeedRec must be 64 bytes");
 
+// Seed record of the FP32 direct-form rescoring pass: x and w split into
+// FP32 high and low parts (x = x_hi + x_lo to ~2^-48 relative), FP32 symmetric A.
+struct __align__(16) SeedRec32 {
+    float xh[3], xl[3];
+    float wh, wl;
+    float a[6];
+    float pad[2];
+};
+static_assert(sizeof(SeedRec32) == 64, "SeedRec32 must be 64 bytes");
+
 constexpr int kChunk = 256;         // seeds per shared-memory chunk (= scoring CTA size)
 constexpr int kGroup = 32;          // seeds per packed-index group (5 low mantissa bits)
 
@@ -62,6 +72,7 @@ struct Workspace {
     int device = 0;
     int n_pad_max = 0;
     SeedRec *recs = nullptr;            // [n_pad_max]
+    SeedRec32 *recs32 = nullptr;        // [n_pad_max]
     unsigned long long *moments = nullptr;  // [max_n * K]
     uint32_t *flags = nullptr;          // [max_j]
     DevScalars *sc = nullptr;           // device

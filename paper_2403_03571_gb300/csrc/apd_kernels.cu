@@ -52,10 +52,48 @@ __global__ void eval_reset_kernel(DevScalars *sc) {
     sc->dual_done = 0u;
 }
 
+// Smallest eigenvalue of a symmetric positive-definite 2x2 or 3x3 matrix (FP64):
+// 2x2 from the characteristic quadratic; 3x3 from the trigonometric solution of
+// the characteristic cubic (shifted by the mean eigenvalue, scaled by the root
+// mean square deviation).  Returned with a small relative safety margin.
+template <int D>
+__device__ double lambda_min_sym(const double (&s)[D][D]) {
+    if (D == 2) {
+        const double m = 0.5 * (s[0][0] + s[1][1]);
+        const double h = 0.5 * (s[0][0] - s[1][1]);
+        const double r = sqrt(h * h + s[0][1] * s[0][1]);
+        // m - r computed as det / (m + r) to avoid cancellation
+        const double det = s[0][0] * s[1][1] - s[0][1] * s[0][1];
+        return (det / (m + r)) * (1.0 - 1e-9);
+    } else {
+        const double p1 = s[0][1] * s[0][1] + s[0][2] * s[0][2] + s[1][2] * s[1][2];
+        const double q = (s[0][0] + s[1][1] + s[2][2]) / 3.0;
+        const double a0 = s[0][0] - q, a1 = s[1][1] - q, a2 = s[2][2] - q;
+        const double p2 = a0 * a0 + a1 * a1 + a2 * a2 + 2.0 * p1;
+        if (!(p2 > 1e-30 * q * q)) return q * (1.0 - 1e-9);  // multiple of the identity
+        const double p = sqrt(p2 / 6.0);
+        const double b00 = a0 / p, b11 = a1 / p, b22 = a2 / p;
+        const double b01 = s[0][1] / p, b02 = s[0][2] / p, b12 = s[1][2] / p;
+        double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                          b02 * (b01 * b12 - b11 * b02));
+        r = fmin(1.0, fmax(-1.0, r));
+        const double phi = acos(r) / 3.0;
+        const double lmin = q + 2.0 * p * cos(phi + 2.0943951023931957);  // + 2 pi / 3
+        // relative and absolute margins cover the rounding of the formula
+        return fmax(lmin * (1.0 - 1e-9) - 1e-12 * q, 0.0);
+    }
+}
+
+__device__ __forceinline__ void split_f32(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 template <int D>
 __global__ void seed_prep_kernel(const int n, const int n_pad, const double *__restrict__ x,
                                  const double *__restrict__ A, const double *__restrict__ w,
-                                 SeedRec *__restrict__ recs, DevScalars *__restrict__ sc) {
+                                 SeedRec *__restrict__ recs, SeedRec32 *__restrict__ recs32,
+                                 DevScalars *__restrict__ sc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     SeedRec r;
 #pragma unroll
@@ -64,6 +102,13 @@ __global__ void seed_prep_kernel(const int n, const int n_pad, const double *__r
 #pragma unroll
     for (int a = 0; a < 6; ++a) r.a[a] = 0.f;
     r.pad[0] = r.pad[1] = 0.f;
+    SeedRec32 r32;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r32.xh[a] = r32.xl[a] = 0.f;
+    r32.wh = r32.wl = 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) r32.a[a] = 0.f;
+    r32.pad[0] = r32.pad[1] = 0.f;
     double wkey_w = -DBL_MAX, frob = 0.0, lam = DBL_MAX;
     bool active = false;
     if (i < n) {
@@ -104,8 +149,7 @@ __global__ void seed_prep_kernel(const int n, const int n_pad, const double *__r
 #pragma unroll
             for (int b = 0; b < D; ++b) f2 += s[a][b] * s[a][b];
         frob = sqrt(f2);
-        // lambda_min >= det / lambda_max^(D-1) >= det / ||A||_F^(D-1)
-        lam = spd ? (D == 2 ? det / frob : det / f2) : 0.0;
+        lam = spd ? lambda_min_sym<D>(s) : 0.0;
         if (!finite) atomicOr(&sc->status, ST_NONFINITE);
         else if (!spd) atomicOr(&sc->status, ST_NOT_SPD);
         if (!finite) {
@@ -128,8 +172,16 @@ __global__ void seed_prep_kernel(const int n, const int n_pad, const double *__r
             r.a[5] = (float)s[2][2];
         }
         wkey_w = finite ? wi : -DBL_MAX;
+#pragma unroll
+        for (int a = 0; a < D; ++a) split_f32(xx[a], r32.xh[a], r32.xl[a]);
+        split_f32(wi, r32.wh, r32.wl);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) r32.a[a] = r.a[a];
     }
-    if (i < n_pad) recs[i] = r;
+    if (i < n_pad) {
+        recs[i] = r;
+        recs32[i] = r32;
+    }
     // one atomic per warp for each statistic
     const double wmax = warp_max(active ? wkey_w : -DBL_MAX);
     const double fmx = warp_max(active ? frob : 0.0);
@@ -351,9 +403,9 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
     const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
     const int blocks = (n_pad + 255) / 256;
     if (g.dim == 3)
-        seed_prep_kernel<3><<<blocks, 256, 0, st>>>(n, n_pad, x, A, w, ws.recs, ws.sc);
+        seed_prep_kernel<3><<<blocks, 256, 0, st>>>(n, n_pad, x, A, w, ws.recs, ws.recs32, ws.sc);
     else
-        seed_prep_kernel<2><<<blocks, 256, 0, st>>>(n, n_pad, x, A, w, ws.recs, ws.sc);
+        seed_prep_kernel<2><<<blocks, 256, 0, st>>>(n, n_pad, x, A, w, ws.recs, ws.recs32, ws.sc);
     return cudaGetLastError();
 }
 
