@@ -193,6 +193,27 @@ int apd_profile_enable(apd_workspace *ws, int32_t enable);
 int apd_profile_read(apd_workspace *ws, double *assign_ms, int64_t *launches, int64_t *pairs,
                      int64_t *kernel_launches);
 
+/* apd_cell_moments without a workspace, for callers that cannot allocate device
+ * memory (a device-memory budget fixed at start-up, a host framework whose
+ * allocator owns all device memory, or a latency-critical loop that cannot take
+ * the implicit synchronisation of cudaMalloc).  The paper has no counterpart:
+ * this is a library convenience.
+ *   - Same result as apd_cell_moments with APD_FP32: moments int64 device
+ *     [n][APD_MOMENT_WIDTH(dim)], overwritten.
+ *   - Scratch is one static device array per GPU (about 8.5 MiB, held by every
+ *     GPU that loads the library until exit); the call allocates nothing.
+ *   - Limits: n <= 4096 seeds and J <= 2,097,152 pixels; larger sizes return
+ *     APD_ERR_WORKSPACE before any work is queued.
+ *   - The first call on a device looks up the array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU race on it.  Each
+ *     call clears what must start at zero; the array keeps the last call's data.
+ *   - Host-synchronous: synchronises `stream` and returns the device-side status
+ *     (APD_OK, APD_ERR_ARG for non-finite input, APD_ERR_NOT_SPD, APD_ERR_TIMEOUT),
+ *     or APD_ERR_ARG / APD_ERR_WORKSPACE / APD_ERR_CUDA. */
+int apd_cell_moments_noalloc(const apd_grid *grid, const apd_seeds *seeds, int64_t *moments,
+                             apd_stream_t stream);
+
 /* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
  * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).
  * Returns M >= 1, or -1 for invalid arguments. */

@@ -34,6 +34,7 @@ EXPORTED = (
     "apd_assign", "apd_cell_moments", "apd_dual_value_grad", "apd_solve_opts_default",
     "apd_solve_weights", "apd_lloyd_step", "apd_lloyd", "apd_choose_resolution",
     "apd_status_string", "apd_version", "apd_profile_enable", "apd_profile_read",
+    "apd_cell_moments_noalloc",
 )
 
 
@@ -112,6 +113,7 @@ def load(path: Optional[str] = None):
     L.apd_status_string.restype = ctypes.c_char_p
     L.apd_version.restype = ctypes.c_int32
     L.apd_profile_enable.argtypes = [_vp, ctypes.c_int32]
+    L.apd_cell_moments_noalloc.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp]
     L.apd_profile_read.argtypes = [_vp, _P(ctypes.c_double), _P(ctypes.c_int64), _P(ctypes.c_int64),
                                    _P(ctypes.c_int64)]
     _lib = L
@@ -221,6 +223,14 @@ def apd_dual_value_grad(grid, x, A, w, v, g_out, grad, err_out, ws: Workspace, p
     return _check(load().apd_dual_value_grad(ctypes.byref(g), ctypes.byref(s), _ptr(v), precision,
                                              _ptr(g_out), _ptr(grad), _ptr(err_out), ws.handle,
                                              _stream(stream)), "apd_dual_value_grad")
+
+
+def apd_cell_moments_noalloc(grid, x, A, w, moments, stream=None):
+    """Per-cell moments without a workspace (static device scratch; for callers that
+    cannot allocate device memory).  Returns the C status code unchanged."""
+    g, s = make_grid(grid), make_seeds(x, A, w)
+    return load().apd_cell_moments_noalloc(ctypes.byref(g), ctypes.byref(s), _ptr(moments),
+                                           _stream(stream))
 
 
 def solve_opts(eps=0.01, max_evals=1000, history=10, precision=APD_FP32, check_volumes=1):
