@@ -77,6 +77,54 @@ __device__ __forceinline__ float pack(float c, unsigned idx) {
     return __uint_as_float((__float_as_uint(c) & ~31u) | idx);
 }
 
+// Row coefficients of two consecutive seeds (see the file comment), returned as
+// duplicated pairs for the packed pixel-pair FMAs.  Every multiply is rounded on
+// its own (no contraction), so the fast and update passes compute identical bits.
+template <int D>
+__device__ __forceinline__ void seed_pair_coeffs(const float4 (*phi)[kChunk], int s0, float f1, float f2,
+                                                 float2 &qa, float2 &qb, float2 &ba, float2 &bbb,
+                                                 float2 &aa2, float2 &ab2) {
+    float a[2], bb[2], q00[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float4 v0 = phi[0][s0 + e];
+        const float4 v1 = phi[1][s0 + e];
+        if (D == 3) {
+            const float4 v2 = phi[2][s0 + e];
+            const float d1 = __fsub_rn(f1, v0.x);
+            const float d2 = __fsub_rn(f2, v0.y);
+            const float e0 = fmaf(v1.z, d2, __fmul_rn(v1.y, d1));
+            bb[e] = fmaf(2.f, e0, v1.w);
+            const float t = fmaf(v0.w, d2, __fmul_rn(v0.z, d1));
+            float aa = fmaf(d1, t, v2.x);
+            aa = fmaf(v2.y, e0, aa);
+            a[e] = fmaf(__fmul_rn(v1.x, d2), d2, aa);
+            q00[e] = v2.z;
+        } else {
+            const float d1 = __fsub_rn(f1, v0.x);
+            const float u1 = fmaf(v0.y, d1, v0.z);
+            a[e] = fmaf(d1, u1, v0.w);
+            bb[e] = fmaf(v1.y, d1, v1.x);
+            q00[e] = v1.z;
+        }
+    }
+    qa = make_float2(q00[0], q00[0]);
+    qb = make_float2(q00[1], q00[1]);
+    ba = make_float2(bb[0], bb[0]);
+    bbb = make_float2(bb[1], bb[1]);
+    aa2 = make_float2(a[0], a[0]);
+    ab2 = make_float2(a[1], a[1]);
+}
+
+// Two new packed keys into the top-2 (b1 <= b2) of one pixel; gi follows b1.
+__device__ __forceinline__ void top2_update(float &b1, float &b2, int &gi, float ka, float kb, int gbase) {
+    const float mn = fminf(ka, kb), mx = fmaxf(ka, kb);
+    const bool lt = mn < b1;
+    b2 = fmin3(b2, fmaxf(b1, mn), mx);
+    b1 = fminf(b1, mn);
+    gi = lt ? (gbase | (int)(__float_as_uint(mn) & 31u)) : gi;
+}
+
 template <int D>
 struct SharedLayout {
     static constexpr int K = moment_width(D);
@@ -85,6 +133,7 @@ struct SharedLayout {
     unsigned long long tval[kTable][K];
     int tkey[kTable];
     uint64_t bar[2];
+    int start_chunk;
 };
 
 template <int D>
@@ -138,7 +187,8 @@ __device__ __forceinline__ void flush_run(SharedLayout<D> &sm, unsigned long lon
 template <int D>
 __global__ void __launch_bounds__(256, 2)
     assign_fp32_kernel(const GridDev g, const int n, const int n_chunks, const float R_tile,
-                       const SeedRec *__restrict__ recs, unsigned long long *__restrict__ gmom,
+                       const SeedRec *__restrict__ recs, const uint32_t *__restrict__ scodes,
+                       const int32_t *__restrict__ perm, unsigned long long *__restrict__ gmom,
                        uint32_t *__restrict__ flags, int32_t *__restrict__ labels,
                        DevScalars *__restrict__ sc) {
     using C = Cfg<D>;
@@ -181,18 +231,45 @@ __global__ void __launch_bounds__(256, 2)
         fence_mbar_init();
     }
     __syncthreads();
+    // Scan order of the seed chunks: with Morton-sorted seeds, start at the chunk
+    // holding this tile's Morton position and zig-zag outwards, so that the near
+    // seeds (the likely winners) come first and later groups are mostly skipped.
+    if (tid == 0) {
+        int start = 0;
+        if (scodes) {
+            double frac[3] = {0.0, 0.0, 0.0};
+            const int kc[3] = {k0b + P / 2, k1b + TY / 2, k2b + C::TZ / 2};
+#pragma unroll
+            for (int a = 0; a < D; ++a) frac[a] = ((double)kc[a] + 0.5) / (double)g.res[a];
+            const uint32_t code = morton_code(D, frac);
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (scodes[mid] < code) lo = mid + 1;
+                else hi = mid;
+            }
+            start = min(lo / kChunk, n_chunks - 1);
+        }
+        sm.start_chunk = start;
+    }
+    __syncthreads();
+    const int start_chunk = sm.start_chunk;
+    auto chunk_at = [&](int k) {
+        const int off = (k & 1) ? ((k + 1) >> 1) : -(k >> 1);
+        int c = (start_chunk + off) % n_chunks;
+        return c < 0 ? c + n_chunks : c;
+    };
     const double wref = dkey_inv(sc->wref_key);
     if (tid == 0) {
-        for (int c = 0; c < 2 && c < n_chunks; ++c) {
-            mbar_expect_tx(&sm.bar[c], kChunk * sizeof(SeedRec));
-            bulk_g2s(&sm.raw[c][0], recs + (size_t)c * kChunk, kChunk * sizeof(SeedRec), &sm.bar[c]);
+        for (int k = 0; k < 2 && k < n_chunks; ++k) {
+            mbar_expect_tx(&sm.bar[k], kChunk * sizeof(SeedRec));
+            bulk_g2s(&sm.raw[k][0], recs + (size_t)chunk_at(k) * kChunk, kChunk * sizeof(SeedRec),
+                     &sm.bar[k]);
         }
     }
 
-    // per pixel: two smallest packed costs (b1 <= b2), index of the best, and b1 at
-    // the start of the current 32-seed group (a change of b1 inside the group
-    // means the new best lies in this group and its local index is in b1's low bits)
-    float b1[P], b2[P], b1s[P];
+    // per pixel: two smallest packed costs (b1 <= b2) and the scan position of the best
+    float b1[P], b2[P];
     int GI[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -202,9 +279,10 @@ __global__ void __launch_bounds__(256, 2)
     }
     bool ok = true;
 
-    for (int c = 0; c < n_chunks; ++c) {
-        const int b = c & 1;
-        if (!mbar_wait_bounded(&sm.bar[b], (uint32_t)((c >> 1) & 1), &sc->status)) ok = false;
+    for (int k = 0; k < n_chunks; ++k) {
+        const int b = k & 1;
+        const int c = chunk_at(k);
+        if (!mbar_wait_bounded(&sm.bar[b], (uint32_t)((k >> 1) & 1), &sc->status)) ok = false;
         // transform this chunk: one seed per thread
         {
             const int s = c * kChunk + tid;
@@ -243,76 +321,61 @@ __global__ void __launch_bounds__(256, 2)
             if (D == 3) sm.phi[2][tid] = v2;
         }
         __syncthreads();
-        if (tid == 0 && ok && c + 2 < n_chunks) {
+        if (tid == 0 && ok && k + 2 < n_chunks) {
             mbar_expect_tx(&sm.bar[b], kChunk * sizeof(SeedRec));
-            bulk_g2s(&sm.raw[b][0], recs + (size_t)(c + 2) * kChunk, kChunk * sizeof(SeedRec),
+            bulk_g2s(&sm.raw[b][0], recs + (size_t)chunk_at(k + 2) * kChunk, kChunk * sizeof(SeedRec),
                      &sm.bar[b]);
         }
         if (ok) {
             const int valid_in_chunk = min(kChunk, n - c * kChunk);
             const int groups = (valid_in_chunk + kGroup - 1) / kGroup;
             for (int gr = 0; gr < groups; ++gr) {
+                // fast pass: smallest cost of this group per pixel (one 3-input min per two pairs)
+                float gm[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) b1s[p] = b1[p];
+                for (int p = 0; p < P; ++p) gm[p] = FLT_MAX;
 #pragma unroll 2
                 for (int l = 0; l < kGroup; l += 2) {
-                    const int s0 = gr * kGroup + l;
-                    float a[2], bb[2], q00[2];
+                    float2 qa, qb, ba, bbb, aa2, ab2;
+                    seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const float4 v0 = sm.phi[0][s0 + e];
-                        const float4 v1 = sm.phi[1][s0 + e];
-                        if (D == 3) {
-                            const float4 v2 = sm.phi[2][s0 + e];
-                            const float d1 = f1 - v0.x;
-                            const float d2 = f2 - v0.y;
-                            float e0 = v1.y * d1;
-                            e0 = fmaf(v1.z, d2, e0);
-                            bb[e] = fmaf(2.f, e0, v1.w);
-                            float t = v0.z * d1;
-                            t = fmaf(v0.w, d2, t);
-                            float aa = fmaf(d1, t, v2.x);
-                            aa = fmaf(v2.y, e0, aa);
-                            const float s22 = v1.x * d2;
-                            a[e] = fmaf(s22, d2, aa);
-                            q00[e] = v2.z;
-                        } else {
-                            const float d1 = f1 - v0.x;
-                            const float u1 = fmaf(v0.y, d1, v0.z);
-                            a[e] = fmaf(d1, u1, v0.w);
-                            bb[e] = fmaf(v1.y, d1, v1.x);
-                            q00[e] = v1.z;
-                        }
+                    for (int q = 0; q < P / 2; ++q) {
+                        const float2 ca = ffma2(ffma2(qa, y2[q], ba), y2[q], aa2);
+                        const float2 cb = ffma2(ffma2(qb, y2[q], bbb), y2[q], ab2);
+                        gm[2 * q] = fmin3(gm[2 * q], ca.x, cb.x);
+                        gm[2 * q + 1] = fmin3(gm[2 * q + 1], ca.y, cb.y);
                     }
-                    const float2 qa = make_float2(q00[0], q00[0]), qb = make_float2(q00[1], q00[1]);
-                    const float2 ba = make_float2(bb[0], bb[0]), bbb = make_float2(bb[1], bb[1]);
-                    const float2 aa2 = make_float2(a[0], a[0]), ab2 = make_float2(a[1], a[1]);
+                }
+                // a packed key differs from its cost by < 32 ulp: a group whose smallest
+                // cost exceeds b2 by the margin cannot change b1 or b2 and is skipped
+                bool need = false;
+#pragma unroll
+                for (int p = 0; p < P; ++p) need |= gm[p] < fmaf(fabsf(b2[p]), 0x1p-15f, b2[p]);
+                if (!__any_sync(0xffffffffu, need)) continue;
+                // update pass: recompute the same costs, packed top-2 with the index
+                const int gbase = c * kChunk + gr * kGroup;
+#pragma unroll 2
+                for (int l = 0; l < kGroup; l += 2) {
+                    float2 qa, qb, ba, bbb, aa2, ab2;
+                    seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
                     const unsigned la = (unsigned)l, lb = (unsigned)(l + 1);
 #pragma unroll
                     for (int q = 0; q < P / 2; ++q) {
                         const float2 ca = ffma2(ffma2(qa, y2[q], ba), y2[q], aa2);
                         const float2 cb = ffma2(ffma2(qb, y2[q], bbb), y2[q], ab2);
-                        {
-                            const float ka = pack(ca.x, la), kb = pack(cb.x, lb);
-                            const float mn = fminf(ka, kb), mx = fmaxf(ka, kb);
-                            b2[2 * q] = fmin3(b2[2 * q], fmaxf(b1[2 * q], mn), mx);
-                            b1[2 * q] = fminf(b1[2 * q], mn);
-                        }
-                        {
-                            const float ka = pack(ca.y, la), kb = pack(cb.y, lb);
-                            const float mn = fminf(ka, kb), mx = fmaxf(ka, kb);
-                            b2[2 * q + 1] = fmin3(b2[2 * q + 1], fmaxf(b1[2 * q + 1], mn), mx);
-                            b1[2 * q + 1] = fminf(b1[2 * q + 1], mn);
-                        }
+                        top2_update(b1[2 * q], b2[2 * q], GI[2 * q], pack(ca.x, la), pack(cb.x, lb), gbase);
+                        top2_update(b1[2 * q + 1], b2[2 * q + 1], GI[2 * q + 1], pack(ca.y, la),
+                                    pack(cb.y, lb), gbase);
                     }
                 }
-                const int gbase = c * kChunk + gr * kGroup;
-#pragma unroll
-                for (int p = 0; p < P; ++p)
-                    GI[p] = (b1[p] != b1s[p]) ? (gbase | (int)(__float_as_uint(b1[p]) & 31u)) : GI[p];
             }
         }
         __syncthreads();
+    }
+    // scan position -> seed index
+    if (perm && ok) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) GI[p] = GI[p] < n ? perm[GI[p]] : GI[p];
     }
 
     // flag near ties, write labels, accumulate moments
@@ -533,8 +596,9 @@ cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t
     const int n_chunks = (n + kChunk - 1) / kChunk;
     double hx = 0.5 * C::P * g.h[0], hy = 0.5 * C::TY * g.h[1], hz = D == 3 ? 0.5 * C::TZ * g.h[2] : 0.0;
     const float R = (float)(sqrt(hx * hx + hy * hy + hz * hz) * (1.0 + 1e-6));
-    assign_fp32_kernel<D><<<grid, C::TY * C::TZ, smem, st>>>(g, n, n_chunks, R, ws.recs, gmom, ws.flags,
-                                                             labels, ws.sc);
+    assign_fp32_kernel<D><<<grid, C::TY * C::TZ, smem, st>>>(
+        g, n, n_chunks, R, ws.recs, ws.sorted ? ws.scodes : nullptr, ws.sorted ? ws.perm : nullptr, gmom,
+        ws.flags, labels, ws.sc);
     return cudaGetLastError();
 }
 

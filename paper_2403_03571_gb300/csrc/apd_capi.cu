@@ -110,7 +110,7 @@ int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, co
     APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
     if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
     APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
-    ws.kernel_launches += 4;
+    ws.kernel_launches += ws.sorted ? 6 : 4;
     ws.last_pixels = g.J;
     ws.last_pairs = g.J * (long long)n;
     return APD_OK;
@@ -462,6 +462,12 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     };
     alloc((void **)&w.recs, (size_t)w.n_pad_max * sizeof(SeedRec));
     alloc((void **)&w.recs32, (size_t)w.n_pad_max * sizeof(SeedRec32));
+    if (w.n_pad_max <= kSortMax) {
+        alloc((void **)&w.recs_tmp, (size_t)w.n_pad_max * sizeof(SeedRec));
+        alloc((void **)&w.codes, (size_t)w.n_pad_max * sizeof(uint32_t));
+        alloc((void **)&w.scodes, (size_t)w.n_pad_max * sizeof(uint32_t));
+        alloc((void **)&w.perm, (size_t)w.n_pad_max * sizeof(int32_t));
+    }
     alloc((void **)&w.moments, (size_t)max_n * K * sizeof(unsigned long long));
     alloc((void **)&w.flags, (size_t)max_j * sizeof(uint32_t));
     alloc((void **)&w.sc, sizeof(DevScalars));
@@ -495,7 +501,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.recs32, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -43,6 +43,7 @@ struct __align__(16) SeedRec32 {
 static_assert(sizeof(SeedRec32) == 64, "SeedRec32 must be 64 bytes");
 
 constexpr int kChunk = 256;         // seeds per shared-memory chunk (= scoring CTA size)
+constexpr int kSortMax = 16384;     // largest padded seed count ordered on the device
 constexpr int kGroup = 32;          // seeds per packed-index group (5 low mantissa bits)
 
 // Small block of device scalars owned by the workspace.
@@ -73,6 +74,12 @@ struct Workspace {
     int n_pad_max = 0;
     SeedRec *recs = nullptr;            // [n_pad_max]
     SeedRec32 *recs32 = nullptr;        // [n_pad_max]
+    // Morton ordering of the seeds for the scoring scan (null: natural order)
+    SeedRec *recs_tmp = nullptr;        // [n_pad_max] records in natural order
+    uint32_t *codes = nullptr;          // [n_pad_max] Morton codes, natural order
+    uint32_t *scodes = nullptr;         // [n_pad_max] sorted codes
+    int32_t *perm = nullptr;            // [n_pad_max] scan position -> seed index
+    bool sorted = false;                // set by launch_seed_prep for the current pass
     unsigned long long *moments = nullptr;  // [max_n * K]
     uint32_t *flags = nullptr;          // [max_j]
     DevScalars *sc = nullptr;           // device
@@ -118,6 +125,43 @@ __device__ __forceinline__ unsigned long long dkey(double v) {
 __device__ __forceinline__ double dkey_inv(unsigned long long k) {
     unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
     return __longlong_as_double((long long)b);
+}
+
+// ----------------------------------------------------------------------------
+// Morton (Z-order) codes on the grid box, 10 bits per axis in 3D, 15 in 2D
+// ----------------------------------------------------------------------------
+__host__ __device__ inline uint32_t spread3_10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ inline uint32_t spread2_15(uint32_t v) {
+    v &= 0x7fffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+// frac: position in [0, 1) of the box per axis
+__host__ __device__ inline uint32_t morton_code(int dim, const double *frac) {
+    if (dim == 3) {
+        uint32_t q[3];
+        for (int a = 0; a < 3; ++a) {
+            double f = frac[a] * 1024.0;
+            q[a] = f <= 0.0 ? 0u : (f >= 1023.0 ? 1023u : (uint32_t)f);
+        }
+        return spread3_10(q[0]) | (spread3_10(q[1]) << 1) | (spread3_10(q[2]) << 2);
+    }
+    uint32_t q[2];
+    for (int a = 0; a < 2; ++a) {
+        double f = frac[a] * 32768.0;
+        q[a] = f <= 0.0 ? 0u : (f >= 32767.0 ? 32767u : (uint32_t)f);
+    }
+    return spread2_15(q[0]) | (spread2_15(q[1]) << 1);
 }
 
 // ----------------------------------------------------------------------------

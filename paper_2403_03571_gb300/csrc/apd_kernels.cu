@@ -90,9 +90,10 @@ __device__ __forceinline__ void split_f32(double v, float &hi, float &lo) {
 }
 
 template <int D>
-__global__ void seed_prep_kernel(const int n, const int n_pad, const double *__restrict__ x,
-                                 const double *__restrict__ A, const double *__restrict__ w,
-                                 SeedRec *__restrict__ recs, SeedRec32 *__restrict__ recs32,
+__global__ void seed_prep_kernel(const GridDev g, const int n, const int n_pad,
+                                 const double *__restrict__ x, const double *__restrict__ A,
+                                 const double *__restrict__ w, SeedRec *__restrict__ recs,
+                                 SeedRec32 *__restrict__ recs32, uint32_t *__restrict__ codes,
                                  DevScalars *__restrict__ sc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     SeedRec r;
@@ -181,6 +182,16 @@ __global__ void seed_prep_kernel(const int n, const int n_pad, const double *__r
     if (i < n_pad) {
         recs[i] = r;
         recs32[i] = r32;
+        if (codes) {
+            uint32_t code = 0xffffffffu;  // padding sorts last
+            if (i < n) {
+                double frac[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int a = 0; a < D; ++a) frac[a] = (r.x[a] - g.lo[a]) / ((double)g.res[a] * g.h[a]);
+                code = morton_code(D, frac);
+            }
+            codes[i] = code;
+        }
     }
     // one atomic per warp for each statistic
     const double wmax = warp_max(active ? wkey_w : -DBL_MAX);
@@ -192,6 +203,45 @@ __global__ void seed_prep_kernel(const int n, const int n_pad, const double *__r
         atomicMax(&sc->lam_abs_bits, (unsigned long long)__double_as_longlong(fmx));
         atomicMin(&sc->lam_min_bits, (unsigned long long)__double_as_longlong(lmn));
     }
+}
+
+// Bitonic sort of (Morton code, seed index) pairs in shared memory, one block;
+// the pair order is total, so the result is deterministic.  m = power of two.
+__global__ void __launch_bounds__(1024)
+    morton_sort_kernel(const int n_pad, const int m, const uint32_t *__restrict__ codes,
+                       uint32_t *__restrict__ scodes, int32_t *__restrict__ perm) {
+    extern __shared__ unsigned long long keys[];  // (code << 32) | index
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const uint32_t c = i < n_pad ? codes[i] : 0xffffffffu;
+        keys[i] = ((unsigned long long)c << 32) | (unsigned)i;
+    }
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = keys[i], b = keys[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n_pad; i += blockDim.x) {
+        scodes[i] = (uint32_t)(keys[i] >> 32);
+        perm[i] = (int32_t)(keys[i] & 0xffffffffu);
+    }
+}
+
+__global__ void gather_recs_kernel(const int n_pad, const int32_t *__restrict__ perm,
+                                   const SeedRec *__restrict__ src, SeedRec *__restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_pad) dst[i] = src[perm[i]];
 }
 
 // Per-cell dual terms from the integer moments, then a deterministic two-phase
@@ -402,10 +452,28 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
                              const double *w, Workspace &ws, cudaStream_t st) {
     const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
     const int blocks = (n_pad + 255) / 256;
+    int m = 1;
+    while (m < n_pad) m <<= 1;
+    // Morton order for the scoring scan when the workspace has the buffers
+    ws.sorted = ws.recs_tmp && ws.codes && ws.scodes && ws.perm && m <= kSortMax;
+    SeedRec *dst = ws.sorted ? ws.recs_tmp : ws.recs;
+    uint32_t *codes = ws.sorted ? ws.codes : nullptr;
     if (g.dim == 3)
-        seed_prep_kernel<3><<<blocks, 256, 0, st>>>(n, n_pad, x, A, w, ws.recs, ws.recs32, ws.sc);
+        seed_prep_kernel<3><<<blocks, 256, 0, st>>>(g, n, n_pad, x, A, w, dst, ws.recs32, codes, ws.sc);
     else
-        seed_prep_kernel<2><<<blocks, 256, 0, st>>>(n, n_pad, x, A, w, ws.recs, ws.recs32, ws.sc);
+        seed_prep_kernel<2><<<blocks, 256, 0, st>>>(g, n, n_pad, x, A, w, dst, ws.recs32, codes, ws.sc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !ws.sorted) return e;
+    const size_t smem = (size_t)m * sizeof(unsigned long long);
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(morton_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kSortMax * sizeof(unsigned long long)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    morton_sort_kernel<<<1, 1024, smem, st>>>(n_pad, m, ws.codes, ws.scodes, ws.perm);
+    gather_recs_kernel<<<blocks, 256, 0, st>>>(n_pad, ws.perm, ws.recs_tmp, ws.recs);
     return cudaGetLastError();
 }
 
