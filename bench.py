@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_tf32", "tc_bf16"],
+                    help="scoring arithmetic of the timed path")
     ap.add_argument("--mode", default="apd", choices=["apd", "assign"],
                     help="apd: the full benchmark; assign: only repeated scoring+moments calls "
                          "(apd_cell_moments) at zero weights, for kernel profiling")
@@ -394,6 +396,10 @@ def run_ours(args):
     return out
 
 
+def precision_code(capi, name):
+    return {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32, "tc_bf16": capi.APD_TC_BF16}[name]
+
+
 def run_assign_only(args):
     """Repeated apd_cell_moments on the workload (inputs resident): one scoring launch,
     one rescoring launch and three small kernels per call."""
@@ -409,17 +415,19 @@ def run_assign_only(args):
     w = torch.from_numpy(0.3 * g.standard_normal(n) * n ** (-2.0 / dim)).cuda()
     mom = torch.zeros((n, 1 + dim + dim * (dim + 1) // 2), dtype=torch.int64, device="cuda")
     ws = capi.Workspace(dim, n, J)
+    prec = precision_code(capi, args.precision)
     for _ in range(args.warmup):
-        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws)
+        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=prec)
     torch.cuda.synchronize()
     ws.profile_read()
     ws.profile(True)
     for _ in range(args.steps):
-        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws)
+        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=prec)
     assert ws.status() == capi.APD_OK
     ms, launches, pairs, _ = ws.profile_read()
     st = ws.last_stats()
-    print(json.dumps({"mode": "assign", "workload": args.workload, "launch_ms": ms / max(1, launches),
+    print(json.dumps({"mode": "assign", "workload": args.workload, "precision": args.precision,
+                      "launch_ms": ms / max(1, launches),
                       "pairs_per_s": pairs / (ms / 1000.0), "rescored_fp64": st.rescored_fp64,
                       "pixels": st.pixels}))
     return 0

@@ -214,6 +214,15 @@ int apd_profile_read(apd_workspace *ws, double *assign_ms, int64_t *launches, in
 int apd_cell_moments_noalloc(const apd_grid *grid, const apd_seeds *seeds, int64_t *moments,
                              apd_stream_t stream);
 
+/* Diagnostic of the tensor-core (tcgen05) plumbing: one 128 x 128 x 16 MMA on
+ * integer-valued operands (exact in TF32 and BF16) from shared memory into
+ * tensor memory, compared element by element with CUDA-core dot products.
+ * kind: 0 = TF32, 1 = BF16; variant: 0 = the operand layout the library uses,
+ * 1 = leading and stride offsets exchanged (expected to fail).  Writes the
+ * number of mismatching accumulator elements and the largest absolute error
+ * (host pointers).  Host-synchronous; runs on the current device. */
+int apd_tensor_core_check(int32_t kind, int32_t variant, int32_t *mismatches, float *max_err);
+
 /* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
  * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).
  * Returns M >= 1, or -1 for invalid arguments. */

@@ -34,7 +34,7 @@ EXPORTED = (
     "apd_assign", "apd_cell_moments", "apd_dual_value_grad", "apd_solve_opts_default",
     "apd_solve_weights", "apd_lloyd_step", "apd_lloyd", "apd_choose_resolution",
     "apd_status_string", "apd_version", "apd_profile_enable", "apd_profile_read",
-    "apd_cell_moments_noalloc",
+    "apd_cell_moments_noalloc", "apd_tensor_core_check",
 )
 
 
@@ -114,6 +114,8 @@ def load(path: Optional[str] = None):
     L.apd_version.restype = ctypes.c_int32
     L.apd_profile_enable.argtypes = [_vp, ctypes.c_int32]
     L.apd_cell_moments_noalloc.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp]
+    L.apd_tensor_core_check.argtypes = [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32),
+                                        _P(ctypes.c_float)]
     L.apd_profile_read.argtypes = [_vp, _P(ctypes.c_double), _P(ctypes.c_int64), _P(ctypes.c_int64),
                                    _P(ctypes.c_int64)]
     _lib = L
@@ -231,6 +233,13 @@ def apd_cell_moments_noalloc(grid, x, A, w, moments, stream=None):
     g, s = make_grid(grid), make_seeds(x, A, w)
     return load().apd_cell_moments_noalloc(ctypes.byref(g), ctypes.byref(s), _ptr(moments),
                                            _stream(stream))
+
+
+def apd_tensor_core_check(kind: int, variant: int = 0):
+    """(status, mismatching elements, max abs error) of the tcgen05 self-check."""
+    mm, err = ctypes.c_int32(), ctypes.c_float()
+    rc = load().apd_tensor_core_check(int(kind), int(variant), ctypes.byref(mm), ctypes.byref(err))
+    return rc, mm.value, err.value
 
 
 def solve_opts(eps=0.01, max_evals=1000, history=10, precision=APD_FP32, check_volumes=1):

@@ -89,7 +89,7 @@ int cuda_ok(cudaError_t e) { return e == cudaSuccess ? APD_OK : APD_ERR_CUDA; }
 int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, const double *w,
                    apd_precision prec, Workspace &ws, int32_t *labels, unsigned long long *mom,
                    cudaStream_t st) {
-    if (prec != APD_FP32) return APD_ERR_UNSUPPORTED;
+    if (prec != APD_FP32 && prec != APD_TC_TF32 && prec != APD_TC_BF16) return APD_ERR_UNSUPPORTED;
     const size_t K = (size_t)moment_width(g.dim);
     APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
     APD_TRY(cuda_ok(launch_eval_reset(ws, st)));
@@ -107,10 +107,15 @@ int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, co
         ws.prof_pairs += g.J * (long long)n;
         APD_TRY(cuda_ok(cudaEventRecord(e0, st)));
     }
-    APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
+    // the tensor-core tiling needs per-tile scratch; grids too thin for the
+    // workspace's tile capacity are scored by the FP32 kernel (same labels)
+    if (prec == APD_FP32 || tc_tile_count(g) > ws.tc_tile_cap)
+        APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
+    else
+        APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
     if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
     APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
-    ws.kernel_launches += ws.sorted ? 6 : 4;
+    ws.kernel_launches += (ws.sorted ? 6 : 4) + (prec == APD_FP32 ? 0 : 2);
     ws.last_pixels = g.J;
     ws.last_pairs = g.J * (long long)n;
     return APD_OK;
@@ -467,10 +472,16 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
         alloc((void **)&w.codes, (size_t)w.n_pad_max * sizeof(uint32_t));
         alloc((void **)&w.scodes, (size_t)w.n_pad_max * sizeof(uint32_t));
         alloc((void **)&w.perm, (size_t)w.n_pad_max * sizeof(int32_t));
+        alloc((void **)&w.recs32s, (size_t)w.n_pad_max * sizeof(SeedRec32));
     }
     alloc((void **)&w.moments, (size_t)max_n * K * sizeof(unsigned long long));
     alloc((void **)&w.flags, (size_t)max_j * sizeof(uint32_t));
     alloc((void **)&w.sc, sizeof(DevScalars));
+    // tensor-core tiles hold 512 pixels; 8x slack covers ragged grids down to thin slabs
+    w.tc_tile_cap = max_j / 64 + 4096;
+    alloc((void **)&w.tc_centre, (size_t)w.tc_tile_cap * 6 * sizeof(float));
+    alloc((void **)&w.tc_start, (size_t)w.tc_tile_cap * sizeof(int));
+    alloc((void **)&w.tc_cand, (size_t)max_j * sizeof(int4));
     alloc((void **)&w.part, nb * 5 * sizeof(double));
     alloc((void **)&w.grad, (size_t)max_n * sizeof(double));
     alloc((void **)&w.W, (size_t)max_n * sizeof(double));
@@ -501,7 +512,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_cand, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -600,7 +611,8 @@ static int solve_entry(const apd_grid *grid, const apd_seeds *seeds, const doubl
     if (opts) o = *opts;
     else apd_solve_opts_default(&o);
     if (!(o.eps > 0.0) || o.max_evals < 1 || o.history < 1) return APD_ERR_ARG;
-    if (o.precision != APD_FP32) return APD_ERR_UNSUPPORTED;
+    if (o.precision != APD_FP32 && o.precision != APD_TC_TF32 && o.precision != APD_TC_BF16)
+        return APD_ERR_UNSUPPORTED;
     // a status latched by earlier stream-ordered calls is reported first
     return take_status(ws->w, st);
 }

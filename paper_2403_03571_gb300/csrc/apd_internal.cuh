@@ -79,6 +79,11 @@ struct Workspace {
     uint32_t *codes = nullptr;          // [n_pad_max] Morton codes, natural order
     uint32_t *scodes = nullptr;         // [n_pad_max] sorted codes
     int32_t *perm = nullptr;            // [n_pad_max] scan position -> seed index
+    SeedRec32 *recs32s = nullptr;       // [n_pad_max] SeedRec32 in scan order
+    float *tc_centre = nullptr;         // [tc_tile_cap][6] tensor-core tile centres (FP32 hi, lo)
+    int *tc_start = nullptr;            // [tc_tile_cap] Morton start chunk per tile
+    long long tc_tile_cap = 0;
+    int4 *tc_cand = nullptr;            // [max_j] tensor-core candidates per pixel (3 seeds, 4th score)
     bool sorted = false;                // set by launch_seed_prep for the current pass
     unsigned long long *moments = nullptr;  // [max_n * K]
     uint32_t *flags = nullptr;          // [max_j]
@@ -189,18 +194,22 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// One poll of the phase; the thread may sleep up to kWaitHintNs while the phase
+// is incomplete (it is woken when the phase completes).
+constexpr uint32_t kWaitHintNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "n"(kWaitHintNs)
         : "memory");
     return ok != 0;
 }
-// Bounded wait: returns false (and latches ST_TIMEOUT) after `limit` polls.
+// Bounded wait: returns false (and latches ST_TIMEOUT) after `limit` polls
+// (at most limit x 20 us, about 1.3 s with the default).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status,
-                                                  uint32_t limit = (1u << 24)) {
+                                                  uint32_t limit = (1u << 16)) {
     for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(status, ST_TIMEOUT);
@@ -220,6 +229,11 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
 // FP32 scoring fused with the moments; queues near ties; labels optional.
 cudaError_t launch_assign_fp32(const GridDev &g, int n, Workspace &ws, int32_t *labels,
                                unsigned long long *moments, cudaStream_t st);
+// tcgen05 scoring fused with the moments (kind 0 = TF32, 1 = BF16); queues near ties.
+cudaError_t launch_assign_tc(const GridDev &g, int n, Workspace &ws, int32_t *labels,
+                             unsigned long long *moments, int kind, cudaStream_t st);
+// number of tensor-core tiles the grid needs (the workspace holds tc_tile_cap)
+long long tc_tile_count(const GridDev &g);
 // FP64 rescoring of the queued pixels (labels optional, moments updated).
 cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,
                                 const double *w, Workspace &ws, int32_t *labels,

@@ -239,9 +239,13 @@ __global__ void __launch_bounds__(1024)
 }
 
 __global__ void gather_recs_kernel(const int n_pad, const int32_t *__restrict__ perm,
-                                   const SeedRec *__restrict__ src, SeedRec *__restrict__ dst) {
+                                   const SeedRec *__restrict__ src, SeedRec *__restrict__ dst,
+                                   const SeedRec32 *__restrict__ src32, SeedRec32 *__restrict__ dst32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_pad) dst[i] = src[perm[i]];
+    if (i < n_pad) {
+        dst[i] = src[perm[i]];
+        if (dst32) dst32[i] = src32[perm[i]];
+    }
 }
 
 // Per-cell dual terms from the integer moments, then a deterministic two-phase
@@ -455,7 +459,7 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
     int m = 1;
     while (m < n_pad) m <<= 1;
     // Morton order for the scoring scan when the workspace has the buffers
-    ws.sorted = ws.recs_tmp && ws.codes && ws.scodes && ws.perm && m <= kSortMax;
+    ws.sorted = ws.recs_tmp && ws.codes && ws.scodes && ws.perm && ws.recs32s && m <= kSortMax;
     SeedRec *dst = ws.sorted ? ws.recs_tmp : ws.recs;
     uint32_t *codes = ws.sorted ? ws.codes : nullptr;
     if (g.dim == 3)
@@ -473,7 +477,7 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
         attr = true;
     }
     morton_sort_kernel<<<1, 1024, smem, st>>>(n_pad, m, ws.codes, ws.scodes, ws.perm);
-    gather_recs_kernel<<<blocks, 256, 0, st>>>(n_pad, ws.perm, ws.recs_tmp, ws.recs);
+    gather_recs_kernel<<<blocks, 256, 0, st>>>(n_pad, ws.perm, ws.recs_tmp, ws.recs, ws.recs32, ws.recs32s);
     return cudaGetLastError();
 }
 

@@ -19,8 +19,10 @@ def capi():
     return c
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tc_tf32", "tc_bf16"])
 @pytest.mark.parametrize("which", ["2d_20", "3d_1000"])
-def test_fullsize_sampled(capi, which):
+def test_fullsize_sampled(capi, which, prec):
+    pc = {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32, "tc_bf16": capi.APD_TC_BF16}[prec]
     inst = synth.workload_2d_20() if which == "2d_20" else synth.workload_3d_1000()
     n, J, dim = inst.n, inst.grid.num_pixels, inst.grid.dim
     g = synth.rng(99)
@@ -29,7 +31,7 @@ def test_fullsize_sampled(capi, which):
     x, A, ww, v = instance_tensors(inst, w)
     ws = capi.Workspace(dim, n, J)
     labels = torch.full((J,), -1, dtype=torch.int32, device="cuda")
-    capi.apd_assign(inst.grid, x, A, ww, labels, ws)
+    capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=pc)
     assert ws.status() == capi.APD_OK
     st = ws.last_stats()
     lab = host(labels)
@@ -39,11 +41,12 @@ def test_fullsize_sampled(capi, which):
     # moments: exact closed-form totals and consistency with the labels
     K = oracle.moment_width(dim)
     mom = torch.zeros((n, K), dtype=torch.int64, device="cuda")
-    capi.apd_cell_moments(inst.grid, x, A, ww, mom, ws)
+    capi.apd_cell_moments(inst.grid, x, A, ww, mom, ws, precision=pc)
     mo = host(mom)
     assert mo[:, 0].sum() == J
     np.testing.assert_array_equal(mo[:, 0], np.bincount(lab, minlength=n))
     for d in range(dim):
         assert mo[:, 1 + d].sum() == J * inst.grid.res[d]
     # the rescored fraction stays small
-    assert st.rescored_fp64 < 1e-3 * J
+    # BF16 operands (2^-9 rounding) queue more near ties than TF32 or FP32
+    assert st.rescored_fp64 < (1e-2 if prec == "tc_bf16" else 2e-3) * J, st.rescored_fp64

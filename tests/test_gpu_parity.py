@@ -26,11 +26,18 @@ def capi():
     return c
 
 
-def gpu_labels(capi, inst, w=None, ws=None):
+PRECISIONS = ["fp32", "tc_tf32", "tc_bf16"]
+
+
+def _prec(capi, name):
+    return {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32, "tc_bf16": capi.APD_TC_BF16}[name]
+
+
+def gpu_labels(capi, inst, w=None, ws=None, prec="fp32"):
     x, A, ww, _ = instance_tensors(inst, w)
     ws = ws or capi.Workspace(inst.grid.dim, inst.n, inst.grid.num_pixels)
     labels = torch.full((inst.grid.num_pixels,), -1, dtype=torch.int32, device="cuda")
-    capi.apd_assign(inst.grid, x, A, ww, labels, ws)
+    capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=_prec(capi, prec))
     assert ws.status() == capi.APD_OK
     st = ws.last_stats()
     return host(labels), st
@@ -67,29 +74,32 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("dim,n,res,seed,wscale", CASES)
-def test_assign_matches_oracle(capi, dim, n, res, seed, wscale):
+def test_assign_matches_oracle(capi, dim, n, res, seed, wscale, prec):
     inst = _case(dim, n, res, seed, wscale)
-    got, st = gpu_labels(capi, inst)
+    got, st = gpu_labels(capi, inst, prec=prec)
     assert st.pixels == inst.grid.num_pixels
     assert_labels_match(inst, got)
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("dim,n,res,seed,wscale", CASES[:5])
-def test_moments_match_oracle(capi, dim, n, res, seed, wscale):
+def test_moments_match_oracle(capi, dim, n, res, seed, wscale, prec):
     inst = _case(dim, n, res, seed, wscale)
     x, A, w, _ = instance_tensors(inst)
     ws = capi.Workspace(dim, n, inst.grid.num_pixels)
     K = oracle.moment_width(dim)
     mom = torch.full((n, K), -7, dtype=torch.int64, device="cuda")
-    capi.apd_cell_moments(inst.grid, x, A, w, mom, ws)
+    capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=_prec(capi, prec))
     assert ws.status() == capi.APD_OK
     ref_lab = oracle.assign(inst.grid, inst.x, inst.A, inst.w)
     ref = oracle.moments(inst.grid, ref_lab, n)
     np.testing.assert_array_equal(host(mom), ref)
 
 
-def test_special_cases(capi):
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_special_cases(capi, prec):
     # Voronoi (A = I, w = 0) with duplicated seeds: exact ties everywhere in their cells
     g = synth.rng(21)
     x = g.random((40, 2))
@@ -97,7 +107,7 @@ def test_special_cases(capi):
     x[17] = x[3]
     inst = synth.Instance(synth.Grid(2, (90, 70)), x, np.tile(np.eye(2), (40, 1, 1)), np.zeros(40),
                           np.full(40, 1 / 40))
-    got, st = gpu_labels(capi, inst)
+    got, st = gpu_labels(capi, inst, prec=prec)
     assert_labels_match(inst, got)
     assert not np.any(got == 5) and not np.any(got == 17)
     assert st.rescored_fp64 > 0
@@ -107,7 +117,7 @@ def test_special_cases(capi):
     x = np.array([[c[8], c[8]], [c[24], c[8]], [c[8], c[24]], [c[24], c[24]]])
     inst = synth.Instance(synth.Grid(2, (res, res)), x, np.tile(np.eye(2), (4, 1, 1)), np.zeros(4),
                           np.full(4, 0.25))
-    got, _ = gpu_labels(capi, inst)
+    got, _ = gpu_labels(capi, inst, prec=prec)
     assert_labels_match(inst, got)
     # extreme anisotropy: eigenvalue ratio 1e4
     g = synth.rng(22)
@@ -116,7 +126,7 @@ def test_special_cases(capi):
     a = np.full(n, 100.0)
     A = synth._rot2_diag(th, a, 1.0 / a)
     inst = synth.Instance(synth.Grid(2, (120, 90)), g.random((n, 2)), A, np.zeros(n), np.full(n, 1 / n))
-    got, _ = gpu_labels(capi, inst)
+    got, _ = gpu_labels(capi, inst, prec=prec)
     assert_labels_match(inst, got)
     # 3D extreme anisotropy and large weights
     g = synth.rng(23)
@@ -128,18 +138,19 @@ def test_special_cases(capi):
     A = 0.5 * (A + A.transpose(0, 2, 1))
     w = 0.05 * g.standard_normal(n) + 3.0
     inst = synth.Instance(synth.Grid(3, (24, 20, 18)), g.random((n, 3)), A, w, np.full(n, 1 / n))
-    got, _ = gpu_labels(capi, inst)
+    got, _ = gpu_labels(capi, inst, prec=prec)
     assert_labels_match(inst, got)
 
 
-def test_shifted_box(capi):
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_shifted_box(capi, prec):
     grid = synth.Grid(3, (21, 18, 25), lo=(-2.0, 0.5, 10.0), hi=(1.0, 1.25, 12.5))
     g = synth.rng(31)
     n = 90
     x = np.array(grid.lo) + (np.array(grid.hi) - np.array(grid.lo)) * g.random((n, 3))
     A = synth.aniso_3d_lognormal(g, n, 0.4)
     inst = synth.Instance(grid, x, A, 0.01 * g.standard_normal(n), np.full(n, grid.measure / n))
-    got, _ = gpu_labels(capi, inst)
+    got, _ = gpu_labels(capi, inst, prec=prec)
     assert_labels_match(inst, got)
 
 
@@ -188,14 +199,23 @@ def test_errors_reported(capi):
     assert e.value.code == capi.APD_ERR_UNSUPPORTED
 
 
-def test_deterministic_moments(capi):
+def test_tensor_core_self_check(capi):
+    for kind in (0, 1):
+        rc, bad, err = capi.apd_tensor_core_check(kind, 0)
+        assert rc == capi.APD_OK and bad == 0 and err == 0.0, (kind, rc, bad, err)
+        rc, bad, err = capi.apd_tensor_core_check(kind, 1)
+        assert rc == capi.APD_OK and bad > 0
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_deterministic_moments(capi, prec):
     inst = _case(3, 200, (32, 30, 28), 51, 0.2)
     x, A, w, _ = instance_tensors(inst)
     ws = capi.Workspace(3, 200, inst.grid.num_pixels)
     outs = []
     for _ in range(5):
         mom = torch.zeros((200, 10), dtype=torch.int64, device="cuda")
-        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws)
+        capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=_prec(capi, prec))
         outs.append(host(mom))
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
