@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_tf32", "tc_bf16"],
-                    help="scoring arithmetic of the timed path")
+                    help="scoring arithmetic of the reported form (the plain FP32 and the "
+                         "tensor-core TF32 forms are always timed too)")
     ap.add_argument("--mode", default="apd", choices=["apd", "assign"],
                     help="apd: the full benchmark; assign: only repeated scoring+moments calls "
                          "(apd_cell_moments) at zero weights, for kernel profiling")
@@ -167,7 +168,7 @@ def run_reference(args, evals_per_apd):
         "impl": "reference", "metric": metric_name(args.workload), "value": val, "unit": "APD/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(args.workload, inst, rounds),
+        "data": "synthetic", "config": config_dict(args.workload, inst, rounds, args.precision),
         "pair_evals_per_s": statistics.mean(pairs_s),
         "cpu_baseline": {"value": val, "unit": "APD/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -176,13 +177,20 @@ def run_reference(args, evals_per_apd):
 
 
 def metric_name(workload):
-    return "APD solves/s to 1% volume error and pixel-seed evals/s, plain FP32 path"
+    return "APD solves/s to 1% volume error and pixel-seed evals/s, chosen vs plain FP32"
 
 
-def config_dict(workload, inst, rounds):
+PRECISION_TEXT = {
+    "fp32": "fp32 CUDA-core scoring, fp64 near-tie rescoring",
+    "tc_tf32": "tcgen05 TF32 scoring (FP32 accumulate), FP32 candidate rescoring, fp64 near-tie rescoring",
+    "tc_bf16": "tcgen05 BF16 scoring (FP32 accumulate), FP32 candidate rescoring, fp64 near-tie rescoring",
+}
+
+
+def config_dict(workload, inst, rounds, precision="fp32"):
     return {"workload": workload, "dim": inst.grid.dim, "seeds": inst.n,
             "grid": list(inst.grid.res), "eps": 0.01, "lloyd_rounds": rounds,
-            "solves_per_apd": rounds + 1, "precision": "fp32 scoring, fp64 near-tie rescoring",
+            "solves_per_apd": rounds + 1, "precision": PRECISION_TEXT[precision],
             "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"}
 
 
@@ -222,64 +230,45 @@ def fp32_peak_tflops(sm_mhz, sms):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def run_ours(args):
+def measure_form(args, ctx, precision):
+    """Warm-up, timed steps (CUDA events on the calling stream, L2 flushed between
+    steps) and the end-to-end pass, for one scoring precision."""
     import torch
     import torch.distributed as dist
-    from paper_2403_03571_gb300 import build, capi
+    from paper_2403_03571_gb300 import capi
+    inst, rounds, dev, stream, world = ctx["inst"], ctx["rounds"], ctx["dev"], ctx["stream"], ctx["world"]
+    x0, A, v, w0, x_out, w_out, ws, flush = (ctx[k] for k in ("x0", "A", "v", "w0", "x_out", "w_out", "ws", "flush"))
+    n = inst.n
+    opts = capi.solve_opts(eps=0.01, precision=precision_code(capi, precision))
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    build.build()
-    capi.load()
-    dev = torch.device("cuda", local)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-
-    inst, rounds = make_instance(args.workload, rank)
-    dim, n, J = inst.grid.dim, inst.n, inst.grid.num_pixels
-    x0 = torch.from_numpy(inst.x).to(dev)
-    A = torch.from_numpy(inst.A).to(dev)
-    v = torch.from_numpy(inst.v).to(dev)
-    w0 = torch.zeros(n, dtype=torch.float64, device=dev)
-    x_out = torch.empty_like(x0)
-    w_out = torch.empty_like(w0)
-    ws = capi.Workspace(dim, n, J)
-    opts = capi.solve_opts(eps=0.01)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step(xin, win):
+    def step(xin, Ain, win, vin):
         if rounds > 0:
-            rc, info = capi.apd_lloyd(inst.grid, xin, A, win, v, rounds, x_out, w_out, ws, opts)
+            rc, info = capi.apd_lloyd(inst.grid, xin, Ain, win, vin, rounds, x_out, w_out, ws, opts)
         else:
-            rc, info = capi.apd_solve_weights(inst.grid, xin, A, win, v, w_out, ws, opts)
+            rc, info = capi.apd_solve_weights(inst.grid, xin, Ain, win, vin, w_out, ws, opts)
         if rc not in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE):
             raise RuntimeError(f"solve did not converge: {info.as_dict()}")
         return info
 
-    infos = []
     for _ in range(args.warmup):
-        infos.append(step(x0, w0))
+        step(x0, A, w0, v)
     torch.cuda.synchronize()
     ws.profile_read()
     ws.profile(True)
-    clk = ClockSampler(local)
+    clk = ClockSampler(ctx["local"])
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
     total_ms = 0.0
-    timed_infos = []
+    infos = []
     t_wall = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        timed_infos.append(step(x0, w0))
+        infos.append(step(x0, A, w0, v))
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
@@ -314,10 +303,7 @@ def run_ours(args):
         dA = hA.to(dev, non_blocking=True)
         dv = hv.to(dev, non_blocking=True)
         dw = hw.to(dev, non_blocking=True)
-        if rounds > 0:
-            capi.apd_lloyd(inst.grid, dx, dA, dw, dv, rounds, x_out, w_out, ws, opts)
-        else:
-            capi.apd_solve_weights(inst.grid, dx, dA, dw, dv, w_out, ws, opts)
+        step(dx, dA, dw, dv)
         hxo.copy_(x_out, non_blocking=True)
         hwo.copy_(w_out, non_blocking=True)
         e1.record(stream)
@@ -326,69 +312,133 @@ def run_ours(args):
     te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = world * args.e2e_steps / (float(te.item()) / 1000.0)
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return None
-
-    evals = [i.evaluations for i in timed_infos]
-    rescored = sum(i.rescored_fp64 for i in timed_infos)
-    pairs_total = sum(i.evaluations for i in timed_infos) * J * n
-    value = world * args.steps / (max_ms / 1000.0)
-    peaks, peak_src = load_peaks()
-    sm_mhz_nominal = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = fp32_peak_tflops(sm_mhz_nominal, sms)
-    F = 10 if dim == 3 else 6
+    J = inst.grid.num_pixels
+    evals = [i.evaluations for i in infos]
     per_launch_ms = assign_ms / max(1, assign_launches)
     pairs_per_launch = assign_pairs / max(1, assign_launches)
-    pair_rate = pairs_per_launch / (per_launch_ms / 1000.0)
-    achieved = pair_rate * FLOPS_PER_PAIR[dim] / 1e12
-    tr = NCU_TRAFFIC.get((kernel_source_hash(), args.workload))
-    traffic = tr / 2 if tr is not None else None  # the capture holds two launches
-    out = {
-        "metric": metric_name(args.workload),
-        "value": value,
-        "unit": "APD/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
+    return {
+        "value": world * args.steps / (max_ms / 1000.0),
         "ms_per_step": max_ms / args.steps,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32/f64",
-        "data": "synthetic",
-        "config": config_dict(args.workload, inst, rounds),
-        "pair_evals_per_s": pairs_total / (max_ms / 1000.0),
-        "assign_kernel_pair_evals_per_s": pairs_per_launch / (per_launch_ms / 1000.0),
+        "pair_evals_per_s": sum(evals) * J * n / (max_ms / 1000.0),
         "evaluations_per_apd": statistics.mean(evals),
-        "rescored_fp64_fraction": rescored / max(1, sum(i.evaluations for i in timed_infos) * J),
-        "roofline": {
-            "bound": "alu",
-            "kernel": "assign_fp32_kernel<%d>" % dim,
-            "achieved": achieved,
-            "peak": fp32_peak,
-            "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak,
-            "traffic": traffic,
-            "work_per_pair_flops": FLOPS_PER_PAIR[dim],
-            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz_nominal:.0f} MHz "
-                           f"(max SM clock from MEASURED_PEAKS.json, {peak_src})",
-            "launch_ms": per_launch_ms,
-            "launches": assign_launches,
-            "dot_product_equivalent_tflops": pair_rate * 2 * F / 1e12,
-        },
-        "e2e": {"value": e2e_val, "unit": "APD/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "rescored_fp64_fraction": sum(i.rescored_fp64 for i in infos) / max(1, sum(evals) * J),
+        "launch_ms": per_launch_ms,
+        "launches": assign_launches,
+        "pair_rate": pairs_per_launch / (per_launch_ms / 1000.0),
+        "e2e": {"value": world * args.e2e_steps / (float(te.item()) / 1000.0) if args.e2e_steps > 0 else None,
+                "unit": "APD/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": kernel_launches,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "wall_s_timed": wall,
     }
-    if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
+
+
+def roofline_block(form, dim, sms, workload):
+    peaks, peak_src = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    F = 10 if dim == 3 else 6
+    pr = form["pair_rate"]
+    if form["precision"] == "fp32":
+        peak = fp32_peak_tflops(sm_mhz, sms)
+        achieved = pr * FLOPS_PER_PAIR[dim] / 1e12
+        tr = NCU_TRAFFIC.get((kernel_source_hash(), workload))
+        return {"bound": "alu", "kernel": "assign_fp32_kernel<%d>" % dim, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": tr / 2 if tr is not None else None,
+                "work_per_pair_flops": FLOPS_PER_PAIR[dim],
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
+                               f"(max SM clock from MEASURED_PEAKS.json, {peak_src})",
+                "launch_ms": form["launch_ms"], "launches": form["launches"],
+                "dot_product_equivalent_tflops": pr * 2 * F / 1e12}
+    # tensor-core form: the dot product [y(x)y, y, 1] . phi of F features per pair, against the
+    # dense peak of its operand type (measured BF16 x the nominal TF32/BF16 ratio 1.1/2.25)
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    peak = bf16 * (1.1 / 2.25) if form["precision"] == "tc_tf32" else bf16
+    achieved = pr * 2 * F / 1e12
+    return {"bound": "tensor", "kernel": "assign_tc_kernel<%d> + tc_resolve_kernel<%d>" % (dim, dim),
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "work_per_pair_flops": 2 * F,
+            "peak_source": f"measured bf16 {bf16:.1f} TFLOP/s ({peak_src})"
+                           + (" x 1.1/2.25 (nominal TF32/BF16)" if form["precision"] == "tc_tf32" else ""),
+            "launch_ms": form["launch_ms"], "launches": form["launches"]}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2403_03571_gb300 import build, capi
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    capi.load()
+    dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    inst, rounds = make_instance(args.workload, rank)
+    dim, n, J = inst.grid.dim, inst.n, inst.grid.num_pixels
+    ctx = {"inst": inst, "rounds": rounds, "dev": dev, "stream": torch.cuda.current_stream(dev), "world": world,
+           "local": local, "x0": torch.from_numpy(inst.x).to(dev), "A": torch.from_numpy(inst.A).to(dev),
+           "v": torch.from_numpy(inst.v).to(dev), "w0": torch.zeros(n, dtype=torch.float64, device=dev)}
+    ctx["x_out"] = torch.empty_like(ctx["x0"])
+    ctx["w_out"] = torch.empty_like(ctx["w0"])
+    ctx["ws"] = capi.Workspace(dim, n, J)
+    ctx["flush"] = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # the chosen form, the plain FP32 form and the tensor-core TF32 form, each timed
+    forms = {}
+    for prec in dict.fromkeys([args.precision, "fp32", "tc_tf32"]):
+        forms[prec] = measure_form(args, ctx, prec)
+        forms[prec]["precision"] = prec
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+    chosen = forms[args.precision]
+
+    def side(f):
+        return {k: f[k] for k in ("value", "ms_per_step", "pair_evals_per_s", "evaluations_per_apd",
+                                  "rescored_fp64_fraction", "e2e", "gpu_launches", "clocks")} \
+            | {"assign_kernel_pair_evals_per_s": f["pair_rate"],
+               "roofline": roofline_block(f, dim, sms, args.workload)}
+
+    out = {
+        "metric": metric_name(args.workload),
+        "value": chosen["value"],
+        "unit": "APD/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": chosen["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"tc_tf32": "tf32/f32/f64", "tc_bf16": "bf16/f32/f64"}.get(args.precision, "f32/f64"),
+        "data": "synthetic",
+        "config": config_dict(args.workload, inst, rounds, args.precision),
+        "pair_evals_per_s": chosen["pair_evals_per_s"],
+        "assign_kernel_pair_evals_per_s": chosen["pair_rate"],
+        "evaluations_per_apd": chosen["evaluations_per_apd"],
+        "rescored_fp64_fraction": chosen["rescored_fp64_fraction"],
+        "roofline": roofline_block(chosen, dim, sms, args.workload),
+        "e2e": chosen["e2e"],
+        "gpu_launches": chosen["gpu_launches"],
+        "clocks": chosen["clocks"],
+        "wall_s_timed": chosen["wall_s_timed"],
+    }
+    for prec, f in forms.items():
+        if prec != args.precision:
+            out["plain_fp32" if prec == "fp32" else prec] = side(f)
+    if not args.no_cpu_baseline:
         ref_args = argparse.Namespace(**vars(args))
         ref_args.steps, ref_args.warmup = 1, 0
-        ref = run_reference(ref_args, int(round(statistics.mean(evals))))
+        ref = run_reference(ref_args, int(round(chosen["evaluations_per_apd"])))
         out["cpu_baseline"] = ref["cpu_baseline"]
         out["cpu_baseline"]["pair_evals_per_s"] = ref["pair_evals_per_s"]
     if world > 1:

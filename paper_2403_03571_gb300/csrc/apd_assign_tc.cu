@@ -333,25 +333,32 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
             };
             for (int q = 0; q < kTcRaw && q < Q; ++q) load_raw(q);
             const uint32_t idesc = tc::instr_desc(KIND, kTcM, kTcN);
+            uint64_t adesc[kTcTiles][Fm::STEPS], bdesc[kTcStages][Fm::STEPS];
+#pragma unroll
+            for (int st = 0; st < Fm::STEPS; ++st) {
+                const uint32_t off = (uint32_t)st * 2u * Fm::LBO;
+#pragma unroll
+                for (int m = 0; m < kTcTiles; ++m)
+                    adesc[m][st] = tc::smem_desc((uint32_t)__cvta_generic_to_shared(sm.A[m]) + off, Fm::LBO, Fm::SBO);
+#pragma unroll
+                for (int bb = 0; bb < kTcStages; ++bb)
+                    bdesc[bb][st] = tc::smem_desc((uint32_t)__cvta_generic_to_shared(sm.B[bb]) + off, Fm::LBO, Fm::SBO);
+            }
             for (int q = 0; q < Q; ++q) {
                 const int b = q & 1;
                 if (!wait(&sm.bar_bfull[b], (uint32_t)((q >> 1) & 1))) break;
                 if (q >= 2 && !wait(&sm.bar_aempty[b], (uint32_t)(((q >> 1) - 1) & 1))) break;
                 tc::fence_after_sync();
-                const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(sm.B[b]);
 #pragma unroll
                 for (int m = 0; m < kTcTiles; ++m) {
-                    const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(sm.A[m]);
                     const uint32_t d = taddr + (uint32_t)((b * kTcTiles + m) * kTcN);
 #pragma unroll
                     for (int st = 0; st < Fm::STEPS; ++st) {
-                        const uint32_t off = (uint32_t)st * 2u * Fm::LBO;
-                        const uint64_t ad = tc::smem_desc(a0 + off, Fm::LBO, Fm::SBO);
-                        const uint64_t bd = tc::smem_desc(b0 + off, Fm::LBO, Fm::SBO);
+                        const uint64_t bd = b ? bdesc[1][st] : bdesc[0][st];
                         if (KIND == tc::KIND_TF32)
-                            tc::mma_tf32(d, ad, bd, idesc, st > 0 ? 1u : 0u);
+                            tc::mma_tf32(d, adesc[m][st], bd, idesc, st > 0 ? 1u : 0u);
                         else
-                            tc::mma_bf16(d, ad, bd, idesc, st > 0 ? 1u : 0u);
+                            tc::mma_bf16(d, adesc[m][st], bd, idesc, st > 0 ? 1u : 0u);
                     }
                 }
                 tc::mma_commit(&sm.bar_acc[b]);
@@ -591,12 +598,16 @@ __global__ void __launch_bounds__(256)
         }
         tc_table_add<D>(tkey, tval, gmom, L, val);
     };
+    int4 cds[kResP];
+#pragma unroll
+    for (int p = 0; p < kResP; ++p)
+        cds[p] = (row_valid && k0b + p < g.res[0]) ? cand[rowbase + k0b + p] : make_int4(-1, -1, -1, 0);
     for (int p = 0; p < kResP; ++p) {
         const int k0 = k0b + p;
         int label = -1;
         if (row_valid && k0 < g.res[0]) {
             const long long j = rowbase + k0;
-            const int4 cd = cand[j];
+            const int4 cd = cds[p];
             const float yp[3] = {((float)(p - kResP / 2) + 0.5f) * g.h32[0], 0.f, 0.f};
             const int ids[3] = {cd.x, cd.y, cd.z};
             int orig[3];
