@@ -223,6 +223,137 @@ int apd_cell_moments_noalloc(const apd_grid *grid, const apd_seeds *seeds, int64
  * (host pointers).  Host-synchronous; runs on the current device. */
 int apd_tensor_core_check(int32_t kind, int32_t variant, int32_t *mismatches, float *max_err);
 
+/* ---- Batched weight solves (many independent problems at once) ------------
+ * A batch holds `count` independent APD problems ("instances") of one
+ * dimension, each with its own grid and seed count n_b.  Its seeds are rows
+ * [off_b, off_b + n_b) of concatenated device arrays (off_b = n_0 + ... +
+ * n_{b-1}, total N = sum n_b): x [N][dim], A [N][dim][dim], w [N], v [N], with
+ * the conventions of the one-instance calls.  Each instance is the problem of
+ * apd_solve_weights on its own grid (Algorithm 2); the batch evaluates all
+ * unconverged instances per iteration with one persistent scoring launch over
+ * a shared tile queue, runs the L-BFGS transitions on the device and replays
+ * the iteration as a captured CUDA graph.  The paper solves one diagram at a
+ * time; batching is a throughput layout of the same computation.  Scoring is
+ * FP32 with exact rescoring, so labels and moments equal apd_cell_moments with
+ * APD_FP32 per instance. */
+typedef struct apd_batch apd_batch;
+
+/* Create a batch for `count` instances (1 .. 50000): grids and n are HOST
+ * arrays [count] (grids[b].dim == dim, n[b] >= 1).  tile = -1 picks the tile
+ * shape of the scoring kernel on the first call by timing every compiled shape
+ * on that call's inputs (autotune); 0 .. apd_batch_tile_info's n_variants - 1
+ * fixes it.  Allocates all scratch (about 400 B per seed plus 4 B per pixel).
+ * Errors: APD_ERR_ARG, APD_ERR_CUDA. */
+int apd_batch_create(apd_batch **batch, int32_t dim, int32_t count, const apd_grid *grids,
+                     const int32_t *n, int32_t tile);
+
+/* Free a batch (NULL ignored); no work using it may be in flight. */
+void apd_batch_destroy(apd_batch *batch);
+
+/* Tile shape in use (-1 until autotuned), the number of compiled shapes, and
+ * (each nullable, HOST arrays [n_variants]) the autotune time of one scoring
+ * pass per shape in ms (-1 if not timed) and the shapes as (P, TY, TZ) triples:
+ * a tile is P x TY x TZ pixels, P along the first axis. */
+int apd_batch_tile_info(apd_batch *batch, int32_t *tile, int32_t *n_variants, double *ms,
+                        int32_t *shape);
+
+/* Kernels this batch has launched (graph replays count their six kernels). */
+int64_t apd_batch_kernel_launches(apd_batch *batch);
+
+/* One evaluation of every instance at weights w: moments int64 device
+ * [N][APD_MOMENT_WIDTH(dim)] (per instance, the layout of apd_cell_moments).
+ * Host-synchronous; returns the device-side status (APD_OK, APD_ERR_ARG,
+ * APD_ERR_NOT_SPD, APD_ERR_TIMEOUT) or APD_ERR_ARG / APD_ERR_CUDA. */
+int apd_batch_cell_moments(apd_batch *batch, const double *x, const double *A, const double *w,
+                           int64_t *moments, apd_stream_t stream);
+
+/* Algorithm 2 for every instance from W0 = w0: w_out device [N] receives each
+ * instance's converged weights (or its best iterate); info, if not NULL, is a
+ * HOST array [count] with each instance's status, iterations, evaluations,
+ * max_rel_err and g (seconds = wall time of the whole call).  opts: eps,
+ * max_evals (per instance), history (clamped to 1..15), check_volumes;
+ * precision must be APD_FP32 (else APD_ERR_UNSUPPORTED).  Host-synchronous.
+ * Returns the first error of any instance, else APD_NOT_CONVERGED if any
+ * instance hit its cap, else APD_WARN_TOL_INFEASIBLE if any instance's grid
+ * fails eq. (2.10), else APD_OK. */
+int apd_batch_solve_weights(apd_batch *batch, const double *x, const double *A, const double *w0,
+                            const double *v, double *w_out, const apd_solve_opts *opts,
+                            apd_solve_info *info, apd_stream_t stream);
+
+/* Algorithm 2 for every instance, started from predicted weights and judged
+ * against the plain start: each instance first evaluates g~ at w_pred and at
+ * W = 0 and starts from the larger (ties: zero), so a poor prediction costs one
+ * evaluation and never a worse start.  used_pred, if not NULL, is a HOST array
+ * [count] set to 1 where the prediction was kept.  Otherwise as
+ * apd_batch_solve_weights (the two first evaluations are counted). */
+int apd_batch_solve_weights_judged(apd_batch *batch, const double *x, const double *A,
+                                   const double *w_pred, const double *v, double *w_out,
+                                   const apd_solve_opts *opts, apd_solve_info *info,
+                                   int32_t *used_pred, apd_stream_t stream);
+
+/* ---- Learned warm start ---------------------------------------------------
+ * A per-seed network predicts initial weights for the weight solve from local
+ * statistics of the generators.  The paper seeds its solves with W = 0 (and
+ * motivates a heuristic initial guess); this predictor is an addition, always
+ * judged against the zero start (apd_batch_solve_weights_judged,
+ * apd_solve_weights_warm).
+ *   Features of seed i of an instance with n seeds on a domain of measure |O|,
+ *   s = n / |O| (F = 20 in 2D, 23 in 3D): [v_i s, upper triangle of
+ *   (A_i + A_i^T)/2, distances to the 8 nearest other seeds x s^(1/D)
+ *   ascending, target volumes of those seeds x s]; missing neighbours give
+ *   distance 4 and volume 0.
+ *   Network: F -> 64 -> 64 -> 64 -> 1, ReLU, FP32; inputs standardised by
+ *   (f - mean) * inv_std.  Prediction w_i = y_i s^(-2/D).
+ *   Parameters: one FP32 array of apd_warmstart_sizes' n_params values in the
+ *   order W1 [64][F], b1 [64], W2 [64][64], b2, W3 [64][64], b3, W4 [64], b4 [1]
+ *   (W row-major [out][in]); norm = mean [F] followed by inv_std [F].
+ * Instances are described as for batches: offsets HOST int64 [count + 1]
+ * (offsets[0] = 0, strictly increasing) into concatenated x / A / v, and
+ * measure HOST double [count] (|O| of each instance). */
+typedef struct apd_mlp apd_mlp;
+
+/* Feature and parameter counts of the network for dim (2 or 3). */
+int32_t apd_warmstart_sizes(int32_t dim, int32_t *n_features, int32_t *n_params);
+
+/* Create a network on the current device from HOST params [n_params] and norm
+ * [2F] (NULL: mean 0, inv_std 1).  Errors: APD_ERR_ARG, APD_ERR_CUDA. */
+int apd_warmstart_create(apd_mlp **net, int32_t dim, const float *params, const float *norm);
+void apd_warmstart_destroy(apd_mlp *net);
+
+/* Copy the current parameters / norm to HOST arrays (each nullable). */
+int apd_warmstart_get(apd_mlp *net, float *params, float *norm);
+
+/* Features of every seed: features FP32 device [N][F].  Stream-ordered. */
+int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, const double *measure,
+                           const double *x, const double *A, const double *v, float *features,
+                           apd_stream_t stream);
+
+/* Set the network's norm to the mean and 1/std of `samples` feature rows
+ * (device [samples][F]).  Stream-ordered. */
+int apd_warmstart_fit_norm(apd_mlp *net, int64_t samples, const float *features, apd_stream_t stream);
+
+/* Predicted weights w_out double device [N] from features.  Stream-ordered. */
+int apd_warmstart_predict(apd_mlp *net, int32_t count, const int64_t *offsets, const double *measure,
+                          const float *features, double *w_out, apd_stream_t stream);
+
+/* One training step on the samples idx[0 .. batch) (int32 device indices into
+ * features [.][F] and targets FP32 device [.], targets in units of y):
+ * loss = (1/batch) sum (y - target)^2, gradient by back-propagation, then an
+ * Adam step (beta 0.9 / 0.999, eps 1e-8, step size lr; lr = 0 leaves the
+ * parameters unchanged).  grad_out (FP32 device [n_params]) and loss_out (FP32
+ * device [1], the SUM of squared residuals) are optional.  Stream-ordered. */
+int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, const float *features,
+                             const float *targets, float lr, float *grad_out, float *loss_out,
+                             apd_stream_t stream);
+
+/* apd_solve_weights started from the network's prediction for this instance,
+ * judged against W = 0 as in apd_batch_solve_weights_judged (seeds->w is not
+ * read).  used_pred (host, nullable) = 1 if the prediction was kept.
+ * Host-synchronous; status as apd_solve_weights. */
+int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const double *v,
+                           double *w_out, const apd_solve_opts *opts, apd_solve_info *info,
+                           apd_workspace *ws, apd_mlp *net, int32_t *used_pred, apd_stream_t stream);
+
 /* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
  * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).
  * Returns M >= 1, or -1 for invalid arguments. */

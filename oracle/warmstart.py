@@ -1,0 +1,119 @@
+"""FP64 CPU oracle of the learned warm start (features and the per-seed network).
+
+TEST INFRASTRUCTURE ONLY: tests/ may import it; the library path never does.
+It shares no code with the CUDA path: neighbours come from scipy's k-d tree,
+the network and its gradient are plain numpy in FP64, written from the
+definitions below.
+
+The paper seeds the weight solve with W = 0 and motivates a better initial
+guess; the predictor these functions describe is this project's addition, so
+there is no passage to follow -- the definitions are:
+
+* features of seed i of an instance with n seeds on a domain of measure |O|,
+  s = n / |O|:  [v_i s, upper triangle of (A_i + A_i^T)/2, distances to the 8
+  nearest other seeds times s^(1/D) (ascending), target volumes of those seeds
+  times s]; missing neighbours (n <= 8) give distance 4 and volume 0;
+* network  y = w4 . relu(W3 relu(W2 relu(W1 z + b1) + b2) + b3) + b4,
+  z = (f - mean) * inv_std, hidden width 64, flat parameter order
+  W1 [64][F], b1, W2 [64][64], b2, W3 [64][64], b3, w4 [64], b4;
+* prediction  w_i = y_i s^(-2/D);
+* training loss over a batch  L = (1/B) sum_s (y_s - t_s)^2.
+
+Pins (tests/test_oracle_pins.py): the k-d tree neighbours against a brute-force
+distance matrix; the gradient against central finite differences of the FP64
+loss; the parameter counts against the layer sizes.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.spatial import cKDTree
+
+H = 64
+KNN = 8
+
+
+def n_features(dim: int) -> int:
+    return 1 + dim * (dim + 1) // 2 + 2 * KNN
+
+
+def n_params(dim: int) -> int:
+    F = n_features(dim)
+    return H * F + H + 2 * (H * H + H) + H + 1
+
+
+def features(x, A, v, measure: float = 1.0) -> np.ndarray:
+    """Feature rows [n][F] of one instance (FP64)."""
+    x = np.asarray(x, dtype=np.float64)
+    n, dim = x.shape
+    s = n / measure
+    k = min(KNN, n - 1)
+    dist = np.full((n, KNN), 4.0)
+    vol = np.zeros((n, KNN))
+    if k > 0:
+        d, idx = cKDTree(x).query(x, k=k + 1)
+        # column 0 is the point itself (distance 0); ties between neighbours at equal
+        # distance are measure-zero for continuous positions
+        dist[:, :k] = d[:, 1:] * s ** (1.0 / dim)
+        vol[:, :k] = np.asarray(v)[idx[:, 1:]] * s
+    sym = 0.5 * (A + np.transpose(A, (0, 2, 1)))
+    iu = np.triu_indices(dim)
+    upper = sym[:, iu[0], iu[1]]
+    return np.concatenate([np.asarray(v)[:, None] * s, upper, dist, vol], axis=1)
+
+
+def unpack(params, dim: int):
+    """(W1, b1, W2, b2, W3, b3, w4, b4) views of the flat parameter vector."""
+    F = n_features(dim)
+    p = np.asarray(params, dtype=np.float64)
+    shapes = [(H, F), (H,), (H, H), (H,), (H, H), (H,), (H,), (1,)]
+    out, o = [], 0
+    for sh in shapes:
+        size = int(np.prod(sh))
+        out.append(p[o:o + size].reshape(sh))
+        o += size
+    assert o == p.size
+    return out
+
+
+def forward(params, norm, feats, dim: int):
+    """Network outputs y [S] and the activations (z, h1, h2, h3)."""
+    F = n_features(dim)
+    W1, b1, W2, b2, W3, b3, w4, b4 = unpack(params, dim)
+    norm = np.asarray(norm, dtype=np.float64)
+    z = (np.asarray(feats, dtype=np.float64) - norm[:F]) * norm[F:]
+    h1 = np.maximum(z @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    h3 = np.maximum(h2 @ W3.T + b3, 0.0)
+    y = h3 @ w4 + b4[0]
+    return y, (z, h1, h2, h3)
+
+
+def predict(params, norm, feats, n: int, measure: float, dim: int):
+    """Predicted weights of one instance: y s^(-2/D)."""
+    y, _ = forward(params, norm, feats, dim)
+    return y * (n / measure) ** (-2.0 / dim)
+
+
+def loss(params, norm, feats, targets, dim: int) -> float:
+    y, _ = forward(params, norm, feats, dim)
+    r = y - np.asarray(targets, dtype=np.float64)
+    return float(np.mean(r * r))
+
+
+def loss_grad(params, norm, feats, targets, dim: int):
+    """(L, dL/dparams) by the chain rule, layer by layer (FP64)."""
+    W1, b1, W2, b2, W3, b3, w4, b4 = unpack(params, dim)
+    y, (z, h1, h2, h3) = forward(params, norm, feats, dim)
+    B = y.shape[0]
+    r = y - np.asarray(targets, dtype=np.float64)
+    dy = 2.0 * r / B                       # dL/dy
+    g_w4 = h3.T @ dy
+    g_b4 = np.array([dy.sum()])
+    d3 = np.outer(dy, w4) * (h3 > 0)       # dL/d(pre-activation of layer 3)
+    g_W3, g_b3 = d3.T @ h2, d3.sum(0)
+    d2 = (d3 @ W3) * (h2 > 0)
+    g_W2, g_b2 = d2.T @ h1, d2.sum(0)
+    d1 = (d2 @ W2) * (h1 > 0)
+    g_W1, g_b1 = d1.T @ z, d1.sum(0)
+    grad = np.concatenate([g.ravel() for g in (g_W1, g_b1, g_W2, g_b2, g_W3, g_b3, g_w4, g_b4)])
+    return float(np.mean(r * r)), grad

@@ -35,6 +35,11 @@ EXPORTED = (
     "apd_solve_weights", "apd_lloyd_step", "apd_lloyd", "apd_choose_resolution",
     "apd_status_string", "apd_version", "apd_profile_enable", "apd_profile_read",
     "apd_cell_moments_noalloc", "apd_tensor_core_check",
+    "apd_batch_create", "apd_batch_destroy", "apd_batch_tile_info", "apd_batch_kernel_launches",
+    "apd_batch_cell_moments", "apd_batch_solve_weights", "apd_batch_solve_weights_judged",
+    "apd_warmstart_sizes", "apd_warmstart_create", "apd_warmstart_destroy", "apd_warmstart_get",
+    "apd_warmstart_features", "apd_warmstart_fit_norm", "apd_warmstart_predict",
+    "apd_warmstart_train_step", "apd_solve_weights_warm",
 )
 
 
@@ -118,6 +123,33 @@ def load(path: Optional[str] = None):
                                         _P(ctypes.c_float)]
     L.apd_profile_read.argtypes = [_vp, _P(ctypes.c_double), _P(ctypes.c_int64), _P(ctypes.c_int64),
                                    _P(ctypes.c_int64)]
+    L.apd_batch_create.argtypes = [_P(_vp), ctypes.c_int32, ctypes.c_int32, _P(ApdGrid),
+                                   _P(ctypes.c_int32), ctypes.c_int32]
+    L.apd_batch_destroy.argtypes = [_vp]
+    L.apd_batch_destroy.restype = None
+    L.apd_batch_tile_info.argtypes = [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32),
+                                      _P(ctypes.c_double), _P(ctypes.c_int32)]
+    L.apd_batch_kernel_launches.argtypes = [_vp]
+    L.apd_batch_kernel_launches.restype = ctypes.c_int64
+    L.apd_batch_cell_moments.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.apd_batch_solve_weights.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _P(ApdSolveOpts),
+                                          _P(ApdSolveInfo), _vp]
+    L.apd_batch_solve_weights_judged.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _P(ApdSolveOpts),
+                                                 _P(ApdSolveInfo), _P(ctypes.c_int32), _vp]
+    L.apd_warmstart_sizes.argtypes = [ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_int32)]
+    L.apd_warmstart_create.argtypes = [_P(_vp), ctypes.c_int32, _P(ctypes.c_float), _P(ctypes.c_float)]
+    L.apd_warmstart_destroy.argtypes = [_vp]
+    L.apd_warmstart_destroy.restype = None
+    L.apd_warmstart_get.argtypes = [_vp, _P(ctypes.c_float), _P(ctypes.c_float)]
+    L.apd_warmstart_features.argtypes = [_vp, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_double),
+                                         _vp, _vp, _vp, _vp, _vp]
+    L.apd_warmstart_fit_norm.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
+    L.apd_warmstart_predict.argtypes = [_vp, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_double),
+                                        _vp, _vp, _vp]
+    L.apd_warmstart_train_step.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_float, _vp, _vp,
+                                           _vp]
+    L.apd_solve_weights_warm.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _P(ApdSolveOpts),
+                                         _P(ApdSolveInfo), _vp, _vp, _P(ctypes.c_int32), _vp]
     _lib = L
     return L
 
@@ -286,3 +318,171 @@ def apd_lloyd(grid, x0, A, w0, v, rounds, x_out, w_out, ws: Workspace, opts=None
 
 def apd_choose_resolution(dim, v_min, eps=0.01, domain_measure=1.0) -> int:
     return int(load().apd_choose_resolution(dim, v_min, eps, domain_measure))
+
+
+class Batch:
+    """Owns an apd_batch: `count` independent instances (grids[b], n[b] seeds) whose
+    seed arrays are concatenated in instance order."""
+
+    def __init__(self, dim: int, grids, n, tile: int = -1):
+        L = load()
+        self.dim = int(dim)
+        self.count = len(grids)
+        self.n = [int(k) for k in n]
+        arr = (ApdGrid * self.count)(*[make_grid(g) for g in grids])
+        nn = (ctypes.c_int32 * self.count)(*self.n)
+        h = ctypes.c_void_p()
+        _check(L.apd_batch_create(ctypes.byref(h), self.dim, self.count, arr, nn, int(tile)),
+               "apd_batch_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().apd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tile_info(self):
+        """(chosen variant or -1, [ms per variant], [(P, TY, TZ) per variant])."""
+        L = load()
+        t, nv = ctypes.c_int32(), ctypes.c_int32()
+        _check(L.apd_batch_tile_info(self.handle, ctypes.byref(t), ctypes.byref(nv), None, None),
+               "apd_batch_tile_info")
+        ms = (ctypes.c_double * nv.value)()
+        sh = (ctypes.c_int32 * (3 * nv.value))()
+        _check(L.apd_batch_tile_info(self.handle, ctypes.byref(t), ctypes.byref(nv), ms, sh),
+               "apd_batch_tile_info")
+        return t.value, list(ms), [tuple(sh[3 * k:3 * k + 3]) for k in range(nv.value)]
+
+    def kernel_launches(self) -> int:
+        return int(load().apd_batch_kernel_launches(self.handle))
+
+
+def apd_batch_cell_moments(batch: Batch, x, A, w, moments, stream=None):
+    """Moments of every instance at weights w (concatenated); returns the C status."""
+    return load().apd_batch_cell_moments(batch.handle, _ptr(x), _ptr(A), _ptr(w), _ptr(moments),
+                                         _stream(stream))
+
+
+def apd_batch_solve_weights(batch: Batch, x, A, w0, v, w_out, opts=None, stream=None):
+    """Algorithm 2 for every instance; returns (C status, [ApdSolveInfo per instance]).
+    The status is not raised: per-instance errors are in each info's status."""
+    info = (ApdSolveInfo * batch.count)()
+    opts = opts or solve_opts()
+    rc = load().apd_batch_solve_weights(batch.handle, _ptr(x), _ptr(A), _ptr(w0), _ptr(v),
+                                        _ptr(w_out), ctypes.byref(opts), info, _stream(stream))
+    return rc, list(info)
+
+
+def apd_batch_solve_weights_judged(batch: Batch, x, A, w_pred, v, w_out, opts=None, stream=None):
+    """Batched solve from predicted weights, each instance judged against W = 0;
+    returns (C status, [ApdSolveInfo], [1 where the prediction was kept])."""
+    info = (ApdSolveInfo * batch.count)()
+    used = (ctypes.c_int32 * batch.count)()
+    opts = opts or solve_opts()
+    rc = load().apd_batch_solve_weights_judged(batch.handle, _ptr(x), _ptr(A), _ptr(w_pred), _ptr(v),
+                                               _ptr(w_out), ctypes.byref(opts), info, used,
+                                               _stream(stream))
+    return rc, list(info), list(used)
+
+
+def warmstart_sizes(dim: int):
+    """(features per seed, network parameters) for dimension dim."""
+    f, p = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().apd_warmstart_sizes(int(dim), ctypes.byref(f), ctypes.byref(p)), "apd_warmstart_sizes")
+    return f.value, p.value
+
+
+def _offsets(counts):
+    import numpy as np
+    offs = np.zeros(len(counts) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(np.asarray(counts, dtype=np.int64))
+    return offs
+
+
+class WarmStart:
+    """Owns an apd_mlp (the warm-start network on the device)."""
+
+    def __init__(self, dim: int, params, norm=None):
+        import numpy as np
+        L = load()
+        self.dim = int(dim)
+        self.n_features, self.n_params = warmstart_sizes(dim)
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (self.n_params,):
+            raise ValueError(f"expected {self.n_params} parameters, got {p.shape}")
+        nz = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        if nz is not None and nz.shape != (2 * self.n_features,):
+            raise ValueError("norm must hold mean and inverse std per feature")
+        h = ctypes.c_void_p()
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(L.apd_warmstart_create(ctypes.byref(h), self.dim, p.ctypes.data_as(fp),
+                                      None if nz is None else nz.ctypes.data_as(fp)), "apd_warmstart_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().apd_warmstart_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        """(params, norm) as float32 numpy arrays."""
+        import numpy as np
+        p = np.zeros(self.n_params, dtype=np.float32)
+        nz = np.zeros(2 * self.n_features, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(load().apd_warmstart_get(self.handle, p.ctypes.data_as(fp), nz.ctypes.data_as(fp)),
+               "apd_warmstart_get")
+        return p, nz
+
+    def features(self, counts, measures, x, A, v, out, stream=None):
+        import numpy as np
+        offs = _offsets(counts)
+        m = np.ascontiguousarray(measures, dtype=np.float64)
+        return _check(load().apd_warmstart_features(
+            self.handle, len(counts), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(x), _ptr(A), _ptr(v), _ptr(out),
+            _stream(stream)), "apd_warmstart_features")
+
+    def fit_norm(self, features, stream=None):
+        return _check(load().apd_warmstart_fit_norm(self.handle, int(features.shape[0]), _ptr(features),
+                                                    _stream(stream)), "apd_warmstart_fit_norm")
+
+    def predict(self, counts, measures, features, w_out, stream=None):
+        import numpy as np
+        offs = _offsets(counts)
+        m = np.ascontiguousarray(measures, dtype=np.float64)
+        return _check(load().apd_warmstart_predict(
+            self.handle, len(counts), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(features), _ptr(w_out),
+            _stream(stream)), "apd_warmstart_predict")
+
+    def train_step(self, idx, features, targets, lr, grad_out=None, loss_out=None, stream=None):
+        return _check(load().apd_warmstart_train_step(self.handle, int(idx.shape[0]), _ptr(idx), _ptr(features),
+                                                      _ptr(targets), float(lr), _ptr(grad_out), _ptr(loss_out),
+                                                      _stream(stream)), "apd_warmstart_train_step")
+
+
+def apd_solve_weights_warm(grid, x, A, v, w_out, ws: Workspace, net: WarmStart, opts=None, stream=None):
+    """Single-instance solve from the network's prediction judged against W = 0;
+    returns (status, ApdSolveInfo, used_prediction)."""
+    g, s = make_grid(grid), make_seeds(x, A, v)
+    info = ApdSolveInfo()
+    used = ctypes.c_int32()
+    opts = opts or solve_opts()
+    rc = load().apd_solve_weights_warm(ctypes.byref(g), ctypes.byref(s), _ptr(v), _ptr(w_out),
+                                       ctypes.byref(opts), ctypes.byref(info), ws.handle, net.handle,
+                                       ctypes.byref(used), _stream(stream))
+    _check(rc, "apd_solve_weights_warm", _SOLVE_OK)
+    return rc, info, used.value

@@ -66,11 +66,11 @@ template <int D>
 struct TcGeom;
 template <>
 struct TcGeom<3> {
-    static constexpr int TX = 8, TY = 8, TZ = 8, F = 10, ROWS = 64;  // 64 rows of 8 pixels
+    static constexpr int TX = 8, TY = 8, TZ = 8, F = 10;  // 64 rows of 8 pixels
 };
 template <>
 struct TcGeom<2> {
-    static constexpr int TX = 32, TY = 16, TZ = 1, F = 6, ROWS = 16;  // 16 rows of 32 pixels
+    static constexpr int TX = 32, TY = 16, TZ = 1, F = 6;  // 16 rows of 32 pixels
 };
 
 template <int D, int KIND>

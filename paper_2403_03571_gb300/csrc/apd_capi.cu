@@ -17,9 +17,7 @@ struct apd_workspace {
 
 using namespace apd;
 
-namespace {
-
-constexpr int kHistCap = 32;
+namespace apd {
 
 int map_bits(int bits) {
     if (bits & ST_NOT_SPD) return APD_ERR_NOT_SPD;
@@ -65,6 +63,12 @@ double domain_measure(const apd_grid *gr) {
     for (int d = 0; d < gr->dim; ++d) m *= gr->hi[d] - gr->lo[d];
     return m;
 }
+
+}  // namespace apd
+
+namespace {
+
+constexpr int kHistCap = 32;
 
 int validate_seeds(const apd_seeds *s) {
     if (!s || s->n < 1 || !s->x || !s->A || !s->w) return APD_ERR_ARG;
@@ -317,6 +321,40 @@ struct Solver {
             converged = true;
             return cuda_ok(cudaMemcpyAsync(out, ws.W, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         }
+        return iterate(f0, out, converged);
+    }
+
+    // Start from the better of W_pred and W = 0 by g~ (ties: zero); both are
+    // evaluated, so the gradient at the chosen start is already known.
+    int run_judged(const double *Wpred, double *out, bool &converged, int &used) {
+        converged = false;
+        used = 1;
+        APD_TRY(cuda_ok(cudaMemcpyAsync(ws.W, Wpred, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st)));
+        double fp, dp, ep;
+        APD_TRY(eval(ws.W, ws.gf, nullptr, fp, dp, ep));
+        if (ep < eps) {
+            converged = true;
+            return cuda_ok(cudaMemcpyAsync(out, ws.W, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+        APD_TRY(cuda_ok(cudaMemsetAsync(ws.Wt, 0, (size_t)n * sizeof(double), st)));
+        double fz, dz, ez;
+        APD_TRY(eval(ws.Wt, ws.gft, nullptr, fz, dz, ez));
+        if (ez < eps) {
+            converged = true;
+            used = 0;
+            return cuda_ok(cudaMemcpyAsync(out, ws.Wt, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+        if (fz <= fp) {
+            std::swap(ws.W, ws.Wt);
+            std::swap(ws.gf, ws.gft);
+            used = 0;
+            return iterate(fz, out, converged);
+        }
+        return iterate(fp, out, converged);
+    }
+
+    // L-BFGS iterations from the evaluated point ws.W (gradient ws.gf, f0 = f(ws.W)).
+    int iterate(double f0, double *out, bool &converged) {
         int hist = 0, newest = kHistCap - 1;
         double gamma = 1.0;
         int fails = 0;
@@ -377,7 +415,8 @@ struct Solver {
 
 int solve_impl(const GridDev &g, const apd_grid *grid, int n, const double *x, const double *A,
                const double *w0, const double *v, double *w_out, const apd_solve_opts &o,
-               apd_solve_info &info, Workspace &ws, cudaStream_t st, bool need_moments_at_out) {
+               apd_solve_info &info, Workspace &ws, cudaStream_t st, bool need_moments_at_out,
+               bool judged = false, int *used = nullptr) {
     Solver s(ws);
     s.g = g;
     s.n = n;
@@ -388,11 +427,13 @@ int solve_impl(const GridDev &g, const apd_grid *grid, int n, const double *x, c
     s.st = st;
     s.eps = o.eps;
     s.max_evals = o.max_evals;
-    s.history = std::max(1, std::min(o.history, kHistCap));
+    s.history = std::max(1, std::min(o.history, kHistCap - 1));  // the slot written next is never in use
     s.check_volumes = o.check_volumes != 0;
     s.measure = domain_measure(grid);
     bool conv = false;
-    int rc = s.run(w0, w_out, conv);
+    int used_pred = 0;
+    int rc = judged ? s.run_judged(w0, w_out, conv, used_pred) : s.run(w0, w_out, conv);
+    if (used) *used = used_pred;
     info.evaluations += s.evals;
     info.iterations += s.iters;
     info.rescored_fp64 += s.rescored;
@@ -496,6 +537,8 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.rho, kHistCap * sizeof(double));
     alloc((void **)&w.X, (size_t)max_n * dim * sizeof(double));
     alloc((void **)&w.vbuf, (size_t)max_n * sizeof(double));
+    alloc((void **)&w.wfeat, (size_t)max_n * kWarmFeatMax * sizeof(float));
+    alloc((void **)&w.wpred, (size_t)max_n * sizeof(double));
     if (ok && cudaMallocHost((void **)&w.sc_host, sizeof(DevScalars)) != cudaSuccess) ok = false;
     if (ok && cudaMemset(w.sc, 0, sizeof(DevScalars)) != cudaSuccess) ok = false;
     if (ok && cudaMemset(w.recs, 0, (size_t)w.n_pad_max * sizeof(SeedRec)) != cudaSuccess) ok = false;
@@ -513,7 +556,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
     void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_cand, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
-                    w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf};
+                    w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.sc_host) cudaFreeHost(w.sc_host);
@@ -630,6 +673,36 @@ int apd_solve_weights(const apd_grid *grid, const apd_seeds *seeds, const double
     if (rc == APD_OK)
         rc = solve_impl(g, grid, seeds->n, seeds->x, seeds->A, seeds->w, v, w_out, o, inf, ws->w, st, false);
     if (rc >= 0) cudaStreamSynchronize(st);
+    inf.status = rc;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
+int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
+                           const apd_solve_opts *opts, apd_solve_info *info, apd_workspace *ws, apd_mlp *net,
+                           int32_t *used_pred, apd_stream_t stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    apd_solve_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    GridDev g;
+    apd_solve_opts o;
+    cudaStream_t st = (cudaStream_t)stream;
+    int used = 0;
+    int rc = net ? solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st) : APD_ERR_ARG;
+    if (rc == APD_OK && warmstart_dim(net) != g.dim) rc = APD_ERR_ARG;
+    if (rc == APD_OK) {
+        const int64_t offs[2] = {0, seeds->n};
+        const double meas = domain_measure(grid);
+        rc = apd_warmstart_features(net, 1, offs, &meas, seeds->x, seeds->A, v, ws->w.wfeat, stream);
+        if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, &meas, ws->w.wfeat, ws->w.wpred, stream);
+        ws->w.kernel_launches += 2;
+    }
+    if (rc == APD_OK)
+        rc = solve_impl(g, grid, seeds->n, seeds->x, seeds->A, ws->w.wpred, v, w_out, o, inf, ws->w, st, false,
+                        true, &used);
+    if (rc >= 0) cudaStreamSynchronize(st);
+    if (used_pred) *used_pred = used;
     inf.status = rc;
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;

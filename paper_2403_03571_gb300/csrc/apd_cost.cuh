@@ -98,4 +98,89 @@ __device__ __forceinline__ void cost32_bound_rel(const SeedRec32 &r, const float
     E = 5.9604644775390625e-8f * (16.f * (qa + fabsf(wp) + fabsf(c)) + 12.f * ya) + 1e-37f;
 }
 
+// Rescoring of a queued pixel, one warp per pixel, lanes over seeds.
+// Pass 1: FP32 direct-form cost of every seed with y - x formed from FP32
+// high/low splits (error <= 2u |y - x|), and a per-seed rounding bound
+//     E_k = 16 u (sum_ab |A_ab| |d_a| |d_b| + |w'_k| + |C_k|),
+// covering the roundings of d, A, the two 3-term dot products, w' and the final
+// subtraction (about 11 u of them) and the FP64 reference's own error.  The
+// threshold is min_k (C_k + E_k).  Pass 2: every seed with C_k - E_k <= threshold
+// is recomputed in FP64 with the reference arithmetic; the smallest FP64 cost
+// wins, ties to the lowest index.  Any seed left out has an exact cost above the
+// exact minimum by more than the FP64 rounding, so the result equals the FP64
+// argmin over all seeds.
+template <int D>
+__device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, const double *__restrict__ x,
+                                              const double *__restrict__ A, const double *__restrict__ w,
+                                              const SeedRec32 *__restrict__ r32, const uint32_t fj,
+                                              const float wrh, const float wrl, DevScalars *__restrict__ sc,
+                                              unsigned long long *__restrict__ gmom,
+                                              int32_t *__restrict__ labels) {
+    constexpr int K = moment_width(D);
+    const int lane = threadIdx.x & 31;
+    const long long j = (long long)fj;
+    int k[3] = {0, 0, 0};
+    long long rr = j;
+    double y[D];
+    float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        k[a] = (int)(rr % g.res[a]);
+        rr /= g.res[a];
+        y[a] = __dadd_rn(g.lo[a], __dmul_rn((double)k[a] + 0.5, g.h[a]));
+        yh[a] = (float)y[a];
+        yl[a] = (float)(y[a] - (double)yh[a]);
+    }
+    // pass 1: threshold = min over seeds of (C + E)
+    float thr = __int_as_float(0x7f800000);
+    for (int s = lane; s < n; s += 32) {
+        float c, E;
+        cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
+        thr = fminf(thr, c + E);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) thr = fminf(thr, __shfl_xor_sync(0xffffffffu, thr, off));
+    // pass 2: FP64 reference cost of the candidates
+    double best = __longlong_as_double(0x7ff0000000000000ll);
+    int bi = 0x7fffffff;
+    for (int s = lane; s < n; s += 32) {
+        float c, E;
+        cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
+        if (!(c - E <= thr)) continue;
+        const double c64 = cost64<D>(y, x + (size_t)s * D, A + (size_t)s * D * D, w[s]);
+        if (c64 < best) {
+            best = c64;
+            bi = s;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob < best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        if (bi < 0 || bi >= n) {
+            atomicOr(&sc->status, ST_BAD_LABEL);
+        } else {
+            if (labels) labels[j] = bi;
+            unsigned long long u[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = 2ull * (unsigned long long)k[a] + 1ull;
+            unsigned long long *o = gmom + (size_t)bi * K;
+            atomicAdd(&o[0], 1ull);
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(&o[1 + a], u[a]);
+            int e = 1 + D;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = a; b < D; ++b) atomicAdd(&o[e++], u[a] * u[b]);
+        }
+    }
+}
+
 }  // namespace apd

@@ -1,0 +1,422 @@
+// FP32 scoring of one pixel tile (Algorithm 1 fused with the moment
+// reduction), shared by the one-instance kernel and the batched persistent
+// kernel.  The method and its rounding bound are described in
+// apd_assign_fp32.cu.
+#pragma once
+
+#include <float.h>
+
+#include "apd_internal.cuh"
+
+namespace apd {
+namespace fp32 {
+
+constexpr float kUnit = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of FP32
+// Rounding-bound multiplier: about 24 roundings of size <= u T in the cost
+// chain plus <= 62 u |C| from the packed 5-bit index, with a 1.8x margin.
+constexpr float kKappa = 160.f;
+constexpr int kTable = 128;  // shared-memory hash slots per CTA
+
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+    return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long b) {
+    return make_float2(__uint_as_float((unsigned)(b & 0xffffffffu)), __uint_as_float((unsigned)(b >> 32)));
+}
+// packed FP32x2 fused multiply-add: (a * b + c) elementwise
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+    return bits_f2(r);
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+// cost with the local seed index in the 5 low mantissa bits
+__device__ __forceinline__ float pack(float c, unsigned idx) {
+    return __uint_as_float((__float_as_uint(c) & ~31u) | idx);
+}
+
+// Row coefficients of two consecutive seeds (see the file comment), returned as
+// duplicated pairs for the packed pixel-pair FMAs.  Every multiply is rounded on
+// its own (no contraction), so the fast and update passes compute identical bits.
+template <int D>
+__device__ __forceinline__ void seed_pair_coeffs(const float4 (*phi)[kChunk], int s0, float f1, float f2,
+                                                 float2 &qa, float2 &qb, float2 &ba, float2 &bbb,
+                                                 float2 &aa2, float2 &ab2) {
+    float a[2], bb[2], q00[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float4 v0 = phi[0][s0 + e];
+        const float4 v1 = phi[1][s0 + e];
+        if (D == 3) {
+            const float4 v2 = phi[2][s0 + e];
+            const float d1 = __fsub_rn(f1, v0.x);
+            const float d2 = __fsub_rn(f2, v0.y);
+            const float e0 = fmaf(v1.z, d2, __fmul_rn(v1.y, d1));
+            bb[e] = fmaf(2.f, e0, v1.w);
+            const float t = fmaf(v0.w, d2, __fmul_rn(v0.z, d1));
+            float aa = fmaf(d1, t, v2.x);
+            aa = fmaf(v2.y, e0, aa);
+            a[e] = fmaf(__fmul_rn(v1.x, d2), d2, aa);
+            q00[e] = v2.z;
+        } else {
+            const float d1 = __fsub_rn(f1, v0.x);
+            const float u1 = fmaf(v0.y, d1, v0.z);
+            a[e] = fmaf(d1, u1, v0.w);
+            bb[e] = fmaf(v1.y, d1, v1.x);
+            q00[e] = v1.z;
+        }
+    }
+    qa = make_float2(q00[0], q00[0]);
+    qb = make_float2(q00[1], q00[1]);
+    ba = make_float2(bb[0], bb[0]);
+    bbb = make_float2(bb[1], bb[1]);
+    aa2 = make_float2(a[0], a[0]);
+    ab2 = make_float2(a[1], a[1]);
+}
+
+// Two new packed keys into the top-2 (b1 <= b2) of one pixel; gi follows b1.
+__device__ __forceinline__ void top2_update(float &b1, float &b2, int &gi, float ka, float kb, int gbase) {
+    const float mn = fminf(ka, kb), mx = fmaxf(ka, kb);
+    const bool lt = mn < b1;
+    b2 = fmin3(b2, fmaxf(b1, mn), mx);
+    b1 = fminf(b1, mn);
+    gi = lt ? (gbase | (int)(__float_as_uint(mn) & 31u)) : gi;
+}
+
+template <int D>
+struct SharedLayout {
+    static constexpr int K = moment_width(D);
+    SeedRec raw[2][kChunk];
+    float4 phi[D][kChunk];
+    unsigned long long tval[kTable][K];
+    int tkey[kTable];
+    uint64_t bar[2];
+    int start_chunk;
+};
+
+template <int D>
+__device__ __forceinline__ void table_add(SharedLayout<D> &sm, unsigned long long *gmom, int label,
+                                          const unsigned long long (&val)[moment_width(D)]) {
+    constexpr int K = moment_width(D);
+    int slot = label & (kTable - 1);
+    for (int probe = 0; probe < kTable; ++probe) {
+        int k = atomicCAS(&sm.tkey[slot], -1, label);
+        if (k == -1 || k == label) {
+#pragma unroll
+            for (int v = 0; v < K; ++v)
+                if (val[v]) atomicAdd(&sm.tval[slot][v], val[v]);
+            return;
+        }
+        slot = (slot + 1) & (kTable - 1);
+    }
+#pragma unroll
+    for (int v = 0; v < K; ++v)
+        if (val[v]) atomicAdd(&gmom[(size_t)label * K + v], val[v]);
+}
+
+template <int D>
+__device__ __forceinline__ void flush_run(SharedLayout<D> &sm, unsigned long long *gmom, int label,
+                                          unsigned long long cnt, unsigned long long s0,
+                                          unsigned long long s00, unsigned long long u1,
+                                          unsigned long long u2) {
+    unsigned long long val[moment_width(D)];
+    if (D == 3) {
+        val[0] = cnt;
+        val[1] = s0;
+        val[2] = cnt * u1;
+        val[3] = cnt * u2;
+        val[4] = s00;
+        val[5] = s0 * u1;
+        val[6] = s0 * u2;
+        val[7] = cnt * u1 * u1;
+        val[8] = cnt * u1 * u2;
+        val[9] = cnt * u2 * u2;
+    } else {
+        val[0] = cnt;
+        val[1] = s0;
+        val[2] = cnt * u1;
+        val[3] = s00;
+        val[4] = s0 * u1;
+        val[5] = cnt * u1 * u1;
+    }
+    table_add<D>(sm, gmom, label, val);
+}
+
+
+// One scoring problem: an instance's grid, seeds in scan order and outputs.
+struct TileSrc {
+    GridDev g;
+    int n;
+    int n_chunks;
+    float R_tile;                 // tile half-diagonal bound
+    const SeedRec *recs;          // [n_chunks * kChunk] scan order
+    const uint32_t *scodes;       // sorted Morton codes (null: natural order)
+    const int32_t *perm;          // scan position -> seed index (null: identity)
+    unsigned long long *gmom;     // [n][K]
+    uint32_t *flags;              // queue of pixels for FP64 rescoring
+    int32_t *labels;              // [J] or null
+    DevScalars *sc;
+};
+
+// Scores the P x TY x TZ tile (bx, by, bz) of `s` with NT = TY * TZ threads.
+// `uses` counts the completed phases of the two chunk barriers across the
+// tiles a CTA has scored; the shared-memory table must be empty on entry and
+// is empty again on return.  Returns false if a chunk wait timed out (the CTA
+// must then stop: a copy may still be in flight).
+template <int D, int P, int TY, int TZ>
+__device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s, const int bx, const int by,
+                                           const int bz, uint32_t (&uses)[2]) {
+    constexpr int K = moment_width(D);
+    constexpr int NT = TY * TZ;
+    const GridDev &g = s.g;
+    const int n = s.n, n_chunks = s.n_chunks;
+
+    const int tid = threadIdx.x;
+    const int ty = tid % TY;
+    const int tz = tid / TY;
+    const int k0b = bx * P;
+    const int k1b = by * TY;
+    const int k2b = (D == 3) ? bz * TZ : 0;
+    const int k1 = k1b + ty;
+    const int k2 = k2b + tz;
+    const bool row_valid = (k1 < g.res[1]) && (D == 2 || k2 < g.res[2]);
+
+    // CTA reference point (FP64): row centre along axis 0, tile centre along 1, 2
+    const double c0 = g.lo[0] + (double)(k0b + P / 2) * g.h[0];
+    const double c1 = g.lo[1] + (double)(k1b + TY / 2) * g.h[1];
+    const double c2 = (D == 3) ? g.lo[2] + (double)(k2b + TZ / 2) * g.h[2] : 0.0;
+    const float f1 = ((float)(ty - TY / 2) + 0.5f) * g.h32[1];
+    const float f2 = (D == 3) ? ((float)(tz - TZ / 2) + 0.5f) * g.h32[2] : 0.f;
+    float2 y2[P / 2];
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q)
+        y2[q] = make_float2(((float)(2 * q - P / 2) + 0.5f) * g.h32[0],
+                            ((float)(2 * q + 1 - P / 2) + 0.5f) * g.h32[0]);
+
+    // Scan order of the seed chunks: with Morton-sorted seeds, start at the chunk
+    // holding this tile's Morton position and zig-zag outwards, so that the near
+    // seeds (the likely winners) come first and later groups are mostly skipped.
+    int start_chunk = 0;
+    if (s.scodes) {
+        double frac[3] = {0.0, 0.0, 0.0};
+        const int kc[3] = {k0b + P / 2, k1b + TY / 2, k2b + TZ / 2};
+#pragma unroll
+        for (int a = 0; a < D; ++a) frac[a] = ((double)kc[a] + 0.5) / (double)g.res[a];
+        const uint32_t code = morton_code(D, frac);
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s.scodes[mid] < code) lo = mid + 1;
+            else hi = mid;
+        }
+        start_chunk = min(lo / kChunk, n_chunks - 1);
+    }
+    auto chunk_at = [&](int k) {
+        const int off = (k & 1) ? ((k + 1) >> 1) : -(k >> 1);
+        int c = (start_chunk + off) % n_chunks;
+        return c < 0 ? c + n_chunks : c;
+    };
+    const double wref = dkey_inv(s.sc->wref_key);
+    if (tid == 0) {
+        for (int k = 0; k < 2 && k < n_chunks; ++k) {
+            mbar_expect_tx(&sm.bar[k], kChunk * sizeof(SeedRec));
+            bulk_g2s(&sm.raw[k][0], s.recs + (size_t)chunk_at(k) * kChunk, kChunk * sizeof(SeedRec),
+                     &sm.bar[k]);
+        }
+    }
+
+    // per pixel: two smallest packed costs (b1 <= b2) and the scan position of the best
+    float b1[P], b2[P];
+    int GI[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        b1[p] = FLT_MAX;
+        b2[p] = FLT_MAX;
+        GI[p] = 0;
+    }
+    bool ok = true;
+
+    for (int k = 0; k < n_chunks; ++k) {
+        const int b = k & 1;
+        const int c = chunk_at(k);
+        if (ok && !mbar_wait_bounded(&sm.bar[b], uses[b] & 1u, &s.sc->status)) ok = false;
+        ++uses[b];
+        // transform this chunk into the row-form coefficients
+        for (int sl = tid; sl < kChunk; sl += NT) {
+            const int si = c * kChunk + sl;
+            float4 v0, v1, v2;
+            if (ok && si < n) {
+                const SeedRec &r = sm.raw[b][sl];
+                const float d0 = (float)(c0 - r.x[0]);
+                const float x1p = (float)(r.x[1] - c1);
+                const float wp = (float)(r.w - wref);  // <= 0
+                if (D == 3) {
+                    const float x2p = (float)(r.x[2] - c2);
+                    const float A00 = r.a[0], A01 = r.a[1], A02 = r.a[2], A11 = r.a[3],
+                                A12 = r.a[4], A22 = r.a[5];
+                    v0 = make_float4(x1p, x2p, A11, 2.f * A12);
+                    v1 = make_float4(A22, A01, A02, 2.f * A00 * d0);
+                    v2 = make_float4(A00 * d0 * d0 - wp, 2.f * d0, A00, 0.f);
+                } else {
+                    const float A00 = r.a[0], A01 = r.a[1], A11 = r.a[2];
+                    v0 = make_float4(x1p, A11, 2.f * A01 * d0, A00 * d0 * d0 - wp);
+                    v1 = make_float4(2.f * A00 * d0, 2.f * A01, A00, 0.f);
+                    v2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            } else {  // padding seed: constant huge cost
+                if (D == 3) {
+                    v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    v2 = make_float4(1e30f, 0.f, 0.f, 0.f);
+                } else {
+                    v0 = make_float4(0.f, 0.f, 0.f, 1e30f);
+                    v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    v2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            sm.phi[0][sl] = v0;
+            sm.phi[1][sl] = v1;
+            if (D == 3) sm.phi[2][sl] = v2;
+        }
+        // a timed-out wait in any thread stops the whole CTA
+        ok = __syncthreads_and(ok);
+        if (tid == 0 && ok && k + 2 < n_chunks) {
+            mbar_expect_tx(&sm.bar[b], kChunk * sizeof(SeedRec));
+            bulk_g2s(&sm.raw[b][0], s.recs + (size_t)chunk_at(k + 2) * kChunk, kChunk * sizeof(SeedRec),
+                     &sm.bar[b]);
+        }
+        if (ok) {
+            const int valid_in_chunk = min(kChunk, n - c * kChunk);
+            const int groups = (valid_in_chunk + kGroup - 1) / kGroup;
+            for (int gr = 0; gr < groups; ++gr) {
+                // fast pass: smallest cost of this group per pixel (one 3-input min per two pairs)
+                float gm[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) gm[p] = FLT_MAX;
+#pragma unroll 2
+                for (int l = 0; l < kGroup; l += 2) {
+                    float2 qa, qb, ba, bbb, aa2, ab2;
+                    seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
+#pragma unroll
+                    for (int q = 0; q < P / 2; ++q) {
+                        const float2 ca = ffma2(ffma2(qa, y2[q], ba), y2[q], aa2);
+                        const float2 cb = ffma2(ffma2(qb, y2[q], bbb), y2[q], ab2);
+                        gm[2 * q] = fmin3(gm[2 * q], ca.x, cb.x);
+                        gm[2 * q + 1] = fmin3(gm[2 * q + 1], ca.y, cb.y);
+                    }
+                }
+                // a packed key differs from its cost by < 32 ulp: a group whose smallest
+                // cost exceeds b2 by the margin cannot change b1 or b2 and is skipped
+                bool need = false;
+#pragma unroll
+                for (int p = 0; p < P; ++p) need |= gm[p] < fmaf(fabsf(b2[p]), 0x1p-15f, b2[p]);
+                if (!__any_sync(0xffffffffu, need)) continue;
+                // update pass: recompute the same costs, packed top-2 with the index
+                const int gbase = c * kChunk + gr * kGroup;
+#pragma unroll 2
+                for (int l = 0; l < kGroup; l += 2) {
+                    float2 qa, qb, ba, bbb, aa2, ab2;
+                    seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
+                    const unsigned la = (unsigned)l, lb = (unsigned)(l + 1);
+#pragma unroll
+                    for (int q = 0; q < P / 2; ++q) {
+                        const float2 ca = ffma2(ffma2(qa, y2[q], ba), y2[q], aa2);
+                        const float2 cb = ffma2(ffma2(qb, y2[q], bbb), y2[q], ab2);
+                        top2_update(b1[2 * q], b2[2 * q], GI[2 * q], pack(ca.x, la), pack(cb.x, lb), gbase);
+                        top2_update(b1[2 * q + 1], b2[2 * q + 1], GI[2 * q + 1], pack(ca.y, la),
+                                    pack(cb.y, lb), gbase);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // scan position -> seed index
+    if (s.perm && ok) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) GI[p] = GI[p] < n ? s.perm[GI[p]] : GI[p];
+    }
+
+    // flag near ties, write labels, accumulate moments
+    const float lam_abs = (float)__longlong_as_double((long long)s.sc->lam_abs_bits);
+    const float lam_min = (float)__longlong_as_double((long long)s.sc->lam_min_bits);
+    const float inv_lam = 1.f / fmaxf(lam_min, 1e-30f);
+    const long long rowbase = (long long)g.res[0] * ((long long)k1 + (long long)g.res[1] * (long long)k2);
+    const unsigned long long u1 = 2ull * (unsigned long long)k1 + 1ull;
+    const unsigned long long u2 = 2ull * (unsigned long long)k2 + 1ull;
+    int cur = -1;
+    unsigned long long cnt = 0, s0 = 0, s00 = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int k0 = k0b + p;
+        const bool valid = ok && row_valid && (k0 < g.res[0]);
+        bool flagged = false;
+        if (valid) {
+            const float cs = fabsf(b1[p]) * 1.0078125f + 1e-30f;
+            const float rr = s.R_tile + sqrtf(cs * inv_lam);
+            const float T = lam_abs * rr * rr + cs;
+            const float E = kKappa * kUnit * T;
+            // GI >= n only if a padding seed won (all real costs non-finite or huge)
+            flagged = !(b2[p] - b1[p] > 2.f * E) || GI[p] >= n;
+            const long long j = rowbase + k0;
+            if (flagged) {
+                const unsigned slot = atomicAdd(&s.sc->flag_count, 1u);
+                s.flags[slot] = (uint32_t)j;
+            }
+            if (s.labels) s.labels[j] = GI[p];
+        }
+        const int L = (valid && !flagged) ? GI[p] : -1;
+        if (L != cur) {
+            if (cur >= 0) flush_run<D>(sm, s.gmom, cur, cnt, s0, s00, u1, u2);
+            cur = L;
+            cnt = s0 = s00 = 0;
+        }
+        if (L >= 0) {
+            const unsigned long long u0 = 2ull * (unsigned long long)k0 + 1ull;
+            cnt += 1;
+            s0 += u0;
+            s00 += u0 * u0;
+        }
+    }
+    if (cur >= 0) flush_run<D>(sm, s.gmom, cur, cnt, s0, s00, u1, u2);
+    __syncthreads();
+    // flush the table to the global moments and leave it empty
+    for (int t = tid; t < kTable; t += NT) {
+        const int key = sm.tkey[t];
+        if (key >= 0) {
+#pragma unroll
+            for (int v = 0; v < K; ++v) {
+                const unsigned long long val = sm.tval[t][v];
+                if (val) atomicAdd(&s.gmom[(size_t)key * K + v], val);
+                sm.tval[t][v] = 0ull;
+            }
+            sm.tkey[t] = -1;
+        }
+    }
+    __syncthreads();
+    return ok;
+}
+
+// Empty table and initialised chunk barriers; call once per CTA.
+template <int D>
+__device__ __forceinline__ void init_shared(SharedLayout<D> &sm) {
+    constexpr int K = moment_width(D);
+    for (int t = threadIdx.x; t < kTable; t += blockDim.x) {
+        sm.tkey[t] = -1;
+#pragma unroll
+        for (int v = 0; v < K; ++v) sm.tval[t][v] = 0ull;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+}  // namespace fp32
+}  // namespace apd

@@ -45,6 +45,7 @@ static_assert(sizeof(SeedRec32) == 64, "SeedRec32 must be 64 bytes");
 constexpr int kChunk = 256;         // seeds per shared-memory chunk (= scoring CTA size)
 constexpr int kSortMax = 16384;     // largest padded seed count ordered on the device
 constexpr int kGroup = 32;          // seeds per packed-index group (5 low mantissa bits)
+constexpr int kWarmFeatMax = 23;    // warm-start features per seed (3D; 20 in 2D)
 
 // Small block of device scalars owned by the workspace.
 struct DevScalars {
@@ -100,6 +101,8 @@ struct Workspace {
     double *rho = nullptr;              // [hist_cap]
     double *X = nullptr;                // [max_n * dim] seed positions for Lloyd
     double *vbuf = nullptr;             // [max_n]
+    float *wfeat = nullptr;             // [max_n][kWarmFeatMax] warm-start features
+    double *wpred = nullptr;            // [max_n] predicted weights
     int64_t last_pixels = 0, last_pairs = 0;
     // optional kernel timing (event pairs around scoring launches)
     bool profiling = false;
@@ -215,6 +218,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     atomicOr(status, ST_TIMEOUT);
     return false;
 }
+
+// ----------------------------------------------------------------------------
+// host helpers (apd_capi.cu)
+// ----------------------------------------------------------------------------
+int map_bits(int bits);                              // ST_* bits -> apd_status
+int validate_grid(const apd_grid *gr, GridDev &g);  // apd_grid -> GridDev, APD_ERR_ARG if invalid
+double domain_measure(const apd_grid *gr);          // |Omega|
+int warmstart_dim(const apd_mlp *net);               // dimension of a warm-start network (apd_warmstart.cu)
 
 // ----------------------------------------------------------------------------
 // launchers (defined in the .cu files)

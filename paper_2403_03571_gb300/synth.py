@@ -27,7 +27,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Optional, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -253,10 +253,61 @@ def workload_3d_10000(instance: int = 0, m: int = 512) -> Instance:
     return make_instance(3, 10000, m, workload_seed(2, instance), name=f"3d_n10000_{m}cube")
 
 
-def batched_2d_table(count: int = 256, seed: Optional[int] = None):
-    """Per-instance (N, M) for the batched 2D workload: N log-uniform in [50, 2000],
-    M the smallest of {256, 384, 512, 768, 1024} meeting eq. (2.10) for that
-    instance's drawn volumes (1024 when none does)."""
-    g = rng(workload_seed(3) if seed is None else seed)
+def required_resolution(dim: int, v_min: float, eps: float = 0.01, measure: float = 1.0) -> int:
+    """Smallest M with measure / M^dim <= eps v_min / 2^dim (the resolution rule of
+    eq. (2.10), non-strict), used to size the grids of the batched workloads."""
+    target = (2.0 ** dim) * measure / (eps * v_min)
+    m = max(1, int(math.floor(target ** (1.0 / dim))))
+    while m ** dim < target:
+        m += 1
+    return m
+
+
+def batched_table(count: int = 256, seed: Optional[int] = None, k: int = 3):
+    """Per-instance seed counts N (log-uniform in [50, 2000]) and generator seeds of a
+    batched workload."""
+    g = rng(workload_seed(k) if seed is None else seed)
     ns = np.exp(g.uniform(math.log(50), math.log(2000), count)).round().astype(int)
     return ns, g.integers(0, 2**31 - 1, count)
+
+
+BATCH_2D_RES = (256, 384, 512, 768, 1024)
+
+
+def batched_2d_instances(count: int = 256, seed: Optional[int] = None) -> List[Instance]:
+    """The batched 2D workload: N log-uniform in [50, 2000], seeds with rejection
+    (C = 0.2), 2D lognormal anisotropy (sigma 0.3), lognormal volumes (sigma 0.5)
+    normalised to 1, and per instance the smallest grid of 256^2 .. 1024^2 that
+    meets eq. (2.10) at eps = 1% (1024^2 when none does)."""
+    ns, seeds = batched_table(count, seed, k=3)
+    out = []
+    for b, (n, sd) in enumerate(zip(ns, seeds)):
+        inst = make_instance(2, int(n), BATCH_2D_RES[0], int(sd), name=f"b2d_{b}")
+        need = required_resolution(2, float(inst.v.min()))
+        m = next((r for r in BATCH_2D_RES if r >= need), BATCH_2D_RES[-1])
+        inst.grid = Grid.cube(2, m)
+        out.append(inst)
+    return out
+
+
+def batched_3d_instances(count: int, seed: int, m_cap: int = 256, n_lo: int = 50,
+                         n_hi: int = 2000) -> List[Instance]:
+    """3D instances with the 1000-seed workload's laws, N log-uniform in
+    [n_lo, n_hi] and M from eq. (2.10) at eps = 1%, capped at m_cap (the
+    training distribution of the learned warm start)."""
+    g = rng(seed)
+    ns = np.exp(g.uniform(math.log(n_lo), math.log(n_hi), count)).round().astype(int)
+    seeds = g.integers(0, 2**31 - 1, count)
+    out = []
+    for b, (n, sd) in enumerate(zip(ns, seeds)):
+        inst = make_instance(3, int(n), 16, int(sd), name=f"b3d_{b}")
+        m = min(m_cap, required_resolution(3, float(inst.v.min())))
+        inst.grid = Grid.cube(3, m)
+        out.append(inst)
+    return out
+
+
+def concat(instances: List[Instance]):
+    """Concatenated (x, A, w, v) of a batch, in instance order."""
+    return (np.concatenate([i.x for i in instances]), np.concatenate([i.A for i in instances]),
+            np.concatenate([i.w for i in instances]), np.concatenate([i.v for i in instances]))

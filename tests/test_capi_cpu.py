@@ -67,3 +67,17 @@ def test_argument_errors_before_cuda(lib):
     assert lib.apd_workspace_create(ctypes.byref(h), 2, 0, 100) == capi.APD_ERR_ARG
     assert lib.apd_workspace_create(None, 2, 10, 100) == capi.APD_ERR_ARG
     lib.apd_workspace_destroy(None)
+    # batches: bad dimension, count, null arrays, tile index out of range
+    grids = (capi.ApdGrid * 2)(g, g)
+    ns = (ctypes.c_int32 * 2)(5, 6)
+    assert lib.apd_batch_create(ctypes.byref(h), 4, 2, grids, ns, -1) == capi.APD_ERR_ARG
+    assert lib.apd_batch_create(ctypes.byref(h), 2, 0, grids, ns, -1) == capi.APD_ERR_ARG
+    assert lib.apd_batch_create(ctypes.byref(h), 2, 2, None, ns, -1) == capi.APD_ERR_ARG
+    assert lib.apd_batch_create(ctypes.byref(h), 2, 2, grids, None, -1) == capi.APD_ERR_ARG
+    assert lib.apd_batch_create(ctypes.byref(h), 2, 2, grids, ns, 99) == capi.APD_ERR_ARG
+    assert lib.apd_batch_create(None, 2, 2, grids, ns, -1) == capi.APD_ERR_ARG
+    assert lib.apd_batch_solve_weights(None, None, None, None, None, None, None, None,
+                                       None) == capi.APD_ERR_ARG
+    assert lib.apd_batch_cell_moments(None, None, None, None, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_batch_kernel_launches(None) == -1
+    lib.apd_batch_destroy(None)

@@ -1,0 +1,98 @@
+"""Pins of the warm-start oracle (oracle/warmstart.py) against things other
+than itself: brute-force neighbours, finite differences of the FP64 loss, the
+layer sizes, and the scale invariance the feature definition implies."""
+import numpy as np
+import pytest
+
+from oracle import warmstart as ow
+from paper_2403_03571_gb300 import synth
+
+
+def _instance(dim, n, seed):
+    g = synth.rng(seed)
+    x = synth.seeds_with_rejection(g, n, dim, 0.2)
+    A = synth.aniso_2d_lognormal(g, n, 0.3) if dim == 2 else synth.aniso_3d_lognormal(g, n, 0.3)
+    v = synth.volumes_lognormal(g, n, 0.5)
+    return x, A, v
+
+
+def test_parameter_counts_from_layer_sizes():
+    # F -> 64 -> 64 -> 64 -> 1 with biases: 9729 (2D, F = 20) and 9921 (3D, F = 23)
+    assert ow.n_features(2) == 20 and ow.n_features(3) == 23
+    assert ow.n_params(2) == 20 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1 == 9729
+    assert ow.n_params(3) == 9921
+
+
+@pytest.mark.parametrize("dim,n", [(2, 300), (3, 200), (2, 5)])
+def test_features_match_brute_force_neighbours(dim, n):
+    x, A, v = _instance(dim, n, 3 + dim)
+    f = ow.features(x, A, v, 1.0)
+    s = n / 1.0
+    d = np.sqrt(((x[:, None, :] - x[None, :, :]) ** 2).sum(-1))
+    np.fill_diagonal(d, np.inf)
+    order = np.argsort(d, axis=1, kind="stable")
+    k = min(8, n - 1)
+    c = 1 + dim * (dim + 1) // 2
+    np.testing.assert_allclose(f[:, 0], v * s, rtol=1e-15)
+    np.testing.assert_allclose(f[:, c:c + k], np.take_along_axis(d, order[:, :k], 1) * s ** (1 / dim), rtol=1e-12)
+    np.testing.assert_allclose(f[:, c + 8:c + 8 + k], v[order[:, :k]] * s, rtol=1e-15)
+    assert np.all(f[:, c + k:c + 8] == 4.0) and np.all(f[:, c + 8 + k:] == 0.0)
+    # A entries: upper triangle of the symmetric part, row by row
+    iu = np.triu_indices(dim)
+    np.testing.assert_allclose(f[:, 1:c], A[:, iu[0], iu[1]], rtol=1e-15)
+
+
+def test_features_scale_invariant():
+    # x -> c x, v -> c^D v, |O| -> c^D |O| leaves every feature unchanged
+    x, A, v = _instance(3, 150, 9)
+    f1 = ow.features(x, A, v, 1.0)
+    c = 2.5
+    f2 = ow.features(c * x, A, c ** 3 * v, c ** 3)
+    np.testing.assert_allclose(f1, f2, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gradient_matches_finite_differences(dim):
+    g = np.random.Generator(np.random.PCG64(11 + dim))
+    F, P = ow.n_features(dim), ow.n_params(dim)
+    # He-scale weights keep y = O(1), so the FP64 rounding of the loss stays far
+    # below the finite-difference step's truncation error
+    params = g.normal(0, 1.0, P) * 0.15
+    norm = np.concatenate([g.normal(0, 0.1, F), np.exp(g.normal(0, 0.1, F))])
+    feats = g.normal(0, 1, (24, F))
+    targets = g.normal(0, 1, 24)
+    L, grad = ow.loss_grad(params, norm, feats, targets, dim)
+    assert L == pytest.approx(ow.loss(params, norm, feats, targets, dim), rel=1e-15)
+    # every layer's weights and biases are represented in the sampled coordinates
+    F64 = 64 * F
+    bounds = [0, F64, F64 + 64, F64 + 64 + 4096, F64 + 128 + 4096, F64 + 128 + 8192, F64 + 192 + 8192,
+              F64 + 256 + 8192, P]
+    picks = np.concatenate([g.choice(np.arange(a, b), size=min(25, b - a), replace=False)
+                            for a, b in zip(bounds[:-1], bounds[1:])])
+    h = 1e-6
+    tol_abs = 16 * 2.3e-16 * max(1.0, L) / h  # rounding of the two loss values over the step
+    for p in picks:
+        e = np.zeros(P)
+        e[p] = h
+        fd = (ow.loss(params + e, norm, feats, targets, dim) - ow.loss(params - e, norm, feats, targets, dim)) / (2 * h)
+        assert fd == pytest.approx(grad[p], rel=2e-6, abs=tol_abs), p
+
+
+def test_gradient_check_catches_a_dropped_relu_mask():
+    # a plausible mistake (no ReLU derivative in the first hidden layer) must fail the pin above
+    dim = 2
+    g = np.random.Generator(np.random.PCG64(5))
+    F, P = ow.n_features(dim), ow.n_params(dim)
+    params = g.normal(0, 0.3, P)
+    norm = np.concatenate([np.zeros(F), np.ones(F)])
+    feats = g.normal(0, 1, (16, F))
+    targets = g.normal(0, 1, 16)
+    W1, b1, W2, b2, W3, b3, w4, b4 = ow.unpack(params, dim)
+    y, (z, h1, h2, h3) = ow.forward(params, norm, feats, dim)
+    dy = 2 * (y - targets) / 16
+    d3 = np.outer(dy, w4) * (h3 > 0)
+    d2 = (d3 @ W3) * (h2 > 0)
+    d1_wrong = d2 @ W2                      # mask dropped
+    gW1_wrong = d1_wrong.T @ z
+    _, grad = ow.loss_grad(params, norm, feats, targets, dim)
+    assert not np.allclose(gW1_wrong.ravel(), grad[:64 * F], rtol=1e-6)

@@ -1,6 +1,7 @@
 """Seeded input generators: laws of Section 3.2 and the workload substitutions."""
 import numpy as np
 
+import oracle
 from paper_2403_03571_gb300 import synth
 
 
@@ -67,3 +68,26 @@ def test_workloads_shapes():
     assert np.allclose(w0.v, 1 / 20)
     w1 = synth.workload_3d_1000(m=16)
     assert w1.x.shape == (1000, 3) and abs(w1.v.sum() - 1) < 1e-12
+
+
+def test_batched_2d_workload_shape():
+    insts = synth.batched_2d_instances(256)
+    ns = np.array([i.n for i in insts])
+    assert ns.min() >= 50 and ns.max() <= 2000
+    for inst in insts:
+        m = inst.grid.res[0]
+        assert m in synth.BATCH_2D_RES and inst.grid.res[1] == m
+        assert abs(inst.v.sum() - 1.0) < 1e-12
+        # the grid is the smallest listed one meeting eq. (2.10), as the oracle's
+        # own resolution rule computes it
+        need = oracle.resolution_practical(2, float(inst.v.min()))
+        assert m >= need or m == synth.BATCH_2D_RES[-1]
+        smaller = [r for r in synth.BATCH_2D_RES if r < m]
+        assert not smaller or smaller[-1] < need
+    total = sum(i.n * i.grid.num_pixels for i in insts)
+    assert 5e10 < total < 3e11
+
+
+def test_required_resolution_matches_oracle():
+    for dim, vmin in [(2, 1 / 20), (3, 1e-4), (3, 2.3e-4), (2, 3.7e-5)]:
+        assert synth.required_resolution(dim, vmin) == oracle.resolution_practical(dim, vmin)
