@@ -32,6 +32,7 @@ WORKLOADS = {
     # name: (builder, Lloyd rounds)
     "3d_n1000_256cube_lloyd5": ("workload_3d_1000", 5),
     "2d_n20_256sq": ("workload_2d_20", 0),
+    "2d_n2000_1024sq": ("workload_2d_2000", 0),
     # 256 independent 2D instances, N log-uniform in [50, 2000], grids 256^2 .. 1024^2
     "2d_batch256": ("batched_2d_instances", 0),
 }
@@ -532,6 +533,8 @@ def run_batch(args):
               "converged": sum(s in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE) for s in status),
               "not_converged": sum(s == capi.APD_NOT_CONVERGED for s in status),
               "tol_infeasible": sum(s == capi.APD_WARN_TOL_INFEASIBLE for s in status),
+              "rescored_fp64_fraction": sum(i.rescored_fp64 for i in infos) / max(
+                  1, sum(i.evaluations * ins.grid.num_pixels for i, ins in zip(infos, insts))),
               "gpu_launches": launches, "tile": {"chosen": list(shapes[tile]),
                                                  "ms": dict(zip(map(str, shapes), tile_ms))}}
     # plain: one instance at a time (sequential calls, inputs resident)

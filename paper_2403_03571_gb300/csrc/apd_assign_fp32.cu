@@ -42,12 +42,12 @@ using namespace fp32;
 template <int D>
 struct Cfg;
 template <>
-struct Cfg<3> {
-    static constexpr int P = 16, TY = 16, TZ = 16;
+struct Cfg<3> {  // 16^3 voxels, one 16-voxel row per thread
+    static constexpr int TX = 1, P = 16, TY = 16, TZ = 16;
 };
 template <>
-struct Cfg<2> {
-    static constexpr int P = 16, TY = 256, TZ = 1;
+struct Cfg<2> {  // 64 x 64 pixels, four 16-pixel row segments per row
+    static constexpr int TX = 4, P = 16, TY = 64, TZ = 1;
 };
 
 template <int D>
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256, 2) assign_fp32_kernel(const __grid_consta
     SharedLayout<D> &sm = *reinterpret_cast<SharedLayout<D> *>(smem_raw);
     init_shared<D>(sm);
     uint32_t uses[2] = {0u, 0u};
-    score_tile<D, C::P, C::TY, C::TZ>(sm, src, blockIdx.x, blockIdx.y, blockIdx.z, uses);
+    score_tile<D, C::TX, C::P, C::TY, C::TZ>(sm, src, blockIdx.x, blockIdx.y, blockIdx.z, uses);
 }
 
 // One warp per queued pixel of one instance.
@@ -92,14 +92,14 @@ cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((g.res[0] + C::P - 1) / C::P, (g.res[1] + C::TY - 1) / C::TY,
+    dim3 grid((g.res[0] + C::TX * C::P - 1) / (C::TX * C::P), (g.res[1] + C::TY - 1) / C::TY,
               D == 3 ? (g.res[2] + C::TZ - 1) / C::TZ : 1);
     const int n_chunks = (n + kChunk - 1) / kChunk;
-    double hx = 0.5 * C::P * g.h[0], hy = 0.5 * C::TY * g.h[1], hz = D == 3 ? 0.5 * C::TZ * g.h[2] : 0.0;
+    double hx = 0.5 * C::TX * C::P * g.h[0], hy = 0.5 * C::TY * g.h[1], hz = D == 3 ? 0.5 * C::TZ * g.h[2] : 0.0;
     const float R = (float)(sqrt(hx * hx + hy * hy + hz * hz) * (1.0 + 1e-6));
     const TileSrc src{g,       n,       n_chunks, R, ws.recs, ws.sorted ? ws.scodes : nullptr,
                       ws.sorted ? ws.perm : nullptr, gmom, ws.flags, labels, ws.sc};
-    assign_fp32_kernel<D><<<grid, C::TY * C::TZ, smem, st>>>(src);
+    assign_fp32_kernel<D><<<grid, C::TX * C::TY * C::TZ, smem, st>>>(src);
     return cudaGetLastError();
 }
 

@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
 // ---------------------------------------------------------------------------
 // persistent scoring over the tiles of all active instances
 // ---------------------------------------------------------------------------
-template <int D, int P, int TY, int TZ, int MINB>
-__global__ void __launch_bounds__(TY *TZ, MINB) batch_assign_kernel(const __grid_constant__ BArgs a) {
+template <int D, int TX, int P, int TY, int TZ, int MINB>
+__global__ void __launch_bounds__(TX *TY *TZ, MINB) batch_assign_kernel(const __grid_constant__ BArgs a) {
     constexpr int K = moment_width(D);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     fp32::SharedLayout<D> &sm = *reinterpret_cast<fp32::SharedLayout<D> *>(smem_raw);
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(TY *TZ, MINB) batch_assign_kernel(const __grid
             cur.sc = a.scs + b;
         }
         __syncthreads();
-        if (!fp32::score_tile<D, P, TY, TZ>(sm, cur, txyz[0], txyz[1], txyz[2], uses)) break;
+        if (!fp32::score_tile<D, TX, P, TY, TZ>(sm, cur, txyz[0], txyz[1], txyz[2], uses)) break;
     }
 }
 
@@ -703,29 +703,32 @@ __global__ void __launch_bounds__(kSolveThreads) batch_lbfgs_kernel(const __grid
 // tile variants of the persistent kernel
 // ---------------------------------------------------------------------------
 struct Variant {
-    int P, TY, TZ, threads;
+    int TX, P, TY, TZ, threads;  // tile (TX P) x TY x TZ
     const void *fn;
     cudaError_t (*launch)(const BArgs &, int grid, size_t smem, cudaStream_t);
 };
 
-template <int D, int P, int TY, int TZ, int MINB>
+template <int D, int TX, int P, int TY, int TZ, int MINB>
 cudaError_t launch_variant(const BArgs &a, int grid, size_t smem, cudaStream_t st) {
-    batch_assign_kernel<D, P, TY, TZ, MINB><<<grid, TY * TZ, smem, st>>>(a);
+    batch_assign_kernel<D, TX, P, TY, TZ, MINB><<<grid, TX * TY * TZ, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int D, int P, int TY, int TZ, int MINB>
+template <int D, int TX, int P, int TY, int TZ, int MINB>
 Variant make_variant() {
-    return Variant{P, TY, TZ, TY * TZ, (const void *)batch_assign_kernel<D, P, TY, TZ, MINB>,
-                   &launch_variant<D, P, TY, TZ, MINB>};
+    return Variant{TX, P, TY, TZ, TX * TY * TZ, (const void *)batch_assign_kernel<D, TX, P, TY, TZ, MINB>,
+                   &launch_variant<D, TX, P, TY, TZ, MINB>};
 }
 
+// Candidate tiles: compact squares and near-squares (short distances from the
+// tile centre keep the rounding bound small and the per-group skips frequent)
+// in CTAs of 256 and 128 threads.
 const std::vector<Variant> &variants(int dim) {
     static const std::vector<Variant> v2 = {
-        make_variant<2, 16, 256, 1, 2>(), make_variant<2, 16, 128, 1, 4>(), make_variant<2, 16, 64, 1, 8>(),
-        make_variant<2, 8, 128, 1, 4>()};
-    static const std::vector<Variant> v3 = {make_variant<3, 16, 16, 16, 2>(), make_variant<3, 16, 8, 16, 4>(),
-                                            make_variant<3, 8, 16, 16, 2>()};
+        make_variant<2, 4, 16, 64, 1, 2>(),  make_variant<2, 2, 16, 128, 1, 2>(), make_variant<2, 8, 16, 32, 1, 2>(),
+        make_variant<2, 4, 16, 32, 1, 4>(),  make_variant<2, 2, 16, 64, 1, 4>(),  make_variant<2, 1, 16, 256, 1, 2>()};
+    static const std::vector<Variant> v3 = {make_variant<3, 1, 16, 16, 16, 2>(), make_variant<3, 1, 16, 8, 16, 4>(),
+                                            make_variant<3, 2, 8, 8, 16, 2>()};
     return dim == 3 ? v3 : v2;
 }
 
@@ -785,11 +788,11 @@ std::vector<BInst> instance_table(const apd_batch &bt, int vi) {
         I.seed_off = bt.seed_off[b];
         I.rec_off = bt.rec_off[b];
         I.flag_off = bt.flag_off[b];
-        I.tiles_x = (I.g.res[0] + V.P - 1) / V.P;
+        I.tiles_x = (I.g.res[0] + V.TX * V.P - 1) / (V.TX * V.P);
         I.tiles_y = (I.g.res[1] + V.TY - 1) / V.TY;
         I.tiles_z = bt.dim == 3 ? (I.g.res[2] + V.TZ - 1) / V.TZ : 1;
         I.ntiles = I.tiles_x * I.tiles_y * I.tiles_z;
-        const double hx = 0.5 * V.P * I.g.h[0], hy = 0.5 * V.TY * I.g.h[1];
+        const double hx = 0.5 * V.TX * V.P * I.g.h[0], hy = 0.5 * V.TY * I.g.h[1];
         const double hz = bt.dim == 3 ? 0.5 * V.TZ * I.g.h[2] : 0.0;
         I.R_tile = (float)(std::sqrt(hx * hx + hy * hy + hz * hz) * (1.0 + 1e-6));
         I.measure = bt.measure[b];
@@ -1057,7 +1060,7 @@ int apd_batch_tile_info(apd_batch *bt, int32_t *tile, int32_t *n_variants, doubl
     for (int k = 0; k < (int)vs.size(); ++k) {
         if (ms) ms[k] = k < (int)bt->variant_ms.size() ? bt->variant_ms[k] : -1.0;
         if (shape) {
-            shape[3 * k] = vs[k].P;
+            shape[3 * k] = vs[k].TX * vs[k].P;
             shape[3 * k + 1] = vs[k].TY;
             shape[3 * k + 2] = vs[k].TZ;
         }

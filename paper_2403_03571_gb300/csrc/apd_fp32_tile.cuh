@@ -162,31 +162,36 @@ struct TileSrc {
     DevScalars *sc;
 };
 
-// Scores the P x TY x TZ tile (bx, by, bz) of `s` with NT = TY * TZ threads.
+// Scores the (TX P) x TY x TZ tile (bx, by, bz) of `s` with NT = TX TY TZ
+// threads; thread (seg, ty, tz) owns the row segment of P pixels starting at
+// first-axis offset seg P inside the tile.
 // `uses` counts the completed phases of the two chunk barriers across the
 // tiles a CTA has scored; the shared-memory table must be empty on entry and
 // is empty again on return.  Returns false if a chunk wait timed out (the CTA
 // must then stop: a copy may still be in flight).
-template <int D, int P, int TY, int TZ>
+template <int D, int TX, int P, int TY, int TZ>
 __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s, const int bx, const int by,
                                            const int bz, uint32_t (&uses)[2]) {
     constexpr int K = moment_width(D);
-    constexpr int NT = TY * TZ;
+    constexpr int NT = TX * TY * TZ;
+    constexpr int W0 = TX * P;  // tile width along the first axis
     const GridDev &g = s.g;
     const int n = s.n, n_chunks = s.n_chunks;
 
     const int tid = threadIdx.x;
-    const int ty = tid % TY;
-    const int tz = tid / TY;
-    const int k0b = bx * P;
+    const int seg = tid % TX;
+    const int ty = (tid / TX) % TY;
+    const int tz = tid / (TX * TY);
+    const int k0t = bx * W0;       // first pixel of the tile along axis 0
+    const int k0b = k0t + seg * P;  // first pixel of this thread's row segment
     const int k1b = by * TY;
     const int k2b = (D == 3) ? bz * TZ : 0;
     const int k1 = k1b + ty;
     const int k2 = k2b + tz;
     const bool row_valid = (k1 < g.res[1]) && (D == 2 || k2 < g.res[2]);
 
-    // CTA reference point (FP64): row centre along axis 0, tile centre along 1, 2
-    const double c0 = g.lo[0] + (double)(k0b + P / 2) * g.h[0];
+    // CTA reference point (FP64): the tile centre
+    const double c0 = g.lo[0] + (double)(k0t + W0 / 2) * g.h[0];
     const double c1 = g.lo[1] + (double)(k1b + TY / 2) * g.h[1];
     const double c2 = (D == 3) ? g.lo[2] + (double)(k2b + TZ / 2) * g.h[2] : 0.0;
     const float f1 = ((float)(ty - TY / 2) + 0.5f) * g.h32[1];
@@ -194,8 +199,8 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     float2 y2[P / 2];
 #pragma unroll
     for (int q = 0; q < P / 2; ++q)
-        y2[q] = make_float2(((float)(2 * q - P / 2) + 0.5f) * g.h32[0],
-                            ((float)(2 * q + 1 - P / 2) + 0.5f) * g.h32[0]);
+        y2[q] = make_float2(((float)(seg * P + 2 * q - W0 / 2) + 0.5f) * g.h32[0],
+                            ((float)(seg * P + 2 * q + 1 - W0 / 2) + 0.5f) * g.h32[0]);
 
     // Scan order of the seed chunks: with Morton-sorted seeds, start at the chunk
     // holding this tile's Morton position and zig-zag outwards, so that the near
@@ -203,7 +208,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     int start_chunk = 0;
     if (s.scodes) {
         double frac[3] = {0.0, 0.0, 0.0};
-        const int kc[3] = {k0b + P / 2, k1b + TY / 2, k2b + TZ / 2};
+        const int kc[3] = {k0t + W0 / 2, k1b + TY / 2, k2b + TZ / 2};
 #pragma unroll
         for (int a = 0; a < D; ++a) frac[a] = ((double)kc[a] + 0.5) / (double)g.res[a];
         const uint32_t code = morton_code(D, frac);

@@ -253,6 +253,12 @@ def workload_3d_10000(instance: int = 0, m: int = 512) -> Instance:
     return make_instance(3, 10000, m, workload_seed(2, instance), name=f"3d_n10000_{m}cube")
 
 
+def workload_2d_2000(instance: int = 0) -> Instance:
+    """2D, 2000 seeds, lognormal volumes, 1024^2 pixels: the largest instance class
+    of the batched 2D workload, for single-instance kernel measurements."""
+    return make_instance(2, 2000, 1024, workload_seed(3, 10_000 + instance), name="2d_n2000_1024sq")
+
+
 def required_resolution(dim: int, v_min: float, eps: float = 0.01, measure: float = 1.0) -> int:
     """Smallest M with measure / M^dim <= eps v_min / 2^dim (the resolution rule of
     eq. (2.10), non-strict), used to size the grids of the batched workloads."""
