@@ -209,11 +209,9 @@ def load_peaks():
 
 
 # DRAM traffic (read + write bytes) of one scoring launch from an ncu capture,
-# keyed by (kernel source sha256 prefix, workload); reported only while the
-# kernel source is unchanged since the capture.
-NCU_TRAFFIC = {
-    ("d3e48913ee46a5c7", "3d_n1000_256cube_lloyd5"): 272384 + 268800,
-}
+# keyed by (sha256 prefix of the scoring sources, workload); reported only
+# while the sources are unchanged since the capture.
+NCU_TRAFFIC = {}
 
 # FP32 flops the row-factored scoring performs per (pixel, seed) pair:
 # 2 FMAs per pixel, plus the per-(row, seed) coefficients (17 flops in 3D,
@@ -223,9 +221,11 @@ FLOPS_PER_PAIR = {3: 4.0 + 17.0 / 16.0, 2: 4.0 + 7.0 / 16.0}
 
 def kernel_source_hash():
     import hashlib
-    p = os.path.join(ROOT, "paper_2403_03571_gb300", "csrc", "apd_assign_fp32.cu")
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("apd_assign_fp32.cu", "apd_fp32_tile.cuh"):
+        with open(os.path.join(ROOT, "paper_2403_03571_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def fp32_peak_tflops(sm_mhz, sms):
@@ -338,28 +338,34 @@ def measure_form(args, ctx, precision):
 
 
 def roofline_block(form, dim, sms, workload):
+    """Roofline of the scoring stage.  `achieved` counts the algorithmic work of the
+    method, 2F flops per (pixel, seed) pair (the F-feature dot product [y(x)y, y, 1] .
+    phi_i, F = 10 in 3D, 6 in 2D).  The FP32 kernel evaluates each pair in the
+    row-factored form a + d (b + A00 d) and executes fewer flops than that
+    (FLOPS_PER_PAIR); its executed fraction of the FP32 peak is reported beside."""
     peaks, peak_src = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     F = 10 if dim == 3 else 6
     pr = form["pair_rate"]
+    alg = pr * 2 * F / 1e12
     if form["precision"] == "fp32":
         peak = fp32_peak_tflops(sm_mhz, sms)
-        achieved = pr * FLOPS_PER_PAIR[dim] / 1e12
         tr = NCU_TRAFFIC.get((kernel_source_hash(), workload))
-        return {"bound": "alu", "kernel": "assign_fp32_kernel<%d>" % dim, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": tr / 2 if tr is not None else None,
-                "work_per_pair_flops": FLOPS_PER_PAIR[dim],
+        return {"bound": "alu", "kernel": "assign_fp32_kernel<%d>" % dim, "achieved": alg, "peak": peak,
+                "unit": "TFLOP/s", "frac": alg / peak, "traffic": tr,
+                "work_per_pair_flops": 2 * F,
+                "executed_flops_per_pair": FLOPS_PER_PAIR[dim],
+                "executed_tflops": pr * FLOPS_PER_PAIR[dim] / 1e12,
+                "executed_frac": pr * FLOPS_PER_PAIR[dim] / 1e12 / peak,
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
                                f"(max SM clock from MEASURED_PEAKS.json, {peak_src})",
-                "launch_ms": form["launch_ms"], "launches": form["launches"],
-                "dot_product_equivalent_tflops": pr * 2 * F / 1e12}
-    # tensor-core form: the dot product [y(x)y, y, 1] . phi of F features per pair, against the
-    # dense peak of its operand type (measured BF16 x the nominal TF32/BF16 ratio 1.1/2.25)
+                "launch_ms": form["launch_ms"], "launches": form["launches"]}
+    # tensor-core form against the dense peak of its operand type
+    # (measured BF16 x the nominal TF32/BF16 ratio 1.1/2.25 for TF32)
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     peak = bf16 * (1.1 / 2.25) if form["precision"] == "tc_tf32" else bf16
-    achieved = pr * 2 * F / 1e12
     return {"bound": "tensor", "kernel": "assign_tc_kernel<%d> + tc_resolve_kernel<%d>" % (dim, dim),
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak, "traffic": None,
             "work_per_pair_flops": 2 * F,
             "peak_source": f"measured bf16 {bf16:.1f} TFLOP/s ({peak_src})"
                            + (" x 1.1/2.25 (nominal TF32/BF16)" if form["precision"] == "tc_tf32" else ""),

@@ -155,6 +155,8 @@ typedef struct {
     double g;              /* g~ at the returned weights */
     int64_t rescored_fp64; /* pixels rescored in FP64, summed over evaluations */
     double seconds;        /* wall time of the call */
+    int32_t coarse_evaluations; /* evaluations on the coarse grid (coarse-to-fine solves; else 0) */
+    int32_t pad;
 } apd_solve_info;
 
 /* Algorithm 2: maximise g~ by L-BFGS from W0 = seeds->w until
@@ -297,11 +299,14 @@ int apd_batch_solve_weights_judged(apd_batch *batch, const double *x, const doub
  * motivates a heuristic initial guess); this predictor is an addition, always
  * judged against the zero start (apd_batch_solve_weights_judged,
  * apd_solve_weights_warm).
- *   Features of seed i of an instance with n seeds on a domain of measure |O|,
- *   s = n / |O| (F = 20 in 2D, 23 in 3D): [v_i s, upper triangle of
- *   (A_i + A_i^T)/2, distances to the 8 nearest other seeds x s^(1/D)
- *   ascending, target volumes of those seeds x s]; missing neighbours give
- *   distance 4 and volume 0.
+ *   Features of seed i of an instance with n seeds on the box [lo, hi] of
+ *   measure |O|, s = n / |O|, lengths in units of s^(-1/D) (F = 28 in 2D, 32
+ *   in 3D): [v_i s; upper triangle of (A_i + A_i^T)/2; distances to the 8
+ *   nearest other seeds, ascending; target volumes of those seeds x s; distance
+ *   to the nearer wall per axis; for r = 2, 4, 8: c_r / E_r and
+ *   (V_r s - c_r) / E_r with c_r the number and V_r the summed target volume
+ *   of the other seeds within distance r, E_r = (unit-ball volume) r^D].
+ *   Missing neighbours (n <= 8) give distance 4 and volume 0.
  *   Network: F -> 64 -> 64 -> 64 -> 1, ReLU, FP32; inputs standardised by
  *   (f - mean) * inv_std.  Prediction w_i = y_i s^(-2/D).
  *   Parameters: one FP32 array of apd_warmstart_sizes' n_params values in the
@@ -309,7 +314,8 @@ int apd_batch_solve_weights_judged(apd_batch *batch, const double *x, const doub
  *   (W row-major [out][in]); norm = mean [F] followed by inv_std [F].
  * Instances are described as for batches: offsets HOST int64 [count + 1]
  * (offsets[0] = 0, strictly increasing) into concatenated x / A / v, and
- * measure HOST double [count] (|O| of each instance). */
+ * box HOST double [count][6] (lo[3] then hi[3] of each instance's domain;
+ * entries beyond dim ignored). */
 typedef struct apd_mlp apd_mlp;
 
 /* Feature and parameter counts of the network for dim (2 or 3). */
@@ -324,7 +330,7 @@ void apd_warmstart_destroy(apd_mlp *net);
 int apd_warmstart_get(apd_mlp *net, float *params, float *norm);
 
 /* Features of every seed: features FP32 device [N][F].  Stream-ordered. */
-int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, const double *measure,
+int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, const double *box,
                            const double *x, const double *A, const double *v, float *features,
                            apd_stream_t stream);
 
@@ -333,7 +339,7 @@ int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, 
 int apd_warmstart_fit_norm(apd_mlp *net, int64_t samples, const float *features, apd_stream_t stream);
 
 /* Predicted weights w_out double device [N] from features.  Stream-ordered. */
-int apd_warmstart_predict(apd_mlp *net, int32_t count, const int64_t *offsets, const double *measure,
+int apd_warmstart_predict(apd_mlp *net, int32_t count, const int64_t *offsets, const double *box,
                           const float *features, double *w_out, apd_stream_t stream);
 
 /* One training step on the samples idx[0 .. batch) (int32 device indices into
@@ -353,6 +359,43 @@ int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, co
 int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const double *v,
                            double *w_out, const apd_solve_opts *opts, apd_solve_info *info,
                            apd_workspace *ws, apd_mlp *net, int32_t *used_pred, apd_stream_t stream);
+
+/* ---- Coarse-to-fine weight solve ------------------------------------------
+ * The weights are per seed, not per pixel, so a solve on a coarser grid of the
+ * same box gives a start for the fine grid directly.  The coarse solve fixes
+ * the smooth, domain-scale part of W that is expensive for L-BFGS on the fine
+ * grid; the fine solve then only corrects the discretisation difference.
+ * This follows the refinement step that Algorithm 2 allows (raise M, reuse W,
+ * continue) run in the opposite order: a cheap coarse solve first. */
+typedef struct {
+    int32_t factor;           /* coarse grid: ceil(res_d / factor) pixels per axis (>= 4); factor >= 2 */
+    double coarse_eps;        /* stop rule of the coarse solve */
+    int32_t coarse_max_evals; /* evaluation cap of the coarse solve (its best iterate is used) */
+} apd_multires_opts;
+
+/* Fill *mo with the defaults: factor 2, coarse_eps 0.05, coarse_max_evals 60. */
+void apd_multires_opts_default(apd_multires_opts *mo);
+
+/* Coarse solve from W0 = seeds->w (or, with net != NULL, from the network's
+ * prediction judged against W = 0), then the fine solve (opts) from the coarse
+ * weights.  info->evaluations counts fine evaluations, coarse_evaluations the
+ * coarse ones.  used_pred as apd_solve_weights_warm (0 without a network).
+ * Host-synchronous; status of the fine solve, as apd_solve_weights. */
+int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, const double *v,
+                               double *w_out, const apd_solve_opts *opts,
+                               const apd_multires_opts *mo, apd_solve_info *info,
+                               apd_workspace *ws, apd_mlp *net, int32_t *used_pred,
+                               apd_stream_t stream);
+
+/* The batched form: every instance solved on its coarse grid (a second batch
+ * over the coarse grids, created on first use and kept), from w0, judged
+ * against zero when judge != 0, then on its own grid from the coarse weights.
+ * Arguments and status as apd_batch_solve_weights_judged. */
+int apd_batch_solve_weights_multires(apd_batch *batch, const double *x, const double *A,
+                                     const double *w0, const double *v, double *w_out,
+                                     const apd_solve_opts *opts, const apd_multires_opts *mo,
+                                     int32_t judge, apd_solve_info *info, int32_t *used_pred,
+                                     apd_stream_t stream);
 
 /* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
  * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).

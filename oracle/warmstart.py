@@ -9,19 +9,24 @@ The paper seeds the weight solve with W = 0 and motivates a better initial
 guess; the predictor these functions describe is this project's addition, so
 there is no passage to follow -- the definitions are:
 
-* features of seed i of an instance with n seeds on a domain of measure |O|,
-  s = n / |O|:  [v_i s, upper triangle of (A_i + A_i^T)/2, distances to the 8
-  nearest other seeds times s^(1/D) (ascending), target volumes of those seeds
-  times s]; missing neighbours (n <= 8) give distance 4 and volume 0;
+* features of seed i of an instance with n seeds on the box [lo, hi] of
+  measure |O|, s = n / |O|, lengths in units of s^(-1/D):  [v_i s, upper
+  triangle of (A_i + A_i^T)/2, distances to the 8 nearest other seeds
+  (ascending), target volumes of those seeds times s, distance to the nearer
+  wall per axis, and for r = 2, 4, 8: c_r / E_r and (V_r s - c_r) / E_r with
+  c_r the number and V_r the summed target volume of the other seeds within
+  distance r, E_r = (unit-ball volume) r^D]; missing neighbours (n <= 8) give
+  distance 4 and volume 0;
 * network  y = w4 . relu(W3 relu(W2 relu(W1 z + b1) + b2) + b3) + b4,
   z = (f - mean) * inv_std, hidden width 64, flat parameter order
   W1 [64][F], b1, W2 [64][64], b2, W3 [64][64], b3, w4 [64], b4;
 * prediction  w_i = y_i s^(-2/D);
 * training loss over a batch  L = (1/B) sum_s (y_s - t_s)^2.
 
-Pins (tests/test_oracle_pins.py): the k-d tree neighbours against a brute-force
-distance matrix; the gradient against central finite differences of the FP64
-loss; the parameter counts against the layer sizes.
+Pins (tests/test_oracle_warmstart.py): the k-d tree neighbours and ball counts
+against a brute-force distance matrix; the wall distances and scale invariance;
+the gradient against central finite differences of the FP64 loss; the
+parameter counts against the layer sizes.
 """
 from __future__ import annotations
 
@@ -30,10 +35,11 @@ from scipy.spatial import cKDTree
 
 H = 64
 KNN = 8
+RADII = (2.0, 4.0, 8.0)
 
 
 def n_features(dim: int) -> int:
-    return 1 + dim * (dim + 1) // 2 + 2 * KNN
+    return 1 + dim * (dim + 1) // 2 + 2 * KNN + dim + 2 * len(RADII)
 
 
 def n_params(dim: int) -> int:
@@ -41,24 +47,38 @@ def n_params(dim: int) -> int:
     return H * F + H + 2 * (H * H + H) + H + 1
 
 
-def features(x, A, v, measure: float = 1.0) -> np.ndarray:
-    """Feature rows [n][F] of one instance (FP64)."""
+def features(x, A, v, lo=None, hi=None) -> np.ndarray:
+    """Feature rows [n][F] of one instance on the box [lo, hi] (default unit box), FP64."""
     x = np.asarray(x, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
     n, dim = x.shape
-    s = n / measure
+    lo = np.zeros(dim) if lo is None else np.asarray(lo, dtype=np.float64)[:dim]
+    hi = np.ones(dim) if hi is None else np.asarray(hi, dtype=np.float64)[:dim]
+    s = n / float(np.prod(hi - lo))
+    ls = s ** (1.0 / dim)
     k = min(KNN, n - 1)
     dist = np.full((n, KNN), 4.0)
     vol = np.zeros((n, KNN))
+    tree = cKDTree(x)
     if k > 0:
-        d, idx = cKDTree(x).query(x, k=k + 1)
+        d, idx = tree.query(x, k=k + 1)
         # column 0 is the point itself (distance 0); ties between neighbours at equal
         # distance are measure-zero for continuous positions
-        dist[:, :k] = d[:, 1:] * s ** (1.0 / dim)
-        vol[:, :k] = np.asarray(v)[idx[:, 1:]] * s
+        dist[:, :k] = d[:, 1:] * ls
+        vol[:, :k] = v[idx[:, 1:]] * s
     sym = 0.5 * (A + np.transpose(A, (0, 2, 1)))
     iu = np.triu_indices(dim)
     upper = sym[:, iu[0], iu[1]]
-    return np.concatenate([np.asarray(v)[:, None] * s, upper, dist, vol], axis=1)
+    walls = np.minimum(x - lo, hi - x) * ls
+    ball = np.pi if dim == 2 else 4.0 * np.pi / 3.0
+    scales = []
+    for r in RADII:
+        members = tree.query_ball_point(x, r / ls)
+        c = np.array([len(m) - 1 for m in members], dtype=np.float64)
+        V = np.array([v[m].sum() - v[i] for i, m in enumerate(members)])
+        e = ball * r ** dim
+        scales += [c / e, (V * s - c) / e]
+    return np.concatenate([v[:, None] * s, upper, dist, vol, walls, np.stack(scales, 1)], axis=1)
 
 
 def unpack(params, dim: int):
@@ -88,7 +108,7 @@ def forward(params, norm, feats, dim: int):
     return y, (z, h1, h2, h3)
 
 
-def predict(params, norm, feats, n: int, measure: float, dim: int):
+def predict(params, norm, feats, n: int, measure: float, dim: int):  # measure = |O|
     """Predicted weights of one instance: y s^(-2/D)."""
     y, _ = forward(params, norm, feats, dim)
     return y * (n / measure) ** (-2.0 / dim)

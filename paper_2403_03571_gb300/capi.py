@@ -40,6 +40,7 @@ EXPORTED = (
     "apd_warmstart_sizes", "apd_warmstart_create", "apd_warmstart_destroy", "apd_warmstart_get",
     "apd_warmstart_features", "apd_warmstart_fit_norm", "apd_warmstart_predict",
     "apd_warmstart_train_step", "apd_solve_weights_warm",
+    "apd_multires_opts_default", "apd_solve_weights_multires", "apd_batch_solve_weights_multires",
 )
 
 
@@ -68,10 +69,16 @@ class ApdSolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("evaluations", ctypes.c_int32), ("solves", ctypes.c_int32),
                 ("max_rel_err", ctypes.c_double), ("g", ctypes.c_double),
-                ("rescored_fp64", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("rescored_fp64", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("coarse_evaluations", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ApdMultiresOpts(ctypes.Structure):
+    _fields_ = [("factor", ctypes.c_int32), ("coarse_eps", ctypes.c_double),
+                ("coarse_max_evals", ctypes.c_int32)]
 
 
 class ApdError(RuntimeError):
@@ -150,6 +157,14 @@ def load(path: Optional[str] = None):
                                            _vp]
     L.apd_solve_weights_warm.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _P(ApdSolveOpts),
                                          _P(ApdSolveInfo), _vp, _vp, _P(ctypes.c_int32), _vp]
+    L.apd_multires_opts_default.argtypes = [_P(ApdMultiresOpts)]
+    L.apd_multires_opts_default.restype = None
+    L.apd_solve_weights_multires.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _P(ApdSolveOpts),
+                                             _P(ApdMultiresOpts), _P(ApdSolveInfo), _vp, _vp,
+                                             _P(ctypes.c_int32), _vp]
+    L.apd_batch_solve_weights_multires.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _P(ApdSolveOpts),
+                                                   _P(ApdMultiresOpts), ctypes.c_int32, _P(ApdSolveInfo),
+                                                   _P(ctypes.c_int32), _vp]
     _lib = L
     return L
 
@@ -398,6 +413,18 @@ def warmstart_sizes(dim: int):
     return f.value, p.value
 
 
+def _boxes(grids):
+    """[count][6] float64 boxes (lo[3], hi[3]) of synth.Grid-like objects."""
+    import numpy as np
+    out = np.zeros((len(grids), 6))
+    out[:, 3:] = 1.0
+    for b, g in enumerate(grids):
+        gg = make_grid(g)
+        for a in range(gg.dim):
+            out[b, a], out[b, 3 + a] = gg.lo[a], gg.hi[a]
+    return np.ascontiguousarray(out)
+
+
 def _offsets(counts):
     import numpy as np
     offs = np.zeros(len(counts) + 1, dtype=np.int64)
@@ -446,10 +473,10 @@ class WarmStart:
                "apd_warmstart_get")
         return p, nz
 
-    def features(self, counts, measures, x, A, v, out, stream=None):
-        import numpy as np
+    def features(self, counts, grids, x, A, v, out, stream=None):
+        """Features of every seed of the instances (counts[b] seeds on grids[b]'s box)."""
         offs = _offsets(counts)
-        m = np.ascontiguousarray(measures, dtype=np.float64)
+        m = _boxes(grids)
         return _check(load().apd_warmstart_features(
             self.handle, len(counts), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(x), _ptr(A), _ptr(v), _ptr(out),
@@ -459,10 +486,9 @@ class WarmStart:
         return _check(load().apd_warmstart_fit_norm(self.handle, int(features.shape[0]), _ptr(features),
                                                     _stream(stream)), "apd_warmstart_fit_norm")
 
-    def predict(self, counts, measures, features, w_out, stream=None):
-        import numpy as np
+    def predict(self, counts, grids, features, w_out, stream=None):
         offs = _offsets(counts)
-        m = np.ascontiguousarray(measures, dtype=np.float64)
+        m = _boxes(grids)
         return _check(load().apd_warmstart_predict(
             self.handle, len(counts), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(features), _ptr(w_out),
@@ -486,3 +512,40 @@ def apd_solve_weights_warm(grid, x, A, v, w_out, ws: Workspace, net: WarmStart, 
                                        ctypes.byref(used), _stream(stream))
     _check(rc, "apd_solve_weights_warm", _SOLVE_OK)
     return rc, info, used.value
+
+
+def multires_opts(factor=2, coarse_eps=0.05, coarse_max_evals=60):
+    m = ApdMultiresOpts()
+    load().apd_multires_opts_default(ctypes.byref(m))
+    m.factor, m.coarse_eps, m.coarse_max_evals = int(factor), float(coarse_eps), int(coarse_max_evals)
+    return m
+
+
+def apd_solve_weights_multires(grid, x, A, w0, v, w_out, ws: Workspace, opts=None, mopts=None,
+                               net: Optional[WarmStart] = None, stream=None):
+    """Coarse-to-fine solve (optionally from the network's judged prediction);
+    returns (status, ApdSolveInfo, used_prediction)."""
+    g, s = make_grid(grid), make_seeds(x, A, w0)
+    info = ApdSolveInfo()
+    used = ctypes.c_int32()
+    opts = opts or solve_opts()
+    mopts = mopts or multires_opts()
+    rc = load().apd_solve_weights_multires(ctypes.byref(g), ctypes.byref(s), _ptr(v), _ptr(w_out),
+                                           ctypes.byref(opts), ctypes.byref(mopts), ctypes.byref(info),
+                                           ws.handle, net.handle if net is not None else None,
+                                           ctypes.byref(used), _stream(stream))
+    _check(rc, "apd_solve_weights_multires", _SOLVE_OK)
+    return rc, info, used.value
+
+
+def apd_batch_solve_weights_multires(batch: Batch, x, A, w0, v, w_out, opts=None, mopts=None, judge=False,
+                                     stream=None):
+    """Batched coarse-to-fine solve; returns (C status, [ApdSolveInfo], [used prediction])."""
+    info = (ApdSolveInfo * batch.count)()
+    used = (ctypes.c_int32 * batch.count)()
+    opts = opts or solve_opts()
+    mopts = mopts or multires_opts()
+    rc = load().apd_batch_solve_weights_multires(batch.handle, _ptr(x), _ptr(A), _ptr(w0), _ptr(v), _ptr(w_out),
+                                                 ctypes.byref(opts), ctypes.byref(mopts), int(bool(judge)), info,
+                                                 used, _stream(stream))
+    return rc, list(info), list(used)

@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256)
     rescore_kernel(const GridDev g, const int n, const double *__restrict__ x,
                    const double *__restrict__ A, const double *__restrict__ w,
                    const SeedRec32 *__restrict__ r32, const uint32_t *__restrict__ flags,
+                   const int32_t *__restrict__ flag_gi, const RescorePrune pr,
                    DevScalars *__restrict__ sc, unsigned long long *__restrict__ gmom,
                    int32_t *__restrict__ labels) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -76,8 +77,10 @@ __global__ void __launch_bounds__(256)
     const double wref = dkey_inv(sc->wref_key);
     const float wrh = (float)wref;
     const float wrl = (float)(wref - (double)wrh);
+    RescorePrune p = pr;
+    p.wref = wref;
     for (unsigned it = warp; it < count; it += nwarps)
-        rescore_pixel<D>(g, n, x, A, w, r32, flags[it], wrh, wrl, sc, gmom, labels);
+        rescore_pixel<D>(g, n, x, A, w, r32, flags[it], flag_gi ? flag_gi[it] : -1, wrh, wrl, p, sc, gmom, labels);
 }
 
 template <int D>
@@ -97,8 +100,8 @@ cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t
     const int n_chunks = (n + kChunk - 1) / kChunk;
     double hx = 0.5 * C::TX * C::P * g.h[0], hy = 0.5 * C::TY * g.h[1], hz = D == 3 ? 0.5 * C::TZ * g.h[2] : 0.0;
     const float R = (float)(sqrt(hx * hx + hy * hy + hz * hz) * (1.0 + 1e-6));
-    const TileSrc src{g,       n,       n_chunks, R, ws.recs, ws.sorted ? ws.scodes : nullptr,
-                      ws.sorted ? ws.perm : nullptr, gmom, ws.flags, labels, ws.sc};
+    const TileSrc src{g,        n,     n_chunks,   R,      ws.recs, ws.sorted ? ws.scodes : nullptr,
+                      ws.sorted ? ws.perm : nullptr, gmom, ws.flags, ws.flag_gi, labels, ws.sc};
     assign_fp32_kernel<D><<<grid, C::TX * C::TY * C::TZ, smem, st>>>(src);
     return cudaGetLastError();
 }
@@ -117,10 +120,19 @@ cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const 
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ws.device);
     const int blocks = dev_sms * 2;
+    RescorePrune pr{nullptr, nullptr, nullptr, 0, 0.0};
+    if (ws.groups && (!ws.sorted || ws.recs32s)) {
+        pr.groups = ws.groups;
+        pr.r32s = ws.sorted ? ws.recs32s : ws.recs32;
+        pr.perm = ws.sorted ? ws.perm : nullptr;
+        pr.n_groups = (n + 31) / 32;
+    }
     if (g.dim == 3)
-        rescore_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.sc, moments, labels);
+        rescore_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.flag_gi, pr, ws.sc, moments,
+                                                  labels);
     else
-        rescore_kernel<2><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.sc, moments, labels);
+        rescore_kernel<2><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.flag_gi, pr, ws.sc, moments,
+                                                  labels);
     return cudaGetLastError();
 }
 

@@ -555,7 +555,8 @@ __global__ void __launch_bounds__(256)
     tc_resolve_kernel(const GridDev g, const int n, const float R_tile, const float err_unit,
                       const int4 *__restrict__ cand, const int32_t *__restrict__ perm,
                       const SeedRec32 *__restrict__ r32, unsigned long long *__restrict__ gmom,
-                      uint32_t *__restrict__ flags, int32_t *__restrict__ labels, DevScalars *__restrict__ sc) {
+                      uint32_t *__restrict__ flags, int32_t *__restrict__ flag_gi, int32_t *__restrict__ labels,
+                      DevScalars *__restrict__ sc) {
     using RG = ResGeom<D>;
     constexpr int KM = moment_width(D);
     __shared__ unsigned long long tval[kTcTable][KM];
@@ -647,6 +648,7 @@ __global__ void __launch_bounds__(256)
             if (queue) {
                 const unsigned slot = atomicAdd(&sc->flag_count, 1u);
                 flags[slot] = (uint32_t)j;
+                if (flag_gi) flag_gi[slot] = best >= 0 ? orig[best] : -1;
             } else if (labels) {
                 labels[j] = label;
             }
@@ -716,7 +718,8 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     const dim3 rgrid((g.res[0] + kResP - 1) / kResP, (g.res[1] + ResGeom<D>::TY - 1) / ResGeom<D>::TY,
                      D == 3 ? (g.res[2] + ResGeom<D>::TZ - 1) / ResGeom<D>::TZ : 1);
     tc_resolve_kernel<D><<<rgrid, ResGeom<D>::TY * ResGeom<D>::TZ, 0, st>>>(
-        g, n, R, err_unit, ws.tc_cand, ws.sorted ? ws.perm : nullptr, ws.recs32, gmom, ws.flags, labels, ws.sc);
+        g, n, R, err_unit, ws.tc_cand, ws.sorted ? ws.perm : nullptr, ws.recs32, gmom, ws.flags, ws.flag_gi, labels,
+        ws.sc);
     return cudaGetLastError();
 }
 

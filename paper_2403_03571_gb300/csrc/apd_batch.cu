@@ -35,7 +35,7 @@ constexpr int kBHist = 16;          // L-BFGS slots per instance (history <= kBH
 constexpr int kBSortMax = 4096;     // padded seed counts Morton-sorted in shared memory
 constexpr int kPrepThreads = 512;
 constexpr int kSolveThreads = 256;
-constexpr int kRescoreBlocks = 4;   // CTAs per instance in the rescoring launch
+constexpr int kRescoreBlocksPerSM = 4;  // CTAs per SM of the persistent rescoring launch
 constexpr int kBMaxCount = 50000;   // instances per batch (scheduler table in shared memory)
 
 // solver phases
@@ -79,6 +79,8 @@ struct BSched {
     unsigned total_items;  // tiles of the active instances
     int n_active;          // active instances this iteration
     int next_active;       // instances still active after this iteration's step
+    unsigned rescore_next; // queue cursor of the rescoring kernel
+    unsigned pad;
 };
 
 struct BParams {
@@ -105,11 +107,13 @@ struct BArgs {             // everything the per-iteration kernels touch
     double *S, *Y;         // [kBHist][total_n]
     double *rho;           // [count][kBHist]
     SeedRec *recs, *recs_tmp;
-    SeedRec32 *recs32;
+    SeedRec32 *recs32, *recs32s;  // natural order, scan order
+    GroupBound *groups;           // [total_rec / 32] bounds of the scan-order groups
     uint32_t *scodes;
     int32_t *perm;
     unsigned long long *mom;  // [total_n][K]
     uint32_t *flags;
+    int32_t *flag_gi;            // FP32 best seed of each queued pixel
 };
 
 __device__ __forceinline__ int map_bits_dev(int bits) {
@@ -170,6 +174,7 @@ __global__ void __launch_bounds__(1024) batch_schedule_kernel(const __grid_const
         a.sched->total_items = acc;
         a.sched->n_active = m;
         a.sched->next_active = 0;
+        a.sched->rescore_next = 0u;
     }
 }
 
@@ -210,6 +215,7 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
             keys[i] = ((unsigned long long)seed_code<D>(I.g, r, i < n) << 32) | (unsigned)i;
         } else {
             a.recs[I.rec_off + i] = r;
+            a.recs32s[I.rec_off + i] = r32;
         }
     }
     wmax = warp_max(wmax);
@@ -233,19 +239,27 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
         sc->lam_abs_bits = (unsigned long long)__double_as_longlong(shf[0]);
         sc->lam_min_bits = (unsigned long long)__double_as_longlong(shl[0]);
     }
-    if (!I.sorted) return;
-    int m = 1;
+    if (I.sorted) {
+        int m = 1;
     while (m < n_pad) m <<= 1;
-    for (int i = n_pad + threadIdx.x; i < m; i += blockDim.x) keys[i] = ~0ull - (unsigned long long)i;
-    __syncthreads();
-    block_bitonic_sort(keys, m);
-    for (int i = threadIdx.x; i < n_pad; i += blockDim.x) {
-        const unsigned long long k = keys[i];
-        const int src = (int)(k & 0xffffffffu);
-        a.scodes[I.rec_off + i] = (uint32_t)(k >> 32);
-        a.perm[I.rec_off + i] = src;
-        a.recs[I.rec_off + i] = a.recs_tmp[I.rec_off + src];
+        while (m < n_pad) m <<= 1;
+        for (int i = n_pad + threadIdx.x; i < m; i += blockDim.x) keys[i] = ~0ull - (unsigned long long)i;
+        __syncthreads();
+        block_bitonic_sort(keys, m);
+        for (int i = threadIdx.x; i < n_pad; i += blockDim.x) {
+            const unsigned long long k = keys[i];
+            const int src = (int)(k & 0xffffffffu);
+            a.scodes[I.rec_off + i] = (uint32_t)(k >> 32);
+            a.perm[I.rec_off + i] = src;
+            a.recs[I.rec_off + i] = a.recs_tmp[I.rec_off + src];
+            a.recs32s[I.rec_off + i] = a.recs32[I.rec_off + src];
+        }
     }
+    // bounds of the scan-order groups of 32 seeds (one warp per group)
+    __syncthreads();
+    const int ngroups = (n + 31) / 32;
+    for (int grp = threadIdx.x >> 5; grp < ngroups; grp += blockDim.x >> 5)
+        group_bound_warp<D>(a.recs + I.rec_off, n, grp, a.groups + I.rec_off / 32);
 }
 
 // ---------------------------------------------------------------------------
@@ -291,6 +305,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, MINB) batch_assign_kernel(const __
             cur.perm = I.sorted ? a.perm + I.rec_off : nullptr;
             cur.gmom = a.mom + I.seed_off * K;
             cur.flags = a.flags + I.flag_off;
+            cur.flag_gi = a.flag_gi + I.flag_off;
             cur.labels = nullptr;
             cur.sc = a.scs + b;
         }
@@ -299,25 +314,50 @@ __global__ void __launch_bounds__(TX *TY *TZ, MINB) batch_assign_kernel(const __
     }
 }
 
+// Near-tie rescoring of the queued pixels of all active instances: every warp
+// pulls pixels (4 at a time) from one queue over the concatenated per-instance
+// queues, so an instance with many queued pixels is spread over the whole GPU.
 template <int D>
 __global__ void __launch_bounds__(256) batch_rescore_kernel(const __grid_constant__ BArgs a) {
     constexpr int K = moment_width(D);
-    const int b = blockIdx.y;
-    if (!a.sol[b].active) return;
-    const BInst &I = a.inst[b];
-    DevScalars *sc = a.scs + b;
-    const unsigned count = sc->flag_count;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && count)
-        atomicAdd((unsigned long long *)&sc->rescored_total, (unsigned long long)count);
-    const double wref = dkey_inv(sc->wref_key);
-    const float wrh = (float)wref;
-    const float wrl = (float)(wref - (double)wrh);
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned it = warp; it < count; it += nwarps)
-        rescore_pixel<D>(I.g, I.n, a.x + I.seed_off * D, a.A + I.seed_off * D * D, a.Wt + I.seed_off,
-                         a.recs32 + I.rec_off, a.flags[I.flag_off + it], wrh, wrl, sc, a.mom + I.seed_off * K,
-                         nullptr);
+    extern __shared__ unsigned pre[];  // [n_active + 1] prefix of the queue lengths
+    const int n_act = a.sched->n_active;
+    for (int k = threadIdx.x; k < n_act; k += blockDim.x) pre[k + 1] = a.scs[a.act_list[k]].flag_count;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        pre[0] = 0u;
+        for (int k = 1; k <= n_act; ++k) pre[k] += pre[k - 1];
+    }
+    __syncthreads();
+    const unsigned total = pre[n_act];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned it0 = 0;
+        if (lane == 0) it0 = atomicAdd(&a.sched->rescore_next, 4u);
+        it0 = __shfl_sync(0xffffffffu, it0, 0);
+        if (it0 >= total) break;
+        const unsigned it1 = min(it0 + 4u, total);
+        for (unsigned it = it0; it < it1; ++it) {
+            int lo = 0, hi = n_act - 1;  // last k with pre[k] <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (pre[mid] <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            const int b = a.act_list[lo];
+            const BInst &I = a.inst[b];
+            const unsigned local = it - pre[lo];
+            DevScalars *sc = a.scs + b;
+            const double wref = dkey_inv(sc->wref_key);
+            const float wrh = (float)wref;
+            const float wrl = (float)(wref - (double)wrh);
+            const RescorePrune pr{a.groups + I.rec_off / 32, a.recs32s + I.rec_off,
+                                  I.sorted ? a.perm + I.rec_off : nullptr, (I.n + 31) / 32, wref};
+            rescore_pixel<D>(I.g, I.n, a.x + I.seed_off * D, a.A + I.seed_off * D * D, a.Wt + I.seed_off,
+                             a.recs32 + I.rec_off, a.flags[I.flag_off + local], a.flag_gi[I.flag_off + local], wrh,
+                             wrl, pr, sc, a.mom + I.seed_off * K, nullptr);
+        }
+    }
 }
 
 // eqs. (2.7)-(2.8) per instance; writes grad f = -(v - m|P|) into gft and the
@@ -741,13 +781,16 @@ struct apd_batch {
     int dim = 0, count = 0, device = 0;
     long long total_n = 0, total_rec = 0, total_j = 0;
     std::vector<GridDev> grids;
+    std::vector<apd_grid> src_grids;   // as passed to apd_batch_create
+    apd_batch *coarse = nullptr;       // coarse-grid batch of the coarse-to-fine solve
+    int coarse_factor = 0;
     std::vector<int> n;
     std::vector<long long> seed_off, rec_off, flag_off;
     std::vector<double> measure;
     std::vector<int> order;
     int variant = -1;                  // chosen tile variant (-1: autotune pending)
     std::vector<double> variant_ms;    // autotune timings
-    int grid_blocks = 0;
+    int grid_blocks = 0, rescore_blocks = 0;
     size_t smem_assign = 0, smem_prep = 0, smem_sched = 0;
     BArgs args{};
     BInst *d_inst = nullptr;
@@ -824,9 +867,8 @@ int enqueue_iteration(apd_batch &bt, int vi, bool solve_steps, cudaStream_t st) 
     else batch_prep_kernel<2><<<bt.count, kPrepThreads, bt.smem_prep, st>>>(a);
     BTRY(cuda_rc(cudaGetLastError()));
     BTRY(cuda_rc(V.launch(a, bt.grid_blocks, bt.smem_assign, st)));
-    const dim3 rg(kRescoreBlocks, bt.count);
-    if (bt.dim == 3) batch_rescore_kernel<3><<<rg, 256, 0, st>>>(a);
-    else batch_rescore_kernel<2><<<rg, 256, 0, st>>>(a);
+    if (bt.dim == 3) batch_rescore_kernel<3><<<bt.rescore_blocks, 256, bt.smem_sched + 4, st>>>(a);
+    else batch_rescore_kernel<2><<<bt.rescore_blocks, 256, bt.smem_sched + 4, st>>>(a);
     bt.launches += 4;
     if (solve_steps) {
         if (bt.dim == 3) batch_dual_kernel<3><<<bt.count, kSolveThreads, 0, st>>>(a);
@@ -933,6 +975,7 @@ int apd_batch_create(apd_batch **out, int32_t dim, int32_t count, const apd_grid
     bt->count = count;
     cudaGetDevice(&bt->device);
     bt->grids.resize(count);
+    bt->src_grids.assign(grids, grids + count);
     bt->n.resize(count);
     bt->seed_off.resize(count);
     bt->rec_off.resize(count);
@@ -1003,10 +1046,13 @@ int apd_batch_create(apd_batch **out, int32_t dim, int32_t count, const apd_grid
     alloc((void **)&a.recs, (size_t)ro * sizeof(SeedRec));
     alloc((void **)&a.recs_tmp, (size_t)ro * sizeof(SeedRec));
     alloc((void **)&a.recs32, (size_t)ro * sizeof(SeedRec32));
+    alloc((void **)&a.recs32s, (size_t)ro * sizeof(SeedRec32));
+    alloc((void **)&a.groups, (size_t)(ro / 32) * sizeof(GroupBound));
     alloc((void **)&a.scodes, (size_t)ro * sizeof(uint32_t));
     alloc((void **)&a.perm, (size_t)ro * sizeof(int32_t));
     alloc((void **)&a.mom, N * K * sizeof(unsigned long long));
     alloc((void **)&a.flags, (size_t)fo * sizeof(uint32_t));
+    alloc((void **)&a.flag_gi, (size_t)fo * sizeof(int32_t));
     if (ok && cudaMallocHost((void **)&bt->h_sol, count * sizeof(BSolve)) != cudaSuccess) ok = false;
     if (ok && cudaMallocHost((void **)&bt->h_sched, sizeof(BSched)) != cudaSuccess) ok = false;
     if (ok && cudaMallocHost((void **)&bt->h_prm, sizeof(BParams)) != cudaSuccess) ok = false;
@@ -1027,6 +1073,12 @@ int apd_batch_create(apd_batch **out, int32_t dim, int32_t count, const apd_grid
     if (ok && cudaFuncSetAttribute(batch_schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)bt->smem_sched) != cudaSuccess)
         ok = false;
+    if (ok && cudaFuncSetAttribute(dim == 3 ? (const void *)batch_rescore_kernel<3> : (const void *)batch_rescore_kernel<2>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem_sched + 4) != cudaSuccess)
+        ok = false;
+    int sms = 0;
+    if (ok && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, bt->device) != cudaSuccess) ok = false;
+    bt->rescore_blocks = std::max(1, sms) * kRescoreBlocksPerSM;
     if (ok && tile >= 0) {
         bt->variant = tile;
         if (use_variant(*bt, tile, nullptr) != APD_OK) ok = false;
@@ -1042,6 +1094,7 @@ int apd_batch_create(apd_batch **out, int32_t dim, int32_t count, const apd_grid
 
 void apd_batch_destroy(apd_batch *bt) {
     if (!bt) return;
+    apd_batch_destroy(bt->coarse);
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->graph) cudaGraphDestroy(bt->graph);
     if (bt->cap) cudaStreamDestroy(bt->cap);
@@ -1169,6 +1222,50 @@ int apd_batch_solve_weights_judged(apd_batch *bt, const double *x, const double 
                                    const double *v, double *w_out, const apd_solve_opts *opts, apd_solve_info *info,
                                    int32_t *used_pred, apd_stream_t stream) {
     return batch_solve(bt, x, A, w_pred, v, w_out, opts, info, used_pred, true, stream);
+}
+
+int apd_batch_solve_weights_multires(apd_batch *bt, const double *x, const double *A, const double *w0,
+                                     const double *v, double *w_out, const apd_solve_opts *opts,
+                                     const apd_multires_opts *mo, int32_t judge, apd_solve_info *info,
+                                     int32_t *used_pred, apd_stream_t stream) {
+    if (!bt || !x || !A || !w0 || !v || !w_out) return APD_ERR_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    apd_multires_opts m;
+    apd_multires_opts_default(&m);
+    if (mo) m = *mo;
+    if (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1) return APD_ERR_ARG;
+    apd_solve_opts o;
+    apd_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (!bt->coarse || bt->coarse_factor != m.factor) {
+        apd_batch_destroy(bt->coarse);
+        bt->coarse = nullptr;
+        std::vector<apd_grid> cg = bt->src_grids;
+        for (apd_grid &g : cg)
+            for (int d = 0; d < g.dim; ++d) g.res[d] = std::max(4, (g.res[d] + m.factor - 1) / m.factor);
+        const int rc = apd_batch_create(&bt->coarse, bt->dim, bt->count, cg.data(), bt->n.data(), -1);
+        if (rc != APD_OK) return rc;
+        bt->coarse_factor = m.factor;
+    }
+    apd_solve_opts oc = o;
+    oc.eps = m.coarse_eps;
+    oc.max_evals = m.coarse_max_evals;
+    std::vector<apd_solve_info> ci(bt->count);
+    // the coarse weights land in w_out and are the fine solve's start (inputs are
+    // copied into the batch before anything is written, so w0 may alias w_out)
+    int rc = batch_solve(bt->coarse, x, A, w0, v, w_out, &oc, ci.data(), used_pred, judge != 0, stream);
+    if (rc < 0) return rc;
+    rc = batch_solve(bt, x, A, w_out, v, w_out, &o, info, nullptr, false, stream);
+    bt->launches += bt->coarse->launches;
+    bt->coarse->launches = 0;
+    if (info)
+        for (int b = 0; b < bt->count; ++b) {
+            info[b].coarse_evaluations = ci[b].evaluations;
+            info[b].solves += 1;
+            info[b].rescored_fp64 += ci[b].rescored_fp64;
+            info[b].seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+    return rc;
 }
 
 }  // extern "C"

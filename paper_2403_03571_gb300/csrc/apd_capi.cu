@@ -98,6 +98,7 @@ int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, co
     APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
     APD_TRY(cuda_ok(launch_eval_reset(ws, st)));
     APD_TRY(cuda_ok(launch_seed_prep(g, n, x, A, w, ws, st)));
+    APD_TRY(cuda_ok(launch_group_bounds(n, ws, st)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ws.profiling) {
         while (ws.ev.size() < ws.ev_used + 2) {
@@ -119,7 +120,7 @@ int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, co
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
     if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
     APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
-    ws.kernel_launches += (ws.sorted ? 6 : 4) + (prec == APD_FP32 ? 0 : 2);
+    ws.kernel_launches += (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 2);
     ws.last_pixels = g.J;
     ws.last_pairs = g.J * (long long)n;
     return APD_OK;
@@ -517,6 +518,8 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     }
     alloc((void **)&w.moments, (size_t)max_n * K * sizeof(unsigned long long));
     alloc((void **)&w.flags, (size_t)max_j * sizeof(uint32_t));
+    alloc((void **)&w.flag_gi, (size_t)max_j * sizeof(int32_t));
+    alloc((void **)&w.groups, (size_t)(w.n_pad_max / 32) * sizeof(GroupBound));
     alloc((void **)&w.sc, sizeof(DevScalars));
     // tensor-core tiles hold 512 pixels; 8x slack covers ragged grids down to thin slabs
     w.tc_tile_cap = max_j / 64 + 4096;
@@ -555,7 +558,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_cand, w.moments, w.flags, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_cand, w.moments, w.flags, w.flag_gi, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -693,9 +696,13 @@ int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const d
     if (rc == APD_OK && warmstart_dim(net) != g.dim) rc = APD_ERR_ARG;
     if (rc == APD_OK) {
         const int64_t offs[2] = {0, seeds->n};
-        const double meas = domain_measure(grid);
-        rc = apd_warmstart_features(net, 1, offs, &meas, seeds->x, seeds->A, v, ws->w.wfeat, stream);
-        if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, &meas, ws->w.wfeat, ws->w.wpred, stream);
+        double box[6] = {0.0, 0.0, 0.0, 1.0, 1.0, 1.0};
+        for (int a = 0; a < grid->dim; ++a) {
+            box[a] = grid->lo[a];
+            box[3 + a] = grid->hi[a];
+        }
+        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, stream);
+        if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, box, ws->w.wfeat, ws->w.wpred, stream);
         ws->w.kernel_launches += 2;
     }
     if (rc == APD_OK)
@@ -704,6 +711,70 @@ int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const d
     if (rc >= 0) cudaStreamSynchronize(st);
     if (used_pred) *used_pred = used;
     inf.status = rc;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
+void apd_multires_opts_default(apd_multires_opts *mo) {
+    if (!mo) return;
+    mo->factor = 2;
+    mo->coarse_eps = 0.05;
+    mo->coarse_max_evals = 60;
+}
+
+int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
+                               const apd_solve_opts *opts, const apd_multires_opts *mo, apd_solve_info *info,
+                               apd_workspace *ws, apd_mlp *net, int32_t *used_pred, apd_stream_t stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    apd_solve_info inf, cinf;
+    std::memset(&inf, 0, sizeof inf);
+    std::memset(&cinf, 0, sizeof cinf);
+    GridDev g, gc;
+    apd_solve_opts o;
+    apd_multires_opts m;
+    apd_multires_opts_default(&m);
+    if (mo) m = *mo;
+    cudaStream_t st = (cudaStream_t)stream;
+    int used = 0;
+    int rc = solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st);
+    if (rc == APD_OK && (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1)) rc = APD_ERR_ARG;
+    if (rc == APD_OK && net && warmstart_dim(net) != g.dim) rc = APD_ERR_ARG;
+    apd_grid cg = *grid;
+    if (rc == APD_OK) {
+        for (int d = 0; d < grid->dim; ++d) cg.res[d] = std::max(4, (grid->res[d] + m.factor - 1) / m.factor);
+        rc = validate_grid(&cg, gc);
+    }
+    apd_solve_opts oc = o;
+    oc.eps = m.coarse_eps;
+    oc.max_evals = m.coarse_max_evals;
+    const double *w0 = seeds->w;
+    if (rc == APD_OK && net) {
+        const int64_t offs[2] = {0, seeds->n};
+        double box[6] = {0.0, 0.0, 0.0, 1.0, 1.0, 1.0};
+        for (int a = 0; a < grid->dim; ++a) {
+            box[a] = grid->lo[a];
+            box[3 + a] = grid->hi[a];
+        }
+        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, stream);
+        if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, box, ws->w.wfeat, ws->w.wpred, stream);
+        ws->w.kernel_launches += 2;
+        w0 = ws->w.wpred;
+    }
+    if (rc == APD_OK) {
+        // the coarse solve writes w_out; its status (often NOT_CONVERGED at the cap) is not an error
+        const int crc = solve_impl(gc, &cg, seeds->n, seeds->x, seeds->A, w0, v, w_out, oc, cinf, ws->w, st, false,
+                                   net != nullptr, &used);
+        if (crc < 0) rc = crc;
+    }
+    if (rc == APD_OK)
+        rc = solve_impl(g, grid, seeds->n, seeds->x, seeds->A, w_out, v, w_out, o, inf, ws->w, st, false);
+    if (rc >= 0) cudaStreamSynchronize(st);
+    if (used_pred) *used_pred = used;
+    inf.status = rc;
+    inf.solves += cinf.solves;
+    inf.rescored_fp64 += cinf.rescored_fp64;
+    inf.coarse_evaluations = cinf.evaluations;
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
     return rc;

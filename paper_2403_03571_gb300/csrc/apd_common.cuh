@@ -166,11 +166,54 @@ __device__ __forceinline__ void build_seed(const int i, const int n, const doubl
         r.a[5] = (float)s[2][2];
     }
     wkey = finite ? wi : -DBL_MAX;
+    r.pad[0] = __double2float_rd(lam);  // lower bound of lambda_min for the group bounds
 #pragma unroll
     for (int a = 0; a < D; ++a) split_f32(xx[a], r32.xh[a], r32.xl[a]);
     split_f32(wi, r32.wh, r32.wl);
 #pragma unroll
     for (int a = 0; a < 6; ++a) r32.a[a] = r.a[a];
+    r32.pad[0] = r.pad[0];
+}
+
+// Bounds of group `grp` (32 consecutive records, positions >= n are padding),
+// computed by one warp and written by lane 0.
+template <int D>
+__device__ __forceinline__ void group_bound_warp(const SeedRec *__restrict__ recs, const int n, const int grp,
+                                                 GroupBound *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int pos = grp * 32 + lane;
+    const bool real = pos < n;
+    float lo[3], hi[3];
+    float lam = real ? recs[pos].pad[0] : FLT_MAX;
+    double wm = real ? recs[pos].w : -DBL_MAX;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double xa = (real && a < D) ? recs[pos].x[a] : 0.0;
+        lo[a] = real ? __double2float_rd(xa) : FLT_MAX;
+        hi[a] = real ? __double2float_ru(xa) : -FLT_MAX;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+        lam = fminf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
+        wm = fmax(wm, __shfl_xor_sync(0xffffffffu, wm, off));
+    }
+    if (lane == 0) {
+        GroupBound gb;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gb.lo[a] = lo[a];
+            gb.hi[a] = hi[a];
+        }
+        gb.lam = lam;
+        gb.pad = 0.f;
+        gb.wmax = wm;
+        out[grp] = gb;
+    }
 }
 
 // Morton code of a seed position on the grid box (padding sorts last).

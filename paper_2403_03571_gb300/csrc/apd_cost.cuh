@@ -109,50 +109,22 @@ __device__ __forceinline__ void cost32_bound_rel(const SeedRec32 &r, const float
 // wins, ties to the lowest index.  Any seed left out has an exact cost above the
 // exact minimum by more than the FP64 rounding, so the result equals the FP64
 // argmin over all seeds.
+//
+// Pruned form (group bounds available and the scoring pass's best seed `gi`
+// known): the threshold is C_gi + E_gi (>= the full threshold, so the
+// candidate set only grows), and a group of 32 scan-order seeds is skipped
+// when a lower bound of the exact cost of all its seeds at y,
+//     lam_g dist(y, box_g)^2 + (w_ref - wmax_g),
+// evaluated with outward rounding, exceeds the threshold by a margin of
+// 1e-6 (|thr| + |bound| + |w_ref - wmax_g|) (far above the FP64 rounding of any
+// seed whose exact cost is near the bound): none of its seeds can be a
+// candidate, nor the FP64 argmin.
 template <int D>
-__device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, const double *__restrict__ x,
-                                              const double *__restrict__ A, const double *__restrict__ w,
-                                              const SeedRec32 *__restrict__ r32, const uint32_t fj,
-                                              const float wrh, const float wrl, DevScalars *__restrict__ sc,
-                                              unsigned long long *__restrict__ gmom,
-                                              int32_t *__restrict__ labels) {
+__device__ __forceinline__ void rescore_finish(const GridDev &g, const int n, const long long j, const int (&k)[3],
+                                               double best, int bi, DevScalars *__restrict__ sc,
+                                               unsigned long long *__restrict__ gmom, int32_t *__restrict__ labels) {
     constexpr int K = moment_width(D);
     const int lane = threadIdx.x & 31;
-    const long long j = (long long)fj;
-    int k[3] = {0, 0, 0};
-    long long rr = j;
-    double y[D];
-    float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        k[a] = (int)(rr % g.res[a]);
-        rr /= g.res[a];
-        y[a] = __dadd_rn(g.lo[a], __dmul_rn((double)k[a] + 0.5, g.h[a]));
-        yh[a] = (float)y[a];
-        yl[a] = (float)(y[a] - (double)yh[a]);
-    }
-    // pass 1: threshold = min over seeds of (C + E)
-    float thr = __int_as_float(0x7f800000);
-    for (int s = lane; s < n; s += 32) {
-        float c, E;
-        cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
-        thr = fminf(thr, c + E);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) thr = fminf(thr, __shfl_xor_sync(0xffffffffu, thr, off));
-    // pass 2: FP64 reference cost of the candidates
-    double best = __longlong_as_double(0x7ff0000000000000ll);
-    int bi = 0x7fffffff;
-    for (int s = lane; s < n; s += 32) {
-        float c, E;
-        cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
-        if (!(c - E <= thr)) continue;
-        const double c64 = cost64<D>(y, x + (size_t)s * D, A + (size_t)s * D * D, w[s]);
-        if (c64 < best) {
-            best = c64;
-            bi = s;
-        }
-    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const double ob = __shfl_xor_sync(0xffffffffu, best, off);
@@ -181,6 +153,105 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
                 for (int b = a; b < D; ++b) atomicAdd(&o[e++], u[a] * u[b]);
         }
     }
+}
+
+// Optional pruning inputs of rescore_pixel (all null / 0 disables pruning).
+struct RescorePrune {
+    const GroupBound *groups;   // [n_groups] bounds of the scan-order groups
+    const SeedRec32 *r32s;      // [n_groups * 32] records in scan order
+    const int32_t *perm;        // scan position -> seed index (null: identity)
+    int n_groups;
+    double wref;
+};
+
+template <int D>
+__device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, const double *__restrict__ x,
+                                              const double *__restrict__ A, const double *__restrict__ w,
+                                              const SeedRec32 *__restrict__ r32, const uint32_t fj, const int gi,
+                                              const float wrh, const float wrl, const RescorePrune &pr,
+                                              DevScalars *__restrict__ sc, unsigned long long *__restrict__ gmom,
+                                              int32_t *__restrict__ labels) {
+    const int lane = threadIdx.x & 31;
+    const long long j = (long long)fj;
+    int k[3] = {0, 0, 0};
+    long long rr = j;
+    double y[D];
+    float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        k[a] = (int)(rr % g.res[a]);
+        rr /= g.res[a];
+        y[a] = __dadd_rn(g.lo[a], __dmul_rn((double)k[a] + 0.5, g.h[a]));
+        yh[a] = (float)y[a];
+        yl[a] = (float)(y[a] - (double)yh[a]);
+    }
+    double best = __longlong_as_double(0x7ff0000000000000ll);
+    int bi = 0x7fffffff;
+    float thr = __int_as_float(0x7f800000);
+    if (pr.groups && gi >= 0 && gi < n) {
+        float c, E;
+        cost32_bound<D>(r32[gi], yh, yl, wrh, wrl, c, E);
+        thr = c + E;
+    }
+    if (thr < __int_as_float(0x7f800000)) {
+        for (int base = 0; base < pr.n_groups; base += 32) {
+            const int grp = base + lane;
+            bool keep = false;
+            if (grp < pr.n_groups) {
+                const GroupBound gb = pr.groups[grp];
+                float d2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const float slack = 1e-6f * (fabsf(yh[a]) + fabsf(gb.lo[a]) + fabsf(gb.hi[a]));
+                    const float t = fmaxf(fmaxf(gb.lo[a] - yh[a], yh[a] - gb.hi[a]) - slack, 0.f);
+                    d2 = fmaf(t, t, d2);
+                }
+                const float wpart = __double2float_rd(pr.wref - gb.wmax);
+                const float lb = __fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f) + wpart;
+                keep = !(lb > thr + 1e-6f * (fabsf(thr) + fabsf(lb) + fabsf(wpart)) + 1e-30f);
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, keep);
+            while (mask) {
+                const int kk = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int pos = (base + kk) * 32 + lane;
+                if (pos < n) {
+                    const int s = pr.perm ? pr.perm[pos] : pos;
+                    float c, E;
+                    cost32_bound<D>(pr.r32s[pos], yh, yl, wrh, wrl, c, E);
+                    if (c - E <= thr) {
+                        const double c64 = cost64<D>(y, x + (size_t)s * D, A + (size_t)s * D * D, w[s]);
+                        if (c64 < best || (c64 == best && s < bi)) {
+                            best = c64;
+                            bi = s;
+                        }
+                    }
+                }
+            }
+        }
+        rescore_finish<D>(g, n, j, k, best, bi, sc, gmom, labels);
+        return;
+    }
+    // full scan: pass 1, threshold = min over seeds of (C + E)
+    for (int s = lane; s < n; s += 32) {
+        float c, E;
+        cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
+        thr = fminf(thr, c + E);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) thr = fminf(thr, __shfl_xor_sync(0xffffffffu, thr, off));
+    // pass 2: FP64 reference cost of the candidates
+    for (int s = lane; s < n; s += 32) {
+        float c, E;
+        cost32_bound<D>(r32[s], yh, yl, wrh, wrl, c, E);
+        if (!(c - E <= thr)) continue;
+        const double c64 = cost64<D>(y, x + (size_t)s * D, A + (size_t)s * D * D, w[s]);
+        if (c64 < best) {
+            best = c64;
+            bi = s;
+        }
+    }
+    rescore_finish<D>(g, n, j, k, best, bi, sc, gmom, labels);
 }
 
 }  // namespace apd

@@ -158,6 +158,7 @@ struct TileSrc {
     const int32_t *perm;          // scan position -> seed index (null: identity)
     unsigned long long *gmom;     // [n][K]
     uint32_t *flags;              // queue of pixels for FP64 rescoring
+    int32_t *flag_gi;             // FP32 best seed of each queued pixel (or null)
     int32_t *labels;              // [J] or null
     DevScalars *sc;
 };
@@ -371,6 +372,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             if (flagged) {
                 const unsigned slot = atomicAdd(&s.sc->flag_count, 1u);
                 s.flags[slot] = (uint32_t)j;
+                if (s.flag_gi) s.flag_gi[slot] = GI[p] < n ? GI[p] : -1;
             }
             if (s.labels) s.labels[j] = GI[p];
         }

@@ -42,10 +42,21 @@ struct __align__(16) SeedRec32 {
 };
 static_assert(sizeof(SeedRec32) == 64, "SeedRec32 must be 64 bytes");
 
+// Bounds of a group of 32 consecutive seeds (scan order) for pruning the
+// near-tie rescoring: FP32 box of the positions (rounded outwards), a lower
+// bound of lambda_min over the group, and the largest weight.
+struct __align__(8) GroupBound {
+    float lo[3], hi[3];
+    float lam;
+    float pad;
+    double wmax;
+};
+static_assert(sizeof(GroupBound) == 40, "GroupBound must be 40 bytes");
+
 constexpr int kChunk = 256;         // seeds per shared-memory chunk (= scoring CTA size)
 constexpr int kSortMax = 16384;     // largest padded seed count ordered on the device
 constexpr int kGroup = 32;          // seeds per packed-index group (5 low mantissa bits)
-constexpr int kWarmFeatMax = 23;    // warm-start features per seed (3D; 20 in 2D)
+constexpr int kWarmFeatMax = 32;    // warm-start features per seed (3D; 28 in 2D)
 
 // Small block of device scalars owned by the workspace.
 struct DevScalars {
@@ -88,6 +99,8 @@ struct Workspace {
     bool sorted = false;                // set by launch_seed_prep for the current pass
     unsigned long long *moments = nullptr;  // [max_n * K]
     uint32_t *flags = nullptr;          // [max_j]
+    int32_t *flag_gi = nullptr;         // [max_j] FP32 best seed of each queued pixel (-1: none)
+    GroupBound *groups = nullptr;       // [n_pad_max / 32] bounds of the scan-order seed groups
     DevScalars *sc = nullptr;           // device
     DevScalars *sc_host = nullptr;      // pinned host mirror
     double *part = nullptr;             // [2 * max_blocks] dual partial sums
@@ -245,6 +258,8 @@ cudaError_t launch_assign_tc(const GridDev &g, int n, Workspace &ws, int32_t *la
                              unsigned long long *moments, int kind, cudaStream_t st);
 // number of tensor-core tiles the grid needs (the workspace holds tc_tile_cap)
 long long tc_tile_count(const GridDev &g);
+// bounds of the 32-seed groups of the scan-order records (ws.groups)
+cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st);
 // FP64 rescoring of the queued pixels (labels optional, moments updated).
 cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,
                                 const double *w, Workspace &ws, int32_t *labels,

@@ -68,6 +68,12 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+template <int D>
+__global__ void group_bounds_kernel(const int n, const SeedRec *__restrict__ recs, GroupBound *__restrict__ groups) {
+    const int grp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (grp * 32 < n) group_bound_warp<D>(recs, n, grp, groups);
+}
+
 __global__ void gather_recs_kernel(const int n_pad, const int32_t *__restrict__ perm,
                                    const SeedRec *__restrict__ src, SeedRec *__restrict__ dst,
                                    const SeedRec32 *__restrict__ src32, SeedRec32 *__restrict__ dst32) {
@@ -283,6 +289,15 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
     }
     morton_sort_kernel<<<1, 1024, smem, st>>>(n_pad, m, ws.codes, ws.scodes, ws.perm);
     gather_recs_kernel<<<blocks, 256, 0, st>>>(n_pad, ws.perm, ws.recs_tmp, ws.recs, ws.recs32, ws.recs32s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st) {
+    if (!ws.groups) return cudaSuccess;
+    const int groups = (n + 31) / 32;
+    const int blocks = (groups * 32 + 255) / 256;
+    if (ws.dim == 3) group_bounds_kernel<3><<<blocks, 256, 0, st>>>(n, ws.recs, ws.groups);
+    else group_bounds_kernel<2><<<blocks, 256, 0, st>>>(n, ws.recs, ws.groups);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,20 @@
 // Learned warm start of the weight solve: a per-seed MLP predicts initial
 // weights from local statistics of the generators, trained on solved instances.
 //
-// Features of seed i of an instance with n seeds on a domain of measure |O|
-// (F = 20 in 2D, 23 in 3D), with s = n / |O| the seed density:
+// Features of seed i of an instance with n seeds on the box [lo, hi] of
+// measure |O| (F = 28 in 2D, 32 in 3D), with s = n / |O| the seed density and
+// lengths in units of the mean spacing s^(-1/D):
 //   [ v_i s,  the upper triangle of (A_i + A_i^T) / 2 (3 or 6 entries),
-//     the distances to the 8 nearest other seeds times s^(1/D) (ascending),
-//     the target volumes of those 8 seeds times s ]
+//     the distances to the 8 nearest other seeds (ascending),
+//     the target volumes of those 8 seeds times s,
+//     the distance to the nearer wall along each axis (D entries),
+//     for the radii r = 2, 4, 8: c_r / E_r and (V_r s - c_r) / E_r, where c_r
+//     counts the other seeds within r, V_r sums their target volumes and
+//     E_r = w_D r^D is the expected count (w_D the unit-ball volume) ]
+// The first four groups describe the seed and its nearest neighbours; the wall
+// distances and the volume/count mismatch at three scales carry what a cell's
+// weight needs from farther away (the solved weights vary smoothly over many
+// cells, driven by the boundary and by the local excess of target volume).
 // Network: F -> 64 -> 64 -> 64 -> 1, ReLU on the hidden layers, inputs
 // standardised by a stored mean / standard deviation.  The output y_i is a
 // weight in units of the mean cell size squared: w_i = y_i s^(-2/D).
@@ -30,8 +39,10 @@ constexpr int kH = 64;       // hidden width
 constexpr int kNN = 8;       // neighbours per seed
 constexpr int kTrainB = 128; // samples (threads) per CTA of the network kernels
 
-__host__ __device__ constexpr int feat_dim(int D) { return 1 + D * (D + 1) / 2 + 2 * kNN; }
+constexpr int kRadii = 3;    // neighbourhood radii 2, 4, 8 (mean spacings)
+__host__ __device__ constexpr int feat_dim(int D) { return 1 + D * (D + 1) / 2 + 2 * kNN + D + 2 * kRadii; }
 static_assert(feat_dim(3) == kWarmFeatMax, "workspace feature scratch");
+constexpr int F2 = feat_dim(2), F3 = feat_dim(3);
 __host__ __device__ constexpr int param_count(int F) { return kH * F + kH + 2 * (kH * kH + kH) + kH + 1; }
 
 // parameter offsets in the flat FP32 array: W1 [64][F], b1, W2 [64][64], b2, W3, b3, W4 [64], b4
@@ -48,7 +59,7 @@ struct Layout {
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(256)
-    features_kernel(const int count, const long long *__restrict__ offs, const double *__restrict__ measure,
+    features_kernel(const int count, const long long *__restrict__ offs, const double *__restrict__ box,
                     const double *__restrict__ x, const double *__restrict__ A, const double *__restrict__ v,
                     float *__restrict__ feat) {
     constexpr int F = feat_dim(D);
@@ -63,10 +74,23 @@ __global__ void __launch_bounds__(256)
     }
     const long long o = offs[lo];
     const int n = (int)(offs[lo + 1] - o);
-    const double dens = (double)n / measure[lo];
+    const double *bx = box + (size_t)lo * 6;  // lo[3], hi[3]
+    double meas = 1.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) meas *= bx[3 + a] - bx[a];
+    const double dens = (double)n / meas;
+    const double ls = pow(dens, 1.0 / D);      // 1 / mean spacing
     double xi[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) xi[a] = x[gi * D + a];
+    double rad2[kRadii], cnt[kRadii], vsum[kRadii];
+#pragma unroll
+    for (int r = 0; r < kRadii; ++r) {
+        const double rr = (double)(2 << r) / ls;
+        rad2[r] = rr * rr;
+        cnt[r] = 0.0;
+        vsum[r] = 0.0;
+    }
     double bd[kNN];
     int bj[kNN];
 #pragma unroll
@@ -82,6 +106,12 @@ __global__ void __launch_bounds__(256)
             const double t = x[(o + j) * D + a] - xi[a];
             d2 += t * t;
         }
+#pragma unroll
+        for (int r = 0; r < kRadii; ++r)
+            if (d2 < rad2[r]) {
+                cnt[r] += 1.0;
+                vsum[r] += v[o + j];
+            }
         if (d2 < bd[kNN - 1]) {  // insertion into the sorted list (ties keep the lower index first)
             int p = kNN - 1;
             while (p > 0 && bd[p - 1] > d2) {
@@ -101,11 +131,20 @@ __global__ void __launch_bounds__(256)
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = a; b < D; ++b) f[c++] = (float)(0.5 * (Ai[a * D + b] + Ai[b * D + a]));
-    const double ls = pow(dens, 1.0 / D);
 #pragma unroll
     for (int k = 0; k < kNN; ++k) f[c + k] = bj[k] >= 0 ? (float)(sqrt(bd[k]) * ls) : 4.f;
 #pragma unroll
     for (int k = 0; k < kNN; ++k) f[c + kNN + k] = bj[k] >= 0 ? (float)(v[o + bj[k]] * dens) : 0.f;
+    c += 2 * kNN;
+#pragma unroll
+    for (int a = 0; a < D; ++a) f[c++] = (float)(fmin(xi[a] - bx[a], bx[3 + a] - xi[a]) * ls);
+    const double wD = D == 2 ? 3.14159265358979323846 : 4.18879020478639098461;  // unit-ball volume
+#pragma unroll
+    for (int r = 0; r < kRadii; ++r) {
+        const double e = wD * (double)((2 << r) * (2 << r) * (D == 3 ? (2 << r) : 1));
+        f[c++] = (float)(cnt[r] / e);
+        f[c++] = (float)((vsum[r] * dens - cnt[r]) / e);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -171,7 +210,7 @@ __device__ __forceinline__ float forward(const float *sp, Rows<F> &R, int t, con
 // W_pred of every seed: y_i s^(-2/D), s = n_b / |O_b|
 template <int D>
 __global__ void __launch_bounds__(kTrainB)
-    predict_kernel(const int count, const long long *__restrict__ offs, const double *__restrict__ measure,
+    predict_kernel(const int count, const long long *__restrict__ offs, const double *__restrict__ box,
                    const float *__restrict__ params, const float *__restrict__ norm, const float *__restrict__ feat,
                    double *__restrict__ w_out) {
     constexpr int F = feat_dim(D);
@@ -189,8 +228,11 @@ __global__ void __launch_bounds__(kTrainB)
         else hi = mid - 1;
     }
     const int n = (int)(offs[lo + 1] - offs[lo]);
+    double meas = 1.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) meas *= box[(size_t)lo * 6 + 3 + a] - box[(size_t)lo * 6 + a];
     const float y = forward<F>(sp, R, threadIdx.x, feat, s);
-    w_out[s] = (double)y * pow((double)n / measure[lo], -2.0 / D);
+    w_out[s] = (double)y * pow((double)n / meas, -2.0 / D);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,7 +386,7 @@ struct apd_mlp {
     float *part = nullptr, *loss_part = nullptr;
     int part_cap = 0;  // CTAs the partial buffer holds
     long long *offs = nullptr;
-    double *meas = nullptr;
+    double *box = nullptr;   // [inst_cap][6] instance boxes (lo, hi)
     int inst_cap = 0;
     int step = 0;
 };
@@ -357,30 +399,35 @@ namespace {
 
 int ws_rc(cudaError_t e) { return e == cudaSuccess ? APD_OK : APD_ERR_CUDA; }
 
-int ensure_instances(apd_mlp *net, int count, const int64_t *offsets, const double *measure, cudaStream_t st) {
+int ensure_instances(apd_mlp *net, int count, const int64_t *offsets, const double *box, cudaStream_t st) {
     if (count > net->inst_cap) {
         if (net->offs) cudaFree(net->offs);
-        if (net->meas) cudaFree(net->meas);
+        if (net->box) cudaFree(net->box);
         net->offs = nullptr;
-        net->meas = nullptr;
+        net->box = nullptr;
         net->inst_cap = 0;
         if (cudaMalloc((void **)&net->offs, (size_t)(count + 1) * sizeof(long long)) != cudaSuccess ||
-            cudaMalloc((void **)&net->meas, (size_t)count * sizeof(double)) != cudaSuccess)
+            cudaMalloc((void **)&net->box, (size_t)count * 6 * sizeof(double)) != cudaSuccess)
             return APD_ERR_CUDA;
         net->inst_cap = count;
     }
     // host arrays -> device (pageable copies are synchronous with respect to the host)
     if (cudaMemcpyAsync(net->offs, offsets, (size_t)(count + 1) * sizeof(long long), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
-        cudaMemcpyAsync(net->meas, measure, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        cudaMemcpyAsync(net->box, box, (size_t)count * 6 * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return APD_ERR_CUDA;
     return APD_OK;
 }
 
-int check_offsets(int count, const int64_t *offsets, const double *measure) {
-    if (count < 1 || !offsets || !measure || offsets[0] != 0) return APD_ERR_ARG;
-    for (int b = 0; b < count; ++b)
-        if (offsets[b + 1] <= offsets[b] || !(measure[b] > 0.0)) return APD_ERR_ARG;
+int check_offsets(int dim, int count, const int64_t *offsets, const double *box) {
+    if (count < 1 || !offsets || !box || offsets[0] != 0) return APD_ERR_ARG;
+    for (int b = 0; b < count; ++b) {
+        if (offsets[b + 1] <= offsets[b]) return APD_ERR_ARG;
+        for (int a = 0; a < dim; ++a)
+            if (!(box[6 * b + 3 + a] > box[6 * b + a]) || !std::isfinite(box[6 * b + a]) ||
+                !std::isfinite(box[6 * b + 3 + a]))
+                return APD_ERR_ARG;
+    }
     return APD_OK;
 }
 
@@ -413,14 +460,14 @@ int apd_warmstart_create(apd_mlp **out, int32_t dim, const float *params, const 
          cudaMemset(net->v, 0, P * sizeof(float)) == cudaSuccess;
     if (ok && dim == 2)
         ok = cudaFuncSetAttribute(predict_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)net_smem<20>()) == cudaSuccess &&
-             cudaFuncSetAttribute(train_grad_kernel<20>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)net_smem<20>()) == cudaSuccess;
+                                  (int)net_smem<F2>()) == cudaSuccess &&
+             cudaFuncSetAttribute(train_grad_kernel<F2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)net_smem<F2>()) == cudaSuccess;
     if (ok && dim == 3)
         ok = cudaFuncSetAttribute(predict_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)net_smem<23>()) == cudaSuccess &&
-             cudaFuncSetAttribute(train_grad_kernel<23>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)net_smem<23>()) == cudaSuccess;
+                                  (int)net_smem<F3>()) == cudaSuccess &&
+             cudaFuncSetAttribute(train_grad_kernel<F3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)net_smem<F3>()) == cudaSuccess;
     if (!ok) {
         apd_warmstart_destroy(net);
         return APD_ERR_CUDA;
@@ -431,7 +478,7 @@ int apd_warmstart_create(apd_mlp **out, int32_t dim, const float *params, const 
 
 void apd_warmstart_destroy(apd_mlp *net) {
     if (!net) return;
-    void *ptrs[] = {net->params, net->m, net->v, net->norm, net->part, net->loss_part, net->offs, net->meas};
+    void *ptrs[] = {net->params, net->m, net->v, net->norm, net->part, net->loss_part, net->offs, net->box};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete net;
@@ -453,20 +500,20 @@ int apd_warmstart_get(apd_mlp *net, float *params, float *norm) {
     return APD_OK;
 }
 
-int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, const double *measure,
+int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, const double *box,
                            const double *x, const double *A, const double *v, float *features, apd_stream_t stream) {
     if (!net || !x || !A || !v || !features) return APD_ERR_ARG;
-    int rc = check_offsets(count, offsets, measure);
+    int rc = check_offsets(net->dim, count, offsets, box);
     if (rc != APD_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = ensure_instances(net, count, offsets, measure, st);
+    rc = ensure_instances(net, count, offsets, box, st);
     if (rc != APD_OK) return rc;
     const long long total = offsets[count];
     const int blocks = (int)((total + 255) / 256);
     if (net->dim == 2)
-        features_kernel<2><<<blocks, 256, 0, st>>>(count, net->offs, net->meas, x, A, v, features);
+        features_kernel<2><<<blocks, 256, 0, st>>>(count, net->offs, net->box, x, A, v, features);
     else
-        features_kernel<3><<<blocks, 256, 0, st>>>(count, net->offs, net->meas, x, A, v, features);
+        features_kernel<3><<<blocks, 256, 0, st>>>(count, net->offs, net->box, x, A, v, features);
     return ws_rc(cudaGetLastError());
 }
 
@@ -476,21 +523,21 @@ int apd_warmstart_fit_norm(apd_mlp *net, int64_t samples, const float *features,
     return ws_rc(cudaGetLastError());
 }
 
-int apd_warmstart_predict(apd_mlp *net, int32_t count, const int64_t *offsets, const double *measure,
+int apd_warmstart_predict(apd_mlp *net, int32_t count, const int64_t *offsets, const double *box,
                           const float *features, double *w_out, apd_stream_t stream) {
     if (!net || !features || !w_out) return APD_ERR_ARG;
-    int rc = check_offsets(count, offsets, measure);
+    int rc = check_offsets(net->dim, count, offsets, box);
     if (rc != APD_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = ensure_instances(net, count, offsets, measure, st);
+    rc = ensure_instances(net, count, offsets, box, st);
     if (rc != APD_OK) return rc;
     const long long total = offsets[count];
     const int blocks = (int)((total + kTrainB - 1) / kTrainB);
     if (net->dim == 2)
-        predict_kernel<2><<<blocks, kTrainB, net_smem<20>(), st>>>(count, net->offs, net->meas, net->params,
+        predict_kernel<2><<<blocks, kTrainB, net_smem<F2>(), st>>>(count, net->offs, net->box, net->params,
                                                                     net->norm, features, w_out);
     else
-        predict_kernel<3><<<blocks, kTrainB, net_smem<23>(), st>>>(count, net->offs, net->meas, net->params,
+        predict_kernel<3><<<blocks, kTrainB, net_smem<F3>(), st>>>(count, net->offs, net->box, net->params,
                                                                     net->norm, features, w_out);
     return ws_rc(cudaGetLastError());
 }
@@ -511,12 +558,12 @@ int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, co
             return APD_ERR_CUDA;
         net->part_cap = nparts;
     }
-    const size_t smem = net->F == 20 ? net_smem<20>() : net_smem<23>();
-    if (net->F == 20)
-        train_grad_kernel<20><<<nparts, kTrainB, smem, st>>>(batch, idx, net->params, net->norm, features, targets,
+    const size_t smem = net->F == F2 ? net_smem<F2>() : net_smem<F3>();
+    if (net->F == F2)
+        train_grad_kernel<F2><<<nparts, kTrainB, smem, st>>>(batch, idx, net->params, net->norm, features, targets,
                                                              net->part, net->loss_part);
     else
-        train_grad_kernel<23><<<nparts, kTrainB, smem, st>>>(batch, idx, net->params, net->norm, features, targets,
+        train_grad_kernel<F3><<<nparts, kTrainB, smem, st>>>(batch, idx, net->params, net->norm, features, targets,
                                                              net->part, net->loss_part);
     float bc1 = 1.f, bc2 = 1.f;
     if (lr > 0.f) {

@@ -82,11 +82,11 @@ def predict(net: capi.WarmStart, insts, x, A, v):
     """Predicted weights (device, concatenated) for the instances."""
     import torch
     counts = [i.n for i in insts]
-    meas = [i.grid.measure for i in insts]
+    grids = [i.grid for i in insts]
     feats = torch.empty((sum(counts), net.n_features), dtype=torch.float32, device=x.device)
-    net.features(counts, meas, x, A, v, feats)
+    net.features(counts, grids, x, A, v, feats)
     w = torch.empty(sum(counts), dtype=torch.float64, device=x.device)
-    net.predict(counts, meas, feats, w)
+    net.predict(counts, grids, feats, w)
     return w
 
 
@@ -109,7 +109,7 @@ def generate(dim: int, count: int, seed: int, chunk: int = 256, log=print):
         w_out = torch.zeros_like(w)
         rc, infos = capi.apd_batch_solve_weights(b, x, A, w, v, w_out, opts)
         f = torch.empty((x.shape[0], F), dtype=torch.float32, device="cuda")
-        feat_net.features([i.n for i in insts], [i.grid.measure for i in insts], x, A, v, f)
+        feat_net.features([i.n for i in insts], [i.grid for i in insts], x, A, v, f)
         W = w_out.cpu().numpy()
         stats["seconds"] += time.time() - t0
         off = 0

@@ -131,3 +131,17 @@ def test_batch_errors(capi):
     # the batch is still usable after the errors
     rc, infos = capi.apd_batch_solve_weights(b, x, A, w, v, w_out)
     _check_solved(insts, host(w_out), infos, capi)
+
+
+def test_batch_coarse_to_fine(capi):
+    insts = [synth.make_instance(3, n, m, 60 + k) for k, (n, m) in enumerate([(200, 48), (80, 32), (400, 64)])]
+    x, A, w, v = _tensors(insts)
+    b = capi.Batch(3, [i.grid for i in insts], [i.n for i in insts])
+    w_out = torch.zeros_like(w)
+    rc, infos, used = capi.apd_batch_solve_weights_multires(b, x, A, w, v, w_out)
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE)
+    assert all(i.coarse_evaluations >= 1 and i.solves == 2 for i in infos)
+    _check_solved(insts, host(w_out), infos, capi)
+    w2 = torch.zeros_like(w)
+    _, plain = capi.apd_batch_solve_weights(b, x, A, w, v, w2)
+    assert sum(i.evaluations for i in infos) < sum(i.evaluations for i in plain)

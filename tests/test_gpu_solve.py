@@ -94,3 +94,20 @@ def test_not_converged_reports_best(capi):
     assert info.evaluations <= 16
     _, _, err = oracle.dual(inst.grid, inst.x, inst.A, host(w_out), inst.v)
     assert abs(err - info.max_rel_err) <= 1e-12
+
+
+@pytest.mark.parametrize("dim,n,m,seed", [(3, 300, 64, 12), (2, 400, 384, 13)])
+def test_coarse_to_fine_solve(capi, dim, n, m, seed):
+    inst = synth.make_instance(dim, n, m, seed)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(dim, n, inst.grid.num_pixels)
+    w_out = torch.zeros_like(w)
+    rc, info, used = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws)
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+    assert used == 0 and info.coarse_evaluations >= 1 and info.solves == 2
+    _, _, err = oracle.dual(inst.grid, inst.x, inst.A, host(w_out), inst.v)
+    assert err < 0.01 and abs(info.max_rel_err - err) <= 1e-12
+    # the fine grid needs fewer evaluations from the coarse weights than from zero
+    w2 = torch.zeros_like(w)
+    rc2, plain = capi.apd_solve_weights(inst.grid, x, A, w, v, w2, ws)
+    assert info.evaluations < plain.evaluations, (info.as_dict(), plain.as_dict())

@@ -17,16 +17,17 @@ def _instance(dim, n, seed):
 
 
 def test_parameter_counts_from_layer_sizes():
-    # F -> 64 -> 64 -> 64 -> 1 with biases: 9729 (2D, F = 20) and 9921 (3D, F = 23)
-    assert ow.n_features(2) == 20 and ow.n_features(3) == 23
-    assert ow.n_params(2) == 20 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1 == 9729
-    assert ow.n_params(3) == 9921
+    # F -> 64 -> 64 -> 64 -> 1 with biases: F = 28 (2D), 32 (3D)
+    assert ow.n_features(2) == 1 + 3 + 16 + 2 + 6 == 28
+    assert ow.n_features(3) == 1 + 6 + 16 + 3 + 6 == 32
+    assert ow.n_params(2) == 28 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1 == 10241
+    assert ow.n_params(3) == 10497
 
 
 @pytest.mark.parametrize("dim,n", [(2, 300), (3, 200), (2, 5)])
 def test_features_match_brute_force_neighbours(dim, n):
     x, A, v = _instance(dim, n, 3 + dim)
-    f = ow.features(x, A, v, 1.0)
+    f = ow.features(x, A, v)
     s = n / 1.0
     d = np.sqrt(((x[:, None, :] - x[None, :, :]) ** 2).sum(-1))
     np.fill_diagonal(d, np.inf)
@@ -36,19 +37,32 @@ def test_features_match_brute_force_neighbours(dim, n):
     np.testing.assert_allclose(f[:, 0], v * s, rtol=1e-15)
     np.testing.assert_allclose(f[:, c:c + k], np.take_along_axis(d, order[:, :k], 1) * s ** (1 / dim), rtol=1e-12)
     np.testing.assert_allclose(f[:, c + 8:c + 8 + k], v[order[:, :k]] * s, rtol=1e-15)
-    assert np.all(f[:, c + k:c + 8] == 4.0) and np.all(f[:, c + 8 + k:] == 0.0)
+    assert np.all(f[:, c + k:c + 8] == 4.0) and np.all(f[:, c + 8 + k:c + 16] == 0.0)
     # A entries: upper triangle of the symmetric part, row by row
     iu = np.triu_indices(dim)
     np.testing.assert_allclose(f[:, 1:c], A[:, iu[0], iu[1]], rtol=1e-15)
+    # wall distances and ball counts / volume excess from the distance matrix
+    ls = s ** (1 / dim)
+    o = c + 16
+    np.testing.assert_allclose(f[:, o:o + dim], np.minimum(x, 1 - x) * ls, rtol=1e-15)
+    ball = np.pi if dim == 2 else 4 * np.pi / 3
+    for q, r in enumerate((2.0, 4.0, 8.0)):
+        inside = d < r / ls
+        cnt = inside.sum(1).astype(float)
+        V = (inside * v[None, :]).sum(1)
+        e = ball * r ** dim
+        np.testing.assert_allclose(f[:, o + dim + 2 * q], cnt / e, rtol=1e-14)
+        np.testing.assert_allclose(f[:, o + dim + 2 * q + 1], (V * s - cnt) / e, rtol=1e-12, atol=1e-14)
 
 
 def test_features_scale_invariant():
     # x -> c x, v -> c^D v, |O| -> c^D |O| leaves every feature unchanged
     x, A, v = _instance(3, 150, 9)
-    f1 = ow.features(x, A, v, 1.0)
+    f1 = ow.features(x, A, v)
     c = 2.5
-    f2 = ow.features(c * x, A, c ** 3 * v, c ** 3)
-    np.testing.assert_allclose(f1, f2, rtol=1e-12)
+    shift = np.array([-1.0, 3.0, 0.5])
+    f2 = ow.features(c * x + shift, A, c ** 3 * v, shift, shift + c)
+    np.testing.assert_allclose(f1, f2, rtol=1e-12, atol=1e-13)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
