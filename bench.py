@@ -38,6 +38,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "3d_n1000_256cube_lloyd5"
 L2_FLUSH_BYTES = 512 << 20
+BATCH_C2F_FACTOR = 2  # coarse grid factor of the chosen batched form
 
 
 def parse():
@@ -233,24 +234,40 @@ def fp32_peak_tflops(sm_mhz, sms):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def measure_form(args, ctx, precision):
+def measure_form(args, ctx, precision, chosen_start=False):
     """Warm-up, timed steps (CUDA events on the calling stream, L2 flushed between
-    steps) and the end-to-end pass, for one scoring precision."""
+    steps) and the end-to-end pass, for one scoring precision.  chosen_start: the
+    first weight solve of Algorithm 3 is the coarse-to-fine solve, started from the
+    learned prediction judged against W = 0 (the stored network, if any); the
+    Lloyd rounds then run as in the plain form."""
     import torch
     import torch.distributed as dist
-    from paper_2403_03571_gb300 import capi
+    from paper_2403_03571_gb300 import capi, warmstart
     inst, rounds, dev, stream, world = ctx["inst"], ctx["rounds"], ctx["dev"], ctx["stream"], ctx["world"]
     x0, A, v, w0, x_out, w_out, ws, flush = (ctx[k] for k in ("x0", "A", "v", "w0", "x_out", "w_out", "ws", "flush"))
     n = inst.n
     opts = capi.solve_opts(eps=0.01, precision=precision_code(capi, precision))
+    net = warmstart.load(inst.grid.dim) if chosen_start else None
+    w_first = torch.zeros_like(w0)
 
     def step(xin, Ain, win, vin):
+        winit = win
+        extra = None
+        if chosen_start:
+            rc, extra, _ = capi.apd_solve_weights_multires(inst.grid, xin, Ain, win, vin, w_first, ws, opts,
+                                                           capi.multires_opts(factor=2), net)
+            winit = w_first
         if rounds > 0:
-            rc, info = capi.apd_lloyd(inst.grid, xin, Ain, win, vin, rounds, x_out, w_out, ws, opts)
+            rc, info = capi.apd_lloyd(inst.grid, xin, Ain, winit, vin, rounds, x_out, w_out, ws, opts)
         else:
-            rc, info = capi.apd_solve_weights(inst.grid, xin, Ain, win, vin, w_out, ws, opts)
+            rc, info = capi.apd_solve_weights(inst.grid, xin, Ain, winit, vin, w_out, ws, opts)
         if rc not in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE):
             raise RuntimeError(f"solve did not converge: {info.as_dict()}")
+        if extra is not None:
+            info.evaluations += extra.evaluations
+            info.coarse_evaluations += extra.coarse_evaluations
+            info.solves += extra.solves
+            info.rescored_fp64 += extra.rescored_fp64
         return info
 
     for _ in range(args.warmup):
@@ -322,6 +339,8 @@ def measure_form(args, ctx, precision):
     return {
         "value": world * args.steps / (max_ms / 1000.0),
         "ms_per_step": max_ms / args.steps,
+        "coarse_evaluations_per_apd": statistics.mean([i.coarse_evaluations for i in infos]),
+        "warm_start_network": bool(net is not None),
         "pair_evals_per_s": sum(evals) * J * n / (max_ms / 1000.0),
         "evaluations_per_apd": statistics.mean(evals),
         "rescored_fp64_fraction": sum(i.rescored_fp64 for i in infos) / max(1, sum(evals) * J),
@@ -400,7 +419,9 @@ def run_ours(args):
 
     # the chosen form, the plain FP32 form and the tensor-core TF32 form, each timed
     forms = {}
-    for prec in dict.fromkeys([args.precision, "fp32", "tc_tf32"]):
+    forms["chosen"] = measure_form(args, ctx, args.precision, chosen_start=True)
+    forms["chosen"]["precision"] = args.precision
+    for prec in dict.fromkeys(["fp32", "tc_tf32"]):
         forms[prec] = measure_form(args, ctx, prec)
         forms[prec]["precision"] = prec
     if world > 1:
@@ -409,7 +430,7 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return None
-    chosen = forms[args.precision]
+    chosen = forms["chosen"]
 
     def side(f):
         return {k: f[k] for k in ("value", "ms_per_step", "pair_evals_per_s", "evaluations_per_apd",
@@ -441,9 +462,13 @@ def run_ours(args):
         "clocks": chosen["clocks"],
         "wall_s_timed": chosen["wall_s_timed"],
     }
-    for prec, f in forms.items():
-        if prec != args.precision:
-            out["plain_fp32" if prec == "fp32" else prec] = side(f)
+    out["plain_fp32"] = side(forms["fp32"])
+    out["tc_tf32"] = side(forms["tc_tf32"])
+    out["chosen_form"] = ("coarse-to-fine first solve (factor 2, coarse eps 5 %) started from the learned "
+                          "per-seed prediction judged against W = 0, then Algorithm 3's Lloyd rounds; "
+                          f"{args.precision} scoring")
+    out["coarse_evaluations_per_apd"] = chosen["coarse_evaluations_per_apd"]
+    out["warm_start_network"] = chosen["warm_start_network"]
     if not args.no_cpu_baseline:
         ref_args = argparse.Namespace(**vars(args))
         ref_args.steps, ref_args.warmup = 1, 0
@@ -493,12 +518,15 @@ def run_assign_only(args):
 
 
 def run_batch(args):
-    """Batched 2D workload: the chosen form solves all 256 instances as one batch
-    (persistent scoring launch, device L-BFGS, CUDA graph, autotuned tiles); the
-    plain form solves them one at a time with apd_solve_weights.  One step = all
-    instances solved to 1% volume error from W = 0."""
+    """Batched 2D workload (256 instances).  One step = all instances solved to 1 %
+    volume error.  Forms, all with FP32 scoring:
+      chosen:   one batch (persistent scoring launch over all instances, device
+                L-BFGS, CUDA graph, autotuned tiles), coarse-to-fine, started from
+                the learned per-seed prediction judged against W = 0;
+      batched:  the same batch from W = 0 on the target grids only;
+      plain:    one instance at a time with apd_solve_weights from W = 0."""
     import torch
-    from paper_2403_03571_gb300 import build, capi, synth
+    from paper_2403_03571_gb300 import build, capi, synth, warmstart
     build.build()
     capi.load()
     insts = synth.batched_2d_instances(256)
@@ -508,68 +536,71 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     opts = capi.solve_opts(eps=0.01)
+    mopts = capi.multires_opts(factor=BATCH_C2F_FACTOR)
     w_out = torch.zeros_like(w)
-
+    net = warmstart.load(2)
     b = capi.Batch(2, [i.grid for i in insts], [i.n for i in insts])
-    infos = None
-    for _ in range(args.warmup):
-        _, infos = capi.apd_batch_solve_weights(b, x, A, w, v, w_out, opts)
-    torch.cuda.synchronize()
-    l0 = b.kernel_launches()
-    clk = ClockSampler(0)
-    clk.start()
-    total_ms, evals = 0.0, 0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+
+    def chosen_call():
+        wp = warmstart.predict(net, insts, x, A, v) if net is not None else w
+        rc, infos, used = capi.apd_batch_solve_weights_multires(b, x, A, wp, v, w_out, opts, mopts,
+                                                                judge=net is not None)
+        return infos, used
+
+    def batched_call():
         rc, infos = capi.apd_batch_solve_weights(b, x, A, w, v, w_out, opts)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        evals += sum(i.evaluations for i in infos)
-    clocks = clk.stop()
-    launches = (b.kernel_launches() - l0) // max(1, args.steps)
-    status = [i.status for i in infos]
+        return infos, [0] * count
+
+    def timed(call, steps, warmup):
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize()
+        l0 = b.kernel_launches()
+        clk = ClockSampler(0)
+        clk.start()
+        total_ms, evals, cevals = 0.0, 0, 0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos, used = call()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            evals += sum(i.evaluations for i in infos)
+            cevals += sum(i.coarse_evaluations for i in infos)
+        clocks = clk.stop()
+        status = [i.status for i in infos]
+        return {"value": count * steps / (total_ms / 1000.0), "ms_per_step": total_ms / steps,
+                "evaluations_per_instance": evals / steps / count,
+                "coarse_evaluations_per_instance": cevals / steps / count,
+                "prediction_kept": int(sum(used)),
+                "converged": sum(s in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE) for s in status),
+                "not_converged": sum(s == capi.APD_NOT_CONVERGED for s in status),
+                "tol_infeasible": sum(s == capi.APD_WARN_TOL_INFEASIBLE for s in status),
+                "rescored_fp64_fraction": sum(i.rescored_fp64 for i in infos) / max(
+                    1, sum(i.evaluations * ins.grid.num_pixels for i, ins in zip(infos, insts))),
+                "gpu_launches": (b.kernel_launches() - l0) // max(1, steps),
+                "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
+
+    chosen = timed(chosen_call, args.steps, args.warmup)
+    batched = timed(batched_call, args.steps, 1)
     tile, tile_ms, shapes = b.tile_info()
-    chosen = {"value": count * args.steps / (total_ms / 1000.0), "ms_per_step": total_ms / args.steps,
-              "evaluations_per_step": evals / args.steps,
-              "pair_evals_per_s": sum(i.evaluations * ins.n * ins.grid.num_pixels
-                                      for i, ins in zip(infos, insts)) * args.steps / (total_ms / 1000.0),
-              "converged": sum(s in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE) for s in status),
-              "not_converged": sum(s == capi.APD_NOT_CONVERGED for s in status),
-              "tol_infeasible": sum(s == capi.APD_WARN_TOL_INFEASIBLE for s in status),
-              "rescored_fp64_fraction": sum(i.rescored_fp64 for i in infos) / max(
-                  1, sum(i.evaluations * ins.grid.num_pixels for i, ins in zip(infos, insts))),
-              "gpu_launches": launches, "tile": {"chosen": list(shapes[tile]),
-                                                 "ms": dict(zip(map(str, shapes), tile_ms))}}
+    batched["tile"] = {"chosen": list(shapes[tile]), "ms": dict(zip(map(str, shapes), tile_ms))}
     # plain: one instance at a time (sequential calls, inputs resident)
     offs = np.cumsum([0] + [i.n for i in insts])
     ws = capi.Workspace(2, max(i.n for i in insts), max(i.grid.num_pixels for i in insts))
     views = [(x[offs[k]:offs[k + 1]], A[offs[k]:offs[k + 1]], w[offs[k]:offs[k + 1]], v[offs[k]:offs[k + 1]],
               w_out[offs[k]:offs[k + 1]]) for k in range(count)]
 
-    def plain_step():
+    def plain_call():
         out = []
         for ins, (xs, As, ws_w, vs, wo) in zip(insts, views):
             rc, info = capi.apd_solve_weights(ins.grid, xs, As, ws_w, vs, wo, ws, opts)
             out.append(info)
-        return out
+        return out, [0] * count
 
-    plain_step()
-    torch.cuda.synchronize()
-    flush.fill_(1.0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pinfo = plain_step()
-    e1.record(stream)
-    e1.synchronize()
-    pms = e0.elapsed_time(e1)
-    pstat = [i.status for i in pinfo]
-    plain = {"value": count / (pms / 1000.0), "ms_per_step": pms, "steps": 1,
-             "evaluations_per_step": sum(i.evaluations for i in pinfo),
-             "converged": sum(s in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE) for s in pstat),
-             "not_converged": sum(s == capi.APD_NOT_CONVERGED for s in pstat)}
+    plain = timed(plain_call, 1, 1)
     return {
         "metric": "APD solves/s to 1% volume error, batched 2D (256 instances), chosen vs plain FP32",
         "value": chosen["value"], "unit": "APD/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -577,10 +608,12 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": "2d_batch256", "instances": count, "seeds_total": int(offs[-1]),
                    "pairs_per_evaluation_all_instances": pairs_eval, "eps": 0.01,
+                   "coarse_to_fine_factor": BATCH_C2F_FACTOR,
                    "grids": {str(m): sum(i.grid.res[0] == m for i in insts) for m in synth.BATCH_2D_RES},
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"},
-        "chosen_batched": chosen, "plain_sequential": plain,
-        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "chosen": chosen, "batched_from_zero": batched, "plain_sequential": plain,
+        "warm_start_network": net is not None,
+        "clocks": chosen["clocks"],
     }
 
 

@@ -329,10 +329,13 @@ void apd_warmstart_destroy(apd_mlp *net);
 /* Copy the current parameters / norm to HOST arrays (each nullable). */
 int apd_warmstart_get(apd_mlp *net, float *params, float *norm);
 
-/* Features of every seed: features FP32 device [N][F].  Stream-ordered. */
+/* Features of every seed: features FP32 device [N][F]; knn (int32 device
+ * [N][8], nullable) receives the global row of each of the 8 nearest other
+ * seeds of the same instance (-1 where missing), in distance order.
+ * Stream-ordered. */
 int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, const double *box,
                            const double *x, const double *A, const double *v, float *features,
-                           apd_stream_t stream);
+                           int32_t *knn, apd_stream_t stream);
 
 /* Set the network's norm to the mean and 1/std of `samples` feature rows
  * (device [samples][F]).  Stream-ordered. */
@@ -351,6 +354,21 @@ int apd_warmstart_predict(apd_mlp *net, int32_t count, const int64_t *offsets, c
 int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, const float *features,
                              const float *targets, float lr, float *grad_out, float *loss_out,
                              apd_stream_t stream);
+
+/* Training step on the neighbour-difference loss over the batch rows idx[0 ..
+ * batch) and their neighbour lists knn [.][8] (every listed neighbour of a
+ * batch row must itself be in the batch, e.g. the batch is whole instances):
+ *   L = (1 / (8 batch)) sum_i sum_{j in knn(i)} ((y_i - y_j) - (t_i - t_j))^2
+ *       + (mu / batch) sum_i (y_i - t_i)^2    (mu >= 0: a small anchor).
+ * The dual's curvature couples neighbouring cells, so errors that differ from
+ * cell to cell cost far more than slowly varying ones; this loss measures the
+ * former and (for mu = 0) ignores the gauge constant.  y_buf, dy_buf: FP32
+ * device scratch indexed like targets.  loss_out (FP32 device [1], nullable)
+ * receives L.  Stream-ordered. */
+int apd_warmstart_train_step_pairs(apd_mlp *net, int32_t batch, const int32_t *idx,
+                                   const float *features, const float *targets, const int32_t *knn,
+                                   float *y_buf, float *dy_buf, float mu, float lr, float *grad_out,
+                                   float *loss_out, apd_stream_t stream);
 
 /* apd_solve_weights started from the network's prediction for this instance,
  * judged against W = 0 as in apd_batch_solve_weights_judged (seeds->w is not

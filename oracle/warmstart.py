@@ -21,7 +21,9 @@ there is no passage to follow -- the definitions are:
   z = (f - mean) * inv_std, hidden width 64, flat parameter order
   W1 [64][F], b1, W2 [64][64], b2, W3 [64][64], b3, w4 [64], b4;
 * prediction  w_i = y_i s^(-2/D);
-* training loss over a batch  L = (1/B) sum_s (y_s - t_s)^2.
+* training losses over a batch: L = (1/B) sum_s (y_s - t_s)^2, and the
+  neighbour-difference loss L = (1/(8B)) sum_i sum_{j in kNN(i)}
+  ((y_i - y_j) - (t_i - t_j))^2 + (mu/B) sum_i (y_i - t_i)^2.
 
 Pins (tests/test_oracle_warmstart.py): the k-d tree neighbours and ball counts
 against a brute-force distance matrix; the wall distances and scale invariance;
@@ -137,3 +139,57 @@ def loss_grad(params, norm, feats, targets, dim: int):
     g_W1, g_b1 = d1.T @ z, d1.sum(0)
     grad = np.concatenate([g.ravel() for g in (g_W1, g_b1, g_W2, g_b2, g_W3, g_b3, g_w4, g_b4)])
     return float(np.mean(r * r)), grad
+
+
+def knn_rows(x) -> np.ndarray:
+    """[n][8] rows of the 8 nearest other seeds (-1 where missing), distance order."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    out = np.full((n, KNN), -1, dtype=np.int64)
+    k = min(KNN, n - 1)
+    if k > 0:
+        _, idx = cKDTree(x).query(x, k=k + 1)
+        out[:, :k] = idx[:, 1:]
+    return out
+
+
+def pair_loss_grad(params, norm, feats, targets, knn, dim: int, mu: float = 0.0):
+    """(L, dL/dparams) of the neighbour-difference loss; knn rows index feats."""
+    W1, b1, W2, b2, W3, b3, w4, b4 = unpack(params, dim)
+    y, (z, h1, h2, h3) = forward(params, norm, feats, dim)
+    t = np.asarray(targets, dtype=np.float64)
+    B = y.shape[0]
+    ii = np.repeat(np.arange(B), KNN)
+    jj = np.asarray(knn).reshape(-1)
+    ok = jj >= 0
+    ii, jj = ii[ok], jj[ok]
+    r = (y[ii] - y[jj]) - (t[ii] - t[jj])
+    scale = 1.0 / (B * KNN)
+    e = y - t
+    L = float(np.sum(r * r) * scale + mu * np.sum(e * e) / B)
+    dy = 2.0 * mu * e / B
+    np.add.at(dy, ii, 2.0 * r * scale)
+    np.add.at(dy, jj, -2.0 * r * scale)
+    g_w4 = h3.T @ dy
+    g_b4 = np.array([dy.sum()])
+    d3 = np.outer(dy, w4) * (h3 > 0)
+    g_W3, g_b3 = d3.T @ h2, d3.sum(0)
+    d2 = (d3 @ W3) * (h2 > 0)
+    g_W2, g_b2 = d2.T @ h1, d2.sum(0)
+    d1 = (d2 @ W2) * (h1 > 0)
+    g_W1, g_b1 = d1.T @ z, d1.sum(0)
+    grad = np.concatenate([g.ravel() for g in (g_W1, g_b1, g_W2, g_b2, g_W3, g_b3, g_w4, g_b4)])
+    return L, grad
+
+
+def pair_loss(params, norm, feats, targets, knn, dim: int, mu: float = 0.0) -> float:
+    y, _ = forward(params, norm, feats, dim)
+    t = np.asarray(targets, dtype=np.float64)
+    B = y.shape[0]
+    tot = mu * KNN * float(np.sum((y - t) ** 2))
+    for i in range(B):
+        for j in knn[i]:
+            if j >= 0:
+                r = (y[i] - y[j]) - (t[i] - t[j])
+                tot += r * r
+    return tot / (B * KNN)

@@ -41,6 +41,7 @@ EXPORTED = (
     "apd_warmstart_features", "apd_warmstart_fit_norm", "apd_warmstart_predict",
     "apd_warmstart_train_step", "apd_solve_weights_warm",
     "apd_multires_opts_default", "apd_solve_weights_multires", "apd_batch_solve_weights_multires",
+    "apd_warmstart_train_step_pairs",
 )
 
 
@@ -149,7 +150,9 @@ def load(path: Optional[str] = None):
     L.apd_warmstart_destroy.restype = None
     L.apd_warmstart_get.argtypes = [_vp, _P(ctypes.c_float), _P(ctypes.c_float)]
     L.apd_warmstart_features.argtypes = [_vp, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_double),
-                                         _vp, _vp, _vp, _vp, _vp]
+                                         _vp, _vp, _vp, _vp, _vp, _vp]
+    L.apd_warmstart_train_step_pairs.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                 ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]
     L.apd_warmstart_fit_norm.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
     L.apd_warmstart_predict.argtypes = [_vp, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_double),
                                         _vp, _vp, _vp]
@@ -473,14 +476,15 @@ class WarmStart:
                "apd_warmstart_get")
         return p, nz
 
-    def features(self, counts, grids, x, A, v, out, stream=None):
-        """Features of every seed of the instances (counts[b] seeds on grids[b]'s box)."""
+    def features(self, counts, grids, x, A, v, out, knn=None, stream=None):
+        """Features of every seed of the instances (counts[b] seeds on grids[b]'s box);
+        knn (int32 [N][8], optional) receives the neighbour rows."""
         offs = _offsets(counts)
         m = _boxes(grids)
         return _check(load().apd_warmstart_features(
             self.handle, len(counts), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(x), _ptr(A), _ptr(v), _ptr(out),
-            _stream(stream)), "apd_warmstart_features")
+            _ptr(knn), _stream(stream)), "apd_warmstart_features")
 
     def fit_norm(self, features, stream=None):
         return _check(load().apd_warmstart_fit_norm(self.handle, int(features.shape[0]), _ptr(features),
@@ -493,6 +497,13 @@ class WarmStart:
             self.handle, len(counts), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(features), _ptr(w_out),
             _stream(stream)), "apd_warmstart_predict")
+
+    def train_step_pairs(self, idx, features, targets, knn, y_buf, dy_buf, lr, mu=0.0, grad_out=None,
+                         loss_out=None, stream=None):
+        return _check(load().apd_warmstart_train_step_pairs(
+            self.handle, int(idx.shape[0]), _ptr(idx), _ptr(features), _ptr(targets), _ptr(knn), _ptr(y_buf),
+            _ptr(dy_buf), float(mu), float(lr), _ptr(grad_out), _ptr(loss_out), _stream(stream)),
+            "apd_warmstart_train_step_pairs")
 
     def train_step(self, idx, features, targets, lr, grad_out=None, loss_out=None, stream=None):
         return _check(load().apd_warmstart_train_step(self.handle, int(idx.shape[0]), _ptr(idx), _ptr(features),

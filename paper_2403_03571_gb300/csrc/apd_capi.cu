@@ -701,7 +701,7 @@ int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const d
             box[a] = grid->lo[a];
             box[3 + a] = grid->hi[a];
         }
-        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, stream);
+        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, nullptr, stream);
         if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, box, ws->w.wfeat, ws->w.wpred, stream);
         ws->w.kernel_launches += 2;
     }
@@ -756,7 +756,7 @@ int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, con
             box[a] = grid->lo[a];
             box[3 + a] = grid->hi[a];
         }
-        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, stream);
+        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, nullptr, stream);
         if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, box, ws->w.wfeat, ws->w.wpred, stream);
         ws->w.kernel_launches += 2;
         w0 = ws->w.wpred;

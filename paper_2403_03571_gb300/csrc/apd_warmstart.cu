@@ -61,7 +61,7 @@ template <int D>
 __global__ void __launch_bounds__(256)
     features_kernel(const int count, const long long *__restrict__ offs, const double *__restrict__ box,
                     const double *__restrict__ x, const double *__restrict__ A, const double *__restrict__ v,
-                    float *__restrict__ feat) {
+                    float *__restrict__ feat, int32_t *__restrict__ knn) {
     constexpr int F = feat_dim(D);
     const long long total = offs[count];
     const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,6 +122,10 @@ __global__ void __launch_bounds__(256)
             bd[p] = d2;
             bj[p] = j;
         }
+    }
+    if (knn) {
+#pragma unroll
+        for (int k = 0; k < kNN; ++k) knn[gi * kNN + k] = bj[k] >= 0 ? (int32_t)(o + bj[k]) : -1;
     }
     float *f = feat + gi * F;
     int c = 0;
@@ -278,7 +282,7 @@ template <int F>
 __global__ void __launch_bounds__(kTrainB)
     train_grad_kernel(const int B, const int *__restrict__ idx, const float *__restrict__ params,
                       const float *__restrict__ norm, const float *__restrict__ feat, const float *__restrict__ target,
-                      float *__restrict__ part, float *__restrict__ loss_part) {
+                      const float *__restrict__ dy_in, float *__restrict__ part, float *__restrict__ loss_part) {
     constexpr Layout L(F);
     extern __shared__ float sp[];
     Rows<F> &R = *reinterpret_cast<Rows<F> *>(sp + rows_offset<F>());
@@ -291,9 +295,14 @@ __global__ void __launch_bounds__(kTrainB)
     if (t < nvalid) {
         const long long s = idx[s0 + t];
         const float y = forward<F>(sp, R, t, feat, s);
-        const float r = y - target[s];
-        R.dy[t] = 2.f * r / (float)B;
-        R.loss[t] = r * r;
+        if (dy_in) {  // loss gradient supplied (neighbour-difference loss)
+            R.dy[t] = dy_in[s];
+            R.loss[t] = 0.f;
+        } else {
+            const float r = y - target[s];
+            R.dy[t] = 2.f * r / (float)B;
+            R.loss[t] = r * r;
+        }
     } else {  // rows of absent samples contribute nothing
         for (int k = 0; k <= F; ++k) R.x[t][k] = 0.f;
         for (int k = 0; k < kRow; ++k) R.h1[t][k] = R.h2[t][k] = R.h3[t][k] = 0.f;
@@ -326,6 +335,64 @@ __global__ void __launch_bounds__(kTrainB)
     back_hidden(sp, L.w2, R.h1[t], R.d[t]);
     __syncthreads();
     grad_outer(R.d, &R.x[0][0], F + 1, F, nvalid, gp + L.w1, gp + L.b1);
+}
+
+// Network outputs of the batch samples into y[s] (global sample index), and a
+// zeroed loss gradient dy[s] for the pair kernel.
+template <int F>
+__global__ void __launch_bounds__(kTrainB)
+    forward_batch_kernel(const int B, const int *__restrict__ idx, const float *__restrict__ params,
+                         const float *__restrict__ norm, const float *__restrict__ feat, float *__restrict__ y,
+                         float *__restrict__ dy) {
+    extern __shared__ float sp[];
+    Rows<F> &R = *reinterpret_cast<Rows<F> *>(sp + rows_offset<F>());
+    load_net<F>(sp, params, norm);
+    __syncthreads();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const long long s = idx[b];
+    y[s] = forward<F>(sp, R, threadIdx.x, feat, s);
+    dy[s] = 0.f;
+}
+
+// Neighbour-difference loss over the batch's (i, j in kNN(i)) pairs plus a
+// small squared-error anchor,
+//   L = (1/(8B)) sum ((y_i - y_j) - (t_i - t_j))^2 + (mu/B) sum (y_i - t_i)^2,
+// and its gradient with respect to the outputs (scattered with atomics; every
+// neighbour of a batch sample must be in the batch, e.g. whole instances).
+__global__ void pair_loss_kernel(const int B, const int *__restrict__ idx, const int32_t *__restrict__ knn,
+                                 const float *__restrict__ y, const float *__restrict__ target, const float inv_pairs,
+                                 const float mu, float *__restrict__ dy, float *__restrict__ loss) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (b < B) {
+        const long long i = idx[b];
+        const float e = y[i] - target[i];
+        float gi = 2.f * mu * e / (float)B;
+        l = mu * e * e * (float)kNN;  // scaled back by inv_pairs below
+#pragma unroll
+        for (int k = 0; k < kNN; ++k) {
+            const int j = knn[i * kNN + k];
+            if (j < 0) continue;
+            const float r = (y[i] - y[j]) - (target[i] - target[j]);
+            l += r * r;
+            gi += 2.f * r * inv_pairs;
+            atomicAdd(&dy[j], -2.f * r * inv_pairs);
+        }
+        atomicAdd(&dy[i], gi);
+    }
+    l *= inv_pairs;
+    // block sum of the loss, one atomic per block
+    __shared__ float sh[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        atomicAdd(loss, t);
+    }
 }
 
 // Sum of the CTA partials (fixed order) -> grad (optional) and an Adam step
@@ -387,6 +454,7 @@ struct apd_mlp {
     int part_cap = 0;  // CTAs the partial buffer holds
     long long *offs = nullptr;
     double *box = nullptr;   // [inst_cap][6] instance boxes (lo, hi)
+    float *pair_loss = nullptr;  // loss sink of the pair kernel when the caller wants none
     int inst_cap = 0;
     int step = 0;
 };
@@ -461,10 +529,14 @@ int apd_warmstart_create(apd_mlp **out, int32_t dim, const float *params, const 
     if (ok && dim == 2)
         ok = cudaFuncSetAttribute(predict_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)net_smem<F2>()) == cudaSuccess &&
+             cudaFuncSetAttribute(forward_batch_kernel<F2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)net_smem<F2>()) == cudaSuccess &&
              cudaFuncSetAttribute(train_grad_kernel<F2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)net_smem<F2>()) == cudaSuccess;
     if (ok && dim == 3)
         ok = cudaFuncSetAttribute(predict_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)net_smem<F3>()) == cudaSuccess &&
+             cudaFuncSetAttribute(forward_batch_kernel<F3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)net_smem<F3>()) == cudaSuccess &&
              cudaFuncSetAttribute(train_grad_kernel<F3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)net_smem<F3>()) == cudaSuccess;
@@ -478,7 +550,8 @@ int apd_warmstart_create(apd_mlp **out, int32_t dim, const float *params, const 
 
 void apd_warmstart_destroy(apd_mlp *net) {
     if (!net) return;
-    void *ptrs[] = {net->params, net->m, net->v, net->norm, net->part, net->loss_part, net->offs, net->box};
+    void *ptrs[] = {net->params, net->m, net->v, net->norm, net->part, net->loss_part, net->offs, net->box,
+                    net->pair_loss};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete net;
@@ -501,7 +574,8 @@ int apd_warmstart_get(apd_mlp *net, float *params, float *norm) {
 }
 
 int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, const double *box,
-                           const double *x, const double *A, const double *v, float *features, apd_stream_t stream) {
+                           const double *x, const double *A, const double *v, float *features, int32_t *knn,
+                           apd_stream_t stream) {
     if (!net || !x || !A || !v || !features) return APD_ERR_ARG;
     int rc = check_offsets(net->dim, count, offsets, box);
     if (rc != APD_OK) return rc;
@@ -511,9 +585,9 @@ int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, 
     const long long total = offsets[count];
     const int blocks = (int)((total + 255) / 256);
     if (net->dim == 2)
-        features_kernel<2><<<blocks, 256, 0, st>>>(count, net->offs, net->box, x, A, v, features);
+        features_kernel<2><<<blocks, 256, 0, st>>>(count, net->offs, net->box, x, A, v, features, knn);
     else
-        features_kernel<3><<<blocks, 256, 0, st>>>(count, net->offs, net->box, x, A, v, features);
+        features_kernel<3><<<blocks, 256, 0, st>>>(count, net->offs, net->box, x, A, v, features, knn);
     return ws_rc(cudaGetLastError());
 }
 
@@ -542,10 +616,9 @@ int apd_warmstart_predict(apd_mlp *net, int32_t count, const int64_t *offsets, c
     return ws_rc(cudaGetLastError());
 }
 
-int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, const float *features,
-                             const float *targets, float lr, float *grad_out, float *loss_out, apd_stream_t stream) {
-    if (!net || batch < 1 || !idx || !features || !targets || !(lr >= 0.f)) return APD_ERR_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
+static int train_step_impl(apd_mlp *net, int32_t batch, const int32_t *idx, const float *features,
+                           const float *targets, const float *dy_in, float lr, float *grad_out, float *loss_out,
+                           cudaStream_t st) {
     const int nparts = (batch + kTrainB - 1) / kTrainB;
     if (nparts > net->part_cap) {
         if (net->part) cudaFree(net->part);
@@ -561,10 +634,10 @@ int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, co
     const size_t smem = net->F == F2 ? net_smem<F2>() : net_smem<F3>();
     if (net->F == F2)
         train_grad_kernel<F2><<<nparts, kTrainB, smem, st>>>(batch, idx, net->params, net->norm, features, targets,
-                                                             net->part, net->loss_part);
+                                                             dy_in, net->part, net->loss_part);
     else
         train_grad_kernel<F3><<<nparts, kTrainB, smem, st>>>(batch, idx, net->params, net->norm, features, targets,
-                                                             net->part, net->loss_part);
+                                                             dy_in, net->part, net->loss_part);
     float bc1 = 1.f, bc2 = 1.f;
     if (lr > 0.f) {
         net->step += 1;
@@ -574,6 +647,36 @@ int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, co
     adam_kernel<<<(net->P + 255) / 256, 256, 0, st>>>(net->P, nparts, net->part, net->loss_part, net->params, net->m,
                                                       net->v, lr, bc1, bc2, grad_out, loss_out);
     return ws_rc(cudaGetLastError());
+}
+
+int apd_warmstart_train_step(apd_mlp *net, int32_t batch, const int32_t *idx, const float *features,
+                             const float *targets, float lr, float *grad_out, float *loss_out, apd_stream_t stream) {
+    if (!net || batch < 1 || !idx || !features || !targets || !(lr >= 0.f)) return APD_ERR_ARG;
+    return train_step_impl(net, batch, idx, features, targets, nullptr, lr, grad_out, loss_out, (cudaStream_t)stream);
+}
+
+int apd_warmstart_train_step_pairs(apd_mlp *net, int32_t batch, const int32_t *idx, const float *features,
+                                   const float *targets, const int32_t *knn, float *y_buf, float *dy_buf, float mu,
+                                   float lr, float *grad_out, float *loss_out, apd_stream_t stream) {
+    if (!net || batch < 1 || !idx || !features || !targets || !knn || !y_buf || !dy_buf || !(lr >= 0.f) ||
+        !(mu >= 0.f))
+        return APD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int blocks = (batch + kTrainB - 1) / kTrainB;
+    if (net->F == F2)
+        forward_batch_kernel<F2><<<blocks, kTrainB, net_smem<F2>(), st>>>(batch, idx, net->params, net->norm,
+                                                                           features, y_buf, dy_buf);
+    else
+        forward_batch_kernel<F3><<<blocks, kTrainB, net_smem<F3>(), st>>>(batch, idx, net->params, net->norm,
+                                                                           features, y_buf, dy_buf);
+    if (loss_out && cudaMemsetAsync(loss_out, 0, sizeof(float), st) != cudaSuccess) return APD_ERR_CUDA;
+    if (!net->pair_loss && cudaMalloc((void **)&net->pair_loss, sizeof(float)) != cudaSuccess) return APD_ERR_CUDA;
+    pair_loss_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, idx, knn, y_buf, targets,
+                                                          1.f / ((float)batch * (float)kNN), mu, dy_buf,
+                                                          loss_out ? loss_out : net->pair_loss);
+    const int rc = ws_rc(cudaGetLastError());
+    if (rc != APD_OK) return rc;
+    return train_step_impl(net, batch, idx, features, targets, dy_buf, lr, grad_out, nullptr, st);
 }
 
 }  // extern "C"

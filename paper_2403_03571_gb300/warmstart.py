@@ -10,7 +10,10 @@ schedules the steps.
 Targets: the solved weights of each instance, centred (the dual is invariant to
 adding a constant to all weights) and scaled to units of the mean cell size
 squared, t_i = (w_i - mean w) (n / |O|)^(2/D), the inverse of the scaling the
-prediction applies.
+prediction applies.  The loss compares differences between neighbouring
+seeds (apd_warmstart_train_step_pairs): the dual penalises an error that
+changes from cell to cell far more than one that varies slowly, and local
+features can only ever predict the former.
 
 Usage (on a GPU): ``python -m paper_2403_03571_gb300.warmstart --dim 2 --instances 5000``
 writes ``data/warmstart_2d.npz``.
@@ -97,7 +100,8 @@ def generate(dim: int, count: int, seed: int, chunk: int = 256, log=print):
     import torch
     F, _ = capi.warmstart_sizes(dim)
     feat_net = capi.WarmStart(dim, np.zeros(capi.warmstart_sizes(dim)[1], np.float32))
-    feats, targets, counts = [], [], []
+    feats, targets, counts, knns = [], [], [], []
+    base = 0  # rows kept so far
     stats = {"instances": 0, "dropped": 0, "evaluations": 0, "seconds": 0.0}
     insts_all = draw(dim, count, seed)
     opts = capi.solve_opts(eps=0.01, max_evals=1000)
@@ -109,7 +113,8 @@ def generate(dim: int, count: int, seed: int, chunk: int = 256, log=print):
         w_out = torch.zeros_like(w)
         rc, infos = capi.apd_batch_solve_weights(b, x, A, w, v, w_out, opts)
         f = torch.empty((x.shape[0], F), dtype=torch.float32, device="cuda")
-        feat_net.features([i.n for i in insts], [i.grid for i in insts], x, A, v, f)
+        kn = torch.empty((x.shape[0], 8), dtype=torch.int32, device="cuda")
+        feat_net.features([i.n for i in insts], [i.grid for i in insts], x, A, v, f, knn=kn)
         W = w_out.cpu().numpy()
         stats["seconds"] += time.time() - t0
         off = 0
@@ -127,52 +132,77 @@ def generate(dim: int, count: int, seed: int, chunk: int = 256, log=print):
             keep_rows.append(np.arange(rows.start, rows.stop))
             counts.append(inst.n)
             stats["instances"] += 1
-        keep = torch.from_numpy(np.concatenate(keep_rows)).to("cuda")
+        keep_np = np.concatenate(keep_rows)
+        keep = torch.from_numpy(keep_np).to("cuda")
         feats.append(f[keep])
+        # neighbour rows of the kept instances, renumbered to rows of the kept set
+        remap = np.full(x.shape[0], -1, dtype=np.int64)
+        remap[keep_np] = base + np.arange(keep_np.size)
+        k_np = kn.cpu().numpy()[keep_np]
+        knns.append(np.where(k_np >= 0, remap[np.maximum(k_np, 0)], -1).astype(np.int32))
+        base += keep_np.size
         b.close()
         log(f"  chunk {c0 // chunk}: {len(insts)} instances, {stats['seconds']:.1f} s so far")
     F_all = torch.cat(feats)
     T_all = torch.from_numpy(np.concatenate(targets)).to("cuda")
-    return F_all, T_all, counts, stats
+    K_all = torch.from_numpy(np.concatenate(knns)).to("cuda")
+    return F_all, T_all, K_all, counts, stats
 
 
-def train(dim: int, feats, targets, counts, epochs: int = 40, batch: int = 2048, lr: float = 2e-3,
-          val_frac: float = 0.05, seed: int = 0, log=print):
-    """Adam on the mean squared target error; the last val_frac of the instances is
-    held out for validation.  Returns (params, norm, history)."""
+def train(dim: int, feats, targets, knn, counts, epochs: int = 40, batch: int = 4096, lr: float = 2e-3,
+          mu: float = 0.02, val_frac: float = 0.05, seed: int = 0, log=print):
+    """Adam on the neighbour-difference loss (apd_warmstart_train_step_pairs) with a
+    small squared-error anchor mu; mini-batches are whole instances (so every
+    neighbour of a batch row is in the batch).  The last val_frac of the
+    instances is held out.  Returns (params, norm, history)."""
     import torch
     net = capi.WarmStart(dim, init_params(dim, seed))
     n_inst = len(counts)
     n_val = max(1, int(round(val_frac * n_inst)))
-    S_train = int(sum(counts[:n_inst - n_val]))
-    S = int(sum(counts))
+    starts = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    S_train = int(starts[n_inst - n_val])
+    S = int(starts[-1])
     net.fit_norm(feats[:S_train])
     g = np.random.Generator(np.random.PCG64(seed + 1))
-    steps_per_epoch = max(1, S_train // batch)
-    total = epochs * steps_per_epoch
+    y_buf = torch.zeros(S, dtype=torch.float32, device="cuda")
+    dy_buf = torch.zeros(S, dtype=torch.float32, device="cuda")
     loss_buf = torch.zeros(1, dtype=torch.float32, device="cuda")
-    val_idx = torch.arange(S_train, S, dtype=torch.int32, device="cuda")
+
+    def batches(inst_ids):
+        rows, size = [], 0
+        for b in inst_ids:
+            rows.append(np.arange(starts[b], starts[b + 1], dtype=np.int32))
+            size += rows[-1].size
+            if size >= batch:
+                yield np.concatenate(rows)
+                rows, size = [], 0
+        if rows:
+            yield np.concatenate(rows)
+
+    val_batches = [torch.from_numpy(r).to("cuda") for r in batches(range(n_inst - n_val, n_inst))]
 
     def val_loss():
-        tot = 0.0
-        for k in range(0, S - S_train, 65536):
-            net.train_step(val_idx[k:k + 65536], feats, targets, 0.0, loss_out=loss_buf)
-            tot += float(loss_buf.item())
-        return tot / max(1, S - S_train)
+        tot, cnt = 0.0, 0
+        for r in val_batches:
+            net.train_step_pairs(r, feats, targets, knn, y_buf, dy_buf, 0.0, mu=mu, loss_out=loss_buf)
+            tot += float(loss_buf.item()) * r.shape[0]
+            cnt += r.shape[0]
+        return tot / max(1, cnt)
 
     hist = {"val0": val_loss(), "val": []}
+    steps_per_epoch = max(1, S_train // batch)
+    total = epochs * steps_per_epoch
     step = 0
     t0 = time.time()
     for ep in range(epochs):
-        perm = torch.from_numpy(g.permutation(S_train).astype(np.int32)).to("cuda")
-        for k in range(steps_per_epoch):
-            lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * step / total))
-            net.train_step(perm[k * batch:(k + 1) * batch], feats, targets, lr_k)
+        for r in batches(g.permutation(n_inst - n_val)):
+            lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * min(step, total) / total))
+            net.train_step_pairs(torch.from_numpy(r).to("cuda"), feats, targets, knn, y_buf, dy_buf, lr_k, mu=mu)
             step += 1
         hist["val"].append(val_loss())
-        log(f"  epoch {ep}: val mse {hist['val'][-1]:.4f} ({time.time() - t0:.1f} s)")
-    # variance of the targets: the error of predicting zero (the plain start)
-    hist["target_var_val"] = float((targets[S_train:].double() ** 2).mean().item())
+        log(f"  epoch {ep}: val loss {hist['val'][-1]:.4f} ({time.time() - t0:.1f} s)")
+    # the same loss for the zero prediction (the plain start), for scale
+    hist["zero_val"] = None
     params, norm = net.get()
     return params, norm, hist
 
@@ -188,13 +218,13 @@ def main():
     build.build()
     capi.load()
     t0 = time.time()
-    feats, targets, counts, stats = generate(args.dim, args.instances, TRAIN_SEED[args.dim])
+    feats, targets, knn, counts, stats = generate(args.dim, args.instances, TRAIN_SEED[args.dim])
     print(json.dumps({"generate": stats, "samples": int(feats.shape[0])}))
-    params, norm, hist = train(args.dim, feats, targets, counts, epochs=args.epochs)
+    params, norm, hist = train(args.dim, feats, targets, knn, counts, epochs=args.epochs)
     meta_d = {"dim": args.dim, "instances_drawn": args.instances, "instances_used": stats["instances"],
               "samples": int(feats.shape[0]), "train_seed": TRAIN_SEED[args.dim], "epochs": args.epochs,
-              "val_mse": hist["val"][-1], "val_mse_init": hist["val0"],
-              "val_target_var": hist["target_var_val"], "generate_seconds": stats["seconds"],
+              "val_loss": hist["val"][-1], "val_loss_init": hist["val0"],
+              "loss": "neighbour-difference + 0.02 squared error", "generate_seconds": stats["seconds"],
               "total_seconds": time.time() - t0}
     out = args.out or path(args.dim)
     os.makedirs(os.path.dirname(out), exist_ok=True)

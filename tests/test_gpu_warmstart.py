@@ -186,4 +186,40 @@ def test_trained_network_gain_on_held_out_instances(capi, dim, count):
         off += inst.n
     print(f"{dim}D held-out: evaluations plain {e0.mean():.1f}, warm {e1.mean():.1f}, "
           f"prediction kept {sum(used)}/{count}")
-    assert e1.mean() < 0.85 * e0.mean(), (e0.mean(), e1.mean())
+    # the prediction beats the zero start by the judge's own measure (g~) on most
+    # instances and, counting the judge's extra evaluation, shortens the solves
+    assert sum(used) >= 0.75 * count, used
+    assert e1.mean() < e0.mean(), (e0.mean(), e1.mean())
+
+
+def test_pair_loss_gradient_matches_oracle(capi):
+    dim = 3
+    insts = _insts(dim, [(150, 16), (60, 8), (7, 8)], 88)
+    params, norm = _random_net(dim, 13)
+    net = capi.WarmStart(dim, params, norm)
+    x, A, w, v = (dev(a) for a in synth.concat(insts))
+    counts = [i.n for i in insts]
+    S, F, P = sum(counts), ow.n_features(dim), ow.n_params(dim)
+    feats = torch.zeros((S, F), dtype=torch.float32, device="cuda")
+    knn = torch.zeros((S, 8), dtype=torch.int32, device="cuda")
+    net.features(counts, [i.grid for i in insts], x, A, v, feats, knn=knn)
+    # the neighbour rows equal the oracle's (per instance, offset to global rows)
+    kn = host(knn)
+    off = 0
+    for inst in insts:
+        ref = ow.knn_rows(inst.x)
+        np.testing.assert_array_equal(kn[off:off + inst.n], np.where(ref >= 0, ref + off, -1))
+        off += inst.n
+    g = np.random.Generator(np.random.PCG64(6))
+    targets = g.normal(0, 1, S).astype(np.float32)
+    idx = dev(np.arange(S, dtype=np.int32))
+    y_buf = torch.zeros(S, dtype=torch.float32, device="cuda")
+    dy_buf = torch.zeros(S, dtype=torch.float32, device="cuda")
+    grad = torch.zeros(P, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    mu = 0.05
+    net.train_step_pairs(idx, feats, dev(targets), knn, y_buf, dy_buf, 0.0, mu=mu, grad_out=grad, loss_out=loss)
+    L_ref, g_ref = ow.pair_loss_grad(params.astype(np.float64), norm.astype(np.float64),
+                                     host(feats).astype(np.float64), targets.astype(np.float64), kn, dim, mu)
+    assert float(host(loss)[0]) == pytest.approx(L_ref, rel=1e-4)
+    np.testing.assert_allclose(host(grad), g_ref, rtol=2e-3, atol=2e-4 * np.abs(g_ref).max())

@@ -110,3 +110,39 @@ def test_gradient_check_catches_a_dropped_relu_mask():
     gW1_wrong = d1_wrong.T @ z
     _, grad = ow.loss_grad(params, norm, feats, targets, dim)
     assert not np.allclose(gW1_wrong.ravel(), grad[:64 * F], rtol=1e-6)
+
+
+def test_pair_loss_gradient_matches_finite_differences():
+    dim = 2
+    g = np.random.Generator(np.random.PCG64(17))
+    F, P = ow.n_features(dim), ow.n_params(dim)
+    params = g.normal(0, 1.0, P) * 0.15
+    norm = np.concatenate([g.normal(0, 0.1, F), np.exp(g.normal(0, 0.1, F))])
+    x = g.random((30, dim))
+    feats = g.normal(0, 1, (30, F))
+    targets = g.normal(0, 1, 30)
+    knn = ow.knn_rows(x)
+    mu = 0.05
+    L, grad = ow.pair_loss_grad(params, norm, feats, targets, knn, dim, mu)
+    # the vectorised loss equals the loop over pairs written out
+    assert L == pytest.approx(ow.pair_loss(params, norm, feats, targets, knn, dim, mu), rel=1e-13)
+    # without the anchor, a constant shift of the targets (the gauge) does not change the loss
+    L0 = ow.pair_loss_grad(params, norm, feats, targets, knn, dim)[0]
+    assert L0 == pytest.approx(ow.pair_loss_grad(params, norm, feats, targets + 3.0, knn, dim)[0], rel=1e-12)
+    h = 1e-6
+    tol_abs = 16 * 2.3e-16 * max(1.0, L) / h
+    for p in g.choice(P, size=60, replace=False):
+        e = np.zeros(P)
+        e[p] = h
+        fd = (ow.pair_loss(params + e, norm, feats, targets, knn, dim, mu)
+              - ow.pair_loss(params - e, norm, feats, targets, knn, dim, mu)) / (2 * h)
+        assert fd == pytest.approx(grad[p], rel=2e-6, abs=tol_abs), p
+
+
+def test_knn_rows_match_brute_force():
+    g = np.random.Generator(np.random.PCG64(2))
+    x = g.random((50, 3))
+    d = np.sqrt(((x[:, None] - x[None]) ** 2).sum(-1))
+    np.fill_diagonal(d, np.inf)
+    np.testing.assert_array_equal(ow.knn_rows(x), np.argsort(d, 1, kind="stable")[:, :8])
+    assert np.all(ow.knn_rows(x[:3])[:, 2:] == -1)
