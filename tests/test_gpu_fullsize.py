@@ -50,3 +50,30 @@ def test_fullsize_sampled(capi, which, prec):
     # the rescored fraction stays small
     # BF16 operands (2^-9 rounding) queue more near ties than TF32 or FP32
     assert st.rescored_fp64 < (1e-2 if prec == "tc_bf16" else 2e-3) * J, st.rescored_fp64
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tc_tf32", "tc_bf16"])
+def test_10000_seeds_512cube_subgrid(capi, prec):
+    """The 10,000-seed 512^3 workload: labels on the 128^3 sub-grid of every 4th
+    voxel per axis (2.1M voxels spanning the box) against the oracle, the
+    mismatch count reported (it must be zero), and closed-form totals."""
+    pc = {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32, "tc_bf16": capi.APD_TC_BF16}[prec]
+    inst = synth.workload_3d_10000()
+    n, J, res = inst.n, inst.grid.num_pixels, inst.grid.res
+    g = synth.rng(7)
+    w = 0.3 * g.standard_normal(n) * n ** (-2.0 / 3)
+    x, A, ww, v = instance_tensors(inst, w)
+    ws = capi.Workspace(3, n, J)
+    labels = torch.full((J,), -1, dtype=torch.int32, device="cuda")
+    capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=pc)
+    assert ws.status() == capi.APD_OK
+    k = np.arange(0, res[0], 4)
+    kk = np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)
+    ids = kk[:, 0] + res[0] * (kk[:, 1] + res[1] * kk[:, 2])
+    lab = host(labels)
+    ref = oracle.assign_ids(inst.grid, inst.x, inst.A, w, ids)
+    mismatches = int(np.sum(lab[ids] != ref))
+    print(f"10^4 seeds 512^3 {prec}: {mismatches} label mismatches on {ids.size} sub-grid voxels; "
+          f"rescored {ws.last_stats().rescored_fp64}")
+    assert mismatches == 0
+    assert np.bincount(lab, minlength=n).sum() == J and lab.min() >= 0
