@@ -33,6 +33,7 @@ WORKLOADS = {
     "3d_n1000_256cube_lloyd5": ("workload_3d_1000", 5),
     "2d_n20_256sq": ("workload_2d_20", 0),
     "2d_n2000_1024sq": ("workload_2d_2000", 0),
+    "3d_n10000_512cube": ("workload_3d_10000", 0),
     # 256 independent 2D instances, N log-uniform in [50, 2000], grids 256^2 .. 1024^2
     "2d_batch256": ("batched_2d_instances", 0),
 }
@@ -53,6 +54,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_tf32", "tc_bf16"],
                     help="scoring arithmetic of the reported form (the plain FP32 and the "
                          "tensor-core TF32 forms are always timed too)")
+    ap.add_argument("--assign-prune", action="store_true",
+                    help="--mode assign: score with seed-group pruning")
+    ap.add_argument("--no-prune", dest="prune", action="store_false",
+                    help="score the chosen form densely (no seed-group pruning)")
     ap.add_argument("--mode", default="apd", choices=["apd", "assign"],
                     help="apd: the full benchmark; assign: only repeated scoring+moments calls "
                          "(apd_cell_moments) at zero weights, for kernel profiling")
@@ -242,13 +247,15 @@ def measure_form(args, ctx, precision, chosen_start=False):
     Lloyd rounds then run as in the plain form."""
     import torch
     import torch.distributed as dist
-    from paper_2403_03571_gb300 import capi, warmstart
+    from paper_2403_03571_gb300 import capi, ranks, warmstart
     inst, rounds, dev, stream, world = ctx["inst"], ctx["rounds"], ctx["dev"], ctx["stream"], ctx["world"]
     x0, A, v, w0, x_out, w_out, ws, flush = (ctx[k] for k in ("x0", "A", "v", "w0", "x_out", "w_out", "ws", "flush"))
     n = inst.n
     opts = capi.solve_opts(eps=0.01, precision=precision_code(capi, precision))
     net = warmstart.load(inst.grid.dim) if chosen_start else None
     w_first = torch.zeros_like(w0)
+    # the chosen form scores with seed-group pruning (same labels); the plain forms sweep densely
+    ws.set_pruning(bool(chosen_start and args.prune))
 
     def step(xin, Ain, win, vin):
         winit = win
@@ -274,6 +281,7 @@ def measure_form(args, ctx, precision, chosen_start=False):
         step(x0, A, w0, v)
     torch.cuda.synchronize()
     ws.profile_read()
+    ws.pairs_scored()
     ws.profile(True)
     clk = ClockSampler(ctx["local"])
     if world > 1:
@@ -296,12 +304,11 @@ def measure_form(args, ctx, precision, chosen_start=False):
     wall = time.perf_counter() - t_wall
     clocks = clk.stop()
     assign_ms, assign_launches, assign_pairs, kernel_launches = ws.profile_read()
+    scored_pairs = ws.pairs_scored()
     ws.profile(False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    max_ms = ranks.max_over_ranks(total_ms, dev)  # the slowest rank's time
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    max_ms = float(t.item())
 
     # end to end through the public API: inputs from pinned host memory, result read back
     hx = torch.from_numpy(inst.x).pin_memory()
@@ -329,9 +336,7 @@ def measure_form(args, ctx, precision, chosen_start=False):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_max = ranks.max_over_ranks(e2e_ms, dev)
     J = inst.grid.num_pixels
     evals = [i.evaluations for i in infos]
     per_launch_ms = assign_ms / max(1, assign_launches)
@@ -347,7 +352,9 @@ def measure_form(args, ctx, precision, chosen_start=False):
         "launch_ms": per_launch_ms,
         "launches": assign_launches,
         "pair_rate": pairs_per_launch / (per_launch_ms / 1000.0),
-        "e2e": {"value": world * args.e2e_steps / (float(te.item()) / 1000.0) if args.e2e_steps > 0 else None,
+        "scored_pair_rate": (scored_pairs / max(1, assign_launches)) / (per_launch_ms / 1000.0)
+        if precision == "fp32" else None,
+        "e2e": {"value": world * args.e2e_steps / (e2e_max / 1000.0) if args.e2e_steps > 0 else None,
                 "unit": "APD/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": kernel_launches,
@@ -370,12 +377,17 @@ def roofline_block(form, dim, sms, workload):
     if form["precision"] == "fp32":
         peak = fp32_peak_tflops(sm_mhz, sms)
         tr = NCU_TRAFFIC.get((kernel_source_hash(), workload))
+        # pairs the kernel evaluated (fewer than N x J when seed groups are pruned)
+        sr = form.get("scored_pair_rate") or pr
+        alg = sr * 2 * F / 1e12
         return {"bound": "alu", "kernel": "assign_fp32_kernel<%d>" % dim, "achieved": alg, "peak": peak,
                 "unit": "TFLOP/s", "frac": alg / peak, "traffic": tr,
                 "work_per_pair_flops": 2 * F,
+                "evaluated_pairs_per_s": sr,
+                "dense_equivalent_pairs_per_s": pr,
                 "executed_flops_per_pair": FLOPS_PER_PAIR[dim],
-                "executed_tflops": pr * FLOPS_PER_PAIR[dim] / 1e12,
-                "executed_frac": pr * FLOPS_PER_PAIR[dim] / 1e12 / peak,
+                "executed_tflops": sr * FLOPS_PER_PAIR[dim] / 1e12,
+                "executed_frac": sr * FLOPS_PER_PAIR[dim] / 1e12 / peak,
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
                                f"(max SM clock from MEASURED_PEAKS.json, {peak_src})",
                 "launch_ms": form["launch_ms"], "launches": form["launches"]}
@@ -394,11 +406,9 @@ def roofline_block(form, dim, sms, workload):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_2403_03571_gb300 import build, capi
+    from paper_2403_03571_gb300 import build, capi, ranks
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = ranks.rank_world()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -466,7 +476,7 @@ def run_ours(args):
     out["tc_tf32"] = side(forms["tc_tf32"])
     out["chosen_form"] = ("coarse-to-fine first solve (factor 2, coarse eps 5 %) started from the learned "
                           "per-seed prediction judged against W = 0, then Algorithm 3's Lloyd rounds; "
-                          f"{args.precision} scoring")
+                          f"{args.precision} scoring" + (" with seed-group pruning" if args.prune else ""))
     out["coarse_evaluations_per_apd"] = chosen["coarse_evaluations_per_apd"]
     out["warm_start_network"] = chosen["warm_start_network"]
     if not args.no_cpu_baseline:
@@ -499,6 +509,7 @@ def run_assign_only(args):
     w = torch.from_numpy(0.3 * g.standard_normal(n) * n ** (-2.0 / dim)).cuda()
     mom = torch.zeros((n, 1 + dim + dim * (dim + 1) // 2), dtype=torch.int64, device="cuda")
     ws = capi.Workspace(dim, n, J)
+    ws.set_pruning(args.prune and args.assign_prune)
     prec = precision_code(capi, args.precision)
     for _ in range(args.warmup):
         capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=prec)
@@ -511,6 +522,7 @@ def run_assign_only(args):
     ms, launches, pairs, _ = ws.profile_read()
     st = ws.last_stats()
     print(json.dumps({"mode": "assign", "workload": args.workload, "precision": args.precision,
+                      "pruned": bool(args.prune and args.assign_prune),
                       "launch_ms": ms / max(1, launches),
                       "pairs_per_s": pairs / (ms / 1000.0), "rescored_fp64": st.rescored_fp64,
                       "pixels": st.pixels}))
@@ -542,12 +554,14 @@ def run_batch(args):
     b = capi.Batch(2, [i.grid for i in insts], [i.n for i in insts])
 
     def chosen_call():
+        b.set_pruning(args.prune)
         wp = warmstart.predict(net, insts, x, A, v) if net is not None else w
         rc, infos, used = capi.apd_batch_solve_weights_multires(b, x, A, wp, v, w_out, opts, mopts,
                                                                 judge=net is not None)
         return infos, used
 
     def batched_call():
+        b.set_pruning(False)
         rc, infos = capi.apd_batch_solve_weights(b, x, A, w, v, w_out, opts)
         return infos, [0] * count
 

@@ -96,6 +96,16 @@ int apd_workspace_create(apd_workspace **ws, int32_t dim, int32_t max_n, int64_t
  * uses it is still in flight. */
 void apd_workspace_destroy(apd_workspace *ws);
 
+/* Seed-group pruning of the FP32 scoring (default off: the dense sweep of
+ * Algorithm 1).  When on, each warp skips every 32-seed group (Morton scan
+ * order) whose cost lower bound over the warp's pixels,
+ *     min lambda_min * dist(pixel box, seed box)^2 - (max w - w_ref),
+ * exceeds the largest second-best cost among those pixels: such seeds can
+ * change no label and no near-tie decision, so labels and moments are the
+ * same as without pruning.  Applies to every later FP32 scoring call on the
+ * workspace (the tensor-core forms are always dense). */
+int apd_workspace_set_pruning(apd_workspace *ws, int32_t enable);
+
 /* Synchronise `stream`, return and clear the device-side status latched by the
  * stream-ordered calls (APD_OK, APD_ERR_ARG, APD_ERR_NOT_SPD, APD_ERR_TIMEOUT),
  * or APD_ERR_CUDA if the synchronisation itself failed. */
@@ -195,6 +205,12 @@ int apd_profile_enable(apd_workspace *ws, int32_t enable);
 int apd_profile_read(apd_workspace *ws, double *assign_ms, int64_t *launches, int64_t *pairs,
                      int64_t *kernel_launches);
 
+/* Pixel-seed pairs the FP32 scoring kernel actually evaluated since the last
+ * call (counted on the device whether or not profiling is on; equal to the
+ * padded N x J of each launch without pruning, fewer with it); resets the
+ * count.  Host-synchronous. */
+int apd_profile_read_scored(apd_workspace *ws, int64_t *pairs_scored);
+
 /* apd_cell_moments without a workspace, for callers that cannot allocate device
  * memory (a device-memory budget fixed at start-up, a host framework whose
  * allocator owns all device memory, or a latency-critical loop that cannot take
@@ -258,6 +274,9 @@ void apd_batch_destroy(apd_batch *batch);
  * a tile is P x TY x TZ pixels, P along the first axis. */
 int apd_batch_tile_info(apd_batch *batch, int32_t *tile, int32_t *n_variants, double *ms,
                         int32_t *shape);
+
+/* Seed-group pruning of the batch's FP32 scoring, as apd_workspace_set_pruning. */
+int apd_batch_set_pruning(apd_batch *batch, int32_t enable);
 
 /* Kernels this batch has launched (graph replays count their six kernels). */
 int64_t apd_batch_kernel_launches(apd_batch *batch);

@@ -41,7 +41,8 @@ EXPORTED = (
     "apd_warmstart_features", "apd_warmstart_fit_norm", "apd_warmstart_predict",
     "apd_warmstart_train_step", "apd_solve_weights_warm",
     "apd_multires_opts_default", "apd_solve_weights_multires", "apd_batch_solve_weights_multires",
-    "apd_warmstart_train_step_pairs",
+    "apd_warmstart_train_step_pairs", "apd_workspace_set_pruning", "apd_batch_set_pruning",
+    "apd_profile_read_scored",
 )
 
 
@@ -168,6 +169,9 @@ def load(path: Optional[str] = None):
     L.apd_batch_solve_weights_multires.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _P(ApdSolveOpts),
                                                    _P(ApdMultiresOpts), ctypes.c_int32, _P(ApdSolveInfo),
                                                    _P(ctypes.c_int32), _vp]
+    L.apd_workspace_set_pruning.argtypes = [_vp, ctypes.c_int32]
+    L.apd_profile_read_scored.argtypes = [_vp, _P(ctypes.c_int64)]
+    L.apd_batch_set_pruning.argtypes = [_vp, ctypes.c_int32]
     _lib = L
     return L
 
@@ -240,6 +244,9 @@ class Workspace:
     def status(self, stream=None) -> int:
         return load().apd_workspace_status(self.handle, _stream(stream))
 
+    def set_pruning(self, enable: bool = True):
+        _check(load().apd_workspace_set_pruning(self.handle, int(bool(enable))), "apd_workspace_set_pruning")
+
     def profile(self, enable: bool = True):
         _check(load().apd_profile_enable(self.handle, int(bool(enable))), "apd_profile_enable")
 
@@ -250,6 +257,12 @@ class Workspace:
         _check(load().apd_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n),
                                        ctypes.byref(pairs), ctypes.byref(kl)), "apd_profile_read")
         return ms.value, n.value, pairs.value, kl.value
+
+    def pairs_scored(self) -> int:
+        """Pairs the FP32 scoring evaluated since the last call (resets the count)."""
+        v = ctypes.c_int64()
+        _check(load().apd_profile_read_scored(self.handle, ctypes.byref(v)), "apd_profile_read_scored")
+        return v.value
 
     def last_stats(self, stream=None) -> ApdEvalStats:
         st = ApdEvalStats()
@@ -379,6 +392,9 @@ class Batch:
 
     def kernel_launches(self) -> int:
         return int(load().apd_batch_kernel_launches(self.handle))
+
+    def set_pruning(self, enable: bool = True):
+        _check(load().apd_batch_set_pruning(self.handle, int(bool(enable))), "apd_batch_set_pruning")
 
 
 def apd_batch_cell_moments(batch: Batch, x, A, w, moments, stream=None):

@@ -101,7 +101,8 @@ cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t
     double hx = 0.5 * C::TX * C::P * g.h[0], hy = 0.5 * C::TY * g.h[1], hz = D == 3 ? 0.5 * C::TZ * g.h[2] : 0.0;
     const float R = (float)(sqrt(hx * hx + hy * hy + hz * hz) * (1.0 + 1e-6));
     const TileSrc src{g,        n,     n_chunks,   R,      ws.recs, ws.sorted ? ws.scodes : nullptr,
-                      ws.sorted ? ws.perm : nullptr, gmom, ws.flags, ws.flag_gi, labels, ws.sc};
+                      ws.sorted ? ws.perm : nullptr, gmom, ws.flags, ws.flag_gi, labels, ws.sc,
+                      ws.prune ? ws.groups : nullptr, ws.pairs_scored};
     assign_fp32_kernel<D><<<grid, C::TX * C::TY * C::TZ, smem, st>>>(src);
     return cudaGetLastError();
 }

@@ -93,6 +93,8 @@ struct BParams {
 
 struct BArgs {             // everything the per-iteration kernels touch
     int count, dim;
+    int prune;             // FP32 scoring skips seed groups by their bounds
+    int pad;
     long long total_n;
     const BInst *inst;
     BSolve *sol;
@@ -308,6 +310,8 @@ __global__ void __launch_bounds__(TX *TY *TZ, MINB) batch_assign_kernel(const __
             cur.flag_gi = a.flag_gi + I.flag_off;
             cur.labels = nullptr;
             cur.sc = a.scs + b;
+            cur.groups = a.prune ? a.groups + I.rec_off / 32 : nullptr;
+            cur.pairs_scored = nullptr;
         }
         __syncthreads();
         if (!fp32::score_tile<D, TX, P, TY, TZ>(sm, cur, txyz[0], txyz[1], txyz[2], uses)) break;
@@ -1123,6 +1127,22 @@ int apd_batch_tile_info(apd_batch *bt, int32_t *tile, int32_t *n_variants, doubl
 
 int64_t apd_batch_kernel_launches(apd_batch *bt) { return bt ? bt->launches : -1; }
 
+int apd_batch_set_pruning(apd_batch *bt, int32_t enable) {
+    if (!bt) return APD_ERR_ARG;
+    const int want = enable != 0;
+    if (bt->args.prune != want) {
+        bt->args.prune = want;
+        // the captured graph holds the old argument block
+        if (bt->exec) cudaGraphExecDestroy(bt->exec);
+        if (bt->graph) cudaGraphDestroy(bt->graph);
+        bt->exec = nullptr;
+        bt->graph = nullptr;
+        bt->graph_variant = -1;
+    }
+    if (bt->coarse) apd_batch_set_pruning(bt->coarse, enable);
+    return APD_OK;
+}
+
 int apd_batch_cell_moments(apd_batch *bt, const double *x, const double *A, const double *w, int64_t *moments,
                            apd_stream_t stream) {
     if (!bt || !x || !A || !w || !moments) return APD_ERR_ARG;
@@ -1245,6 +1265,7 @@ int apd_batch_solve_weights_multires(apd_batch *bt, const double *x, const doubl
             for (int d = 0; d < g.dim; ++d) g.res[d] = std::max(4, (g.res[d] + m.factor - 1) / m.factor);
         const int rc = apd_batch_create(&bt->coarse, bt->dim, bt->count, cg.data(), bt->n.data(), -1);
         if (rc != APD_OK) return rc;
+        apd_batch_set_pruning(bt->coarse, bt->args.prune);
         bt->coarse_factor = m.factor;
     }
     apd_solve_opts oc = o;

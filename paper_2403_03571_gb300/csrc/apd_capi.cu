@@ -519,6 +519,7 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.moments, (size_t)max_n * K * sizeof(unsigned long long));
     alloc((void **)&w.flags, (size_t)max_j * sizeof(uint32_t));
     alloc((void **)&w.flag_gi, (size_t)max_j * sizeof(int32_t));
+    alloc((void **)&w.pairs_scored, sizeof(unsigned long long));
     alloc((void **)&w.groups, (size_t)(w.n_pad_max / 32) * sizeof(GroupBound));
     alloc((void **)&w.sc, sizeof(DevScalars));
     // tensor-core tiles hold 512 pixels; 8x slack covers ragged grids down to thin slabs
@@ -544,6 +545,7 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.wpred, (size_t)max_n * sizeof(double));
     if (ok && cudaMallocHost((void **)&w.sc_host, sizeof(DevScalars)) != cudaSuccess) ok = false;
     if (ok && cudaMemset(w.sc, 0, sizeof(DevScalars)) != cudaSuccess) ok = false;
+    if (ok && cudaMemset(w.pairs_scored, 0, sizeof(unsigned long long)) != cudaSuccess) ok = false;
     if (ok && cudaMemset(w.recs, 0, (size_t)w.n_pad_max * sizeof(SeedRec)) != cudaSuccess) ok = false;
     if (ok && cudaDeviceSynchronize() != cudaSuccess) ok = false;
     if (!ok) {
@@ -558,12 +560,27 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_cand, w.moments, w.flags, w.flag_gi, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_cand, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.sc_host) cudaFreeHost(w.sc_host);
     delete ws;
+}
+
+int apd_profile_read_scored(apd_workspace *ws, int64_t *pairs_scored) {
+    if (!ws || !pairs_scored) return APD_ERR_ARG;
+    unsigned long long v = 0;
+    APD_TRY(cuda_ok(cudaMemcpy(&v, ws->w.pairs_scored, sizeof v, cudaMemcpyDeviceToHost)));
+    APD_TRY(cuda_ok(cudaMemset(ws->w.pairs_scored, 0, sizeof v)));
+    *pairs_scored = (int64_t)v;
+    return APD_OK;
+}
+
+int apd_workspace_set_pruning(apd_workspace *ws, int32_t enable) {
+    if (!ws) return APD_ERR_ARG;
+    ws->w.prune = enable != 0;
+    return APD_OK;
 }
 
 int apd_profile_enable(apd_workspace *ws, int32_t enable) {
@@ -682,6 +699,20 @@ int apd_solve_weights(const apd_grid *grid, const apd_seeds *seeds, const double
     return rc;
 }
 
+// The network's predicted weights for one instance into ws.wpred.
+static int predict_start(const apd_grid *grid, const apd_seeds *seeds, const double *v, apd_mlp *net, Workspace &ws,
+                         apd_stream_t stream) {
+    const int64_t offs[2] = {0, seeds->n};
+    double box[6] = {0.0, 0.0, 0.0, 1.0, 1.0, 1.0};
+    for (int a = 0; a < grid->dim; ++a) {
+        box[a] = grid->lo[a];
+        box[3 + a] = grid->hi[a];
+    }
+    ws.kernel_launches += 2;
+    APD_TRY(apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws.wfeat, nullptr, stream));
+    return apd_warmstart_predict(net, 1, offs, box, ws.wfeat, ws.wpred, stream);
+}
+
 int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
                            const apd_solve_opts *opts, apd_solve_info *info, apd_workspace *ws, apd_mlp *net,
                            int32_t *used_pred, apd_stream_t stream) {
@@ -695,15 +726,7 @@ int apd_solve_weights_warm(const apd_grid *grid, const apd_seeds *seeds, const d
     int rc = net ? solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st) : APD_ERR_ARG;
     if (rc == APD_OK && warmstart_dim(net) != g.dim) rc = APD_ERR_ARG;
     if (rc == APD_OK) {
-        const int64_t offs[2] = {0, seeds->n};
-        double box[6] = {0.0, 0.0, 0.0, 1.0, 1.0, 1.0};
-        for (int a = 0; a < grid->dim; ++a) {
-            box[a] = grid->lo[a];
-            box[3 + a] = grid->hi[a];
-        }
-        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, nullptr, stream);
-        if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, box, ws->w.wfeat, ws->w.wpred, stream);
-        ws->w.kernel_launches += 2;
+        rc = predict_start(grid, seeds, v, net, ws->w, stream);
     }
     if (rc == APD_OK)
         rc = solve_impl(g, grid, seeds->n, seeds->x, seeds->A, ws->w.wpred, v, w_out, o, inf, ws->w, st, false,
@@ -750,15 +773,7 @@ int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, con
     oc.max_evals = m.coarse_max_evals;
     const double *w0 = seeds->w;
     if (rc == APD_OK && net) {
-        const int64_t offs[2] = {0, seeds->n};
-        double box[6] = {0.0, 0.0, 0.0, 1.0, 1.0, 1.0};
-        for (int a = 0; a < grid->dim; ++a) {
-            box[a] = grid->lo[a];
-            box[3 + a] = grid->hi[a];
-        }
-        rc = apd_warmstart_features(net, 1, offs, box, seeds->x, seeds->A, v, ws->w.wfeat, nullptr, stream);
-        if (rc == APD_OK) rc = apd_warmstart_predict(net, 1, offs, box, ws->w.wfeat, ws->w.wpred, stream);
-        ws->w.kernel_launches += 2;
+        rc = predict_start(grid, seeds, v, net, ws->w, stream);
         w0 = ws->w.wpred;
     }
     if (rc == APD_OK) {

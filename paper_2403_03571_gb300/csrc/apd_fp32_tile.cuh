@@ -96,6 +96,8 @@ struct SharedLayout {
     int tkey[kTable];
     uint64_t bar[2];
     int start_chunk;
+    float wbox[16][6];  // per warp: pixel box lo[3], hi[3] (pruning)
+    unsigned long long scored;  // pixel-seed pairs the CTA's fast passes evaluated in this tile
 };
 
 template <int D>
@@ -161,6 +163,8 @@ struct TileSrc {
     int32_t *flag_gi;             // FP32 best seed of each queued pixel (or null)
     int32_t *labels;              // [J] or null
     DevScalars *sc;
+    const GroupBound *groups;     // bounds of the scan-order 32-seed groups: pruning (null: dense)
+    unsigned long long *pairs_scored;  // pixel-seed pairs the fast pass evaluated (or null)
 };
 
 // Scores the (TX P) x TY x TZ tile (bx, by, bz) of `s` with NT = TX TY TZ
@@ -227,6 +231,36 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         return c < 0 ? c + n_chunks : c;
     };
     const double wref = dkey_inv(s.sc->wref_key);
+    // Pruning (optional): the box of this warp's pixels (FP32, rounded outwards);
+    // a seed group whose cost lower bound over the box exceeds every pixel's
+    // second-best cost cannot change any label or queue decision and is skipped.
+    const int lane = tid & 31;
+    if (s.groups) {
+        float wlo[3] = {0.f, 0.f, 0.f}, whi[3] = {0.f, 0.f, 0.f};
+        const double cx[3] = {g.lo[0] + ((double)k0b + 0.5) * g.h[0], g.lo[1] + ((double)k1 + 0.5) * g.h[1],
+                              D == 3 ? g.lo[2] + ((double)k2 + 0.5) * g.h[2] : 0.0};
+        const double ex = (double)(P - 1) * g.h[0];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            wlo[a] = __double2float_rd(cx[a]);
+            whi[a] = __double2float_ru(a == 0 ? cx[0] + ex : cx[a]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                wlo[a] = fminf(wlo[a], __shfl_xor_sync(0xffffffffu, wlo[a], off));
+                whi[a] = fmaxf(whi[a], __shfl_xor_sync(0xffffffffu, whi[a], off));
+            }
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                sm.wbox[tid >> 5][a] = wlo[a];
+                sm.wbox[tid >> 5][3 + a] = whi[a];
+            }
+        }
+        __syncwarp();
+    }
     if (tid == 0) {
         for (int k = 0; k < 2 && k < n_chunks; ++k) {
             mbar_expect_tx(&sm.bar[k], kChunk * sizeof(SeedRec));
@@ -251,8 +285,37 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         const int c = chunk_at(k);
         if (ok && !mbar_wait_bounded(&sm.bar[b], uses[b] & 1u, &s.sc->status)) ok = false;
         ++uses[b];
+        // Pruning decision for this chunk's groups (before the transform, which is
+        // skipped when no warp of the CTA scores any of them)
+        const int valid_in_chunk = min(kChunk, n - c * kChunk);
+        const int groups = (valid_in_chunk + kGroup - 1) / kGroup;
+        unsigned live = 0xffffffffu;  // groups of this chunk the warp must score
+        if (s.groups) {
+            float bmax = b2[0];
+#pragma unroll
+            for (int p = 1; p < P; ++p) bmax = fmaxf(bmax, b2[p]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
+            bool keep = true;
+            if (lane < groups && bmax < FLT_MAX) {
+                const GroupBound gb = s.groups[c * (kChunk / kGroup) + lane];
+                float d2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const float lo = sm.wbox[tid >> 5][a], hi = sm.wbox[tid >> 5][3 + a];
+                    const float slack = 1e-6f * (fabsf(lo) + fabsf(hi) + fabsf(gb.lo[a]) + fabsf(gb.hi[a]));
+                    const float t = fmaxf(fmaxf(gb.lo[a] - hi, lo - gb.hi[a]) - slack, 0.f);
+                    d2 = fmaf(t, t, d2);
+                }
+                const float wpart = __double2float_rd(wref - gb.wmax);
+                const float lb = __fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f) + wpart;
+                keep = !(lb > bmax + 1e-6f * (fabsf(bmax) + fabsf(lb) + fabsf(wpart)) + 1e-30f);
+            }
+            live = __ballot_sync(0xffffffffu, keep) & ((1u << groups) - 1u);
+        }
+        const bool need_chunk = s.groups ? (__syncthreads_or(live != 0u) != 0) : true;
         // transform this chunk into the row-form coefficients
-        for (int sl = tid; sl < kChunk; sl += NT) {
+        for (int sl = need_chunk ? tid : kChunk; sl < kChunk; sl += NT) {
             const int si = c * kChunk + sl;
             float4 v0, v1, v2;
             if (ok && si < n) {
@@ -295,10 +358,17 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             bulk_g2s(&sm.raw[b][0], s.recs + (size_t)chunk_at(k + 2) * kChunk, kChunk * sizeof(SeedRec),
                      &sm.bar[b]);
         }
-        if (ok) {
-            const int valid_in_chunk = min(kChunk, n - c * kChunk);
-            const int groups = (valid_in_chunk + kGroup - 1) / kGroup;
+        if (ok && need_chunk) {
+            if (s.pairs_scored && lane == 0) {
+                const unsigned m = live & ((1u << groups) - 1u);
+                // live groups x 32 seeds, less the padding of a live partial last group
+                unsigned seeds = (unsigned)__popc(m) * kGroup;
+                if (((m >> (groups - 1)) & 1u) && valid_in_chunk < groups * kGroup)
+                    seeds -= (unsigned)(groups * kGroup - valid_in_chunk);
+                atomicAdd(&sm.scored, (unsigned long long)seeds * (unsigned long long)(32 * P));
+            }
             for (int gr = 0; gr < groups; ++gr) {
+                if (!((live >> gr) & 1u)) continue;
                 // fast pass: smallest cost of this group per pixel (one 3-input min per two pairs)
                 float gm[P];
 #pragma unroll
@@ -391,6 +461,10 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     }
     if (cur >= 0) flush_run<D>(sm, s.gmom, cur, cnt, s0, s00, u1, u2);
     __syncthreads();
+    if (tid == 0 && s.pairs_scored) {
+        atomicAdd(s.pairs_scored, sm.scored);
+        sm.scored = 0ull;
+    }
     // flush the table to the global moments and leave it empty
     for (int t = tid; t < kTable; t += NT) {
         const int key = sm.tkey[t];
@@ -421,6 +495,7 @@ __device__ __forceinline__ void init_shared(SharedLayout<D> &sm) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
+        sm.scored = 0ull;
     }
     __syncthreads();
 }

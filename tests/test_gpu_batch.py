@@ -58,6 +58,7 @@ def test_batch_moments_every_tile_shape(capi, dim, specs):
     _, _, shapes = capi.Batch(dim, [i.grid for i in insts], [i.n for i in insts], tile=0).tile_info()
     for tile in range(len(shapes)):
         b = capi.Batch(dim, [i.grid for i in insts], [i.n for i in insts], tile=tile)
+        b.set_pruning(tile % 2 == 1)  # every other shape with seed-group pruning
         for _ in range(2):  # two calls in a row on one batch
             mom = torch.full((total, K), -3, dtype=torch.int64, device="cuda")
             assert capi.apd_batch_cell_moments(b, x, A, w, mom) == capi.APD_OK
@@ -99,6 +100,7 @@ def test_batch_solve_meets_stop_rule(capi, dim):
                  enumerate([(40, 32), (120, 48), (15, 24)])]
     x, A, w, v = _tensors(insts)
     b = capi.Batch(dim, [i.grid for i in insts], [i.n for i in insts])
+    b.set_pruning(dim == 3)
     w_out = torch.zeros_like(w)
     rc, infos = capi.apd_batch_solve_weights(b, x, A, w, v, w_out, capi.solve_opts(eps=0.01))
     assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE)

@@ -19,10 +19,18 @@ def capi():
     return c
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tc_tf32", "tc_bf16"])
+PRECS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16"]
+
+
+def _pc(capi, prec):
+    return {"fp32": capi.APD_FP32, "fp32_pruned": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32,
+            "tc_bf16": capi.APD_TC_BF16}[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("which", ["2d_20", "3d_1000"])
 def test_fullsize_sampled(capi, which, prec):
-    pc = {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32, "tc_bf16": capi.APD_TC_BF16}[prec]
+    pc = _pc(capi, prec)
     inst = synth.workload_2d_20() if which == "2d_20" else synth.workload_3d_1000()
     n, J, dim = inst.n, inst.grid.num_pixels, inst.grid.dim
     g = synth.rng(99)
@@ -30,6 +38,7 @@ def test_fullsize_sampled(capi, which, prec):
     w = 0.3 * g.standard_normal(n) * n ** (-2.0 / dim)
     x, A, ww, v = instance_tensors(inst, w)
     ws = capi.Workspace(dim, n, J)
+    ws.set_pruning(prec == "fp32_pruned")
     labels = torch.full((J,), -1, dtype=torch.int32, device="cuda")
     capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=pc)
     assert ws.status() == capi.APD_OK
@@ -52,18 +61,19 @@ def test_fullsize_sampled(capi, which, prec):
     assert st.rescored_fp64 < (1e-2 if prec == "tc_bf16" else 2e-3) * J, st.rescored_fp64
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tc_tf32", "tc_bf16"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_10000_seeds_512cube_subgrid(capi, prec):
     """The 10,000-seed 512^3 workload: labels on the 128^3 sub-grid of every 4th
     voxel per axis (2.1M voxels spanning the box) against the oracle, the
     mismatch count reported (it must be zero), and closed-form totals."""
-    pc = {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32, "tc_bf16": capi.APD_TC_BF16}[prec]
+    pc = _pc(capi, prec)
     inst = synth.workload_3d_10000()
     n, J, res = inst.n, inst.grid.num_pixels, inst.grid.res
     g = synth.rng(7)
     w = 0.3 * g.standard_normal(n) * n ** (-2.0 / 3)
     x, A, ww, v = instance_tensors(inst, w)
     ws = capi.Workspace(3, n, J)
+    ws.set_pruning(prec == "fp32_pruned")
     labels = torch.full((J,), -1, dtype=torch.int32, device="cuda")
     capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=pc)
     assert ws.status() == capi.APD_OK

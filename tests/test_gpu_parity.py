@@ -26,16 +26,23 @@ def capi():
     return c
 
 
-PRECISIONS = ["fp32", "tc_tf32", "tc_bf16"]
+PRECISIONS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16"]
 
 
 def _prec(capi, name):
-    return {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32, "tc_bf16": capi.APD_TC_BF16}[name]
+    return {"fp32": capi.APD_FP32, "fp32_pruned": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32,
+            "tc_bf16": capi.APD_TC_BF16}[name]
+
+
+def _ws(capi, dim, n, J, prec):
+    ws = capi.Workspace(dim, n, J)
+    ws.set_pruning(prec == "fp32_pruned")
+    return ws
 
 
 def gpu_labels(capi, inst, w=None, ws=None, prec="fp32"):
     x, A, ww, _ = instance_tensors(inst, w)
-    ws = ws or capi.Workspace(inst.grid.dim, inst.n, inst.grid.num_pixels)
+    ws = ws or _ws(capi, inst.grid.dim, inst.n, inst.grid.num_pixels, prec)
     labels = torch.full((inst.grid.num_pixels,), -1, dtype=torch.int32, device="cuda")
     capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=_prec(capi, prec))
     assert ws.status() == capi.APD_OK
@@ -88,7 +95,7 @@ def test_assign_matches_oracle(capi, dim, n, res, seed, wscale, prec):
 def test_moments_match_oracle(capi, dim, n, res, seed, wscale, prec):
     inst = _case(dim, n, res, seed, wscale)
     x, A, w, _ = instance_tensors(inst)
-    ws = capi.Workspace(dim, n, inst.grid.num_pixels)
+    ws = _ws(capi, dim, n, inst.grid.num_pixels, prec)
     K = oracle.moment_width(dim)
     mom = torch.full((n, K), -7, dtype=torch.int64, device="cuda")
     capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=_prec(capi, prec))
@@ -211,7 +218,7 @@ def test_tensor_core_self_check(capi):
 def test_deterministic_moments(capi, prec):
     inst = _case(3, 200, (32, 30, 28), 51, 0.2)
     x, A, w, _ = instance_tensors(inst)
-    ws = capi.Workspace(3, 200, inst.grid.num_pixels)
+    ws = _ws(capi, 3, 200, inst.grid.num_pixels, prec)
     outs = []
     for _ in range(5):
         mom = torch.zeros((200, 10), dtype=torch.int64, device="cuda")
