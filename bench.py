@@ -215,9 +215,12 @@ def load_peaks():
 
 
 # DRAM traffic (read + write bytes) of one scoring launch from an ncu capture,
-# keyed by (sha256 prefix of the scoring sources, workload); reported only
-# while the sources are unchanged since the capture.
-NCU_TRAFFIC = {}
+# keyed by (sha256 prefix of the scoring sources, workload, pruned); reported
+# only while the sources are unchanged since the capture.
+NCU_TRAFFIC = {
+    # profiles/assign_fp32_pruned_3d_n1000_256cube.md: dram read 279.3 KB, write 0
+    ("df31f7417324f61b", "3d_n1000_256cube_lloyd5", True): 279296 + 0,
+}
 
 # FP32 flops the row-factored scoring performs per (pixel, seed) pair:
 # 2 FMAs per pixel, plus the per-(row, seed) coefficients (17 flops in 3D,
@@ -376,7 +379,7 @@ def roofline_block(form, dim, sms, workload):
     alg = pr * 2 * F / 1e12
     if form["precision"] == "fp32":
         peak = fp32_peak_tflops(sm_mhz, sms)
-        tr = NCU_TRAFFIC.get((kernel_source_hash(), workload))
+        tr = NCU_TRAFFIC.get((kernel_source_hash(), workload, bool(form.get("pruned"))))
         # pairs the kernel evaluated (fewer than N x J when seed groups are pruned)
         sr = form.get("scored_pair_rate") or pr
         alg = sr * 2 * F / 1e12
@@ -431,6 +434,7 @@ def run_ours(args):
     forms = {}
     forms["chosen"] = measure_form(args, ctx, args.precision, chosen_start=True)
     forms["chosen"]["precision"] = args.precision
+    forms["chosen"]["pruned"] = bool(args.prune)
     for prec in dict.fromkeys(["fp32", "tc_tf32"]):
         forms[prec] = measure_form(args, ctx, prec)
         forms[prec]["precision"] = prec
