@@ -39,7 +39,10 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "3d_n1000_256cube_lloyd5"
 L2_FLUSH_BYTES = 512 << 20
-BATCH_C2F_FACTOR = 2  # coarse grid factor of the chosen batched form
+def chosen_multires(capi):
+    """Coarse-to-fine settings of the chosen forms: grid factor 2, coarse solves
+    to 1.5 % volume error or 80 evaluations (tuned on the 3D workload)."""
+    return capi.multires_opts(factor=2, coarse_eps=0.015, coarse_max_evals=80)
 
 
 def parse():
@@ -256,28 +259,22 @@ def measure_form(args, ctx, precision, chosen_start=False):
     n = inst.n
     opts = capi.solve_opts(eps=0.01, precision=precision_code(capi, precision))
     net = warmstart.load(inst.grid.dim) if chosen_start else None
-    w_first = torch.zeros_like(w0)
     # the chosen form scores with seed-group pruning (same labels); the plain forms sweep densely
     ws.set_pruning(bool(chosen_start and args.prune))
 
     def step(xin, Ain, win, vin):
-        winit = win
-        extra = None
-        if chosen_start:
-            rc, extra, _ = capi.apd_solve_weights_multires(inst.grid, xin, Ain, win, vin, w_first, ws, opts,
-                                                           capi.multires_opts(factor=2), net)
-            winit = w_first
-        if rounds > 0:
-            rc, info = capi.apd_lloyd(inst.grid, xin, Ain, winit, vin, rounds, x_out, w_out, ws, opts)
+        if chosen_start and rounds > 0:
+            rc, info, _ = capi.apd_lloyd_multires(inst.grid, xin, Ain, win, vin, rounds, x_out, w_out, ws, opts,
+                                                  chosen_multires(capi), net)
+        elif chosen_start:
+            rc, info, _ = capi.apd_solve_weights_multires(inst.grid, xin, Ain, win, vin, w_out, ws, opts,
+                                                          chosen_multires(capi), net)
+        elif rounds > 0:
+            rc, info = capi.apd_lloyd(inst.grid, xin, Ain, win, vin, rounds, x_out, w_out, ws, opts)
         else:
-            rc, info = capi.apd_solve_weights(inst.grid, xin, Ain, winit, vin, w_out, ws, opts)
+            rc, info = capi.apd_solve_weights(inst.grid, xin, Ain, win, vin, w_out, ws, opts)
         if rc not in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE):
             raise RuntimeError(f"solve did not converge: {info.as_dict()}")
-        if extra is not None:
-            info.evaluations += extra.evaluations
-            info.coarse_evaluations += extra.coarse_evaluations
-            info.solves += extra.solves
-            info.rescored_fp64 += extra.rescored_fp64
         return info
 
     for _ in range(args.warmup):
@@ -478,9 +475,10 @@ def run_ours(args):
     }
     out["plain_fp32"] = side(forms["fp32"])
     out["tc_tf32"] = side(forms["tc_tf32"])
-    out["chosen_form"] = ("coarse-to-fine first solve (factor 2, coarse eps 5 %) started from the learned "
-                          "per-seed prediction judged against W = 0, then Algorithm 3's Lloyd rounds; "
-                          f"{args.precision} scoring" + (" with seed-group pruning" if args.prune else ""))
+    out["chosen_form"] = ("Algorithm 3 with every weight solve coarse-to-fine (grid factor 2, coarse eps "
+                          "1.5 %, at most 80 coarse evaluations), the first started from the learned per-seed "
+                          f"prediction judged against W = 0; {args.precision} scoring"
+                          + (" with seed-group pruning" if args.prune else ""))
     out["coarse_evaluations_per_apd"] = chosen["coarse_evaluations_per_apd"]
     out["warm_start_network"] = chosen["warm_start_network"]
     if not args.no_cpu_baseline:
@@ -552,7 +550,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     opts = capi.solve_opts(eps=0.01)
-    mopts = capi.multires_opts(factor=BATCH_C2F_FACTOR)
+    mopts = chosen_multires(capi)
     w_out = torch.zeros_like(w)
     net = warmstart.load(2)
     b = capi.Batch(2, [i.grid for i in insts], [i.n for i in insts])
@@ -626,7 +624,7 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": "2d_batch256", "instances": count, "seeds_total": int(offs[-1]),
                    "pairs_per_evaluation_all_instances": pairs_eval, "eps": 0.01,
-                   "coarse_to_fine_factor": BATCH_C2F_FACTOR,
+                   "coarse_to_fine": "factor 2, coarse eps 1.5 %, at most 80 coarse evaluations",
                    "grids": {str(m): sum(i.grid.res[0] == m for i in insts) for m in synth.BATCH_2D_RES},
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"},
         "chosen": chosen, "batched_from_zero": batched, "plain_sequential": plain,

@@ -424,6 +424,17 @@ int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, con
                                apd_workspace *ws, apd_mlp *net, int32_t *used_pred,
                                apd_stream_t stream);
 
+/* Algorithm 3 with every weight solve coarse-to-fine: `rounds` Lloyd moves
+ * and a final solve as apd_lloyd, each solve first on the coarse grid from the
+ * previous weights (the first from seeds->w, or from the network's prediction
+ * judged against W = 0 when net != NULL), then on the target grid.
+ * info->evaluations / coarse_evaluations sum over all solves.  Host-synchronous;
+ * status as apd_lloyd. */
+int apd_lloyd_multires(const apd_grid *grid, const apd_seeds *seeds, const double *v, int32_t rounds,
+                       double *x_out, double *w_out, const apd_solve_opts *opts,
+                       const apd_multires_opts *mo, apd_solve_info *info, apd_workspace *ws,
+                       apd_mlp *net, int32_t *used_pred, apd_stream_t stream);
+
 /* The batched form: every instance solved on its coarse grid (a second batch
  * over the coarse grids, created on first use and kept), from w0, judged
  * against zero when judge != 0, then on its own grid from the coarse weights.

@@ -42,7 +42,7 @@ EXPORTED = (
     "apd_warmstart_train_step", "apd_solve_weights_warm",
     "apd_multires_opts_default", "apd_solve_weights_multires", "apd_batch_solve_weights_multires",
     "apd_warmstart_train_step_pairs", "apd_workspace_set_pruning", "apd_batch_set_pruning",
-    "apd_profile_read_scored",
+    "apd_profile_read_scored", "apd_lloyd_multires",
 )
 
 
@@ -171,6 +171,8 @@ def load(path: Optional[str] = None):
                                                    _P(ctypes.c_int32), _vp]
     L.apd_workspace_set_pruning.argtypes = [_vp, ctypes.c_int32]
     L.apd_profile_read_scored.argtypes = [_vp, _P(ctypes.c_int64)]
+    L.apd_lloyd_multires.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, ctypes.c_int32, _vp, _vp, _P(ApdSolveOpts),
+                                     _P(ApdMultiresOpts), _P(ApdSolveInfo), _vp, _vp, _P(ctypes.c_int32), _vp]
     L.apd_batch_set_pruning.argtypes = [_vp, ctypes.c_int32]
     _lib = L
     return L
@@ -576,3 +578,19 @@ def apd_batch_solve_weights_multires(batch: Batch, x, A, w0, v, w_out, opts=None
                                                  ctypes.byref(opts), ctypes.byref(mopts), int(bool(judge)), info,
                                                  used, _stream(stream))
     return rc, list(info), list(used)
+
+
+def apd_lloyd_multires(grid, x0, A, w0, v, rounds, x_out, w_out, ws: Workspace, opts=None, mopts=None,
+                       net: Optional[WarmStart] = None, stream=None):
+    """Algorithm 3 with coarse-to-fine solves; returns (status, ApdSolveInfo, used_prediction)."""
+    g, s = make_grid(grid), make_seeds(x0, A, w0)
+    info = ApdSolveInfo()
+    used = ctypes.c_int32()
+    opts = opts or solve_opts()
+    mopts = mopts or multires_opts()
+    rc = load().apd_lloyd_multires(ctypes.byref(g), ctypes.byref(s), _ptr(v), int(rounds), _ptr(x_out),
+                                   _ptr(w_out), ctypes.byref(opts), ctypes.byref(mopts), ctypes.byref(info),
+                                   ws.handle, net.handle if net is not None else None, ctypes.byref(used),
+                                   _stream(stream))
+    _check(rc, "apd_lloyd_multires", _SOLVE_OK)
+    return rc, info, used.value

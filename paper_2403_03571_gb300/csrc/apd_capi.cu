@@ -746,6 +746,30 @@ void apd_multires_opts_default(apd_multires_opts *mo) {
     mo->coarse_max_evals = 60;
 }
 
+// Coarse grid of a coarse-to-fine solve (same box, ceil(res / factor) >= 4 per axis).
+static int coarse_grid(const apd_grid *grid, const apd_multires_opts &m, apd_grid &cg, GridDev &gc) {
+    if (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1) return APD_ERR_ARG;
+    cg = *grid;
+    for (int d = 0; d < grid->dim; ++d) cg.res[d] = std::max(4, (grid->res[d] + m.factor - 1) / m.factor);
+    return validate_grid(&cg, gc);
+}
+
+// Solve on the coarse grid from w0 (judged against zero if asked), then on the
+// fine grid from the coarse weights; w_out receives both in turn.  The coarse
+// status (often NOT_CONVERGED at its cap) is not an error.
+static int c2f_solve(const GridDev &g, const apd_grid *grid, const GridDev &gc, const apd_grid *cg, int n,
+                     const double *x, const double *A, const double *w0, const double *v, double *w_out,
+                     const apd_solve_opts &o, const apd_multires_opts &m, apd_solve_info &inf,
+                     apd_solve_info &cinf, Workspace &ws, cudaStream_t st, bool judged, int *used,
+                     bool need_moments_at_out) {
+    apd_solve_opts oc = o;
+    oc.eps = m.coarse_eps;
+    oc.max_evals = m.coarse_max_evals;
+    const int crc = solve_impl(gc, cg, n, x, A, w0, v, w_out, oc, cinf, ws, st, false, judged, used);
+    if (crc < 0) return crc;
+    return solve_impl(g, grid, n, x, A, w_out, v, w_out, o, inf, ws, st, need_moments_at_out);
+}
+
 int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
                                const apd_solve_opts *opts, const apd_multires_opts *mo, apd_solve_info *info,
                                apd_workspace *ws, apd_mlp *net, int32_t *used_pred, apd_stream_t stream) {
@@ -754,6 +778,7 @@ int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, con
     std::memset(&inf, 0, sizeof inf);
     std::memset(&cinf, 0, sizeof cinf);
     GridDev g, gc;
+    apd_grid cg;
     apd_solve_opts o;
     apd_multires_opts m;
     apd_multires_opts_default(&m);
@@ -761,29 +786,73 @@ int apd_solve_weights_multires(const apd_grid *grid, const apd_seeds *seeds, con
     cudaStream_t st = (cudaStream_t)stream;
     int used = 0;
     int rc = solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st);
-    if (rc == APD_OK && (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1)) rc = APD_ERR_ARG;
     if (rc == APD_OK && net && warmstart_dim(net) != g.dim) rc = APD_ERR_ARG;
-    apd_grid cg = *grid;
-    if (rc == APD_OK) {
-        for (int d = 0; d < grid->dim; ++d) cg.res[d] = std::max(4, (grid->res[d] + m.factor - 1) / m.factor);
-        rc = validate_grid(&cg, gc);
-    }
-    apd_solve_opts oc = o;
-    oc.eps = m.coarse_eps;
-    oc.max_evals = m.coarse_max_evals;
+    if (rc == APD_OK) rc = coarse_grid(grid, m, cg, gc);
     const double *w0 = seeds->w;
     if (rc == APD_OK && net) {
         rc = predict_start(grid, seeds, v, net, ws->w, stream);
         w0 = ws->w.wpred;
     }
-    if (rc == APD_OK) {
-        // the coarse solve writes w_out; its status (often NOT_CONVERGED at the cap) is not an error
-        const int crc = solve_impl(gc, &cg, seeds->n, seeds->x, seeds->A, w0, v, w_out, oc, cinf, ws->w, st, false,
-                                   net != nullptr, &used);
-        if (crc < 0) rc = crc;
-    }
     if (rc == APD_OK)
-        rc = solve_impl(g, grid, seeds->n, seeds->x, seeds->A, w_out, v, w_out, o, inf, ws->w, st, false);
+        rc = c2f_solve(g, grid, gc, &cg, seeds->n, seeds->x, seeds->A, w0, v, w_out, o, m, inf, cinf, ws->w, st,
+                       net != nullptr, &used, false);
+    if (rc >= 0) cudaStreamSynchronize(st);
+    if (used_pred) *used_pred = used;
+    inf.status = rc;
+    inf.solves += cinf.solves;
+    inf.rescored_fp64 += cinf.rescored_fp64;
+    inf.coarse_evaluations = cinf.evaluations;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
+int apd_lloyd_multires(const apd_grid *grid, const apd_seeds *seeds, const double *v, int32_t rounds,
+                       double *x_out, double *w_out, const apd_solve_opts *opts, const apd_multires_opts *mo,
+                       apd_solve_info *info, apd_workspace *ws, apd_mlp *net, int32_t *used_pred,
+                       apd_stream_t stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    apd_solve_info inf, cinf;
+    std::memset(&inf, 0, sizeof inf);
+    std::memset(&cinf, 0, sizeof cinf);
+    GridDev g, gc;
+    apd_grid cg;
+    apd_solve_opts o;
+    apd_multires_opts m;
+    apd_multires_opts_default(&m);
+    if (mo) m = *mo;
+    cudaStream_t st = (cudaStream_t)stream;
+    int used = 0, worst = APD_OK;
+    int rc = solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st);
+    if (rc == APD_OK && (!x_out || rounds < 0)) rc = APD_ERR_ARG;
+    if (rc == APD_OK && net && warmstart_dim(net) != g.dim) rc = APD_ERR_ARG;
+    if (rc == APD_OK) rc = coarse_grid(grid, m, cg, gc);
+    const int n = seeds->n;
+    const double *w0 = w_out;
+    if (rc == APD_OK && net) {
+        rc = predict_start(grid, seeds, v, net, ws->w, stream);
+        w0 = ws->w.wpred;
+    }
+    if (rc == APD_OK && x_out != seeds->x)
+        rc = cuda_ok(cudaMemcpyAsync(x_out, seeds->x, (size_t)n * g.dim * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (rc == APD_OK && w_out != seeds->w)
+        rc = cuda_ok(cudaMemcpyAsync(w_out, seeds->w, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; rc == APD_OK && k <= rounds; ++k) {
+        const bool last = k == rounds;
+        const int r = c2f_solve(g, grid, gc, &cg, n, x_out, seeds->A, k == 0 ? w0 : w_out, v, w_out, o, m, inf, cinf,
+                                ws->w, st, k == 0 && net != nullptr, k == 0 ? &used : nullptr, !last);
+        if (r < 0) {
+            rc = r;
+            break;
+        }
+        if (r > worst) worst = r;
+        if (!last) {
+            // the workspace moments belong to (x_out, w_out): move seeds to the discrete centroids
+            ws->w.kernel_launches += 1;
+            rc = cuda_ok(launch_centroids(g, n, x_out, ws->w.moments, x_out, st));
+        }
+    }
+    if (rc == APD_OK) rc = worst;
     if (rc >= 0) cudaStreamSynchronize(st);
     if (used_pred) *used_pred = used;
     inf.status = rc;

@@ -111,3 +111,22 @@ def test_coarse_to_fine_solve(capi, dim, n, m, seed):
     w2 = torch.zeros_like(w)
     rc2, plain = capi.apd_solve_weights(inst.grid, x, A, w, v, w2, ws)
     assert info.evaluations < plain.evaluations, (info.as_dict(), plain.as_dict())
+
+
+def test_lloyd_coarse_to_fine(capi):
+    from paper_2403_03571_gb300 import warmstart
+    inst = synth.make_instance(3, 150, 40, 17)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(3, inst.n, inst.grid.num_pixels)
+    ws.set_pruning(True)
+    x_out, w_out = torch.zeros_like(x), torch.zeros_like(w)
+    rc, info, used = capi.apd_lloyd_multires(inst.grid, x, A, w, v, 3, x_out, w_out, ws,
+                                             mopts=capi.multires_opts(2, 0.02, 60), net=warmstart.load(3))
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+    assert info.solves == 8 and info.coarse_evaluations >= 4
+    X, W = host(x_out), host(w_out)
+    # the returned weights solve the final positions (oracle's own evaluation) ...
+    _, _, err = oracle.dual(inst.grid, X, inst.A, W, inst.v)
+    assert err < 0.01
+    # ... and the positions moved: they are the discrete centroids of an earlier round
+    assert np.abs(X - inst.x).max() > 1e-3
