@@ -331,15 +331,19 @@ cudaError_t launch_axpy(int n, const double *a, double t, const double *b, doubl
     return cudaGetLastError();
 }
 
+// One block runs the whole recursion; its 2 hist + 1 reductions are the cost,
+// so small problems use a smaller block (fewer warps per reduction).
+static int lbfgs_threads(int n) { return n <= 2048 ? 256 : kRedThreads; }
+
 cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma, Workspace &ws,
                                    cudaStream_t st) {
-    lbfgs_direction_kernel<<<1, kRedThreads, 0, st>>>(n, hist, newest, cap, gamma, ws.S, ws.Y, ws.rho,
+    lbfgs_direction_kernel<<<1, lbfgs_threads(n), 0, st>>>(n, hist, newest, cap, gamma, ws.S, ws.Y, ws.rho,
                                                       ws.alpha, ws.gf, ws.p, ws.sc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lbfgs_push(int n, int slot, Workspace &ws, cudaStream_t st) {
-    lbfgs_push_kernel<<<1, kRedThreads, 0, st>>>(n, slot, ws.W, ws.Wt, ws.gf, ws.gft, ws.S, ws.Y,
+    lbfgs_push_kernel<<<1, lbfgs_threads(n), 0, st>>>(n, slot, ws.W, ws.Wt, ws.gf, ws.gft, ws.S, ws.Y,
                                                  ws.rho, ws.sc);
     return cudaGetLastError();
 }
