@@ -236,7 +236,9 @@ int apd_cell_moments_noalloc(const apd_grid *grid, const apd_seeds *seeds, int64
  * integer-valued operands (exact in TF32 and BF16) from shared memory into
  * tensor memory, compared element by element with CUDA-core dot products.
  * kind: 0 = TF32, 1 = BF16; variant: 0 = the operand layout the library uses,
- * 1 = leading and stride offsets exchanged (expected to fail).  Writes the
+ * 1 = leading and stride offsets exchanged (expected to fail), 2 = as 0 but
+ * read back with the min-reducing tensor-memory load (sm_103), whose minimum
+ * over each 32-column slice is compared as well.  Writes the
  * number of mismatching accumulator elements and the largest absolute error
  * (host pointers).  Host-synchronous; runs on the current device. */
 int apd_tensor_core_check(int32_t kind, int32_t variant, int32_t *mismatches, float *max_err);

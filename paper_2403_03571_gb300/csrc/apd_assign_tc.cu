@@ -112,6 +112,23 @@ __device__ __forceinline__ void put_op(uint8_t *base, uint32_t off, float v) {
         *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(v);
 }
 
+// One 16-byte core-matrix row: 4 TF32 or 8 BF16 operand values.
+template <int KIND>
+__device__ __forceinline__ void put_row(uint8_t *dst, const float (&e)[KIND == tc::KIND_TF32 ? 4 : 8]) {
+    if (KIND == tc::KIND_TF32) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(tc::to_tf32(e[0]), tc::to_tf32(e[1]), tc::to_tf32(e[2]),
+                                                       tc::to_tf32(e[3]));
+    } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(e[2 * i], e[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -391,14 +408,18 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) phv[i] = 0.f;
             if (okw && s < n) {
-                const SeedRec32 &r = sm.raw[slot][sl];
+                // the 64-byte record as four 16-byte loads (x hi, x lo, w hi/lo, A)
+                const float4 *rv = reinterpret_cast<const float4 *>(&sm.raw[slot][sl]);
+                const float4 q0 = rv[0], q1 = rv[1], q2 = rv[2], q3 = rv[3];
+                const float rxh[3] = {q0.x, q0.y, q0.z}, rxl[3] = {q0.w, q1.x, q1.y};
+                const float ra[6] = {q2.x, q2.y, q2.z, q2.w, q3.x, q3.y};
                 float xp[3] = {0.f, 0.f, 0.f};
 #pragma unroll
                 for (int a = 0; a < D; ++a)
-                    xp[a] = (r.xh[a] - xch[a]) + (r.xl[a] - xcl[a]);
-                const float wp = (r.wh - wrh) + (r.wl - wrl);  // <= 0 up to rounding
+                    xp[a] = (rxh[a] - xch[a]) + (rxl[a] - xcl[a]);
+                const float wp = (q1.z - wrh) + (q1.w - wrl);  // <= 0 up to rounding
                 if (D == 3) {
-                    const float A00 = r.a[0], A01 = r.a[1], A02 = r.a[2], A11 = r.a[3], A12 = r.a[4], A22 = r.a[5];
+                    const float A00 = ra[0], A01 = ra[1], A02 = ra[2], A11 = ra[3], A12 = ra[4], A22 = ra[5];
                     const float t0 = fmaf(A02, xp[2], fmaf(A01, xp[1], A00 * xp[0]));
                     const float t1 = fmaf(A12, xp[2], fmaf(A11, xp[1], A01 * xp[0]));
                     const float t2 = fmaf(A22, xp[2], fmaf(A12, xp[1], A02 * xp[0]));
@@ -413,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
                     phv[8] = -2.f * t2;
                     phv[9] = fmaf(xp[2], t2, fmaf(xp[1], t1, xp[0] * t0)) - wp;
                 } else {
-                    const float A00 = r.a[0], A01 = r.a[1], A11 = r.a[2];
+                    const float A00 = ra[0], A01 = ra[1], A11 = ra[2];
                     const float t0 = fmaf(A01, xp[1], A00 * xp[0]);
                     const float t1 = fmaf(A11, xp[1], A01 * xp[0]);
                     phv[0] = A00;
@@ -426,12 +447,15 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
             } else {
                 phv[G::F - 1] = 1e30f;  // padding seed: constant huge score
             }
+            // this thread's half of the K features, one 16-byte core-matrix row per store
             constexpr int HALF = Fm::KT / 2;
             uint8_t *B = sm.B[q & 1];
 #pragma unroll
-            for (int i = 0; i < HALF; ++i) {
-                const int kq = half * HALF + i;
-                put_op<KIND>(B, cm_off(sl, kq, Fm::EB, Fm::EPR, Fm::LBO, Fm::SBO), phv[kq]);
+            for (int ch = 0; ch < HALF / Fm::EPR; ++ch) {
+                float e[Fm::EPR];
+#pragma unroll
+                for (int i = 0; i < Fm::EPR; ++i) e[i] = half ? phv[HALF + ch * Fm::EPR + i] : phv[ch * Fm::EPR + i];
+                put_row<KIND>(B + cm_off(sl, half * HALF + ch * Fm::EPR, Fm::EB, Fm::EPR, Fm::LBO, Fm::SBO), e);
             }
             tc::fence_proxy_async_smem();
             __syncwarp();
@@ -454,8 +478,10 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
                 const int base = chunk_id(c_epi) * kTcN;
 #pragma unroll
                 for (int h = 0; h < kTcN / 32; ++h) {
-                    float v[32];
-                    tc::tmem_ld32(taddr + lane_base + (uint32_t)((b * kTcTiles + mt) * kTcN + h * 32), v);
+                    float v[32], gm;
+                    // the reducing load returns the slice's smallest score with the scores
+                    tc::tmem_ld32_min(taddr + lane_base + (uint32_t)((b * kTcTiles + mt) * kTcN + h * 32), v,
+                                      gm);
                     tc::tmem_wait_ld();
                     if (h == kTcN / 32 - 1) {
                         // every score of the stage is in registers: the stage can be refilled
@@ -463,15 +489,14 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&sm.bar_aempty[b]);
                     }
-                    // minima of the 8-seed slices (3-input min)
-                    float m8[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        m8[j] = fmin3_f(fmin3_f(v[8 * j], v[8 * j + 1], v[8 * j + 2]),
-                                        fmin3_f(v[8 * j + 3], v[8 * j + 4], v[8 * j + 5]),
-                                        fminf(v[8 * j + 6], v[8 * j + 7]));
-                    const float gm = fminf(fminf(m8[0], m8[1]), fminf(m8[2], m8[3]));
                     if (__any_sync(0xffffffffu, gm < s4[3])) {
+                        // minima of the 8-seed slices (3-input min), only when some pixel may improve
+                        float m8[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            m8[j] = fmin3_f(fmin3_f(v[8 * j], v[8 * j + 1], v[8 * j + 2]),
+                                            fmin3_f(v[8 * j + 3], v[8 * j + 4], v[8 * j + 5]),
+                                            fminf(v[8 * j + 6], v[8 * j + 7]));
                         // The slice minima are distinct scores, so the 4th smallest of {top-4} +
                         // {slice minima} bounds the new 4th-best from above: only values at or
                         // below it can enter (min/max network, branch free).
@@ -599,16 +624,12 @@ __global__ void __launch_bounds__(256)
         }
         tc_table_add<D>(tkey, tval, gmom, L, val);
     };
-    int4 cds[kResP];
-#pragma unroll
-    for (int p = 0; p < kResP; ++p)
-        cds[p] = (row_valid && k0b + p < g.res[0]) ? cand[rowbase + k0b + p] : make_int4(-1, -1, -1, 0);
     for (int p = 0; p < kResP; ++p) {
         const int k0 = k0b + p;
         int label = -1;
         if (row_valid && k0 < g.res[0]) {
             const long long j = rowbase + k0;
-            const int4 cd = cds[p];
+            const int4 cd = cand[j];
             const float yp[3] = {((float)(p - kResP / 2) + 0.5f) * g.h32[0], 0.f, 0.f};
             const int ids[3] = {cd.x, cd.y, cd.z};
             int orig[3];
@@ -622,7 +643,7 @@ __global__ void __launch_bounds__(256)
                 orig[qq] = (id >= 0 && id < n) ? id : n;
                 if (orig[qq] < n) {
                     cost32_bound_rel<D>(r32[orig[qq]], ch, cl, yp, wrh, wrl, cv[qq], ev[qq]);
-                    if (best < 0 || cv[qq] < cv[best]) best = qq;
+                    if (best < 0 || cv[qq] < (best == 0 ? cv[0] : (best == 1 ? cv[1] : cv[2]))) best = qq;
                 } else {
                     cv[qq] = FLT_MAX;
                     ev[qq] = 0.f;
@@ -631,7 +652,11 @@ __global__ void __launch_bounds__(256)
             if (best < 0) {
                 queue = true;
             } else {
-                const float U = cv[best] + ev[best];
+                // the best candidate's values, selected without indexing by a run-time value
+                const float cb = best == 0 ? cv[0] : (best == 1 ? cv[1] : cv[2]);
+                const float eb = best == 0 ? ev[0] : (best == 1 ? ev[1] : ev[2]);
+                const int ob = best == 0 ? orig[0] : (best == 1 ? orig[1] : orig[2]);
+                const float U = cb + eb;
                 const float s3 = __int_as_float(cd.w);
                 float c_out = fabsf(s3);
                 float r1 = 2.f * R_tile + sqrtf(c_out * inv_lam);
@@ -643,12 +668,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
                 for (int qq = 0; qq < 3; ++qq)
                     if (qq != best && orig[qq] < n && !(cv[qq] - ev[qq] > U)) queue = true;
-                if (!queue) label = orig[best];
+                if (!queue) label = ob;
             }
             if (queue) {
                 const unsigned slot = atomicAdd(&sc->flag_count, 1u);
                 flags[slot] = (uint32_t)j;
-                if (flag_gi) flag_gi[slot] = best >= 0 ? orig[best] : -1;
+                if (flag_gi) flag_gi[slot] = best == 0 ? orig[0] : (best == 1 ? orig[1] : (best == 2 ? orig[2] : -1));
             } else if (labels) {
                 labels[j] = label;
             }

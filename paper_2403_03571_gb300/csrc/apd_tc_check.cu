@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatc
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = tslot;
-    const uint32_t dl = variant == 0 ? LBO : SBO, ds = variant == 0 ? SBO : LBO;
+    const uint32_t dl = variant == 1 ? SBO : LBO, ds = variant == 1 ? LBO : SBO;
     if (tid == 0) {
         const uint32_t idesc = tc::instr_desc(KIND, kM, kN);
         const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(smA);
@@ -85,17 +85,24 @@ __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatc
     if (ok) {
         const int r = warp * 32 + lane;
         for (int c0 = 0; c0 < kN; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            float v[32], mn = 0.f;
+            if (variant == 2)
+                tc::tmem_ld32_min(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v, mn);
+            else
+                tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             tc::tmem_wait_ld();
+            float ref_min = 3.0e38f;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 float ref = 0.f;
                 for (int k = 0; k < kK; ++k) ref += check_a(r, k) * check_b(c0 + i, k);
+                ref_min = fminf(ref_min, ref);
                 const float e = fabsf(v[i] - ref);
                 if (!(e == 0.f)) ++bad;
                 worst = fmaxf(worst, e == e ? e : 3.0e38f);
             }
+            // the reduced load's minimum must equal the minimum of the 32 references
+            if (variant == 2 && !(mn == ref_min)) ++bad;
         }
     }
     atomicAdd(mismatches, bad);
@@ -110,8 +117,7 @@ __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatc
 }  // namespace apd
 
 extern "C" int apd_tensor_core_check(int32_t kind, int32_t variant, int32_t *mismatches, float *max_err) {
-    if ((kind != 0 && kind != 1) || (variant != 0 && variant != 1) || !mismatches || !max_err)
-        return APD_ERR_ARG;
+    if ((kind != 0 && kind != 1) || variant < 0 || variant > 2 || !mismatches || !max_err) return APD_ERR_ARG;
     int *d = nullptr;
     if (cudaMalloc((void **)&d, 3 * sizeof(int)) != cudaSuccess) return APD_ERR_CUDA;
     cudaMemset(d, 0, 3 * sizeof(int));

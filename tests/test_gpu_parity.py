@@ -212,6 +212,8 @@ def test_tensor_core_self_check(capi):
         assert rc == capi.APD_OK and bad == 0 and err == 0.0, (kind, rc, bad, err)
         rc, bad, err = capi.apd_tensor_core_check(kind, 1)
         assert rc == capi.APD_OK and bad > 0
+        rc, bad, err = capi.apd_tensor_core_check(kind, 2)
+        assert rc == capi.APD_OK and bad == 0 and err == 0.0, (kind, rc, bad, err)
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
