@@ -81,3 +81,32 @@ def test_argument_errors_before_cuda(lib):
     assert lib.apd_batch_cell_moments(None, None, None, None, None, None) == capi.APD_ERR_ARG
     assert lib.apd_batch_kernel_launches(None) == -1
     lib.apd_batch_destroy(None)
+    assert lib.apd_batch_set_pruning(None, 1) == capi.APD_ERR_ARG
+    assert lib.apd_workspace_set_pruning(None, 1) == capi.APD_ERR_ARG
+    assert lib.apd_batch_solve_weights_multires(None, None, None, None, None, None, None, None, 0, None, None,
+                                                None) == capi.APD_ERR_ARG
+    # coarse-to-fine and warm-start solves: a bad grid is rejected before any CUDA call
+    g.dim = 4
+    assert lib.apd_solve_weights_multires(ctypes.byref(g), ctypes.byref(s), None, None, None, None, None,
+                                          None, None, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_lloyd_multires(ctypes.byref(g), ctypes.byref(s), None, 1, None, None, None, None, None,
+                                  None, None, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_solve_weights_warm(ctypes.byref(g), ctypes.byref(s), None, None, None, None, None, None,
+                                      None, None) == capi.APD_ERR_ARG
+    g.dim = 2
+    # warm-start network: sizes, argument checks without a device
+    f, p = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.apd_warmstart_sizes(2, ctypes.byref(f), ctypes.byref(p)) == capi.APD_OK
+    assert (f.value, p.value) == (28, 10241)
+    assert lib.apd_warmstart_sizes(3, ctypes.byref(f), ctypes.byref(p)) == capi.APD_OK
+    assert (f.value, p.value) == (32, 10497)
+    assert lib.apd_warmstart_sizes(4, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_warmstart_create(ctypes.byref(h), 4, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_warmstart_create(ctypes.byref(h), 2, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_warmstart_train_step(None, 1, None, None, None, ctypes.c_float(0.0), None, None,
+                                        None) == capi.APD_ERR_ARG
+    assert lib.apd_warmstart_train_step_pairs(None, 1, None, None, None, None, None, None, ctypes.c_float(0.0),
+                                              ctypes.c_float(0.0), None, None, None) == capi.APD_ERR_ARG
+    lib.apd_warmstart_destroy(None)
+    assert lib.apd_tensor_core_check(0, 3, ctypes.byref(ctypes.c_int32()),
+                                     ctypes.byref(ctypes.c_float())) == capi.APD_ERR_ARG
