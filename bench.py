@@ -520,17 +520,19 @@ def run_assign_only(args):
         capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=prec)
     torch.cuda.synchronize()
     ws.profile_read()
+    ws.pairs_scored()
     ws.profile(True)
     for _ in range(args.steps):
         capi.apd_cell_moments(inst.grid, x, A, w, mom, ws, precision=prec)
     assert ws.status() == capi.APD_OK
     ms, launches, pairs, _ = ws.profile_read()
+    scored = ws.pairs_scored()
     st = ws.last_stats()
     print(json.dumps({"mode": "assign", "workload": args.workload, "precision": args.precision,
                       "pruned": bool(args.prune and args.assign_prune),
                       "launch_ms": ms / max(1, launches),
-                      "pairs_per_s": pairs / (ms / 1000.0), "rescored_fp64": st.rescored_fp64,
-                      "pixels": st.pixels}))
+                      "pairs_per_s": pairs / (ms / 1000.0), "scored_fraction": scored / max(1, pairs),
+                      "rescored_fp64": st.rescored_fp64, "pixels": st.pixels}))
     return 0
 
 

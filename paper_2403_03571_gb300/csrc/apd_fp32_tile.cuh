@@ -87,6 +87,28 @@ __device__ __forceinline__ void top2_update(float &b1, float &b2, int &gi, float
     gi = lt ? (gbase | (int)(__float_as_uint(mn) & 31u)) : gi;
 }
 
+// Largest second-best key over the warp's pixels.
+template <int P>
+__device__ __forceinline__ float warp_max_b2(const float (&b2)[P]) {
+    float m = b2[0];
+#pragma unroll
+    for (int p = 1; p < P; ++p) m = fmaxf(m, b2[p]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    return m;
+}
+// True when a group whose cost lower bound is lb (wpart: its weight part) lies
+// above the largest second-best key bmax by more than the rounding margin, so
+// that none of its seeds can change a top-2 of the warp's pixels.
+__device__ __forceinline__ bool group_beyond(float lb, float wpart, float bmax) {
+    return bmax < FLT_MAX && lb > bmax + 1e-6f * (fabsf(bmax) + fabsf(lb) + fabsf(wpart)) + 1e-30f;
+}
+// Order-preserving map of a float to an unsigned key.
+__device__ __forceinline__ unsigned sortable_key(float v) {
+    const unsigned u = __float_as_uint(v);
+    return u ^ ((u >> 31) ? 0xffffffffu : 0x80000000u);
+}
+
 template <int D>
 struct SharedLayout {
     static constexpr int K = moment_width(D);
@@ -97,6 +119,9 @@ struct SharedLayout {
     uint64_t bar[2];
     int start_chunk;
     float wbox[16][6];  // per warp: pixel box lo[3], hi[3] (pruning)
+    float glb[16][kChunk / kGroup];  // per warp: cost lower bound of each group of the chunk
+    float gwp[16][kChunk / kGroup];  // per warp: the weight part of that bound
+    double cref[4];  // tile centre (FP64) and the reference weight wref
     unsigned long long scored;  // pixel-seed pairs the CTA's fast passes evaluated in this tile
 };
 
@@ -196,9 +221,13 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     const bool row_valid = (k1 < g.res[1]) && (D == 2 || k2 < g.res[2]);
 
     // CTA reference point (FP64): the tile centre
-    const double c0 = g.lo[0] + (double)(k0t + W0 / 2) * g.h[0];
-    const double c1 = g.lo[1] + (double)(k1b + TY / 2) * g.h[1];
-    const double c2 = (D == 3) ? g.lo[2] + (double)(k2b + TZ / 2) * g.h[2] : 0.0;
+    // (kept in shared memory: CTA-uniform, read once per chunk by the transform)
+    if (tid == 0) {
+        sm.cref[0] = g.lo[0] + (double)(k0t + W0 / 2) * g.h[0];
+        sm.cref[1] = g.lo[1] + (double)(k1b + TY / 2) * g.h[1];
+        sm.cref[2] = (D == 3) ? g.lo[2] + (double)(k2b + TZ / 2) * g.h[2] : 0.0;
+        sm.cref[3] = dkey_inv(s.sc->wref_key);
+    }
     const float f1 = ((float)(ty - TY / 2) + 0.5f) * g.h32[1];
     const float f2 = (D == 3) ? ((float)(tz - TZ / 2) + 0.5f) * g.h32[2] : 0.f;
     float2 y2[P / 2];
@@ -230,7 +259,6 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         int c = (start_chunk + off) % n_chunks;
         return c < 0 ? c + n_chunks : c;
     };
-    const double wref = dkey_inv(s.sc->wref_key);
     // Pruning (optional): the box of this warp's pixels (FP32, rounded outwards);
     // a seed group whose cost lower bound over the box exceeds every pixel's
     // second-best cost cannot change any label or queue decision and is skipped.
@@ -268,6 +296,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                      &sm.bar[k]);
         }
     }
+    __syncthreads();  // sm.cref
 
     // per pixel: two smallest packed costs (b1 <= b2) and the scan position of the best
     float b1[P], b2[P];
@@ -285,19 +314,18 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         const int c = chunk_at(k);
         if (ok && !mbar_wait_bounded(&sm.bar[b], uses[b] & 1u, &s.sc->status)) ok = false;
         ++uses[b];
-        // Pruning decision for this chunk's groups (before the transform, which is
-        // skipped when no warp of the CTA scores any of them)
+        // Group bounds of this chunk (lane = group): the cost lower bound over the
+        // warp's pixel box, used to order the groups (nearest first) and to skip
+        // those above every pixel's second-best cost.  The dense sweep takes the
+        // groups in index order.
         const int valid_in_chunk = min(kChunk, n - c * kChunk);
         const int groups = (valid_in_chunk + kGroup - 1) / kGroup;
-        unsigned live = 0xffffffffu;  // groups of this chunk the warp must score
+        const int wid = tid >> 5;
+        unsigned live = (1u << groups) - 1u;  // groups of this chunk the warp may score
         if (s.groups) {
-            float bmax = b2[0];
-#pragma unroll
-            for (int p = 1; p < P; ++p) bmax = fmaxf(bmax, b2[p]);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
-            bool keep = true;
-            if (lane < groups && bmax < FLT_MAX) {
+            const float bmax = warp_max_b2<P>(b2);  // all lanes: it shuffles across the warp
+            bool drop = false;
+            if (lane < groups) {
                 const GroupBound gb = s.groups[c * (kChunk / kGroup) + lane];
                 float d2 = 0.f;
 #pragma unroll
@@ -307,11 +335,14 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                     const float t = fmaxf(fmaxf(gb.lo[a] - hi, lo - gb.hi[a]) - slack, 0.f);
                     d2 = fmaf(t, t, d2);
                 }
-                const float wpart = __double2float_rd(wref - gb.wmax);
-                const float lb = __fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f) + wpart;
-                keep = !(lb > bmax + 1e-6f * (fabsf(bmax) + fabsf(lb) + fabsf(wpart)) + 1e-30f);
+                const float wp = __double2float_rd(sm.cref[3] - gb.wmax);
+                const float lb = __fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f) + wp;
+                sm.glb[wid][lane] = lb;
+                sm.gwp[wid][lane] = wp;
+                drop = group_beyond(lb, wp, bmax);
             }
-            live = __ballot_sync(0xffffffffu, keep) & ((1u << groups) - 1u);
+            live &= ~__ballot_sync(0xffffffffu, drop);
+            __syncwarp();
         }
         const bool need_chunk = s.groups ? (__syncthreads_or(live != 0u) != 0) : true;
         // transform this chunk into the row-form coefficients
@@ -320,11 +351,11 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             float4 v0, v1, v2;
             if (ok && si < n) {
                 const SeedRec &r = sm.raw[b][sl];
-                const float d0 = (float)(c0 - r.x[0]);
-                const float x1p = (float)(r.x[1] - c1);
-                const float wp = (float)(r.w - wref);  // <= 0
+                const float d0 = (float)(sm.cref[0] - r.x[0]);
+                const float x1p = (float)(r.x[1] - sm.cref[1]);
+                const float wp = (float)(r.w - sm.cref[3]);  // <= 0
                 if (D == 3) {
-                    const float x2p = (float)(r.x[2] - c2);
+                    const float x2p = (float)(r.x[2] - sm.cref[2]);
                     const float A00 = r.a[0], A01 = r.a[1], A02 = r.a[2], A11 = r.a[3],
                                 A12 = r.a[4], A22 = r.a[5];
                     v0 = make_float4(x1p, x2p, A11, 2.f * A12);
@@ -359,16 +390,27 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                      &sm.bar[b]);
         }
         if (ok && need_chunk) {
-            if (s.pairs_scored && lane == 0) {
-                const unsigned m = live & ((1u << groups) - 1u);
-                // live groups x 32 seeds, less the padding of a live partial last group
-                unsigned seeds = (unsigned)__popc(m) * kGroup;
-                if (((m >> (groups - 1)) & 1u) && valid_in_chunk < groups * kGroup)
-                    seeds -= (unsigned)(groups * kGroup - valid_in_chunk);
-                atomicAdd(&sm.scored, (unsigned long long)seeds * (unsigned long long)(32 * P));
-            }
-            for (int gr = 0; gr < groups; ++gr) {
-                if (!((live >> gr) & 1u)) continue;
+            while (true) {
+                // drop the groups that the current second-best costs rule out,
+                // then take the remaining one with the smallest bound
+                const bool mine = (live >> lane) & 1u;
+                if (s.groups) {
+                    const float bmax = warp_max_b2<P>(b2);
+                    live &= ~__ballot_sync(0xffffffffu,
+                                           mine && group_beyond(sm.glb[wid][lane], sm.gwp[wid][lane], bmax));
+                }
+                if (!live) break;
+                const bool cand = (live >> lane) & 1u;
+                const unsigned key =
+                    cand ? (s.groups ? sortable_key(sm.glb[wid][lane]) : (unsigned)lane) : 0xffffffffu;
+                const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+                const unsigned pick = __ballot_sync(0xffffffffu, cand && key == kmin);
+                if (!pick) break;  // cannot happen: kmin is a candidate's key
+                const int gr = __ffs(pick) - 1;
+                live &= ~(1u << gr);
+                if (s.pairs_scored && lane == 0)
+                    atomicAdd(&sm.scored, (unsigned long long)min(kGroup, valid_in_chunk - gr * kGroup) *
+                                              (unsigned long long)(32 * P));
                 // fast pass: smallest cost of this group per pixel (one 3-input min per two pairs)
                 float gm[P];
 #pragma unroll
