@@ -114,6 +114,8 @@ struct SharedLayout {
     static constexpr int K = moment_width(D);
     SeedRec raw[2][kChunk];
     float4 phi[D][kChunk];
+    float4 sbd[kChunk];  // per seed of the chunk: x (FP32, nearest) and the lambda_min lower bound
+    float swp[kChunk];   // per seed: wref - w rounded down (the weight part of its cost bound)
     unsigned long long tval[kTable][K];
     int tkey[kTable];
     uint64_t bar[2];
@@ -381,6 +383,11 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             sm.phi[0][sl] = v0;
             sm.phi[1][sl] = v1;
             if (D == 3) sm.phi[2][sl] = v2;
+            if (s.groups && ok && si < n) {
+                const SeedRec &r = sm.raw[b][sl];
+                sm.sbd[sl] = make_float4((float)r.x[0], (float)r.x[1], D == 3 ? (float)r.x[2] : 0.f, r.pad[0]);
+                sm.swp[sl] = __double2float_rd(sm.cref[3] - r.w);
+            }
         }
         // a timed-out wait in any thread stops the whole CTA
         ok = __syncthreads_and(ok);
@@ -394,8 +401,9 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                 // drop the groups that the current second-best costs rule out,
                 // then take the remaining one with the smallest bound
                 const bool mine = (live >> lane) & 1u;
+                float bmax = FLT_MAX;
                 if (s.groups) {
-                    const float bmax = warp_max_b2<P>(b2);
+                    bmax = warp_max_b2<P>(b2);
                     live &= ~__ballot_sync(0xffffffffu,
                                            mine && group_beyond(sm.glb[wid][lane], sm.gwp[wid][lane], bmax));
                 }
@@ -408,15 +416,42 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                 if (!pick) break;  // cannot happen: kmin is a candidate's key
                 const int gr = __ffs(pick) - 1;
                 live &= ~(1u << gr);
+                // Pruned: the seeds of the group whose own bound (lambda_i times the
+                // squared distance from x_i to the warp's pixel box, plus wref - w_i)
+                // is not above every pixel's second-best cost; scored in pairs
+                // (l, l+1), marked at the even bit l.
+                unsigned pm = 0x55555555u;
+                if (s.groups) {
+                    const int sl = gr * kGroup + lane;
+                    bool need_s = false;
+                    if (sl < valid_in_chunk) {
+                        const float4 sb = sm.sbd[sl];
+                        const float wp = sm.swp[sl];
+                        const float xs[3] = {sb.x, sb.y, sb.z};
+                        float d2 = 0.f;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const float lo = sm.wbox[wid][a], hi = sm.wbox[wid][3 + a];
+                            const float slack = 1e-6f * (fabsf(lo) + fabsf(hi) + 2.f * fabsf(xs[a]));
+                            const float t = fmaxf(fmaxf(xs[a] - hi, lo - xs[a]) - slack, 0.f);
+                            d2 = fmaf(t, t, d2);
+                        }
+                        const float lb = __fmul_rd(__fmul_rd(sb.w, d2), 1.f - 1e-5f) + wp;
+                        need_s = !group_beyond(lb, wp, bmax);
+                    }
+                    const unsigned sv = __ballot_sync(0xffffffffu, need_s);
+                    pm = (sv | (sv >> 1)) & 0x55555555u;
+                    if (!pm) continue;
+                }
                 if (s.pairs_scored && lane == 0)
-                    atomicAdd(&sm.scored, (unsigned long long)min(kGroup, valid_in_chunk - gr * kGroup) *
+                    atomicAdd(&sm.scored, (unsigned long long)(s.groups ? 2 * __popc(pm)
+                                                                        : min(kGroup, valid_in_chunk - gr * kGroup)) *
                                               (unsigned long long)(32 * P));
                 // fast pass: smallest cost of this group per pixel (one 3-input min per two pairs)
                 float gm[P];
 #pragma unroll
                 for (int p = 0; p < P; ++p) gm[p] = FLT_MAX;
-#pragma unroll 2
-                for (int l = 0; l < kGroup; l += 2) {
+                auto fast_pair = [&](const int l) {
                     float2 qa, qb, ba, bbb, aa2, ab2;
                     seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
 #pragma unroll
@@ -426,6 +461,12 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                         gm[2 * q] = fmin3(gm[2 * q], ca.x, cb.x);
                         gm[2 * q + 1] = fmin3(gm[2 * q + 1], ca.y, cb.y);
                     }
+                };
+                if (s.groups) {
+                    for (unsigned m = pm; m; m &= m - 1u) fast_pair(__ffs(m) - 1);
+                } else {
+#pragma unroll 2
+                    for (int l = 0; l < kGroup; l += 2) fast_pair(l);
                 }
                 // a packed key differs from its cost by < 32 ulp: a group whose smallest
                 // cost exceeds b2 by the margin cannot change b1 or b2 and is skipped
@@ -435,8 +476,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                 if (!__any_sync(0xffffffffu, need)) continue;
                 // update pass: recompute the same costs, packed top-2 with the index
                 const int gbase = c * kChunk + gr * kGroup;
-#pragma unroll 2
-                for (int l = 0; l < kGroup; l += 2) {
+                auto update_pair = [&](const int l) {
                     float2 qa, qb, ba, bbb, aa2, ab2;
                     seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
                     const unsigned la = (unsigned)l, lb = (unsigned)(l + 1);
@@ -448,6 +488,12 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                         top2_update(b1[2 * q + 1], b2[2 * q + 1], GI[2 * q + 1], pack(ca.y, la),
                                     pack(cb.y, lb), gbase);
                     }
+                };
+                if (s.groups) {
+                    for (unsigned m = pm; m; m &= m - 1u) update_pair(__ffs(m) - 1);
+                } else {
+#pragma unroll 2
+                    for (int l = 0; l < kGroup; l += 2) update_pair(l);
                 }
             }
         }
