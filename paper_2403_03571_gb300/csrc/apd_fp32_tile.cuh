@@ -114,13 +114,14 @@ struct SharedLayout {
     static constexpr int K = moment_width(D);
     SeedRec raw[2][kChunk];
     float4 phi[D][kChunk];
-    float4 sbd[kChunk];  // per seed of the chunk: x (FP32, nearest) and the lambda_min lower bound
-    float swp[kChunk];   // per seed: wref - w rounded down (the weight part of its cost bound)
+    float4 sbd[kChunk];  // per seed of the chunk: offset from the tile centre, lambda_min lower bound
+    float swp[kChunk];   // per seed: a lower bound of wref - w (the weight part of its cost bound)
     unsigned long long tval[kTable][K];
     int tkey[kTable];
     uint64_t bar[2];
     int start_chunk;
-    float wbox[16][6];  // per warp: pixel box lo[3], hi[3] (pruning)
+    float wbox[16][6];  // per warp: pixel box lo[3], hi[3], absolute (pruning)
+    float wrel[16][6];  // per warp: the same box relative to the tile centre
     float glb[16][kChunk / kGroup];  // per warp: cost lower bound of each group of the chunk
     float gwp[16][kChunk / kGroup];  // per warp: the weight part of that bound
     double cref[4];  // tile centre (FP64) and the reference weight wref
@@ -222,13 +223,45 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     const int k2 = k2b + tz;
     const bool row_valid = (k1 < g.res[1]) && (D == 2 || k2 < g.res[2]);
 
-    // CTA reference point (FP64): the tile centre
-    // (kept in shared memory: CTA-uniform, read once per chunk by the transform)
+    const int lane = tid & 31;
+    const int wid = tid >> 5;
+    const int kc0 = k0t + W0 / 2, kc1 = k1b + TY / 2, kc2 = k2b + TZ / 2;  // tile centre pixel
+    // CTA-uniform values, computed by one thread and kept in shared memory: the
+    // tile centre (FP64, the reference point of the row form), the reference
+    // weight, and the first chunk of the scan.  With Morton-sorted seeds the scan
+    // starts at the chunk holding this tile's Morton position and zig-zags
+    // outwards, so that the near seeds (the likely winners) come first.
+    auto chunk_from = [n_chunks](int start, int k) {
+        const int off = (k & 1) ? ((k + 1) >> 1) : -(k >> 1);
+        int c = (start + off) % n_chunks;
+        return c < 0 ? c + n_chunks : c;
+    };
     if (tid == 0) {
-        sm.cref[0] = g.lo[0] + (double)(k0t + W0 / 2) * g.h[0];
-        sm.cref[1] = g.lo[1] + (double)(k1b + TY / 2) * g.h[1];
-        sm.cref[2] = (D == 3) ? g.lo[2] + (double)(k2b + TZ / 2) * g.h[2] : 0.0;
+        sm.cref[0] = g.lo[0] + (double)kc0 * g.h[0];
+        sm.cref[1] = g.lo[1] + (double)kc1 * g.h[1];
+        sm.cref[2] = (D == 3) ? g.lo[2] + (double)kc2 * g.h[2] : 0.0;
         sm.cref[3] = dkey_inv(s.sc->wref_key);
+        int start = 0;
+        if (s.scodes) {
+            double frac[3] = {0.0, 0.0, 0.0};
+            const int kc[3] = {kc0, kc1, kc2};
+#pragma unroll
+            for (int a = 0; a < D; ++a) frac[a] = ((double)kc[a] + 0.5) / (double)g.res[a];
+            const uint32_t code = morton_code(D, frac);
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s.scodes[mid] < code) lo = mid + 1;
+                else hi = mid;
+            }
+            start = min(lo / kChunk, n_chunks - 1);
+        }
+        sm.start_chunk = start;
+        for (int k = 0; k < 2 && k < n_chunks; ++k) {
+            mbar_expect_tx(&sm.bar[k], kChunk * sizeof(SeedRec));
+            bulk_g2s(&sm.raw[k][0], s.recs + (size_t)chunk_from(start, k) * kChunk, kChunk * sizeof(SeedRec),
+                     &sm.bar[k]);
+        }
     }
     const float f1 = ((float)(ty - TY / 2) + 0.5f) * g.h32[1];
     const float f2 = (D == 3) ? ((float)(tz - TZ / 2) + 0.5f) * g.h32[2] : 0.f;
@@ -238,67 +271,31 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         y2[q] = make_float2(((float)(seg * P + 2 * q - W0 / 2) + 0.5f) * g.h32[0],
                             ((float)(seg * P + 2 * q + 1 - W0 / 2) + 0.5f) * g.h32[0]);
 
-    // Scan order of the seed chunks: with Morton-sorted seeds, start at the chunk
-    // holding this tile's Morton position and zig-zag outwards, so that the near
-    // seeds (the likely winners) come first and later groups are mostly skipped.
-    int start_chunk = 0;
-    if (s.scodes) {
-        double frac[3] = {0.0, 0.0, 0.0};
-        const int kc[3] = {k0t + W0 / 2, k1b + TY / 2, k2b + TZ / 2};
-#pragma unroll
-        for (int a = 0; a < D; ++a) frac[a] = ((double)kc[a] + 0.5) / (double)g.res[a];
-        const uint32_t code = morton_code(D, frac);
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s.scodes[mid] < code) lo = mid + 1;
-            else hi = mid;
-        }
-        start_chunk = min(lo / kChunk, n_chunks - 1);
-    }
-    auto chunk_at = [&](int k) {
-        const int off = (k & 1) ? ((k + 1) >> 1) : -(k >> 1);
-        int c = (start_chunk + off) % n_chunks;
-        return c < 0 ? c + n_chunks : c;
-    };
-    // Pruning (optional): the box of this warp's pixels (FP32, rounded outwards);
-    // a seed group whose cost lower bound over the box exceeds every pixel's
-    // second-best cost cannot change any label or queue decision and is skipped.
-    const int lane = tid & 31;
+    // Pruning (optional): the box of this warp's pixel centres, in absolute FP32
+    // coordinates rounded outwards (against the seed-group boxes) and relative to
+    // the tile centre (against the seeds' own offsets from it); a seed or group
+    // whose cost lower bound over the box exceeds every pixel's second-best cost
+    // cannot change any label or queue decision and is skipped.
     if (s.groups) {
-        float wlo[3] = {0.f, 0.f, 0.f}, whi[3] = {0.f, 0.f, 0.f};
-        const double cx[3] = {g.lo[0] + ((double)k0b + 0.5) * g.h[0], g.lo[1] + ((double)k1 + 0.5) * g.h[1],
-                              D == 3 ? g.lo[2] + ((double)k2 + 0.5) * g.h[2] : 0.0};
-        const double ex = (double)(P - 1) * g.h[0];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            wlo[a] = __double2float_rd(cx[a]);
-            whi[a] = __double2float_ru(a == 0 ? cx[0] + ex : cx[a]);
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                wlo[a] = fminf(wlo[a], __shfl_xor_sync(0xffffffffu, wlo[a], off));
-                whi[a] = fmaxf(whi[a], __shfl_xor_sync(0xffffffffu, whi[a], off));
-            }
+        const int klo[3] = {__reduce_min_sync(0xffffffffu, k0b), __reduce_min_sync(0xffffffffu, k1),
+                            __reduce_min_sync(0xffffffffu, k2)};
+        const int khi[3] = {__reduce_max_sync(0xffffffffu, k0b + P - 1), __reduce_max_sync(0xffffffffu, k1),
+                            __reduce_max_sync(0xffffffffu, k2)};
         if (lane == 0) {
+            const int kc[3] = {kc0, kc1, kc2};
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                sm.wbox[tid >> 5][a] = wlo[a];
-                sm.wbox[tid >> 5][3 + a] = whi[a];
+                const bool ax = a < D;
+                sm.wbox[wid][a] = ax ? __double2float_rd(g.lo[a] + ((double)klo[a] + 0.5) * g.h[a]) : 0.f;
+                sm.wbox[wid][3 + a] = ax ? __double2float_ru(g.lo[a] + ((double)khi[a] + 0.5) * g.h[a]) : 0.f;
+                sm.wrel[wid][a] = ax ? ((float)(klo[a] - kc[a]) + 0.5f) * g.h32[a] : 0.f;
+                sm.wrel[wid][3 + a] = ax ? ((float)(khi[a] - kc[a]) + 0.5f) * g.h32[a] : 0.f;
             }
         }
-        __syncwarp();
     }
-    if (tid == 0) {
-        for (int k = 0; k < 2 && k < n_chunks; ++k) {
-            mbar_expect_tx(&sm.bar[k], kChunk * sizeof(SeedRec));
-            bulk_g2s(&sm.raw[k][0], s.recs + (size_t)chunk_at(k) * kChunk, kChunk * sizeof(SeedRec),
-                     &sm.bar[k]);
-        }
-    }
-    __syncthreads();  // sm.cref
+    __syncthreads();  // sm.cref, sm.start_chunk, sm.wbox, sm.wrel
+    const int start_chunk = sm.start_chunk;
+    auto chunk_at = [&](int k) { return chunk_from(start_chunk, k); };
 
     // per pixel: two smallest packed costs (b1 <= b2) and the scan position of the best
     float b1[P], b2[P];
@@ -322,7 +319,6 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         // groups in index order.
         const int valid_in_chunk = min(kChunk, n - c * kChunk);
         const int groups = (valid_in_chunk + kGroup - 1) / kGroup;
-        const int wid = tid >> 5;
         unsigned live = (1u << groups) - 1u;  // groups of this chunk the warp may score
         if (s.groups) {
             const float bmax = warp_max_b2<P>(b2);  // all lanes: it shuffles across the warp
@@ -351,13 +347,19 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         for (int sl = need_chunk ? tid : kChunk; sl < kChunk; sl += NT) {
             const int si = c * kChunk + sl;
             float4 v0, v1, v2;
+            // pruning data: the seed's offset from the tile centre (FP32 of the FP64
+            // difference), its lambda_min lower bound, and a lower bound of wref - w
+            float4 bd = make_float4(0.f, 0.f, 0.f, 0.f);
+            float bw = 0.f;
             if (ok && si < n) {
                 const SeedRec &r = sm.raw[b][sl];
                 const float d0 = (float)(sm.cref[0] - r.x[0]);
                 const float x1p = (float)(r.x[1] - sm.cref[1]);
+                const float x2p = (D == 3) ? (float)(r.x[2] - sm.cref[2]) : 0.f;
                 const float wp = (float)(r.w - sm.cref[3]);  // <= 0
+                bd = make_float4(-d0, x1p, x2p, r.pad[0]);
+                bw = __fmul_rd(-wp, 1.f - 0x1p-23f);  // rounding of wp is below 2^-24 relative
                 if (D == 3) {
-                    const float x2p = (float)(r.x[2] - sm.cref[2]);
                     const float A00 = r.a[0], A01 = r.a[1], A02 = r.a[2], A11 = r.a[3],
                                 A12 = r.a[4], A22 = r.a[5];
                     v0 = make_float4(x1p, x2p, A11, 2.f * A12);
@@ -383,10 +385,9 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             sm.phi[0][sl] = v0;
             sm.phi[1][sl] = v1;
             if (D == 3) sm.phi[2][sl] = v2;
-            if (s.groups && ok && si < n) {
-                const SeedRec &r = sm.raw[b][sl];
-                sm.sbd[sl] = make_float4((float)r.x[0], (float)r.x[1], D == 3 ? (float)r.x[2] : 0.f, r.pad[0]);
-                sm.swp[sl] = __double2float_rd(sm.cref[3] - r.w);
+            if (s.groups) {
+                sm.sbd[sl] = bd;
+                sm.swp[sl] = bw;
             }
         }
         // a timed-out wait in any thread stops the whole CTA
@@ -408,74 +409,18 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                                            mine && group_beyond(sm.glb[wid][lane], sm.gwp[wid][lane], bmax));
                 }
                 if (!live) break;
-                const bool cand = (live >> lane) & 1u;
-                const unsigned key =
-                    cand ? (s.groups ? sortable_key(sm.glb[wid][lane]) : (unsigned)lane) : 0xffffffffu;
-                const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
-                const unsigned pick = __ballot_sync(0xffffffffu, cand && key == kmin);
-                if (!pick) break;  // cannot happen: kmin is a candidate's key
+                unsigned pick = live;  // dense: index order
+                if (s.groups) {
+                    const bool cand = (live >> lane) & 1u;
+                    const unsigned key = cand ? sortable_key(sm.glb[wid][lane]) : 0xffffffffu;
+                    const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+                    pick = __ballot_sync(0xffffffffu, cand && key == kmin);
+                    if (!pick) break;  // cannot happen: kmin is a candidate's key
+                }
                 const int gr = __ffs(pick) - 1;
                 live &= ~(1u << gr);
-                // Pruned: the seeds of the group whose own bound (lambda_i times the
-                // squared distance from x_i to the warp's pixel box, plus wref - w_i)
-                // is not above every pixel's second-best cost; scored in pairs
-                // (l, l+1), marked at the even bit l.
-                unsigned pm = 0x55555555u;
-                if (s.groups) {
-                    const int sl = gr * kGroup + lane;
-                    bool need_s = false;
-                    if (sl < valid_in_chunk) {
-                        const float4 sb = sm.sbd[sl];
-                        const float wp = sm.swp[sl];
-                        const float xs[3] = {sb.x, sb.y, sb.z};
-                        float d2 = 0.f;
-#pragma unroll
-                        for (int a = 0; a < D; ++a) {
-                            const float lo = sm.wbox[wid][a], hi = sm.wbox[wid][3 + a];
-                            const float slack = 1e-6f * (fabsf(lo) + fabsf(hi) + 2.f * fabsf(xs[a]));
-                            const float t = fmaxf(fmaxf(xs[a] - hi, lo - xs[a]) - slack, 0.f);
-                            d2 = fmaf(t, t, d2);
-                        }
-                        const float lb = __fmul_rd(__fmul_rd(sb.w, d2), 1.f - 1e-5f) + wp;
-                        need_s = !group_beyond(lb, wp, bmax);
-                    }
-                    const unsigned sv = __ballot_sync(0xffffffffu, need_s);
-                    pm = (sv | (sv >> 1)) & 0x55555555u;
-                    if (!pm) continue;
-                }
-                if (s.pairs_scored && lane == 0)
-                    atomicAdd(&sm.scored, (unsigned long long)(s.groups ? 2 * __popc(pm)
-                                                                        : min(kGroup, valid_in_chunk - gr * kGroup)) *
-                                              (unsigned long long)(32 * P));
-                // fast pass: smallest cost of this group per pixel (one 3-input min per two pairs)
-                float gm[P];
-#pragma unroll
-                for (int p = 0; p < P; ++p) gm[p] = FLT_MAX;
-                auto fast_pair = [&](const int l) {
-                    float2 qa, qb, ba, bbb, aa2, ab2;
-                    seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
-#pragma unroll
-                    for (int q = 0; q < P / 2; ++q) {
-                        const float2 ca = ffma2(ffma2(qa, y2[q], ba), y2[q], aa2);
-                        const float2 cb = ffma2(ffma2(qb, y2[q], bbb), y2[q], ab2);
-                        gm[2 * q] = fmin3(gm[2 * q], ca.x, cb.x);
-                        gm[2 * q + 1] = fmin3(gm[2 * q + 1], ca.y, cb.y);
-                    }
-                };
-                if (s.groups) {
-                    for (unsigned m = pm; m; m &= m - 1u) fast_pair(__ffs(m) - 1);
-                } else {
-#pragma unroll 2
-                    for (int l = 0; l < kGroup; l += 2) fast_pair(l);
-                }
-                // a packed key differs from its cost by < 32 ulp: a group whose smallest
-                // cost exceeds b2 by the margin cannot change b1 or b2 and is skipped
-                bool need = false;
-#pragma unroll
-                for (int p = 0; p < P; ++p) need |= gm[p] < fmaf(fabsf(b2[p]), 0x1p-15f, b2[p]);
-                if (!__any_sync(0xffffffffu, need)) continue;
-                // update pass: recompute the same costs, packed top-2 with the index
                 const int gbase = c * kChunk + gr * kGroup;
+                // exact top-2 update of every pixel with the seed pair (l, l+1)
                 auto update_pair = [&](const int l) {
                     float2 qa, qb, ba, bbb, aa2, ab2;
                     seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
@@ -490,11 +435,75 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                     }
                 };
                 if (s.groups) {
+                    // Pruned: the seeds of the group whose own bound (lambda_i times the
+                    // squared distance from x_i to the warp's pixel box, plus wref - w_i)
+                    // is not above every pixel's second-best cost, scored in pairs
+                    // (l, l+1) (marked at the even bit l) by the exact update directly:
+                    // nearly every such pair changes some pixel's top-2.
+                    const int sl = gr * kGroup + lane;
+                    const bool real = sl < valid_in_chunk;
+                    float slb = FLT_MAX, swp = 0.f;
+                    if (real) {
+                        const float4 sb = sm.sbd[sl];
+                        swp = sm.swp[sl];
+                        const float xs[3] = {sb.x, sb.y, sb.z};
+                        float d2 = 0.f;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const float lo = sm.wrel[wid][a], hi = sm.wrel[wid][3 + a];
+                            const float slack = 1e-6f * (fabsf(lo) + fabsf(hi) + 2.f * fabsf(xs[a]));
+                            const float t = fmaxf(fmaxf(xs[a] - hi, lo - xs[a]) - slack, 0.f);
+                            d2 = fmaf(t, t, d2);
+                        }
+                        slb = __fmul_rd(__fmul_rd(sb.w, d2), 1.f - 1e-5f) + swp;
+                    }
+                    unsigned done = 0u;
+                    if (!(bmax < FLT_MAX)) {
+                        // first group of the tile: the pair holding the seed of smallest
+                        // bound goes first, so that the rest is tested against real costs
+                        const unsigned key = real ? sortable_key(slb) : 0xffffffffu;
+                        const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+                        const int j = (__ffs(__ballot_sync(0xffffffffu, key == kmin)) - 1) & ~1;
+                        update_pair(j);
+                        done = 1u << j;
+                        bmax = warp_max_b2<P>(b2);
+                    }
+                    const unsigned sv = __ballot_sync(0xffffffffu, real && !group_beyond(slb, swp, bmax));
+                    const unsigned pm = (sv | (sv >> 1)) & 0x55555555u & ~done;
+                    if (s.pairs_scored && lane == 0)
+                        atomicAdd(&sm.scored, (unsigned long long)(2 * __popc(pm | done)) *
+                                                  (unsigned long long)(32 * P));
                     for (unsigned m = pm; m; m &= m - 1u) update_pair(__ffs(m) - 1);
-                } else {
-#pragma unroll 2
-                    for (int l = 0; l < kGroup; l += 2) update_pair(l);
+                    continue;
                 }
+                if (s.pairs_scored && lane == 0)
+                    atomicAdd(&sm.scored, (unsigned long long)min(kGroup, valid_in_chunk - gr * kGroup) *
+                                              (unsigned long long)(32 * P));
+                // dense: fast pass (smallest cost of this group per pixel, one 3-input
+                // min per two pairs), then the update pass only where it can matter
+                float gm[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) gm[p] = FLT_MAX;
+#pragma unroll 2
+                for (int l = 0; l < kGroup; l += 2) {
+                    float2 qa, qb, ba, bbb, aa2, ab2;
+                    seed_pair_coeffs<D>(sm.phi, gr * kGroup + l, f1, f2, qa, qb, ba, bbb, aa2, ab2);
+#pragma unroll
+                    for (int q = 0; q < P / 2; ++q) {
+                        const float2 ca = ffma2(ffma2(qa, y2[q], ba), y2[q], aa2);
+                        const float2 cb = ffma2(ffma2(qb, y2[q], bbb), y2[q], ab2);
+                        gm[2 * q] = fmin3(gm[2 * q], ca.x, cb.x);
+                        gm[2 * q + 1] = fmin3(gm[2 * q + 1], ca.y, cb.y);
+                    }
+                }
+                // a packed key differs from its cost by < 32 ulp: a group whose smallest
+                // cost exceeds b2 by the margin cannot change b1 or b2 and is skipped
+                bool need = false;
+#pragma unroll
+                for (int p = 0; p < P; ++p) need |= gm[p] < fmaf(fabsf(b2[p]), 0x1p-15f, b2[p]);
+                if (!__any_sync(0xffffffffu, need)) continue;
+#pragma unroll 2
+                for (int l = 0; l < kGroup; l += 2) update_pair(l);
             }
         }
         __syncthreads();
