@@ -118,9 +118,19 @@ cudaError_t launch_assign_fp32(const GridDev &g, int n, Workspace &ws, int32_t *
 cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,
                                 const double *w, Workspace &ws, int32_t *labels,
                                 unsigned long long *moments, cudaStream_t st) {
-    int dev_sms = 152;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ws.device);
-    const int blocks = dev_sms * 2;
+    // one warp per queued pixel, latency-bound (dependent record loads): as many
+    // resident warps as the registers allow
+    static int blocks_per_sm[2] = {0, 0}, dev_sms = 0;
+    int &bps = blocks_per_sm[g.dim == 3 ? 1 : 0];
+    if (!dev_sms && cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ws.device) != cudaSuccess)
+        dev_sms = 152;
+    if (!bps) {
+        const cudaError_t e = g.dim == 3
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rescore_kernel<3>, 256, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rescore_kernel<2>, 256, 0);
+        if (e != cudaSuccess || bps < 1) bps = 2;
+    }
+    const int blocks = dev_sms * bps;
     RescorePrune pr{nullptr, nullptr, nullptr, 0, 0.0};
     if (ws.groups && (!ws.sorted || ws.recs32s)) {
         pr.groups = ws.groups;

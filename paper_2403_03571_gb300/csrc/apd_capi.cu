@@ -92,13 +92,18 @@ int cuda_ok(cudaError_t e) { return e == cudaSuccess ? APD_OK : APD_ERR_CUDA; }
 // Algorithm 1 + moments (+ FP64 rescoring of near ties) on `st`.
 int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, const double *w,
                    apd_precision prec, Workspace &ws, int32_t *labels, unsigned long long *mom,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool weights_only = false) {
     if (prec != APD_FP32 && prec != APD_TC_TF32 && prec != APD_TC_BF16) return APD_ERR_UNSUPPORTED;
     const size_t K = (size_t)moment_width(g.dim);
     APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
-    APD_TRY(cuda_ok(launch_eval_reset(ws, st)));
-    APD_TRY(cuda_ok(launch_seed_prep(g, n, x, A, w, ws, st)));
-    APD_TRY(cuda_ok(launch_group_bounds(n, ws, st)));
+    APD_TRY(cuda_ok(launch_eval_reset(ws, st, weights_only)));
+    if (weights_only) {
+        // positions and matrices as in the previous pass: only the weights change
+        APD_TRY(cuda_ok(launch_weights_prep(n, w, ws, st)));
+    } else {
+        APD_TRY(cuda_ok(launch_seed_prep(g, n, x, A, w, ws, st)));
+        APD_TRY(cuda_ok(launch_group_bounds(n, ws, st)));
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ws.profiling) {
         while (ws.ev.size() < ws.ev_used + 2) {
@@ -120,7 +125,8 @@ int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, co
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
     if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
     APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
-    ws.kernel_launches += (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 2);
+    ws.kernel_launches += weights_only ? 4 + (prec == APD_FP32 ? 0 : 2)
+                                       : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 2);
     ws.last_pixels = g.J;
     ws.last_pairs = g.J * (long long)n;
     return APD_OK;
@@ -159,13 +165,16 @@ struct Solver {
     const double *last_point = nullptr;  // device pointer evaluated last
     bool last_is_best = false;
     bool first = true;
+    bool geometry_ready = false;  // records of x, A built (they are fixed for the solve)
 
     Solver(Workspace &w) : ws(w) {}
 
     // Evaluate at Wp; gf_out receives grad f = -(v - |P| m); pdir (nullable) for <grad f, p>.
     int eval(const double *Wp, double *gf_out, const double *pdir, double &f, double &dphi,
              double &err) {
-        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, st));
+        // the records' positions and matrices are built once per solve
+        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, st, geometry_ready));
+        geometry_ready = true;
         APD_TRY(cuda_ok(launch_dual(g, n, x, A, Wp, v, pdir, ws.moments, ws, nullptr, ws.grad, gf_out,
                                     nullptr, st)));
         ws.kernel_launches += 1;

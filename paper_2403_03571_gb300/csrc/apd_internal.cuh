@@ -248,7 +248,9 @@ int warmstart_dim(const apd_mlp *net);               // dimension of a warm-star
 constexpr int moment_width(int dim) { return 1 + dim + dim * (dim + 1) / 2; }
 
 // zero the per-evaluation counters and statistics in sc
-cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st);
+cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry = false);
+// new weights into the records of the last launch_seed_prep (same x, A, n)
+cudaError_t launch_weights_prep(int n, const double *w, Workspace &ws, cudaStream_t st);
 // seed records (FP64 x, w; FP32 symmetric A) + stats (max w, max ||A||_F, min lambda bound)
 cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const double *A,
                              const double *w, Workspace &ws, cudaStream_t st);

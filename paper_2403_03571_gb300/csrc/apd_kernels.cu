@@ -11,12 +11,49 @@ namespace {
 
 constexpr int kRedThreads = 1024;
 
-__global__ void eval_reset_kernel(DevScalars *sc) {
+__global__ void eval_reset_kernel(DevScalars *sc, const int keep_geometry) {
     sc->flag_count = 0u;
     sc->wref_key = 0ull;
-    sc->lam_abs_bits = 0ull;
-    sc->lam_min_bits = 0x7ff0000000000000ull;
     sc->dual_done = 0u;
+    if (!keep_geometry) {
+        sc->lam_abs_bits = 0ull;
+        sc->lam_min_bits = 0x7ff0000000000000ull;
+    }
+}
+
+// New weights for records whose positions and matrices are unchanged: the
+// weight fields of the scored records (scan order), of both rescoring record
+// arrays, the reference weight wref = max w, and the groups' largest weight.
+// One thread per scan position; a warp covers one 32-seed group.
+__global__ void weights_prep_kernel(const int n, const int n_pad, const double *__restrict__ w,
+                                    const int32_t *__restrict__ perm, SeedRec *__restrict__ recs,
+                                    SeedRec32 *__restrict__ recs32, SeedRec32 *__restrict__ recs32s,
+                                    GroupBound *__restrict__ groups, DevScalars *__restrict__ sc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int src = i < n_pad ? (perm ? perm[i] : i) : n;
+    const bool real = src < n;
+    double wkey = -DBL_MAX;
+    if (real) {
+        const double wi = w[src];
+        const bool finite = isfinite(wi);
+        if (!finite) atomicOr(&sc->status, ST_NONFINITE);
+        recs[i].w = wi;
+        float wh, wl;
+        split_f32(wi, wh, wl);
+        recs32[src].wh = wh;
+        recs32[src].wl = wl;
+        if (recs32s) {
+            recs32s[i].wh = wh;
+            recs32s[i].wl = wl;
+        }
+        wkey = finite ? wi : -DBL_MAX;
+    }
+    const double wmax = warp_max(wkey);
+    const bool any = __any_sync(0xffffffffu, real);
+    if ((threadIdx.x & 31) == 0 && any) {
+        atomicMax(&sc->wref_key, dkey(wmax));
+        if (groups) groups[i >> 5].wmax = wmax;
+    }
 }
 
 template <int D>
@@ -258,8 +295,16 @@ __global__ void __launch_bounds__(kRedThreads)
 
 }  // namespace
 
-cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st) {
-    eval_reset_kernel<<<1, 1, 0, st>>>(ws.sc);
+cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry) {
+    eval_reset_kernel<<<1, 1, 0, st>>>(ws.sc, keep_geometry ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights_prep(int n, const double *w, Workspace &ws, cudaStream_t st) {
+    const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
+    weights_prep_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, w, ws.sorted ? ws.perm : nullptr, ws.recs,
+                                                             ws.recs32, ws.sorted ? ws.recs32s : nullptr,
+                                                             ws.groups, ws.sc);
     return cudaGetLastError();
 }
 
