@@ -511,7 +511,7 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     w.n_pad_max = ((max_n + kChunk - 1) / kChunk) * kChunk;
     w.hist_cap = kHistCap;
     const size_t K = (size_t)moment_width(dim);
-    const size_t nb = (size_t)((max_n + 255) / 256);
+    const size_t nb = std::max<size_t>((size_t)((max_n + 255) / 256), 64);  // dual partials (launch_dual)
     bool ok = true;
     auto alloc = [&](void **p, size_t bytes) {
         if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;

@@ -350,13 +350,16 @@ cudaError_t launch_dual(const GridDev &g, int n, const double *x, const double *
                         const double *v, const double *p_dir, const unsigned long long *moments,
                         Workspace &ws, double *g_out, double *grad_out, double *gf_out,
                         double *err_out, cudaStream_t st) {
-    const int blocks = (n + 255) / 256;
+    // one thread per cell, FP64: small problems spread over more SMs (at most 64
+    // blocks of 64, the workspace's minimum partials count)
+    const int threads = n <= 4096 ? 64 : 256;
+    const int blocks = (n + threads - 1) / threads;
     if (g.dim == 3)
-        dual_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
-                                               grad_out, gf_out, err_out);
+        dual_kernel<3><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
+                                                   grad_out, gf_out, err_out);
     else
-        dual_kernel<2><<<blocks, 256, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
-                                               grad_out, gf_out, err_out);
+        dual_kernel<2><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
+                                                   grad_out, gf_out, err_out);
     return cudaGetLastError();
 }
 
