@@ -77,10 +77,8 @@ __global__ void __launch_bounds__(256)
     const double wref = dkey_inv(sc->wref_key);
     const float wrh = (float)wref;
     const float wrl = (float)(wref - (double)wrh);
-    RescorePrune p = pr;
-    p.wref = wref;
     for (unsigned it = warp; it < count; it += nwarps)
-        rescore_pixel<D>(g, n, x, A, w, r32, flags[it], flag_gi ? flag_gi[it] : -1, wrh, wrl, p, sc, gmom, labels);
+        rescore_pixel<D>(g, n, x, A, w, r32, flags[it], flag_gi ? flag_gi[it] : -1, wrh, wrl, pr, sc, gmom, labels);
 }
 
 template <int D>
@@ -131,7 +129,7 @@ cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const 
         if (e != cudaSuccess || bps < 1) bps = 2;
     }
     const int blocks = dev_sms * bps;
-    RescorePrune pr{nullptr, nullptr, nullptr, 0, 0.0};
+    RescorePrune pr{nullptr, nullptr, nullptr, 0};
     if (ws.groups && (!ws.sorted || ws.recs32s)) {
         pr.groups = ws.groups;
         pr.r32s = ws.sorted ? ws.recs32s : ws.recs32;

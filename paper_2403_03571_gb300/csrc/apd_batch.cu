@@ -243,7 +243,6 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
     }
     if (I.sorted) {
         int m = 1;
-    while (m < n_pad) m <<= 1;
         while (m < n_pad) m <<= 1;
         for (int i = n_pad + threadIdx.x; i < m; i += blockDim.x) keys[i] = ~0ull - (unsigned long long)i;
         __syncthreads();
@@ -261,7 +260,7 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
     __syncthreads();
     const int ngroups = (n + 31) / 32;
     for (int grp = threadIdx.x >> 5; grp < ngroups; grp += blockDim.x >> 5)
-        group_bound_warp<D>(a.recs + I.rec_off, n, grp, a.groups + I.rec_off / 32);
+        group_bound_warp<D>(a.recs + I.rec_off, n, grp, a.groups + I.rec_off / 32, shw[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,7 +355,7 @@ __global__ void __launch_bounds__(256) batch_rescore_kernel(const __grid_constan
             const float wrh = (float)wref;
             const float wrl = (float)(wref - (double)wrh);
             const RescorePrune pr{a.groups + I.rec_off / 32, a.recs32s + I.rec_off,
-                                  I.sorted ? a.perm + I.rec_off : nullptr, (I.n + 31) / 32, wref};
+                                  I.sorted ? a.perm + I.rec_off : nullptr, (I.n + 31) / 32};
             rescore_pixel<D>(I.g, I.n, a.x + I.seed_off * D, a.A + I.seed_off * D * D, a.Wt + I.seed_off,
                              a.recs32 + I.rec_off, a.flags[I.flag_off + local], a.flag_gi[I.flag_off + local], wrh,
                              wrl, pr, sc, a.mom + I.seed_off * K, nullptr);

@@ -179,7 +179,7 @@ __device__ __forceinline__ void build_seed(const int i, const int n, const doubl
 // computed by one warp and written by lane 0.
 template <int D>
 __device__ __forceinline__ void group_bound_warp(const SeedRec *__restrict__ recs, const int n, const int grp,
-                                                 GroupBound *__restrict__ out) {
+                                                 GroupBound *__restrict__ out, const double wref) {
     const int lane = threadIdx.x & 31;
     const int pos = grp * 32 + lane;
     const bool real = pos < n;
@@ -210,7 +210,7 @@ __device__ __forceinline__ void group_bound_warp(const SeedRec *__restrict__ rec
             gb.hi[a] = hi[a];
         }
         gb.lam = lam;
-        gb.pad = 0.f;
+        gb.wgap = __double2float_rd(wref - wm);
         gb.wmax = wm;
         out[grp] = gb;
     }

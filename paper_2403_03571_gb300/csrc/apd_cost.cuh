@@ -161,7 +161,6 @@ struct RescorePrune {
     const SeedRec32 *r32s;      // [n_groups * 32] records in scan order
     const int32_t *perm;        // scan position -> seed index (null: identity)
     int n_groups;
-    double wref;
 };
 
 template <int D>
@@ -175,15 +174,31 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
     const long long j = (long long)fj;
     int k[3] = {0, 0, 0};
     long long rr = j;
-    double y[D];
-    float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         k[a] = (int)(rr % g.res[a]);
         rr /= g.res[a];
-        y[a] = __dadd_rn(g.lo[a], __dmul_rn((double)k[a] + 0.5, g.h[a]));
-        yh[a] = (float)y[a];
-        yl[a] = (float)(y[a] - (double)yh[a]);
+    }
+    // the pixel centre (FP64) and its FP32 split: lane a computes axis a
+    double y[D];
+    float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
+    {
+        double ya = 0.0;
+        float yha = 0.f, yla = 0.f;
+        if (lane < D) {
+            const int ka = lane == 0 ? k[0] : (lane == 1 ? k[1] : k[2]);
+            const double loa = lane == 0 ? g.lo[0] : (lane == 1 ? g.lo[1] : g.lo[D - 1]);
+            const double ha = lane == 0 ? g.h[0] : (lane == 1 ? g.h[1] : g.h[D - 1]);
+            ya = __dadd_rn(loa, __dmul_rn((double)ka + 0.5, ha));
+            yha = (float)ya;
+            yla = (float)(ya - (double)yha);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            y[a] = __shfl_sync(0xffffffffu, ya, a);
+            yh[a] = __shfl_sync(0xffffffffu, yha, a);
+            yl[a] = __shfl_sync(0xffffffffu, yla, a);
+        }
     }
     double best = __longlong_as_double(0x7ff0000000000000ll);
     int bi = 0x7fffffff;
@@ -206,7 +221,7 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
                     const float t = fmaxf(fmaxf(gb.lo[a] - yh[a], yh[a] - gb.hi[a]) - slack, 0.f);
                     d2 = fmaf(t, t, d2);
                 }
-                const float wpart = __double2float_rd(pr.wref - gb.wmax);
+                const float wpart = gb.wgap;
                 const float lb = __fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f) + wpart;
                 keep = !(lb > thr + 1e-6f * (fabsf(thr) + fabsf(lb) + fabsf(wpart)) + 1e-30f);
             }

@@ -333,7 +333,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
                     const float t = fmaxf(fmaxf(gb.lo[a] - hi, lo - gb.hi[a]) - slack, 0.f);
                     d2 = fmaf(t, t, d2);
                 }
-                const float wp = __double2float_rd(sm.cref[3] - gb.wmax);
+                const float wp = gb.wgap;
                 const float lb = __fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f) + wp;
                 sm.glb[wid][lane] = lb;
                 sm.gwp[wid][lane] = wp;

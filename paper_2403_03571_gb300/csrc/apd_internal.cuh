@@ -43,12 +43,13 @@ struct __align__(16) SeedRec32 {
 static_assert(sizeof(SeedRec32) == 64, "SeedRec32 must be 64 bytes");
 
 // Bounds of a group of 32 consecutive seeds (scan order) for pruning the
-// near-tie rescoring: FP32 box of the positions (rounded outwards), a lower
-// bound of lambda_min over the group, and the largest weight.
+// scoring and the near-tie rescoring: FP32 box of the positions (rounded
+// outwards), a lower bound of lambda_min over the group, the largest weight,
+// and wref - wmax rounded down (wref = the largest weight of all seeds).
 struct __align__(8) GroupBound {
     float lo[3], hi[3];
     float lam;
-    float pad;
+    float wgap;
     double wmax;
 };
 static_assert(sizeof(GroupBound) == 40, "GroupBound must be 40 bytes");

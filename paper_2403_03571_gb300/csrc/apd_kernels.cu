@@ -54,6 +54,24 @@ __global__ void weights_prep_kernel(const int n, const int n_pad, const double *
         atomicMax(&sc->wref_key, dkey(wmax));
         if (groups) groups[i >> 5].wmax = wmax;
     }
+    if (!groups) return;
+    __threadfence();  // this thread's group write before the block's arrival count
+    // the last block to finish has the final wref: the groups' weight gaps
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&sc->dual_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double wref = dkey_inv(*(volatile unsigned long long *)&sc->wref_key);
+    for (int gidx = threadIdx.x; gidx * 32 < n; gidx += blockDim.x) {
+        const double wm = *(volatile double *)&groups[gidx].wmax;
+        groups[gidx].wgap = __double2float_rd(wref - wm);
+    }
+    if (threadIdx.x == 0) sc->dual_done = 0u;
 }
 
 template <int D>
@@ -106,9 +124,10 @@ __global__ void __launch_bounds__(1024)
 }
 
 template <int D>
-__global__ void group_bounds_kernel(const int n, const SeedRec *__restrict__ recs, GroupBound *__restrict__ groups) {
+__global__ void group_bounds_kernel(const int n, const SeedRec *__restrict__ recs, GroupBound *__restrict__ groups,
+                                    const DevScalars *__restrict__ sc) {
     const int grp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (grp * 32 < n) group_bound_warp<D>(recs, n, grp, groups);
+    if (grp * 32 < n) group_bound_warp<D>(recs, n, grp, groups, dkey_inv(sc->wref_key));
 }
 
 __global__ void gather_recs_kernel(const int n_pad, const int32_t *__restrict__ perm,
@@ -341,8 +360,8 @@ cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st) {
     if (!ws.groups) return cudaSuccess;
     const int groups = (n + 31) / 32;
     const int blocks = (groups * 32 + 255) / 256;
-    if (ws.dim == 3) group_bounds_kernel<3><<<blocks, 256, 0, st>>>(n, ws.recs, ws.groups);
-    else group_bounds_kernel<2><<<blocks, 256, 0, st>>>(n, ws.recs, ws.groups);
+    if (ws.dim == 3) group_bounds_kernel<3><<<blocks, 256, 0, st>>>(n, ws.recs, ws.groups, ws.sc);
+    else group_bounds_kernel<2><<<blocks, 256, 0, st>>>(n, ws.recs, ws.groups, ws.sc);
     return cudaGetLastError();
 }
 
