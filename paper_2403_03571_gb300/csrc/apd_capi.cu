@@ -211,12 +211,17 @@ struct Solver {
         return APD_OK;
     }
 
-    enum LsResult { LS_ACCEPT, LS_CONVERGED, LS_FAIL, LS_BUDGET };
+    enum LsResult { LS_ACCEPT, LS_CONVERGED, LS_FAIL, LS_BUDGET, LS_NOT_DESCENT };
 
     // phi(t) = f(W + t p); on LS_ACCEPT ws.Wt / ws.gft hold the accepted point.
-    int line_search(double f0, double dphi0, double t_init, LsResult &res, double &f_acc) {
+    // The direction kernel's <grad f, p> (phi'(0)) arrives with the first
+    // evaluation's scalars, so the direction needs no read of its own; a
+    // direction that is not a descent direction ends the search (LS_NOT_DESCENT)
+    // unless that first point has already converged.
+    int line_search(double f0, double t_init, LsResult &res, double &f_acc) {
         const double c1 = 1e-4, c2 = 0.9;
-        double t_prev = 0.0, phi_prev = f0, dphi_prev = dphi0;
+        double dphi0 = 0.0;
+        double t_prev = 0.0, phi_prev = f0, dphi_prev = 0.0;
         double t = t_init;
         double best_t = 0.0, best_phi = f0;
         double cur_t = -1.0;  // t at which Wt/gft were last evaluated
@@ -302,6 +307,14 @@ struct Solver {
                 res = LS_CONVERGED;
                 return APD_OK;
             }
+            if (i == 0) {
+                dphi0 = ws.sc_host->gp0;
+                dphi_prev = dphi0;
+                if (!(dphi0 < 0.0)) {
+                    res = LS_NOT_DESCENT;
+                    return APD_OK;
+                }
+            }
             if (phi > f0 + c1 * t * dphi0 || (i > 0 && phi >= phi_prev))
                 return zoom(t_prev, phi_prev, dphi_prev, t, phi, dphi);
             if (phi < best_phi) {
@@ -364,24 +377,22 @@ struct Solver {
     }
 
     // L-BFGS iterations from the evaluated point ws.W (gradient ws.gf, f0 = f(ws.W)).
+    // The direction, the trial point and its evaluation are queued back to back
+    // and read once; a pair pushed after an accepted step is taken or dropped by
+    // the device (its curvature test) and the host learns which at that read.
     int iterate(double f0, double *out, bool &converged) {
         int hist = 0, newest = kHistCap - 1;
         double gamma = 1.0;
         int fails = 0;
+        bool pending = false;  // a pushed pair whose test result is not read yet
+        int p_slot = 0;
         while (evals < max_evals) {
-            APD_TRY(cuda_ok(launch_lbfgs_direction(n, hist, newest, kHistCap, gamma, ws, st)));
+            const int hist_acc = std::min(hist + 1, history);
+            APD_TRY(cuda_ok(launch_lbfgs_direction(n, hist, newest, kHistCap, gamma, pending, hist_acc, p_slot,
+                                                   ws, st)));
             ws.kernel_launches += 1;
-            APD_TRY(cuda_ok(cudaMemcpyAsync(ws.sc_host, ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st)));
-            APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
-            double gp0 = ws.sc_host->gp0;
-            if (!(gp0 < 0.0)) {
-                if (hist == 0) break;
-                hist = 0;
-                gamma = 1.0;
-                continue;
-            }
             double t0 = 1.0;
-            if (hist == 0) {
+            if (!pending && hist == 0) {
                 // first step (or after a reset): p = -grad f; take t0 ~ 1 / H_ii with the
                 // cell-volume sensitivity H_ii ~ D V^(1 - 2/D) of a cell of volume V = |Omega| / n
                 const double V = measure / (double)n;
@@ -389,7 +400,22 @@ struct Solver {
             }
             LsResult res;
             double f_acc = f0;
-            APD_TRY(line_search(f0, gp0, t0, res, f_acc));
+            const int evals_before = evals;
+            APD_TRY(line_search(f0, t0, res, f_acc));
+            if (pending && evals > evals_before) {
+                if (ws.sc_host->pair_ok) {
+                    newest = p_slot;
+                    hist = hist_acc;
+                    gamma = ws.sc_host->sy / ws.sc_host->yy;
+                }
+                pending = false;
+            }
+            if (res == LS_NOT_DESCENT) {
+                if (hist == 0) break;
+                hist = 0;
+                gamma = 1.0;
+                continue;
+            }
             if (res == LS_CONVERGED) {
                 converged = true;
                 ++iters;
@@ -407,14 +433,8 @@ struct Solver {
             const int slot = (newest + 1) % kHistCap;
             APD_TRY(cuda_ok(launch_lbfgs_push(n, slot, ws, st)));
             ws.kernel_launches += 1;
-            APD_TRY(cuda_ok(cudaMemcpyAsync(ws.sc_host, ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st)));
-            APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
-            const double sy = ws.sc_host->sy, yy = ws.sc_host->yy, ss = ws.sc_host->ss;
-            if (sy > 1e-12 * std::sqrt(ss * yy) && yy > 0.0) {
-                newest = slot;
-                hist = std::min(hist + 1, history);
-                gamma = sy / yy;
-            }
+            pending = true;
+            p_slot = slot;
             std::swap(ws.W, ws.Wt);
             std::swap(ws.gf, ws.gft);
             f0 = f_acc;

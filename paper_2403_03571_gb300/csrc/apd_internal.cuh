@@ -74,7 +74,7 @@ struct DevScalars {
     double sy, yy, ss;                  // L-BFGS curvature pair products
     double gp0;                         // <grad f, p> at the start of a line search
     unsigned int dual_done;             // block counter of the two-phase dual reduction
-    unsigned int pad0;
+    int pair_ok;                        // the last pushed L-BFGS pair passed the curvature test
     long long rescored_total;
 };
 
@@ -280,7 +280,8 @@ cudaError_t launch_centroids(const GridDev &g, int n, const double *x,
 // L-BFGS helpers
 cudaError_t launch_axpy(int n, const double *a, double t, const double *b, double *out,
                         cudaStream_t st);
-cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma,
+cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma, bool use_pair,
+                                   int hist_acc, int newest_acc,
                                    Workspace &ws, cudaStream_t st);
 cudaError_t launch_lbfgs_push(int n, int slot, Workspace &ws, cudaStream_t st);
 

@@ -242,14 +242,21 @@ __global__ void axpy_kernel(const int n, const double *a, const double t, const 
 }
 
 // Two-loop recursion: p = -H gf with H0 = gamma I and the stored pairs
-// (s_k, y_k), newest at slot `newest`; also <gf, p> into sc->gp0.
+// (s_k, y_k), newest at slot `newest`; also <gf, p> into sc->gp0.  With
+// use_pair, the pair just pushed (slot newest_acc) is used if it passed the
+// push kernel's curvature test: then hist_acc pairs and gamma = s.y / y.y.
 __global__ void __launch_bounds__(kRedThreads)
-    lbfgs_direction_kernel(const int n, const int hist, const int newest, const int cap,
-                           const double gamma, const double *__restrict__ S,
-                           const double *__restrict__ Y, const double *__restrict__ rho,
-                           double *__restrict__ alpha, const double *__restrict__ gf,
-                           double *__restrict__ p, DevScalars *sc) {
+    lbfgs_direction_kernel(const int n, int hist, int newest, const int cap, double gamma,
+                           const int use_pair, const int hist_acc, const int newest_acc,
+                           const double *__restrict__ S, const double *__restrict__ Y,
+                           const double *__restrict__ rho, double *__restrict__ alpha,
+                           const double *__restrict__ gf, double *__restrict__ p, DevScalars *sc) {
     __shared__ double sh[33];
+    if (use_pair && sc->pair_ok) {
+        hist = hist_acc;
+        newest = newest_acc;
+        gamma = sc->sy / sc->yy;
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = gf[i];
     for (int k = 0; k < hist; ++k) {
         const int idx = (newest - k + cap) % cap;
@@ -308,6 +315,7 @@ __global__ void __launch_bounds__(kRedThreads)
         sc->sy = sy;
         sc->yy = yy;
         sc->ss = ss;
+        sc->pair_ok = (sy > 1e-12 * sqrt(ss * yy) && yy > 0.0) ? 1 : 0;
         rho[slot] = sy != 0.0 ? 1.0 / sy : 0.0;
     }
 }
@@ -402,10 +410,11 @@ cudaError_t launch_axpy(int n, const double *a, double t, const double *b, doubl
 // so small problems use a smaller block (fewer warps per reduction).
 static int lbfgs_threads(int n) { return n <= 2048 ? 256 : kRedThreads; }
 
-cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma, Workspace &ws,
-                                   cudaStream_t st) {
-    lbfgs_direction_kernel<<<1, lbfgs_threads(n), 0, st>>>(n, hist, newest, cap, gamma, ws.S, ws.Y, ws.rho,
-                                                      ws.alpha, ws.gf, ws.p, ws.sc);
+cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma, bool use_pair,
+                                   int hist_acc, int newest_acc, Workspace &ws, cudaStream_t st) {
+    lbfgs_direction_kernel<<<1, lbfgs_threads(n), 0, st>>>(n, hist, newest, cap, gamma, use_pair ? 1 : 0,
+                                                           hist_acc, newest_acc, ws.S, ws.Y, ws.rho, ws.alpha,
+                                                           ws.gf, ws.p, ws.sc);
     return cudaGetLastError();
 }
 
