@@ -90,17 +90,30 @@ int cuda_ok(cudaError_t e) { return e == cudaSuccess ? APD_OK : APD_ERR_CUDA; }
     } while (0)
 
 // Algorithm 1 + moments (+ FP64 rescoring of near ties) on `st`.
+// A trial point W + t p of the weight solve, written to the evaluated weights.
+struct TrialStep {
+    const double *W;
+    double t;
+    const double *p;
+};
+
+// Queues one pass of scoring + rescoring + moments at weights w.  With
+// weights_only the records of the previous pass (same x, A, n) are reused and
+// only the weights change; with a step, w (device, n) is first set to
+// step->W + step->t step->p.
 int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, const double *w,
                    apd_precision prec, Workspace &ws, int32_t *labels, unsigned long long *mom,
-                   cudaStream_t st, bool weights_only = false) {
+                   cudaStream_t st, bool weights_only = false, const TrialStep *step = nullptr) {
     if (prec != APD_FP32 && prec != APD_TC_TF32 && prec != APD_TC_BF16) return APD_ERR_UNSUPPORTED;
     const size_t K = (size_t)moment_width(g.dim);
-    APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
-    APD_TRY(cuda_ok(launch_eval_reset(ws, st, weights_only)));
     if (weights_only) {
-        // positions and matrices as in the previous pass: only the weights change
-        APD_TRY(cuda_ok(launch_weights_prep(n, w, ws, st)));
+        // one launch: moments and counters cleared, trial weights into the records
+        APD_TRY(cuda_ok(launch_eval_begin(n, step ? step->W : w, step ? step->t : 0.0, step ? step->p : nullptr,
+                                          const_cast<double *>(w), mom, ws, st)));
     } else {
+        if (step) APD_TRY(cuda_ok(launch_axpy(n, step->W, step->t, step->p, const_cast<double *>(w), st)));
+        APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
+        APD_TRY(cuda_ok(launch_eval_reset(ws, st, false)));
         APD_TRY(cuda_ok(launch_seed_prep(g, n, x, A, w, ws, st)));
         APD_TRY(cuda_ok(launch_group_bounds(n, ws, st)));
     }
@@ -125,8 +138,9 @@ int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, co
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
     if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
     APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
-    ws.kernel_launches += weights_only ? 4 + (prec == APD_FP32 ? 0 : 2)
-                                       : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 2);
+    ws.kernel_launches += weights_only ? 3 + (prec == APD_FP32 ? 0 : 2)
+                                       : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 2) +
+                                             (step ? 1 : 0);
     ws.last_pixels = g.J;
     ws.last_pairs = g.J * (long long)n;
     return APD_OK;
@@ -170,10 +184,11 @@ struct Solver {
     Solver(Workspace &w) : ws(w) {}
 
     // Evaluate at Wp; gf_out receives grad f = -(v - |P| m); pdir (nullable) for <grad f, p>.
+    // With a step, Wp (device, n) is first set to step->W + step->t step->p.
     int eval(const double *Wp, double *gf_out, const double *pdir, double &f, double &dphi,
-             double &err) {
+             double &err, const TrialStep *step = nullptr) {
         // the records' positions and matrices are built once per solve
-        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, st, geometry_ready));
+        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, st, geometry_ready, step));
         geometry_ready = true;
         APD_TRY(cuda_ok(launch_dual(g, n, x, A, Wp, v, pdir, ws.moments, ws, nullptr, ws.grad, gf_out,
                                     nullptr, st)));
@@ -226,9 +241,8 @@ struct Solver {
         double best_t = 0.0, best_phi = f0;
         double cur_t = -1.0;  // t at which Wt/gft were last evaluated
         auto evaluate = [&](double tt, double &phi, double &dphi, double &err) -> int {
-            APD_TRY(cuda_ok(launch_axpy(n, ws.W, tt, ws.p, ws.Wt, st)));
-            ws.kernel_launches += 1;
-            APD_TRY(eval(ws.Wt, ws.gft, ws.p, phi, dphi, err));
+            const TrialStep step{ws.W, tt, ws.p};  // Wt = W + tt p, formed by the evaluation's first kernel
+            APD_TRY(eval(ws.Wt, ws.gft, ws.p, phi, dphi, err, &step));
             cur_t = tt;
             return APD_OK;
         };

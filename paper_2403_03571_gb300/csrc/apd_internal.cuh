@@ -250,8 +250,11 @@ constexpr int moment_width(int dim) { return 1 + dim + dim * (dim + 1) / 2; }
 
 // zero the per-evaluation counters and statistics in sc
 cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry = false);
-// new weights into the records of the last launch_seed_prep (same x, A, n)
-cudaError_t launch_weights_prep(int n, const double *w, Workspace &ws, cudaStream_t st);
+// start of an evaluation with the records of the last launch_seed_prep (same x,
+// A, n): zeroed moments and counters, weights W0 + t pdir (into Wt; pdir null:
+// W0 itself) in the records, wref and the group weight gaps
+cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *pdir, double *Wt,
+                              unsigned long long *mom, Workspace &ws, cudaStream_t st);
 // seed records (FP64 x, w; FP32 symmetric A) + stats (max w, max ||A||_F, min lambda bound)
 cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const double *A,
                              const double *w, Workspace &ws, cudaStream_t st);

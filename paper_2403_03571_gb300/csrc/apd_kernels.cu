@@ -21,20 +21,36 @@ __global__ void eval_reset_kernel(DevScalars *sc, const int keep_geometry) {
     }
 }
 
-// New weights for records whose positions and matrices are unchanged: the
-// weight fields of the scored records (scan order), of both rescoring record
-// arrays, the reference weight wref = max w, and the groups' largest weight.
-// One thread per scan position; a warp covers one 32-seed group.
-__global__ void weights_prep_kernel(const int n, const int n_pad, const double *__restrict__ w,
-                                    const int32_t *__restrict__ perm, SeedRec *__restrict__ recs,
-                                    SeedRec32 *__restrict__ recs32, SeedRec32 *__restrict__ recs32s,
-                                    GroupBound *__restrict__ groups, DevScalars *__restrict__ sc) {
+// Start of an evaluation whose records' positions and matrices are unchanged
+// (same x, A, n as the last seed preparation): zeroed moments and queue count,
+// the trial weights (w = W0 + t p into Wt when p is given, else w = W0), their
+// copies in the scored records (scan order) and both rescoring record arrays,
+// the reference weight wref = max w (per-block maxima reduced by the last block
+// to finish), and each 32-seed group's largest weight and gap wref - wmax.  One
+// thread per scan position; a warp covers one group.
+__global__ void __launch_bounds__(256)
+    eval_begin_kernel(const int n, const int n_pad, const long long n_mom, const double *__restrict__ W0,
+                      const double t, const double *__restrict__ pdir, double *__restrict__ Wt,
+                      const int32_t *__restrict__ perm, SeedRec *__restrict__ recs,
+                      SeedRec32 *__restrict__ recs32, SeedRec32 *__restrict__ recs32s,
+                      GroupBound *__restrict__ groups, unsigned long long *__restrict__ mom,
+                      double *__restrict__ part, DevScalars *__restrict__ sc) {
+    __shared__ double shw[8];
+    __shared__ bool last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long e = i; e < n_mom; e += (long long)gridDim.x * blockDim.x) mom[e] = 0ull;
+    if (i == 0) sc->flag_count = 0u;
     const int src = i < n_pad ? (perm ? perm[i] : i) : n;
     const bool real = src < n;
     double wkey = -DBL_MAX;
     if (real) {
-        const double wi = w[src];
+        double wi;
+        if (pdir) {
+            wi = fma(t, pdir[src], W0[src]);
+            Wt[src] = wi;
+        } else {
+            wi = W0[src];
+        }
         const bool finite = isfinite(wi);
         if (!finite) atomicOr(&sc->status, ST_NONFINITE);
         recs[i].w = wi;
@@ -49,29 +65,34 @@ __global__ void weights_prep_kernel(const int n, const int n_pad, const double *
         wkey = finite ? wi : -DBL_MAX;
     }
     const double wmax = warp_max(wkey);
-    const bool any = __any_sync(0xffffffffu, real);
-    if ((threadIdx.x & 31) == 0 && any) {
-        atomicMax(&sc->wref_key, dkey(wmax));
-        if (groups) groups[i >> 5].wmax = wmax;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        shw[wid] = wmax;
+        if (groups && i < n_pad && (i & ~31) < n) groups[i >> 5].wmax = wmax;
     }
-    if (!groups) return;
-    __threadfence();  // this thread's group write before the block's arrival count
-    // the last block to finish has the final wref: the groups' weight gaps
-    __shared__ bool last;
+    __threadfence();  // group writes before the block's arrival count
     __syncthreads();
     if (threadIdx.x == 0) {
+        double b = shw[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) b = fmax(b, shw[k]);
+        part[(size_t)blockIdx.x * 5] = b;
         __threadfence();
         last = atomicAdd(&sc->dual_done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const double wref = dkey_inv(*(volatile unsigned long long *)&sc->wref_key);
-    for (int gidx = threadIdx.x; gidx * 32 < n; gidx += blockDim.x) {
-        const double wm = *(volatile double *)&groups[gidx].wmax;
-        groups[gidx].wgap = __double2float_rd(wref - wm);
+    double wref = -DBL_MAX;
+    for (unsigned k = 0; k < gridDim.x; ++k) wref = fmax(wref, *(volatile double *)&part[(size_t)k * 5]);
+    if (groups)
+        for (int gidx = threadIdx.x; gidx * 32 < n; gidx += blockDim.x) {
+            const double wm = *(volatile double *)&groups[gidx].wmax;
+            groups[gidx].wgap = __double2float_rd(wref - wm);
+        }
+    if (threadIdx.x == 0) {
+        sc->wref_key = dkey(wref);
+        sc->dual_done = 0u;
     }
-    if (threadIdx.x == 0) sc->dual_done = 0u;
 }
 
 template <int D>
@@ -327,11 +348,14 @@ cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry
     return cudaGetLastError();
 }
 
-cudaError_t launch_weights_prep(int n, const double *w, Workspace &ws, cudaStream_t st) {
+cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *pdir, double *Wt,
+                              unsigned long long *mom, Workspace &ws, cudaStream_t st) {
     const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
-    weights_prep_kernel<<<(n_pad + 255) / 256, 256, 0, st>>>(n, n_pad, w, ws.sorted ? ws.perm : nullptr, ws.recs,
-                                                             ws.recs32, ws.sorted ? ws.recs32s : nullptr,
-                                                             ws.groups, ws.sc);
+    const long long n_mom = (long long)n * moment_width(ws.dim);
+    if (n_pad == 0) return cudaSuccess;
+    eval_begin_kernel<<<n_pad / 256, 256, 0, st>>>(n, n_pad, n_mom, W0, t, pdir, Wt, ws.sorted ? ws.perm : nullptr,
+                                                   ws.recs, ws.recs32, ws.sorted ? ws.recs32s : nullptr, ws.groups,
+                                                   mom, ws.part, ws.sc);
     return cudaGetLastError();
 }
 
