@@ -82,8 +82,15 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // block maxima loaded in parallel (max is order-independent)
     double wref = -DBL_MAX;
-    for (unsigned k = 0; k < gridDim.x; ++k) wref = fmax(wref, *(volatile double *)&part[(size_t)k * 5]);
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x)
+        wref = fmax(wref, *(volatile double *)&part[(size_t)k * 5]);
+    wref = warp_max(wref);
+    if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = wref;
+    __syncthreads();
+    wref = shw[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) wref = fmax(wref, shw[k]);
     if (groups)
         for (int gidx = threadIdx.x; gidx * 32 < n; gidx += blockDim.x) {
             const double wm = *(volatile double *)&groups[gidx].wmax;
@@ -220,17 +227,29 @@ __global__ void __launch_bounds__(256)
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double G = 0.0, E = 0.0, GP = 0.0, SV = 0.0, VM = DBL_MAX;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            const volatile double *pp = part + (size_t)k * 5;
-            G += pp[0];
-            E = fmax(E, pp[1]);
-            GP += pp[2];
-            SV += pp[3];
-            VM = fmin(VM, pp[4]);
-        }
+    if (!last) return;
+    __threadfence();
+    // the partials are loaded in parallel, then summed in block order by one thread
+    __shared__ double pl[5 * 64];
+    const unsigned chunk = min(gridDim.x, 64u);
+    double G = 0.0, E = 0.0, GP = 0.0, SV = 0.0, VM = DBL_MAX;
+    for (unsigned k0 = 0; k0 < gridDim.x; k0 += chunk) {
+        const unsigned m = min(chunk, gridDim.x - k0);
+        for (unsigned e = threadIdx.x; e < 5 * m; e += blockDim.x)
+            pl[e] = *(const volatile double *)(part + (size_t)k0 * 5 + e);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (unsigned k = 0; k < m; ++k) {
+                const double *pp = pl + (size_t)k * 5;
+                G += pp[0];
+                E = fmax(E, pp[1]);
+                GP += pp[2];
+                SV += pp[3];
+                VM = fmin(VM, pp[4]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
         sc->g = G;
         sc->max_rel_err = E;
         sc->dot_gp = GP;

@@ -57,6 +57,11 @@ struct Layout {
 // ---------------------------------------------------------------------------
 // features: one thread per seed, brute-force 8 nearest neighbours
 // ---------------------------------------------------------------------------
+// One warp per seed: the lanes scan the other seeds of the instance (FP64
+// distances), each keeping its 8 nearest in order and its partial ball counts;
+// the 8 nearest of the seed are then drawn from the lanes' lists in the order
+// (distance, index), which is also the order of the sequential scan (ties keep
+// the lower index first).
 template <int D>
 __global__ void __launch_bounds__(256)
     features_kernel(const int count, const long long *__restrict__ offs, const double *__restrict__ box,
@@ -64,8 +69,9 @@ __global__ void __launch_bounds__(256)
                     float *__restrict__ feat, int32_t *__restrict__ knn) {
     constexpr int F = feat_dim(D);
     const long long total = offs[count];
-    const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= total) return;
+    const long long gi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gi >= total) return;  // whole warps leave together
     int lo = 0, hi = count - 1;  // instance: last b with offs[b] <= gi
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -98,7 +104,7 @@ __global__ void __launch_bounds__(256)
         bd[k] = 1e300;
         bj[k] = -1;
     }
-    for (int j = 0; j < n; ++j) {
+    for (int j = lane; j < n; j += 32) {
         if (o + j == gi) continue;
         double d2 = 0.0;
 #pragma unroll
@@ -112,20 +118,58 @@ __global__ void __launch_bounds__(256)
                 cnt[r] += 1.0;
                 vsum[r] += v[o + j];
             }
-        if (d2 < bd[kNN - 1]) {  // insertion into the sorted list (ties keep the lower index first)
-            int p = kNN - 1;
-            while (p > 0 && bd[p - 1] > d2) {
-                bd[p] = bd[p - 1];
-                bj[p] = bj[p - 1];
-                --p;
+        if (d2 < bd[kNN - 1]) {  // insertion into the lane's sorted list (j increases along the scan)
+#pragma unroll
+            for (int p = kNN - 1; p > 0; --p) {
+                const bool shift = bd[p - 1] > d2;
+                const bool here = !shift && bd[p] > d2;
+                bd[p] = shift ? bd[p - 1] : (here ? d2 : bd[p]);
+                bj[p] = shift ? bj[p - 1] : (here ? j : bj[p]);
             }
-            bd[p] = d2;
-            bj[p] = j;
+            if (bd[0] > d2) {
+                bd[0] = d2;
+                bj[0] = j;
+            }
         }
     }
+#pragma unroll
+    for (int r = 0; r < kRadii; ++r) {
+        cnt[r] = warp_sum(cnt[r]);
+        vsum[r] = warp_sum(vsum[r]);
+    }
+    // merge: 8 rounds of the smallest (distance, index) head over the lanes
+    double fd[kNN];
+    int fj[kNN];
+#pragma unroll
+    for (int k = 0; k < kNN; ++k) {
+        double md = bd[0];
+        int mj = bj[0] < 0 ? 0x7fffffff : bj[0];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double od = __shfl_xor_sync(0xffffffffu, md, off);
+            const int oj = __shfl_xor_sync(0xffffffffu, mj, off);
+            if (od < md || (od == md && oj < mj)) {
+                md = od;
+                mj = oj;
+            }
+        }
+        const bool mine = (bd[0] == md) && ((bj[0] < 0 ? 0x7fffffff : bj[0]) == mj);
+        fd[k] = md;
+        fj[k] = mj == 0x7fffffff ? -1 : mj;
+        if (mine && mj != 0x7fffffff) {  // pop the head
+#pragma unroll
+            for (int p = 0; p < kNN - 1; ++p) {
+                bd[p] = bd[p + 1];
+                bj[p] = bj[p + 1];
+            }
+            bd[kNN - 1] = 1e300;
+            bj[kNN - 1] = -1;
+        }
+    }
+    if (lane != 0) return;
     if (knn) {
 #pragma unroll
-        for (int k = 0; k < kNN; ++k) knn[gi * kNN + k] = bj[k] >= 0 ? (int32_t)(o + bj[k]) : -1;
+        for (int k = 0; k < kNN; ++k) knn[gi * kNN + k] = fj[k] >= 0 ? (int32_t)(o + fj[k]) : -1;
     }
     float *f = feat + gi * F;
     int c = 0;
@@ -136,9 +180,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int b = a; b < D; ++b) f[c++] = (float)(0.5 * (Ai[a * D + b] + Ai[b * D + a]));
 #pragma unroll
-    for (int k = 0; k < kNN; ++k) f[c + k] = bj[k] >= 0 ? (float)(sqrt(bd[k]) * ls) : 4.f;
+    for (int k = 0; k < kNN; ++k) f[c + k] = fj[k] >= 0 ? (float)(sqrt(fd[k]) * ls) : 4.f;
 #pragma unroll
-    for (int k = 0; k < kNN; ++k) f[c + kNN + k] = bj[k] >= 0 ? (float)(v[o + bj[k]] * dens) : 0.f;
+    for (int k = 0; k < kNN; ++k) f[c + kNN + k] = fj[k] >= 0 ? (float)(v[o + fj[k]] * dens) : 0.f;
     c += 2 * kNN;
 #pragma unroll
     for (int a = 0; a < D; ++a) f[c++] = (float)(fmin(xi[a] - bx[a], bx[3 + a] - xi[a]) * ls);
@@ -583,7 +627,7 @@ int apd_warmstart_features(apd_mlp *net, int32_t count, const int64_t *offsets, 
     rc = ensure_instances(net, count, offsets, box, st);
     if (rc != APD_OK) return rc;
     const long long total = offsets[count];
-    const int blocks = (int)((total + 255) / 256);
+    const int blocks = (int)((total + 7) / 8);  // one warp per seed
     if (net->dim == 2)
         features_kernel<2><<<blocks, 256, 0, st>>>(count, net->offs, net->box, x, A, v, features, knn);
     else
