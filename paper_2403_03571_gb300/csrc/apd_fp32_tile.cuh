@@ -148,12 +148,12 @@ __device__ __forceinline__ void table_add(SharedLayout<D> &sm, unsigned long lon
         if (val[v]) atomicAdd(&gmom[(size_t)label * K + v], val[v]);
 }
 
+// Integer moments of a run of cnt pixels along the first axis (sum of the
+// doubled first coordinate s0, of its square s00) on the row (u1, u2).
 template <int D>
-__device__ __forceinline__ void flush_run(SharedLayout<D> &sm, unsigned long long *gmom, int label,
-                                          unsigned long long cnt, unsigned long long s0,
-                                          unsigned long long s00, unsigned long long u1,
-                                          unsigned long long u2) {
-    unsigned long long val[moment_width(D)];
+__device__ __forceinline__ void run_moments(unsigned long long cnt, unsigned long long s0, unsigned long long s00,
+                                            unsigned long long u1, unsigned long long u2,
+                                            unsigned long long (&val)[moment_width(D)]) {
     if (D == 3) {
         val[0] = cnt;
         val[1] = s0;
@@ -173,7 +173,22 @@ __device__ __forceinline__ void flush_run(SharedLayout<D> &sm, unsigned long lon
         val[4] = s0 * u1;
         val[5] = cnt * u1 * u1;
     }
+}
+
+template <int D>
+__device__ __forceinline__ void flush_run(SharedLayout<D> &sm, unsigned long long *gmom, int label,
+                                          unsigned long long cnt, unsigned long long s0,
+                                          unsigned long long s00, unsigned long long u1,
+                                          unsigned long long u2) {
+    unsigned long long val[moment_width(D)];
+    run_moments<D>(cnt, s0, s00, u1, u2, val);
     table_add<D>(sm, gmom, label, val);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
 }
 
 
@@ -521,6 +536,32 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     const long long rowbase = (long long)g.res[0] * ((long long)k1 + (long long)g.res[1] * (long long)k2);
     const unsigned long long u1 = 2ull * (unsigned long long)k1 + 1ull;
     const unsigned long long u2 = 2ull * (unsigned long long)k2 + 1ull;
+    // Runs of equal labels along the thread's row: the first kRuns are kept for
+    // the warp-level aggregation below, any further ones go to the table at once.
+    constexpr int kRuns = 4;
+    int rlab[kRuns];
+    unsigned long long rcnt[kRuns], rs0[kRuns], rs00[kRuns];
+#pragma unroll
+    for (int q = 0; q < kRuns; ++q) {
+        rlab[q] = -1;
+        rcnt[q] = rs0[q] = rs00[q] = 0ull;
+    }
+    int nr = 0;
+    auto end_run = [&](int lab, unsigned long long c_, unsigned long long a_, unsigned long long b_) {
+        if (nr < kRuns) {
+#pragma unroll
+            for (int q = 0; q < kRuns; ++q)
+                if (q == nr) {
+                    rlab[q] = lab;
+                    rcnt[q] = c_;
+                    rs0[q] = a_;
+                    rs00[q] = b_;
+                }
+            ++nr;
+        } else {
+            flush_run<D>(sm, s.gmom, lab, c_, a_, b_, u1, u2);
+        }
+    };
     int cur = -1;
     unsigned long long cnt = 0, s0 = 0, s00 = 0;
 #pragma unroll
@@ -545,7 +586,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         }
         const int L = (valid && !flagged) ? GI[p] : -1;
         if (L != cur) {
-            if (cur >= 0) flush_run<D>(sm, s.gmom, cur, cnt, s0, s00, u1, u2);
+            if (cur >= 0) end_run(cur, cnt, s0, s00);
             cur = L;
             cnt = s0 = s00 = 0;
         }
@@ -556,7 +597,35 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             s00 += u0 * u0;
         }
     }
-    if (cur >= 0) flush_run<D>(sm, s.gmom, cur, cnt, s0, s00, u1, u2);
+    if (cur >= 0) end_run(cur, cnt, s0, s00);
+    // Warp-level aggregation (neighbouring rows mostly share their labels): in
+    // round q every lane offers its q-th run; the lanes holding the label of
+    // the lowest offering lane sum their moments and that lane adds the sums
+    // to the table, so each label costs one set of shared atomics per warp and
+    // round instead of one per row.
+#pragma unroll
+    for (int q = 0; q < kRuns; ++q) {
+        const bool has = rlab[q] >= 0;
+        unsigned todo = __ballot_sync(0xffffffffu, has);
+        if (!todo) break;
+        unsigned long long own[K];
+        run_moments<D>(rcnt[q], rs0[q], rs00[q], u1, u2, own);
+        while (todo) {
+            const int leader = __ffs(todo) - 1;
+            const int L0 = __shfl_sync(0xffffffffu, rlab[q], leader);
+            const bool mine = has && rlab[q] == L0;
+            const unsigned grp = __ballot_sync(0xffffffffu, mine);
+            if (grp == (1u << leader)) {
+                if (lane == leader) table_add<D>(sm, s.gmom, L0, own);
+            } else {
+                unsigned long long sum[K];
+#pragma unroll
+                for (int v = 0; v < K; ++v) sum[v] = warp_sum_u64(mine ? own[v] : 0ull);
+                if (lane == leader) table_add<D>(sm, s.gmom, L0, sum);
+            }
+            todo &= ~grp;
+        }
+    }
     __syncthreads();
     if (tid == 0 && s.pairs_scored) {
         atomicAdd(s.pairs_scored, sm.scored);
