@@ -260,18 +260,21 @@ __device__ __forceinline__ void dual_terms(const GridDev &g, const unsigned long
     gr = __dsub_rn(vi, __dmul_rn(m, g.cell));
     Q = 0.0;
     if (mo[0] == 0ull) return;
+    // one division (the FP64 divide is a long dependent sequence on this part);
+    // the products with 1/m differ from the quotients by a few ulp
+    const double inv_m = 1.0 / m;
     double S1[D], e[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         S1[a] = (double)mo[1 + a];
-        e[a] = (g.lo[a] + 0.5 * g.h[a] * (S1[a] / m)) - xi[a];
+        e[a] = (g.lo[a] + 0.5 * g.h[a] * (S1[a] * inv_m)) - xi[a];
     }
     int t = 1 + D;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = a; b < D; ++b) {
-            const double Cab = (double)mo[t++] - S1[a] * S1[b] / m;
+            const double Cab = (double)mo[t++] - S1[a] * S1[b] * inv_m;
             const double Mab = 0.25 * g.h[a] * g.h[b] * Cab + m * e[a] * e[b];
             const double Aab = (a == b) ? Ai[a * D + a] : Ai[a * D + b] + Ai[b * D + a];
             Q += Aab * Mab;
