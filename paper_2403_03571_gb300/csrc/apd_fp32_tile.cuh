@@ -78,13 +78,15 @@ __device__ __forceinline__ void seed_pair_coeffs(const float4 (*phi)[kChunk], in
     ab2 = make_float2(a[1], a[1]);
 }
 
-// Two new packed keys into the top-2 (b1 <= b2) of one pixel; gi follows b1.
+// Two new packed keys of the group at scan position gbase into the top-2
+// (b1 <= b2) of one pixel; gi follows b1's group (the index inside the group is
+// in b1's low bits and is added once, after the scan).
 __device__ __forceinline__ void top2_update(float &b1, float &b2, int &gi, float ka, float kb, int gbase) {
     const float mn = fminf(ka, kb), mx = fmaxf(ka, kb);
     const bool lt = mn < b1;
     b2 = fmin3(b2, fmaxf(b1, mn), mx);
     b1 = fminf(b1, mn);
-    gi = lt ? (gbase | (int)(__float_as_uint(mn) & 31u)) : gi;
+    gi = lt ? gbase : gi;
 }
 
 // Largest second-best key over the warp's pixels.
@@ -207,7 +209,7 @@ struct TileSrc {
     int32_t *labels;              // [J] or null
     DevScalars *sc;
     const GroupBound *groups;     // bounds of the scan-order 32-seed groups: pruning (null: dense)
-    unsigned long long *pairs_scored;  // pixel-seed pairs the fast pass evaluated (or null)
+    unsigned long long *pairs_scored;  // pixel-seed pairs the scoring evaluated (or null)
 };
 
 // Scores the (TX P) x TY x TZ tile (bx, by, bz) of `s` with NT = TX TY TZ
@@ -228,8 +230,11 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
 
     const int tid = threadIdx.x;
     const int seg = tid % TX;
-    const int ty = (tid / TX) % TY;
-    const int tz = tid / (TX * TY);
+    // 3D tiles of 16 x 16 rows: each warp takes an 8 x 4 block of rows, a more
+    // compact pixel box than 16 x 2 for the pruning bounds
+    constexpr bool kBlockRows = D == 3 && TX == 1 && TY == 16 && TZ == 16;
+    const int ty = kBlockRows ? ((tid & 7) + 8 * ((tid >> 5) & 1)) : (tid / TX) % TY;
+    const int tz = kBlockRows ? (((tid >> 3) & 3) + 4 * (tid >> 6)) : tid / (TX * TY);
     const int k0t = bx * W0;       // first pixel of the tile along axis 0
     const int k0b = k0t + seg * P;  // first pixel of this thread's row segment
     const int k1b = by * TY;
@@ -523,6 +528,9 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
         }
         __syncthreads();
     }
+    // scan position of the best: its group base and the index bits of its key
+#pragma unroll
+    for (int p = 0; p < P; ++p) GI[p] |= (int)(__float_as_uint(b1[p]) & 31u);
     // scan position -> seed index
     if (s.perm && ok) {
 #pragma unroll
