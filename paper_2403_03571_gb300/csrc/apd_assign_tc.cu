@@ -614,15 +614,43 @@ __global__ void __launch_bounds__(256)
     const unsigned long long u2 = 2ull * (unsigned long long)k2 + 1ull;
     int cur = -1;
     unsigned long long cnt = 0, s0 = 0, s00 = 0;
-    auto flush = [&](int L) {
-        unsigned long long val[KM];
+    auto moments_of = [&](unsigned long long c_, unsigned long long a_, unsigned long long b_,
+                          unsigned long long (&val)[KM]) {
         if (D == 3) {
-            val[0] = cnt; val[1] = s0; val[2] = cnt * u1; val[3] = cnt * u2; val[4] = s00;
-            val[5] = s0 * u1; val[6] = s0 * u2; val[7] = cnt * u1 * u1; val[8] = cnt * u1 * u2; val[9] = cnt * u2 * u2;
+            val[0] = c_; val[1] = a_; val[2] = c_ * u1; val[3] = c_ * u2; val[4] = b_;
+            val[5] = a_ * u1; val[6] = a_ * u2; val[7] = c_ * u1 * u1; val[8] = c_ * u1 * u2; val[9] = c_ * u2 * u2;
         } else {
-            val[0] = cnt; val[1] = s0; val[2] = cnt * u1; val[3] = s00; val[4] = s0 * u1; val[5] = cnt * u1 * u1;
+            val[0] = c_; val[1] = a_; val[2] = c_ * u1; val[3] = b_; val[4] = a_ * u1; val[5] = c_ * u1 * u1;
         }
-        tc_table_add<D>(tkey, tval, gmom, L, val);
+    };
+    // runs of equal labels along the row: the first kRuns are summed across the
+    // warp per label below (one set of shared atomics per label and warp), any
+    // further ones go to the table at once
+    constexpr int kRuns = 4;
+    int rlab[kRuns];
+    unsigned long long rcnt[kRuns], rs0[kRuns], rs00[kRuns];
+#pragma unroll
+    for (int q = 0; q < kRuns; ++q) {
+        rlab[q] = -1;
+        rcnt[q] = rs0[q] = rs00[q] = 0ull;
+    }
+    int nr = 0;
+    auto flush = [&](int L) {
+        if (nr < kRuns) {
+#pragma unroll
+            for (int q = 0; q < kRuns; ++q)
+                if (q == nr) {
+                    rlab[q] = L;
+                    rcnt[q] = cnt;
+                    rs0[q] = s0;
+                    rs00[q] = s00;
+                }
+            ++nr;
+        } else {
+            unsigned long long val[KM];
+            moments_of(cnt, s0, s00, val);
+            tc_table_add<D>(tkey, tval, gmom, L, val);
+        }
     };
     for (int p = 0; p < kResP; ++p) {
         const int k0 = k0b + p;
@@ -691,6 +719,35 @@ __global__ void __launch_bounds__(256)
         }
     }
     if (cur >= 0) flush(cur);
+    const int lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < kRuns; ++q) {
+        const bool has = rlab[q] >= 0;
+        unsigned todo = __ballot_sync(0xffffffffu, has);
+        if (!todo) break;
+        unsigned long long own[KM];
+        moments_of(rcnt[q], rs0[q], rs00[q], own);
+        while (todo) {
+            const int leader = __ffs(todo) - 1;
+            const int L0 = __shfl_sync(0xffffffffu, rlab[q], leader);
+            const bool mine = has && rlab[q] == L0;
+            const unsigned grp = __ballot_sync(0xffffffffu, mine);
+            if (grp == (1u << leader)) {
+                if (lane == leader) tc_table_add<D>(tkey, tval, gmom, L0, own);
+            } else {
+                unsigned long long sum[KM];
+#pragma unroll
+                for (int v = 0; v < KM; ++v) {
+                    unsigned long long t = mine ? own[v] : 0ull;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+                    sum[v] = t;
+                }
+                if (lane == leader) tc_table_add<D>(tkey, tval, gmom, L0, sum);
+            }
+            todo &= ~grp;
+        }
+    }
     __syncthreads();
     for (int t = tid; t < kTcTable; t += blockDim.x) {
         const int key = tkey[t];
