@@ -223,8 +223,8 @@ def load_peaks():
 # keyed by (sha256 prefix of the scoring sources, workload, pruned); reported
 # only while the sources are unchanged since the capture.
 NCU_TRAFFIC = {
-    # profiles/assign_fp32_pruned_3d_n1000_256cube.md: dram read 307.7 KB, write 0
-    ("31a71b5822f8217b", "3d_n1000_256cube_lloyd5", True): 307712 + 0,
+    # profiles/assign_fp32_pruned_3d_n1000_256cube.md: dram read 624.9 KB, write 0
+    ("6af1923dad02aaf5", "3d_n1000_256cube_lloyd5", True): 624896 + 0,
 }
 
 # FP32 flops the row-factored scoring performs per (pixel, seed) pair:
