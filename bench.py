@@ -387,6 +387,9 @@ def roofline_block(form, dim, sms, workload):
                 "work_per_pair_flops": 2 * F,
                 "evaluated_pairs_per_s": sr,
                 "dense_equivalent_pairs_per_s": pr,
+                # all N x J pairs of Algorithm 1 over the launch time (pruned pairs
+                # are proven irrelevant, not computed): above 1 when pruning works
+                "dense_equivalent_frac": pr * 2 * F / 1e12 / peak,
                 "executed_flops_per_pair": FLOPS_PER_PAIR[dim],
                 "executed_tflops": sr * FLOPS_PER_PAIR[dim] / 1e12,
                 "executed_frac": sr * FLOPS_PER_PAIR[dim] / 1e12 / peak,
