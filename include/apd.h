@@ -447,6 +447,34 @@ int apd_batch_solve_weights_multires(apd_batch *batch, const double *x, const do
                                      int32_t judge, apd_solve_info *info, int32_t *used_pred,
                                      apd_stream_t stream);
 
+/* ---- Refining weight solve (Algorithm 2, step 4) -------------------------
+ * When the weights cannot reach the tolerance on the grid (the solve stalls at
+ * its evaluation cap, or the grid is coarser than eq. (2.10) asks for the
+ * smallest target volume), the grid of the same box is refined and the solve
+ * restarts from the weights found: they are per seed, so they carry over. */
+typedef struct {
+    double growth;          /* resolution factor per refinement, > 1 (default 1.5) */
+    int32_t max_res[3];     /* largest resolution per axis; 0: bounded by the workspace's pixel capacity */
+    int32_t max_rounds;     /* refinements at most (default 4) */
+} apd_refine_opts;
+
+void apd_refine_opts_default(apd_refine_opts *ro);
+
+/* Solves on `grid` from seeds->w (as apd_solve_weights).  While the result is
+ * APD_NOT_CONVERGED or APD_WARN_TOL_INFEASIBLE and rounds remain, every axis
+ * grows by the same factor f = max(growth, (J_(2.10) / J)^(1/D)), J_(2.10) the
+ * pixel count at which eq. (2.10) holds for the smallest v, each resolution
+ * rounded up; the solve restarts from the weights found.  The round stops
+ * early when the next grid exceeds max_res or the workspace's max_j.
+ * grid_out (host, nullable) receives the grid of the last solve; info sums the
+ * evaluations and iterations over the rounds (info->solves = rounds + 1) and
+ * reports the last solve's error and status.  Arguments as apd_solve_weights;
+ * ro null: defaults; growth <= 1, max_rounds < 0 or a max_res below the
+ * grid's resolution on an axis: APD_ERR_ARG. */
+int apd_solve_weights_refine(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
+                             const apd_solve_opts *opts, const apd_refine_opts *ro, apd_solve_info *info,
+                             apd_grid *grid_out, apd_workspace *ws, apd_stream_t stream);
+
 /* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
  * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).
  * Returns M >= 1, or -1 for invalid arguments. */

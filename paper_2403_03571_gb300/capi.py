@@ -42,7 +42,7 @@ EXPORTED = (
     "apd_warmstart_train_step", "apd_solve_weights_warm",
     "apd_multires_opts_default", "apd_solve_weights_multires", "apd_batch_solve_weights_multires",
     "apd_warmstart_train_step_pairs", "apd_workspace_set_pruning", "apd_batch_set_pruning",
-    "apd_profile_read_scored", "apd_lloyd_multires",
+    "apd_profile_read_scored", "apd_lloyd_multires", "apd_refine_opts_default", "apd_solve_weights_refine",
 )
 
 
@@ -81,6 +81,10 @@ class ApdSolveInfo(ctypes.Structure):
 class ApdMultiresOpts(ctypes.Structure):
     _fields_ = [("factor", ctypes.c_int32), ("coarse_eps", ctypes.c_double),
                 ("coarse_max_evals", ctypes.c_int32)]
+
+
+class ApdRefineOpts(ctypes.Structure):
+    _fields_ = [("growth", ctypes.c_double), ("max_res", ctypes.c_int32 * 3), ("max_rounds", ctypes.c_int32)]
 
 
 class ApdError(RuntimeError):
@@ -174,6 +178,10 @@ def load(path: Optional[str] = None):
     L.apd_lloyd_multires.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, ctypes.c_int32, _vp, _vp, _P(ApdSolveOpts),
                                      _P(ApdMultiresOpts), _P(ApdSolveInfo), _vp, _vp, _P(ctypes.c_int32), _vp]
     L.apd_batch_set_pruning.argtypes = [_vp, ctypes.c_int32]
+    L.apd_refine_opts_default.argtypes = [_P(ApdRefineOpts)]
+    L.apd_refine_opts_default.restype = None
+    L.apd_solve_weights_refine.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _P(ApdSolveOpts),
+                                           _P(ApdRefineOpts), _P(ApdSolveInfo), _P(ApdGrid), _vp, _vp]
     _lib = L
     return L
 
@@ -565,6 +573,34 @@ def apd_solve_weights_multires(grid, x, A, w0, v, w_out, ws: Workspace, opts=Non
                                            ctypes.byref(used), _stream(stream))
     _check(rc, "apd_solve_weights_multires", _SOLVE_OK)
     return rc, info, used.value
+
+
+def refine_opts(growth=1.5, max_res=(0, 0, 0), max_rounds=4) -> ApdRefineOpts:
+    r = ApdRefineOpts()
+    r.growth = growth
+    for d in range(3):
+        r.max_res[d] = int(max_res[d]) if d < len(max_res) else 0
+    r.max_rounds = max_rounds
+    return r
+
+
+def apd_solve_weights_refine(grid, x, A, w0, v, w_out, ws: Workspace, opts=None, ropts=None, stream=None):
+    """Weight solve that refines the grid while the tolerance is out of reach
+    (Algorithm 2, step 4); returns (status, ApdSolveInfo, final grid as a
+    synth.Grid)."""
+    from paper_2403_03571_gb300 import synth
+    g, s = make_grid(grid), make_seeds(x, A, w0)
+    info = ApdSolveInfo()
+    out = ApdGrid()
+    opts = opts or solve_opts()
+    ropts = ropts or refine_opts()
+    rc = load().apd_solve_weights_refine(ctypes.byref(g), ctypes.byref(s), _ptr(v), _ptr(w_out),
+                                         ctypes.byref(opts), ctypes.byref(ropts), ctypes.byref(info),
+                                         ctypes.byref(out), ws.handle, _stream(stream))
+    _check(rc, "apd_solve_weights_refine", _SOLVE_OK)
+    final = synth.Grid(grid.dim, tuple(out.res[d] for d in range(grid.dim)),
+                       lo=tuple(out.lo[d] for d in range(grid.dim)), hi=tuple(out.hi[d] for d in range(grid.dim)))
+    return rc, info, final
 
 
 def apd_batch_solve_weights_multires(batch: Batch, x, A, w0, v, w_out, opts=None, mopts=None, judge=False,

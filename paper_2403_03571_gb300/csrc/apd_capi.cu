@@ -723,6 +723,73 @@ static int solve_entry(const apd_grid *grid, const apd_seeds *seeds, const doubl
     return take_status(ws->w, st);
 }
 
+void apd_refine_opts_default(apd_refine_opts *ro) {
+    if (!ro) return;
+    ro->growth = 1.5;
+    ro->max_res[0] = ro->max_res[1] = ro->max_res[2] = 0;
+    ro->max_rounds = 4;
+}
+
+int apd_solve_weights_refine(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
+                             const apd_solve_opts *opts, const apd_refine_opts *ro, apd_solve_info *info,
+                             apd_grid *grid_out, apd_workspace *ws, apd_stream_t stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    apd_solve_info inf, last;
+    std::memset(&inf, 0, sizeof inf);
+    GridDev g;
+    apd_solve_opts o;
+    apd_refine_opts r;
+    apd_refine_opts_default(&r);
+    if (ro) r = *ro;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the options are checked before anything touches the device
+    int rc = (!(r.growth > 1.0) || !std::isfinite(r.growth) || r.max_rounds < 0) ? APD_ERR_ARG : APD_OK;
+    if (rc == APD_OK) rc = solve_entry(grid, seeds, v, w_out, opts, g, o, ws, st);
+    for (int d = 0; rc == APD_OK && d < grid->dim; ++d)
+        if (r.max_res[d] < 0 || (r.max_res[d] > 0 && r.max_res[d] < grid->res[d])) rc = APD_ERR_ARG;
+    apd_grid cur = rc == APD_OK ? *grid : apd_grid{};
+    const double *w0 = rc == APD_OK ? seeds->w : nullptr;
+    for (int round = 0; rc == APD_OK || rc == APD_NOT_CONVERGED || rc == APD_WARN_TOL_INFEASIBLE; ++round) {
+        std::memset(&last, 0, sizeof last);
+        rc = solve_impl(g, &cur, seeds->n, seeds->x, seeds->A, w0, v, w_out, o, last, ws->w, st, false);
+        inf.evaluations += last.evaluations;
+        inf.iterations += last.iterations;
+        inf.rescored_fp64 += last.rescored_fp64;
+        inf.solves += 1;
+        inf.max_rel_err = last.max_rel_err;
+        inf.g = last.g;
+        if (rc != APD_NOT_CONVERGED && rc != APD_WARN_TOL_INFEASIBLE) break;
+        if (round >= r.max_rounds) break;
+        // eq. (2.10) for the smallest target volume: J >= |Omega| 2^D / (eps v_min)
+        const double vmin = ws->w.sc_host->min_v;
+        const double J = (double)g.J;
+        const double J_need = domain_measure(&cur) * std::pow(2.0, cur.dim) / (o.eps * vmin);
+        const double f = std::max(r.growth, std::pow(std::max(J_need / J, 1.0), 1.0 / cur.dim));
+        apd_grid nxt = cur;
+        bool fits = true;
+        double Jn = 1.0;
+        for (int d = 0; d < cur.dim; ++d) {
+            const double m = std::ceil(cur.res[d] * f);
+            const double cap = r.max_res[d] > 0 ? (double)r.max_res[d] : 2147483647.0;
+            if (!(m <= cap)) fits = false;
+            nxt.res[d] = fits ? (int32_t)m : cur.res[d];
+            Jn *= m;
+        }
+        if (!fits || Jn > (double)ws->w.max_j) break;
+        GridDev gn;
+        if (validate_grid(&nxt, gn) != APD_OK) break;
+        cur = nxt;
+        g = gn;
+        w0 = w_out;  // the weights found carry over
+    }
+    if (rc >= 0) cudaStreamSynchronize(st);
+    if (grid_out && rc >= 0) *grid_out = cur;
+    inf.status = rc;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
 int apd_solve_weights(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
                       const apd_solve_opts *opts, apd_solve_info *info, apd_workspace *ws,
                       apd_stream_t stream) {

@@ -93,7 +93,22 @@ def test_argument_errors_before_cuda(lib):
                                   None, None, None, None) == capi.APD_ERR_ARG
     assert lib.apd_solve_weights_warm(ctypes.byref(g), ctypes.byref(s), None, None, None, None, None, None,
                                       None, None) == capi.APD_ERR_ARG
+    # refining solve: options checked first, then the grid, before any CUDA call
+    r = capi.ApdRefineOpts()
+    lib.apd_refine_opts_default(ctypes.byref(r))
+    assert (r.growth, list(r.max_res), r.max_rounds) == (1.5, [0, 0, 0], 4)
+    assert lib.apd_solve_weights_refine(ctypes.byref(g), ctypes.byref(s), None, None, None, ctypes.byref(r), None,
+                                        None, None, None) == capi.APD_ERR_ARG
     g.dim = 2
+    for bad in ({"growth": 1.0}, {"growth": float("nan")}, {"max_rounds": -1}):
+        rb = capi.ApdRefineOpts()
+        lib.apd_refine_opts_default(ctypes.byref(rb))
+        for k, val in bad.items():
+            setattr(rb, k, val)
+        assert lib.apd_solve_weights_refine(ctypes.byref(g), ctypes.byref(s), None, None, None, ctypes.byref(rb),
+                                            None, None, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_solve_weights_refine(None, None, None, None, None, None, None, None, None,
+                                        None) == capi.APD_ERR_ARG
     # warm-start network: sizes, argument checks without a device
     f, p = ctypes.c_int32(), ctypes.c_int32()
     assert lib.apd_warmstart_sizes(2, ctypes.byref(f), ctypes.byref(p)) == capi.APD_OK

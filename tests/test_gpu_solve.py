@@ -130,3 +130,32 @@ def test_lloyd_coarse_to_fine(capi):
     assert err < 0.01
     # ... and the positions moved: they are the discrete centroids of an earlier round
     assert np.abs(X - inst.x).max() > 1e-3
+
+
+def test_refining_solve_raises_the_resolution(capi):
+    # Algorithm 2 with its step 4: on a 40^2 grid the smallest cell is a few
+    # pixels, so 1 % is out of reach; the solve refines the grid of the same box,
+    # restarts from the weights found, and converges on the finer grid
+    inst = synth.make_instance(2, 60, 40, 23)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(2, inst.n, 400 * 400)
+    w_out = torch.zeros_like(w)
+    rc, info, grid = capi.apd_solve_weights_refine(inst.grid, x, A, w, v, w_out, ws,
+                                                   capi.solve_opts(max_evals=120),
+                                                   capi.refine_opts(growth=1.5, max_rounds=4))
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+    assert info.solves >= 2 and grid.res[0] > 40 and grid.res[0] == grid.res[1]
+    assert grid.lo == inst.grid.lo and grid.hi == inst.grid.hi and grid.num_pixels <= 400 * 400
+    # eq. (2.10) for the smallest target volume drives the first refinement
+    need = 4.0 / (0.01 * inst.v.min())
+    assert grid.num_pixels >= min(need, 400 * 400) * 0.999 or grid.num_pixels >= 1.5 ** 2 * 40 * 40
+    # the oracle confirms the 1 % rule on the final grid
+    _, _, err = oracle.dual(grid, inst.x, inst.A, host(w_out), inst.v)
+    assert err < 0.01 and abs(info.max_rel_err - err) <= 1e-12
+    # a cap below the next grid keeps the first grid and reports its status
+    w2 = torch.zeros_like(w)
+    rc2, info2, grid2 = capi.apd_solve_weights_refine(inst.grid, x, A, w, v, w2, ws,
+                                                      capi.solve_opts(max_evals=60),
+                                                      capi.refine_opts(max_res=(40, 40, 0)))
+    assert grid2.res == (40, 40) and info2.solves == 1
+    assert rc2 in (capi.APD_NOT_CONVERGED, capi.APD_WARN_TOL_INFEASIBLE)
