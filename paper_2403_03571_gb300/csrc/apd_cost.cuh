@@ -125,15 +125,23 @@ __device__ __forceinline__ void rescore_finish(const GridDev &g, const int n, co
                                                unsigned long long *__restrict__ gmom, int32_t *__restrict__ labels) {
     constexpr int K = moment_width(D);
     const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ob < best || (ob == best && oi < bi)) {
-            best = ob;
-            bi = oi;
+    // smallest (cost, index) over the few lanes holding a candidate (FP64 compares
+    // are slow on this part: visit those lanes only, every lane computing the same)
+    unsigned cm = __ballot_sync(0xffffffffu, bi != 0x7fffffff);
+    double b = __longlong_as_double(0x7ff0000000000000ll);
+    int ib = 0x7fffffff;
+    while (cm) {
+        const int l = __ffs(cm) - 1;
+        cm &= cm - 1u;
+        const double ob = __shfl_sync(0xffffffffu, best, l);
+        const int oi = __shfl_sync(0xffffffffu, bi, l);
+        if (ob < b || (ob == b && oi < ib)) {
+            b = ob;
+            ib = oi;
         }
     }
+    best = b;
+    bi = ib;
     if (lane == 0) {
         if (bi < 0 || bi >= n) {
             atomicOr(&sc->status, ST_BAD_LABEL);
