@@ -224,7 +224,8 @@ def load_peaks():
 # only while the sources are unchanged since the capture.
 NCU_TRAFFIC = {
     # profiles/assign_fp32_pruned_3d_n1000_256cube.md: dram read 624.9 KB, write 0
-    ("6af1923dad02aaf5", "3d_n1000_256cube_lloyd5", True): 624896 + 0,
+    # (code hash; the capture's file hash was 6af1923dad02aaf5)
+    ("997d6d8f19e1c5c9", "3d_n1000_256cube_lloyd5", True): 624896 + 0,
 }
 
 # FP32 flops the row-factored scoring performs per (pixel, seed) pair:
@@ -234,11 +235,17 @@ FLOPS_PER_PAIR = {3: 4.0 + 17.0 / 16.0, 2: 4.0 + 7.0 / 16.0}
 
 
 def kernel_source_hash():
+    """Hash of the FP32 scoring kernel's code (comments and blank lines left out,
+    so that a comment edit keeps the traffic entry of unchanged code)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in ("apd_assign_fp32.cu", "apd_fp32_tile.cuh"):
-        with open(os.path.join(ROOT, "paper_2403_03571_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2403_03571_gb300", "csrc", name), encoding="utf-8") as f:
+            for line in f:
+                code = re.sub(r"//.*$", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

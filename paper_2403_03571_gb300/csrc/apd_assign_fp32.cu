@@ -26,10 +26,17 @@
 // 1-D bulk async copies (TMA) into a double buffer; each chunk is transformed
 // once per CTA into the row-form coefficients above.
 //
+// Pruning (optional).  Lower bounds of the exact cost over a warp's pixel box,
+// per 32-seed group and per seed (lambda_min times the squared distance plus
+// the weight gap w_ref - w), skip the groups and seed pairs that cannot enter
+// any pixel's top two; groups are taken nearest-bound first and re-tested as
+// the second-best costs fall.  Labels and moments equal the dense sweep's.
+//
 // Moments.  Each thread run-length encodes its row (neighbouring pixels share a
-// label), accumulates count, sum u and sum u u^T (u = 2k + 1) per run, and adds
-// runs into a per-CTA shared-memory hash table keyed by label; the table is
-// flushed to the global int64 moments with one atomic per (cell, word).
+// label), accumulates count, sum u and sum u u^T (u = 2k + 1) per run; the lanes
+// of a warp holding the same label sum their runs with shuffles and one lane
+// adds the sums to a per-CTA shared-memory hash table keyed by label; the table
+// is flushed to the global int64 moments with one atomic per (cell, word).
 #include "apd_fp32_tile.cuh"
 #include "apd_cost.cuh"
 
