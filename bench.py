@@ -63,9 +63,20 @@ def parse():
                     help="--mode assign: score with seed-group pruning")
     ap.add_argument("--no-prune", dest="prune", action="store_false",
                     help="score the chosen form densely (no seed-group pruning)")
-    ap.add_argument("--mode", default="apd", choices=["apd", "assign"],
+    ap.add_argument("--mode", default="apd", choices=["apd", "assign", "sweep"],
                     help="apd: the full benchmark; assign: only repeated scoring+moments calls "
-                         "(apd_cell_moments) at zero weights, for kernel profiling")
+                         "(apd_cell_moments) at zero weights, for kernel profiling; sweep: the "
+                         "paper's runtime tests (Section 3.2), one JSON line per point")
+    ap.add_argument("--sweep-test", default="ab", help="sweep: 'a' (Algorithm 1), 'b' (Algorithm 2) or both")
+    ap.add_argument("--sweep-dims", default="2,3")
+    ap.add_argument("--sweep-alpha", default="0,0.3,0.7")
+    ap.add_argument("--sweep-n2", default="25,50,100,250,500,1000,2500,5000")
+    ap.add_argument("--sweep-n3", default="50,100,250,500,1000,2500,5000,10000")
+    ap.add_argument("--sweep-n3-b", default="50,100,250,500,1000,2500",
+                    help="sweep: 3D seed counts of test (b) (the largest solves take minutes)")
+    ap.add_argument("--sweep-runs", type=int, default=1, help="sweep: random instances per point")
+    ap.add_argument("--sweep-m-cap", default="4096,384", help="sweep: largest M in 2D, 3D (eq. (2.10) otherwise)")
+    ap.add_argument("--sweep-max-evals", type=int, default=400, help="sweep: evaluation cap of the test (b) solves")
     return ap.parse_args()
 
 
@@ -648,10 +659,95 @@ def run_batch(args):
     }
 
 
+def run_sweep(args):
+    """The paper's runtime tests (Section 3.2) on this GPU, one JSON line per point:
+    (a) Algorithm 1 for a fixed (X, W = 0, Lambda) in FP32 (labels), dense and
+        pruned, single-phase M of eq. (2.10) (v = 1/N);
+    (b) Algorithm 2 to 1 % (single and multi phase, M of eq. (2.10) for the
+        smallest volume, capped), the plain form (W = 0, dense) and the chosen
+        form (coarse-to-fine, pruned).
+    Seeds by the sequential rejection C = 0.2, the alpha anisotropy laws,
+    instance seeds 2403035710 + 7e6 + run; times are CUDA-event (a) or wall (b,
+    synchronised) seconds."""
+    import torch
+    from paper_2403_03571_gb300 import build, capi, synth
+    build.build()
+    capi.load()
+    dims = [int(d) for d in args.sweep_dims.split(",") if d]
+    alphas = [float(a) for a in args.sweep_alpha.split(",") if a]
+    caps = [int(c) for c in args.sweep_m_cap.split(",")]
+    ns = {2: [int(n) for n in args.sweep_n2.split(",") if n], 3: [int(n) for n in args.sweep_n3.split(",") if n]}
+    ns_b = {2: ns[2], 3: [int(n) for n in args.sweep_n3_b.split(",") if n]}
+    base = synth.BASE_SEED + 7_000_000
+    mopts = chosen_multires(capi)
+    if "a" in args.sweep_test:
+        for dim in dims:
+            for n in ns[dim]:
+                for alpha in alphas:
+                    for run in range(args.sweep_runs):
+                        inst = synth.runtime_test_instance(dim, n, alpha, False, base + run + 1000 * n,
+                                                           m_cap=caps[dim - 2])
+                        x, A, w = (torch.from_numpy(a).cuda() for a in (inst.x, inst.A, inst.w))
+                        labels = torch.empty(inst.grid.num_pixels, dtype=torch.int32, device="cuda")
+                        ws = capi.Workspace(dim, n, inst.grid.num_pixels)
+                        row = {"test": "a", "dim": dim, "n": n, "alpha": alpha, "run": run,
+                               "m": inst.grid.res[0], "pixels": inst.grid.num_pixels}
+                        for prune in (False, True):
+                            ws.set_pruning(prune)
+                            for _ in range(2):
+                                capi.apd_assign(inst.grid, x, A, w, labels, ws)
+                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            torch.cuda.synchronize()
+                            e0.record()
+                            for _ in range(5):
+                                capi.apd_assign(inst.grid, x, A, w, labels, ws)
+                            e1.record()
+                            torch.cuda.synchronize()
+                            assert ws.status() == capi.APD_OK
+                            row["pruned_s" if prune else "dense_s"] = e0.elapsed_time(e1) / 5 / 1000.0
+                        print(json.dumps(row), flush=True)
+                        del ws
+    if "b" in args.sweep_test:
+        for dim in dims:
+            for n in ns_b[dim]:
+                for alpha in alphas:
+                    for multi in (False, True):
+                        for run in range(args.sweep_runs):
+                            inst = synth.runtime_test_instance(dim, n, alpha, multi, base + run + 1000 * n + 1,
+                                                               m_cap=caps[dim - 2])
+                            x, A, w, v = (torch.from_numpy(a).cuda() for a in (inst.x, inst.A, inst.w, inst.v))
+                            ws = capi.Workspace(dim, n, inst.grid.num_pixels)
+                            row = {"test": "b", "dim": dim, "n": n, "alpha": alpha, "phase": "multi" if multi else "single",
+                                   "run": run, "m": inst.grid.res[0], "m_eq_2_10": synth.required_resolution(
+                                       dim, float(inst.v.min()), 0.01)}
+                            opts = capi.solve_opts(eps=0.01, max_evals=args.sweep_max_evals)
+                            for form in ("plain", "chosen"):
+                                w_out = torch.zeros_like(w)
+                                ws.set_pruning(form == "chosen")
+                                torch.cuda.synchronize()
+                                t0 = time.perf_counter()
+                                if form == "plain":
+                                    rc, info = capi.apd_solve_weights(inst.grid, x, A, w, v, w_out, ws, opts)
+                                    coarse = 0
+                                else:
+                                    rc, info, _ = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws,
+                                                                                  opts=opts, mopts=mopts)
+                                    coarse = info.coarse_evaluations
+                                torch.cuda.synchronize()
+                                row[form] = {"s": time.perf_counter() - t0, "status": capi.status_string(rc),
+                                             "evaluations": info.evaluations, "coarse_evaluations": coarse,
+                                             "max_rel_err": info.max_rel_err}
+                            print(json.dumps(row), flush=True)
+                            del ws
+    return 0
+
+
 def main():
     args = parse()
     if args.mode == "assign":
         return run_assign_only(args)
+    if args.mode == "sweep":
+        return run_sweep(args)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:

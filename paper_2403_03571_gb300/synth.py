@@ -186,6 +186,59 @@ def uniform_rotations(g: np.random.Generator, n: int) -> np.ndarray:
     return R
 
 
+def _rot_zyz(theta: np.ndarray, phi: np.ndarray, gamma: np.ndarray) -> np.ndarray:
+    """R = Rz(theta) Ry(phi) Rz(gamma) per seed (the z-y-z Euler convention)."""
+    def rz(t):
+        c, s = np.cos(t), np.sin(t)
+        R = np.zeros((t.shape[0], 3, 3))
+        R[:, 0, 0], R[:, 0, 1], R[:, 1, 0], R[:, 1, 1], R[:, 2, 2] = c, -s, s, c, 1.0
+        return R
+
+    def ry(t):
+        c, s = np.cos(t), np.sin(t)
+        R = np.zeros((t.shape[0], 3, 3))
+        R[:, 0, 0], R[:, 0, 2], R[:, 2, 0], R[:, 2, 2], R[:, 1, 1] = c, s, -s, c, 1.0
+        return R
+
+    return rz(theta) @ ry(phi) @ rz(gamma)
+
+
+def aniso_3d_alpha(g: np.random.Generator, n: int, alpha: float) -> np.ndarray:
+    """The paper's 3D runtime-test law: axes a_hat ~ U(1-alpha, 1), b_hat ~
+    U(1-alpha, 1/(1-alpha)) and 1/(a_hat b_hat) (det A = 1), angles theta, phi,
+    gamma ~ U(0, 2 pi) of a z-y-z rotation R (the paper does not name the
+    convention); A = R diag(axes^-2) R^T as in eq. (2.2)."""
+    if alpha > 0:
+        a_hat = g.uniform(1.0 - alpha, 1.0, n)
+        b_hat = g.uniform(1.0 - alpha, 1.0 / (1.0 - alpha), n)
+    else:
+        a_hat, b_hat = np.ones(n), np.ones(n)
+    ang = g.uniform(0.0, 2.0 * math.pi, (3, n))
+    R = _rot_zyz(ang[0], ang[1], ang[2])
+    axes = np.stack([a_hat, b_hat, 1.0 / (a_hat * b_hat)], axis=1)
+    A = np.einsum("nij,nj,nkj->nik", R, axes ** -2, R)
+    return 0.5 * (A + np.transpose(A, (0, 2, 1)))
+
+
+def runtime_test_instance(dim: int, n: int, alpha: float, multiphase: bool, seed: int,
+                          m: Optional[int] = None, eps: float = 0.01, m_cap: Optional[int] = None) -> Instance:
+    """An instance of the paper's runtime tests (Section 3.2): seeds uniform on
+    [0,1]^D with the sequential rejection C = 0.2, the alpha anisotropy law,
+    equal volumes (single phase) or lognormal volumes with shape 1.0 normalised
+    to |Omega| = 1 (multi phase), and M from eq. (2.10) for the smallest volume
+    (capped at m_cap) unless given."""
+    g = rng(seed)
+    x = seeds_with_rejection(g, n, dim, c=0.2)
+    A = aniso_2d_alpha(g, n, alpha) if dim == 2 else aniso_3d_alpha(g, n, alpha)
+    v = volumes_lognormal(g, n, 1.0, 1.0) if multiphase else volumes_equal(n, 1.0)
+    if m is None:
+        m = required_resolution(dim, float(v.min()), eps)
+        if m_cap is not None:
+            m = min(m, m_cap)
+    return Instance(Grid.cube(dim, m), _contig(x), _contig(A), np.zeros(n), _contig(v),
+                    f"runtime_{dim}d_n{n}_a{alpha}_{'multi' if multiphase else 'single'}")
+
+
 def aniso_3d_lognormal(g: np.random.Generator, n: int, sigma: float = 0.3) -> np.ndarray:
     """A = Q diag(s) Q^T, Q uniform rotation, ln s_k ~ N(0, sigma^2) rescaled to det 1."""
     Q = uniform_rotations(g, n)

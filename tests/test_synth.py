@@ -91,3 +91,36 @@ def test_batched_2d_workload_shape():
 def test_required_resolution_matches_oracle():
     for dim, vmin in [(2, 1 / 20), (3, 1e-4), (3, 2.3e-4), (2, 3.7e-5)]:
         assert synth.required_resolution(dim, vmin) == oracle.resolution_practical(dim, vmin)
+
+
+def test_runtime_test_anisotropy_laws():
+    # the paper's runtime-test laws (Section 3.2): det A = 1, eigenvalues the
+    # inverse squared axes, identity at alpha = 0
+    g = synth.rng(5)
+    A = synth.aniso_3d_alpha(g, 200, 0.7)
+    assert np.allclose(A, np.transpose(A, (0, 2, 1)), atol=0)
+    assert np.allclose(np.linalg.det(A), 1.0, rtol=1e-12)
+    ev = np.linalg.eigvalsh(A)
+    assert (ev > 0).all()
+    # axes a in [0.3, 1], b in [0.3, 1/0.3]: every eigenvalue a^-2, b^-2 or (ab)^2 lies in range
+    assert ev.min() >= 0.3 ** 2 * 0.3 ** 2 * (1 - 1e-12) and ev.max() <= 0.3 ** -2 * 0.3 ** -2 * (1 + 1e-12)
+    assert np.allclose(synth.aniso_3d_alpha(synth.rng(6), 10, 0.0), np.eye(3), atol=1e-14)
+    A2 = synth.aniso_2d_alpha(synth.rng(7), 50, 0.3)
+    assert np.allclose(np.linalg.det(A2), 1.0, rtol=1e-12)
+    # the z-y-z rotation is orthogonal
+    R = synth._rot_zyz(*synth.rng(8).uniform(0, 6.3, (3, 20)))
+    assert np.allclose(np.einsum("nij,nkj->nik", R, R), np.eye(3), atol=1e-14)
+
+
+def test_runtime_test_instances():
+    single = synth.runtime_test_instance(3, 500, 0.3, False, 11)
+    assert np.allclose(single.v, 1.0 / 500) and abs(single.v.sum() - 1.0) < 1e-12
+    assert single.grid.res[0] == synth.required_resolution(3, 1.0 / 500, 0.01)
+    multi = synth.runtime_test_instance(2, 300, 0.7, True, 12, m_cap=1000)
+    assert abs(multi.v.sum() - 1.0) < 1e-12 and multi.v.std() > 0
+    assert multi.grid.res[0] == min(1000, synth.required_resolution(2, float(multi.v.min()), 0.01))
+    # the resolution the paper states for N = 10^4 single-phase grains in 3D: M = 200
+    assert synth.required_resolution(3, 1e-4, 0.01) == 200
+    # the rejection rule keeps seeds at least 0.2 N^(-1/D) apart
+    d = np.linalg.norm(single.x[:, None] - single.x[None], axis=-1) + np.eye(500)
+    assert d.min() > 0.2 * 500 ** (-1 / 3)
