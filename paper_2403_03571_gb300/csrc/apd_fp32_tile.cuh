@@ -127,7 +127,7 @@ struct SharedLayout {
     float glb[16][kChunk / kGroup];  // per warp: cost lower bound of each group of the chunk
     float gwp[16][kChunk / kGroup];  // per warp: the weight part of that bound
     double cref[4];  // tile centre (FP64) and the reference weight wref
-    unsigned long long scored;  // pixel-seed pairs the CTA's fast passes evaluated in this tile
+    unsigned long long scored;  // pixel-seed pairs the CTA's scoring evaluated in this tile
 };
 
 template <int D>

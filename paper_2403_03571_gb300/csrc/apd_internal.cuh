@@ -99,7 +99,7 @@ struct Workspace {
     int4 *tc_cand = nullptr;            // [max_j] tensor-core candidates per pixel (3 seeds, 4th score)
     bool sorted = false;                // set by launch_seed_prep for the current pass
     bool prune = false;                 // FP32 scoring skips seed groups by their bounds
-    unsigned long long *pairs_scored = nullptr;  // device counter: pairs the FP32 fast pass evaluated
+    unsigned long long *pairs_scored = nullptr;  // device counter: pairs the FP32 scoring evaluated
     unsigned long long *moments = nullptr;  // [max_n * K]
     uint32_t *flags = nullptr;          // [max_j]
     int32_t *flag_gi = nullptr;         // [max_j] FP32 best seed of each queued pixel (-1: none)
