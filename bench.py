@@ -63,7 +63,7 @@ def parse():
                     help="--mode assign: score with seed-group pruning")
     ap.add_argument("--no-prune", dest="prune", action="store_false",
                     help="score the chosen form densely (no seed-group pruning)")
-    ap.add_argument("--mode", default="apd", choices=["apd", "assign", "sweep"],
+    ap.add_argument("--mode", default="apd", choices=["apd", "assign", "sweep", "points"],
                     help="apd: the full benchmark; assign: only repeated scoring+moments calls "
                          "(apd_cell_moments) at zero weights, for kernel profiling; sweep: the "
                          "paper's runtime tests (Section 3.2), one JSON line per point")
@@ -659,6 +659,40 @@ def run_batch(args):
     }
 
 
+def run_points(args):
+    """Non-uniform discretisation: apd_points_moments over random sample points
+    (as many as the workload's pixels, uniform in the box, equal measures) with
+    the workload's seeds at random weights; one JSON line with pairs/s."""
+    import torch
+    from paper_2403_03571_gb300 import build, capi
+    build.build()
+    capi.load()
+    inst, _ = make_instance(args.workload, 0)
+    dim, n, count = inst.grid.dim, inst.n, inst.grid.num_pixels
+    g = np.random.Generator(np.random.PCG64(17))
+    lo, hi = np.asarray(inst.grid.lo), np.asarray(inst.grid.hi)
+    y = torch.from_numpy(lo + (hi - lo) * g.random((count, dim))).cuda()
+    mass = torch.full((count,), float(np.prod(hi - lo)) / count, dtype=torch.float64, device="cuda")
+    x, A = torch.from_numpy(inst.x).cuda(), torch.from_numpy(inst.A).cuda()
+    w = torch.from_numpy(0.3 * g.standard_normal(n) * n ** (-2.0 / dim)).cuda()
+    mom = torch.zeros((n, 1 + dim + dim * (dim + 1) // 2), dtype=torch.float64, device="cuda")
+    ws = capi.Workspace(dim, n, 64)
+    for _ in range(args.warmup):
+        capi.apd_points_moments(y, mass, x, A, w, mom, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        capi.apd_points_moments(y, mass, x, A, w, mom, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    assert ws.status() == capi.APD_OK
+    s = e0.elapsed_time(e1) / args.steps / 1000.0
+    print(json.dumps({"mode": "points", "workload": args.workload, "points": count, "seeds": n,
+                      "call_ms": s * 1e3, "pairs_per_s": count * n / s}))
+    return 0
+
+
 def run_sweep(args):
     """The paper's runtime tests (Section 3.2) on this GPU, one JSON line per point:
     (a) Algorithm 1 for a fixed (X, W = 0, Lambda) in FP32 (labels), dense and
@@ -748,6 +782,8 @@ def main():
         return run_assign_only(args)
     if args.mode == "sweep":
         return run_sweep(args)
+    if args.mode == "points":
+        return run_points(args)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:

@@ -475,6 +475,34 @@ int apd_solve_weights_refine(const apd_grid *grid, const apd_seeds *seeds, const
                              const apd_solve_opts *opts, const apd_refine_opts *ro, apd_solve_info *info,
                              apd_grid *grid_out, apd_workspace *ws, apd_stream_t stream);
 
+/* ---- Non-uniform discretisation (Section 2.3) -----------------------------
+ * Elements P_j of any shape, given by a sample point y_j and a measure |P_j|
+ * (the regular grid is the case y_j = pixel centre, |P_j| = |P|).  Labels as
+ * Algorithm 1 (FP64 argmin, lowest index on ties, equal to a full FP64
+ * evaluation); moments are the measure-weighted sums m_i = sum |P_j|,
+ * S1_i = sum |P_j| y_j and S2_i = sum |P_j| y_j y_j^T (upper triangle, a <= b,
+ * row-major), in FP64, accumulated with atomics (their last bits depend on the
+ * order of the additions). */
+typedef struct {
+    int32_t dim;          /* 2 or 3 */
+    int64_t count;        /* number of elements, >= 1 */
+    const double *y;      /* [count][dim] sample points (device) */
+    const double *mass;   /* [count] element measures |P_j| (device) */
+} apd_points;
+
+/* Labels (nullable, [count] int32) and FP64 moments [n][1 + D + D(D+1)/2]
+ * (device, overwritten) of the elements.  Stream-ordered; argument errors are
+ * returned (null pointers, count < 1, dim mismatch, n above the workspace's
+ * max_n), device-side errors latch in the workspace. */
+int apd_points_moments(const apd_points *pts, const apd_seeds *seeds, double *moments, int32_t *labels,
+                       apd_workspace *ws, apd_stream_t stream);
+
+/* Eqs. (2.7)-(2.8) on the elements: g~ = sum_i v_i w_i + sum_j |P_j| c_{H_j j}
+ * into g_out[0], grad_i = v_i - m_i into grad [n], max_i |grad_i| / v_i into
+ * max_rel_err[0] (all device).  Stream-ordered; errors as apd_points_moments. */
+int apd_points_dual_value_grad(const apd_points *pts, const apd_seeds *seeds, const double *v, double *g_out,
+                               double *grad, double *max_rel_err, apd_workspace *ws, apd_stream_t stream);
+
 /* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
  * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).
  * Returns M >= 1, or -1 for invalid arguments. */

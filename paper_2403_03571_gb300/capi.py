@@ -43,6 +43,7 @@ EXPORTED = (
     "apd_multires_opts_default", "apd_solve_weights_multires", "apd_batch_solve_weights_multires",
     "apd_warmstart_train_step_pairs", "apd_workspace_set_pruning", "apd_batch_set_pruning",
     "apd_profile_read_scored", "apd_lloyd_multires", "apd_refine_opts_default", "apd_solve_weights_refine",
+    "apd_points_moments", "apd_points_dual_value_grad",
 )
 
 
@@ -85,6 +86,11 @@ class ApdMultiresOpts(ctypes.Structure):
 
 class ApdRefineOpts(ctypes.Structure):
     _fields_ = [("growth", ctypes.c_double), ("max_res", ctypes.c_int32 * 3), ("max_rounds", ctypes.c_int32)]
+
+
+class ApdPoints(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("count", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p)]
 
 
 class ApdError(RuntimeError):
@@ -178,6 +184,8 @@ def load(path: Optional[str] = None):
     L.apd_lloyd_multires.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, ctypes.c_int32, _vp, _vp, _P(ApdSolveOpts),
                                      _P(ApdMultiresOpts), _P(ApdSolveInfo), _vp, _vp, _P(ctypes.c_int32), _vp]
     L.apd_batch_set_pruning.argtypes = [_vp, ctypes.c_int32]
+    L.apd_points_moments.argtypes = [_P(ApdPoints), _P(ApdSeeds), _vp, _vp, _vp, _vp]
+    L.apd_points_dual_value_grad.argtypes = [_P(ApdPoints), _P(ApdSeeds), _vp, _vp, _vp, _vp, _vp, _vp]
     L.apd_refine_opts_default.argtypes = [_P(ApdRefineOpts)]
     L.apd_refine_opts_default.restype = None
     L.apd_solve_weights_refine.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _P(ApdSolveOpts),
@@ -573,6 +581,31 @@ def apd_solve_weights_multires(grid, x, A, w0, v, w_out, ws: Workspace, opts=Non
                                            ctypes.byref(used), _stream(stream))
     _check(rc, "apd_solve_weights_multires", _SOLVE_OK)
     return rc, info, used.value
+
+
+def make_points(y, mass) -> ApdPoints:
+    """ApdPoints over device tensors y [count, dim] and mass [count] (FP64, contiguous)."""
+    p = ApdPoints()
+    p.dim = int(y.shape[1])
+    p.count = int(y.shape[0])
+    p.y = _ptr(y)
+    p.mass = _ptr(mass)
+    return p
+
+
+def apd_points_moments(y, mass, x, A, w, moments, ws: Workspace, labels=None, stream=None):
+    """Labels (optional) and FP64 measure-weighted moments of arbitrary elements."""
+    p, s = make_points(y, mass), make_seeds(x, A, w)
+    _check(load().apd_points_moments(ctypes.byref(p), ctypes.byref(s), _ptr(moments), _ptr(labels), ws.handle,
+                                     _stream(stream)), "apd_points_moments")
+
+
+def apd_points_dual_value_grad(y, mass, x, A, w, v, g_out, grad, err_out, ws: Workspace, stream=None):
+    """Eqs. (2.7)-(2.8) on arbitrary elements (device outputs)."""
+    p, s = make_points(y, mass), make_seeds(x, A, w)
+    _check(load().apd_points_dual_value_grad(ctypes.byref(p), ctypes.byref(s), _ptr(v), _ptr(g_out), _ptr(grad),
+                                             _ptr(err_out), ws.handle, _stream(stream)),
+           "apd_points_dual_value_grad")
 
 
 def refine_opts(growth=1.5, max_res=(0, 0, 0), max_rounds=4) -> ApdRefineOpts:

@@ -707,6 +707,37 @@ int apd_dual_value_grad(const apd_grid *grid, const apd_seeds *seeds, const doub
                                ws->w, g_out, grad, nullptr, max_rel_err, st));
 }
 
+static int points_entry(const apd_points *pts, const apd_seeds *seeds, apd_workspace *ws) {
+    if (!pts || (pts->dim != 2 && pts->dim != 3) || pts->count < 1 || !pts->y || !pts->mass) return APD_ERR_ARG;
+    APD_TRY(validate_seeds(seeds));
+    if (!ws) return APD_ERR_ARG;
+    if (ws->w.dim != pts->dim || seeds->n > ws->w.max_n) return APD_ERR_WORKSPACE;
+    return APD_OK;
+}
+
+int apd_points_moments(const apd_points *pts, const apd_seeds *seeds, double *moments, int32_t *labels,
+                       apd_workspace *ws, apd_stream_t stream) {
+    APD_TRY(points_entry(pts, seeds, ws));
+    if (!moments) return APD_ERR_ARG;
+    ws->w.kernel_launches += 4;
+    return cuda_ok(launch_points_assign(pts->dim, pts->count, pts->y, pts->mass, seeds->n, seeds->x, seeds->A,
+                                        seeds->w, moments, labels, ws->w, (cudaStream_t)stream));
+}
+
+int apd_points_dual_value_grad(const apd_points *pts, const apd_seeds *seeds, const double *v, double *g_out,
+                               double *grad, double *max_rel_err, apd_workspace *ws, apd_stream_t stream) {
+    APD_TRY(points_entry(pts, seeds, ws));
+    if (!v || !g_out || !max_rel_err) return APD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the workspace's moment buffer ([max_n][K] words) holds the FP64 moments
+    double *mom = reinterpret_cast<double *>(ws->w.moments);
+    APD_TRY(cuda_ok(launch_points_assign(pts->dim, pts->count, pts->y, pts->mass, seeds->n, seeds->x, seeds->A,
+                                         seeds->w, mom, nullptr, ws->w, st)));
+    ws->w.kernel_launches += 5;
+    return cuda_ok(launch_points_dual(pts->dim, seeds->n, seeds->x, seeds->A, seeds->w, v, mom, ws->w, g_out, grad,
+                                      max_rel_err, st));
+}
+
 static int solve_entry(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
                        const apd_solve_opts *opts, GridDev &g, apd_solve_opts &o, apd_workspace *ws,
                        cudaStream_t st) {

@@ -281,4 +281,25 @@ __device__ __forceinline__ void dual_terms(const GridDev &g, const unsigned long
         }
 }
 
+// Per-cell dual terms from FP64 element-measure moments (non-uniform
+// discretisation): m = sum |P_j|, S1 = sum |P_j| y_j, S2 = sum |P_j| y_j y_j^T
+// (upper triangle); Q = sum_j |P_j| (y_j - x)^T A (y_j - x) expanded in them.
+template <int D>
+__device__ __forceinline__ void dual_terms_points(const double *__restrict__ mo, const double vi,
+                                                  const double *__restrict__ xi, const double *__restrict__ Ai,
+                                                  double &gr, double &Q) {
+    const double m = mo[0];
+    gr = vi - m;
+    Q = 0.0;
+    int t = 1 + D;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) {
+            const double Cab = mo[t++] - mo[1 + a] * xi[b] - xi[a] * mo[1 + b] + m * xi[a] * xi[b];
+            const double Aab = (a == b) ? Ai[a * D + a] : Ai[a * D + b] + Ai[b * D + a];
+            Q += Aab * Cab;
+        }
+}
+
 }  // namespace apd

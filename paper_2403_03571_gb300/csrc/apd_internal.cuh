@@ -250,6 +250,14 @@ constexpr int moment_width(int dim) { return 1 + dim + dim * (dim + 1) / 2; }
 
 // zero the per-evaluation counters and statistics in sc
 cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry = false);
+// non-uniform discretisation (apd_points.cu, apd_kernels.cu): labels and FP64
+// element-measure moments of `count` points; the dual from those moments
+cudaError_t launch_points_assign(int dim, long long count, const double *y, const double *mass, int n,
+                                 const double *x, const double *A, const double *w, double *mom,
+                                 int32_t *labels, Workspace &ws, cudaStream_t st);
+cudaError_t launch_points_dual(int dim, int n, const double *x, const double *A, const double *w, const double *v,
+                               const double *mom_pts, Workspace &ws, double *g_out, double *grad_out,
+                               double *err_out, cudaStream_t st);
 // start of an evaluation with the records of the last launch_seed_prep (same x,
 // A, n): zeroed moments and counters, weights W0 + t pdir (into Wt; pdir null:
 // W0 itself) in the records, wref and the group weight gaps

@@ -2,6 +2,7 @@
 // moments, the discrete centroids of Algorithm 3, and the vector kernels of
 // the L-BFGS weight solve (Algorithm 2).
 #include <float.h>
+#include <string.h>
 
 #include "apd_common.cuh"
 
@@ -171,26 +172,32 @@ __global__ void gather_recs_kernel(const int n_pad, const int32_t *__restrict__ 
 // Per-cell dual terms from the integer moments (dual_terms), then a
 // deterministic two-phase reduction (block partials summed in block order by
 // the last block):  g_i = (v_i - m_i |P|) w_i + |P| Q_i,  grad_i = v_i - m_i |P|.
-template <int D>
+// kPoints: FP64 element-measure moments of a non-uniform discretisation
+// (mom_pts), g_i = (v_i - m_i) w_i + Q_i, grad_i = v_i - m_i.
+template <int D, bool kPoints = false>
 __global__ void __launch_bounds__(256)
     dual_kernel(const GridDev g, const int n, const double *__restrict__ x,
                 const double *__restrict__ A, const double *__restrict__ w,
                 const double *__restrict__ v, const double *__restrict__ p_dir,
                 const unsigned long long *__restrict__ mom, double *__restrict__ part,
                 DevScalars *__restrict__ sc, double *g_out, double *grad_out, double *gf_out,
-                double *err_out) {
+                double *err_out, const double *__restrict__ mom_pts = nullptr) {
     constexpr int K = moment_width(D);
     __shared__ double sh[33];
     __shared__ bool last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double gsum = 0.0, emax = 0.0, gp = 0.0, sv = 0.0, vmin = DBL_MAX;
     if (i < n) {
-        const unsigned long long *mo = mom + (size_t)i * K;
         const double vi = v[i], wi = w[i];
         if (!(vi > 0.0) || !isfinite(vi)) atomicOr(&sc->status, ST_BAD_VOLUME);
         double gr, Q;
-        dual_terms<D>(g, mo, vi, x + (size_t)i * D, A + (size_t)i * D * D, gr, Q);
-        gsum = gr * wi + g.cell * Q;
+        if (kPoints) {
+            dual_terms_points<D>(mom_pts + (size_t)i * K, vi, x + (size_t)i * D, A + (size_t)i * D * D, gr, Q);
+            gsum = gr * wi + Q;
+        } else {
+            dual_terms<D>(g, mom + (size_t)i * K, vi, x + (size_t)i * D, A + (size_t)i * D * D, gr, Q);
+            gsum = gr * wi + g.cell * Q;
+        }
         emax = __ddiv_rn(fabs(gr), vi);
         if (grad_out) grad_out[i] = gr;
         if (gf_out) gf_out[i] = -gr;
@@ -430,6 +437,23 @@ cudaError_t launch_dual(const GridDev &g, int n, const double *x, const double *
     else
         dual_kernel<2><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
                                                    grad_out, gf_out, err_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points_dual(int dim, int n, const double *x, const double *A, const double *w, const double *v,
+                               const double *mom_pts, Workspace &ws, double *g_out, double *grad_out,
+                               double *err_out, cudaStream_t st) {
+    const int threads = n <= 4096 ? 64 : 256;
+    const int blocks = (n + threads - 1) / threads;
+    GridDev g;
+    memset(&g, 0, sizeof g);
+    g.dim = dim;
+    if (dim == 3)
+        dual_kernel<3, true><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, nullptr, nullptr, ws.part, ws.sc, g_out,
+                                                         grad_out, nullptr, err_out, mom_pts);
+    else
+        dual_kernel<2, true><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, nullptr, nullptr, ws.part, ws.sc, g_out,
+                                                         grad_out, nullptr, err_out, mom_pts);
     return cudaGetLastError();
 }
 

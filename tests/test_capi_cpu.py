@@ -109,6 +109,18 @@ def test_argument_errors_before_cuda(lib):
                                             None, None, None, None) == capi.APD_ERR_ARG
     assert lib.apd_solve_weights_refine(None, None, None, None, None, None, None, None, None,
                                         None) == capi.APD_ERR_ARG
+    # non-uniform discretisation: argument checks before any CUDA call
+    pts = capi.ApdPoints()
+    pts.dim, pts.count = 2, 10
+    assert lib.apd_points_moments(ctypes.byref(pts), ctypes.byref(s), None, None, None, None) == capi.APD_ERR_ARG
+    pts.y = pts.mass = 16  # non-null, never dereferenced on this path
+    assert lib.apd_points_moments(ctypes.byref(pts), None, None, None, None, None) == capi.APD_ERR_ARG
+    pts.dim = 4
+    assert lib.apd_points_dual_value_grad(ctypes.byref(pts), ctypes.byref(s), None, None, None, None, None,
+                                          None) == capi.APD_ERR_ARG
+    pts.dim, pts.count = 2, 0
+    assert lib.apd_points_moments(ctypes.byref(pts), ctypes.byref(s), None, None, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_points_moments(None, None, None, None, None, None) == capi.APD_ERR_ARG
     # warm-start network: sizes, argument checks without a device
     f, p = ctypes.c_int32(), ctypes.c_int32()
     assert lib.apd_warmstart_sizes(2, ctypes.byref(f), ctypes.byref(p)) == capi.APD_OK
