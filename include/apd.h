@@ -475,6 +475,14 @@ int apd_solve_weights_refine(const apd_grid *grid, const apd_seeds *seeds, const
                              const apd_solve_opts *opts, const apd_refine_opts *ro, apd_solve_info *info,
                              apd_grid *grid_out, apd_workspace *ws, apd_stream_t stream);
 
+/* The refinement rule of apd_solve_weights_refine, on the host: the grid of
+ * the same box with every resolution scaled by f = max(growth, (J_(2.10) /
+ * J)^(1/D)) and rounded up, J_(2.10) = |Omega| 2^D / (eps v_min).  Returns
+ * APD_OK with *next written, 1 when it exceeds ro->max_res on an axis or
+ * max_pixels (> 0), APD_ERR_ARG for invalid arguments (no device use). */
+int apd_refine_next_grid(const apd_grid *grid, double v_min, double eps, const apd_refine_opts *ro,
+                         int64_t max_pixels, apd_grid *next);
+
 /* ---- Non-uniform discretisation (Section 2.3) -----------------------------
  * Elements P_j of any shape, given by a sample point y_j and a measure |P_j|
  * (the regular grid is the case y_j = pixel centre, |P_j| = |P|).  Labels as

@@ -43,7 +43,7 @@ EXPORTED = (
     "apd_multires_opts_default", "apd_solve_weights_multires", "apd_batch_solve_weights_multires",
     "apd_warmstart_train_step_pairs", "apd_workspace_set_pruning", "apd_batch_set_pruning",
     "apd_profile_read_scored", "apd_lloyd_multires", "apd_refine_opts_default", "apd_solve_weights_refine",
-    "apd_points_moments", "apd_points_dual_value_grad",
+    "apd_points_moments", "apd_points_dual_value_grad", "apd_refine_next_grid",
 )
 
 
@@ -186,6 +186,8 @@ def load(path: Optional[str] = None):
     L.apd_batch_set_pruning.argtypes = [_vp, ctypes.c_int32]
     L.apd_points_moments.argtypes = [_P(ApdPoints), _P(ApdSeeds), _vp, _vp, _vp, _vp]
     L.apd_points_dual_value_grad.argtypes = [_P(ApdPoints), _P(ApdSeeds), _vp, _vp, _vp, _vp, _vp, _vp]
+    L.apd_refine_next_grid.argtypes = [_P(ApdGrid), ctypes.c_double, ctypes.c_double, _P(ApdRefineOpts),
+                                       ctypes.c_int64, _P(ApdGrid)]
     L.apd_refine_opts_default.argtypes = [_P(ApdRefineOpts)]
     L.apd_refine_opts_default.restype = None
     L.apd_solve_weights_refine.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp, _P(ApdSolveOpts),

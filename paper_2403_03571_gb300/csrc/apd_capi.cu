@@ -754,6 +754,31 @@ static int solve_entry(const apd_grid *grid, const apd_seeds *seeds, const doubl
     return take_status(ws->w, st);
 }
 
+int apd_refine_next_grid(const apd_grid *grid, double v_min, double eps, const apd_refine_opts *ro,
+                         int64_t max_pixels, apd_grid *next) {
+    GridDev g;
+    if (!ro || !next || validate_grid(grid, g) != APD_OK) return APD_ERR_ARG;
+    if (!(v_min > 0.0) || !(eps > 0.0) || !std::isfinite(v_min) || !std::isfinite(eps) || !(ro->growth > 1.0) ||
+        !std::isfinite(ro->growth))
+        return APD_ERR_ARG;
+    // eq. (2.10) for the smallest target volume: J >= |Omega| 2^D / (eps v_min)
+    const double J = (double)g.J;
+    const double J_need = domain_measure(grid) * std::pow(2.0, grid->dim) / (eps * v_min);
+    const double f = std::max(ro->growth, std::pow(std::max(J_need / J, 1.0), 1.0 / grid->dim));
+    apd_grid nxt = *grid;
+    double Jn = 1.0;
+    for (int d = 0; d < grid->dim; ++d) {
+        const double m = std::ceil(grid->res[d] * f);
+        const double cap = ro->max_res[d] > 0 ? (double)ro->max_res[d] : 2147483647.0;
+        if (!(m <= cap)) return 1;
+        nxt.res[d] = (int32_t)m;
+        Jn *= m;
+    }
+    if (max_pixels > 0 && Jn > (double)max_pixels) return 1;
+    *next = nxt;
+    return APD_OK;
+}
+
 void apd_refine_opts_default(apd_refine_opts *ro) {
     if (!ro) return;
     ro->growth = 1.5;
@@ -791,22 +816,8 @@ int apd_solve_weights_refine(const apd_grid *grid, const apd_seeds *seeds, const
         inf.g = last.g;
         if (rc != APD_NOT_CONVERGED && rc != APD_WARN_TOL_INFEASIBLE) break;
         if (round >= r.max_rounds) break;
-        // eq. (2.10) for the smallest target volume: J >= |Omega| 2^D / (eps v_min)
-        const double vmin = ws->w.sc_host->min_v;
-        const double J = (double)g.J;
-        const double J_need = domain_measure(&cur) * std::pow(2.0, cur.dim) / (o.eps * vmin);
-        const double f = std::max(r.growth, std::pow(std::max(J_need / J, 1.0), 1.0 / cur.dim));
-        apd_grid nxt = cur;
-        bool fits = true;
-        double Jn = 1.0;
-        for (int d = 0; d < cur.dim; ++d) {
-            const double m = std::ceil(cur.res[d] * f);
-            const double cap = r.max_res[d] > 0 ? (double)r.max_res[d] : 2147483647.0;
-            if (!(m <= cap)) fits = false;
-            nxt.res[d] = fits ? (int32_t)m : cur.res[d];
-            Jn *= m;
-        }
-        if (!fits || Jn > (double)ws->w.max_j) break;
+        apd_grid nxt;
+        if (apd_refine_next_grid(&cur, ws->w.sc_host->min_v, o.eps, &r, ws->w.max_j, &nxt) != APD_OK) break;
         GridDev gn;
         if (validate_grid(&nxt, gn) != APD_OK) break;
         cur = nxt;

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import oracle
@@ -109,6 +110,36 @@ def test_argument_errors_before_cuda(lib):
                                             None, None, None, None) == capi.APD_ERR_ARG
     assert lib.apd_solve_weights_refine(None, None, None, None, None, None, None, None, None,
                                         None) == capi.APD_ERR_ARG
+    # the refinement rule on the host: eq. (2.10) for the smallest volume, or the growth factor
+    gr = capi.ApdGrid()
+    gr.dim = 2
+    gr.res[0] = gr.res[1] = 40
+    gr.lo[0] = gr.lo[1] = 0.0
+    gr.hi[0] = gr.hi[1] = 1.0
+    ro = capi.ApdRefineOpts()
+    lib.apd_refine_opts_default(ctypes.byref(ro))
+    nxt = capi.ApdGrid()
+    vmin = 0.005
+    assert lib.apd_refine_next_grid(ctypes.byref(gr), vmin, 0.01, ctypes.byref(ro), 0, ctypes.byref(nxt)) == 0
+    f = max(1.5, (4.0 / (0.01 * vmin) / 1600.0) ** 0.5)
+    assert nxt.res[0] == nxt.res[1] == int(np.ceil(40 * f)) == 283
+    assert (nxt.lo[0], nxt.hi[1]) == (0.0, 1.0)
+    assert lib.apd_refine_next_grid(ctypes.byref(gr), 0.5, 0.01, ctypes.byref(ro), 0, ctypes.byref(nxt)) == 0
+    assert nxt.res[0] == 60  # eq. (2.10) already holds: the growth factor 1.5
+    ro.max_res[0] = 200
+    assert lib.apd_refine_next_grid(ctypes.byref(gr), vmin, 0.01, ctypes.byref(ro), 0, ctypes.byref(nxt)) == 1
+    ro.max_res[0] = 0
+    assert lib.apd_refine_next_grid(ctypes.byref(gr), vmin, 0.01, ctypes.byref(ro), 283 * 283 - 1,
+                                    ctypes.byref(nxt)) == 1
+    assert lib.apd_refine_next_grid(ctypes.byref(gr), 0.0, 0.01, ctypes.byref(ro), 0,
+                                    ctypes.byref(nxt)) == capi.APD_ERR_ARG
+    g3 = capi.ApdGrid()
+    g3.dim = 3
+    for d in range(3):
+        g3.res[d], g3.lo[d], g3.hi[d] = 32, 0.0, 2.0
+    assert lib.apd_refine_next_grid(ctypes.byref(g3), 1e-3, 0.01, ctypes.byref(ro), 0, ctypes.byref(nxt)) == 0
+    f3 = max(1.5, (8.0 * 8.0 / (0.01 * 1e-3) / 32 ** 3) ** (1 / 3))
+    assert nxt.res[0] == nxt.res[2] == int(np.ceil(32 * f3))
     # non-uniform discretisation: argument checks before any CUDA call
     pts = capi.ApdPoints()
     pts.dim, pts.count = 2, 10
