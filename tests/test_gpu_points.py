@@ -37,7 +37,7 @@ def _check_moments(got, ref):
 
 
 @pytest.mark.parametrize("dim,n,count,seed", [(2, 300, 20001, 1), (3, 257, 12345, 2), (2, 1, 777, 3),
-                                             (3, 600, 5000, 4)])
+                                             (3, 600, 5000, 4), (2, 50, 1, 7), (3, 513, 255, 8)])
 def test_points_labels_and_moments_match_oracle(capi, dim, n, count, seed):
     inst = synth.make_instance(dim, n, 8, seed)
     w = _weights(n, dim, seed)
@@ -91,3 +91,20 @@ def test_points_dual_matches_oracle(capi, dim, n, count, seed):
     assert abs(gg - g_ref) <= 1e-10 * max(1e-12, abs(g_ref)) + 1e-15
     np.testing.assert_allclose(host(grad), grad_ref, rtol=0, atol=1e-13)
     assert float(host(e_out)[0]) == pytest.approx(err_ref, rel=1e-10)
+
+
+def test_points_exact_ties_go_to_the_lowest_index(capi):
+    # two seeds with the same A and w, points on their bisector: equal FP64 costs
+    x = np.array([[0.25, 0.5], [0.75, 0.5], [0.5, 0.9]])
+    A = np.stack([np.eye(2)] * 3)
+    w = np.zeros(3)
+    y = np.stack([np.full(64, 0.5), np.linspace(0.0, 0.6, 64)], axis=1)
+    mass = np.full(64, 1.0 / 64)
+    ws = capi.Workspace(2, 3, 64)
+    mom = torch.zeros((3, 6), dtype=torch.float64, device="cuda")
+    labels = torch.full((64,), -1, dtype=torch.int32, device="cuda")
+    capi.apd_points_moments(dev(y), dev(mass), dev(x), dev(A), dev(w), mom, ws, labels=labels)
+    assert ws.status() == capi.APD_OK
+    ref = op.assign(y, x, A, w)
+    assert np.array_equal(host(labels), ref)
+    assert (ref[y[:, 1] < 0.5] == 0).all()
