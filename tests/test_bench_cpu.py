@@ -1,0 +1,45 @@
+"""bench.py's host side without a GPU: the reference arm (the FP64 oracle on the
+host cores) prints one JSON line with the contract's keys, and only rank 0 of
+a multi-rank launch prints it."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(extra_env=None, *args):
+    env = dict(os.environ)
+    env.update(extra_env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = _run({"RANK": "0"}, "--workload", "2d_n20_256sq", "--steps", "2", "--warmup", "1")
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in out, key
+    assert out["impl"] == "reference"
+    assert out["steps"] == 2 and out["warmup"] == 1 and out["n_gpus"] == 1
+    assert out["higher_is_better"] is True and out["dtype"] == "f64"
+    assert out["value"] > 0 and out["cpu_baseline"]["value"] == out["value"]
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
+    assert out["config"]["workload"] == "2d_n20_256sq"
+    # the time per APD is the evaluation time times the evaluations per APD
+    assert out["ms_per_step"] == pytest.approx(1000.0 / out["value"], rel=1e-9)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run({"RANK": "1", "WORLD_SIZE": "2"}, "--workload", "2d_n20_256sq", "--steps", "1", "--warmup", "0")
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
