@@ -63,10 +63,13 @@ def parse():
                     help="--mode assign: score with seed-group pruning")
     ap.add_argument("--no-prune", dest="prune", action="store_false",
                     help="score the chosen form densely (no seed-group pruning)")
-    ap.add_argument("--mode", default="apd", choices=["apd", "assign", "sweep", "points"],
+    ap.add_argument("--mode", default="apd", choices=["apd", "assign", "sweep", "points", "masked"],
                     help="apd: the full benchmark; assign: only repeated scoring+moments calls "
                          "(apd_cell_moments) at zero weights, for kernel profiling; sweep: the "
-                         "paper's runtime tests (Section 3.2), one JSON line per point")
+                         "paper's runtime tests (Section 3.2), one JSON line per point; points: "
+                         "the non-uniform discretisation; masked: the masked two-level "
+                         "discretisation against the full fine grid")
+    ap.add_argument("--masked-refine", type=int, default=2, help="masked: refinement factor r")
     ap.add_argument("--sweep-test", default="ab", help="sweep: 'a' (Algorithm 1), 'b' (Algorithm 2) or both")
     ap.add_argument("--sweep-dims", default="2,3")
     ap.add_argument("--sweep-alpha", default="0,0.3,0.7")
@@ -693,6 +696,60 @@ def run_points(args):
     return 0
 
 
+def run_masked(args):
+    """Masked two-level discretisation against the full fine grid: the workload's
+    grid is the fine grid F, the coarse grid has 1/r of its resolution; seeds
+    at random weights.  One JSON line: the time of apd_masked_moments and of
+    apd_cell_moments on F (both with seed pruning), the fraction of F scored by
+    the masked call, and how far its cell volumes are from F's exact ones."""
+    import torch
+    from paper_2403_03571_gb300 import build, capi, synth
+    build.build()
+    capi.load()
+    inst, _ = make_instance(args.workload, 0)
+    r = args.masked_refine
+    fg = inst.grid
+    if any(m % r for m in fg.res):
+        raise SystemExit(f"the resolution {fg.res} is not a multiple of {r}")
+    cg = synth.Grid(fg.dim, tuple(m // r for m in fg.res), lo=fg.lo, hi=fg.hi)
+    dim, n = fg.dim, inst.n
+    g = np.random.Generator(np.random.PCG64(5))
+    x, A = torch.from_numpy(inst.x).cuda(), torch.from_numpy(inst.A).cuda()
+    w = torch.from_numpy(0.3 * g.standard_normal(n) * n ** (-2.0 / dim)).cuda()
+    K = 1 + dim + dim * (dim + 1) // 2
+    mom = torch.zeros((n, K), dtype=torch.int64, device="cuda")
+    full = torch.zeros((n, K), dtype=torch.int64, device="cuda")
+    lab = torch.empty(cg.num_pixels, dtype=torch.int32, device="cuda")
+    refined = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = capi.Workspace(dim, n, fg.num_pixels)
+    ws.set_pruning(True)
+
+    def timed(call):
+        for _ in range(args.warmup):
+            call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_masked = timed(lambda: capi.apd_masked_moments(cg, r, x, A, w, mom, lab, ws, refined=refined))
+    ms_full = timed(lambda: capi.apd_cell_moments(fg, x, A, w, full, ws))
+    assert ws.status() == capi.APD_OK
+    m_masked = mom[:, 0].double().cpu().numpy()
+    m_full = full[:, 0].double().cpu().numpy()
+    dev_rel = np.abs(m_masked - m_full) / np.maximum(m_full, 1.0)
+    print(json.dumps({"mode": "masked", "workload": args.workload, "refine": r, "coarse": list(cg.res),
+                      "fine": list(fg.res), "seeds": n, "masked_ms": ms_masked, "fine_grid_ms": ms_full,
+                      "refined_fraction": int(refined.item()) / fg.num_pixels,
+                      "max_rel_volume_dev": float(dev_rel.max()),
+                      "pixels_moved_lower_bound": int(np.abs(m_masked - m_full).sum() // 2)}))
+    return 0
+
+
 def run_sweep(args):
     """The paper's runtime tests (Section 3.2) on this GPU, one JSON line per point:
     (a) Algorithm 1 for a fixed (X, W = 0, Lambda) in FP32 (labels), dense and
@@ -784,6 +841,8 @@ def main():
         return run_sweep(args)
     if args.mode == "points":
         return run_points(args)
+    if args.mode == "masked":
+        return run_masked(args)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:

@@ -511,6 +511,48 @@ int apd_points_moments(const apd_points *pts, const apd_seeds *seeds, double *mo
 int apd_points_dual_value_grad(const apd_points *pts, const apd_seeds *seeds, const double *v, double *g_out,
                                double *grad, double *max_rel_err, apd_workspace *ws, apd_stream_t stream);
 
+/* ---- Masked two-level discretisation (Section 4) ---------------------------
+ * The paper's outlook: adaptable pixel sizes, with the pixels at the cell
+ * boundaries found and refined by masking.  It gives no algorithm; this
+ * library's reading, on a coarse grid G (the `coarse` argument) and an
+ * integer factor r >= 1:
+ *   1. Algorithm 1 on G gives the coarse labels H^G.
+ *   2. A coarse pixel is a boundary pixel when a pixel of its 3^D
+ *      neighbourhood (faces, edges and corners) inside the grid has another
+ *      label, else an interior pixel.
+ *   3. The fine grid F has r res[d] pixels per axis on the same box.  A fine
+ *      pixel inside an interior coarse pixel takes that pixel's label; a fine
+ *      pixel inside a boundary coarse pixel is labelled by Algorithm 1 on F
+ *      (exact FP64 argmin, lowest index on ties).
+ * The result is a labelling of F: its integer moments (count, sum u,
+ * sum u u^T with u = 2k + 1 of the fine pixel indices k, the layout of
+ * apd_cell_moments) feed eqs. (2.7)-(2.8) on F.  It equals the full
+ * Algorithm 1 on F wherever no cell boundary passes through an interior
+ * coarse pixel (always, for example, across the straight boundary of two
+ * seeds with equal A away from the grid's outer layer); the fine pixels
+ * scored cost the full seed scan each, so the saving is the fraction of
+ * interior coarse pixels.
+ *
+ * moments: device int64 [n][1 + D + D(D+1)/2], overwritten.
+ * coarse_labels: device int32 [J_G], written with H^G.
+ * refined: device int64 [1], nullable: the number of fine pixels of step 3
+ *          labelled by Algorithm 1 (r^D times the boundary coarse pixels).
+ * Stream-ordered.  APD_ERR_ARG: invalid grid or seeds, null moments or
+ * coarse_labels, r < 1, or a fine grid of 2^31 pixels or more;
+ * APD_ERR_WORKSPACE: the workspace does not hold the coarse grid and n
+ * seeds.  Device-side errors latch in the workspace. */
+int apd_masked_moments(const apd_grid *coarse, int32_t refine, const apd_seeds *seeds, int64_t *moments,
+                       int32_t *coarse_labels, int64_t *refined, apd_workspace *ws, apd_stream_t stream);
+
+/* Eqs. (2.7)-(2.8) on the fine grid F from the moments of apd_masked_moments
+ * (held in the workspace): g~ into g_out[0], grad_i = v_i - |P_F| m_i into
+ * grad [n] (nullable), max_i |grad_i| / v_i into max_rel_err[0] (all
+ * device).  Arguments and errors as apd_masked_moments, plus null v, g_out
+ * or max_rel_err: APD_ERR_ARG. */
+int apd_masked_dual_value_grad(const apd_grid *coarse, int32_t refine, const apd_seeds *seeds, const double *v,
+                               double *g_out, double *grad, double *max_rel_err, int32_t *coarse_labels,
+                               apd_workspace *ws, apd_stream_t stream);
+
 /* Eq. (2.10): smallest M with |Omega| / M^D <= eps v_min / 2^D (the non-strict
  * reading, which gives the paper's M = 200 for D = 3, N = 10^4, v = 1/N).
  * Returns M >= 1, or -1 for invalid arguments. */

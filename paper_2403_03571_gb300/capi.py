@@ -44,6 +44,7 @@ EXPORTED = (
     "apd_warmstart_train_step_pairs", "apd_workspace_set_pruning", "apd_batch_set_pruning",
     "apd_profile_read_scored", "apd_lloyd_multires", "apd_refine_opts_default", "apd_solve_weights_refine",
     "apd_points_moments", "apd_points_dual_value_grad", "apd_refine_next_grid",
+    "apd_masked_moments", "apd_masked_dual_value_grad",
 )
 
 
@@ -186,6 +187,9 @@ def load(path: Optional[str] = None):
     L.apd_batch_set_pruning.argtypes = [_vp, ctypes.c_int32]
     L.apd_points_moments.argtypes = [_P(ApdPoints), _P(ApdSeeds), _vp, _vp, _vp, _vp]
     L.apd_points_dual_value_grad.argtypes = [_P(ApdPoints), _P(ApdSeeds), _vp, _vp, _vp, _vp, _vp, _vp]
+    L.apd_masked_moments.argtypes = [_P(ApdGrid), ctypes.c_int32, _P(ApdSeeds), _vp, _vp, _vp, _vp, _vp]
+    L.apd_masked_dual_value_grad.argtypes = [_P(ApdGrid), ctypes.c_int32, _P(ApdSeeds), _vp, _vp, _vp, _vp, _vp,
+                                             _vp, _vp]
     L.apd_refine_next_grid.argtypes = [_P(ApdGrid), ctypes.c_double, ctypes.c_double, _P(ApdRefineOpts),
                                        ctypes.c_int64, _P(ApdGrid)]
     L.apd_refine_opts_default.argtypes = [_P(ApdRefineOpts)]
@@ -608,6 +612,26 @@ def apd_points_dual_value_grad(y, mass, x, A, w, v, g_out, grad, err_out, ws: Wo
     _check(load().apd_points_dual_value_grad(ctypes.byref(p), ctypes.byref(s), _ptr(v), _ptr(g_out), _ptr(grad),
                                              _ptr(err_out), ws.handle, _stream(stream)),
            "apd_points_dual_value_grad")
+
+
+def apd_masked_moments(grid, refine, x, A, w, moments, coarse_labels, ws: Workspace, refined=None, stream=None):
+    """Masked two-level discretisation: Algorithm 1 on `grid`, boundary coarse
+    pixels refined by `refine` per axis; integer moments of the fine grid into
+    `moments`, coarse labels into `coarse_labels`, the count of fine pixels
+    scored into `refined` (optional, int64 [1])."""
+    g, s = make_grid(grid), make_seeds(x, A, w)
+    _check(load().apd_masked_moments(ctypes.byref(g), int(refine), ctypes.byref(s), _ptr(moments),
+                                     _ptr(coarse_labels), _ptr(refined), ws.handle, _stream(stream)),
+           "apd_masked_moments")
+
+
+def apd_masked_dual_value_grad(grid, refine, x, A, w, v, g_out, grad, err_out, coarse_labels, ws: Workspace,
+                               stream=None):
+    """Eqs. (2.7)-(2.8) on the fine grid of the masked discretisation (device outputs)."""
+    g, s = make_grid(grid), make_seeds(x, A, w)
+    _check(load().apd_masked_dual_value_grad(ctypes.byref(g), int(refine), ctypes.byref(s), _ptr(v), _ptr(g_out),
+                                             _ptr(grad), _ptr(err_out), _ptr(coarse_labels), ws.handle,
+                                             _stream(stream)), "apd_masked_dual_value_grad")
 
 
 def refine_opts(growth=1.5, max_res=(0, 0, 0), max_rounds=4) -> ApdRefineOpts:

@@ -738,6 +738,54 @@ int apd_points_dual_value_grad(const apd_points *pts, const apd_seeds *seeds, co
                                       max_rel_err, st));
 }
 
+static int masked_entry(const apd_grid *coarse, int32_t refine, const apd_seeds *seeds, const int32_t *coarse_labels,
+                        GridDev &gc, GridDev &gf, apd_workspace *ws) {
+    APD_TRY(validate_grid(coarse, gc));
+    APD_TRY(validate_seeds(seeds));
+    if (refine < 1 || !coarse_labels) return APD_ERR_ARG;
+    apd_grid fine = *coarse;
+    for (int d = 0; d < coarse->dim; ++d) {
+        const long long fr = (long long)coarse->res[d] * refine;
+        if (fr >= (1ll << 31)) return APD_ERR_ARG;
+        fine.res[d] = (int32_t)fr;
+    }
+    APD_TRY(validate_grid(&fine, gf));
+    return check_ws(ws, gc, seeds->n);
+}
+
+// Algorithm 1 on the coarse grid (labels into coarse_labels, its moments into
+// the workspace's scratch), then the mask and the fine scoring into `mom`.
+static int masked_enqueue(const GridDev &gc, const GridDev &gf, int32_t refine, const apd_seeds *seeds,
+                          int32_t *coarse_labels, unsigned long long *mom, int64_t *refined, Workspace &w,
+                          cudaStream_t st) {
+    APD_TRY(enqueue_assign(gc, seeds->n, seeds->x, seeds->A, seeds->w, APD_FP32, w, coarse_labels, w.moments, st));
+    w.kernel_launches += 2;
+    return cuda_ok(launch_masked_refine(gc, gf, refine, seeds->n, seeds->x, seeds->A, seeds->w, coarse_labels, mom,
+                                        reinterpret_cast<long long *>(refined), w, st));
+}
+
+int apd_masked_moments(const apd_grid *coarse, int32_t refine, const apd_seeds *seeds, int64_t *moments,
+                       int32_t *coarse_labels, int64_t *refined, apd_workspace *ws, apd_stream_t stream) {
+    GridDev gc, gf;
+    APD_TRY(masked_entry(coarse, refine, seeds, coarse_labels, gc, gf, ws));
+    if (!moments) return APD_ERR_ARG;
+    return masked_enqueue(gc, gf, refine, seeds, coarse_labels, reinterpret_cast<unsigned long long *>(moments),
+                          refined, ws->w, (cudaStream_t)stream);
+}
+
+int apd_masked_dual_value_grad(const apd_grid *coarse, int32_t refine, const apd_seeds *seeds, const double *v,
+                               double *g_out, double *grad, double *max_rel_err, int32_t *coarse_labels,
+                               apd_workspace *ws, apd_stream_t stream) {
+    GridDev gc, gf;
+    APD_TRY(masked_entry(coarse, refine, seeds, coarse_labels, gc, gf, ws));
+    if (!v || !g_out || !max_rel_err) return APD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    APD_TRY(masked_enqueue(gc, gf, refine, seeds, coarse_labels, ws->w.moments, nullptr, ws->w, st));
+    ws->w.kernel_launches += 1;
+    return cuda_ok(launch_dual(gf, seeds->n, seeds->x, seeds->A, seeds->w, v, nullptr, ws->w.moments, ws->w, g_out,
+                               grad, nullptr, max_rel_err, st));
+}
+
 static int solve_entry(const apd_grid *grid, const apd_seeds *seeds, const double *v, double *w_out,
                        const apd_solve_opts *opts, GridDev &g, apd_solve_opts &o, apd_workspace *ws,
                        cudaStream_t st) {

@@ -76,6 +76,7 @@ struct DevScalars {
     unsigned int dual_done;             // block counter of the two-phase dual reduction
     int pair_ok;                        // the last pushed L-BFGS pair passed the curvature test
     long long rescored_total;
+    unsigned int mask_count;            // boundary coarse pixels listed by the masked discretisation
 };
 
 // Workspace (host struct; device pointers inside).
@@ -258,6 +259,14 @@ cudaError_t launch_points_assign(int dim, long long count, const double *y, cons
 cudaError_t launch_points_dual(int dim, int n, const double *x, const double *A, const double *w, const double *v,
                                const double *mom_pts, Workspace &ws, double *g_out, double *grad_out,
                                double *err_out, cudaStream_t st);
+// masked two-level discretisation (apd_masked.cu), after a coarse scoring pass
+// that left its labels in `coarse_labels` and the seed records in ws: boundary
+// mask, closed-form fine moments of the interior coarse pixels and the fine
+// pixels of the boundary ones scored in FP64 (moments zeroed first; `refined`
+// nullable)
+cudaError_t launch_masked_refine(const GridDev &gc, const GridDev &gf, int r, int n, const double *x,
+                                 const double *A, const double *w, const int32_t *coarse_labels,
+                                 unsigned long long *mom, long long *refined, Workspace &ws, cudaStream_t st);
 // start of an evaluation with the records of the last launch_seed_prep (same x,
 // A, n): zeroed moments and counters, weights W0 + t pdir (into Wt; pdir null:
 // W0 itself) in the records, wref and the group weight gaps

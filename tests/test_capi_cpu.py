@@ -168,3 +168,39 @@ def test_argument_errors_before_cuda(lib):
     lib.apd_warmstart_destroy(None)
     assert lib.apd_tensor_core_check(0, 3, ctypes.byref(ctypes.c_int32()),
                                      ctypes.byref(ctypes.c_float())) == capi.APD_ERR_ARG
+
+
+def test_masked_argument_errors_before_cuda(lib):
+    g = capi.ApdGrid()
+    g.dim = 2
+    g.res[0], g.res[1] = 8, 8
+    g.hi[0], g.hi[1] = 1.0, 1.0
+    s = capi.ApdSeeds()
+    s.n = 3
+    s.x = s.A = s.w = 16  # non-null, never dereferenced on this path
+    lab = ctypes.c_void_p(16)
+    mom = ctypes.c_void_p(16)
+    one = ctypes.c_void_p(16)
+    # refinement factor below one, null coarse labels, a fine grid of 2^31 pixels or more
+    for r in (0, -2):
+        assert lib.apd_masked_moments(ctypes.byref(g), r, ctypes.byref(s), mom, lab, None, None,
+                                      None) == capi.APD_ERR_ARG
+    assert lib.apd_masked_moments(ctypes.byref(g), 2, ctypes.byref(s), mom, None, None, None,
+                                  None) == capi.APD_ERR_ARG
+    assert lib.apd_masked_moments(ctypes.byref(g), 8192, ctypes.byref(s), mom, lab, None, None,
+                                  None) == capi.APD_ERR_ARG
+    assert lib.apd_masked_moments(ctypes.byref(g), 1 << 30, ctypes.byref(s), mom, lab, None, None,
+                                  None) == capi.APD_ERR_ARG
+    # no workspace, bad grid, bad seeds
+    assert lib.apd_masked_moments(ctypes.byref(g), 2, ctypes.byref(s), mom, lab, None, None,
+                                  None) == capi.APD_ERR_ARG
+    assert lib.apd_masked_dual_value_grad(ctypes.byref(g), 2, ctypes.byref(s), one, one, None, one, lab, None,
+                                          None) == capi.APD_ERR_ARG
+    g.dim = 4
+    assert lib.apd_masked_moments(ctypes.byref(g), 2, ctypes.byref(s), mom, lab, None, None,
+                                  None) == capi.APD_ERR_ARG
+    g.dim = 2
+    s.n = 0
+    assert lib.apd_masked_dual_value_grad(ctypes.byref(g), 2, ctypes.byref(s), one, one, None, one, lab, None,
+                                          None) == capi.APD_ERR_ARG
+    assert lib.apd_masked_moments(None, 2, None, None, None, None, None, None) == capi.APD_ERR_ARG
