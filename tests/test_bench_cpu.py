@@ -1,6 +1,6 @@
 """bench.py's host side without a GPU: the reference arm (the FP64 oracle on the
-host cores) prints one JSON line with the contract's keys, and only rank 0 of
-a multi-rank launch prints it."""
+host cores) prints one JSON line with the contract's keys, only rank 0 of a
+multi-rank launch prints it, and the roofline block's arithmetic."""
 import json
 import os
 import subprocess
@@ -43,3 +43,24 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"}, "--workload", "2d_n20_256sq", "--steps", "1", "--warmup", "0")
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_roofline_arithmetic():
+    # the JSON line's roofline block: achieved = evaluated pairs x 2F flops / time,
+    # peak = SMs x 128 FP32 lanes x 2 flops x the max SM clock, frac = achieved / peak
+    import bench
+    peaks, _ = bench.load_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    form = {"precision": "fp32", "pair_rate": 6.0e12, "scored_pair_rate": 3.0e11, "pruned": True,
+            "launch_ms": 0.6, "launches": 10}
+    rb = bench.roofline_block(form, 3, 152, "3d_n1000_256cube_lloyd5")
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    assert rb["bound"] == "alu" and rb["unit"] == "TFLOP/s"
+    assert rb["peak"] == pytest.approx(peak)
+    assert rb["achieved"] == pytest.approx(3.0e11 * 20 / 1e12)
+    assert rb["frac"] == pytest.approx(rb["achieved"] / peak)
+    assert rb["dense_equivalent_frac"] == pytest.approx(6.0e12 * 20 / 1e12 / peak)
+    rb2 = bench.roofline_block(dict(form, precision="tc_tf32"), 2, 152, "2d_n2000_1024sq")
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    assert rb2["bound"] == "tensor" and rb2["peak"] == pytest.approx(bf16 * 1.1 / 2.25)
+    assert rb2["achieved"] == pytest.approx(6.0e12 * 12 / 1e12)
