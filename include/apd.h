@@ -529,9 +529,9 @@ int apd_points_dual_value_grad(const apd_points *pts, const apd_seeds *seeds, co
  * apd_cell_moments) feed eqs. (2.7)-(2.8) on F.  It equals the full
  * Algorithm 1 on F wherever no cell boundary passes through an interior
  * coarse pixel (always, for example, across the straight boundary of two
- * seeds with equal A away from the grid's outer layer); the fine pixels
- * scored cost the full seed scan each, so the saving is the fraction of
- * interior coarse pixels.
+ * seeds with equal A away from the grid's outer layer).  Each fine pixel of a
+ * boundary coarse pixel is scored against every seed (no pruning), so the
+ * call only pays where few coarse pixels are boundary pixels.
  *
  * moments: device int64 [n][1 + D + D(D+1)/2], overwritten.
  * coarse_labels: device int32 [J_G], written with H^G.
