@@ -17,6 +17,10 @@ Functions and the passages they follow (arXiv 2403.03571):
 * ``resolution_lower_bound``   -- eq. (2.9) / Table 1;
 * ``resolution_practical``     -- eq. (2.10).
 
+Submodules: ``points`` (non-uniform discretisation, Section 2.3), ``masked``
+(the masked two-level grid of the Section 4 outlook), ``warmstart`` (features,
+network and losses of the learned warm start).
+
 Parity unpinned: iteration counts of ``solve_weights`` (the paper leaves the
 L-BFGS details open); only its end state (volumes within tolerance) is pinned.
 """
