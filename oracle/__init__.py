@@ -11,6 +11,9 @@ Functions and the passages they follow (arXiv 2403.03571):
 * ``pixel_centres``            -- eq. (2.6), Section 2.3 (regular grid);
 * ``assign`` / ``assign_ids``  -- Algorithm 1 (cost matrix, argmin; lowest index on ties);
 * ``moments``                  -- per-cell counts and integer coordinate moments;
+* ``moments_ids``              -- the same over a listed subset of pixels (a slab of the grid);
+* ``dual_from_moments``        -- eq. (2.7) written through those moments (the form a
+                                  sharded evaluation exchanges);
 * ``dual``                     -- eqs. (2.7), (2.8) and the stop rule of Algorithm 2;
 * ``solve_weights``            -- Algorithm 2 with a library L-BFGS (scipy L-BFGS-B);
 * ``lloyd``                    -- Algorithm 3 (discrete centroids, warm-started weights);
@@ -54,6 +57,8 @@ def lib():
                                         ctypes.c_int32]
         L.oracle_moments.argtypes = [ctypes.c_int32, _c_i32p, ctypes.c_int32, _c_i32p, _c_i64p,
                                      ctypes.c_int32]
+        L.oracle_moments_ids.argtypes = [ctypes.c_int32, _c_i32p, ctypes.c_int32, _c_i64p, ctypes.c_int64,
+                                         _c_i32p, _c_i64p, ctypes.c_int32]
         L.oracle_dual_from_labels.argtypes = [ctypes.c_int32, _c_dp, _c_dp, _c_i32p, ctypes.c_int32,
                                               _c_dp, _c_dp, _c_dp, _c_dp, _c_i32p, _c_dp, _c_dp,
                                               _c_dp, _c_i64p, _c_dp, ctypes.c_int32]
@@ -62,7 +67,7 @@ def lib():
         L.oracle_cost.argtypes = [ctypes.c_int32, _c_dp, _c_dp, _c_dp, ctypes.c_double]
         L.oracle_cost.restype = ctypes.c_double
         L.oracle_max_threads.restype = ctypes.c_int
-        for f in (L.oracle_assign, L.oracle_assign_ids, L.oracle_moments,
+        for f in (L.oracle_assign, L.oracle_assign_ids, L.oracle_moments, L.oracle_moments_ids,
                   L.oracle_dual_from_labels, L.oracle_centroids):
             f.restype = ctypes.c_int
         _lib = L
@@ -160,6 +165,59 @@ def moments(grid, labels, n: int, nthreads: int = 0) -> np.ndarray:
                               _p(out, _c_i64p), nthreads)
     _check(rc, "moments")
     return out
+
+
+def moments_ids(grid, ids, labels, n: int, nthreads: int = 0) -> np.ndarray:
+    """Integer moments (layout of ``moments``) of the listed pixels only: labels[t]
+    belongs to full-grid pixel ids[t], and the odd coordinates u = 2k + 1 are the
+    full grid's, so the moments of a partition of the grid sum to ``moments``."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    if ids.shape != labels.shape:
+        raise ValueError("ids and labels differ in length")
+    res = np.ascontiguousarray(grid.res, dtype=np.int32)
+    out = np.empty((n, moment_width(grid.dim)), dtype=np.int64)
+    rc = lib().oracle_moments_ids(grid.dim, _p(res, _c_i32p), n, _p(ids, _c_i64p), ids.shape[0],
+                                  _p(labels, _c_i32p), _p(out, _c_i64p), nthreads)
+    _check(rc, "moments_ids")
+    return out
+
+
+def slab_ids(grid, k_begin: int, k_count: int) -> np.ndarray:
+    """Linear ids of the pixels whose last-axis index lies in [k_begin, k_begin + k_count)."""
+    per = int(np.prod(grid.res[:-1], dtype=np.int64))
+    return np.arange(k_begin * per, (k_begin + k_count) * per, dtype=np.int64)
+
+
+def dual_from_moments(grid, x, A, w, v, mom):
+    """Eqs. (2.7)-(2.8) from the integer moments alone: with y_j = lo + (h / 2) u_j,
+    c_i = lo - x_i and D = diag(h / 2), the cost sum of cell i is
+        Q_i = m_i c_i^T A_i c_i + 2 c_i^T A_i D S1_i + tr(D A_i D S2_i),
+    so g~ = sum_i (v_i - m_i |P|) w_i + |P| Q_i and grad_i = v_i - m_i |P|.
+    Returns (g~, grad, max_rel_err)."""
+    x, A, w, v = _f64(x), _f64(A), _f64(w), _f64(v)
+    mom = np.asarray(mom, dtype=np.int64)
+    dim = grid.dim
+    h = grid_steps(grid)
+    P = pixel_volume(grid)
+    m = mom[:, 0].astype(np.float64)
+    S1 = mom[:, 1:1 + dim].astype(np.float64)
+    S2 = np.zeros((x.shape[0], dim, dim))
+    e = 1 + dim
+    for a in range(dim):
+        for b in range(a, dim):
+            S2[:, a, b] = mom[:, e]
+            S2[:, b, a] = mom[:, e]
+            e += 1
+    As = 0.5 * (A + np.transpose(A, (0, 2, 1)))
+    c = np.asarray(grid.lo, dtype=np.float64)[None, :] - x
+    Dh = 0.5 * h
+    Ac = np.einsum("nab,nb->na", As, c)
+    Q = m * np.einsum("na,na->n", c, Ac) + 2.0 * np.einsum("na,na->n", Ac * Dh[None, :], S1)
+    Q += np.einsum("nab,nab->n", As * Dh[None, :, None] * Dh[None, None, :], S2)
+    grad = v - m * P
+    g = float(np.sum(grad * w + P * Q))
+    return g, grad, float(np.max(np.abs(grad) / v))
 
 
 def dual_from_labels(grid, x, A, w, v, labels, nthreads: int = 0):

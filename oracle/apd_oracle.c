@@ -189,6 +189,50 @@ int oracle_moments(int32_t dim, const int32_t *res, int32_t n, const int32_t *la
     return bad ? OR_ERR_ARG : OR_OK;
 }
 
+/* The same integer moments over a listed subset of pixels: labels[t] is the
+ * label of pixel ids[t] (full-grid linear id), and u = 2k + 1 uses the full
+ * grid's indices k, so the moments of disjoint subsets add up to those of
+ * their union. */
+int oracle_moments_ids(int32_t dim, const int32_t *res, int32_t n, const int64_t *ids, int64_t count,
+                       const int32_t *labels, int64_t *out, int32_t nthreads) {
+    if (check_common(dim, res, n) || !ids || !labels || !out || count < 0) return OR_ERR_ARG;
+    const int K = 1 + dim + dim * (dim + 1) / 2;
+    int64_t J = 1;
+    for (int d = 0; d < dim; ++d) J *= res[d];
+    int nt = nthreads_or_default(nthreads);
+    int64_t *part = (int64_t *)calloc((size_t)nt * (size_t)n * K, sizeof(int64_t));
+    if (!part) return OR_ERR_MEM;
+    int bad = 0;
+#pragma omp parallel num_threads(nt) reduction(| : bad)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        int64_t *p = part + (size_t)t * n * K;
+#pragma omp for schedule(static)
+        for (int64_t e = 0; e < count; ++e) {
+            int32_t l = labels[e];
+            int64_t j = ids[e];
+            if (l < 0 || l >= n || j < 0 || j >= J) { bad = 1; continue; }
+            int64_t u[3];
+            int64_t r = j;
+            for (int d = 0; d < dim; ++d) { u[d] = 2 * (r % res[d]) + 1; r /= res[d]; }
+            int64_t *o = p + (size_t)l * K;
+            o[0] += 1;
+            for (int d = 0; d < dim; ++d) o[1 + d] += u[d];
+            int s = 1 + dim;
+            for (int a = 0; a < dim; ++a)
+                for (int b = a; b < dim; ++b) o[s++] += u[a] * u[b];
+        }
+    }
+    memset(out, 0, sizeof(int64_t) * (size_t)n * K);
+    for (int t = 0; t < nt; ++t)
+        for (int64_t e = 0; e < (int64_t)n * K; ++e) out[e] += part[(size_t)t * n * K + e];
+    free(part);
+    return bad ? OR_ERR_ARG : OR_OK;
+}
+
 /* Per-cell direct sums for a given labelling: count m_i, cost sum
  * Qsum_i = sum_{H_j=i} q_ij, and coordinate sums Ysum_i = sum_{H_j=i} y_j. */
 static int cell_sums(int32_t dim, const double *lo, const double *hi, const int32_t *res, int32_t n,
