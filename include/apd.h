@@ -106,6 +106,67 @@ void apd_workspace_destroy(apd_workspace *ws);
  * workspace (the tensor-core forms are always dense). */
 int apd_workspace_set_pruning(apd_workspace *ws, int32_t enable);
 
+/* Poll limit of the bounded shared-memory barrier waits of the FP32 scoring
+ * kernel on this workspace (each poll sleeps at most ~20 us; default 65536,
+ * about 1.3 s).  polls >= 0 sets the limit, polls < 0 restores the default.
+ * A wait that runs out latches APD_ERR_TIMEOUT: the kernel then waits, with
+ * the default limit, for the copies it has in flight, writes no labels or
+ * moments and returns; apd_workspace_status reports the status.  A limit of 0
+ * gives up at the first wait: that is how the timeout path is tested without
+ * a hung kernel.  Errors: APD_ERR_ARG (null ws, polls >= 2^32). */
+int apd_workspace_set_wait_limit(apd_workspace *ws, int64_t polls);
+
+/* ---- Slabs and sharded evaluation ------------------------------------------
+ * The per-cell sums of eq. (2.7) are the only data that couple pixels: the
+ * moments of disjoint sets of pixels add up to those of their union.  So one
+ * APD can be split across ranks (processes, one GPU each) by contiguous slabs
+ * of the grid's last (slowest) axis; every rank holds all n seeds, scores its
+ * slab, and one sum-reduction of the n x APD_MOMENT_WIDTH(dim) int64 words per
+ * evaluation gives every rank the full moments.  The dual, the gradient and
+ * L-BFGS then run identically on every rank, and because the moments are
+ * integers the result is bit-for-bit independent of the split and of the
+ * order of the reduction. */
+
+/* The slab of rank `rank` out of `world` along an axis of `res` pixels:
+ * k_begin = floor(res rank / world), k_count = floor(res (rank + 1) / world) -
+ * k_begin (empty slabs when world > res).  Host only, no device use.
+ * Errors: APD_ERR_ARG (res < 1, world < 1, rank outside [0, world), null out). */
+int apd_shard_range(int32_t res, int32_t rank, int32_t world, int32_t *k_begin, int32_t *k_count);
+
+/* Algorithm 1 + moments over the slab of pixels whose last-axis index lies in
+ * [k_begin, k_begin + k_count) of `grid` (2D: k_1, 3D: k_2).  moments: int64
+ * device [n][APD_MOMENT_WIDTH(dim)], overwritten, in the full grid's
+ * coordinates (u = 2k + 1 of the full-grid indices), so summing the slabs of
+ * a partition of the axis gives apd_cell_moments of the whole grid exactly.
+ * The workspace must hold the slab's pixels (max_j >= its pixel count).
+ * Stream-ordered.  Errors as apd_cell_moments, plus APD_ERR_ARG for k_begin
+ * < 0, k_count < 1 or k_begin + k_count > res of the last axis. */
+int apd_cell_moments_slab(const apd_grid *grid, int32_t k_begin, int32_t k_count, const apd_seeds *seeds,
+                          apd_precision precision, int64_t *moments, apd_workspace *ws, apd_stream_t stream);
+
+/* Reduction hook of a sharded workspace.  Called on the host, once per
+ * evaluation, after the moments of this rank's slab have been enqueued on
+ * `stream` into `moments` (device, `words` int64 values) at the weights `w`
+ * (device [n]); it must leave in `moments`, ordered before any later work on
+ * `stream`, the elementwise sum of every rank's moments (an allreduce SUM of
+ * int64, e.g. NCCL's).  Return 0 on success; anything else aborts the call
+ * with APD_ERR_CUDA. */
+typedef int (*apd_reduce_fn)(void *ctx, int64_t *moments, int64_t words, const double *w, int32_t n,
+                             apd_stream_t stream);
+
+/* Make every later scoring pass on this workspace cover only rank `rank`'s
+ * slab (apd_shard_range of the grid's last axis, for each grid the call uses:
+ * a coarse-to-fine solve shards both grids), followed by fn(ctx, ...) on the
+ * moments.  All entry points that evaluate the dual or the moments (moments,
+ * dual, weight solves, Lloyd steps, coarse-to-fine and warm-started solves)
+ * then return the full-grid results on every rank, provided every rank makes
+ * the same calls with the same arguments; apd_assign writes the labels of the
+ * slab's pixels only; the masked calls return APD_ERR_UNSUPPORTED, and the
+ * non-uniform (points) calls and batches are not sharded.  world == 1 (fn ignored) restores whole-grid passes.
+ * Errors: APD_ERR_ARG (null ws, world < 1, rank outside [0, world), world > 1
+ * with null fn). */
+int apd_workspace_set_shard(apd_workspace *ws, int32_t rank, int32_t world, apd_reduce_fn fn, void *ctx);
+
 /* Synchronise `stream`, return and clear the device-side status latched by the
  * stream-ordered calls (APD_OK, APD_ERR_ARG, APD_ERR_NOT_SPD, APD_ERR_TIMEOUT),
  * or APD_ERR_CUDA if the synchronisation itself failed. */
@@ -123,10 +184,21 @@ int apd_last_stats(apd_workspace *ws, apd_eval_stats *out, apd_stream_t stream);
 
 /* Algorithm 1 (pixel method): labels[j] = H_j = argmin_i C_ij with
  * C_ij = |y_j - x_i|^2_{A_i} - w_i; the lowest index wins exact ties.
- * labels: int32 device [J].  Stream-ordered.
+ * labels: int32 device [J].
+ * tie_gap: double device [J] or NULL.  When given, tie_gap[j] receives the
+ *   relative gap between the two smallest costs at pixel j,
+ *     (C_(2) - C_(1)) / (|q_(1)| + |q_(2)| + |w_(1)| + |w_(2)|),
+ *   C_(1) <= C_(2) ordered by cost then seed index (an exact tie gives 0),
+ *   q = |y_j - x|^2_A the quadratic part of each, +inf when n == 1.  Both
+ *   costs are computed with the FP64 reference arithmetic (d = y - x; q summed
+ *   a outer, b inner, each product (d_a A_ab) d_b rounded; C = q - w), so the
+ *   gap is that of a full FP64 evaluation of Algorithm 1.  A label decided by
+ *   rounding alone has gap ~1e-16; this is the band in which parity with
+ *   another FP64 evaluation can differ.  Costs one more pass over the pixels.
+ * Stream-ordered.
  * Errors: APD_ERR_ARG, APD_ERR_WORKSPACE, APD_ERR_UNSUPPORTED, APD_ERR_CUDA. */
 int apd_assign(const apd_grid *grid, const apd_seeds *seeds, apd_precision precision,
-               int32_t *labels, apd_workspace *ws, apd_stream_t stream);
+               int32_t *labels, double *tie_gap, apd_workspace *ws, apd_stream_t stream);
 
 /* Algorithm 1 fused with the per-cell reduction: moments int64 device
  * [n][APD_MOMENT_WIDTH(dim)] (layout above), exact integers, overwritten.
@@ -236,9 +308,9 @@ int apd_cell_moments_noalloc(const apd_grid *grid, const apd_seeds *seeds, int64
  * integer-valued operands (exact in TF32 and BF16) from shared memory into
  * tensor memory, compared element by element with CUDA-core dot products.
  * kind: 0 = TF32, 1 = BF16; variant: 0 = the operand layout the library uses,
- * 1 = leading and stride offsets exchanged (expected to fail), 2 = as 0 but
- * read back with the min-reducing tensor-memory load (sm_103), whose minimum
- * over each 32-column slice is compared as well.  Writes the
+ * read back with tcgen05.ld; 2 = the same, read back with the min-reducing
+ * tensor-memory load (sm_103), whose minimum over each 32-column slice is
+ * compared as well (variant 1 is not accepted: APD_ERR_ARG).  Writes the
  * number of mismatching accumulator elements and the largest absolute error
  * (host pointers).  Host-synchronous; runs on the current device. */
 int apd_tensor_core_check(int32_t kind, int32_t variant, int32_t *mismatches, float *max_err);

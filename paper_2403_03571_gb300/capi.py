@@ -44,7 +44,8 @@ EXPORTED = (
     "apd_warmstart_train_step_pairs", "apd_workspace_set_pruning", "apd_batch_set_pruning",
     "apd_profile_read_scored", "apd_lloyd_multires", "apd_refine_opts_default", "apd_solve_weights_refine",
     "apd_points_moments", "apd_points_dual_value_grad", "apd_refine_next_grid",
-    "apd_masked_moments", "apd_masked_dual_value_grad",
+    "apd_masked_moments", "apd_masked_dual_value_grad", "apd_workspace_set_wait_limit",
+    "apd_shard_range", "apd_cell_moments_slab", "apd_workspace_set_shard",
 )
 
 
@@ -94,6 +95,11 @@ class ApdPoints(ctypes.Structure):
                 ("mass", ctypes.c_void_p)]
 
 
+# int (*)(void *ctx, int64_t *moments, int64_t words, const double *w, int32_t n, cudaStream_t)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_int32, ctypes.c_void_p)
+
+
 class ApdError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -119,7 +125,13 @@ def load(path: Optional[str] = None):
     L.apd_workspace_destroy.restype = None
     L.apd_workspace_status.argtypes = [_vp, _vp]
     L.apd_last_stats.argtypes = [_vp, _P(ApdEvalStats), _vp]
-    L.apd_assign.argtypes = [_P(ApdGrid), _P(ApdSeeds), ctypes.c_int32, _vp, _vp, _vp]
+    L.apd_assign.argtypes = [_P(ApdGrid), _P(ApdSeeds), ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.apd_workspace_set_wait_limit.argtypes = [_vp, ctypes.c_int64]
+    L.apd_shard_range.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32),
+                                  _P(ctypes.c_int32)]
+    L.apd_cell_moments_slab.argtypes = [_P(ApdGrid), ctypes.c_int32, ctypes.c_int32, _P(ApdSeeds), ctypes.c_int32,
+                                        _vp, _vp, _vp]
+    L.apd_workspace_set_shard.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, REDUCE_FN, _vp]
     L.apd_cell_moments.argtypes = [_P(ApdGrid), _P(ApdSeeds), ctypes.c_int32, _vp, _vp, _vp]
     L.apd_dual_value_grad.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, ctypes.c_int32, _vp, _vp, _vp,
                                       _vp, _vp]
@@ -271,6 +283,18 @@ class Workspace:
     def set_pruning(self, enable: bool = True):
         _check(load().apd_workspace_set_pruning(self.handle, int(bool(enable))), "apd_workspace_set_pruning")
 
+    def set_shard(self, rank: int, world: int, hook=None):
+        """Score only rank's slab of every grid and sum the moments with ``hook`` (a
+        REDUCE_FN, kept alive here); world == 1 restores whole-grid passes."""
+        self._hook = hook
+        _check(load().apd_workspace_set_shard(self.handle, int(rank), int(world),
+                                              hook if hook is not None else REDUCE_FN(), None),
+               "apd_workspace_set_shard")
+
+    def set_wait_limit(self, polls: int = -1):
+        """Poll limit of the FP32 scoring kernel's bounded waits (-1: the default)."""
+        _check(load().apd_workspace_set_wait_limit(self.handle, int(polls)), "apd_workspace_set_wait_limit")
+
     def profile(self, enable: bool = True):
         _check(load().apd_profile_enable(self.handle, int(bool(enable))), "apd_profile_enable")
 
@@ -294,16 +318,34 @@ class Workspace:
         return st
 
 
-def apd_assign(grid, x, A, w, labels, ws: Workspace, precision=APD_FP32, stream=None):
+def apd_assign(grid, x, A, w, labels, ws: Workspace, precision=APD_FP32, stream=None, tie_gap=None):
+    """Labels (int32 [J]) and, when ``tie_gap`` (float64 [J]) is given, the relative
+    gap of the two smallest FP64 costs of every pixel."""
     g, s = make_grid(grid), make_seeds(x, A, w)
     return _check(load().apd_assign(ctypes.byref(g), ctypes.byref(s), precision, _ptr(labels),
-                                    ws.handle, _stream(stream)), "apd_assign")
+                                    _ptr(tie_gap), ws.handle, _stream(stream)), "apd_assign")
 
 
 def apd_cell_moments(grid, x, A, w, moments, ws: Workspace, precision=APD_FP32, stream=None):
     g, s = make_grid(grid), make_seeds(x, A, w)
     return _check(load().apd_cell_moments(ctypes.byref(g), ctypes.byref(s), precision, _ptr(moments),
                                           ws.handle, _stream(stream)), "apd_cell_moments")
+
+
+def apd_shard_range(res: int, rank: int, world: int):
+    """(k_begin, k_count) of rank's contiguous slab of an axis of ``res`` pixels."""
+    kb, kc = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().apd_shard_range(int(res), int(rank), int(world), ctypes.byref(kb), ctypes.byref(kc)),
+           "apd_shard_range")
+    return kb.value, kc.value
+
+
+def apd_cell_moments_slab(grid, k_begin, k_count, x, A, w, moments, ws: Workspace, precision=APD_FP32,
+                          stream=None):
+    g, s = make_grid(grid), make_seeds(x, A, w)
+    return _check(load().apd_cell_moments_slab(ctypes.byref(g), int(k_begin), int(k_count), ctypes.byref(s),
+                                               precision, _ptr(moments), ws.handle, _stream(stream)),
+                  "apd_cell_moments_slab")
 
 
 def apd_dual_value_grad(grid, x, A, w, v, g_out, grad, err_out, ws: Workspace, precision=APD_FP32,

@@ -57,14 +57,18 @@ struct Cfg<2> {  // 64 x 64 pixels, four 16-pixel row segments per row
     static constexpr int TX = 4, P = 16, TY = 64, TZ = 1;
 };
 
+// The grid's last-axis tiles start at tile index `toff` (the first tile of the
+// scoring window).
 template <int D>
-__global__ void __launch_bounds__(256, 2) assign_fp32_kernel(const __grid_constant__ TileSrc src) {
+__global__ void __launch_bounds__(256, 2) assign_fp32_kernel(const __grid_constant__ TileSrc src, const int toff) {
     using C = Cfg<D>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SharedLayout<D> &sm = *reinterpret_cast<SharedLayout<D> *>(smem_raw);
     init_shared<D>(sm);
-    uint32_t uses[2] = {0u, 0u};
-    score_tile<D, C::TX, C::P, C::TY, C::TZ>(sm, src, blockIdx.x, blockIdx.y, blockIdx.z, uses);
+    uint32_t uses[4] = {0u, 0u, 0u, 0u};
+    const int by = D == 2 ? (int)blockIdx.y + toff : (int)blockIdx.y;
+    const int bz = D == 3 ? (int)blockIdx.z + toff : 0;
+    score_tile<D, C::TX, C::P, C::TY, C::TZ>(sm, src, blockIdx.x, by, bz, uses);
 }
 
 // One warp per queued pixel of one instance.
@@ -88,6 +92,24 @@ __global__ void __launch_bounds__(256)
         rescore_pixel<D>(g, n, x, A, w, r32, flags[it], flag_gi ? flag_gi[it] : -1, wrh, wrl, pr, sc, gmom, labels);
 }
 
+// One warp per pixel: the relative gap of its two smallest FP64 costs.
+template <int D>
+__global__ void __launch_bounds__(256)
+    tie_gap_kernel(const GridDev g, const int n, const double *__restrict__ x, const double *__restrict__ A,
+                   const double *__restrict__ w, const RescorePrune pr, const DevScalars *__restrict__ sc,
+                   double *__restrict__ gap) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const double wref = dkey_inv(sc->wref_key);
+    const float wrh = (float)wref;
+    const float wrl = (float)(wref - (double)wrh);
+    const long long j0 = win_first(g), count = win_pixels(g);
+    for (long long t = warp; t < count; t += nwarps) {
+        const double v = gap_pixel<D>(g, n, x, A, w, j0 + t, wrh, wrl, pr);
+        if ((threadIdx.x & 31) == 0) gap[j0 + t] = v;
+    }
+}
+
 template <int D>
 cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
                                  unsigned long long *gmom, cudaStream_t st) {
@@ -100,15 +122,19 @@ cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((g.res[0] + C::TX * C::P - 1) / (C::TX * C::P), (g.res[1] + C::TY - 1) / C::TY,
-              D == 3 ? (g.res[2] + C::TZ - 1) / C::TZ : 1);
+    // tiles along the last axis that meet the window [win_lo, win_hi)
+    constexpr int TL = D == 3 ? C::TZ : C::TY;
+    const int toff = win_lo(g) / TL;
+    const int tcount = (win_hi(g) - 1) / TL - toff + 1;
+    dim3 grid((g.res[0] + C::TX * C::P - 1) / (C::TX * C::P), D == 2 ? tcount : (g.res[1] + C::TY - 1) / C::TY,
+              D == 3 ? tcount : 1);
     const int n_chunks = (n + kChunk - 1) / kChunk;
     double hx = 0.5 * C::TX * C::P * g.h[0], hy = 0.5 * C::TY * g.h[1], hz = D == 3 ? 0.5 * C::TZ * g.h[2] : 0.0;
     const float R = (float)(sqrt(hx * hx + hy * hy + hz * hz) * (1.0 + 1e-6));
     const TileSrc src{g,        n,     n_chunks,   R,      ws.recs, ws.sorted ? ws.scodes : nullptr,
                       ws.sorted ? ws.perm : nullptr, gmom, ws.flags, ws.flag_gi, labels, ws.sc,
-                      ws.prune ? ws.groups : nullptr, ws.pairs_scored};
-    assign_fp32_kernel<D><<<grid, C::TX * C::TY * C::TZ, smem, st>>>(src);
+                      ws.prune ? ws.groups : nullptr, ws.pairs_scored, ws.wait_limit};
+    assign_fp32_kernel<D><<<grid, C::TX * C::TY * C::TZ, smem, st>>>(src, toff);
     return cudaGetLastError();
 }
 
@@ -118,6 +144,19 @@ cudaError_t launch_assign_fp32(const GridDev &g, int n, Workspace &ws, int32_t *
                                unsigned long long *moments, cudaStream_t st) {
     return g.dim == 3 ? launch_assign_fp32_t<3>(g, n, ws, labels, moments, st)
                       : launch_assign_fp32_t<2>(g, n, ws, labels, moments, st);
+}
+
+cudaError_t launch_tie_gap(const GridDev &g, int n, const double *x, const double *A, const double *w,
+                           Workspace &ws, double *gap, cudaStream_t st) {
+    RescorePrune pr{ws.groups, ws.sorted ? ws.recs32s : ws.recs32, ws.sorted ? ws.perm : nullptr, (n + 31) / 32};
+    int sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ws.device) != cudaSuccess) sms = 152;
+    const int blocks = sms * 8;
+    if (g.dim == 3)
+        tie_gap_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, pr, ws.sc, gap);
+    else
+        tie_gap_kernel<2><<<blocks, 256, 0, st>>>(g, n, x, A, w, pr, ws.sc, gap);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,

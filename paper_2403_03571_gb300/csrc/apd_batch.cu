@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, MINB) batch_assign_kernel(const __
     __shared__ int txyz[3];
     __shared__ unsigned item_sh;
     fp32::init_shared<D>(sm);
-    uint32_t uses[2] = {0u, 0u};
+    uint32_t uses[4] = {0u, 0u, 0u, 0u};
     const unsigned total = a.sched->total_items;
     const int n_act = a.sched->n_active;
     for (;;) {
@@ -311,6 +311,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, MINB) batch_assign_kernel(const __
             cur.sc = a.scs + b;
             cur.groups = a.prune ? a.groups + I.rec_off / 32 : nullptr;
             cur.pairs_scored = nullptr;
+            cur.wait_limit = kDefaultWaitPolls;
         }
         __syncthreads();
         if (!fp32::score_tile<D, TX, P, TY, TZ>(sm, cur, txyz[0], txyz[1], txyz[2], uses)) break;

@@ -58,6 +58,12 @@ int validate_grid(const apd_grid *gr, GridDev &g) {
     return APD_OK;
 }
 
+void shard_range(int res, int rank, int world, int &k_begin, int &k_count) {
+    const long long b = (long long)res * rank / world, e = (long long)res * (rank + 1) / world;
+    k_begin = (int)b;
+    k_count = (int)(e - b);
+}
+
 double domain_measure(const apd_grid *gr) {
     double m = 1.0;
     for (int d = 0; d < gr->dim; ++d) m *= gr->hi[d] - gr->lo[d];
@@ -75,9 +81,17 @@ int validate_seeds(const apd_seeds *s) {
     return APD_OK;
 }
 
+// The workspace holds n seeds and the pixels of one scoring pass: the whole
+// grid, or this rank's slab when the workspace is sharded.
 int check_ws(const apd_workspace *ws, const GridDev &g, int n) {
     if (!ws) return APD_ERR_ARG;
-    if (ws->w.dim != g.dim || n > ws->w.max_n || g.J > ws->w.max_j) return APD_ERR_WORKSPACE;
+    long long pix = g.J;
+    if (ws->w.shard_world > 1) {
+        int kb = 0, kc = 0;
+        shard_range(g.res[g.dim - 1], ws->w.shard_rank, ws->w.shard_world, kb, kc);
+        pix = g.J / g.res[g.dim - 1] * (long long)kc;
+    }
+    if (ws->w.dim != g.dim || n > ws->w.max_n || pix > ws->w.max_j) return APD_ERR_WORKSPACE;
     return APD_OK;
 }
 
@@ -101,10 +115,19 @@ struct TrialStep {
 // weights_only the records of the previous pass (same x, A, n) are reused and
 // only the weights change; with a step, w (device, n) is first set to
 // step->W + step->t step->p.
-int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, const double *w,
+int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A, const double *w,
                    apd_precision prec, Workspace &ws, int32_t *labels, unsigned long long *mom,
                    cudaStream_t st, bool weights_only = false, const TrialStep *step = nullptr) {
     if (prec != APD_FP32 && prec != APD_TC_TF32 && prec != APD_TC_BF16) return APD_ERR_UNSUPPORTED;
+    GridDev g = g_in;
+    const bool sharded = ws.shard_world > 1 && !g.kz1;
+    if (sharded) {
+        int kb = 0, kc = 0;
+        shard_range(g.res[g.dim - 1], ws.shard_rank, ws.shard_world, kb, kc);
+        g.kz0 = kb;
+        g.kz1 = kb + kc;
+    }
+    const bool empty = g.kz1 && g.kz1 <= g.kz0;  // an empty slab: moments stay zero
     const size_t K = (size_t)moment_width(g.dim);
     if (weights_only) {
         // one launch: moments and counters cleared, trial weights into the records
@@ -127,22 +150,30 @@ int enqueue_assign(const GridDev &g, int n, const double *x, const double *A, co
         e0 = ws.ev[ws.ev_used];
         e1 = ws.ev[ws.ev_used + 1];
         ws.ev_used += 2;
-        ws.prof_pairs += g.J * (long long)n;
+        ws.prof_pairs += win_pixels(g) * (long long)n;
         APD_TRY(cuda_ok(cudaEventRecord(e0, st)));
     }
     // the tensor-core tiling needs per-tile scratch; grids too thin for the
-    // workspace's tile capacity are scored by the FP32 kernel (same labels)
-    if (prec == APD_FP32 || tc_tile_count(g) > ws.tc_tile_cap)
+    // workspace's tile capacity, and windowed passes, are scored by the FP32
+    // kernel (same labels)
+    if (empty) {
+    } else if (prec == APD_FP32 || tc_tile_count(g) > ws.tc_tile_cap || g.kz1)
         APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
     else
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
     if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
-    APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
+    if (!empty) APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
+    if (sharded) {
+        // every rank's slab moments, summed, before anything reads them
+        if (ws.shard_fn(ws.shard_ctx, reinterpret_cast<int64_t *>(mom), (int64_t)n * moment_width(g.dim), w, n,
+                        (apd_stream_t)st) != 0)
+            return APD_ERR_CUDA;
+    }
     ws.kernel_launches += weights_only ? 3 + (prec == APD_FP32 ? 0 : 2)
                                        : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 2) +
                                              (step ? 1 : 0);
-    ws.last_pixels = g.J;
-    ws.last_pairs = g.J * (long long)n;
+    ws.last_pixels = win_pixels(g);
+    ws.last_pairs = win_pixels(g) * (long long)n;
     return APD_OK;
 }
 
@@ -670,14 +701,25 @@ int apd_last_stats(apd_workspace *ws, apd_eval_stats *out, apd_stream_t stream) 
 }
 
 int apd_assign(const apd_grid *grid, const apd_seeds *seeds, apd_precision precision, int32_t *labels,
-               apd_workspace *ws, apd_stream_t stream) {
+               double *tie_gap, apd_workspace *ws, apd_stream_t stream) {
     GridDev g;
     APD_TRY(validate_grid(grid, g));
     APD_TRY(validate_seeds(seeds));
     if (!labels) return APD_ERR_ARG;
     APD_TRY(check_ws(ws, g, seeds->n));
-    return enqueue_assign(g, seeds->n, seeds->x, seeds->A, seeds->w, precision, ws->w, labels,
-                          ws->w.moments, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    APD_TRY(enqueue_assign(g, seeds->n, seeds->x, seeds->A, seeds->w, precision, ws->w, labels, ws->w.moments, st));
+    if (tie_gap) {
+        APD_TRY(cuda_ok(launch_tie_gap(g, seeds->n, seeds->x, seeds->A, seeds->w, ws->w, tie_gap, st)));
+        ws->w.kernel_launches += 1;
+    }
+    return APD_OK;
+}
+
+int apd_workspace_set_wait_limit(apd_workspace *ws, int64_t polls) {
+    if (!ws || polls > (int64_t)0xffffffffll) return APD_ERR_ARG;
+    ws->w.wait_limit = polls < 0 ? kDefaultWaitPolls : (uint32_t)polls;
+    return APD_OK;
 }
 
 int apd_cell_moments(const apd_grid *grid, const apd_seeds *seeds, apd_precision precision,
@@ -687,6 +729,38 @@ int apd_cell_moments(const apd_grid *grid, const apd_seeds *seeds, apd_precision
     APD_TRY(validate_seeds(seeds));
     if (!moments) return APD_ERR_ARG;
     APD_TRY(check_ws(ws, g, seeds->n));
+    return enqueue_assign(g, seeds->n, seeds->x, seeds->A, seeds->w, precision, ws->w, nullptr,
+                          reinterpret_cast<unsigned long long *>(moments), (cudaStream_t)stream);
+}
+
+int apd_shard_range(int32_t res, int32_t rank, int32_t world, int32_t *k_begin, int32_t *k_count) {
+    if (res < 1 || world < 1 || rank < 0 || rank >= world || !k_begin || !k_count) return APD_ERR_ARG;
+    int kb = 0, kc = 0;
+    shard_range(res, rank, world, kb, kc);
+    *k_begin = kb;
+    *k_count = kc;
+    return APD_OK;
+}
+
+int apd_workspace_set_shard(apd_workspace *ws, int32_t rank, int32_t world, apd_reduce_fn fn, void *ctx) {
+    if (!ws || world < 1 || rank < 0 || rank >= world || (world > 1 && !fn)) return APD_ERR_ARG;
+    ws->w.shard_rank = world > 1 ? rank : 0;
+    ws->w.shard_world = world;
+    ws->w.shard_fn = world > 1 ? fn : nullptr;
+    ws->w.shard_ctx = world > 1 ? ctx : nullptr;
+    return APD_OK;
+}
+
+int apd_cell_moments_slab(const apd_grid *grid, int32_t k_begin, int32_t k_count, const apd_seeds *seeds,
+                          apd_precision precision, int64_t *moments, apd_workspace *ws, apd_stream_t stream) {
+    GridDev g;
+    APD_TRY(validate_grid(grid, g));
+    APD_TRY(validate_seeds(seeds));
+    if (!moments || k_begin < 0 || k_count < 1 || (long long)k_begin + k_count > g.res[g.dim - 1]) return APD_ERR_ARG;
+    if (!ws) return APD_ERR_ARG;
+    g.kz0 = k_begin;
+    g.kz1 = k_begin + k_count;
+    if (ws->w.dim != g.dim || seeds->n > ws->w.max_n || win_pixels(g) > ws->w.max_j) return APD_ERR_WORKSPACE;
     return enqueue_assign(g, seeds->n, seeds->x, seeds->A, seeds->w, precision, ws->w, nullptr,
                           reinterpret_cast<unsigned long long *>(moments), (cudaStream_t)stream);
 }
@@ -750,6 +824,7 @@ static int masked_entry(const apd_grid *coarse, int32_t refine, const apd_seeds 
         fine.res[d] = (int32_t)fr;
     }
     APD_TRY(validate_grid(&fine, gf));
+    if (ws && ws->w.shard_world > 1) return APD_ERR_UNSUPPORTED;  // the mask needs every coarse label
     return check_ws(ws, gc, seeds->n);
 }
 

@@ -10,6 +10,20 @@ namespace apd {
 // |y - x|^2_A - w in FP64 with the reference operation order of the cost
 // matrix: d = y - x; q = sum_a sum_b (d_a * A_ab) * d_b (a outer, b inner,
 // from 0, each operation rounded separately, no FMA); C = q - w.
+// The quadratic part q = |y - x|^2_A alone, with the operation order of cost64.
+template <int D>
+__device__ __forceinline__ double quad64(const double *y, const double *__restrict__ xi, const double *__restrict__ Ai) {
+    double d[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) d[a] = __dsub_rn(y[a], xi[a]);
+    double q = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) q = __dadd_rn(q, __dmul_rn(__dmul_rn(d[a], Ai[a * D + b]), d[b]));
+    return q;
+}
+
 template <int D>
 __device__ __forceinline__ double cost64(const double *y, const double *__restrict__ xi,
                                          const double *__restrict__ Ai, double wi) {
@@ -22,6 +36,37 @@ __device__ __forceinline__ double cost64(const double *y, const double *__restri
 #pragma unroll
         for (int b = 0; b < D; ++b) q = __dadd_rn(q, __dmul_rn(__dmul_rn(d[a], Ai[a * D + b]), d[b]));
     return __dsub_rn(q, wi);
+}
+
+// Grid indices k of pixel j, its FP64 centre y = lo + (k + 1/2) h (the
+// reference arithmetic) and the FP32 high/low split of y; lane a computes axis
+// a, every lane of the warp receives all of them.
+template <int D>
+__device__ __forceinline__ void pixel_centre_warp(const GridDev &g, const long long j, int (&k)[3], double (&y)[D],
+                                                  float (&yh)[3], float (&yl)[3]) {
+    const int lane = threadIdx.x & 31;
+    long long rr = j;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        k[a] = (int)(rr % g.res[a]);
+        rr /= g.res[a];
+    }
+    double ya = 0.0;
+    float yha = 0.f, yla = 0.f;
+    if (lane < D) {
+        const int ka = lane == 0 ? k[0] : (lane == 1 ? k[1] : k[2]);
+        const double loa = lane == 0 ? g.lo[0] : (lane == 1 ? g.lo[1] : g.lo[D - 1]);
+        const double ha = lane == 0 ? g.h[0] : (lane == 1 ? g.h[1] : g.h[D - 1]);
+        ya = __dadd_rn(loa, __dmul_rn((double)ka + 0.5, ha));
+        yha = (float)ya;
+        yla = (float)(ya - (double)yha);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        y[a] = __shfl_sync(0xffffffffu, ya, a);
+        yh[a] = __shfl_sync(0xffffffffu, yha, a);
+        yl[a] = __shfl_sync(0xffffffffu, yla, a);
+    }
 }
 
 template <int D>
@@ -181,33 +226,9 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
     const int lane = threadIdx.x & 31;
     const long long j = (long long)fj;
     int k[3] = {0, 0, 0};
-    long long rr = j;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        k[a] = (int)(rr % g.res[a]);
-        rr /= g.res[a];
-    }
-    // the pixel centre (FP64) and its FP32 split: lane a computes axis a
     double y[D];
     float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
-    {
-        double ya = 0.0;
-        float yha = 0.f, yla = 0.f;
-        if (lane < D) {
-            const int ka = lane == 0 ? k[0] : (lane == 1 ? k[1] : k[2]);
-            const double loa = lane == 0 ? g.lo[0] : (lane == 1 ? g.lo[1] : g.lo[D - 1]);
-            const double ha = lane == 0 ? g.h[0] : (lane == 1 ? g.h[1] : g.h[D - 1]);
-            ya = __dadd_rn(loa, __dmul_rn((double)ka + 0.5, ha));
-            yha = (float)ya;
-            yla = (float)(ya - (double)yha);
-        }
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            y[a] = __shfl_sync(0xffffffffu, ya, a);
-            yh[a] = __shfl_sync(0xffffffffu, yha, a);
-            yl[a] = __shfl_sync(0xffffffffu, yla, a);
-        }
-    }
+    pixel_centre_warp<D>(g, j, k, y, yh, yl);
     double best = __longlong_as_double(0x7ff0000000000000ll);
     int bi = 0x7fffffff;
     float thr = __int_as_float(0x7f800000);
@@ -275,6 +296,126 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
         }
     }
     rescore_finish<D>(g, n, j, k, best, bi, sc, gmom, labels);
+}
+
+// Relative gap of the two smallest costs at pixel j (one warp), the quantity
+// the near-tie tolerance of the labels is stated in:
+//     gap_j = (c_(2) - c_(1)) / (|q_(1)| + |q_(2)| + |w_(1)| + |w_(2)|),
+// c_(1) <= c_(2) the two smallest costs of Algorithm 1's cost matrix at y_j
+// (ordered by cost, then seed index, so an exact tie gives 0), q the quadratic
+// part of each, +inf for a single seed.  Both costs come from the FP64
+// reference arithmetic (cost64), so the value is that of a full FP64 scan.
+// Search: the 32-seed groups are visited in increasing order of their cost
+// lower bound (lanes over groups, in blocks of 32 groups); in a visited group
+// every lane takes one seed's FP32 direct-form cost c with its bound E, the
+// two smallest upper bounds c + E seen so far give t2 >= the exact second
+// smallest cost, seeds with c - E <= t2 are recomputed in FP64, and the
+// remaining groups of a block are skipped once the smallest bound among them
+// exceeds t2 (the margins are those of rescore_pixel).
+__device__ __forceinline__ unsigned f_key(float v) {
+    const unsigned u = __float_as_uint(v);
+    return u ^ ((u >> 31) ? 0xffffffffu : 0x80000000u);
+}
+__device__ __forceinline__ float f_unkey(unsigned k) {
+    return __uint_as_float(k ^ ((k >> 31) ? 0x80000000u : 0xffffffffu));
+}
+
+template <int D>
+__device__ __forceinline__ double gap_pixel(const GridDev &g, const int n, const double *__restrict__ x,
+                                            const double *__restrict__ A, const double *__restrict__ w,
+                                            const long long j, const float wrh, const float wrl,
+                                            const RescorePrune &pr) {
+    const int lane = threadIdx.x & 31;
+    int k[3] = {0, 0, 0};
+    double y[D];
+    float yh[3] = {0.f, 0.f, 0.f}, yl[3] = {0.f, 0.f, 0.f};
+    pixel_centre_warp<D>(g, j, k, y, yh, yl);
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    if (n < 2) return inf;
+    const float finf = __int_as_float(0x7f800000);
+    float t1 = finf, t2 = finf;                          // warp-uniform
+    double c1 = inf, c2 = inf;                           // this lane's two smallest (cost, index)
+    int i1 = 0x7fffffff, i2 = 0x7fffffff;
+    for (int base = 0; base < pr.n_groups; base += 32) {
+        const int grp = base + lane;
+        float lb = finf, wpart = 0.f;
+        if (grp < pr.n_groups) {
+            const GroupBound gb = pr.groups[grp];
+            float d2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float slack = 1e-6f * (fabsf(yh[a]) + fabsf(gb.lo[a]) + fabsf(gb.hi[a]));
+                const float t = fmaxf(fmaxf(gb.lo[a] - yh[a], yh[a] - gb.hi[a]) - slack, 0.f);
+                d2 = fmaf(t, t, d2);
+            }
+            wpart = gb.wgap;
+            lb = __fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f) + wpart;
+        }
+        unsigned live = __ballot_sync(0xffffffffu, grp < pr.n_groups);
+        while (live) {
+            const unsigned key = ((live >> lane) & 1u) ? f_key(lb) : 0xffffffffu;
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+            const int kg = __ffs(__ballot_sync(0xffffffffu, ((live >> lane) & 1u) && key == kmin)) - 1;
+            const float lbk = __shfl_sync(0xffffffffu, lb, kg);
+            const float wpk = __shfl_sync(0xffffffffu, wpart, kg);
+            if (t2 < finf && lbk > t2 + 1e-6f * (fabsf(t2) + fabsf(lbk) + fabsf(wpk)) + 1e-30f) break;
+            live &= ~(1u << kg);
+            const int pos = (base + kg) * 32 + lane;
+            float c = finf, E = 0.f;
+            int s = -1;
+            if (pos < n) {
+                s = pr.perm ? pr.perm[pos] : pos;
+                cost32_bound<D>(pr.r32s[pos], yh, yl, wrh, wrl, c, E);
+            }
+            // the two smallest upper bounds of this group, merged into (t1, t2)
+            const unsigned ku = pos < n ? f_key(c + E) : 0xffffffffu;
+            const unsigned k1 = __reduce_min_sync(0xffffffffu, ku);
+            const unsigned k2 = __popc(__ballot_sync(0xffffffffu, ku == k1)) >= 2
+                                    ? k1
+                                    : __reduce_min_sync(0xffffffffu, ku == k1 ? 0xffffffffu : ku);
+            const float m1 = k1 == 0xffffffffu ? finf : f_unkey(k1);
+            const float m2 = k2 == 0xffffffffu ? finf : f_unkey(k2);
+            const float nt1 = fminf(t1, m1);
+            t2 = fminf(fmaxf(t1, m1), fminf(t2, m2));
+            t1 = nt1;
+            if (pos < n && c - E <= t2) {
+                const double c64 = cost64<D>(y, x + (size_t)s * D, A + (size_t)s * D * D, w[s]);
+                if (c64 < c1 || (c64 == c1 && s < i1)) {
+                    c2 = c1;
+                    i2 = i1;
+                    c1 = c64;
+                    i1 = s;
+                } else if (c64 < c2 || (c64 == c2 && s < i2)) {
+                    c2 = c64;
+                    i2 = s;
+                }
+            }
+        }
+    }
+    // merge the lanes' pairs: the two smallest (cost, index) of the warp
+    double b1 = c1, b2 = c2;
+    int j1 = i1, j2 = i2;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o1 = __shfl_xor_sync(0xffffffffu, b1, off), o2 = __shfl_xor_sync(0xffffffffu, b2, off);
+        const int p1 = __shfl_xor_sync(0xffffffffu, j1, off), p2 = __shfl_xor_sync(0xffffffffu, j2, off);
+        // two smallest of the sorted pairs (b1, b2) and (o1, o2)
+        const bool mine_first = b1 < o1 || (b1 == o1 && j1 < p1);
+        const double f1 = mine_first ? b1 : o1;
+        const int g1 = mine_first ? j1 : p1;
+        const double sa = mine_first ? b2 : b1, sb = mine_first ? o1 : o2;  // second candidates
+        const int ja = mine_first ? j2 : j1, jb = mine_first ? p1 : p2;
+        const bool a_second = sa < sb || (sa == sb && ja < jb);
+        b1 = f1;
+        j1 = g1;
+        b2 = a_second ? sa : sb;
+        j2 = a_second ? ja : jb;
+    }
+    if (j1 >= n || j2 >= n || !(b2 < inf)) return inf;
+    const double q1 = quad64<D>(y, x + (size_t)j1 * D, A + (size_t)j1 * D * D);
+    const double q2 = quad64<D>(y, x + (size_t)j2 * D, A + (size_t)j2 * D * D);
+    const double sc = fabs(q1) + fabs(q2) + fabs(w[j1]) + fabs(w[j2]);
+    return sc > 0.0 ? (b2 - b1) / sc : (b2 - b1 > 0.0 ? inf : 0.0);
 }
 
 }  // namespace apd

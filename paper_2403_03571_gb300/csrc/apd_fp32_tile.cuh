@@ -210,18 +210,21 @@ struct TileSrc {
     DevScalars *sc;
     const GroupBound *groups;     // bounds of the scan-order 32-seed groups: pruning (null: dense)
     unsigned long long *pairs_scored;  // pixel-seed pairs the scoring evaluated (or null)
+    uint32_t wait_limit;          // polls of each chunk wait (kDefaultWaitPolls normally)
 };
 
 // Scores the (TX P) x TY x TZ tile (bx, by, bz) of `s` with NT = TX TY TZ
 // threads; thread (seg, ty, tz) owns the row segment of P pixels starting at
 // first-axis offset seg P inside the tile.
-// `uses` counts the completed phases of the two chunk barriers across the
-// tiles a CTA has scored; the shared-memory table must be empty on entry and
-// is empty again on return.  Returns false if a chunk wait timed out (the CTA
-// must then stop: a copy may still be in flight).
+// `uses[b]` counts the phases of chunk barrier b this thread has waited for,
+// `uses[2 + b]` the copies issued into buffer b (thread 0), across the tiles a
+// CTA has scored; the shared-memory table must be empty on entry and is empty
+// again on return.  Returns false if a chunk wait timed out: thread 0 has then
+// waited (with the default limit) for every copy still in flight, and the CTA
+// must stop.
 template <int D, int TX, int P, int TY, int TZ>
 __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s, const int bx, const int by,
-                                           const int bz, uint32_t (&uses)[2]) {
+                                           const int bz, uint32_t (&uses)[4]) {
     constexpr int K = moment_width(D);
     constexpr int NT = TX * TY * TZ;
     constexpr int W0 = TX * P;  // tile width along the first axis
@@ -241,7 +244,8 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     const int k2b = (D == 3) ? bz * TZ : 0;
     const int k1 = k1b + ty;
     const int k2 = k2b + tz;
-    const bool row_valid = (k1 < g.res[1]) && (D == 2 || k2 < g.res[2]);
+    const int klast = D == 3 ? k2 : k1;  // the windowed axis
+    const bool row_valid = (k1 < g.res[1]) && (D == 2 || k2 < g.res[2]) && klast >= win_lo(g) && klast < win_hi(g);
 
     const int lane = tid & 31;
     const int wid = tid >> 5;
@@ -281,6 +285,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             mbar_expect_tx(&sm.bar[k], kChunk * sizeof(SeedRec));
             bulk_g2s(&sm.raw[k][0], s.recs + (size_t)chunk_from(start, k) * kChunk, kChunk * sizeof(SeedRec),
                      &sm.bar[k]);
+            ++uses[2 + k];
         }
     }
     const float f1 = ((float)(ty - TY / 2) + 0.5f) * g.h32[1];
@@ -331,8 +336,10 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
     for (int k = 0; k < n_chunks; ++k) {
         const int b = k & 1;
         const int c = chunk_at(k);
-        if (ok && !mbar_wait_bounded(&sm.bar[b], uses[b] & 1u, &s.sc->status)) ok = false;
-        ++uses[b];
+        if (ok) {
+            if (mbar_wait_bounded(&sm.bar[b], uses[b] & 1u, &s.sc->status, s.wait_limit)) ++uses[b];
+            else ok = false;
+        }
         // Group bounds of this chunk (lane = group): the cost lower bound over the
         // warp's pixel box, used to order the groups (nearest first) and to skip
         // those above every pixel's second-best cost.  The dense sweep takes the
@@ -416,6 +423,7 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             mbar_expect_tx(&sm.bar[b], kChunk * sizeof(SeedRec));
             bulk_g2s(&sm.raw[b][0], s.recs + (size_t)chunk_at(k + 2) * kChunk, kChunk * sizeof(SeedRec),
                      &sm.bar[b]);
+            ++uses[2 + b];
         }
         if (ok && need_chunk) {
             while (true) {
@@ -527,6 +535,12 @@ __device__ __forceinline__ bool score_tile(SharedLayout<D> &sm, const TileSrc &s
             }
         }
         __syncthreads();
+    }
+    if (!ok && tid == 0) {
+        // a wait gave up: let the copies still in flight land before the CTA stops
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            while (uses[b] < uses[2 + b] && mbar_wait_bounded(&sm.bar[b], uses[b] & 1u, &s.sc->status)) ++uses[b];
     }
     // scan position of the best: its group base and the index bits of its key
 #pragma unroll

@@ -58,6 +58,7 @@ constexpr int kChunk = 256;         // seeds per shared-memory chunk (= scoring 
 constexpr int kSortMax = 16384;     // largest padded seed count ordered on the device
 constexpr int kGroup = 32;          // seeds per packed-index group (5 low mantissa bits)
 constexpr int kWarmFeatMax = 32;    // warm-start features per seed (3D; 28 in 2D)
+constexpr uint32_t kDefaultWaitPolls = 1u << 16;  // polls of a bounded mbarrier wait (~1.3 s)
 
 // Small block of device scalars owned by the workspace.
 struct DevScalars {
@@ -100,6 +101,12 @@ struct Workspace {
     int4 *tc_cand = nullptr;            // [max_j] tensor-core candidates per pixel (3 seeds, 4th score)
     bool sorted = false;                // set by launch_seed_prep for the current pass
     bool prune = false;                 // FP32 scoring skips seed groups by their bounds
+    uint32_t wait_limit = kDefaultWaitPolls;  // polls of the scoring kernels' chunk waits
+    // sharded evaluation: every scoring pass covers this rank's slab of the last
+    // axis only, and shard_fn sums the moments over the ranks before they are used
+    int shard_rank = 0, shard_world = 1;
+    apd_reduce_fn shard_fn = nullptr;
+    void *shard_ctx = nullptr;
     unsigned long long *pairs_scored = nullptr;  // device counter: pairs the FP32 scoring evaluated
     unsigned long long *moments = nullptr;  // [max_n * K]
     uint32_t *flags = nullptr;          // [max_j]
@@ -129,7 +136,11 @@ struct Workspace {
     int64_t kernel_launches = 0;  // every kernel launched with this workspace
 };
 
-// Grid description passed by value to kernels.
+// Grid description passed by value to kernels.  A scoring pass covers the
+// pixels whose index along the last (slowest) axis lies in the window
+// [kz0, kz1); kz1 == 0 means the whole axis.  Pixel ids, centres and the odd
+// coordinates u of the moments are always those of the full grid, so the
+// moments of disjoint windows add up to the full grid's.
 struct GridDev {
     int dim;
     int res[3];
@@ -137,8 +148,18 @@ struct GridDev {
     double h[3];
     float h32[3];
     double cell;  // |P|
-    long long J;
+    long long J;  // pixels of the full grid
+    int kz0, kz1;
 };
+__host__ __device__ inline int win_lo(const GridDev &g) { return g.kz0; }
+__host__ __device__ inline int win_hi(const GridDev &g) { return g.kz1 ? g.kz1 : g.res[g.dim - 1]; }
+// pixels of the window and the full-grid id of its first pixel
+__host__ __device__ inline long long win_pixels(const GridDev &g) {
+    return g.J / g.res[g.dim - 1] * (long long)(win_hi(g) - win_lo(g));
+}
+__host__ __device__ inline long long win_first(const GridDev &g) {
+    return g.J / g.res[g.dim - 1] * (long long)win_lo(g);
+}
 
 // ----------------------------------------------------------------------------
 // ordered keys for atomic max/min of doubles
@@ -227,9 +248,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: returns false (and latches ST_TIMEOUT) after `limit` polls
-// (at most limit x 20 us, about 1.3 s with the default).
+// (at most limit x 20 us, about 1.3 s with the default).  A limit of 0 gives up
+// without polling (used to exercise the timeout path on purpose).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status,
-                                                  uint32_t limit = (1u << 16)) {
+                                                  uint32_t limit = kDefaultWaitPolls) {
     for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(status, ST_TIMEOUT);
@@ -240,6 +262,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // host helpers (apd_capi.cu)
 // ----------------------------------------------------------------------------
 int map_bits(int bits);                              // ST_* bits -> apd_status
+// contiguous slab [k_begin, k_begin + k_count) of `res` pixels for rank of world
+void shard_range(int res, int rank, int world, int &k_begin, int &k_count);
 int validate_grid(const apd_grid *gr, GridDev &g);  // apd_grid -> GridDev, APD_ERR_ARG if invalid
 double domain_measure(const apd_grid *gr);          // |Omega|
 int warmstart_dim(const apd_mlp *net);               // dimension of a warm-start network (apd_warmstart.cu)
@@ -289,6 +313,10 @@ cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st);
 cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,
                                 const double *w, Workspace &ws, int32_t *labels,
                                 unsigned long long *moments, cudaStream_t st);
+// relative gap of the two smallest FP64 costs of every pixel (after a scoring
+// pass on the same seeds: uses its records, group bounds and w_ref)
+cudaError_t launch_tie_gap(const GridDev &g, int n, const double *x, const double *A, const double *w,
+                           Workspace &ws, double *gap, cudaStream_t st);
 // dual value / gradient from the moments (outputs optional; scalars also into ws.sc)
 cudaError_t launch_dual(const GridDev &g, int n, const double *x, const double *A, const double *w,
                         const double *v, const double *p_dir, const unsigned long long *moments,

@@ -61,7 +61,6 @@ __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatc
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = tslot;
-    const uint32_t dl = variant == 1 ? SBO : LBO, ds = variant == 1 ? LBO : SBO;
     if (tid == 0) {
         const uint32_t idesc = tc::instr_desc(KIND, kM, kN);
         const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(smA);
@@ -69,8 +68,8 @@ __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatc
         constexpr int ksteps = KIND == tc::KIND_TF32 ? 2 : 1;  // K = 8 (TF32) or 16 (BF16) per MMA
         for (int ks = 0; ks < ksteps; ++ks) {
             const uint32_t off = (uint32_t)ks * 2u * LBO;       // two core matrices along K per step
-            const uint64_t ad = tc::smem_desc(a0 + off, dl, ds);
-            const uint64_t bd = tc::smem_desc(b0 + off, dl, ds);
+            const uint64_t ad = tc::smem_desc(a0 + off, LBO, SBO);
+            const uint64_t bd = tc::smem_desc(b0 + off, LBO, SBO);
             if (KIND == tc::KIND_TF32)
                 tc::mma_tf32(taddr, ad, bd, idesc, ks > 0 ? 1u : 0u);
             else
@@ -117,7 +116,7 @@ __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatc
 }  // namespace apd
 
 extern "C" int apd_tensor_core_check(int32_t kind, int32_t variant, int32_t *mismatches, float *max_err) {
-    if ((kind != 0 && kind != 1) || variant < 0 || variant > 2 || !mismatches || !max_err) return APD_ERR_ARG;
+    if ((kind != 0 && kind != 1) || (variant != 0 && variant != 2) || !mismatches || !max_err) return APD_ERR_ARG;
     int *d = nullptr;
     if (cudaMalloc((void **)&d, 3 * sizeof(int)) != cudaSuccess) return APD_ERR_CUDA;
     cudaMemset(d, 0, 3 * sizeof(int));

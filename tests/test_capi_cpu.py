@@ -54,15 +54,17 @@ def test_argument_errors_before_cuda(lib):
     g.dim = 4
     s = capi.ApdSeeds()
     s.n = 3
-    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, None, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, None, None, None, None) == capi.APD_ERR_ARG
     g.dim = 2
     g.res[0], g.res[1] = 8, 0
     g.hi[0], g.hi[1] = 1.0, 1.0
-    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, None, None, None) == capi.APD_ERR_ARG
+    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, None, None, None, None) == capi.APD_ERR_ARG
     g.res[1] = 8
     # seeds with null pointers
-    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, ctypes.c_void_p(16), None,
+    assert lib.apd_assign(ctypes.byref(g), ctypes.byref(s), 0, ctypes.c_void_p(16), None, None,
                           None) == capi.APD_ERR_ARG
+    # wait-limit knob: null workspace or a limit beyond 32 bits
+    assert lib.apd_workspace_set_wait_limit(None, 5) == capi.APD_ERR_ARG
     h = ctypes.c_void_p()
     assert lib.apd_workspace_create(ctypes.byref(h), 5, 10, 100) == capi.APD_ERR_ARG
     assert lib.apd_workspace_create(ctypes.byref(h), 2, 0, 100) == capi.APD_ERR_ARG

@@ -1,15 +1,30 @@
-"""Full-size parity in the benchmark's launch configuration: the 1000-seed 3D
-workload on 256^3 voxels (and the 20-seed 2D one on 256^2).  The oracle
-recomputes a random sample of pixels one by one; properties that hold at any
-size (counts sum to J, coordinate sums in closed form) cover the rest."""
+"""Full-size parity in the benchmark's launch configuration.
+
+* 3D, 1000 seeds, 256^3 voxels (the benchmark workload) and 2D, 20 seeds,
+  256^2 pixels: every label and every moment word (count, sum u, sum u u^T per
+  cell) against the oracle, for each scoring arithmetic, at weights of the size
+  a solve produces and at W = 0.  Labels may differ from the oracle only where
+  its relative best/second-best gap is below 1e-9 (Algorithm 1's argmin is
+  ambiguous there); the GPU rescoring resolves those in FP64 with the oracle's
+  arithmetic, so zero mismatches are required.
+* 3D, 10,000 seeds, 512^3 voxels: labels on the 128^3 sub-grid of every 4th
+  voxel per axis (spanning the box), and every moment word of a 32-voxel slab
+  of the full grid (8.4M voxels) in the full grid's coordinates.
+
+The oracle's labels of each case are computed once per module (a few seconds
+each on the host cores) and shared by the arithmetic variants.
+"""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2403_03571_gb300 import synth
-from _gpu import dev, host, instance_tensors, require_gpu, torch
+from _gpu import host, instance_tensors, require_gpu, torch
 
 pytestmark = pytest.mark.gpu
+
+TIE_BAND = 1e-9
+PRECS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16"]
 
 
 @pytest.fixture(scope="module")
@@ -19,53 +34,78 @@ def capi():
     return c
 
 
-PRECS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16"]
-
-
 def _pc(capi, prec):
     return {"fp32": capi.APD_FP32, "fp32_pruned": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32,
             "tc_bf16": capi.APD_TC_BF16}[prec]
 
 
-@pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("which", ["2d_20", "3d_1000"])
-def test_fullsize_sampled(capi, which, prec):
-    pc = _pc(capi, prec)
-    inst = synth.workload_2d_20() if which == "2d_20" else synth.workload_3d_1000()
-    n, J, dim = inst.n, inst.grid.num_pixels, inst.grid.dim
+def _weights(inst, which):
+    if which == "zero":
+        return np.zeros(inst.n)
     g = synth.rng(99)
-    # weights of the size a solve produces
-    w = 0.3 * g.standard_normal(n) * n ** (-2.0 / dim)
-    x, A, ww, v = instance_tensors(inst, w)
+    return 0.3 * g.standard_normal(inst.n) * inst.n ** (-2.0 / inst.grid.dim)
+
+
+_INST = {}
+_REF = {}
+
+
+def _instance(name):
+    if name not in _INST:
+        _INST[name] = synth.workload_2d_20() if name == "2d_20" else synth.workload_3d_1000()
+    return _INST[name]
+
+
+def _oracle(name, which):
+    """Oracle labels, gaps and moments of the whole grid (cached)."""
+    key = (name, which)
+    if key not in _REF:
+        inst = _instance(name)
+        w = _weights(inst, which)
+        lab, gap = oracle.assign(inst.grid, inst.x, inst.A, w, with_gap=True)
+        _REF[key] = (lab, gap, oracle.moments(inst.grid, lab, inst.n))
+    return _REF[key]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("which", ["solve", "zero"])
+@pytest.mark.parametrize("name", ["2d_20", "3d_1000"])
+def test_fullsize_every_label_and_moment(capi, name, which, prec):
+    inst = _instance(name)
+    n, J, dim = inst.n, inst.grid.num_pixels, inst.grid.dim
+    w = _weights(inst, which)
+    x, A, ww, _ = instance_tensors(inst, w)
     ws = capi.Workspace(dim, n, J)
     ws.set_pruning(prec == "fp32_pruned")
     labels = torch.full((J,), -1, dtype=torch.int32, device="cuda")
-    capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=pc)
+    capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=_pc(capi, prec))
     assert ws.status() == capi.APD_OK
-    st = ws.last_stats()
-    lab = host(labels)
-    ids = g.choice(J, size=min(J, 20000), replace=False)
-    ref, gap = oracle.assign_ids(inst.grid, inst.x, inst.A, w, ids, with_gap=True)
-    np.testing.assert_array_equal(lab[ids], ref)
-    # moments: exact closed-form totals and consistency with the labels
+    rescored = ws.last_stats().rescored_fp64
     K = oracle.moment_width(dim)
-    mom = torch.zeros((n, K), dtype=torch.int64, device="cuda")
-    capi.apd_cell_moments(inst.grid, x, A, ww, mom, ws, precision=pc)
-    mo = host(mom)
-    assert mo[:, 0].sum() == J
-    np.testing.assert_array_equal(mo[:, 0], np.bincount(lab, minlength=n))
-    for d in range(dim):
-        assert mo[:, 1 + d].sum() == J * inst.grid.res[d]
-    # the rescored fraction stays small
-    # BF16 operands (2^-9 rounding) queue more near ties than TF32 or FP32
-    assert st.rescored_fp64 < (1e-2 if prec == "tc_bf16" else 2e-3) * J, st.rescored_fp64
+    mom = torch.full((n, K), -1, dtype=torch.int64, device="cuda")
+    capi.apd_cell_moments(inst.grid, x, A, ww, mom, ws, precision=_pc(capi, prec))
+    assert ws.status() == capi.APD_OK
+    ref_lab, ref_gap, ref_mom = _oracle(name, which)
+    lab = host(labels)
+    bad = lab != ref_lab
+    print(f"{name} W={which} {prec}: {int(bad.sum())} label mismatches of {J}; "
+          f"{int(np.sum(ref_gap < TIE_BAND))} oracle pixels in the 1e-9 tie band; {rescored} rescored in FP64")
+    assert not np.any(bad & (ref_gap >= TIE_BAND)), "mismatches outside the tie band"
+    assert int(bad.sum()) == 0
+    got = host(mom)
+    np.testing.assert_array_equal(got, ref_mom)
+    # volumes (m |P|) within 1e-6 relative: implied by the equal counts, stated for the record
+    assert np.max(np.abs(got[:, 0] - ref_mom[:, 0]) / np.maximum(ref_mom[:, 0], 1)) <= 1e-6
+    # the FP64 rescoring stays a small fraction of the grid
+    assert rescored < (1e-2 if prec == "tc_bf16" else 2e-3) * J, rescored
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_10000_seeds_512cube_subgrid(capi, prec):
-    """The 10,000-seed 512^3 workload: labels on the 128^3 sub-grid of every 4th
-    voxel per axis (2.1M voxels spanning the box) against the oracle, the
-    mismatch count reported (it must be zero), and closed-form totals."""
+def test_10000_seeds_512cube(capi, prec):
+    """The 10,000-seed 512^3 workload: labels of the 128^3 sub-grid of every 4th
+    voxel per axis against the oracle (zero mismatches), and every moment word
+    of the slab k_2 in [240, 272) of the full grid against the oracle's moments
+    of the same voxels in full-grid coordinates."""
     pc = _pc(capi, prec)
     inst = synth.workload_3d_10000()
     n, J, res = inst.n, inst.grid.num_pixels, inst.grid.res
@@ -81,9 +121,22 @@ def test_10000_seeds_512cube_subgrid(capi, prec):
     kk = np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)
     ids = kk[:, 0] + res[0] * (kk[:, 1] + res[1] * kk[:, 2])
     lab = host(labels)
-    ref = oracle.assign_ids(inst.grid, inst.x, inst.A, w, ids)
+    del labels
+    kb, kc = 240, 32
+    sids = oracle.slab_ids(inst.grid, kb, kc)
+    if "10k" not in _REF:  # the oracle's sub-grid and slab labels, once for all arithmetics
+        _REF["10k"] = (oracle.assign_ids(inst.grid, inst.x, inst.A, w, ids),
+                       oracle.assign_ids(inst.grid, inst.x, inst.A, w, sids))
+    ref, slab_lab = _REF["10k"]
     mismatches = int(np.sum(lab[ids] != ref))
-    print(f"10^4 seeds 512^3 {prec}: {mismatches} label mismatches on {ids.size} sub-grid voxels; "
-          f"rescored {ws.last_stats().rescored_fp64}")
+    print(f"10^4 seeds 512^3 {prec}: {mismatches} label mismatches on {ids.size} sub-grid voxels")
     assert mismatches == 0
-    assert np.bincount(lab, minlength=n).sum() == J and lab.min() >= 0
+    assert lab.min() >= 0 and np.bincount(lab, minlength=n).sum() == J
+    # one slab of the full grid: every moment word
+    K = oracle.moment_width(3)
+    mom = torch.full((n, K), -1, dtype=torch.int64, device="cuda")
+    capi.apd_cell_moments_slab(inst.grid, kb, kc, x, A, ww, mom, ws, precision=pc)
+    assert ws.status() == capi.APD_OK
+    np.testing.assert_array_equal(host(mom), oracle.moments_ids(inst.grid, sids, slab_lab, n))
+    # the GPU's own full labels agree on the slab too
+    np.testing.assert_array_equal(lab[sids], slab_lab)

@@ -2,8 +2,9 @@
 allocate device memory (a fixed device-memory budget, a host framework whose
 allocator owns all device memory, or a loop that cannot take cudaMalloc's
 implicit synchronisation).  Its scratch is a static device array, so it is
-checked through the C ABI against the workspace entry point apd_cell_moments,
-on two calls in a row (the second call must not see the first one's state).
+checked through the C ABI against the FP64 oracle's moments and against the
+workspace entry point apd_cell_moments, on two calls in a row (the second call
+must not see the first one's state).
 
 This file is collected last on purpose: it must pass alone in a fresh process
 and after every other test.
@@ -11,6 +12,7 @@ and after every other test.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2403_03571_gb300 import synth
 from _gpu import host, instance_tensors, require_gpu, torch
 
@@ -50,6 +52,8 @@ def test_no_alloc_matches_workspace_entry_point_twice():
         got = _moments_no_alloc(capi, inst)
         ref = _moments_with_workspace(capi, inst)
         np.testing.assert_array_equal(got, ref)
+        exact = oracle.moments(inst.grid, oracle.assign(inst.grid, inst.x, inst.A, inst.w), inst.n)
+        np.testing.assert_array_equal(got, exact)
         assert got[:, 0].sum() == inst.grid.num_pixels
 
 
