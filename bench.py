@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_tf32", "tc_bf16"],
                     help="scoring arithmetic of the reported form (the plain FP32 and the "
                          "tensor-core TF32 forms are always timed too)")
@@ -149,17 +149,34 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- reference arm
 
 
+# Evaluations one APD of each workload takes with the plain method (FP32 scoring,
+# W = 0, dense) on the GPU, measured by this benchmark's plain form; the oracle's
+# per-evaluation time is scaled by it to APD/s.
+PLAIN_EVALS_PER_APD = {"3d_n1000_256cube_lloyd5": 136, "2d_n20_256sq": 32, "2d_n2000_1024sq": 150,
+                       "3d_n10000_512cube": 60, "2d_batch256": 130}
+
+
 def oracle_sample_eval(inst, frac_den=16, threads=0, seed=7):
-    """Time one oracle evaluation of the dual on a 1/frac_den random pixel sample."""
+    """Time one oracle assignment (Algorithm 1, FP64) on a 1/frac_den random pixel sample."""
     import oracle
     rng = np.random.Generator(np.random.PCG64(seed))
     J = inst.grid.num_pixels
-    ids = np.sort(rng.choice(J, size=J // frac_den, replace=False))
+    ids = np.sort(rng.choice(J, size=max(1, J // frac_den), replace=False))
     w = np.zeros(inst.n)
     t0 = time.perf_counter()
     oracle.assign_ids(inst.grid, inst.x, inst.A, w, ids, nthreads=threads)
     dt = time.perf_counter() - t0
     return dt, ids.shape[0] * inst.n, J * inst.n
+
+
+def oracle_full_eval(inst, x, w, threads=0):
+    """One complete FP64 evaluation by the oracle: Algorithm 1 over every pixel and
+    the per-cell sums of eqs. (2.7)-(2.8).  Returns (seconds, labels, max rel error)."""
+    import oracle
+    t0 = time.perf_counter()
+    lab = oracle.assign(inst.grid, x, inst.A, w, nthreads=threads)
+    _, _, err, _, _ = oracle.dual_from_labels(inst.grid, x, inst.A, w, inst.v, lab, nthreads=threads)
+    return time.perf_counter() - t0, lab, err
 
 
 def cpu_cores():
@@ -170,38 +187,78 @@ def cpu_cores():
 
 
 def run_reference(args, evals_per_apd):
-    """The oracle on the host cores: each step times one evaluation on a pixel sample,
-    scaled to the full grid and to the evaluations one APD needs."""
+    """The oracle on the host cores.  Each step is one complete FP64 evaluation of
+    the workload's dual (every pixel, every seed), timed as it runs; the APD rate
+    scales the mean evaluation time by the evaluations one APD takes with the plain
+    method.  Warm-up steps assign a 1/64 pixel sample."""
     import oracle
     oracle.lib()
     inst, rounds = make_instance(args.workload, 0)
-    frac = 16 if inst.grid.dim == 3 else 1
+    w = np.zeros(inst.n)
     for _ in range(max(0, args.warmup)):
-        oracle_sample_eval(inst, frac_den=frac * 4)
+        oracle_sample_eval(inst, frac_den=64)
     times = []
-    pairs_s = []
-    for k in range(args.steps):
-        dt, pairs, full_pairs = oracle_sample_eval(inst, frac_den=frac, seed=100 + k)
-        t_eval = dt * full_pairs / pairs
-        times.append(t_eval * evals_per_apd)
-        pairs_s.append(pairs / dt)
-    ms = 1000.0 * statistics.mean(times)
-    val = 1.0 / statistics.mean(times)
+    for _ in range(args.steps):
+        dt, _, _ = oracle_full_eval(inst, inst.x, w)
+        times.append(dt)
+    t_eval = statistics.mean(times)
+    val = 1.0 / (t_eval * evals_per_apd)
     cores = oracle.max_threads()
-    sample = (f"one FP64 evaluation (Algorithm 1 + moments) on a random 1/{frac} pixel sample "
-              f"({inst.grid.num_pixels // frac} of {inst.grid.num_pixels} pixels x {inst.n} seeds) per "
-              f"step, scaled to the full grid and to {evals_per_apd} evaluations per APD "
-              f"(the plain method's count on the GPU)")
+    pairs = inst.grid.num_pixels * inst.n
+    sample = (f"each step one complete FP64 evaluation (Algorithm 1 over all {inst.grid.num_pixels} pixels x "
+              f"{inst.n} seeds, then the per-cell sums of eqs. (2.7)-(2.8)) at W = 0, timed; the APD rate "
+              f"divides by {evals_per_apd} evaluations per APD (the plain method's count on the GPU)")
     return {
         "impl": "reference", "metric": metric_name(args.workload), "value": val, "unit": "APD/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_eval, "step": "one complete FP64 evaluation of the dual",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(args.workload, inst, rounds, args.precision),
-        "pair_evals_per_s": statistics.mean(pairs_s),
-        "cpu_baseline": {"value": val, "unit": "APD/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+        "pair_evals_per_s": pairs / t_eval, "evaluation_s": t_eval, "evals_per_apd": evals_per_apd,
+        "cpu_baseline": {"value": val, "unit": "APD/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "APD/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+def cpu_baseline_block(args, inst, x_fin, w_fin, gpu_labels, evals_per_apd):
+    """The oracle timed on the host cores beside the GPU run (rank 0, N = 1):
+    one complete FP64 evaluation at the chosen form's final generators (all
+    cores), the same on a 1/64 pixel sample with one thread, and a full oracle
+    solve (scipy L-BFGS-B, Algorithm 2) of the 20-seed 2D workload.  The final
+    evaluation also gives the accuracy report: label mismatches of the GPU
+    against the oracle outside the 1e-9 tie band, and the largest relative
+    difference of cell volumes."""
+    import oracle
+    from paper_2403_03571_gb300 import synth
+    oracle.lib()
+    cores = oracle.max_threads()
+    t_full, lab, err = oracle_full_eval(inst, x_fin, w_fin)
+    pairs = inst.grid.num_pixels * inst.n
+    out = {"value": 1.0 / (t_full * evals_per_apd), "unit": "APD/s", "cores": cores, "kind": "oracle",
+           "sample": (f"one complete FP64 evaluation ({inst.grid.num_pixels} pixels x {inst.n} seeds) at the "
+                      f"chosen form's final generators on {cores} threads, scaled by {evals_per_apd} "
+                      "evaluations per APD (the plain method's count on the GPU)"),
+           "evaluation_s": t_full, "pair_evals_per_s": pairs / t_full}
+    dt1, p1, _ = oracle_sample_eval(inst, frac_den=64, threads=1, seed=11)
+    out["one_thread"] = {"pair_evals_per_s": p1 / dt1, "evaluation_s_est": pairs / (p1 / dt1),
+                         "sample": "1/64 of the pixels, one thread"}
+    c0 = synth.workload_2d_20()
+    t0 = time.perf_counter()
+    w0, info0 = oracle.solve_weights(c0.grid, c0.x, c0.A, c0.v, eps=0.01)
+    out["config0_full_solve"] = {"workload": "2d_n20_256sq", "seconds": time.perf_counter() - t0,
+                                 "evaluations": int(info0["evals"]), "converged": bool(info0["converged"]),
+                                 "max_rel_err": float(info0["max_rel_err"]), "threads": cores,
+                                 "solver": "scipy L-BFGS-B on the oracle's dual"}
+    acc = None
+    if gpu_labels is not None:
+        ref_lab, gap = oracle.assign(inst.grid, x_fin, inst.A, w_fin, with_gap=True)
+        bad = gpu_labels != ref_lab
+        m_gpu = np.bincount(gpu_labels, minlength=inst.n)
+        m_ref = np.bincount(ref_lab, minlength=inst.n)
+        acc = {"label_mismatches": int(bad.sum()), "outside_tie_band": int(np.sum(bad & (gap >= 1e-9))),
+               "max_rel_volume_diff": float(np.max(np.abs(m_gpu - m_ref) / np.maximum(m_ref, 1))),
+               "oracle_max_rel_volume_error": float(err), "pixels": int(inst.grid.num_pixels)}
+    return out, acc
 
 
 def metric_name(workload):
@@ -458,6 +515,16 @@ def run_ours(args):
     forms["chosen"] = measure_form(args, ctx, args.precision, chosen_start=True)
     forms["chosen"]["precision"] = args.precision
     forms["chosen"]["pruned"] = bool(args.prune)
+    # the chosen form's final generators and its labels there (for the accuracy report)
+    x_fin = (ctx["x_out"] if rounds > 0 else ctx["x0"]).clone()
+    w_fin = ctx["w_out"].clone()
+    gpu_lab = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        lab_t = torch.empty(J, dtype=torch.int32, device=dev)
+        ctx["ws"].set_pruning(bool(args.prune))
+        capi.apd_assign(inst.grid, x_fin, ctx["A"], w_fin, lab_t, ctx["ws"], precision=precision_code(capi, args.precision))
+        gpu_lab = lab_t.cpu().numpy()
+        del lab_t
     for prec in dict.fromkeys(["fp32", "tc_tf32"]):
         forms[prec] = measure_form(args, ctx, prec)
         forms[prec]["precision"] = prec
@@ -507,13 +574,12 @@ def run_ours(args):
                           + (" with seed-group pruning" if args.prune else ""))
     out["coarse_evaluations_per_apd"] = chosen["coarse_evaluations_per_apd"]
     out["warm_start_network"] = chosen["warm_start_network"]
-    if not args.no_cpu_baseline:
-        ref_args = argparse.Namespace(**vars(args))
-        ref_args.steps, ref_args.warmup = 1, 0
+    if not args.no_cpu_baseline and world == 1:
         # the oracle does the APD with the plain method: scale by the plain form's evaluation count
-        ref = run_reference(ref_args, int(round(forms["fp32"]["evaluations_per_apd"])))
-        out["cpu_baseline"] = ref["cpu_baseline"]
-        out["cpu_baseline"]["pair_evals_per_s"] = ref["pair_evals_per_s"]
+        cb, acc = cpu_baseline_block(args, inst, x_fin.cpu().numpy(), w_fin.cpu().numpy(), gpu_lab,
+                                     int(round(forms["fp32"]["evaluations_per_apd"])))
+        out["cpu_baseline"] = cb
+        out["accuracy_vs_oracle"] = acc
     if world > 1:
         dist.destroy_process_group()
     return out
@@ -847,10 +913,7 @@ def main():
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:
             return 0
-        # evaluations per APD measured on the GPU are not known here: use the
-        # count this workload needed in the committed GPU profile run
-        evals = int(os.environ.get("APD_EVALS_PER_APD", "136"))
-        print(json.dumps(run_reference(args, evals)))
+        print(json.dumps(run_reference(args, PLAIN_EVALS_PER_APD.get(args.workload, 136))))
         return 0
     if args.workload == "2d_batch256":
         out = run_batch(args)

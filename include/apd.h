@@ -68,12 +68,15 @@ typedef struct {
 } apd_seeds;
 
 /* Arithmetic of the scoring stage (Algorithm 1).  Every precision returns the
- * same labels: candidates are rescored exactly (FP32, then FP64 for near ties
- * with the reference arithmetic of the cost matrix). */
+ * same labels: a label is kept only when a rigorous rounding bound certifies
+ * it, and every other pixel is rescored in FP64 with the reference arithmetic
+ * of the cost matrix. */
 typedef enum {
     APD_FP32 = 0,    /* CUDA-core FP32 scoring of the expanded quadratic */
-    APD_TC_BF16 = 1, /* tcgen05 BF16 contraction of [y (x) y, y, 1] . phi_i, FP32 accumulate */
-    APD_TC_TF32 = 2  /* tcgen05 TF32 contraction, FP32 accumulate */
+    APD_TC_BF16 = 1, /* tcgen05 contraction of the features [y (x) y, y, 1] . phi_i, each FP32
+                        feature split into two BF16 operands (hi + lo; three products summed,
+                        K = 32), FP32 accumulate: ~1e-4 relative score error */
+    APD_TC_TF32 = 2  /* the same with TF32 operands: ~3e-5 relative score error */
 } apd_precision;
 
 typedef struct apd_workspace apd_workspace;
@@ -96,14 +99,16 @@ int apd_workspace_create(apd_workspace **ws, int32_t dim, int32_t max_n, int64_t
  * uses it is still in flight. */
 void apd_workspace_destroy(apd_workspace *ws);
 
-/* Seed-group pruning of the FP32 scoring (default off: the dense sweep of
- * Algorithm 1).  When on, each warp skips every 32-seed group (Morton scan
- * order) whose cost lower bound over the warp's pixels,
+/* Seed pruning of the scoring (default off: the dense sweep of Algorithm 1).
+ * FP32: each warp skips every 32-seed group (Morton scan order) whose cost
+ * lower bound over the warp's pixels,
  *     min lambda_min * dist(pixel box, seed box)^2 - (max w - w_ref),
- * exceeds the largest second-best cost among those pixels: such seeds can
- * change no label and no near-tie decision, so labels and moments are the
- * same as without pruning.  Applies to every later FP32 scoring call on the
- * workspace (the tensor-core forms are always dense). */
+ * exceeds the largest second-best cost among those pixels.  Tensor cores:
+ * each 512-pixel tile scores only the seeds whose lower bound over the tile
+ * lies below the fourth smallest upper bound lambda_max maxdist^2 - (w - w_ref);
+ * the smallest bound of the seeds left out enters the certificate of every
+ * label of the tile.  Either way labels and moments are the same as without
+ * pruning.  Applies to every later scoring call on the workspace. */
 int apd_workspace_set_pruning(apd_workspace *ws, int32_t enable);
 
 /* Poll limit of the bounded shared-memory barrier waits of the FP32 scoring
@@ -146,12 +151,13 @@ int apd_cell_moments_slab(const apd_grid *grid, int32_t k_begin, int32_t k_count
 
 /* Reduction hook of a sharded workspace.  Called on the host, once per
  * evaluation, after the moments of this rank's slab have been enqueued on
- * `stream` into `moments` (device, `words` int64 values) at the weights `w`
- * (device [n]); it must leave in `moments`, ordered before any later work on
- * `stream`, the elementwise sum of every rank's moments (an allreduce SUM of
- * int64, e.g. NCCL's).  Return 0 on success; anything else aborts the call
- * with APD_ERR_CUDA. */
-typedef int (*apd_reduce_fn)(void *ctx, int64_t *moments, int64_t words, const double *w, int32_t n,
+ * `stream` into `moments` (device, `words` int64 values) for the generators
+ * `seeds` of that evaluation (device pointers: the positions, matrices and
+ * trial weights it scored); it must leave in `moments`, ordered before any
+ * later work on `stream`, the elementwise sum of every rank's moments (an
+ * allreduce SUM of int64, e.g. NCCL's).  Return 0 on success; anything else
+ * aborts the call with APD_ERR_CUDA. */
+typedef int (*apd_reduce_fn)(void *ctx, int64_t *moments, int64_t words, const apd_seeds *seeds,
                              apd_stream_t stream);
 
 /* Make every later scoring pass on this workspace cover only rank `rank`'s

@@ -81,6 +81,11 @@ class ApdSolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+# int (*)(void *ctx, int64_t *moments, int64_t words, const apd_seeds *seeds, cudaStream_t stream)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.POINTER(ApdSeeds), ctypes.c_void_p)
+
+
 class ApdMultiresOpts(ctypes.Structure):
     _fields_ = [("factor", ctypes.c_int32), ("coarse_eps", ctypes.c_double),
                 ("coarse_max_evals", ctypes.c_int32)]
@@ -93,11 +98,6 @@ class ApdRefineOpts(ctypes.Structure):
 class ApdPoints(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("count", ctypes.c_int64), ("y", ctypes.c_void_p),
                 ("mass", ctypes.c_void_p)]
-
-
-# int (*)(void *ctx, int64_t *moments, int64_t words, const double *w, int32_t n, cudaStream_t)
-REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                             ctypes.c_int32, ctypes.c_void_p)
 
 
 class ApdError(RuntimeError):

@@ -154,10 +154,9 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
         APD_TRY(cuda_ok(cudaEventRecord(e0, st)));
     }
     // the tensor-core tiling needs per-tile scratch; grids too thin for the
-    // workspace's tile capacity, and windowed passes, are scored by the FP32
-    // kernel (same labels)
+    // workspace's tile capacity are scored by the FP32 kernel (same labels)
     if (empty) {
-    } else if (prec == APD_FP32 || tc_tile_count(g) > ws.tc_tile_cap || g.kz1)
+    } else if (prec == APD_FP32 || tc_tile_count(g) > ws.tc_tile_cap)
         APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
     else
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
@@ -165,12 +164,13 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
     if (!empty) APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
     if (sharded) {
         // every rank's slab moments, summed, before anything reads them
-        if (ws.shard_fn(ws.shard_ctx, reinterpret_cast<int64_t *>(mom), (int64_t)n * moment_width(g.dim), w, n,
+        const apd_seeds cur{n, x, A, w};
+        if (ws.shard_fn(ws.shard_ctx, reinterpret_cast<int64_t *>(mom), (int64_t)n * moment_width(g.dim), &cur,
                         (apd_stream_t)st) != 0)
             return APD_ERR_CUDA;
     }
-    ws.kernel_launches += weights_only ? 3 + (prec == APD_FP32 ? 0 : 2)
-                                       : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 2) +
+    ws.kernel_launches += weights_only ? 3 + (prec == APD_FP32 ? 0 : 1)
+                                       : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 1) +
                                              (step ? 1 : 0);
     ws.last_pixels = win_pixels(g);
     ws.last_pairs = win_pixels(g) * (long long)n;
@@ -600,7 +600,9 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     w.tc_tile_cap = max_j / 64 + 4096;
     alloc((void **)&w.tc_centre, (size_t)w.tc_tile_cap * 6 * sizeof(float));
     alloc((void **)&w.tc_start, (size_t)w.tc_tile_cap * sizeof(int));
-    alloc((void **)&w.tc_cand, (size_t)max_j * sizeof(int4));
+    alloc((void **)&w.tc_count, (size_t)w.tc_tile_cap * sizeof(int));
+    alloc((void **)&w.tc_texcl, (size_t)w.tc_tile_cap * sizeof(float));
+    alloc((void **)&w.tc_list, (size_t)w.tc_tile_cap * tc_list_cap() * sizeof(int));
     alloc((void **)&w.part, nb * 5 * sizeof(double));
     alloc((void **)&w.grad, (size_t)max_n * sizeof(double));
     alloc((void **)&w.W, (size_t)max_n * sizeof(double));
@@ -634,7 +636,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_cand, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_count, w.tc_texcl, w.tc_list, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
         if (p) cudaFree(p);

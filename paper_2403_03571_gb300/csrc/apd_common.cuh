@@ -173,6 +173,7 @@ __device__ __forceinline__ void build_seed(const int i, const int n, const doubl
 #pragma unroll
     for (int a = 0; a < 6; ++a) r32.a[a] = r.a[a];
     r32.pad[0] = r.pad[0];
+    r32.pad[1] = __double2float_ru(frob * (1.0 + 1e-12));  // upper bound of lambda_max: ||sym A||_F
 }
 
 // Bounds of group `grp` (32 consecutive records, positions >= n are padding),

@@ -33,12 +33,13 @@ struct __align__(16) SeedRec {
 static_assert(sizeof(SeedRec) == 64, "SeedRec must be 64 bytes");
 
 // Seed record of the FP32 direct-form rescoring pass: x and w split into
-// FP32 high and low parts (x = x_hi + x_lo to ~2^-48 relative), FP32 symmetric A.
+// FP32 high and low parts (x = x_hi + x_lo to ~2^-48 relative), FP32 symmetric A,
+// a lower bound of lambda_min and an upper bound of lambda_max of the FP64 A.
 struct __align__(16) SeedRec32 {
     float xh[3], xl[3];
     float wh, wl;
     float a[6];
-    float pad[2];
+    float pad[2];  // [0] lambda_min lower bound, [1] lambda_max upper bound
 };
 static_assert(sizeof(SeedRec32) == 64, "SeedRec32 must be 64 bytes");
 
@@ -96,9 +97,11 @@ struct Workspace {
     int32_t *perm = nullptr;            // [n_pad_max] scan position -> seed index
     SeedRec32 *recs32s = nullptr;       // [n_pad_max] SeedRec32 in scan order
     float *tc_centre = nullptr;         // [tc_tile_cap][6] tensor-core tile centres (FP32 hi, lo)
-    int *tc_start = nullptr;            // [tc_tile_cap] Morton start chunk per tile
+    int *tc_start = nullptr;            // [tc_tile_cap] Morton start chunk per tile (dense form)
+    int *tc_count = nullptr;            // [tc_tile_cap] candidate seeds per tile (pruned form)
+    float *tc_texcl = nullptr;          // [tc_tile_cap] cost lower bound of the seeds left out
+    int *tc_list = nullptr;             // [tc_tile_cap][tc_list_cap()] candidates (scan positions)
     long long tc_tile_cap = 0;
-    int4 *tc_cand = nullptr;            // [max_j] tensor-core candidates per pixel (3 seeds, 4th score)
     bool sorted = false;                // set by launch_seed_prep for the current pass
     bool prune = false;                 // FP32 scoring skips seed groups by their bounds
     uint32_t wait_limit = kDefaultWaitPolls;  // polls of the scoring kernels' chunk waits
@@ -302,11 +305,14 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
 // FP32 scoring fused with the moments; queues near ties; labels optional.
 cudaError_t launch_assign_fp32(const GridDev &g, int n, Workspace &ws, int32_t *labels,
                                unsigned long long *moments, cudaStream_t st);
-// tcgen05 scoring fused with the moments (kind 0 = TF32, 1 = BF16); queues near ties.
+// tcgen05 scoring fused with the moments (kind 0 = TF32, 1 = BF16; per-tile candidate
+// lists when ws.prune); queues the pixels it cannot certify.
 cudaError_t launch_assign_tc(const GridDev &g, int n, Workspace &ws, int32_t *labels,
                              unsigned long long *moments, int kind, cudaStream_t st);
-// number of tensor-core tiles the grid needs (the workspace holds tc_tile_cap)
+// number of tensor-core tiles the grid's scoring window needs (the workspace holds
+// tc_tile_cap), and the candidate seeds stored per tile
 long long tc_tile_count(const GridDev &g);
+int tc_list_cap();
 // bounds of the 32-seed groups of the scan-order records (ws.groups)
 cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st);
 // FP64 rescoring of the queued pixels (labels optional, moments updated).

@@ -17,13 +17,6 @@ constexpr int kM = 128, kN = 128, kK = 16;
 __device__ __forceinline__ float check_a(int r, int k) { return (float)(((r * 5 + k * 3) % 9) - 4); }
 __device__ __forceinline__ float check_b(int n, int k) { return (float)(((n * 7 + k) % 7) - 3); }
 
-// byte offset of element (row, k) in the K-major, no-swizzle core-matrix layout
-__device__ __forceinline__ uint32_t cm_offset(int row, int k, int eb, uint32_t lbo, uint32_t sbo) {
-    const int epr = 16 / eb;  // elements per 16-byte core-matrix row
-    return (uint32_t)(row / 8) * sbo + (uint32_t)(k / epr) * lbo + (uint32_t)(row % 8) * 16u +
-           (uint32_t)(k % epr) * (uint32_t)eb;
-}
-
 template <int KIND>
 __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatches, unsigned *max_err_bits,
                                                        int *status) {
@@ -39,7 +32,7 @@ __global__ void __launch_bounds__(128) tc_check_kernel(int variant, int *mismatc
 
     for (int e = tid; e < kM * kK; e += blockDim.x) {
         const int r = e / kK, k = e % kK;
-        const uint32_t oa = cm_offset(r, k, eb, LBO, SBO);
+        const uint32_t oa = tc::core_offset(r, k, eb, LBO, SBO);
         if (KIND == tc::KIND_TF32) {
             *reinterpret_cast<float *>(smA + oa) = check_a(r, k);
             *reinterpret_cast<float *>(smB + oa) = check_b(r, k);

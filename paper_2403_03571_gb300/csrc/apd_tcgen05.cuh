@@ -36,11 +36,20 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // ---- descriptors ---------------------------------------------------------------
-// Shared-memory matrix descriptor, K-major operand without swizzling: the
+// Byte offset of element (row, k) of a K-major operand without swizzling: the
 // operand is tiled in "core matrices" of 8 rows x 16 bytes (128 contiguous
-// bytes); `lbo` is the byte distance between core matrices adjacent along K,
-// `sbo` between core matrices adjacent along M (or N).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// bytes, row r of a core matrix at 16 r); `lbo` is the byte distance between
+// core matrices adjacent along K, `sbo` between core matrices adjacent along
+// M (or N); eb = bytes per element.
+__host__ __device__ __forceinline__ uint32_t core_offset(int row, int k, int eb, uint32_t lbo, uint32_t sbo) {
+    const int epr = 16 / eb;  // elements per 16-byte core-matrix row
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / epr) * lbo + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k % epr) * (uint32_t)eb;
+}
+
+// Shared-memory matrix descriptor of such an operand starting at shared
+// address saddr (16-byte aligned).
+__host__ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3ffffu) >> 4);          // bits 0-13: start address / 16
     d |= (uint64_t)((lbo >> 4) & 0x3fffu) << 16;        // bits 16-29: leading byte offset / 16

@@ -42,7 +42,7 @@ def allreduce_hook(group=None):
     library's stream."""
     import torch.distributed as dist
 
-    def hook(ctx, mom_ptr, words, w_ptr, n, stream_ptr):
+    def hook(ctx, mom_ptr, words, seeds, stream_ptr):
         try:
             import torch
             t = device_view(mom_ptr, words, "int64")

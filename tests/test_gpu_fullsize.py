@@ -24,7 +24,7 @@ from _gpu import host, instance_tensors, require_gpu, torch
 pytestmark = pytest.mark.gpu
 
 TIE_BAND = 1e-9
-PRECS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16"]
+PRECS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16", "tc_tf32_pruned", "tc_bf16_pruned"]
 
 
 @pytest.fixture(scope="module")
@@ -35,8 +35,8 @@ def capi():
 
 
 def _pc(capi, prec):
-    return {"fp32": capi.APD_FP32, "fp32_pruned": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32,
-            "tc_bf16": capi.APD_TC_BF16}[prec]
+    return {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32,
+            "tc_bf16": capi.APD_TC_BF16}[prec.replace("_pruned", "")]
 
 
 def _weights(inst, which):
@@ -76,7 +76,7 @@ def test_fullsize_every_label_and_moment(capi, name, which, prec):
     w = _weights(inst, which)
     x, A, ww, _ = instance_tensors(inst, w)
     ws = capi.Workspace(dim, n, J)
-    ws.set_pruning(prec == "fp32_pruned")
+    ws.set_pruning(prec.endswith("_pruned"))
     labels = torch.full((J,), -1, dtype=torch.int32, device="cuda")
     capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=_pc(capi, prec))
     assert ws.status() == capi.APD_OK
@@ -97,7 +97,7 @@ def test_fullsize_every_label_and_moment(capi, name, which, prec):
     # volumes (m |P|) within 1e-6 relative: implied by the equal counts, stated for the record
     assert np.max(np.abs(got[:, 0] - ref_mom[:, 0]) / np.maximum(ref_mom[:, 0], 1)) <= 1e-6
     # the FP64 rescoring stays a small fraction of the grid
-    assert rescored < (1e-2 if prec == "tc_bf16" else 2e-3) * J, rescored
+    assert rescored < 1e-2 * J, rescored
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -113,7 +113,7 @@ def test_10000_seeds_512cube(capi, prec):
     w = 0.3 * g.standard_normal(n) * n ** (-2.0 / 3)
     x, A, ww, v = instance_tensors(inst, w)
     ws = capi.Workspace(3, n, J)
-    ws.set_pruning(prec == "fp32_pruned")
+    ws.set_pruning(prec.endswith("_pruned"))
     labels = torch.full((J,), -1, dtype=torch.int32, device="cuda")
     capi.apd_assign(inst.grid, x, A, ww, labels, ws, precision=pc)
     assert ws.status() == capi.APD_OK

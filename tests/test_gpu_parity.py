@@ -26,17 +26,17 @@ def capi():
     return c
 
 
-PRECISIONS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16"]
+PRECISIONS = ["fp32", "fp32_pruned", "tc_tf32", "tc_bf16", "tc_tf32_pruned", "tc_bf16_pruned"]
 
 
 def _prec(capi, name):
-    return {"fp32": capi.APD_FP32, "fp32_pruned": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32,
-            "tc_bf16": capi.APD_TC_BF16}[name]
+    return {"fp32": capi.APD_FP32, "tc_tf32": capi.APD_TC_TF32,
+            "tc_bf16": capi.APD_TC_BF16}[name.replace("_pruned", "")]
 
 
 def _ws(capi, dim, n, J, prec):
     ws = capi.Workspace(dim, n, J)
-    ws.set_pruning(prec == "fp32_pruned")
+    ws.set_pruning(prec.endswith("_pruned"))
     return ws
 
 
@@ -234,7 +234,7 @@ def test_deterministic_moments(capi, prec):
 GAP_RTOL = 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp32_pruned", "tc_bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_pruned", "tc_bf16_pruned"])
 @pytest.mark.parametrize("dim,n,res,seed,wscale", CASES)
 def test_tie_gap_matches_oracle(capi, dim, n, res, seed, wscale, prec):
     """apd_assign's optional tie_gap output: the relative gap of the two smallest

@@ -1,20 +1,26 @@
-"""The tensor-core scorer's rounding bounds, checked on the CPU.
+"""The tensor-core scorer's rounding bounds and certificate, checked on the CPU.
 
 A tile of the tcgen05 kernel (8^3 voxels in 3D, 32 x 16 pixels in 2D) scores
-pixel j against seed i as the dot product of pixel features
-f = [y'_a y'_b (a <= b), y'_a, 1] (y' = pixel centre - tile centre, FP32) and
+pixel j against seed i as the dot product of the pixel features
+f = [y'_a y'_b (a <= b), y'_a, 1] (y' = pixel centre - tile centre, FP32) and the
 seed features phi = [A_ab (x2 off the diagonal), -2 (A x')_a, x'^T A x' - w']
-(x' = x_i - tile centre from FP32 high/low splits, w' = w_i - w_ref), both
-rounded to TF32 (round to nearest, ties away) or BF16 (round to nearest even),
-products summed in FP32.  The kernel relies on two facts:
-  1. |score - C_exact| <= err_unit * sum_k |f_k phi_k|,
-     err_unit = 1.5 (2 e + e^2 + 100 u), e = 2^-11 (TF32) or 2^-9 (BF16);
-  2. every seed outside a pixel's three best scores has an exact cost of at
-     least s4 - psi, s4 the fourth-best score and psi the kernel's bound from
-     max ||A||_F, min lambda_min and the tile radius R.
-This file restates the scores in numpy (two summation orders) and checks both
-facts against exact rational costs; an err_unit without the operand roundings
-fails fact 1 (planted mistake)."""
+(x' = x_i - tile centre from FP32 high/low splits, w' = w_i - w_ref).  Each
+FP32 feature v is split into operands vh = rnd(v), vl = rnd(v - vh) of the
+tensor format (TF32: round to nearest, ties away; BF16: round to nearest even),
+the contraction sums fh.phih + fl.phih + fh.phil in FP32, and the kernel keeps
+the score with the step-local seed index in its five low mantissa bits.
+
+This file restates that arithmetic in numpy and checks, against exact rational
+costs C' = (y - x)^T A (y - x) + (w_ref - w):
+  1. every packed score lies within err_unit * sum_k |f_k phi_k| of C';
+  2. the candidate pre-pass's lower bound (lambda_min dist^2 + (w_ref - w),
+     FP32 with its directed roundings and slacks, restated with exact
+     rounding) never exceeds C' at a pixel of the tile;
+  3. the certificate: whenever s1 + psi(s1) < min(s2 - psi(s2), T_excl), the
+     best score's seed is the exact argmin over all seeds (those left out of
+     the candidate list included).
+Planted mistakes: operands that are not split, and a lower bound built with
+the largest eigenvalue in place of the smallest, must fail."""
 from fractions import Fraction as Fr
 
 import numpy as np
@@ -29,7 +35,7 @@ def f32(v):
 
 
 def fma32(a, b, c):
-    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+    return np.float32(Fr(float(a)) * Fr(float(b)) + Fr(float(c)))
 
 
 def to_tf32(v):
@@ -47,6 +53,16 @@ def to_bf16(v):
 def split(v):
     h = np.float32(v)
     return h, np.float32(np.float64(v) - np.float64(h))
+
+
+def rd32(x):
+    """Largest float32 <= the rational x (exact directed rounding)."""
+    f = np.float32(float(x))
+    while Fr(float(f)) > x:
+        f = np.nextafter(f, np.float32(-np.inf))
+    while Fr(float(np.nextafter(f, np.float32(np.inf)))) <= x:
+        f = np.nextafter(f, np.float32(np.inf))
+    return f
 
 
 def spd(g, dim, cond):
@@ -82,18 +98,33 @@ def seed_features(D, x, A, w, cen, wref):
         q = fma32(xp[i], t[i], q)
     two = f32(2.0)
     if D == 3:
-        return [a[0][0], two * a[0][1], two * a[0][2], a[1][1], two * a[1][2], a[2][2],
-                -two * t[0], -two * t[1], -two * t[2], f32(q - wp)]
-    return [a[0][0], two * a[0][1], a[1][1], -two * t[0], -two * t[1], f32(q - wp)]
+        feats = [a[0][0], two * a[0][1], two * a[0][2], a[1][1], two * a[1][2], a[2][2],
+                 -two * t[0], -two * t[1], -two * t[2], f32(q - wp)]
+    else:
+        feats = [a[0][0], two * a[0][1], a[1][1], -two * t[0], -two * t[1], f32(q - wp)]
+    return feats, xp, wp
 
 
-def score(f, phi, rnd, order):
-    prods = [np.float64(rnd(fk)) * np.float64(rnd(pk)) for fk, pk in zip(f, phi)]  # exact
+def score(f, phi, rnd, order, split_ops=True):
+    """Packed-free score: the split contraction summed in FP32 in one of two orders."""
+    prods = []
+    for fk, pk in zip(f, phi):
+        fh, ph = rnd(fk), rnd(pk)
+        if split_ops:
+            fl, pl = rnd(f32(fk - fh)), rnd(f32(pk - ph))
+            prods += [Fr(float(fh)) * Fr(float(ph)), Fr(float(fl)) * Fr(float(ph)), Fr(float(fh)) * Fr(float(pl))]
+        else:
+            prods.append(Fr(float(fh)) * Fr(float(ph)))
     idx = range(len(prods)) if order == 0 else reversed(range(len(prods)))
     s = f32(0.0)
     for k in idx:
-        s = f32(np.float64(s) + prods[k])
+        s = np.float32(Fr(float(s)) + prods[k])
     return s
+
+
+def pack(s, idx):
+    b = np.array([s], dtype=np.float32).view(np.uint32)[0]
+    return np.array([(b & np.uint32(0xFFFFFFE0)) | np.uint32(idx)], dtype=np.uint32).view(np.float32)[0]
 
 
 def exact_cost(y, x, A, w, wref):
@@ -103,18 +134,41 @@ def exact_cost(y, x, A, w, wref):
     return q - (Fr(float(w)) - Fr(float(wref)))
 
 
-def err_unit(kind, with_operands=True):
-    e = 2.0 ** -11 if kind == "tf32" else 2.0 ** -9
-    return 1.5 * ((2 * e + e * e) if with_operands else 0.0) + 1.5 * 100 * U
+def err_unit(kind):
+    e = 2.0 ** -11 if kind == "tf32" else 2.0 ** -8
+    return 1.5 * (3.1 * e * e + 32 * 2.0 ** -22 + 100 * U + 2.0 ** -18)
 
 
-def run_case(D, kind, seed, eu, order, n=48, pixels=12):
-    """(violations of fact 1, violations of fact 2) for one random tile."""
+def psi(s, eu, Lam, lam, R):
+    c = abs(s)
+    r1 = 2 * R + np.sqrt(c / lam)
+    p = eu * (Lam * r1 * r1 + c)
+    c = abs(s) + p
+    r1 = 2 * R + np.sqrt(c / lam)
+    return 1.1 * eu * (Lam * r1 * r1 + c)
+
+
+def lower_bound(D, xp, wp, lam_i, rlo, rhi, with_slack=True):
+    """The pre-pass's FP32 lower bound of C' over the tile's pixel box, with the
+    kernel's directed roundings done exactly."""
+    d2 = f32(0.0)
+    for a in range(D):
+        xs = xp[a]
+        slack = f32(f32(1e-6) * f32(f32(abs(rlo[a]) + abs(rhi[a])) + f32(2.0) * abs(xs))) + f32(1e-30)
+        if not with_slack:
+            slack = f32(0.0)
+        dl = max(f32(max(f32(xs - rhi[a]), f32(rlo[a] - xs)) - slack), f32(0.0))
+        d2 = rd32(Fr(float(dl)) * Fr(float(dl)) + Fr(float(d2)))
+    wn = f32(-wp)
+    wslack = f32(f32(1e-6) * abs(wn)) + f32(1e-30)
+    t = rd32(Fr(float(rd32(Fr(float(lam_i)) * Fr(float(d2))))) * Fr(float(f32(1.0 - 1e-5))))
+    return rd32(Fr(float(t)) + Fr(float(rd32(Fr(float(wn)) - Fr(float(wslack))))))
+
+
+def make_tile(D, seed, n):
     g = np.random.Generator(np.random.PCG64(seed))
-    rnd = to_tf32 if kind == "tf32" else to_bf16
     res = (256, 256, 256) if D == 3 else (1024, 1024)
     h = 1.0 / np.asarray(res, dtype=np.float64)
-    h32 = [f32(v) for v in h]
     td = GEOM[D]
     kb = [int(g.integers(0, res[a] // td[a])) * td[a] for a in range(D)]
     cen = [(kb[a] + td[a] // 2) * h[a] for a in range(D)]
@@ -125,45 +179,76 @@ def run_case(D, kind, seed, eu, order, n=48, pixels=12):
     As = [spd(g, D, [1.0, 10.0, 1e3][seed % 3]) * 10 ** g.uniform(-0.5, 0.5) for _ in range(n)]
     ws = g.uniform(0.0, 1.0, n) * span ** 2
     wref = float(ws.max())
+    return g, h, td, kb, cen, R, xs, As, ws, wref
+
+
+def run_case(D, kind, seed, order, n=40, pixels=10, split_ops=True, with_slack=True):
+    """(violations of fact 1, of fact 2, of fact 3) on one random tile."""
+    g, h, td, kb, cen, R, xs, As, ws, wref = make_tile(D, seed, n)
+    rnd = to_tf32 if kind == "tf32" else to_bf16
+    h32 = [f32(v) for v in h]
+    eu = err_unit(kind)
     Lam = max(float(np.linalg.norm(A)) for A in As)
-    lam = min(float(np.linalg.eigvalsh(A).min()) for A in As) * (1 - 1e-9)
-    phis = [seed_features(D, xs[i], As[i], ws[i], cen, wref) for i in range(n)]
-    bad1 = bad2 = 0
+    lam_i = [f32(np.linalg.eigvalsh(A).min() * (1 - 1e-6)) for A in As]
+    lam = min(float(v) for v in lam_i)
+    feats = [seed_features(D, xs[i], As[i], ws[i], cen, wref) for i in range(n)]
+    rlo = [f32(f32(f32(-(td[a] // 2)) + f32(0.5)) * h32[a]) for a in range(D)]
+    rhi = [f32(f32(f32(td[a] - 1 - td[a] // 2) + f32(0.5)) * h32[a]) for a in range(D)]
+    lbs = [lower_bound(D, feats[i][1], feats[i][2], lam_i[i], rlo, rhi, with_slack) for i in range(n)]
+    # candidates: a random half of the seeds (the certificate must hold for any split)
+    cand = g.random(n) < 0.5
+    cand[int(np.argmin([float(v) for v in lbs]))] = True
+    texcl = min([float(lbs[i]) for i in range(n) if not cand[i]], default=np.inf)
+    bad1 = bad2 = bad3 = 0
     for _ in range(pixels):
         lk = [int(g.integers(0, td[a])) for a in range(D)]
         yp = [f32(f32(f32(lk[a] - td[a] // 2) + f32(0.5)) * h32[a]) for a in range(D)]
         f = pixel_features(D, yp)
         y = [(Fr(kb[a] + lk[a]) + Fr(1, 2)) * Fr(float(h[a])) for a in range(D)]
-        sc, ex = [], []
+        ex = [exact_cost(y, xs[i], As[i], ws[i], wref) for i in range(n)]
+        keys = []
         for i in range(n):
-            s = score(f, phis[i], rnd, order)
-            c = exact_cost(y, xs[i], As[i], ws[i], wref)
-            mag = sum(abs(float(fk) * float(pk)) for fk, pk in zip(f, phis[i]))
-            bad1 += abs(Fr(float(s)) - c) > Fr(eu * mag)
-            sc.append(float(s))
-            ex.append(c)
-        order_s = np.argsort(sc, kind="stable")
-        s3 = sc[order_s[3]]
-        eu0 = err_unit(kind)
-        c_out = abs(s3)
-        r1 = 2 * R + np.sqrt(c_out / lam)
-        psi = eu0 * (Lam * r1 * r1 + c_out)
-        c_out = abs(s3) + psi
-        r1 = 2 * R + np.sqrt(c_out / lam)
-        psi = 1.1 * eu0 * (Lam * r1 * r1 + c_out)
-        for i in order_s[3:]:
-            bad2 += ex[i] < Fr(s3 - psi)
-    return bad1, bad2
+            k = pack(score(f, feats[i][0], rnd, order, split_ops), i % 32)
+            mag = sum(abs(float(fk) * float(pk)) for fk, pk in zip(f, feats[i][0]))
+            bad1 += abs(Fr(float(k)) - ex[i]) > Fr(eu * mag)
+            bad2 += Fr(float(lbs[i])) > ex[i]
+            keys.append(float(k) if cand[i] else np.inf)
+        o = np.argsort(keys, kind="stable")
+        s1, s2 = keys[o[0]], keys[o[1]]
+        Ub = s1 + psi(s1, eu, Lam, lam, R)
+        if Ub < s2 - psi(s2, eu, Lam, lam, R) and Ub < texcl:
+            best = min(range(n), key=lambda i: (ex[i], i))
+            bad3 += best != o[0]
+    return bad1, bad2, bad3
 
 
 @pytest.mark.parametrize("D", [3, 2])
 @pytest.mark.parametrize("kind", ["tf32", "bf16"])
-def test_tensor_core_scores_within_bounds(D, kind):
-    for seed in range(6):
+def test_tensor_core_scores_bounds_and_certificate(D, kind):
+    for seed in range(4):
         for order in (0, 1):
-            assert run_case(D, kind, seed, err_unit(kind), order) == (0, 0), (seed, order)
+            assert run_case(D, kind, seed, order) == (0, 0, 0), (seed, order)
 
 
-def test_err_unit_without_operand_rounding_is_violated():
-    # planted mistake: only the FP32 part of err_unit
-    assert run_case(3, "tf32", 0, err_unit("tf32", with_operands=False), 0)[0] > 0
+def test_unsplit_operands_violate_the_bound():
+    # planted mistake: plain BF16 operands with the split form's err_unit
+    assert run_case(3, "bf16", 0, 0, split_ops=False)[0] > 0
+
+
+def test_lower_bound_with_lambda_max_is_violated():
+    # planted mistake: the largest eigenvalue in place of the smallest in the lower bound
+    viol = 0
+    for seed in range(3):
+        g, h, td, kb, cen, R, xs, As, ws, wref = make_tile(3, seed, 30)
+        h32 = [f32(v) for v in h]
+        rlo = [f32(f32(f32(-(td[a] // 2)) + f32(0.5)) * h32[a]) for a in range(3)]
+        rhi = [f32(f32(f32(td[a] - 1 - td[a] // 2) + f32(0.5)) * h32[a]) for a in range(3)]
+        for i in range(30):
+            feats, xp, wp = seed_features(3, xs[i], As[i], ws[i], cen, wref)
+            lmax = f32(np.linalg.eigvalsh(As[i]).max())
+            lb = lower_bound(3, xp, wp, lmax, rlo, rhi)
+            for _ in range(4):
+                lk = [int(g.integers(0, td[a])) for a in range(3)]
+                y = [(Fr(kb[a] + lk[a]) + Fr(1, 2)) * Fr(float(h[a])) for a in range(3)]
+                viol += Fr(float(lb)) > exact_cost(y, xs[i], As[i], ws[i], wref)
+    assert viol > 0
