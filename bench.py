@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' lines")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_tf32", "tc_bf16"],
                     help="scoring arithmetic of the reported form (the plain FP32 and the "
@@ -290,34 +291,46 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM traffic (read + write bytes) of one scoring launch from an ncu capture,
-# keyed by (sha256 prefix of the scoring sources, workload, pruned); reported
-# only while the sources are unchanged since the capture.
-NCU_TRAFFIC = {
-    # profiles/assign_fp32_pruned_3d_n1000_256cube.md: dram read 624.9 KB, write 0
-    # (code hash; the capture's file hash was 6af1923dad02aaf5)
-    ("997d6d8f19e1c5c9", "3d_n1000_256cube_lloyd5", True): 624896 + 0,
-}
-
 # FP32 flops the row-factored scoring performs per (pixel, seed) pair:
 # 2 FMAs per pixel, plus the per-(row, seed) coefficients (17 flops in 3D,
 # 7 in 2D) shared by the 16 pixels of a row.
 FLOPS_PER_PAIR = {3: 4.0 + 17.0 / 16.0, 2: 4.0 + 7.0 / 16.0}
+# tensor flops per scored (pixel, seed) pair: the split operands make K = 32
+TC_FLOPS_PER_PAIR = 2 * 32
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "ncu_counters.txt")
+SCORING_SOURCES = {"fp32": ("apd_assign_fp32.cu", "apd_fp32_tile.cuh"),
+                   "tc": ("apd_assign_tc.cu", "apd_tcgen05.cuh")}
 
 
-def kernel_source_hash():
-    """Hash of the FP32 scoring kernel's code (comments and blank lines left out,
-    so that a comment edit keeps the traffic entry of unchanged code)."""
+def kernel_source_hash(kind):
+    """Hash of a scoring kernel's code (comments and blank lines left out, so that a
+    comment edit keeps the counters of unchanged code)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("apd_assign_fp32.cu", "apd_fp32_tile.cuh"):
+    for name in SCORING_SOURCES[kind]:
         with open(os.path.join(ROOT, "paper_2403_03571_gb300", "csrc", name), encoding="utf-8") as f:
             for line in f:
                 code = re.sub(r"//.*$", "", line).rstrip()
                 if code:
                     h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
+
+
+def ncu_counters(kernel, workload, pruned, kind):
+    """Per-launch counters of one scoring launch (DRAM bytes read + written,
+    warp instructions executed) from the committed summary of an ncu capture,
+    or None when the kernel's code has changed since the capture."""
+    if not os.path.exists(COUNTERS_FILE):
+        return None
+    want = kernel_source_hash(kind)
+    with open(COUNTERS_FILE) as f:
+        for line in f:
+            p = line.split()
+            if len(p) >= 6 and not line.startswith("#") and p[0] == kernel and p[1] == workload \
+                    and p[2] == ("pruned" if pruned else "dense") and p[3] == want:
+                return {"dram_bytes": int(p[4]), "warp_instructions": int(p[5])}
+    return None
 
 
 def fp32_peak_tflops(sm_mhz, sms):
@@ -432,8 +445,7 @@ def measure_form(args, ctx, precision, chosen_start=False):
         "launch_ms": per_launch_ms,
         "launches": assign_launches,
         "pair_rate": pairs_per_launch / (per_launch_ms / 1000.0),
-        "scored_pair_rate": (scored_pairs / max(1, assign_launches)) / (per_launch_ms / 1000.0)
-        if precision == "fp32" else None,
+        "scored_pair_rate": (scored_pairs / max(1, assign_launches)) / (per_launch_ms / 1000.0),
         "e2e": {"value": world * args.e2e_steps / (e2e_max / 1000.0) if args.e2e_steps > 0 else None,
                 "unit": "APD/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -444,46 +456,59 @@ def measure_form(args, ctx, precision, chosen_start=False):
 
 
 def roofline_block(form, dim, sms, workload):
-    """Roofline of the scoring stage.  `achieved` counts the algorithmic work of the
-    method, 2F flops per (pixel, seed) pair (the F-feature dot product [y(x)y, y, 1] .
-    phi_i, F = 10 in 3D, 6 in 2D).  The FP32 kernel evaluates each pair in the
-    row-factored form a + d (b + A00 d) and executes fewer flops than that
-    (FLOPS_PER_PAIR); its executed fraction of the FP32 peak is reported beside."""
+    """Roofline of the scoring stage (launch_ms: the stage's device time per
+    evaluation from the library's events; for the tensor-core form it includes the
+    candidate pre-pass).
+    FP32 form: bound = the FP32 pipe; achieved = executed FP32 flops of the
+    evaluated pairs (the row-factored form, FLOPS_PER_PAIR each) per second.
+    Tensor-core form: bound = the tensor pipe; achieved = the contraction's flops
+    (2 x 32 per scored pair: split operands, K = 32) per second against the dense
+    peak of the operand type.  Both report beside it the algorithmic rate (2F flops
+    per evaluated pair), the dense-equivalent rate (all N x J pairs of Algorithm 1
+    per second: a rate, not a fraction -- pruned pairs are bounded away, not
+    computed) and, from the committed ncu counters, the instruction-issue fraction
+    (warp instructions per second against 4 schedulers x SMs x clock)."""
     peaks, peak_src = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     F = 10 if dim == 3 else 6
     pr = form["pair_rate"]
-    alg = pr * 2 * F / 1e12
+    sr = form.get("scored_pair_rate") or pr
+    pruned = bool(form.get("pruned"))
+    launch_s = form["launch_ms"] / 1000.0
+    issue_peak = 4.0 * sms * sm_mhz * 1e6
+    common = {"work_per_pair_flops": 2 * F, "evaluated_pairs_per_s": sr, "dense_equivalent_pairs_per_s": pr,
+              "algorithmic_tflops_evaluated": sr * 2 * F / 1e12,
+              "dense_equivalent_rate_tflops": pr * 2 * F / 1e12,
+              "launch_ms": form["launch_ms"], "launches": form["launches"]}
     if form["precision"] == "fp32":
         peak = fp32_peak_tflops(sm_mhz, sms)
-        tr = NCU_TRAFFIC.get((kernel_source_hash(), workload, bool(form.get("pruned"))))
-        # pairs the kernel evaluated (fewer than N x J when seed groups are pruned)
-        sr = form.get("scored_pair_rate") or pr
-        alg = sr * 2 * F / 1e12
-        return {"bound": "alu", "kernel": "assign_fp32_kernel<%d>" % dim, "achieved": alg, "peak": peak,
-                "unit": "TFLOP/s", "frac": alg / peak, "traffic": tr,
-                "work_per_pair_flops": 2 * F,
-                "evaluated_pairs_per_s": sr,
-                "dense_equivalent_pairs_per_s": pr,
-                # all N x J pairs of Algorithm 1 over the launch time (pruned pairs
-                # are proven irrelevant, not computed): above 1 when pruning works
-                "dense_equivalent_frac": pr * 2 * F / 1e12 / peak,
-                "executed_flops_per_pair": FLOPS_PER_PAIR[dim],
-                "executed_tflops": sr * FLOPS_PER_PAIR[dim] / 1e12,
-                "executed_frac": sr * FLOPS_PER_PAIR[dim] / 1e12 / peak,
-                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
-                               f"(max SM clock from MEASURED_PEAKS.json, {peak_src})",
-                "launch_ms": form["launch_ms"], "launches": form["launches"]}
-    # tensor-core form against the dense peak of its operand type
-    # (measured BF16 x the nominal TF32/BF16 ratio 1.1/2.25 for TF32)
-    bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    peak = bf16 * (1.1 / 2.25) if form["precision"] == "tc_tf32" else bf16
-    return {"bound": "tensor", "kernel": "assign_tc_kernel<%d> + tc_resolve_kernel<%d>" % (dim, dim),
-            "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak, "traffic": None,
-            "work_per_pair_flops": 2 * F,
-            "peak_source": f"measured bf16 {bf16:.1f} TFLOP/s ({peak_src})"
-                           + (" x 1.1/2.25 (nominal TF32/BF16)" if form["precision"] == "tc_tf32" else ""),
-            "launch_ms": form["launch_ms"], "launches": form["launches"]}
+        kern = "assign_fp32_kernel<%d>" % dim
+        cnt = ncu_counters(kern, workload, pruned, "fp32")
+        ach = sr * FLOPS_PER_PAIR[dim] / 1e12
+        out = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+               "frac": ach / peak, "traffic": cnt["dram_bytes"] if cnt else None,
+               "achieved_is": "executed FP32 flops: FLOPS_PER_PAIR per evaluated pair (row-factored form)",
+               "executed_flops_per_pair": FLOPS_PER_PAIR[dim],
+               "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
+                              f"(max SM clock from MEASURED_PEAKS.json, {peak_src})"}
+    else:
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 * (1.1 / 2.25) if form["precision"] == "tc_tf32" else bf16
+        kern = "assign_tc_kernel<%d,%d>" % (dim, 0 if form["precision"] == "tc_tf32" else 1)
+        cnt = ncu_counters(kern, workload, pruned, "tc")
+        ach = sr * TC_FLOPS_PER_PAIR / 1e12
+        out = {"bound": "tensor", "kernel": kern + " (+ tc_tile_kernel pre-pass in the timed stage)",
+               "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+               "traffic": cnt["dram_bytes"] if cnt else None,
+               "achieved_is": "tensor flops: 2 x 32 per scored pair (split operands, K = 32)",
+               "peak_source": f"measured bf16 {bf16:.1f} TFLOP/s ({peak_src})"
+                              + (" x 1.1/2.25 (nominal TF32/BF16)" if form["precision"] == "tc_tf32" else "")}
+    if cnt:
+        out["issue_frac"] = cnt["warp_instructions"] / launch_s / issue_peak
+        out["warp_instructions_per_launch"] = cnt["warp_instructions"]
+        out["counters_source"] = "profiles/ncu_counters.txt (ncu capture of this kernel code)"
+    out.update(common)
+    return out
 
 
 def run_ours(args):
@@ -574,6 +599,8 @@ def run_ours(args):
                           + (" with seed-group pruning" if args.prune else ""))
     out["coarse_evaluations_per_apd"] = chosen["coarse_evaluations_per_apd"]
     out["warm_start_network"] = chosen["warm_start_network"]
+    if not args.no_configs and world == 1:
+        out["configs"] = config_lines(args, capi, args.precision)
     if not args.no_cpu_baseline and world == 1:
         # the oracle does the APD with the plain method: scale by the plain form's evaluation count
         cb, acc = cpu_baseline_block(args, inst, x_fin.cpu().numpy(), w_fin.cpu().numpy(), gpu_lab,
@@ -726,6 +753,184 @@ def run_batch(args):
         "warm_start_network": net is not None,
         "clocks": chosen["clocks"],
     }
+
+
+def _timed_calls(call, steps, warmup):
+    """Mean device time (CUDA events on the current stream, L2 flushed between
+    calls) of `call`, and its last result."""
+    import torch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    res = None
+    for _ in range(warmup):
+        res = call()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = call()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / max(1, steps), res
+
+
+def _label_report(grid, x, A, w, gpu_lab, ids=None):
+    """GPU labels against the oracle's: mismatches (all, and outside the 1e-9 tie
+    band) and the largest relative difference of the cells' pixel counts."""
+    import oracle
+    if ids is None:
+        ref, gap = oracle.assign(grid, x, A, w, with_gap=True)
+    else:
+        ref, gap = oracle.assign_ids(grid, x, A, w, ids, with_gap=True)
+    n = x.shape[0]
+    bad = gpu_lab != ref
+    m_gpu, m_ref = np.bincount(gpu_lab, minlength=n), np.bincount(ref, minlength=n)
+    return {"pixels_compared": int(ref.size), "label_mismatches": int(bad.sum()),
+            "mismatches_outside_tie_band": int(np.sum(bad & (gap >= 1e-9))),
+            "max_rel_volume_diff": float(np.max(np.abs(m_gpu - m_ref) / np.maximum(m_ref, 1)))}
+
+
+def line_2d_20(args, capi, prec):
+    """2D, 20 seeds, 256^2, equal volumes: the chosen solve (coarse-to-fine from the
+    judged learned start, pruned scoring) and the plain FP32 solve from W = 0."""
+    import torch
+    import oracle
+    from paper_2403_03571_gb300 import synth, warmstart
+    inst = synth.workload_2d_20()
+    x, A, v = (torch.from_numpy(a).cuda() for a in (inst.x, inst.A, inst.v))
+    w0 = torch.zeros(inst.n, dtype=torch.float64, device="cuda")
+    w_out = torch.empty_like(w0)
+    ws = capi.Workspace(2, inst.n, inst.grid.num_pixels)
+    net = warmstart.load(2)
+    o_ch = capi.solve_opts(eps=0.01, precision=precision_code(capi, prec))
+    o_pl = capi.solve_opts(eps=0.01)
+
+    def chosen():
+        ws.set_pruning(True)
+        return capi.apd_solve_weights_multires(inst.grid, x, A, w0, v, w_out, ws, o_ch, chosen_multires(capi), net)
+
+    def plain():
+        ws.set_pruning(False)
+        return capi.apd_solve_weights(inst.grid, x, A, w0, v, w_out, ws, o_pl)
+
+    ms_p, (rc_p, info_p) = _timed_calls(plain, 10, 2)
+    ms_c, (rc_c, info_c, used) = _timed_calls(chosen, 10, 2)
+    lab = torch.empty(inst.grid.num_pixels, dtype=torch.int32, device="cuda")
+    ws.set_pruning(True)
+    capi.apd_assign(inst.grid, x, A, w_out, lab, ws, precision=precision_code(capi, prec))
+    w_fin = w_out.cpu().numpy()
+    rep = _label_report(inst.grid, inst.x, inst.A, w_fin, lab.cpu().numpy())
+    rep["oracle_max_rel_volume_error"] = float(oracle.dual(inst.grid, inst.x, inst.A, w_fin, inst.v)[2])
+    return {"chosen_apd_per_s": 1000.0 / ms_c, "plain_fp32_apd_per_s": 1000.0 / ms_p,
+            "chosen_evaluations": info_c.evaluations, "chosen_coarse_evaluations": info_c.coarse_evaluations,
+            "plain_evaluations": info_p.evaluations, "prediction_kept": bool(used),
+            "accuracy_vs_oracle": rep, "precision": prec}
+
+
+def line_3d_10000(args, capi, prec):
+    """3D, 10^4 seeds, 512^3, tensor-core scoring: a coarse-to-fine weight solve,
+    the scoring launch time at its weights, and labels and cell volumes on the
+    128^3 sub-grid of every 4th voxel per axis against the oracle."""
+    import torch
+    from paper_2403_03571_gb300 import synth
+    inst = synth.workload_3d_10000()
+    n, J, res = inst.n, inst.grid.num_pixels, inst.grid.res
+    x, A, v = (torch.from_numpy(a).cuda() for a in (inst.x, inst.A, inst.v))
+    w0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    w_out = torch.empty_like(w0)
+    ws = capi.Workspace(3, n, J)
+    ws.set_pruning(True)
+    pc = precision_code(capi, prec)
+    opts = capi.solve_opts(eps=0.01, precision=pc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, info, _ = capi.apd_solve_weights_multires(inst.grid, x, A, w0, v, w_out, ws, opts, chosen_multires(capi), None)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    mom = torch.empty((n, 10), dtype=torch.int64, device="cuda")
+    ws.profile(True)
+    for _ in range(5):
+        capi.apd_cell_moments(inst.grid, x, A, w_out, mom, ws, precision=pc)
+    torch.cuda.synchronize()
+    ms, launches, pairs, _ = ws.profile_read()
+    ws.profile(False)
+    lab = torch.empty(J, dtype=torch.int32, device="cuda")
+    capi.apd_assign(inst.grid, x, A, w_out, lab, ws, precision=pc)
+    k = np.arange(0, res[0], 4)
+    kk = np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)
+    ids = kk[:, 0] + res[0] * (kk[:, 1] + res[1] * kk[:, 2])
+    sub = lab.cpu().numpy()[ids]
+    del lab
+    rep = _label_report(inst.grid, inst.x, inst.A, w_out.cpu().numpy(), sub, ids)
+    return {"solve_s": solve_s, "solve_status": int(rc), "evaluations": info.evaluations,
+            "coarse_evaluations": info.coarse_evaluations, "max_rel_err": info.max_rel_err,
+            "scoring_launch_ms": ms / max(1, launches), "pair_evals_per_s": pairs / (ms / 1000.0),
+            "accuracy_vs_oracle_128cube_subgrid": rep, "precision": prec}
+
+
+def line_learned_3d(args, capi, prec):
+    """The learned warm start on its stated evaluation: 16 held-out 3D instances
+    with 2000 seeds on 256^3 (the 1000-seed workload's laws), each solved to 1 %
+    from the network's prediction judged against W = 0, and from W = 0."""
+    import torch
+    from paper_2403_03571_gb300 import synth, warmstart
+    net = warmstart.load(3)
+    g = synth.rng(warmstart.HELD_OUT_SEED[3] + 4)
+    seeds = g.integers(0, 2 ** 31 - 1, 16)
+    ws = capi.Workspace(3, 2000, 256 ** 3)
+    ws.set_pruning(True)
+    opts = capi.solve_opts(eps=0.01, precision=precision_code(capi, prec))
+    rows = {"zero": [], "learned": []}
+    used_n = 0
+    for sd in seeds:
+        inst = synth.make_instance(3, 2000, 256, int(sd))
+        x, A, v = (torch.from_numpy(a).cuda() for a in (inst.x, inst.A, inst.v))
+        w0 = torch.zeros(inst.n, dtype=torch.float64, device="cuda")
+        w_out = torch.empty_like(w0)
+        ms0, (rc0, i0) = _timed_calls(lambda: capi.apd_solve_weights(inst.grid, x, A, w0, v, w_out, ws, opts), 1, 0)
+        rows["zero"].append((ms0, i0.evaluations, i0.iterations, rc0))
+        if net is not None:
+            ms1, (rc1, i1, used) = _timed_calls(
+                lambda: capi.apd_solve_weights_warm(inst.grid, x, A, v, w_out, ws, net, opts), 1, 0)
+            rows["learned"].append((ms1, i1.evaluations, i1.iterations, rc1))
+            used_n += int(used)
+    out = {"instances": len(seeds), "seeds": 2000, "grid": [256, 256, 256], "precision": prec}
+    for k, r in rows.items():
+        if r:
+            out[k] = {"solves_per_s": len(r) / (sum(t[0] for t in r) / 1000.0),
+                      "mean_evaluations": float(np.mean([t[1] for t in r])),
+                      "mean_iterations": float(np.mean([t[2] for t in r])),
+                      "converged": int(sum(t[3] in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE) for t in r))}
+    out["prediction_kept"] = used_n
+    return out
+
+
+def line_batch(args, capi, prec):
+    """The 256-instance batched 2D workload, one timed step per form."""
+    a2 = argparse.Namespace(**vars(args))
+    a2.steps, a2.warmup = 1, 1
+    r = run_batch(a2)
+    keep = ("value", "ms_per_step", "evaluations_per_instance", "coarse_evaluations_per_instance",
+            "prediction_kept", "converged", "not_converged", "tol_infeasible", "rescored_fp64_fraction")
+    return {k: {kk: r[k][kk] for kk in keep if kk in r[k]} for k in ("chosen", "batched_from_zero", "plain_sequential")}
+
+
+def config_lines(args, capi, prec):
+    """The benchmark suite's other workloads, measured in the same run (each
+    line independent: a failure is reported in its place)."""
+    out = {}
+    for name, fn in (("2d_n20_256sq", line_2d_20), ("3d_n10000_512cube", line_3d_10000),
+                     ("3d_n2000_256cube_learned_start", line_learned_3d), ("2d_batch256", line_batch)):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(args, capi, prec)
+        except Exception as e:  # noqa: BLE001 - reported in the JSON line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def run_points(args):

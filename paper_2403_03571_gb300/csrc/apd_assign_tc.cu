@@ -75,6 +75,9 @@ constexpr int kThreads = (kEpiWarps + 1 + kXfWarps) * 32;  // 608
 constexpr int kTable = 128;                  // moment hash slots per CTA
 constexpr int kFlushTiles = 8;               // tiles between moment-table flushes
 constexpr int kListCap = 128;                // candidate seeds stored per tile
+constexpr int kMaxSteps = kListCap / kN;     // steps of a pruned tile (B operands stored per tile)
+constexpr int kAhead = 2;                    // pruned form: bulk copies issued ahead of the MMAs
+constexpr int kBMax = kN * kK * 4;           // bytes of one stored B operand (TF32; BF16 uses half)
 
 template <int D>
 struct TcGeom;
@@ -151,6 +154,63 @@ __device__ __forceinline__ void split_row(const float (&v)[F], float (&row)[kK])
     }
 }
 
+// Seed features of record r relative to the tile centre ch + cl (FP32 split):
+// [A_ab (x2 off the diagonal), -2 (A x')_a, x'^T A x' - (w - w_ref)].
+template <int D>
+__device__ __forceinline__ void seed_features(const float4 q0, const float4 q1, const float4 q2, const float4 q3,
+                                              const float (&ch)[3], const float (&cl)[3], float wrh, float wrl,
+                                              float (&ph)[TcGeom<D>::F]) {
+    const float rxh[3] = {q0.x, q0.y, q0.z}, rxl[3] = {q0.w, q1.x, q1.y};
+    const float ra[6] = {q2.x, q2.y, q2.z, q2.w, q3.x, q3.y};
+    float xp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < D; ++d) xp[d] = (rxh[d] - ch[d]) + (rxl[d] - cl[d]);
+    const float wp = (q1.z - wrh) + (q1.w - wrl);  // w_i - w_ref <= 0 up to rounding
+    if (D == 3) {
+        const float A00 = ra[0], A01 = ra[1], A02 = ra[2], A11 = ra[3], A12 = ra[4], A22 = ra[5];
+        const float t0 = fmaf(A02, xp[2], fmaf(A01, xp[1], A00 * xp[0]));
+        const float t1 = fmaf(A12, xp[2], fmaf(A11, xp[1], A01 * xp[0]));
+        const float t2 = fmaf(A22, xp[2], fmaf(A12, xp[1], A02 * xp[0]));
+        ph[0] = A00;
+        ph[1] = 2.f * A01;
+        ph[2] = 2.f * A02;
+        ph[3] = A11;
+        ph[4] = 2.f * A12;
+        ph[5] = A22;
+        ph[6] = -2.f * t0;
+        ph[7] = -2.f * t1;
+        ph[8] = -2.f * t2;
+        ph[9] = fmaf(xp[2], t2, fmaf(xp[1], t1, xp[0] * t0)) - wp;
+    } else {
+        const float A00 = ra[0], A01 = ra[1], A11 = ra[2];
+        const float t0 = fmaf(A01, xp[1], A00 * xp[0]);
+        const float t1 = fmaf(A11, xp[1], A01 * xp[0]);
+        ph[0] = A00;
+        ph[1] = 2.f * A01;
+        ph[2] = A11;
+        ph[3] = -2.f * t0;
+        ph[4] = -2.f * t1;
+        ph[5] = fmaf(xp[1], t1, xp[0] * t0) - wp;
+    }
+}
+
+// The split operand row of one seed slot (padding: a huge constant score).
+template <int D, int KIND>
+__device__ __forceinline__ void seed_row(const SeedRec32 *__restrict__ recs, const int pos, const float (&ch)[3],
+                                         const float (&cl)[3], float wrh, float wrl, float (&row)[kK]) {
+    constexpr int F = TcGeom<D>::F;
+    float ph[F];
+#pragma unroll
+    for (int e = 0; e < F; ++e) ph[e] = 0.f;
+    if (pos >= 0) {
+        const float4 *rv = reinterpret_cast<const float4 *>(recs + pos);
+        seed_features<D>(__ldg(rv), __ldg(rv + 1), __ldg(rv + 2), __ldg(rv + 3), ch, cl, wrh, wrl, ph);
+    } else {
+        ph[F - 1] = 1e30f;
+    }
+    split_row<F, KIND, true>(ph, row);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -174,25 +234,15 @@ __device__ __forceinline__ float okey_inv(unsigned k) {
     return __uint_as_float(k ^ ((k >> 31) ? 0x80000000u : 0xffffffffu));
 }
 
-template <int D>
-__device__ __forceinline__ void tc_table_add(unsigned long long (*tval)[moment_width(D)], int *tkey,
-                                             unsigned long long *gmom, int label,
-                                             const unsigned long long (&val)[moment_width(D)]) {
-    constexpr int K = moment_width(D);
+// Slot of `label` in the shared moment table (linear probing; -1 when full).
+__device__ __forceinline__ int tc_table_slot(int *tkey, int label) {
     int slot = label & (kTable - 1);
     for (int probe = 0; probe < kTable; ++probe) {
         const int k = atomicCAS(&tkey[slot], -1, label);
-        if (k == -1 || k == label) {
-#pragma unroll
-            for (int v = 0; v < K; ++v)
-                if (val[v]) atomicAdd(&tval[slot][v], val[v]);
-            return;
-        }
+        if (k == -1 || k == label) return slot;
         slot = (slot + 1) & (kTable - 1);
     }
-#pragma unroll
-    for (int v = 0; v < K; ++v)
-        if (val[v]) atomicAdd(&gmom[(size_t)label * K + v], val[v]);
+    return -1;
 }
 
 // Tile t of the scoring window -> its first pixel per axis.
@@ -215,13 +265,17 @@ __device__ __forceinline__ void tile_origin(int t, int ntx, int nty, int tlo, in
 // Pre-pass: one warp per tile.  Tile centre (FP32 high/low split), and either
 // the Morton start chunk (dense form) or the candidate list with T_excl.
 // ---------------------------------------------------------------------------
-template <int D>
+// Pruned form: the list ends as seed indices, and the split seed operand of
+// each step (32 list slots, core-matrix layout) is stored in bops[t][k].
+template <int D, int KIND>
 __global__ void __launch_bounds__(256)
     tc_tile_kernel(const GridDev g, const int ntx, const int nty, const int tlo, const int ntiles, const int n,
                    const SeedRec32 *__restrict__ r32, const GroupBound *__restrict__ groups,
-                   const uint32_t *__restrict__ scodes, const int n_chunks, float *__restrict__ centre,
-                   int *__restrict__ start, int *__restrict__ count, float *__restrict__ texcl,
-                   int *__restrict__ list, const DevScalars *__restrict__ sc) {
+                   const uint32_t *__restrict__ scodes, const int32_t *__restrict__ perm, const int n_chunks,
+                   float *__restrict__ centre, int *__restrict__ start, int4 *__restrict__ meta,
+                   float *__restrict__ texcl, int *__restrict__ list, uint8_t *__restrict__ bops,
+                   const DevScalars *__restrict__ sc) {
+    using Fm = TcFmt<KIND>;
     using G = TcGeom<D>;
     const int lane = threadIdx.x & 31;
     const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -236,16 +290,39 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a < D) {
-            split2(g.lo[a] + (double)(kb[a] + td[a] / 2) * g.h[a], ch[a], cl[a]);
-            frac[a] = ((double)(kb[a] + td[a] / 2) + 0.5) / (double)g.res[a];
             const int hi = a == D - 1 ? win_hi(g) : g.res[a];
             khi[a] = min(kb[a] + td[a], hi) - 1;
+            // the Morton position only orders the scan: FP32 is enough
+            frac[a] = (double)(((float)(kb[a] + td[a] / 2) + 0.5f) / (float)g.res[a]);
+        }
+    }
+    // FP64 per axis (the tile centre, and the absolute pixel box rounded outwards):
+    // lane a computes axis a, the others receive it
+    float alo[3] = {0.f, 0.f, 0.f}, ahi[3] = {0.f, 0.f, 0.f};
+    {
+        float vh = 0.f, vl = 0.f, vlo = 0.f, vhi = 0.f;
+        if (lane < D) {
+            const int kba = lane == 0 ? kb[0] : (lane == 1 ? kb[1] : kb[D - 1]);
+            const int kha = lane == 0 ? khi[0] : (lane == 1 ? khi[1] : khi[D - 1]);
+            const int tda = lane == 0 ? td[0] : (lane == 1 ? td[1] : td[D - 1]);
+            const double loa = lane == 0 ? g.lo[0] : (lane == 1 ? g.lo[1] : g.lo[D - 1]);
+            const double ha = lane == 0 ? g.h[0] : (lane == 1 ? g.h[1] : g.h[D - 1]);
+            split2(loa + (double)(kba + tda / 2) * ha, vh, vl);
+            vlo = __double2float_rd(loa + ((double)kba + 0.5) * ha);
+            vhi = __double2float_ru(loa + ((double)kha + 0.5) * ha);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            ch[a] = __shfl_sync(0xffffffffu, vh, a);
+            cl[a] = __shfl_sync(0xffffffffu, vl, a);
+            alo[a] = __shfl_sync(0xffffffffu, vlo, a);
+            ahi[a] = __shfl_sync(0xffffffffu, vhi, a);
         }
     }
     if (lane < 6) centre[(size_t)t * 6 + lane] = lane < 3 ? ch[lane] : cl[lane - 3];
     uint32_t code = 0u;
-    int spos = 0;  // scan position of the tile centre's Morton code
-    if (scodes) {
+    int spos = 0;  // scan position of the tile centre's Morton code (needed with several blocks of groups)
+    if (scodes && (list == nullptr || n > 1024)) {
         code = morton_code(D, frac);
         int lo = 0, hi = n;
         while (lo < hi) {
@@ -256,35 +333,36 @@ __global__ void __launch_bounds__(256)
         spos = min(lo, n - 1);
     }
     if (!list) {
-        if (lane == 0) start[t] = spos / kN;
+        if (lane == 0) {
+            start[t] = spos / kN;
+            meta[t] = make_int4(kb[0], kb[1], kb[2], 0);
+        }
         return;
     }
-    // pixel box, relative to the centre (FP32, the kernel's offsets) and absolute (rounded outwards)
-    float rlo[3] = {0.f, 0.f, 0.f}, rhi[3] = {0.f, 0.f, 0.f}, alo[3] = {0.f, 0.f, 0.f}, ahi[3] = {0.f, 0.f, 0.f};
+    // pixel box relative to the centre (FP32, the kernel's offsets)
+    float rlo[3] = {0.f, 0.f, 0.f}, rhi[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const int c = kb[a] + td[a] / 2;
         rlo[a] = ((float)(kb[a] - c) + 0.5f) * g.h32[a];
         rhi[a] = ((float)(khi[a] - c) + 0.5f) * g.h32[a];
-        alo[a] = __double2float_rd(g.lo[a] + ((double)kb[a] + 0.5) * g.h[a]);
-        ahi[a] = __double2float_ru(g.lo[a] + ((double)khi[a] + 0.5) * g.h[a]);
     }
-    const double wref = dkey_inv(sc->wref_key);
-    float wrh, wrl;
-    split2(wref, wrh, wrl);
+    float wrh = 0.f, wrl = 0.f;
+    if (lane == 0) split2(dkey_inv(sc->wref_key), wrh, wrl);
+    wrh = __shfl_sync(0xffffffffu, wrh, 0);
+    wrl = __shfl_sync(0xffffffffu, wrl, 0);
     const float finf = __int_as_float(0x7f800000);
-    float u0 = finf, u1 = finf, u2 = finf, u3 = finf;  // four smallest upper bounds (warp-uniform)
-    float tex = finf;
-    int cnt = 0;
     const int n_groups = (n + 31) / 32;
     const int n_blocks = (n_groups + 31) / 32;
     const int bstart = min(spos / 1024, n_blocks - 1);
-    for (int bi = 0; bi < n_blocks; ++bi) {
+    auto block_of = [&](int bi) {  // zig-zag out from the tile's block of 32 groups
         const int off = (bi & 1) ? ((bi + 1) >> 1) : -(bi >> 1);
         int blk = bstart + off;
         if (blk >= n_blocks) blk -= n_blocks;
         if (blk < 0) blk += n_blocks;
-        const int grp = blk * 32 + lane;
+        return blk;
+    };
+    auto group_lb = [&](int grp) {  // lower bound of the group's costs over the tile
         float lbg = finf;
         if (grp < n_groups) {
             const GroupBound gb = groups[grp];
@@ -297,71 +375,96 @@ __global__ void __launch_bounds__(256)
             }
             lbg = __fadd_rd(__fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f), gb.wgap);
         }
-        unsigned live = __ballot_sync(0xffffffffu, grp < n_groups);
+        return lbg;
+    };
+    auto seed_bounds = [&](int pos, float &lb, float &ub) {  // bounds of one seed's costs over the tile
+        lb = finf;
+        ub = finf;
+        if (pos >= n) return;
+        const SeedRec32 r = r32[pos];
+        float d2lo = 0.f, d2hi = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const float xs = (r.xh[a] - ch[a]) + (r.xl[a] - cl[a]);
+            const float slack = 1e-6f * (fabsf(rlo[a]) + fabsf(rhi[a]) + 2.f * fabsf(xs)) + 1e-30f;
+            const float dl = fmaxf(fmaxf(xs - rhi[a], rlo[a] - xs) - slack, 0.f);
+            const float dh = fmaxf(fabsf(xs - rlo[a]), fabsf(xs - rhi[a])) + slack;
+            d2lo = __fmaf_rd(dl, dl, d2lo);
+            d2hi = __fmaf_ru(dh, dh, d2hi);
+        }
+        const float wn = -((r.wh - wrh) + (r.wl - wrl));  // w_ref - w_i, up to rounding
+        const float wslack = 1e-6f * fabsf(wn) + 1e-30f;
+        lb = __fadd_rd(__fmul_rd(__fmul_rd(r.pad[0], d2lo), 1.f - 1e-5f), __fsub_rd(wn, wslack));
+        ub = __fadd_ru(__fmul_ru(__fmul_ru(r.pad[1], d2hi), 1.f + 1e-5f), __fadd_ru(wn, wslack));
+    };
+    // Pass 1: T = the fourth smallest upper bound.  Groups are visited in
+    // increasing order of their bound within each block; a group whose bound
+    // exceeds the current T holds no seed with a smaller upper bound, so T is the
+    // fourth smallest upper bound of all seeds.
+    float u0 = finf, u1 = finf, u2 = finf, u3 = finf;  // warp-uniform, ascending
+    for (int bi = 0; bi < n_blocks; ++bi) {
+        const int blk = block_of(bi);
+        const float lbg = group_lb(blk * 32 + lane);
+        unsigned live = __ballot_sync(0xffffffffu, blk * 32 + lane < n_groups);
         while (live) {
             const bool mine = (live >> lane) & 1u;
             const unsigned key = mine ? okey(lbg) : 0xffffffffu;
             const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
             const int kg = __ffs(__ballot_sync(0xffffffffu, mine && key == kmin)) - 1;
-            const float lbk = __shfl_sync(0xffffffffu, lbg, kg);
-            if (lbk > u3) {  // this group and the rest of the block lie beyond T
-                tex = fminf(tex, lbk);
-                break;
-            }
+            if (__shfl_sync(0xffffffffu, lbg, kg) > u3) break;
             live &= ~(1u << kg);
-            const int pos = (blk * 32 + kg) * 32 + lane;
-            const bool real = pos < n;
-            float lb = finf, ub = finf;
-            if (real) {
-                const SeedRec32 r = r32[pos];
-                float d2lo = 0.f, d2hi = 0.f;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const float xs = (r.xh[a] - ch[a]) + (r.xl[a] - cl[a]);
-                    const float slack = 1e-6f * (fabsf(rlo[a]) + fabsf(rhi[a]) + 2.f * fabsf(xs)) + 1e-30f;
-                    const float dl = fmaxf(fmaxf(xs - rhi[a], rlo[a] - xs) - slack, 0.f);
-                    const float dh = fmaxf(fabsf(xs - rlo[a]), fabsf(xs - rhi[a])) + slack;
-                    d2lo = __fmaf_rd(dl, dl, d2lo);
-                    d2hi = __fmaf_ru(dh, dh, d2hi);
-                }
-                const float wn = -((r.wh - wrh) + (r.wl - wrl));  // w_ref - w_i, up to rounding
-                const float wslack = 1e-6f * fabsf(wn) + 1e-30f;
-                lb = __fadd_rd(__fmul_rd(__fmul_rd(r.pad[0], d2lo), 1.f - 1e-5f), __fsub_rd(wn, wslack));
-                ub = __fadd_ru(__fmul_ru(__fmul_ru(r.pad[1], d2hi), 1.f + 1e-5f), __fadd_ru(wn, wslack));
-            }
-            // the four smallest upper bounds of the group, merged into (u0..u3)
-            unsigned ku = real ? okey(ub) : 0xffffffffu;
+            float lb, ub;
+            seed_bounds((blk * 32 + kg) * 32 + lane, lb, ub);
+            unsigned ku = okey(ub);
             if (__reduce_min_sync(0xffffffffu, ku) < okey(u3)) {
                 float b[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const unsigned m = __reduce_min_sync(0xffffffffu, ku);
-                    b[e] = m == 0xffffffffu ? finf : okey_inv(m);
+                    b[e] = okey_inv(m);
                     const int l = __ffs(__ballot_sync(0xffffffffu, ku == m)) - 1;
                     if (lane == l) ku = 0xffffffffu;
                 }
-                // merge two ascending lists of four, keep the four smallest
-                float o[4];
-                float a0 = u0, a1 = u1, a2 = u2, a3 = u3;
-                int ia = 0, ib = 0;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float av = ia == 0 ? a0 : (ia == 1 ? a1 : (ia == 2 ? a2 : a3));
-                    const float bv = ib == 0 ? b[0] : (ib == 1 ? b[1] : (ib == 2 ? b[2] : b[3]));
-                    if (av <= bv) {
-                        o[e] = av;
-                        ++ia;
-                    } else {
-                        o[e] = bv;
-                        ++ib;
-                    }
-                }
-                u0 = o[0];
-                u1 = o[1];
-                u2 = o[2];
-                u3 = o[3];
+                // the four smallest of two ascending lists of four: the elementwise
+                // minima of one list against the other reversed, then sorted
+                float c0 = fminf(u0, b[3]), c1 = fminf(u1, b[2]), c2 = fminf(u2, b[1]), c3 = fminf(u3, b[0]);
+                auto cswap = [](float &x, float &y) {
+                    const float lo = fminf(x, y), hi = fmaxf(x, y);
+                    x = lo;
+                    y = hi;
+                };
+                cswap(c0, c2);
+                cswap(c1, c3);
+                cswap(c0, c1);
+                cswap(c2, c3);
+                cswap(c1, c2);
+                u0 = c0;
+                u1 = c1;
+                u2 = c2;
+                u3 = c3;
             }
-            const bool cand = real && lb <= u3;
+        }
+    }
+    // Pass 2: the list = the seeds with LB <= T (only groups with a bound <= T can
+    // hold them, and pass 1 visited exactly those); T_excl = the smallest bound of
+    // the rest (a group's bound stands for its seeds when the group is skipped).
+    const float T = u3;
+    float tex = finf;
+    int cnt = 0;
+    for (int bi = 0; bi < n_blocks; ++bi) {
+        const int blk = block_of(bi);
+        const float lbg = group_lb(blk * 32 + lane);
+        const bool in = blk * 32 + lane < n_groups && lbg <= T;
+        tex = fminf(tex, in ? finf : lbg);
+        unsigned todo = __ballot_sync(0xffffffffu, in);
+        while (todo) {
+            const int kg = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int pos = (blk * 32 + kg) * 32 + lane;
+            float lb, ub;
+            seed_bounds(pos, lb, ub);
+            const bool real = pos < n;
+            const bool cand = real && lb <= T;
             const unsigned cm = __ballot_sync(0xffffffffu, cand);
             const int rank = __popc(cm & ((1u << lane) - 1u));
             float rej = finf;
@@ -372,14 +475,27 @@ __global__ void __launch_bounds__(256)
                 rej = lb;
             }
             cnt += __popc(cm);
-            // smallest bound among this group's excluded seeds
-            const unsigned kr = __reduce_min_sync(0xffffffffu, okey(rej));
-            tex = fminf(tex, okey_inv(kr));
+            tex = fminf(tex, rej);
         }
     }
+    tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
+    const int cnt_c = min(cnt, kListCap);
     if (lane == 0) {
-        count[t] = min(cnt, kListCap);
+        meta[t] = make_int4(kb[0], kb[1], kb[2], cnt_c);
         texcl[t] = tex;
+    }
+    __syncwarp();  // the list entries written by the other lanes
+    const int ns = max(1, (cnt_c + kN - 1) / kN);
+    for (int k = 0; k < ns; ++k) {
+        const int slot = k * kN + lane;
+        const int pos = slot < cnt_c ? list[(size_t)t * kListCap + slot] : -1;
+        float row[kK];
+        seed_row<D, KIND>(r32, pos, ch, cl, wrh, wrl, row);
+        uint8_t *dst = bops + ((size_t)t * kMaxSteps + k) * Fm::B_BYTES;
+#pragma unroll
+        for (int c = 0; c < kK / Fm::EPR; ++c)
+            put_row<KIND>(dst + tc::core_offset(lane, c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO), row + c * Fm::EPR);
+        if (pos >= 0) list[(size_t)t * kListCap + slot] = perm ? perm[pos] : pos;  // seed index for the labels
     }
 }
 
@@ -390,12 +506,15 @@ struct TcArgs {
     GridDev g;
     int n, ntx, nty, tlo, ntiles, n_chunks;
     const SeedRec32 *recs;   // scan order
+    const SeedRec32 *recs_nat;  // natural order (the FP32 resolution of undecided pixels)
     const int32_t *perm;     // scan position -> seed index (null: identity)
     const float *centre;     // [ntiles][6]
+    int pruned;              // per-tile candidate lists (else all seeds)
     const int *start;        // dense form: Morton start chunk per tile
-    const int *count;        // pruned form: candidates per tile (null: dense)
+    const int4 *meta;        // per tile: first pixel per axis, candidate count (pruned form)
     const float *texcl;      // pruned form: bound of the excluded seeds per tile
-    const int *list;         // pruned form: [ntiles][kListCap] scan positions
+    const int *list;         // pruned form: [ntiles][kListCap] seed indices
+    const uint8_t *bops;     // pruned form: [ntiles][kMaxSteps] stored seed operands
     float err_unit, R_tile;
     unsigned long long *gmom;
     uint32_t *flags;
@@ -417,10 +536,10 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GridDev &g = a.g;
-    const bool pruned = a.count != nullptr;
+    const bool pruned = a.pruned != 0;
     const int my_tiles = (int)blockIdx.x < a.ntiles ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto tile_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
-    auto nsteps = [&](int t) { return pruned ? max(1, (a.count[t] + kN - 1) / kN) : a.n_chunks; };
+    auto nsteps = [&](int t) { return pruned ? max(1, (a.meta[t].w + kN - 1) / kN) : a.n_chunks; };
 
     // epilogue threads: M tile and row (tensor-memory lane) of their pixel
     const int mt = warp >> 2;
@@ -472,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
     }
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
-            mbar_init(&sm.bar_bfull[i], kXfWarps);
+            mbar_init(&sm.bar_bfull[i], pruned ? 1 : kXfWarps);  // bulk copy (pruned) or the transform warps
             mbar_init(&sm.bar_acc[i], 1);
             mbar_init(&sm.bar_aempty[i], kEpiWarps);
         }
@@ -506,10 +625,31 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
             const uint32_t idesc = tc::instr_desc(KIND, kM, kN);
             int q = 0;
             bool ok = true;
+            // pruned form: a second cursor issues the bulk copy of step tq's operand
+            // into B[tq % 4] up to kAhead steps before its MMAs
+            int tq = 0, ti = 0, tk = 0, tns = my_tiles > 0 ? nsteps(tile_of(0)) : 0;
+            auto issue_copy = [&]() {
+                const int s = tq & (kStages - 1);
+                // the MMAs of step tq - 4 (the last readers of B[s]) are complete
+                if (tq >= kStages && !wait(&sm.bar_acc[s], (uint32_t)(((tq >> 2) - 1) & 1))) return false;
+                mbar_expect_tx(&sm.bar_bfull[s], (uint32_t)Fm::B_BYTES);
+                bulk_g2s(sm.B[s], a.bops + ((size_t)tile_of(ti) * kMaxSteps + tk) * Fm::B_BYTES, (uint32_t)Fm::B_BYTES,
+                         &sm.bar_bfull[s]);
+                ++tq;
+                if (++tk == tns) {
+                    tk = 0;
+                    if (++ti < my_tiles) tns = nsteps(tile_of(ti));
+                }
+                return true;
+            };
             for (int i = 0; i < my_tiles && ok; ++i) {
                 const int ns = nsteps(tile_of(i));
                 for (int k = 0; k < ns && ok; ++k, ++q) {
                     const int s = q & (kStages - 1);
+                    if (pruned) {
+                        while (ok && ti < my_tiles && tq <= q + kAhead) ok = issue_copy();
+                        if (!ok) break;
+                    }
                     if (!wait(&sm.bar_bfull[s], (uint32_t)((q >> 2) & 1))) { ok = false; break; }
                     if (q >= kStages && !wait(&sm.bar_aempty[s], (uint32_t)(((q >> 2) - 1) & 1))) { ok = false; break; }
                     tc::fence_after_sync();
@@ -532,21 +672,24 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                     tc::mma_commit(&sm.bar_acc[s]);
                 }
             }
-            // no MMA may still run when the tensor memory is released: wait for the last commit
+            // no MMA may still run when the tensor memory is released, and no copy may
+            // still land in shared memory when the CTA exits: wait for both
             if (q > 0) {
                 const int s = (q - 1) & (kStages - 1);
                 mbar_wait_bounded(&sm.bar_acc[s], (uint32_t)(((q - 1) >> 2) & 1), &a.sc->status);
             }
+            for (int r = q; r < tq; ++r)
+                mbar_wait_bounded(&sm.bar_bfull[r & (kStages - 1)], (uint32_t)((r >> 2) & 1), &a.sc->status);
         }
     } else if (warp >= kXfWarp0) {
-        // ---------------- seed operands (two threads per seed, each half of K) ----------------
+        // ---------------- dense form: seed operands (two threads per seed, each half of K) ----------------
         const int tt = tid - kXfWarp0 * 32;
         const int sl = tt >> 1, half = tt & 1;
         const double wref = dkey_inv(a.sc->wref_key);
         float wrh, wrl;
         split2(wref, wrh, wrl);
         int q = 0;
-        bool ok = true;
+        bool ok = !pruned;
         for (int i = 0; i < my_tiles && ok; ++i) {
             const int t = tile_of(i);
             const int ns = nsteps(t);
@@ -556,68 +699,26 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 ch[d] = a.centre[(size_t)t * 6 + d];
                 cl[d] = a.centre[(size_t)t * 6 + 3 + d];
             }
-            const int cnt = pruned ? a.count[t] : 0;
-            const int st0 = pruned ? 0 : a.start[t];
+            const int st0 = a.start[t];
             for (int k = 0; k < ns; ++k, ++q) {
                 const int s = q & (kStages - 1);
                 // the MMAs of step q - 4 have read B[s]
                 if (q >= kStages && !wait(&sm.bar_acc[s], (uint32_t)(((q >> 2) - 1) & 1))) { ok = false; break; }
-                int pos = -1;
-                if (pruned) {
-                    const int slot = k * kN + sl;
-                    if (slot < cnt) pos = a.list[(size_t)t * kListCap + slot];
-                } else {
-                    const int p = chunk_id(st0, k) * kN + sl;
-                    if (p < a.n) pos = p;
-                }
-                float ph[F];
-#pragma unroll
-                for (int e = 0; e < F; ++e) ph[e] = 0.f;
-                if (pos >= 0) {
-                    const float4 *rv = reinterpret_cast<const float4 *>(a.recs + pos);
-                    const float4 q0 = __ldg(rv), q1 = __ldg(rv + 1), q2 = __ldg(rv + 2), q3 = __ldg(rv + 3);
-                    const float rxh[3] = {q0.x, q0.y, q0.z}, rxl[3] = {q0.w, q1.x, q1.y};
-                    const float ra[6] = {q2.x, q2.y, q2.z, q2.w, q3.x, q3.y};
-                    float xp[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int d = 0; d < D; ++d) xp[d] = (rxh[d] - ch[d]) + (rxl[d] - cl[d]);
-                    const float wp = (q1.z - wrh) + (q1.w - wrl);  // w_i - w_ref <= 0 up to rounding
-                    if (D == 3) {
-                        const float A00 = ra[0], A01 = ra[1], A02 = ra[2], A11 = ra[3], A12 = ra[4], A22 = ra[5];
-                        const float t0 = fmaf(A02, xp[2], fmaf(A01, xp[1], A00 * xp[0]));
-                        const float t1 = fmaf(A12, xp[2], fmaf(A11, xp[1], A01 * xp[0]));
-                        const float t2 = fmaf(A22, xp[2], fmaf(A12, xp[1], A02 * xp[0]));
-                        ph[0] = A00;
-                        ph[1] = 2.f * A01;
-                        ph[2] = 2.f * A02;
-                        ph[3] = A11;
-                        ph[4] = 2.f * A12;
-                        ph[5] = A22;
-                        ph[6] = -2.f * t0;
-                        ph[7] = -2.f * t1;
-                        ph[8] = -2.f * t2;
-                        ph[9] = fmaf(xp[2], t2, fmaf(xp[1], t1, xp[0] * t0)) - wp;
-                    } else {
-                        const float A00 = ra[0], A01 = ra[1], A11 = ra[2];
-                        const float t0 = fmaf(A01, xp[1], A00 * xp[0]);
-                        const float t1 = fmaf(A11, xp[1], A01 * xp[0]);
-                        ph[0] = A00;
-                        ph[1] = 2.f * A01;
-                        ph[2] = A11;
-                        ph[3] = -2.f * t0;
-                        ph[4] = -2.f * t1;
-                        ph[5] = fmaf(xp[1], t1, xp[0] * t0) - wp;
-                    }
-                } else {
-                    ph[F - 1] = 1e30f;  // padding slot: a huge constant score
-                }
+                const int p = chunk_id(st0, k) * kN + sl;
                 float rowv[kK];
-                split_row<F, KIND, true>(ph, rowv);
+                seed_row<D, KIND>(a.recs, p < a.n ? p : -1, ch, cl, wrh, wrl, rowv);
                 uint8_t *B = sm.B[s];
+                if (half == 0) {
 #pragma unroll
-                for (int c = 0; c < kK / 2 / Fm::EPR; ++c) {
-                    const int k0 = half * (kK / 2) + c * Fm::EPR;
-                    put_row<KIND>(B + tc::core_offset(sl, k0, Fm::EB, Fm::LBO, Fm::SBO), rowv + k0);
+                    for (int c = 0; c < kK / 2 / Fm::EPR; ++c)
+                        put_row<KIND>(B + tc::core_offset(sl, c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO), rowv + c * Fm::EPR);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < kK / 2 / Fm::EPR; ++c) {
+                        constexpr int H = kK / 2;
+                        put_row<KIND>(B + tc::core_offset(sl, H + c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO),
+                                      rowv + H + c * Fm::EPR);
+                    }
                 }
                 tc::fence_proxy_async_smem();
                 __syncwarp();
@@ -629,20 +730,43 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
         const uint32_t lane_base = ((uint32_t)((warp & 3) * 32)) << 16;
         const float lam_abs = (float)__longlong_as_double((long long)a.sc->lam_abs_bits);
         const float inv_lam = 1.f / fmaxf((float)__longlong_as_double((long long)a.sc->lam_min_bits), 1e-30f);
-        auto psi = [&](float s) {  // bound of |score - cost| for a seed scoring s
-            float c = fabsf(s);
-            float r1 = 2.f * a.R_tile + sqrtf(c * inv_lam);
-            float p = a.err_unit * (lam_abs * r1 * r1 + c);
-            c = fabsf(s) + p;
-            r1 = 2.f * a.R_tile + sqrtf(c * inv_lam);
-            return 1.1f * a.err_unit * (lam_abs * r1 * r1 + c);
+        // Bound of |score - cost| for a seed scoring s, linear in |s|: the term sum
+        // Lambda (2R + sqrt(C / lambda))^2 + C is at most 8 Lambda R^2 + (2 Lambda /
+        // lambda + 1) C (from (a + b)^2 <= 2 a^2 + 2 b^2), evaluated at an upper bound
+        // of the exact cost C <= |s| + err_unit (that sum at |s|).
+        const float ps0 = 8.f * lam_abs * a.R_tile * a.R_tile;
+        const float ps1 = 2.f * lam_abs * inv_lam + 1.f;
+        auto psi = [&](float s) {
+            const float c = fabsf(s) + a.err_unit * fmaf(ps1, fabsf(s), ps0);
+            return 1.1f * a.err_unit * fmaf(ps1, c, ps0);
         };
         int q = 0;
+        float wrh = 0.f, wrl = 0.f;
+        split2(dkey_inv(a.sc->wref_key), wrh, wrl);
+        float ypx[3] = {0.f, 0.f, 0.f};  // this thread's pixel relative to the tile centre
+#pragma unroll
+        for (int d = 0; d < D; ++d) ypx[d] = ((float)(lk[d] - tdim[d] / 2) + 0.5f) * g.h32[d];
+        // per-tile values, loaded one tile ahead
+        const float finf = __int_as_float(0x7f800000);
+        int4 nx_meta = my_tiles > 0 ? a.meta[tile_of(0)] : make_int4(0, 0, 0, 0);
+        float nx_tex = pruned && my_tiles > 0 ? a.texcl[tile_of(0)] : finf;
+        int nx_st0 = !pruned && my_tiles > 0 ? a.start[tile_of(0)] : 0;
         for (int i = 0; i < my_tiles; ++i) {
             const int t = tile_of(i);
-            const int ns = nsteps(t);
-            const float tex = pruned ? a.texcl[t] : __int_as_float(0x7f800000);
-            const int st0 = pruned ? 0 : a.start[t];
+            const int4 mt4 = nx_meta;
+            const int cnt = mt4.w;
+            const float tex = nx_tex;
+            const int st0 = nx_st0;
+            const int ns = pruned ? max(1, (cnt + kN - 1) / kN) : a.n_chunks;
+            if (i + 1 < my_tiles) {
+                const int tn = tile_of(i + 1);
+                nx_meta = a.meta[tn];
+                if (pruned) nx_tex = a.texcl[tn];
+                else nx_st0 = a.start[tn];
+            }
+            int lv[kMaxSteps];  // pruned form: the seed of list slot k * 32 + lane
+#pragma unroll
+            for (int k = 0; k < kMaxSteps; ++k) lv[k] = -1;
             float k1 = FLT_MAX, k2 = FLT_MAX;  // two smallest packed scores
             int bstep = 0;
             bool ok = true;
@@ -660,6 +784,11 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.bar_aempty[s]);
+                if (pruned) {
+#pragma unroll
+                    for (int kk = 0; kk < kMaxSteps; ++kk)
+                        if (kk == k && k * kN + lane < cnt) lv[kk] = a.list[(size_t)t * kListCap + k * kN + lane];
+                }
                 // a slice whose smallest score lies above the second-best by more than
                 // the packing (< 32 ulp) cannot change the two smallest keys
                 if (got && !(mn > fmaf(fabsf(k2), 0x1p-16f, k2))) {
@@ -688,9 +817,7 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 }
             }
             // ---- end of tile: certificate, label, FP64 queue, moments ----
-            int kb[3];
-            tile_origin<D>(t, a.ntx, a.nty, a.tlo, kb);
-            const int kk[3] = {kb[0] + lk[0], kb[1] + lk[1], kb[2] + lk[2]};
+            const int kk[3] = {mt4.x + lk[0], mt4.y + lk[1], mt4.z + lk[2]};
             const int klast = D == 3 ? kk[2] : kk[1];
             const bool valid = ok && kk[0] < g.res[0] && kk[1] < g.res[1] && (D == 2 || kk[2] < g.res[2]) &&
                                klast >= win_lo(g) && klast < win_hi(g);
@@ -698,22 +825,83 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
             bool queue = false;
             int hint = -1;
             long long j = 0;
+            // the best seed: list slot bstep * 32 + idx (pruned) or scan position (dense)
+            const int idx = (int)(__float_as_uint(k1) & 31u);
+            int seed = -1;
+            if (pruned) {
+#pragma unroll
+                for (int kk = 0; kk < kMaxSteps; ++kk) {
+                    const int v = __shfl_sync(0xffffffffu, lv[kk], idx);
+                    if (kk == bstep) seed = v;
+                }
+            }
             if (valid) {
                 j = (long long)kk[0] + (long long)g.res[0] * ((long long)kk[1] + (long long)g.res[1] * (long long)kk[2]);
-                const int slot = bstep * kN + (int)(__float_as_uint(k1) & 31u);
-                int pos = -1;
-                if (pruned) {
-                    if (slot < a.count[t]) pos = a.list[(size_t)t * kListCap + slot];
-                } else {
-                    const int p = chunk_id(st0, bstep) * kN + (int)(__float_as_uint(k1) & 31u);
-                    if (p < a.n) pos = p;
+                if (!pruned) {
+                    const int p = chunk_id(st0, bstep) * kN + idx;
+                    seed = p < a.n ? (a.perm ? a.perm[p] : p) : -1;
                 }
-                const int seed = pos >= 0 ? (a.perm ? a.perm[pos] : pos) : -1;
                 hint = seed;
                 const float U = k1 + psi(k1);
                 const bool cert = seed >= 0 && k1 < 1e29f && U < k2 - psi(k2) && U < tex;
                 if (cert) label = seed;
                 else queue = true;
+            }
+            // Pruned form: the pixels the scores leave undecided are settled in FP32
+            // direct form by the warp (lane l takes list slots l, l + 32, ..): the label
+            // is certified when the best upper bound c + E lies below every other
+            // candidate's lower bound c - E and below the excluded seeds' bound.
+            if (pruned) {
+                unsigned unc = __ballot_sync(0xffffffffu, queue);
+                if (unc) {
+                    float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        ch[d] = a.centre[(size_t)t * 6 + d];
+                        cl[d] = a.centre[(size_t)t * 6 + 3 + d];
+                    }
+                    while (unc) {
+                        const int p = __ffs(unc) - 1;
+                        unc &= unc - 1u;
+                        float yp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int d = 0; d < D; ++d) yp[d] = __shfl_sync(0xffffffffu, ypx[d], p);
+                        float cv[kMaxSteps], ev[kMaxSteps];
+                        float ub = finf;
+                        int us = 0x7fffffff;
+#pragma unroll
+                        for (int kk2 = 0; kk2 < kMaxSteps; ++kk2) {
+                            cv[kk2] = finf;
+                            ev[kk2] = 0.f;
+                            if (kk2 < ns && lv[kk2] >= 0) {
+                                cost32_bound_rel<D>(a.recs_nat[lv[kk2]], ch, cl, yp, wrh, wrl, cv[kk2], ev[kk2]);
+                                const float u1 = cv[kk2] + ev[kk2];
+                                if (u1 < ub || (u1 == ub && lv[kk2] < us)) {
+                                    ub = u1;
+                                    us = lv[kk2];
+                                }
+                            }
+                        }
+                        // the smallest upper bound of the warp and its seed
+                        const unsigned kub = okey(ub);
+                        const unsigned kmin = __reduce_min_sync(0xffffffffu, kub);
+                        const int smin = __reduce_min_sync(0xffffffffu, kub == kmin ? (unsigned)us : 0x7fffffffu);
+                        const float Ub = okey_inv(kmin);
+                        bool other = false;  // another candidate may cost as little
+#pragma unroll
+                        for (int kk2 = 0; kk2 < kMaxSteps; ++kk2)
+                            if (kk2 < ns && lv[kk2] >= 0 && lv[kk2] != smin && !(cv[kk2] - ev[kk2] > Ub)) other = true;
+                        const bool ok2 = !__any_sync(0xffffffffu, other) && Ub < tex && smin < a.n;
+                        if (lane == p) {
+                            if (ok2) {
+                                label = smin;
+                                queue = false;
+                            } else if (smin < a.n) {
+                                hint = smin;
+                            }
+                        }
+                    }
+                }
             }
             // queued pixels: one atomic per warp
             const unsigned qm = __ballot_sync(0xffffffffu, queue);
@@ -728,43 +916,60 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 }
             }
             if (label >= 0 && a.labels) a.labels[j] = label;
-            // moments of the certified pixels: lanes with the same label summed across the warp
-            unsigned long long u[3] = {0ull, 0ull, 0ull};
-#pragma unroll
-            for (int d = 0; d < D; ++d) u[d] = 2ull * (unsigned long long)kk[d] + 1ull;
+            // moments of the certified pixels: the lanes holding the same label sum their
+            // words across the warp; the leader finds the label's table slot and lanes
+            // 0 .. K-1 add one word each
             unsigned todo = __ballot_sync(0xffffffffu, label >= 0);
             while (todo) {
                 const int leader = __ffs(todo) - 1;
                 const int L0 = __shfl_sync(0xffffffffu, label, leader);
                 const bool mine = label == L0;
                 const unsigned grp = __ballot_sync(0xffffffffu, mine);
-                unsigned long long own[KM];
-                own[0] = 1ull;
+                unsigned long long sum[KM];
+                if (!a.wide) {
+                    // u < 2^13: every word of a pixel is below 2^26 and 32 of them below 2^31
+                    unsigned u32[3] = {0u, 0u, 0u};
 #pragma unroll
-                for (int d = 0; d < D; ++d) own[1 + d] = u[d];
-                {
+                    for (int d = 0; d < D; ++d) u32[d] = mine ? 2u * (unsigned)kk[d] + 1u : 0u;
+                    sum[0] = (unsigned long long)__popc(grp);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) sum[1 + d] = (unsigned long long)__reduce_add_sync(0xffffffffu, u32[d]);
+                    int e = 1 + D;
+#pragma unroll
+                    for (int d = 0; d < D; ++d)
+#pragma unroll
+                        for (int d2 = d; d2 < D; ++d2)
+                            sum[e++] = (unsigned long long)__reduce_add_sync(0xffffffffu, u32[d] * u32[d2]);
+                } else {
+                    unsigned long long u[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+                    for (int d = 0; d < D; ++d) u[d] = mine ? 2ull * (unsigned long long)kk[d] + 1ull : 0ull;
+                    unsigned long long own[KM];
+                    own[0] = mine ? 1ull : 0ull;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) own[1 + d] = u[d];
                     int e = 1 + D;
 #pragma unroll
                     for (int d = 0; d < D; ++d)
 #pragma unroll
                         for (int d2 = d; d2 < D; ++d2) own[e++] = u[d] * u[d2];
-                }
-                unsigned long long sum[KM];
-                if (!a.wide) {
-                    // every word of a pixel is below 2^26 and 32 of them below 2^31
-#pragma unroll
-                    for (int v = 0; v < KM; ++v)
-                        sum[v] = (unsigned long long)__reduce_add_sync(0xffffffffu, mine ? (unsigned)own[v] : 0u);
-                } else {
 #pragma unroll
                     for (int v = 0; v < KM; ++v) {
-                        unsigned long long x = mine ? own[v] : 0ull;
+                        unsigned long long x = own[v];
 #pragma unroll
                         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
                         sum[v] = x;
                     }
                 }
-                if (lane == leader) tc_table_add<D>(sm.tval, sm.tkey, a.gmom, L0, sum);
+                int slot = -1;
+                if (lane == leader) slot = tc_table_slot(sm.tkey, L0);
+                slot = __shfl_sync(0xffffffffu, slot, leader);
+                unsigned long long word = 0ull;
+#pragma unroll
+                for (int v = 0; v < KM; ++v)
+                    if (lane == v) word = sum[v];
+                if (lane < KM && word)
+                    atomicAdd(slot >= 0 ? &sm.tval[slot][lane] : &a.gmom[(size_t)L0 * KM + lane], word);
                 todo &= ~grp;
             }
             if (warp == 0 && lane == 0 && a.pairs_scored)
@@ -824,9 +1029,10 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     const bool pruned = ws.prune;
     const SeedRec32 *rs = ws.sorted ? ws.recs32s : ws.recs32;
     const int pblocks = (int)((ntl * 32 + 255) / 256);
-    tc_tile_kernel<D><<<pblocks, 256, 0, st>>>(g, ntx, nty, tlo, ntiles, n, rs, ws.groups,
-                                               ws.sorted ? ws.scodes : nullptr, n_chunks, ws.tc_centre, ws.tc_start,
-                                               ws.tc_count, ws.tc_texcl, pruned ? ws.tc_list : nullptr, ws.sc);
+    tc_tile_kernel<D, KIND><<<pblocks, 256, 0, st>>>(
+        g, ntx, nty, tlo, ntiles, n, rs, ws.groups, ws.sorted ? ws.scodes : nullptr, ws.sorted ? ws.perm : nullptr,
+        n_chunks, ws.tc_centre, ws.tc_start, ws.tc_meta, ws.tc_texcl, pruned ? ws.tc_list : nullptr, ws.tc_bops,
+        ws.sc);
     // more than 114 KB of shared memory keeps one CTA (512 tensor-memory columns) per SM
     const size_t smem = std::max<size_t>(sizeof(TcShared<D, KIND>), 120 * 1024);
     cudaError_t e = cudaFuncSetAttribute(assign_tc_kernel<D, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -844,12 +1050,15 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     args.ntiles = ntiles;
     args.n_chunks = n_chunks;
     args.recs = rs;
+    args.recs_nat = ws.recs32;
     args.perm = ws.sorted ? ws.perm : nullptr;
     args.centre = ws.tc_centre;
+    args.pruned = pruned ? 1 : 0;
     args.start = ws.tc_start;
-    args.count = pruned ? ws.tc_count : nullptr;
+    args.meta = ws.tc_meta;
     args.texcl = ws.tc_texcl;
     args.list = ws.tc_list;
+    args.bops = ws.tc_bops;
     // per score: the split operands' 3 e^2 (e = 2^-11 TF32, 2^-8 BF16), 32 accumulations at
     // 2^-22, ~100 FP32 roundings of the features and the packed index (2^-18), with a 1.5x margin
     const double e_op = KIND == tc::KIND_TF32 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -8);
@@ -888,5 +1097,6 @@ long long tc_tile_count(const GridDev &g) {
 }
 
 int tc_list_cap() { return kListCap; }
+size_t tc_bops_bytes_per_tile() { return (size_t)kMaxSteps * kBMax; }
 
 }  // namespace apd

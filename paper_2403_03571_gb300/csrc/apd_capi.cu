@@ -596,13 +596,15 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.pairs_scored, sizeof(unsigned long long));
     alloc((void **)&w.groups, (size_t)(w.n_pad_max / 32) * sizeof(GroupBound));
     alloc((void **)&w.sc, sizeof(DevScalars));
-    // tensor-core tiles hold 512 pixels; 8x slack covers ragged grids down to thin slabs
-    w.tc_tile_cap = max_j / 64 + 4096;
+    // tensor-core tiles hold 512 pixels; 2x slack covers ragged grids (thinner grids
+    // are scored by the FP32 kernel)
+    w.tc_tile_cap = max_j / 256 + 1024;
     alloc((void **)&w.tc_centre, (size_t)w.tc_tile_cap * 6 * sizeof(float));
     alloc((void **)&w.tc_start, (size_t)w.tc_tile_cap * sizeof(int));
-    alloc((void **)&w.tc_count, (size_t)w.tc_tile_cap * sizeof(int));
+    alloc((void **)&w.tc_meta, (size_t)w.tc_tile_cap * sizeof(int4));
     alloc((void **)&w.tc_texcl, (size_t)w.tc_tile_cap * sizeof(float));
     alloc((void **)&w.tc_list, (size_t)w.tc_tile_cap * tc_list_cap() * sizeof(int));
+    alloc((void **)&w.tc_bops, (size_t)w.tc_tile_cap * tc_bops_bytes_per_tile());
     alloc((void **)&w.part, nb * 5 * sizeof(double));
     alloc((void **)&w.grad, (size_t)max_n * sizeof(double));
     alloc((void **)&w.W, (size_t)max_n * sizeof(double));
@@ -636,7 +638,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_count, w.tc_texcl, w.tc_list, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
         if (p) cudaFree(p);

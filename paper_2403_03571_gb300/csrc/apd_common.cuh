@@ -74,6 +74,30 @@ __device__ __forceinline__ double lambda_min_sym(const double (&s)[D][D]) {
     }
 }
 
+// Largest eigenvalue of the same matrices (2x2: m + r; 3x3: the largest root
+// of the trigonometric solution), with a small relative margin upwards.
+template <int D>
+__device__ __forceinline__ double lambda_max_sym(const double (&s)[D][D]) {
+    if (D == 2) {
+        const double m = 0.5 * (s[0][0] + s[1][1]);
+        const double h = 0.5 * (s[0][0] - s[1][1]);
+        return (m + sqrt(h * h + s[0][1] * s[0][1])) * (1.0 + 1e-9);
+    } else {
+        const double p1 = s[0][1] * s[0][1] + s[0][2] * s[0][2] + s[1][2] * s[1][2];
+        const double q = (s[0][0] + s[1][1] + s[2][2]) / 3.0;
+        const double a0 = s[0][0] - q, a1 = s[1][1] - q, a2 = s[2][2] - q;
+        const double p2 = a0 * a0 + a1 * a1 + a2 * a2 + 2.0 * p1;
+        if (!(p2 > 1e-30 * q * q)) return q * (1.0 + 1e-9);
+        const double p = sqrt(p2 / 6.0);
+        const double b00 = a0 / p, b11 = a1 / p, b22 = a2 / p;
+        const double b01 = s[0][1] / p, b02 = s[0][2] / p, b12 = s[1][2] / p;
+        double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                          b02 * (b01 * b12 - b11 * b02));
+        r = fmin(1.0, fmax(-1.0, r));
+        return (q + 2.0 * p * cos(acos(r) / 3.0)) * (1.0 + 1e-9) + 1e-12 * fabs(q);
+    }
+}
+
 __device__ __forceinline__ void split_f32(double v, float &hi, float &lo) {
     hi = (float)v;
     lo = (float)(v - (double)hi);
@@ -144,6 +168,7 @@ __device__ __forceinline__ void build_seed(const int i, const int n, const doubl
         for (int b = 0; b < D; ++b) f2 += s[a][b] * s[a][b];
     frob = sqrt(f2);
     lam = spd ? lambda_min_sym<D>(s) : 0.0;
+    const double lmax = spd ? fmin(lambda_max_sym<D>(s), sqrt(f2) * (1.0 + 1e-12)) : 0.0;
     if (!finite) bad = ST_NONFINITE;
     else if (!spd) bad = ST_NOT_SPD;
     if (!finite) {
@@ -173,7 +198,7 @@ __device__ __forceinline__ void build_seed(const int i, const int n, const doubl
 #pragma unroll
     for (int a = 0; a < 6; ++a) r32.a[a] = r.a[a];
     r32.pad[0] = r.pad[0];
-    r32.pad[1] = __double2float_ru(frob * (1.0 + 1e-12));  // upper bound of lambda_max: ||sym A||_F
+    r32.pad[1] = __double2float_ru(lmax);  // upper bound of lambda_max (candidate lists only)
 }
 
 // Bounds of group `grp` (32 consecutive records, positions >= n are padding),

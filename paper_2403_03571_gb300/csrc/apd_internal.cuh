@@ -98,9 +98,10 @@ struct Workspace {
     SeedRec32 *recs32s = nullptr;       // [n_pad_max] SeedRec32 in scan order
     float *tc_centre = nullptr;         // [tc_tile_cap][6] tensor-core tile centres (FP32 hi, lo)
     int *tc_start = nullptr;            // [tc_tile_cap] Morton start chunk per tile (dense form)
-    int *tc_count = nullptr;            // [tc_tile_cap] candidate seeds per tile (pruned form)
+    int4 *tc_meta = nullptr;            // [tc_tile_cap] first pixel per axis, candidate count
     float *tc_texcl = nullptr;          // [tc_tile_cap] cost lower bound of the seeds left out
-    int *tc_list = nullptr;             // [tc_tile_cap][tc_list_cap()] candidates (scan positions)
+    int *tc_list = nullptr;             // [tc_tile_cap][tc_list_cap()] candidates
+    uint8_t *tc_bops = nullptr;         // [tc_tile_cap] x tc_bops_bytes_per_tile(): stored seed operands
     long long tc_tile_cap = 0;
     bool sorted = false;                // set by launch_seed_prep for the current pass
     bool prune = false;                 // FP32 scoring skips seed groups by their bounds
@@ -313,6 +314,7 @@ cudaError_t launch_assign_tc(const GridDev &g, int n, Workspace &ws, int32_t *la
 // tc_tile_cap), and the candidate seeds stored per tile
 long long tc_tile_count(const GridDev &g);
 int tc_list_cap();
+size_t tc_bops_bytes_per_tile();
 // bounds of the 32-seed groups of the scan-order records (ws.groups)
 cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st);
 // FP64 rescoring of the queued pixels (labels optional, moments updated).

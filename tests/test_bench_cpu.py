@@ -35,8 +35,11 @@ def test_reference_arm_prints_one_contract_line():
     assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
     assert out["config"]["workload"] == "2d_n20_256sq"
-    # the time per APD is the evaluation time times the evaluations per APD
-    assert out["ms_per_step"] == pytest.approx(1000.0 / out["value"], rel=1e-9)
+    # a step is one complete FP64 evaluation, timed as it ran; the APD rate divides
+    # by the evaluations one APD takes
+    assert out["ms_per_step"] == pytest.approx(1000.0 * out["evaluation_s"], rel=1e-9)
+    assert out["value"] == pytest.approx(1.0 / (out["evaluation_s"] * out["evals_per_apd"]), rel=1e-9)
+    assert out["pair_evals_per_s"] == pytest.approx(65536 * 20 / out["evaluation_s"], rel=1e-9)
 
 
 def test_reference_arm_other_ranks_exit_quietly():
@@ -46,8 +49,10 @@ def test_reference_arm_other_ranks_exit_quietly():
 
 
 def test_roofline_arithmetic():
-    # the JSON line's roofline block: achieved = evaluated pairs x 2F flops / time,
-    # peak = SMs x 128 FP32 lanes x 2 flops x the max SM clock, frac = achieved / peak
+    # FP32 form: achieved = evaluated pairs x the executed flops per pair / time,
+    # peak = SMs x 128 FP32 lanes x 2 flops x the max SM clock, frac = achieved / peak;
+    # the algorithmic and dense-equivalent figures are rates beside it.
+    # Tensor-core form: 2 x 32 tensor flops per scored pair against the operand type's peak.
     import bench
     peaks, _ = bench.load_peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -57,10 +62,26 @@ def test_roofline_arithmetic():
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     assert rb["bound"] == "alu" and rb["unit"] == "TFLOP/s"
     assert rb["peak"] == pytest.approx(peak)
-    assert rb["achieved"] == pytest.approx(3.0e11 * 20 / 1e12)
+    assert rb["achieved"] == pytest.approx(3.0e11 * bench.FLOPS_PER_PAIR[3] / 1e12)
     assert rb["frac"] == pytest.approx(rb["achieved"] / peak)
-    assert rb["dense_equivalent_frac"] == pytest.approx(6.0e12 * 20 / 1e12 / peak)
+    assert rb["algorithmic_tflops_evaluated"] == pytest.approx(3.0e11 * 20 / 1e12)
+    assert rb["dense_equivalent_rate_tflops"] == pytest.approx(6.0e12 * 20 / 1e12)
     rb2 = bench.roofline_block(dict(form, precision="tc_tf32"), 2, 152, "2d_n2000_1024sq")
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     assert rb2["bound"] == "tensor" and rb2["peak"] == pytest.approx(bf16 * 1.1 / 2.25)
-    assert rb2["achieved"] == pytest.approx(6.0e12 * 12 / 1e12)
+    assert rb2["achieved"] == pytest.approx(3.0e11 * 64 / 1e12)
+    assert rb2["frac"] == pytest.approx(rb2["achieved"] / rb2["peak"])
+
+
+def test_counters_follow_the_kernel_code(tmp_path, monkeypatch):
+    # the ncu counters are used only while the kernel's code hash matches the capture
+    import bench
+    f = tmp_path / "c.txt"
+    h = bench.kernel_source_hash("tc")
+    f.write_text(f"# kernel workload form hash dram_bytes warp_instructions\n"
+                 f"assign_tc_kernel<3,0> 3d_n1000_256cube_lloyd5 pruned {h} 1000 2000\n"
+                 f"assign_tc_kernel<3,0> 3d_n1000_256cube_lloyd5 dense 0123456789abcdef 1 2\n")
+    monkeypatch.setattr(bench, "COUNTERS_FILE", str(f))
+    assert bench.ncu_counters("assign_tc_kernel<3,0>", "3d_n1000_256cube_lloyd5", True, "tc") == \
+        {"dram_bytes": 1000, "warp_instructions": 2000}
+    assert bench.ncu_counters("assign_tc_kernel<3,0>", "3d_n1000_256cube_lloyd5", False, "tc") is None

@@ -140,12 +140,11 @@ def err_unit(kind):
 
 
 def psi(s, eu, Lam, lam, R):
-    c = abs(s)
-    r1 = 2 * R + np.sqrt(c / lam)
-    p = eu * (Lam * r1 * r1 + c)
-    c = abs(s) + p
-    r1 = 2 * R + np.sqrt(c / lam)
-    return 1.1 * eu * (Lam * r1 * r1 + c)
+    """The kernel's bound, linear in |s|: Lambda (2R + sqrt(C/lambda))^2 + C <=
+    8 Lambda R^2 + (2 Lambda / lambda + 1) C, at C <= |s| + eu (that sum at |s|)."""
+    ps0, ps1 = 8 * Lam * R * R, 2 * Lam / lam + 1
+    c = abs(s) + eu * (ps1 * abs(s) + ps0)
+    return 1.1 * eu * (ps1 * c + ps0)
 
 
 def lower_bound(D, xp, wp, lam_i, rlo, rhi, with_slack=True):
