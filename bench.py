@@ -57,9 +57,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' lines")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_tf32", "tc_bf16"],
-                    help="scoring arithmetic of the reported form (the plain FP32 and the "
-                         "tensor-core TF32 forms are always timed too)")
+    ap.add_argument("--precision", default="tc_tf32", choices=["fp32", "tc_tf32", "tc_bf16"],
+                    help="scoring arithmetic of the chosen form (the same pipeline with the other "
+                         "arithmetic, and the plain FP32 form, are always timed too)")
+    ap.add_argument("--assign-res", type=int, default=0,
+                    help="--mode assign: grid resolution per axis in place of the workload's")
     ap.add_argument("--assign-prune", action="store_true",
                     help="--mode assign: score with seed-group pruning")
     ap.add_argument("--no-prune", dest="prune", action="store_false",
@@ -76,9 +78,12 @@ def parse():
     ap.add_argument("--sweep-alpha", default="0,0.3,0.7")
     ap.add_argument("--sweep-n2", default="25,50,100,250,500,1000,2500,5000")
     ap.add_argument("--sweep-n3", default="50,100,250,500,1000,2500,5000,10000")
-    ap.add_argument("--sweep-n3-b", default="50,100,250,500,1000,2500",
-                    help="sweep: 3D seed counts of test (b) (the largest solves take minutes)")
-    ap.add_argument("--sweep-runs", type=int, default=1, help="sweep: random instances per point")
+    ap.add_argument("--sweep-n3-b", default="50,100,250,500,1000,2500,5000,10000",
+                    help="sweep: 3D seed counts of test (b)")
+    ap.add_argument("--sweep-runs", type=int, default=10,
+                    help="sweep: random instances per point (the paper averages ten)")
+    ap.add_argument("--sweep-point-budget", type=float, default=30.0,
+                    help="sweep: no further runs of a point once it has taken this many seconds")
     ap.add_argument("--sweep-m-cap", default="4096,384", help="sweep: largest M in 2D, 3D (eq. (2.10) otherwise)")
     ap.add_argument("--sweep-max-evals", type=int, default=400, help="sweep: evaluation cap of the test (b) solves")
     return ap.parse_args()
@@ -213,7 +218,7 @@ def run_reference(args, evals_per_apd):
         "impl": "reference", "metric": metric_name(args.workload), "value": val, "unit": "APD/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t_eval, "step": "one complete FP64 evaluation of the dual",
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(args.workload, inst, rounds, args.precision),
         "pair_evals_per_s": pairs / t_eval, "evaluation_s": t_eval, "evals_per_apd": evals_per_apd,
         "cpu_baseline": {"value": val, "unit": "APD/s", "cores": cores, "kind": "oracle", "sample": sample},
@@ -435,7 +440,7 @@ def measure_form(args, ctx, precision, chosen_start=False):
     per_launch_ms = assign_ms / max(1, assign_launches)
     pairs_per_launch = assign_pairs / max(1, assign_launches)
     return {
-        "value": world * args.steps / (max_ms / 1000.0),
+        "value": args.steps / (max_ms / 1000.0),
         "ms_per_step": max_ms / args.steps,
         "coarse_evaluations_per_apd": statistics.mean([i.coarse_evaluations for i in infos]),
         "warm_start_network": bool(net is not None),
@@ -446,7 +451,7 @@ def measure_form(args, ctx, precision, chosen_start=False):
         "launches": assign_launches,
         "pair_rate": pairs_per_launch / (per_launch_ms / 1000.0),
         "scored_pair_rate": (scored_pairs / max(1, assign_launches)) / (per_launch_ms / 1000.0),
-        "e2e": {"value": world * args.e2e_steps / (e2e_max / 1000.0) if args.e2e_steps > 0 else None,
+        "e2e": {"value": args.e2e_steps / (e2e_max / 1000.0) if args.e2e_steps > 0 else None,
                 "unit": "APD/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": kernel_launches,
@@ -525,7 +530,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    inst, rounds = make_instance(args.workload, rank)
+    # one diagram for the whole job: with several ranks every evaluation is split
+    # by slabs of the grid's last axis and the moments are summed over the ranks
+    inst, rounds = make_instance(args.workload, 0)
     dim, n, J = inst.grid.dim, inst.n, inst.grid.num_pixels
     ctx = {"inst": inst, "rounds": rounds, "dev": dev, "stream": torch.cuda.current_stream(dev), "world": world,
            "local": local, "x0": torch.from_numpy(inst.x).to(dev), "A": torch.from_numpy(inst.A).to(dev),
@@ -533,6 +540,9 @@ def run_ours(args):
     ctx["x_out"] = torch.empty_like(ctx["x0"])
     ctx["w_out"] = torch.empty_like(ctx["w0"])
     ctx["ws"] = capi.Workspace(dim, n, J)
+    if world > 1:
+        from paper_2403_03571_gb300 import shard
+        shard.shard_workspace(ctx["ws"], rank, world)
     ctx["flush"] = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # the chosen form, the plain FP32 form and the tensor-core TF32 form, each timed
@@ -550,9 +560,13 @@ def run_ours(args):
         capi.apd_assign(inst.grid, x_fin, ctx["A"], w_fin, lab_t, ctx["ws"], precision=precision_code(capi, args.precision))
         gpu_lab = lab_t.cpu().numpy()
         del lab_t
-    for prec in dict.fromkeys(["fp32", "tc_tf32"]):
-        forms[prec] = measure_form(args, ctx, prec)
-        forms[prec]["precision"] = prec
+    # the same chosen pipeline with the other scoring arithmetic, and the plain method
+    alt = "fp32" if args.precision != "fp32" else "tc_tf32"
+    forms["chosen_alt"] = measure_form(args, ctx, alt, chosen_start=True)
+    forms["chosen_alt"]["precision"] = alt
+    forms["chosen_alt"]["pruned"] = bool(args.prune)
+    forms["fp32"] = measure_form(args, ctx, "fp32")
+    forms["fp32"]["precision"] = "fp32"
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -576,11 +590,13 @@ def run_ours(args):
         "warmup": args.warmup,
         "ms_per_step": chosen["ms_per_step"],
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong",
         "vs_baseline": None,
         "dtype": {"tc_tf32": "tf32/f32/f64", "tc_bf16": "bf16/f32/f64"}.get(args.precision, "f32/f64"),
         "data": "synthetic",
-        "config": config_dict(args.workload, inst, rounds, args.precision),
+        "config": config_dict(args.workload, inst, rounds, args.precision)
+        | {"parallelism": (f"one diagram over {world} ranks: slabs of the last grid axis, int64 allreduce "
+                           "of the per-cell moments per evaluation (NCCL)") if world > 1 else "one GPU"},
         "pair_evals_per_s": chosen["pair_evals_per_s"],
         "assign_kernel_pair_evals_per_s": chosen["pair_rate"],
         "evaluations_per_apd": chosen["evaluations_per_apd"],
@@ -592,11 +608,12 @@ def run_ours(args):
         "wall_s_timed": chosen["wall_s_timed"],
     }
     out["plain_fp32"] = side(forms["fp32"])
-    out["tc_tf32"] = side(forms["tc_tf32"])
+    out["chosen_" + forms["chosen_alt"]["precision"]] = side(forms["chosen_alt"])
     out["chosen_form"] = ("Algorithm 3 with every weight solve coarse-to-fine (grid factor 2, coarse eps "
                           "1.5 %, at most 200 coarse evaluations), the first started from the learned per-seed "
                           f"prediction judged against W = 0; {args.precision} scoring"
-                          + (" with seed-group pruning" if args.prune else ""))
+                          + (" with seed pruning (tensor cores: per-tile candidate lists; FP32: group and "
+                             "per-seed bounds)" if args.prune else ""))
     out["coarse_evaluations_per_apd"] = chosen["coarse_evaluations_per_apd"]
     out["warm_start_network"] = chosen["warm_start_network"]
     if not args.no_configs and world == 1:
@@ -624,6 +641,9 @@ def run_assign_only(args):
     build.build()
     capi.load()
     inst, _ = make_instance(args.workload, 0)
+    if args.assign_res:
+        from paper_2403_03571_gb300 import synth
+        inst.grid = synth.Grid.cube(inst.grid.dim, args.assign_res)
     dim, n, J = inst.grid.dim, inst.n, inst.grid.num_pixels
     x = torch.from_numpy(inst.x).cuda()
     A = torch.from_numpy(inst.A).cuda()
@@ -645,7 +665,8 @@ def run_assign_only(args):
     ms, launches, pairs, _ = ws.profile_read()
     scored = ws.pairs_scored()
     st = ws.last_stats()
-    print(json.dumps({"mode": "assign", "workload": args.workload, "precision": args.precision,
+    print(json.dumps({"mode": "assign", "workload": args.workload, "grid": list(inst.grid.res),
+                      "precision": args.precision,
                       "pruned": bool(args.prune and args.assign_prune),
                       "launch_ms": ms / max(1, launches),
                       "pairs_per_s": pairs / (ms / 1000.0), "scored_fraction": scored / max(1, pairs),
@@ -1030,7 +1051,8 @@ def run_sweep(args):
         form (coarse-to-fine, pruned).
     Seeds by the sequential rejection C = 0.2, the alpha anisotropy laws,
     instance seeds 2403035710 + 7e6 + run; times are CUDA-event (a) or wall (b,
-    synchronised) seconds."""
+    synchronised) seconds.  Up to --sweep-runs random instances per point, fewer
+    when a point exceeds --sweep-point-budget seconds (the rows state the count)."""
     import torch
     from paper_2403_03571_gb300 import build, capi, synth
     build.build()
@@ -1046,7 +1068,10 @@ def run_sweep(args):
         for dim in dims:
             for n in ns[dim]:
                 for alpha in alphas:
+                    t_point = time.perf_counter()
                     for run in range(args.sweep_runs):
+                        if run > 0 and time.perf_counter() - t_point > args.sweep_point_budget:
+                            break
                         inst = synth.runtime_test_instance(dim, n, alpha, False, base + run + 1000 * n,
                                                            m_cap=caps[dim - 2])
                         x, A, w = (torch.from_numpy(a).cuda() for a in (inst.x, inst.A, inst.w))
@@ -1074,7 +1099,10 @@ def run_sweep(args):
             for n in ns_b[dim]:
                 for alpha in alphas:
                     for multi in (False, True):
+                        t_point = time.perf_counter()
                         for run in range(args.sweep_runs):
+                            if run > 0 and time.perf_counter() - t_point > args.sweep_point_budget:
+                                break
                             inst = synth.runtime_test_instance(dim, n, alpha, multi, base + run + 1000 * n + 1,
                                                                m_cap=caps[dim - 2])
                             x, A, w, v = (torch.from_numpy(a).cuda() for a in (inst.x, inst.A, inst.w, inst.v))

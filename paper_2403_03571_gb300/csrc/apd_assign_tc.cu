@@ -42,10 +42,12 @@
 // U < T_excl: every other candidate and every excluded seed then costs more
 // than the best one.  Other pixels go to the FP64 rescoring queue (with the
 // best seed as the threshold hint), which settles them with the reference
-// arithmetic.  Certified pixels enter the integer moments in the epilogue:
-// the lanes of a warp holding the same label sum their moments (32-bit
-// warp reductions), one lane adds the sums to a per-CTA shared hash table,
-// flushed to the global int64 moments every few tiles.
+// arithmetic (pixels the scores leave undecided are first settled in FP32
+// direct form by the warp over the tile's candidate list).  Certified pixels
+// enter the integer moments in the epilogue: the lanes of a warp holding the
+// same label sum their moments (32-bit warp reductions; the last axis's
+// coordinate is uniform over a warp), and lanes 0 .. K-1 add the K words to
+// the global int64 moments.
 #include <cuda_bf16.h>
 #include <float.h>
 
@@ -72,8 +74,6 @@ constexpr int kProdWarp = kEpiWarps;         // warp 16: MMA issue
 constexpr int kXfWarp0 = kEpiWarps + 1;      // warps 17, 18: seed operands
 constexpr int kXfWarps = 2;
 constexpr int kThreads = (kEpiWarps + 1 + kXfWarps) * 32;  // 608
-constexpr int kTable = 128;                  // moment hash slots per CTA
-constexpr int kFlushTiles = 8;               // tiles between moment-table flushes
 constexpr int kListCap = 128;                // candidate seeds stored per tile
 constexpr int kMaxSteps = kListCap / kN;     // steps of a pruned tile (B operands stored per tile)
 constexpr int kAhead = 2;                    // pruned form: bulk copies issued ahead of the MMAs
@@ -104,11 +104,8 @@ struct TcFmt {
 
 template <int D, int KIND>
 struct TcShared {
-    static constexpr int KM = moment_width(D);
     alignas(1024) uint8_t A[kMT][TcFmt<KIND>::A_BYTES];
     alignas(1024) uint8_t B[kStages][TcFmt<KIND>::B_BYTES];
-    unsigned long long tval[kTable][KM];
-    int tkey[kTable];
     uint64_t bar_bfull[kStages];   // B operand built (the transform warps)
     uint64_t bar_acc[kStages];     // accumulator stage written (MMA commit)
     uint64_t bar_aempty[kStages];  // accumulator stage read (the epilogue warps)
@@ -214,9 +211,6 @@ __device__ __forceinline__ void seed_row(const SeedRec32 *__restrict__ recs, con
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void epi_barrier() {  // the sixteen epilogue warps only
-    asm volatile("bar.sync 1, %0;" ::"n"(kPix) : "memory");
-}
 __device__ __forceinline__ float fmin3_f(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -234,16 +228,6 @@ __device__ __forceinline__ float okey_inv(unsigned k) {
     return __uint_as_float(k ^ ((k >> 31) ? 0x80000000u : 0xffffffffu));
 }
 
-// Slot of `label` in the shared moment table (linear probing; -1 when full).
-__device__ __forceinline__ int tc_table_slot(int *tkey, int label) {
-    int slot = label & (kTable - 1);
-    for (int probe = 0; probe < kTable; ++probe) {
-        const int k = atomicCAS(&tkey[slot], -1, label);
-        if (k == -1 || k == label) return slot;
-        slot = (slot + 1) & (kTable - 1);
-    }
-    return -1;
-}
 
 // Tile t of the scoring window -> its first pixel per axis.
 template <int D>
@@ -261,6 +245,43 @@ __device__ __forceinline__ void tile_origin(int t, int ntx, int nty, int tlo, in
     }
 }
 
+// Per-axis tile data, FP64 once per tile coordinate: for coordinate c along
+// axis a (table entry off_a + c, off = 0, ntx, ntx + nty), the FP32 split of
+// the tile centre lo + (kb + T/2) h and the absolute box of the tile's valid
+// pixel centres rounded outwards.
+template <int D>
+__global__ void __launch_bounds__(256)
+    tc_axis_kernel(const GridDev g, const int ntx, const int nty, const int ntz, const int tlo,
+                   float4 *__restrict__ tab) {
+    using G = TcGeom<D>;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int a, c;
+    if (i < ntx) {
+        a = 0;
+        c = i;
+    } else if (i < ntx + nty) {
+        a = 1;
+        c = i - ntx;
+    } else if (D == 3 && i < ntx + nty + ntz) {
+        a = 2;
+        c = i - ntx - nty;
+    } else {
+        return;
+    }
+    const int td = a == 0 ? G::TX : (a == 1 ? G::TY : G::TZ);
+    const bool last = a == D - 1;
+    const int kb = (c + (last ? tlo : 0)) * td;
+    const int resa = a == 0 ? g.res[0] : (a == 1 ? g.res[1] : g.res[2]);
+    const int hi = last ? win_hi(g) : resa;
+    const int khi = min(kb + td, hi) - 1;
+    const double lo = a == 0 ? g.lo[0] : (a == 1 ? g.lo[1] : g.lo[2]);
+    const double h = a == 0 ? g.h[0] : (a == 1 ? g.h[1] : g.h[2]);
+    float ch, cl;
+    split2(lo + (double)(kb + td / 2) * h, ch, cl);
+    tab[i] = make_float4(ch, cl, __double2float_rd(lo + ((double)kb + 0.5) * h),
+                         __double2float_ru(lo + ((double)khi + 0.5) * h));
+}
+
 // ---------------------------------------------------------------------------
 // Pre-pass: one warp per tile.  Tile centre (FP32 high/low split), and either
 // the Morton start chunk (dense form) or the candidate list with T_excl.
@@ -274,7 +295,7 @@ __global__ void __launch_bounds__(256)
                    const uint32_t *__restrict__ scodes, const int32_t *__restrict__ perm, const int n_chunks,
                    float *__restrict__ centre, int *__restrict__ start, int4 *__restrict__ meta,
                    float *__restrict__ texcl, int *__restrict__ list, uint8_t *__restrict__ bops,
-                   const DevScalars *__restrict__ sc) {
+                   const float4 *__restrict__ axis_tab, const DevScalars *__restrict__ sc) {
     using Fm = TcFmt<KIND>;
     using G = TcGeom<D>;
     const int lane = threadIdx.x & 31;
@@ -296,27 +317,18 @@ __global__ void __launch_bounds__(256)
             frac[a] = (double)(((float)(kb[a] + td[a] / 2) + 0.5f) / (float)g.res[a]);
         }
     }
-    // FP64 per axis (the tile centre, and the absolute pixel box rounded outwards):
-    // lane a computes axis a, the others receive it
+    // the tile centre and the absolute pixel box, per axis from the table
     float alo[3] = {0.f, 0.f, 0.f}, ahi[3] = {0.f, 0.f, 0.f};
     {
-        float vh = 0.f, vl = 0.f, vlo = 0.f, vhi = 0.f;
-        if (lane < D) {
-            const int kba = lane == 0 ? kb[0] : (lane == 1 ? kb[1] : kb[D - 1]);
-            const int kha = lane == 0 ? khi[0] : (lane == 1 ? khi[1] : khi[D - 1]);
-            const int tda = lane == 0 ? td[0] : (lane == 1 ? td[1] : td[D - 1]);
-            const double loa = lane == 0 ? g.lo[0] : (lane == 1 ? g.lo[1] : g.lo[D - 1]);
-            const double ha = lane == 0 ? g.h[0] : (lane == 1 ? g.h[1] : g.h[D - 1]);
-            split2(loa + (double)(kba + tda / 2) * ha, vh, vl);
-            vlo = __double2float_rd(loa + ((double)kba + 0.5) * ha);
-            vhi = __double2float_ru(loa + ((double)kha + 0.5) * ha);
-        }
+        const int tx = t % ntx, r = t / ntx;
+        const int idx[3] = {tx, ntx + (D == 3 ? r % nty : r), ntx + nty + (D == 3 ? r / nty : 0)};
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            ch[a] = __shfl_sync(0xffffffffu, vh, a);
-            cl[a] = __shfl_sync(0xffffffffu, vl, a);
-            alo[a] = __shfl_sync(0xffffffffu, vlo, a);
-            ahi[a] = __shfl_sync(0xffffffffu, vhi, a);
+            const float4 e = axis_tab[idx[a]];
+            ch[a] = e.x;
+            cl[a] = e.y;
+            alo[a] = e.z;
+            ahi[a] = e.w;
         }
     }
     if (lane < 6) centre[(size_t)t * 6 + lane] = lane < 3 ? ch[lane] : cl[lane - 3];
@@ -499,6 +511,323 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Lower bound of the costs of the seeds of group gb over an absolute box of
+// pixel centres [alo, ahi] (FP32 rounded outwards).
+template <int D>
+__device__ __forceinline__ float group_lower(const GroupBound &gb, const float (&alo)[3], const float (&ahi)[3]) {
+    float d2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float slack = 1e-6f * (fabsf(alo[a]) + fabsf(ahi[a]) + fabsf(gb.lo[a]) + fabsf(gb.hi[a]));
+        const float q = fmaxf(fmaxf(gb.lo[a] - ahi[a], alo[a] - gb.hi[a]) - slack, 0.f);
+        d2 = __fmaf_rd(q, q, d2);
+    }
+    return __fadd_rd(__fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f), gb.wgap);
+}
+
+// Lower and upper bounds of seed r's costs (relative to w_ref) over the box
+// [rlo, rhi] of pixel centres given relative to the centre ch + cl.
+template <int D>
+__device__ __forceinline__ void seed_bounds(const SeedRec32 &r, const float (&ch)[3], const float (&cl)[3],
+                                            const float (&rlo)[3], const float (&rhi)[3], float wrh, float wrl,
+                                            float &lb, float &ub) {
+    float d2lo = 0.f, d2hi = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float xs = (r.xh[a] - ch[a]) + (r.xl[a] - cl[a]);
+        const float slack = 1e-6f * (fabsf(rlo[a]) + fabsf(rhi[a]) + 2.f * fabsf(xs)) + 1e-30f;
+        const float dl = fmaxf(fmaxf(xs - rhi[a], rlo[a] - xs) - slack, 0.f);
+        const float dh = fmaxf(fabsf(xs - rlo[a]), fabsf(xs - rhi[a])) + slack;
+        d2lo = __fmaf_rd(dl, dl, d2lo);
+        d2hi = __fmaf_ru(dh, dh, d2hi);
+    }
+    const float wn = -((r.wh - wrh) + (r.wl - wrl));  // w_ref - w_i, up to rounding
+    const float wslack = 1e-6f * fabsf(wn) + 1e-30f;
+    lb = __fadd_rd(__fmul_rd(__fmul_rd(r.pad[0], d2lo), 1.f - 1e-5f), __fsub_rd(wn, wslack));
+    ub = __fadd_ru(__fmul_ru(__fmul_ru(r.pad[1], d2hi), 1.f + 1e-5f), __fadd_ru(wn, wslack));
+}
+
+// Merge the smallest four of the warp's 32 keys (one per lane) into the
+// warp-uniform ascending four smallest values u0 <= u1 <= u2 <= u3.
+__device__ __forceinline__ void merge_smallest4(unsigned ku, float &u0, float &u1, float &u2, float &u3) {
+    const int lane = threadIdx.x & 31;
+    if (!(__reduce_min_sync(0xffffffffu, ku) < okey(u3))) return;
+    float b[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const unsigned m = __reduce_min_sync(0xffffffffu, ku);
+        b[e] = m == 0xffffffffu ? __int_as_float(0x7f800000) : okey_inv(m);
+        const int l = __ffs(__ballot_sync(0xffffffffu, ku == m)) - 1;
+        if (lane == l) ku = 0xffffffffu;
+    }
+    // the four smallest of two ascending lists of four: the elementwise minima of
+    // one list against the other reversed, then sorted
+    float c0 = fminf(u0, b[3]), c1 = fminf(u1, b[2]), c2 = fminf(u2, b[1]), c3 = fminf(u3, b[0]);
+    auto cswap = [](float &x, float &y) {
+        const float lo = fminf(x, y), hi = fmaxf(x, y);
+        x = lo;
+        y = hi;
+    };
+    cswap(c0, c2);
+    cswap(c1, c3);
+    cswap(c0, c1);
+    cswap(c2, c3);
+    cswap(c1, c2);
+    u0 = c0;
+    u1 = c1;
+    u2 = c2;
+    u3 = c3;
+}
+
+// Pruned form, step 1: one warp per super-tile of 2 x 2 (x 2) tiles finds the
+// candidates of the super-tile's box (groups visited by increasing bound; the
+// threshold is the fourth smallest upper bound, then the seeds with a lower
+// bound below it) and T_excl.  A seed left out there is left out of each tile
+// too: its bound over a sub-box is at least its bound over the box.
+constexpr int kSuperCap = 256;
+
+// Tile-coordinate range of a super-tile, and the box of a tile range [ca, cb]:
+// centre of tile ca (FP32 split), pixel box relative to it and absolute.
+struct SuperGeom {
+    int ntx, nty, ntz, tlo;
+};
+template <int D>
+__device__ __forceinline__ void super_range(const SuperGeom &sg, int sup, int (&c0)[3], int (&c1)[3]) {
+    const int nsx = (sg.ntx + 1) / 2, nsy = (sg.nty + 1) / 2;
+    const int sx = sup % nsx, rr = sup / nsx;
+    const int sy = rr % nsy, sz = D == 3 ? rr / nsy : 0;
+    c0[0] = 2 * sx;
+    c0[1] = 2 * sy;
+    c0[2] = 2 * sz;
+    c1[0] = min(2 * sx + 1, sg.ntx - 1);
+    c1[1] = min(2 * sy + 1, sg.nty - 1);
+    c1[2] = D == 3 ? min(2 * sz + 1, sg.ntz - 1) : 0;
+}
+template <int D>
+__device__ __forceinline__ void range_box(const GridDev &g, const SuperGeom &sg, const float4 *__restrict__ axis_tab,
+                                          const int (&ca)[3], const int (&cb)[3], float (&ch)[3], float (&cl)[3],
+                                          float (&rlo)[3], float (&rhi)[3], float (&alo)[3], float (&ahi)[3]) {
+    using G = TcGeom<D>;
+    const int td[3] = {G::TX, G::TY, G::TZ};
+    const int toff[3] = {0, sg.ntx, sg.ntx + sg.nty};
+    const int tl[3] = {0, D == 2 ? sg.tlo : 0, D == 3 ? sg.tlo : 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ch[a] = cl[a] = rlo[a] = rhi[a] = alo[a] = ahi[a] = 0.f;
+        if (a < D) {
+            const float4 ea = axis_tab[toff[a] + ca[a]], eb = axis_tab[toff[a] + cb[a]];
+            ch[a] = ea.x;
+            cl[a] = ea.y;
+            alo[a] = ea.z;
+            ahi[a] = eb.w;
+            const int kb = (ca[a] + tl[a]) * td[a];
+            const int hi = a == D - 1 ? win_hi(g) : g.res[a];
+            const int khi = min((cb[a] + tl[a]) * td[a] + td[a], hi) - 1;
+            const int cc = kb + td[a] / 2;
+            rlo[a] = ((float)(kb - cc) + 0.5f) * g.h32[a];
+            rhi[a] = ((float)(khi - cc) + 0.5f) * g.h32[a];
+        }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+    tc_super_kernel(const GridDev g, const SuperGeom sg, const int nsup, const int n,
+                    const SeedRec32 *__restrict__ r32, const GroupBound *__restrict__ groups,
+                    const uint32_t *__restrict__ scodes, const float4 *__restrict__ axis_tab,
+                    int *__restrict__ slist, int *__restrict__ scount, float *__restrict__ stex,
+                    const DevScalars *__restrict__ sc) {
+    using G = TcGeom<D>;
+    const int lane = threadIdx.x & 31;
+    const int sup = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (sup >= nsup) return;
+    const float finf = __int_as_float(0x7f800000);
+    int c0[3], c1[3];
+    super_range<D>(sg, sup, c0, c1);
+    float ch[3], cl[3], rlo[3], rhi[3], alo[3], ahi[3];
+    range_box<D>(g, sg, axis_tab, c0, c1, ch, cl, rlo, rhi, alo, ahi);
+    float wrh = 0.f, wrl = 0.f;
+    {
+        float h = 0.f, l = 0.f;
+        if (lane == 0) split2(dkey_inv(sc->wref_key), h, l);
+        wrh = __shfl_sync(0xffffffffu, h, 0);
+        wrl = __shfl_sync(0xffffffffu, l, 0);
+    }
+    const int n_groups = (n + 31) / 32;
+    const int n_blocks = (n_groups + 31) / 32;
+    int bstart = 0;
+    if (scodes && n_blocks > 1) {
+        const int td[3] = {G::TX, G::TY, G::TZ};
+        const int tl[3] = {0, D == 2 ? sg.tlo : 0, D == 3 ? sg.tlo : 0};
+        double frac[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            frac[a] = (double)(((float)((c0[a] + tl[a]) * td[a] + td[a]) + 0.5f) / (float)g.res[a]);
+        const uint32_t code = morton_code(D, frac);
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (scodes[mid] < code) lo = mid + 1;
+            else hi = mid;
+        }
+        bstart = min(min(lo, n - 1) / 1024, n_blocks - 1);
+    }
+    auto block_of = [&](int bi) {
+        const int off = (bi & 1) ? ((bi + 1) >> 1) : -(bi >> 1);
+        int blk = bstart + off;
+        if (blk >= n_blocks) blk -= n_blocks;
+        if (blk < 0) blk += n_blocks;
+        return blk;
+    };
+    // pass 1: the threshold
+    float u0 = finf, u1 = finf, u2 = finf, u3 = finf;
+    for (int bi = 0; bi < n_blocks; ++bi) {
+        const int blk = block_of(bi);
+        const int grp = blk * 32 + lane;
+        const float lbg = grp < n_groups ? group_lower<D>(groups[grp], alo, ahi) : finf;
+        unsigned live = __ballot_sync(0xffffffffu, grp < n_groups);
+        while (live) {
+            const bool mine = (live >> lane) & 1u;
+            const unsigned key = mine ? okey(lbg) : 0xffffffffu;
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+            const int kg = __ffs(__ballot_sync(0xffffffffu, mine && key == kmin)) - 1;
+            if (__shfl_sync(0xffffffffu, lbg, kg) > u3) break;
+            live &= ~(1u << kg);
+            const int pos = (blk * 32 + kg) * 32 + lane;
+            float lb = finf, ub = finf;
+            if (pos < n) seed_bounds<D>(r32[pos], ch, cl, rlo, rhi, wrh, wrl, lb, ub);
+            merge_smallest4(pos < n ? okey(ub) : 0xffffffffu, u0, u1, u2, u3);
+        }
+    }
+    // pass 2: the list and T_excl
+    const float T = u3;
+    float tex = finf;
+    int cnt = 0;
+    int *out = slist + (size_t)sup * kSuperCap;
+    for (int bi = 0; bi < n_blocks; ++bi) {
+        const int blk = block_of(bi);
+        const int grp = blk * 32 + lane;
+        const float lbg = grp < n_groups ? group_lower<D>(groups[grp], alo, ahi) : finf;
+        const bool in = grp < n_groups && lbg <= T;
+        tex = fminf(tex, in ? finf : lbg);
+        unsigned todo = __ballot_sync(0xffffffffu, in);
+        while (todo) {
+            const int kg = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int pos = (blk * 32 + kg) * 32 + lane;
+            float lb = finf, ub = finf;
+            if (pos < n) seed_bounds<D>(r32[pos], ch, cl, rlo, rhi, wrh, wrl, lb, ub);
+            const bool cand = pos < n && lb <= T;
+            const unsigned cm = __ballot_sync(0xffffffffu, cand);
+            const int rank = __popc(cm & ((1u << lane) - 1u));
+            if (cand) {
+                if (cnt + rank < kSuperCap) out[cnt + rank] = pos;
+                else tex = fminf(tex, lb);  // beyond the capacity: excluded
+            } else if (pos < n) {
+                tex = fminf(tex, lb);
+            }
+            cnt += __popc(cm);
+        }
+    }
+    tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
+    if (lane == 0) {
+        scount[sup] = min(cnt, kSuperCap);
+        stex[sup] = tex;
+    }
+}
+
+// Pruned form, step 2: one warp per tile narrows its super-tile's list with
+// the tile's own bounds (the fourth smallest upper bound over the tile), sets
+// T_excl = min(the super-tile's, the bounds of the seeds it drops), and stores
+// its list (seed indices) and split seed operands.
+template <int D, int KIND>
+__global__ void __launch_bounds__(256)
+    tc_list_kernel(const GridDev g, const SuperGeom sg, const int ntiles, const int n,
+                   const SeedRec32 *__restrict__ r32, const int32_t *__restrict__ perm,
+                   const float4 *__restrict__ axis_tab, const int *__restrict__ slist, const int *__restrict__ scount,
+                   const float *__restrict__ stex, float *__restrict__ centre, int4 *__restrict__ meta,
+                   float *__restrict__ texcl, int *__restrict__ list, uint8_t *__restrict__ bops,
+                   const DevScalars *__restrict__ sc) {
+    using G = TcGeom<D>;
+    using Fm = TcFmt<KIND>;
+    const int lane = threadIdx.x & 31;
+    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (t >= ntiles) return;
+    const float finf = __int_as_float(0x7f800000);
+    const int tx = t % sg.ntx, rr = t / sg.ntx;
+    const int tc3[3] = {tx, D == 3 ? rr % sg.nty : rr, D == 3 ? rr / sg.nty : 0};
+    const int nsx = (sg.ntx + 1) / 2, nsy = (sg.nty + 1) / 2;
+    const int sup = tc3[0] / 2 + nsx * (tc3[1] / 2 + nsy * (tc3[2] / 2));
+    float ch[3], cl[3], rlo[3], rhi[3], alo[3], ahi[3];
+    range_box<D>(g, sg, axis_tab, tc3, tc3, ch, cl, rlo, rhi, alo, ahi);
+    if (lane < 6) centre[(size_t)t * 6 + lane] = lane < 3 ? ch[lane] : cl[lane - 3];
+    float wrh = 0.f, wrl = 0.f;
+    {
+        float h = 0.f, l = 0.f;
+        if (lane == 0) split2(dkey_inv(sc->wref_key), h, l);
+        wrh = __shfl_sync(0xffffffffu, h, 0);
+        wrl = __shfl_sync(0xffffffffu, l, 0);
+    }
+    const int cntS = scount[sup];
+    const int *sl = slist + (size_t)sup * kSuperCap;
+    // the tile's bounds of the super-tile's candidates: at most 8 rounds of 32
+    float lbv[kSuperCap / 32];
+    float u0 = finf, u1 = finf, u2 = finf, u3 = finf;
+#pragma unroll
+    for (int r = 0; r < kSuperCap / 32; ++r) {
+        lbv[r] = finf;
+        if (r * 32 < cntS) {
+            const int e = r * 32 + lane;
+            float ub = finf;
+            if (e < cntS) seed_bounds<D>(r32[sl[e]], ch, cl, rlo, rhi, wrh, wrl, lbv[r], ub);
+            merge_smallest4(e < cntS ? okey(ub) : 0xffffffffu, u0, u1, u2, u3);
+        }
+    }
+    const float T = u3;
+    float tex = stex[sup];
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kSuperCap / 32; ++r) {
+        if (r * 32 < cntS) {
+            const int e = r * 32 + lane;
+            const bool cand = e < cntS && lbv[r] <= T;
+            const unsigned cm = __ballot_sync(0xffffffffu, cand);
+            const int rank = __popc(cm & ((1u << lane) - 1u));
+            if (cand) {
+                if (cnt + rank < kListCap) list[(size_t)t * kListCap + cnt + rank] = sl[e];
+                else tex = fminf(tex, lbv[r]);
+            } else if (e < cntS) {
+                tex = fminf(tex, lbv[r]);
+            }
+            cnt += __popc(cm);
+        }
+    }
+    tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
+    const int cnt_c = min(cnt, kListCap);
+    if (lane == 0) {
+        const int td[3] = {G::TX, G::TY, G::TZ};
+        const int tl[3] = {0, D == 2 ? sg.tlo : 0, D == 3 ? sg.tlo : 0};
+        int kb[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) kb[a] = (tc3[a] + tl[a]) * td[a];
+        meta[t] = make_int4(kb[0], kb[1], kb[2], cnt_c);
+        texcl[t] = tex;
+    }
+    __syncwarp();  // the list entries written by the other lanes
+    const int ns = max(1, (cnt_c + kN - 1) / kN);
+    for (int k = 0; k < ns; ++k) {
+        const int slot = k * kN + lane;
+        const int pos = slot < cnt_c ? list[(size_t)t * kListCap + slot] : -1;
+        float row[kK];
+        seed_row<D, KIND>(r32, pos, ch, cl, wrh, wrl, row);
+        uint8_t *dst = bops + ((size_t)t * kMaxSteps + k) * Fm::B_BYTES;
+#pragma unroll
+        for (int c = 0; c < kK / Fm::EPR; ++c)
+            put_row<KIND>(dst + tc::core_offset(lane, c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO), row + c * Fm::EPR);
+        if (pos >= 0) list[(size_t)t * kListCap + slot] = perm ? perm[pos] : pos;  // seed index for the labels
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Main kernel
 // ---------------------------------------------------------------------------
@@ -579,11 +908,6 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
         for (int c = 0; c < kK / Fm::EPR; ++c)
             put_row<KIND>(sm.A[mt] + tc::core_offset(row, c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO),
                           rowv + c * Fm::EPR);
-    }
-    for (int t = tid; t < kTable; t += blockDim.x) {
-        sm.tkey[t] = -1;
-#pragma unroll
-        for (int v = 0; v < KM; ++v) sm.tval[t][v] = 0ull;
     }
     if (warp == 0) {
         tc::tmem_alloc(&sm.tslot, kCols);
@@ -766,7 +1090,8 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
             }
             int lv[kMaxSteps];  // pruned form: the seed of list slot k * 32 + lane
 #pragma unroll
-            for (int k = 0; k < kMaxSteps; ++k) lv[k] = -1;
+            for (int k = 0; k < kMaxSteps; ++k)
+                lv[k] = (pruned && k * kN + lane < cnt) ? a.list[(size_t)t * kListCap + k * kN + lane] : -1;
             float k1 = FLT_MAX, k2 = FLT_MAX;  // two smallest packed scores
             int bstep = 0;
             bool ok = true;
@@ -784,11 +1109,6 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.bar_aempty[s]);
-                if (pruned) {
-#pragma unroll
-                    for (int kk = 0; kk < kMaxSteps; ++kk)
-                        if (kk == k && k * kN + lane < cnt) lv[kk] = a.list[(size_t)t * kListCap + k * kN + lane];
-                }
                 // a slice whose smallest score lies above the second-best by more than
                 // the packing (< 32 ulp) cannot change the two smallest keys
                 if (got && !(mn > fmaf(fabsf(k2), 0x1p-16f, k2))) {
@@ -916,30 +1236,37 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 }
             }
             if (label >= 0 && a.labels) a.labels[j] = label;
-            // moments of the certified pixels: the lanes holding the same label sum their
-            // words across the warp; the leader finds the label's table slot and lanes
-            // 0 .. K-1 add one word each
+            // Moments of the certified pixels.  The lanes holding the same label sum
+            // their words across the warp; the last axis's coordinate is the same for
+            // the whole warp (3D: one z of an 8 x 4 block, 2D: one row), so the words
+            // with it follow from the count and the other sums.  Lanes 0 .. K-1 then
+            // add one word each to the global int64 moments.
             unsigned todo = __ballot_sync(0xffffffffu, label >= 0);
+            const unsigned long long uz = 2ull * (unsigned long long)(D == 3 ? kk[2] : kk[1]) + 1ull;
             while (todo) {
                 const int leader = __ffs(todo) - 1;
                 const int L0 = __shfl_sync(0xffffffffu, label, leader);
                 const bool mine = label == L0;
                 const unsigned grp = __ballot_sync(0xffffffffu, mine);
+                const unsigned long long m = (unsigned long long)__popc(grp);
                 unsigned long long sum[KM];
                 if (!a.wide) {
-                    // u < 2^13: every word of a pixel is below 2^26 and 32 of them below 2^31
-                    unsigned u32[3] = {0u, 0u, 0u};
-#pragma unroll
-                    for (int d = 0; d < D; ++d) u32[d] = mine ? 2u * (unsigned)kk[d] + 1u : 0u;
-                    sum[0] = (unsigned long long)__popc(grp);
-#pragma unroll
-                    for (int d = 0; d < D; ++d) sum[1 + d] = (unsigned long long)__reduce_add_sync(0xffffffffu, u32[d]);
-                    int e = 1 + D;
-#pragma unroll
-                    for (int d = 0; d < D; ++d)
-#pragma unroll
-                        for (int d2 = d; d2 < D; ++d2)
-                            sum[e++] = (unsigned long long)__reduce_add_sync(0xffffffffu, u32[d] * u32[d2]);
+                    // u < 2^13: every product is below 2^26 and 32 of them below 2^31
+                    const unsigned u0 = mine ? 2u * (unsigned)kk[0] + 1u : 0u;
+                    const unsigned u1 = (mine && D == 3) ? 2u * (unsigned)kk[1] + 1u : 0u;
+                    const unsigned long long s0 = __reduce_add_sync(0xffffffffu, u0);
+                    const unsigned long long s00 = __reduce_add_sync(0xffffffffu, u0 * u0);
+                    if (D == 3) {
+                        const unsigned long long s1 = __reduce_add_sync(0xffffffffu, u1);
+                        const unsigned long long s01 = __reduce_add_sync(0xffffffffu, u0 * u1);
+                        const unsigned long long s11 = __reduce_add_sync(0xffffffffu, u1 * u1);
+                        sum[0] = m; sum[1] = s0; sum[2] = s1; sum[3] = m * uz;
+                        sum[4] = s00; sum[5] = s01; sum[6] = s0 * uz; sum[7] = s11; sum[8] = s1 * uz;
+                        sum[9] = m * uz * uz;
+                    } else {
+                        sum[0] = m; sum[1] = s0; sum[2] = m * uz; sum[3] = s00; sum[4] = s0 * uz;
+                        sum[5] = m * uz * uz;
+                    }
                 } else {
                     unsigned long long u[3] = {0ull, 0ull, 0ull};
 #pragma unroll
@@ -961,36 +1288,15 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                         sum[v] = x;
                     }
                 }
-                int slot = -1;
-                if (lane == leader) slot = tc_table_slot(sm.tkey, L0);
-                slot = __shfl_sync(0xffffffffu, slot, leader);
                 unsigned long long word = 0ull;
 #pragma unroll
                 for (int v = 0; v < KM; ++v)
                     if (lane == v) word = sum[v];
-                if (lane < KM && word)
-                    atomicAdd(slot >= 0 ? &sm.tval[slot][lane] : &a.gmom[(size_t)L0 * KM + lane], word);
+                if (lane < KM && word) atomicAdd(&a.gmom[(size_t)L0 * KM + lane], word);
                 todo &= ~grp;
             }
             if (warp == 0 && lane == 0 && a.pairs_scored)
                 atomicAdd(a.pairs_scored, (unsigned long long)ns * kN * kPix);
-            // flush the table every few tiles (all sixteen epilogue warps take part)
-            if ((i % kFlushTiles) == kFlushTiles - 1 || i == my_tiles - 1) {
-                epi_barrier();
-                for (int e = tid; e < kTable; e += kPix) {
-                    const int key = sm.tkey[e];
-                    if (key >= 0) {
-#pragma unroll
-                        for (int v = 0; v < KM; ++v) {
-                            const unsigned long long val = sm.tval[e][v];
-                            if (val) atomicAdd(&a.gmom[(size_t)key * KM + v], val);
-                            sm.tval[e][v] = 0ull;
-                        }
-                        sm.tkey[e] = -1;
-                    }
-                }
-                epi_barrier();
-            }
         }
     }
     tc::fence_before_sync();
@@ -1028,11 +1334,25 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     const int n_chunks = (n + kN - 1) / kN;
     const bool pruned = ws.prune;
     const SeedRec32 *rs = ws.sorted ? ws.recs32s : ws.recs32;
-    const int pblocks = (int)((ntl * 32 + 255) / 256);
-    tc_tile_kernel<D, KIND><<<pblocks, 256, 0, st>>>(
-        g, ntx, nty, tlo, ntiles, n, rs, ws.groups, ws.sorted ? ws.scodes : nullptr, ws.sorted ? ws.perm : nullptr,
-        n_chunks, ws.tc_centre, ws.tc_start, ws.tc_meta, ws.tc_texcl, pruned ? ws.tc_list : nullptr, ws.tc_bops,
-        ws.sc);
+    const int ntz = D == 3 ? (int)(ntl / ((long long)ntx * nty)) : 0;
+    const int naxis = ntx + nty + ntz;
+    tc_axis_kernel<D><<<(naxis + 255) / 256, 256, 0, st>>>(g, ntx, nty, ntz, tlo, ws.tc_axis);
+    if (pruned) {
+        const SuperGeom sg{ntx, nty, ntz, tlo};
+        const int nsup = ((ntx + 1) / 2) * ((nty + 1) / 2) * (D == 3 ? (ntz + 1) / 2 : 1);
+        tc_super_kernel<D><<<(nsup * 32 + 255) / 256, 256, 0, st>>>(g, sg, nsup, n, rs, ws.groups,
+                                                                    ws.sorted ? ws.scodes : nullptr, ws.tc_axis,
+                                                                    ws.tc_slist, ws.tc_scount, ws.tc_stex, ws.sc);
+        tc_list_kernel<D, KIND><<<(ntiles * 32 + 255) / 256, 256, 0, st>>>(
+            g, sg, ntiles, n, rs, ws.sorted ? ws.perm : nullptr, ws.tc_axis, ws.tc_slist, ws.tc_scount, ws.tc_stex,
+            ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.tc_bops, ws.sc);
+    } else {
+        const int pblocks = (int)((ntl * 32 + 255) / 256);
+        tc_tile_kernel<D, KIND><<<pblocks, 256, 0, st>>>(
+            g, ntx, nty, tlo, ntiles, n, rs, ws.groups, ws.sorted ? ws.scodes : nullptr,
+            ws.sorted ? ws.perm : nullptr, n_chunks, ws.tc_centre, ws.tc_start, ws.tc_meta, ws.tc_texcl, nullptr,
+            ws.tc_bops, ws.tc_axis, ws.sc);
+    }
     // more than 114 KB of shared memory keeps one CTA (512 tensor-memory columns) per SM
     const size_t smem = std::max<size_t>(sizeof(TcShared<D, KIND>), 120 * 1024);
     cudaError_t e = cudaFuncSetAttribute(assign_tc_kernel<D, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1098,5 +1418,6 @@ long long tc_tile_count(const GridDev &g) {
 
 int tc_list_cap() { return kListCap; }
 size_t tc_bops_bytes_per_tile() { return (size_t)kMaxSteps * kBMax; }
+int tc_super_cap() { return kSuperCap; }
 
 }  // namespace apd

@@ -605,6 +605,11 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.tc_texcl, (size_t)w.tc_tile_cap * sizeof(float));
     alloc((void **)&w.tc_list, (size_t)w.tc_tile_cap * tc_list_cap() * sizeof(int));
     alloc((void **)&w.tc_bops, (size_t)w.tc_tile_cap * tc_bops_bytes_per_tile());
+    alloc((void **)&w.tc_axis, (size_t)3 * w.tc_tile_cap * sizeof(float4));
+    // super-tiles: at most one per tile
+    alloc((void **)&w.tc_slist, (size_t)w.tc_tile_cap * tc_super_cap() * sizeof(int));
+    alloc((void **)&w.tc_scount, (size_t)w.tc_tile_cap * sizeof(int));
+    alloc((void **)&w.tc_stex, (size_t)w.tc_tile_cap * sizeof(float));
     alloc((void **)&w.part, nb * 5 * sizeof(double));
     alloc((void **)&w.grad, (size_t)max_n * sizeof(double));
     alloc((void **)&w.W, (size_t)max_n * sizeof(double));
@@ -638,7 +643,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
-    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.tc_axis, w.tc_slist, w.tc_scount, w.tc_stex, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
         if (p) cudaFree(p);

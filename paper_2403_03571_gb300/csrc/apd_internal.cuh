@@ -102,6 +102,10 @@ struct Workspace {
     float *tc_texcl = nullptr;          // [tc_tile_cap] cost lower bound of the seeds left out
     int *tc_list = nullptr;             // [tc_tile_cap][tc_list_cap()] candidates
     uint8_t *tc_bops = nullptr;         // [tc_tile_cap] x tc_bops_bytes_per_tile(): stored seed operands
+    float4 *tc_axis = nullptr;          // [3 tc_tile_cap] per-axis tile centres and pixel boxes
+    int *tc_slist = nullptr;            // [tc_tile_cap][tc_super_cap()] candidates of the super-tiles
+    int *tc_scount = nullptr;           // [tc_tile_cap] their counts
+    float *tc_stex = nullptr;           // [tc_tile_cap] their bounds of the seeds left out
     long long tc_tile_cap = 0;
     bool sorted = false;                // set by launch_seed_prep for the current pass
     bool prune = false;                 // FP32 scoring skips seed groups by their bounds
@@ -315,6 +319,7 @@ cudaError_t launch_assign_tc(const GridDev &g, int n, Workspace &ws, int32_t *la
 long long tc_tile_count(const GridDev &g);
 int tc_list_cap();
 size_t tc_bops_bytes_per_tile();
+int tc_super_cap();
 // bounds of the 32-seed groups of the scan-order records (ws.groups)
 cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st);
 // FP64 rescoring of the queued pixels (labels optional, moments updated).

@@ -132,6 +132,18 @@ __device__ __forceinline__ void tmem_ld32_min(uint32_t taddr, float (&v)[32], fl
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 8 consecutive columns with their minimum.
+__device__ __forceinline__ void tmem_ld8_min(uint32_t taddr, float (&v)[8], float &mn) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x8.min.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, %8, [%9];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=f"(mn)
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ---- rounding to the operand formats ------------------------------------------
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
