@@ -321,6 +321,27 @@ int apd_cell_moments_noalloc(const apd_grid *grid, const apd_seeds *seeds, int64
  * (host pointers).  Host-synchronous; runs on the current device. */
 int apd_tensor_core_check(int32_t kind, int32_t variant, int32_t *mismatches, float *max_err);
 
+/* Diagnostic of the L-BFGS direction kernels of Algorithm 2's weight solve.  The
+ * hist pairs (s_k, y_k) are pushed, oldest first, through the device push
+ * kernel (which stores them with their Gram entries s_i.y_j, y_i.y_j), then the
+ * direction p = -H g is formed as in the solve, with H0 = gamma I and
+ * gamma = s.y / y.y of the newest pair, taken only if that pair passes the
+ * curvature test s.y > 1e-12 |s| |y| (otherwise the direction uses the older
+ * hist - 1 pairs and gamma = 1).
+ *   fused = 0: every pair pushed alone, then the direction kernels (the path of
+ *     a solve's first step and of a restart);
+ *   fused = 1: the newest pair pushed by the kernel that also forms the
+ *     direction's coefficients (the path after every accepted step).  That pair
+ *     enters as the step from gradient g - y to gradient g, with g - y and
+ *     then y = g - (g - y) rounded on the device.
+ *   S, Y: host, [hist][n] row-major, row k = pair k (k = hist - 1 newest);
+ *   g: host [n]; p: host [n], written; gp: host, written with <g, p>.
+ * Returns APD_ERR_ARG for n < 1, hist outside [1, 31], fused outside {0, 1} or
+ * a null pointer.  Host-synchronous; allocates and frees its own device
+ * buffers on the current device. */
+int apd_lbfgs_check(int32_t n, int32_t hist, const double *S, const double *Y, const double *g, int32_t fused,
+                    double *p, double *gp);
+
 /* ---- Batched weight solves (many independent problems at once) ------------
  * A batch holds `count` independent APD problems ("instances") of one
  * dimension, each with its own grid and seed count n_b.  Its seeds are rows

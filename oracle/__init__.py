@@ -16,6 +16,9 @@ Functions and the passages they follow (arXiv 2403.03571):
                                   sharded evaluation exchanges);
 * ``dual``                     -- eqs. (2.7), (2.8) and the stop rule of Algorithm 2;
 * ``solve_weights``            -- Algorithm 2 with a library L-BFGS (scipy L-BFGS-B);
+* ``lbfgs_direction``          -- the limited-memory BFGS direction of Algorithm 2's ascent
+                                  (the two-loop recursion of Nocedal and Wright, Numerical
+                                  Optimization, 2nd ed., Algorithm 7.4);
 * ``lloyd``                    -- Algorithm 3 (discrete centroids, warm-started weights);
 * ``resolution_lower_bound``   -- eq. (2.9) / Table 1;
 * ``resolution_practical``     -- eq. (2.10).
@@ -311,6 +314,27 @@ def solve_weights(grid, x, A, v, w0=None, eps: float = 0.01, max_evals: int = 50
     Wb, err, g = state["best"]
     converged = err < eps
     return Wb, {"converged": converged, "evals": state["evals"], "max_rel_err": err, "g": g}
+
+
+def lbfgs_direction(S, Y, g, gamma: float) -> np.ndarray:
+    """p = -H g for the limited-memory BFGS matrix H built from H0 = gamma I and the
+    pairs (s_k, y_k), rows of S and Y with the newest last: the two-loop recursion
+    (Nocedal and Wright, Algorithm 7.4), in FP64.  Algorithm 2 ascends g~ with
+    L-BFGS; in the minimisation of -g~ this is the search direction for gradient g."""
+    S = np.asarray(S, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    q = np.array(g, dtype=np.float64)
+    m = S.shape[0]
+    rho = [1.0 / float(S[k] @ Y[k]) for k in range(m)]
+    alpha = [0.0] * m
+    for k in range(m - 1, -1, -1):        # newest to oldest
+        alpha[k] = rho[k] * float(S[k] @ q)
+        q = q - alpha[k] * Y[k]
+    r = gamma * q
+    for k in range(m):                    # oldest to newest
+        beta = rho[k] * float(Y[k] @ r)
+        r = r + (alpha[k] - beta) * S[k]
+    return -r
 
 
 def lloyd(grid, x, A, v, K: int = 5, eps: float = 0.01, w0=None, max_evals: int = 5000,

@@ -45,7 +45,7 @@ EXPORTED = (
     "apd_profile_read_scored", "apd_lloyd_multires", "apd_refine_opts_default", "apd_solve_weights_refine",
     "apd_points_moments", "apd_points_dual_value_grad", "apd_refine_next_grid",
     "apd_masked_moments", "apd_masked_dual_value_grad", "apd_workspace_set_wait_limit",
-    "apd_shard_range", "apd_cell_moments_slab", "apd_workspace_set_shard",
+    "apd_shard_range", "apd_cell_moments_slab", "apd_workspace_set_shard", "apd_lbfgs_check",
 )
 
 
@@ -153,6 +153,8 @@ def load(path: Optional[str] = None):
     L.apd_cell_moments_noalloc.argtypes = [_P(ApdGrid), _P(ApdSeeds), _vp, _vp]
     L.apd_tensor_core_check.argtypes = [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32),
                                         _P(ctypes.c_float)]
+    L.apd_lbfgs_check.argtypes = [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int32, _vp,
+                                  _P(ctypes.c_double)]
     L.apd_profile_read.argtypes = [_vp, _P(ctypes.c_double), _P(ctypes.c_int64), _P(ctypes.c_int64),
                                    _P(ctypes.c_int64)]
     L.apd_batch_create.argtypes = [_P(_vp), ctypes.c_int32, ctypes.c_int32, _P(ApdGrid),
@@ -369,6 +371,23 @@ def apd_tensor_core_check(kind: int, variant: int = 0):
     mm, err = ctypes.c_int32(), ctypes.c_float()
     rc = load().apd_tensor_core_check(int(kind), int(variant), ctypes.byref(mm), ctypes.byref(err))
     return rc, mm.value, err.value
+
+
+def apd_lbfgs_check(S, Y, g, fused=False):
+    """(status, p, <g, p>) of the L-BFGS direction self-check: S, Y float64
+    [hist, n] (row k = pair k, newest last), g float64 [n]; host arrays.  fused:
+    the newest pair goes through the push kernel that also forms the direction
+    (it then enters as y = g - (g - y), rounded on the device)."""
+    import numpy as np
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    hist, n = S.shape
+    p = np.empty(n, dtype=np.float64)
+    gp = ctypes.c_double()
+    rc = load().apd_lbfgs_check(int(n), int(hist), S.ctypes.data, Y.ctypes.data, g.ctypes.data, int(bool(fused)),
+                                p.ctypes.data, ctypes.byref(gp))
+    return rc, p, gp.value
 
 
 def solve_opts(eps=0.01, max_evals=1000, history=10, precision=APD_FP32, check_volumes=1):

@@ -115,12 +115,12 @@ cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t
                                  unsigned long long *gmom, cudaStream_t st) {
     using C = Cfg<D>;
     const size_t smem = sizeof(SharedLayout<D>);
-    static bool attr_set = false;
-    if (!attr_set) {
+    constexpr unsigned bit = D == 3 ? kAttrFp32Score3 : kAttrFp32Score2;
+    if (!(ws.attr_done & bit)) {
         cudaError_t e = cudaFuncSetAttribute(assign_fp32_kernel<D>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        ws.attr_done |= bit;
     }
     // tiles along the last axis that meet the window [win_lo, win_hi)
     constexpr int TL = D == 3 ? C::TZ : C::TY;
@@ -149,9 +149,7 @@ cudaError_t launch_assign_fp32(const GridDev &g, int n, Workspace &ws, int32_t *
 cudaError_t launch_tie_gap(const GridDev &g, int n, const double *x, const double *A, const double *w,
                            Workspace &ws, double *gap, cudaStream_t st) {
     RescorePrune pr{ws.groups, ws.sorted ? ws.recs32s : ws.recs32, ws.sorted ? ws.perm : nullptr, (n + 31) / 32};
-    int sms = 152;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ws.device) != cudaSuccess) sms = 152;
-    const int blocks = sms * 8;
+    const int blocks = ws.sms * 8;
     if (g.dim == 3)
         tie_gap_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, pr, ws.sc, gap);
     else
@@ -164,17 +162,14 @@ cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const 
                                 unsigned long long *moments, cudaStream_t st) {
     // one warp per queued pixel, latency-bound (dependent record loads): as many
     // resident warps as the registers allow
-    static int blocks_per_sm[2] = {0, 0}, dev_sms = 0;
-    int &bps = blocks_per_sm[g.dim == 3 ? 1 : 0];
-    if (!dev_sms && cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ws.device) != cudaSuccess)
-        dev_sms = 152;
+    int &bps = ws.rescore_bps[g.dim == 3 ? 1 : 0];
     if (!bps) {
         const cudaError_t e = g.dim == 3
             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rescore_kernel<3>, 256, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rescore_kernel<2>, 256, 0);
         if (e != cudaSuccess || bps < 1) bps = 2;
     }
-    const int blocks = dev_sms * bps;
+    const int blocks = ws.sms * bps;
     RescorePrune pr{nullptr, nullptr, nullptr, 0};
     if (ws.groups && (!ws.sorted || ws.recs32s)) {
         pr.groups = ws.groups;

@@ -53,6 +53,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "apd_cost.cuh"
 #include "apd_internal.cuh"
@@ -679,7 +680,11 @@ __global__ void __launch_bounds__(256)
         if (blk < 0) blk += n_blocks;
         return blk;
     };
-    // pass 1: the threshold
+    // pass 1: the threshold.  Groups are taken two at a time (their records
+    // loaded together); the second is taken only if its bound is below the
+    // current threshold, and extra seeds merged can only be ones a sequential
+    // visit would also have merged or ones with no smaller upper bound.
+    const SeedRec32 zrec{};
     float u0 = finf, u1 = finf, u2 = finf, u3 = finf;
     for (int bi = 0; bi < n_blocks; ++bi) {
         const int blk = block_of(bi);
@@ -689,21 +694,48 @@ __global__ void __launch_bounds__(256)
         while (live) {
             const bool mine = (live >> lane) & 1u;
             const unsigned key = mine ? okey(lbg) : 0xffffffffu;
-            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
-            const int kg = __ffs(__ballot_sync(0xffffffffu, mine && key == kmin)) - 1;
-            if (__shfl_sync(0xffffffffu, lbg, kg) > u3) break;
-            live &= ~(1u << kg);
-            const int pos = (blk * 32 + kg) * 32 + lane;
-            float lb = finf, ub = finf;
-            if (pos < n) seed_bounds<D>(r32[pos], ch, cl, rlo, rhi, wrh, wrl, lb, ub);
-            merge_smallest4(pos < n ? okey(ub) : 0xffffffffu, u0, u1, u2, u3);
+            const unsigned k1 = __reduce_min_sync(0xffffffffu, key);
+            const int g1 = __ffs(__ballot_sync(0xffffffffu, mine && key == k1)) - 1;
+            if (__shfl_sync(0xffffffffu, lbg, g1) > u3) break;
+            live &= ~(1u << g1);
+            const unsigned key2 = lane == g1 ? 0xffffffffu : key;
+            const unsigned k2 = __reduce_min_sync(0xffffffffu, key2);
+            int g2 = -1;
+            if (k2 != 0xffffffffu) {
+                g2 = __ffs(__ballot_sync(0xffffffffu, key2 == k2)) - 1;
+                if (__shfl_sync(0xffffffffu, lbg, g2) <= u3) live &= ~(1u << g2);
+                else g2 = -1;
+            }
+            const int p1 = (blk * 32 + g1) * 32 + lane;
+            const int p2 = g2 >= 0 ? (blk * 32 + g2) * 32 + lane : n;
+            const SeedRec32 q1 = p1 < n ? r32[p1] : zrec;
+            const SeedRec32 q2 = p2 < n ? r32[p2] : zrec;
+            float lb, ub1 = finf, ub2 = finf;
+            if (p1 < n) seed_bounds<D>(q1, ch, cl, rlo, rhi, wrh, wrl, lb, ub1);
+            if (p2 < n) seed_bounds<D>(q2, ch, cl, rlo, rhi, wrh, wrl, lb, ub2);
+            merge_smallest4(p1 < n ? okey(ub1) : 0xffffffffu, u0, u1, u2, u3);
+            if (g2 >= 0) merge_smallest4(p2 < n ? okey(ub2) : 0xffffffffu, u0, u1, u2, u3);
         }
     }
-    // pass 2: the list and T_excl
+    // pass 2: the list and T_excl (groups two at a time, records loaded together)
     const float T = u3;
     float tex = finf;
     int cnt = 0;
     int *out = slist + (size_t)sup * kSuperCap;
+    auto take = [&](const SeedRec32 &q, int pos) {
+        float lb = finf, ub = finf;
+        if (pos < n) seed_bounds<D>(q, ch, cl, rlo, rhi, wrh, wrl, lb, ub);
+        const bool cand = pos < n && lb <= T;
+        const unsigned cm = __ballot_sync(0xffffffffu, cand);
+        const int rank = __popc(cm & ((1u << lane) - 1u));
+        if (cand) {
+            if (cnt + rank < kSuperCap) out[cnt + rank] = pos;
+            else tex = fminf(tex, lb);  // beyond the capacity: excluded
+        } else if (pos < n) {
+            tex = fminf(tex, lb);
+        }
+        cnt += __popc(cm);
+    };
     for (int bi = 0; bi < n_blocks; ++bi) {
         const int blk = block_of(bi);
         const int grp = blk * 32 + lane;
@@ -712,21 +744,19 @@ __global__ void __launch_bounds__(256)
         tex = fminf(tex, in ? finf : lbg);
         unsigned todo = __ballot_sync(0xffffffffu, in);
         while (todo) {
-            const int kg = __ffs(todo) - 1;
+            const int ga = __ffs(todo) - 1;
             todo &= todo - 1u;
-            const int pos = (blk * 32 + kg) * 32 + lane;
-            float lb = finf, ub = finf;
-            if (pos < n) seed_bounds<D>(r32[pos], ch, cl, rlo, rhi, wrh, wrl, lb, ub);
-            const bool cand = pos < n && lb <= T;
-            const unsigned cm = __ballot_sync(0xffffffffu, cand);
-            const int rank = __popc(cm & ((1u << lane) - 1u));
-            if (cand) {
-                if (cnt + rank < kSuperCap) out[cnt + rank] = pos;
-                else tex = fminf(tex, lb);  // beyond the capacity: excluded
-            } else if (pos < n) {
-                tex = fminf(tex, lb);
+            int gb = -1;
+            if (todo) {
+                gb = __ffs(todo) - 1;
+                todo &= todo - 1u;
             }
-            cnt += __popc(cm);
+            const int pa = (blk * 32 + ga) * 32 + lane;
+            const int pb = gb >= 0 ? (blk * 32 + gb) * 32 + lane : n;
+            const SeedRec32 qa = pa < n ? r32[pa] : zrec;
+            const SeedRec32 qb = pb < n ? r32[pb] : zrec;
+            take(qa, pa);
+            if (gb >= 0) take(qb, pb);
         }
     }
     tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
@@ -770,17 +800,24 @@ __global__ void __launch_bounds__(256)
     }
     const int cntS = scount[sup];
     const int *sl = slist + (size_t)sup * kSuperCap;
-    // the tile's bounds of the super-tile's candidates: at most 8 rounds of 32
+    // the tile's bounds of the super-tile's candidates: at most 8 rounds of 32,
+    // taken two at a time (indices, then records, loaded together)
     float lbv[kSuperCap / 32];
     float u0 = finf, u1 = finf, u2 = finf, u3 = finf;
+    const SeedRec32 zrec{};
 #pragma unroll
-    for (int r = 0; r < kSuperCap / 32; ++r) {
-        lbv[r] = finf;
+    for (int r = 0; r < kSuperCap / 32; r += 2) {
+        lbv[r] = lbv[r + 1] = finf;
         if (r * 32 < cntS) {
-            const int e = r * 32 + lane;
-            float ub = finf;
-            if (e < cntS) seed_bounds<D>(r32[sl[e]], ch, cl, rlo, rhi, wrh, wrl, lbv[r], ub);
-            merge_smallest4(e < cntS ? okey(ub) : 0xffffffffu, u0, u1, u2, u3);
+            const int e0 = r * 32 + lane, e1 = e0 + 32;
+            const int i0 = e0 < cntS ? sl[e0] : -1, i1 = e1 < cntS ? sl[e1] : -1;
+            const SeedRec32 q0 = i0 >= 0 ? r32[i0] : zrec;
+            const SeedRec32 q1 = i1 >= 0 ? r32[i1] : zrec;
+            float ub0 = finf, ub1 = finf;
+            if (i0 >= 0) seed_bounds<D>(q0, ch, cl, rlo, rhi, wrh, wrl, lbv[r], ub0);
+            if (i1 >= 0) seed_bounds<D>(q1, ch, cl, rlo, rhi, wrh, wrl, lbv[r + 1], ub1);
+            merge_smallest4(i0 >= 0 ? okey(ub0) : 0xffffffffu, u0, u1, u2, u3);
+            if ((r + 1) * 32 < cntS) merge_smallest4(i1 >= 0 ? okey(ub1) : 0xffffffffu, u0, u1, u2, u3);
         }
     }
     const float T = u3;
@@ -1336,18 +1373,28 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     const SeedRec32 *rs = ws.sorted ? ws.recs32s : ws.recs32;
     const int ntz = D == 3 ? (int)(ntl / ((long long)ntx * nty)) : 0;
     const int naxis = ntx + nty + ntz;
-    tc_axis_kernel<D><<<(naxis + 255) / 256, 256, 0, st>>>(g, ntx, nty, ntz, tlo, ws.tc_axis);
+    // the per-axis table depends on the grid and the tiling only: recomputed when they change
+    const double key[12] = {(double)D,          (double)g.res[0], (double)g.res[1], (double)g.res[2],
+                            g.lo[0],            g.lo[1],          g.lo[2],          g.h[0],
+                            g.h[1],             g.h[2],           (double)tlo,      (double)win_hi(g)};
+    if (std::memcmp(key, ws.tc_axis_key, sizeof key) != 0) {
+        tc_axis_kernel<D><<<(naxis + 255) / 256, 256, 0, st>>>(g, ntx, nty, ntz, tlo, ws.tc_axis);
+        std::memcpy(ws.tc_axis_key, key, sizeof key);
+        ++ws.kernel_launches;
+    }
     if (pruned) {
         const SuperGeom sg{ntx, nty, ntz, tlo};
         const int nsup = ((ntx + 1) / 2) * ((nty + 1) / 2) * (D == 3 ? (ntz + 1) / 2 : 1);
         tc_super_kernel<D><<<(nsup * 32 + 255) / 256, 256, 0, st>>>(g, sg, nsup, n, rs, ws.groups,
                                                                     ws.sorted ? ws.scodes : nullptr, ws.tc_axis,
                                                                     ws.tc_slist, ws.tc_scount, ws.tc_stex, ws.sc);
+        ws.kernel_launches += 2;
         tc_list_kernel<D, KIND><<<(ntiles * 32 + 255) / 256, 256, 0, st>>>(
             g, sg, ntiles, n, rs, ws.sorted ? ws.perm : nullptr, ws.tc_axis, ws.tc_slist, ws.tc_scount, ws.tc_stex,
             ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.tc_bops, ws.sc);
     } else {
         const int pblocks = (int)((ntl * 32 + 255) / 256);
+        ws.kernel_launches += 1;
         tc_tile_kernel<D, KIND><<<pblocks, 256, 0, st>>>(
             g, ntx, nty, tlo, ntiles, n, rs, ws.groups, ws.sorted ? ws.scodes : nullptr,
             ws.sorted ? ws.perm : nullptr, n_chunks, ws.tc_centre, ws.tc_start, ws.tc_meta, ws.tc_texcl, nullptr,
@@ -1355,11 +1402,14 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     }
     // more than 114 KB of shared memory keeps one CTA (512 tensor-memory columns) per SM
     const size_t smem = std::max<size_t>(sizeof(TcShared<D, KIND>), 120 * 1024);
-    cudaError_t e = cudaFuncSetAttribute(assign_tc_kernel<D, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    int sms = 152;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ws.device) != cudaSuccess) sms = 152;
+    const unsigned bit = kAttrTcScore << ((D == 3 ? 2 : 0) + (KIND == tc::KIND_BF16 ? 1 : 0));
+    if (!(ws.attr_done & bit)) {
+        const cudaError_t e = cudaFuncSetAttribute(assign_tc_kernel<D, KIND>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ws.attr_done |= bit;
+    }
+    const int sms = ws.sms;
     const double hx = 0.5 * G::TX * g.h[0], hy = 0.5 * G::TY * g.h[1], hz = D == 3 ? 0.5 * G::TZ * g.h[2] : 0.0;
     TcArgs args;
     args.g = g;

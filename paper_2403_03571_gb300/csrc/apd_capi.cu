@@ -169,9 +169,9 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
                         (apd_stream_t)st) != 0)
             return APD_ERR_CUDA;
     }
-    ws.kernel_launches += weights_only ? 3 + (prec == APD_FP32 ? 0 : 1)
-                                       : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (prec == APD_FP32 ? 0 : 1) +
-                                             (step ? 1 : 0);
+    // the tensor-core launcher counts its pre-pass launches itself
+    ws.kernel_launches += (weights_only ? 3 : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (step ? 1 : 0)) -
+                          (empty ? 2 : 0);  // an empty slab launches neither scoring nor rescoring
     ws.last_pixels = win_pixels(g);
     ws.last_pairs = win_pixels(g) * (long long)n;
     return APD_OK;
@@ -431,11 +431,18 @@ struct Solver {
         int fails = 0;
         bool pending = false;  // a pushed pair whose test result is not read yet
         int p_slot = 0;
+        bool dir_ready = false;  // the last push also formed this direction's coefficients
         while (evals < max_evals) {
             const int hist_acc = std::min(hist + 1, history);
-            APD_TRY(cuda_ok(launch_lbfgs_direction(n, hist, newest, kHistCap, gamma, pending, hist_acc, p_slot,
-                                                   ws, st)));
-            ws.kernel_launches += 1;
+            if (dir_ready) {
+                APD_TRY(cuda_ok(launch_lbfgs_pdir(n, ws, st)));
+                ws.kernel_launches += 1;
+            } else {
+                APD_TRY(cuda_ok(launch_lbfgs_direction(n, hist, newest, kHistCap, gamma, pending, hist_acc, p_slot,
+                                                       ws, st)));
+                ws.kernel_launches += 2;
+            }
+            dir_ready = false;
             double t0 = 1.0;
             if (!pending && hist == 0) {
                 // first step (or after a reset): p = -grad f; take t0 ~ 1 / H_ii with the
@@ -476,8 +483,12 @@ struct Solver {
             fails = 0;
             ++iters;
             const int slot = (newest + 1) % kHistCap;
-            APD_TRY(cuda_ok(launch_lbfgs_push(n, slot, ws, st)));
+            // Gram entries with the pairs kept beside it if it is accepted, and the
+            // next direction's coefficients for either outcome of its curvature test
+            const int next_acc = std::min(hist + 1, history);
+            APD_TRY(cuda_ok(launch_lbfgs_push(n, slot, kHistCap, next_acc - 1, true, hist, next_acc, gamma, ws, st)));
             ws.kernel_launches += 1;
+            dir_ready = true;
             pending = true;
             p_slot = slot;
             std::swap(ws.W, ws.Wt);
@@ -573,6 +584,8 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     w.max_n = max_n;
     w.max_j = max_j;
     cudaGetDevice(&w.device);
+    if (cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, w.device) != cudaSuccess || w.sms < 1)
+        w.sms = 152;
     w.n_pad_max = ((max_n + kChunk - 1) / kChunk) * kChunk;
     w.hist_cap = kHistCap;
     const size_t K = (size_t)moment_width(dim);
@@ -620,7 +633,10 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.Wbest, (size_t)max_n * sizeof(double));
     alloc((void **)&w.S, (size_t)kHistCap * max_n * sizeof(double));
     alloc((void **)&w.Y, (size_t)kHistCap * max_n * sizeof(double));
-    alloc((void **)&w.alpha, kHistCap * sizeof(double));
+    alloc((void **)&w.gram, 2 * kHistCap * kHistCap * sizeof(double));
+    w.lb_rows = w.sms;
+    alloc((void **)&w.lb_part, (size_t)w.lb_rows * kLbfgsDots * sizeof(double));
+    alloc((void **)&w.lb_coef, sizeof(LbfgsCoef));
     alloc((void **)&w.rho, kHistCap * sizeof(double));
     alloc((void **)&w.X, (size_t)max_n * dim * sizeof(double));
     alloc((void **)&w.vbuf, (size_t)max_n * sizeof(double));
@@ -644,7 +660,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
     void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.tc_axis, w.tc_slist, w.tc_scount, w.tc_stex, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
-                    w.Wbest, w.S, w.Y, w.alpha, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
+                    w.Wbest, w.S, w.Y, w.gram, w.lb_part, w.lb_coef, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.sc_host) cudaFreeHost(w.sc_host);
@@ -722,6 +738,69 @@ int apd_assign(const apd_grid *grid, const apd_seeds *seeds, apd_precision preci
         APD_TRY(cuda_ok(launch_tie_gap(g, seeds->n, seeds->x, seeds->A, seeds->w, ws->w, tie_gap, st)));
         ws->w.kernel_launches += 1;
     }
+    return APD_OK;
+}
+
+int apd_lbfgs_check(int32_t n, int32_t hist, const double *S, const double *Y, const double *g, int32_t fused,
+                    double *p, double *gp) {
+    if (n < 1 || hist < 1 || hist > kHistCap - 1 || !S || !Y || !g || !p || !gp || (fused != 0 && fused != 1))
+        return APD_ERR_ARG;
+    Workspace w;
+    bool ok = true;
+    std::vector<void *> bufs;
+    auto alloc = [&](void **q, size_t bytes) {
+        if (ok && cudaMalloc(q, bytes) != cudaSuccess) ok = false;
+        if (ok) bufs.push_back(*q);
+    };
+    const size_t nb = (size_t)n * sizeof(double);
+    alloc((void **)&w.W, nb);
+    alloc((void **)&w.Wt, nb);
+    alloc((void **)&w.gf, nb);
+    alloc((void **)&w.gft, nb);
+    alloc((void **)&w.p, nb);
+    alloc((void **)&w.S, kHistCap * nb);
+    alloc((void **)&w.Y, kHistCap * nb);
+    alloc((void **)&w.rho, kHistCap * sizeof(double));
+    alloc((void **)&w.gram, 2 * kHistCap * kHistCap * sizeof(double));
+    cudaGetDevice(&w.device);
+    if (cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, w.device) != cudaSuccess || w.sms < 1)
+        w.sms = 152;
+    w.lb_rows = w.sms;
+    alloc((void **)&w.lb_part, (size_t)w.lb_rows * kLbfgsDots * sizeof(double));
+    alloc((void **)&w.lb_coef, sizeof(LbfgsCoef));
+    alloc((void **)&w.sc, sizeof(DevScalars));
+    cudaStream_t st = 0;
+    // pair k enters as W = 0, Wt = s_k, gf = 0, gft = y_k in slot k
+    if (ok) ok = cudaMemset(w.W, 0, nb) == cudaSuccess && cudaMemset(w.gf, 0, nb) == cudaSuccess &&
+                 cudaMemset(w.sc, 0, sizeof(DevScalars)) == cudaSuccess;
+    const int plain = fused ? hist - 1 : hist;
+    for (int k = 0; ok && k < plain; ++k) {
+        ok = cudaMemcpy(w.Wt, S + (size_t)k * n, nb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(w.gft, Y + (size_t)k * n, nb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             launch_lbfgs_push(n, k, kHistCap, k, false, 0, 0, 1.0, w, st) == cudaSuccess;
+    }
+    if (ok && !fused) {
+        // the newest pair is the pending one, taken by the direction kernels if it passed
+        ok = cudaMemcpy(w.gf, g, nb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             launch_lbfgs_direction(n, hist - 1, hist - 2 < 0 ? kHistCap - 1 : hist - 2, kHistCap, 1.0, true, hist,
+                                    hist - 1, w, st) == cudaSuccess;
+    } else if (ok) {
+        // the newest pair enters as W = 0, Wt = s, gft = g, gf = g - y (formed on the device),
+        // pushed with the direction for the gradient g; then gf and gft change places
+        ok = cudaMemcpy(w.Wt, S + (size_t)(hist - 1) * n, nb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(w.gft, g, nb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(w.p, Y + (size_t)(hist - 1) * n, nb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             launch_axpy(n, w.gft, -1.0, w.p, w.gf, st) == cudaSuccess &&
+             launch_lbfgs_push(n, hist - 1, kHistCap, hist - 1, true, hist - 1, hist, 1.0, w, st) == cudaSuccess;
+        std::swap(w.gf, w.gft);
+        if (ok) ok = launch_lbfgs_pdir(n, w, st) == cudaSuccess;
+    }
+    DevScalars h{};
+    if (ok) ok = cudaMemcpy(p, w.p, nb, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                 cudaMemcpy(&h, w.sc, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess;
+    for (void *q : bufs) cudaFree(q);
+    if (!ok) return APD_ERR_CUDA;
+    *gp = h.gp0;
     return APD_OK;
 }
 

@@ -79,7 +79,26 @@ struct DevScalars {
     int pair_ok;                        // the last pushed L-BFGS pair passed the curvature test
     long long rescored_total;
     unsigned int mask_count;            // boundary coarse pixels listed by the masked discretisation
+    unsigned int lbfgs_done;            // block counter of the L-BFGS kernels' last-block reductions
 };
+
+// Partial sums per block row of the L-BFGS dot-product kernels: the push's
+// 3 + 3 (cap - 1) Gram products and 2 + 2 (cap - 1) direction products, cap = 32.
+constexpr int kLbfgsDots = 160;
+
+// Coefficients of an L-BFGS direction p = -gamma g + sum_k (cy_k y_k + cs_k s_k)
+// over the pairs in slot[0..hist) (device; written by the direction's first kernel).
+struct LbfgsCoef {
+    int hist;
+    int slot[32];
+    double gamma;
+    double cy[32], cs[32];
+};
+
+// Bits of Workspace::attr_done: the dynamic shared-memory limit of these
+// kernels is raised once per workspace (a workspace lives on one device).
+constexpr unsigned kAttrFp32Score2 = 1u << 0, kAttrFp32Score3 = 1u << 1, kAttrMortonSort = 1u << 2;
+constexpr unsigned kAttrTcScore = 1u << 3;  // + 1 bit per (dimension, operand kind): 4 bits
 
 // Workspace (host struct; device pointers inside).
 struct Workspace {
@@ -87,6 +106,9 @@ struct Workspace {
     int max_n = 0;
     int64_t max_j = 0;
     int device = 0;
+    int sms = 152;                      // the device's SM count, read when the workspace is made
+    unsigned attr_done = 0;             // kAttr* bits: shared-memory attribute set on this device
+    int rescore_bps[2] = {0, 0};        // resident rescoring blocks per SM (2-D, 3-D)
     int n_pad_max = 0;
     SeedRec *recs = nullptr;            // [n_pad_max]
     SeedRec32 *recs32 = nullptr;        // [n_pad_max]
@@ -103,6 +125,7 @@ struct Workspace {
     int *tc_list = nullptr;             // [tc_tile_cap][tc_list_cap()] candidates
     uint8_t *tc_bops = nullptr;         // [tc_tile_cap] x tc_bops_bytes_per_tile(): stored seed operands
     float4 *tc_axis = nullptr;          // [3 tc_tile_cap] per-axis tile centres and pixel boxes
+    double tc_axis_key[12] = {};        // the grid and tiling tc_axis was computed for (all 0: none)
     int *tc_slist = nullptr;            // [tc_tile_cap][tc_super_cap()] candidates of the super-tiles
     int *tc_scount = nullptr;           // [tc_tile_cap] their counts
     float *tc_stex = nullptr;           // [tc_tile_cap] their bounds of the seeds left out
@@ -129,7 +152,10 @@ struct Workspace {
     double *W = nullptr, *Wt = nullptr, *p = nullptr, *gf = nullptr, *gft = nullptr;
     double *Wbest = nullptr;
     double *S = nullptr, *Y = nullptr;  // [hist_cap][max_n]
-    double *alpha = nullptr;            // [hist_cap]
+    double *gram = nullptr;             // [2][hist_cap][hist_cap] s_i.y_j, y_i.y_j of the stored pairs
+    double *lb_part = nullptr;          // [lb_rows][kLbfgsDots] per-block partial sums of the L-BFGS kernels
+    int lb_rows = 0;
+    LbfgsCoef *lb_coef = nullptr;       // the last direction's coefficients
     double *rho = nullptr;              // [hist_cap]
     double *X = nullptr;                // [max_n * dim] seed positions for Lloyd
     double *vbuf = nullptr;             // [max_n]
@@ -344,6 +370,13 @@ cudaError_t launch_axpy(int n, const double *a, double t, const double *b, doubl
 cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma, bool use_pair,
                                    int hist_acc, int newest_acc,
                                    Workspace &ws, cudaStream_t st);
-cudaError_t launch_lbfgs_push(int n, int slot, Workspace &ws, cudaStream_t st);
+// Push of the pair (Wt - W, gft - gf) into `slot` with its Gram entries against
+// the nprev slots before it; with dir, also the coefficients of the direction
+// for the gradient gft (taken with the pair if it passes the curvature test:
+// hist_acc pairs; else the hist pairs before it and gamma).  launch_lbfgs_pdir
+// then forms p from the last coefficients and the gradient ws.gf.
+cudaError_t launch_lbfgs_push(int n, int slot, int cap, int nprev, bool dir, int hist, int hist_acc, double gamma,
+                              Workspace &ws, cudaStream_t st);
+cudaError_t launch_lbfgs_pdir(int n, Workspace &ws, cudaStream_t st);
 
 }  // namespace apd

@@ -288,83 +288,294 @@ __global__ void axpy_kernel(const int n, const double *a, const double t, const 
     if (i < n) out[i] = a[i] + t * b[i];
 }
 
-// Two-loop recursion: p = -H gf with H0 = gamma I and the stored pairs
-// (s_k, y_k), newest at slot `newest`; also <gf, p> into sc->gp0.  With
-// use_pair, the pair just pushed (slot newest_acc) is used if it passed the
-// push kernel's curvature test: then hist_acc pairs and gamma = s.y / y.y.
-__global__ void __launch_bounds__(kRedThreads)
-    lbfgs_direction_kernel(const int n, int hist, int newest, const int cap, double gamma,
-                           const int use_pair, const int hist_acc, const int newest_acc,
-                           const double *__restrict__ S, const double *__restrict__ Y,
-                           const double *__restrict__ rho, double *__restrict__ alpha,
-                           const double *__restrict__ gf, double *__restrict__ p, DevScalars *sc) {
-    __shared__ double sh[33];
+// The L-BFGS pairs (s_k, y_k) live in slots of a ring of `cap`; beside them the
+// Gram entries gram[0][i][j] = s_i . y_j and gram[1][i][j] = y_i . y_j (slot
+// indices), filled by the push kernel for every pair of slots that can be in
+// the history together.  With them the two-loop recursion of the L-BFGS
+// direction (Nocedal and Wright, Algorithm 7.4) needs only the 2 hist dot
+// products s_k . g, y_k . g over the seeds; its scalar recursion then runs on
+// the Gram entries and p is assembled in one pass as
+//   p = -gamma g + sum_k gamma alpha_k y_k - sum_k (alpha_k - beta_k) s_k,
+// the same vector as the two-loop form in exact arithmetic.
+//
+// FP64 runs at a few operations per clock per SM and every dependent global
+// load costs about a microsecond of latency, so the dot products are spread
+// over up to one block per SM (32 seeds per block range, a warp per dot, all
+// of a block's loads in flight together) and the last block to finish reduces
+// the per-block sums in block order (deterministic) and runs the scalar part
+// in one warp, column by column (one shuffle per step).  The push kernel also
+// forms the next direction's dot products (for both outcomes of its curvature
+// test), so an accepted step costs two launches: push-and-coefficients, then p.
+constexpr int kLbfgsMax = 32;    // ring capacity the kernels below support
+static_assert(kLbfgsDots >= 5 + 5 * (kLbfgsMax - 1), "partial-sum rows hold the push's products");
+constexpr int kLbT = 1024;       // threads per block of the dot-product kernels
+constexpr int kLbR = 32;         // seeds per block range
+constexpr int kLbP = 64;         // threads per block of the p kernel
+
+// Partial dot products of one block over its ranges of 32 seeds (range r
+// starts at (blockIdx.x + r gridDim.x) 32): dot d (of nd) is sum_i f(d, i),
+// warp w takes the dots d = w mod 32.  part[blockIdx.x * kLbfgsDots + d]
+// receives the block's sums.
+template <class F>
+__device__ void block_partial_dots(const int nd, const int n, F f, double *part) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int d = wid; d < nd; d += kLbT / 32) {
+        double v = 0.0;
+        for (int r0 = blockIdx.x * kLbR; r0 < n; r0 += gridDim.x * kLbR)
+            if (r0 + lane < n) v += f(d, r0 + lane);
+        v = warp_sum(v);
+        if (lane == 0) part[(size_t)blockIdx.x * kLbfgsDots + d] = v;
+    }
+}
+
+// Called by every block after its partial sums are stored: true in the last
+// block to arrive (which then sees every block's sums).
+__device__ bool lbfgs_last_block(DevScalars *sc) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&sc->lbfgs_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// out[d] = sum over blocks (lane-strided, then the warp tree) of part[.][d], d < nd.
+__device__ void reduce_partials(const int nd, const double *part, double *out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int d = wid; d < nd; d += (int)(blockDim.x >> 5)) {
+        double v = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) v += *(const volatile double *)(part + (size_t)b * kLbfgsDots + d);
+        v = warp_sum(v);
+        if (lane == 0) out[d] = v;
+    }
+    __syncthreads();
+}
+
+// Shared state of the scalar part: the history's Gram entries (padded rows:
+// the column-wise steps read one column across the lanes), 1 / s.y, s_k . g,
+// y_k . g and the slots, k = 0 the newest pair.
+struct LbfgsScalars {
+    double sy[kLbfgsMax][kLbfgsMax + 1];  // s_k . y_j
+    double yy[kLbfgsMax][kLbfgsMax + 1];  // y_k . y_j
+    double rh[kLbfgsMax], sg[kLbfgsMax], yg[kLbfgsMax], al[kLbfgsMax];
+    int slot[kLbfgsMax];
+};
+
+// The last block's gather of the history's Gram entries and 1 / s.y.
+__device__ void load_gram(LbfgsScalars &L, const int hist, const int cap, const double *__restrict__ gram,
+                          const double *__restrict__ rho) {
+    for (int e = threadIdx.x; e < hist * hist; e += blockDim.x) {
+        const int k = e / hist, j = e % hist;
+        L.sy[k][j] = gram[(size_t)L.slot[k] * cap + L.slot[j]];
+        L.yy[k][j] = gram[(size_t)cap * cap + (size_t)L.slot[k] * cap + L.slot[j]];
+    }
+    for (int k = threadIdx.x; k < hist; k += blockDim.x) L.rh[k] = rho[L.slot[k]];
+    __syncthreads();
+}
+
+// The two-loop recursion on the Gram entries, by warp 0, column by column:
+// alpha_k = rho_k (s_k . g - sum_{j<k} alpha_j s_k . y_j)          (newest first)
+// c_k = alpha_k - rho_k (gamma y_k . q + sum_{j>k} c_j s_j . y_k)   (oldest first)
+// with y_k . q = y_k . g - sum_j alpha_j y_k . y_j; then the coefficients of p.
+__device__ void lbfgs_coefficients(LbfgsScalars &L, const int hist, const double gamma, LbfgsCoef *coef) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double t = 0.0, al = 0.0;
+    for (int k = 0; k < hist; ++k) {
+        double a = lane == k ? L.rh[k] * (L.sg[k] - t) : 0.0;
+        a = __shfl_sync(0xffffffffu, a, k);
+        if (lane == k) al = a;
+        if (lane > k && lane < hist) t += a * L.sy[lane][k];
+    }
+    if (lane < hist) L.al[lane] = al;
+    __syncwarp();
+    double yq = 0.0;
+    if (lane < hist) {
+        yq = L.yg[lane];
+        for (int j = 0; j < hist; ++j) yq -= L.al[j] * L.yy[lane][j];
+    }
+    double u = 0.0, c = 0.0;
+    for (int k = hist - 1; k >= 0; --k) {
+        double ck = lane == k ? al - L.rh[k] * (gamma * yq + u) : 0.0;
+        ck = __shfl_sync(0xffffffffu, ck, k);
+        if (lane == k) c = ck;
+        if (lane < k) u += ck * L.sy[k][lane];
+    }
+    // p = -gamma g + sum_k gamma alpha_k y_k - sum_k (alpha_k - beta_k) s_k
+    if (lane < hist) {
+        coef->cs[lane] = -c;
+        coef->cy[lane] = gamma * al;
+        coef->slot[lane] = L.slot[lane];
+    }
+    if (lane == 0) {
+        coef->hist = hist;
+        coef->gamma = gamma;
+    }
+}
+
+// Coefficients of p = -H gf (H0 = gamma I, the stored pairs newest at slot
+// `newest`).  With use_pair, the pair just pushed (slot newest_acc) is used if
+// it passed the push kernel's curvature test: then hist_acc pairs and
+// gamma = s.y / y.y.
+__global__ void __launch_bounds__(kLbT)
+    lbfgs_dots_kernel(const int n, int hist, int newest, const int cap, double gamma, const int use_pair,
+                      const int hist_acc, const int newest_acc, const double *__restrict__ S,
+                      const double *__restrict__ Y, const double *__restrict__ rho,
+                      const double *__restrict__ gram, const double *__restrict__ gf, double *part,
+                      LbfgsCoef *coef, DevScalars *sc) {
+    __shared__ LbfgsScalars L;
+    __shared__ double dots[2 * kLbfgsMax];
     if (use_pair && sc->pair_ok) {
         hist = hist_acc;
         newest = newest_acc;
         gamma = sc->sy / sc->yy;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = gf[i];
-    for (int k = 0; k < hist; ++k) {
-        const int idx = (newest - k + cap) % cap;
-        const double *s = S + (size_t)idx * n;
-        const double *y = Y + (size_t)idx * n;
-        double d = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) d += s[i] * p[i];
-        const double a = rho[idx] * block_sum(d, sh);
-        if (threadIdx.x == 0) alpha[idx] = a;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] -= a * y[i];
+    hist = min(hist, kLbfgsMax - 1);
+    for (int k = threadIdx.x; k < hist; k += blockDim.x) L.slot[k] = (newest - k + cap) % cap;
+    __syncthreads();
+    // dots 2k: s_k . g, 2k + 1: y_k . g
+    block_partial_dots(2 * hist, n, [&](int d, int i) {
+        return ((d & 1) ? Y : S)[(size_t)L.slot[d >> 1] * n + i] * gf[i];
+    }, part);
+    if (!lbfgs_last_block(sc)) return;
+    reduce_partials(2 * hist, part, dots);
+    for (int k = threadIdx.x; k < hist; k += blockDim.x) {
+        L.sg[k] = dots[2 * k];
+        L.yg[k] = dots[2 * k + 1];
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] *= gamma;
-    for (int k = hist - 1; k >= 0; --k) {
-        const int idx = (newest - k + cap) % cap;
-        const double *s = S + (size_t)idx * n;
-        const double *y = Y + (size_t)idx * n;
-        double d = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) d += y[i] * p[i];
-        const double bta = rho[idx] * block_sum(d, sh);
-        __syncthreads();
-        const double a = alpha[idx];
-        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] += s[i] * (a - bta);
-    }
-    double d = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        p[i] = -p[i];
-        d += gf[i] * p[i];
-    }
-    const double gp = block_sum(d, sh);
-    if (threadIdx.x == 0) sc->gp0 = gp;
+    load_gram(L, hist, cap, gram, rho);
+    lbfgs_coefficients(L, hist, gamma, coef);
+    if (threadIdx.x == 0) sc->lbfgs_done = 0u;
 }
 
-// Store the pair s = Wt - W, y = gft - gf in slot `slot`; sy, yy, ss into sc.
-__global__ void __launch_bounds__(kRedThreads)
-    lbfgs_push_kernel(const int n, const int slot, const double *__restrict__ W,
-                      const double *__restrict__ Wt, const double *__restrict__ gf,
-                      const double *__restrict__ gft, double *__restrict__ S,
-                      double *__restrict__ Y, double *__restrict__ rho, DevScalars *sc) {
-    __shared__ double sh[33];
-    double sy = 0.0, yy = 0.0, ss = 0.0;
+// p = -gamma gf + sum_k (cy_k y_k + cs_k s_k) and <gf, p> into sc->gp0.
+__global__ void __launch_bounds__(kLbP)
+    lbfgs_pdir_kernel(const int n, const LbfgsCoef *__restrict__ coef, const double *__restrict__ S,
+                      const double *__restrict__ Y, const double *__restrict__ gf, double *__restrict__ p,
+                      double *part, DevScalars *sc) {
+    __shared__ double cy[kLbfgsMax], cs[kLbfgsMax];
+    __shared__ int slot[kLbfgsMax];
+    __shared__ double red[kLbP / 32];
+    const int hist = coef->hist;
+    const double gamma = coef->gamma;
+    for (int k = threadIdx.x; k < hist; k += blockDim.x) {
+        cy[k] = coef->cy[k];
+        cs[k] = coef->cs[k];
+        slot[k] = coef->slot[k];
+    }
+    __syncthreads();
+    double d = 0.0;
+    for (int i = blockIdx.x * kLbP + threadIdx.x; i < n; i += gridDim.x * kLbP) {
+        const double g = gf[i];
+        double v = -gamma * g;
+#pragma unroll 8
+        for (int k = 0; k < hist; ++k) {
+            const size_t o = (size_t)slot[k] * n + i;
+            v += cy[k] * Y[o] + cs[k] * S[o];
+        }
+        p[i] = v;
+        d += g * v;
+    }
+    d = warp_sum(d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kLbP / 32; ++w) t += red[w];
+        part[(size_t)blockIdx.x * kLbfgsDots] = t;
+    }
+    if (!lbfgs_last_block(sc)) return;
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) t += *(const volatile double *)(part + (size_t)b * kLbfgsDots);
+        t = warp_sum(t);
+        if (threadIdx.x == 0) {
+            sc->gp0 = t;
+            sc->lbfgs_done = 0u;
+        }
+    }
+}
+
+// Store the pair s = Wt - W, y = gft - gf in slot `slot`; sy, yy, ss, the
+// curvature test and 1 / s.y into sc and rho; the Gram entries of the new pair
+// with itself and with the nprev pairs in the slots before it (slot - 1, ...,
+// slot - nprev, cyclically).  With dir, also the coefficients of the next
+// direction for the gradient gft: the pair taken (then min(hist + 1, hist_acc)
+// = hist_acc pairs newest first from `slot`, gamma = s.y / y.y) if it passes
+// the test, else the hist pairs before it with the given gamma.
+__global__ void __launch_bounds__(kLbT)
+    lbfgs_push_kernel(const int n, const int slot, const int cap, const int nprev,
+                      const double *__restrict__ W, const double *__restrict__ Wt,
+                      const double *__restrict__ gf, const double *__restrict__ gft, double *S,
+                      double *Y, double *__restrict__ rho, double *__restrict__ gram, double *part,
+                      DevScalars *sc, const int dir, const int hist, const int hist_acc, const double gamma,
+                      LbfgsCoef *coef) {
+    __shared__ LbfgsScalars L;
+    __shared__ double dots[kLbfgsDots];
     double *s = S + (size_t)slot * n;
     double *y = Y + (size_t)slot * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double si = Wt[i] - W[i];
-        const double yi = gft[i] - gf[i];
-        s[i] = si;
-        y[i] = yi;
-        sy += si * yi;
-        yy += yi * yi;
-        ss += si * si;
+    for (int i = (blockIdx.x + (int)(threadIdx.x >> 5) * gridDim.x) * kLbR + (threadIdx.x & 31); i < n;
+         i += gridDim.x * kLbT) {
+        s[i] = Wt[i] - W[i];
+        y[i] = gft[i] - gf[i];
     }
-    sy = block_sum(sy, sh);
-    yy = block_sum(yy, sh);
-    ss = block_sum(ss, sh);
+    __syncthreads();  // the block's global writes are visible to the block after the barrier
+    // dots 0..2: s.y, y.y, s.s; 3 + 3j..: s . y_j, s_j . y, y . y_j (j < np, slot j = slot - 1 - j);
+    // with dir, at o = 3 + 3 np: s . g, y . g, then s_j . g, y_j . g (j < nh)
+    const int np = min(nprev, kLbfgsMax - 1);
+    const int nh = dir ? min(hist, kLbfgsMax - 1) : 0;
+    const int o = 3 + 3 * np;
+    const int nd = o + (dir ? 2 + 2 * nh : 0);
+    block_partial_dots(nd, n, [&](int d, int i) {
+        if (d < 3) return d == 0 ? s[i] * y[i] : d == 1 ? y[i] * y[i] : s[i] * s[i];
+        if (d < o) {
+            const int j = (d - 3) / 3, c = (d - 3) % 3;
+            const size_t q = (size_t)((slot - 1 - j + 2 * cap) % cap) * n + i;
+            return c == 0 ? s[i] * Y[q] : c == 1 ? S[q] * y[i] : y[i] * Y[q];
+        }
+        if (d < o + 2) return (d == o ? s[i] : y[i]) * gft[i];
+        const int e = d - o - 2;
+        const size_t q = (size_t)((slot - 1 - (e >> 1) + 2 * cap) % cap) * n + i;
+        return ((e & 1) ? Y[q] : S[q]) * gft[i];
+    }, part);
+    if (!lbfgs_last_block(sc)) return;
+    reduce_partials(nd, part, dots);
+    double *gsy = gram, *gyy = gram + (size_t)cap * cap;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const int sj = (slot - 1 - j + 2 * cap) % cap;
+        gsy[(size_t)slot * cap + sj] = dots[3 + 3 * j];
+        gsy[(size_t)sj * cap + slot] = dots[4 + 3 * j];
+        gyy[(size_t)slot * cap + sj] = dots[5 + 3 * j];
+        gyy[(size_t)sj * cap + slot] = dots[5 + 3 * j];
+    }
+    const double vsy = dots[0], vyy = dots[1], vss = dots[2];
+    const bool ok = vsy > 1e-12 * sqrt(vss * vyy) && vyy > 0.0;
     if (threadIdx.x == 0) {
-        sc->sy = sy;
-        sc->yy = yy;
-        sc->ss = ss;
-        sc->pair_ok = (sy > 1e-12 * sqrt(ss * yy) && yy > 0.0) ? 1 : 0;
-        rho[slot] = sy != 0.0 ? 1.0 / sy : 0.0;
+        gsy[(size_t)slot * cap + slot] = vsy;
+        gyy[(size_t)slot * cap + slot] = vyy;
+        sc->sy = vsy;
+        sc->yy = vyy;
+        sc->ss = vss;
+        sc->pair_ok = ok ? 1 : 0;
+        rho[slot] = vsy != 0.0 ? 1.0 / vsy : 0.0;
     }
+    if (dir) {
+        __syncthreads();  // the Gram entries and rho written above, read by load_gram
+        const int h = ok ? min(hist_acc, kLbfgsMax - 1) : nh;
+        for (int k = threadIdx.x; k < h; k += blockDim.x) {
+            const int j = ok ? k - 1 : k;  // index among the previous pairs (-1: the new pair)
+            L.slot[k] = (slot - 1 - j + 2 * cap) % cap;
+            L.sg[k] = j < 0 ? dots[o] : dots[o + 2 + 2 * j];
+            L.yg[k] = j < 0 ? dots[o + 1] : dots[o + 3 + 2 * j];
+        }
+        __syncthreads();
+        load_gram(L, h, cap, gram, rho);
+        lbfgs_coefficients(L, h, ok ? vsy / vyy : gamma, coef);
+    }
+    if (threadIdx.x == 0) sc->lbfgs_done = 0u;
 }
 
 }  // namespace
@@ -402,12 +613,11 @@ cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const dou
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !ws.sorted) return e;
     const size_t smem = (size_t)m * sizeof(unsigned long long);
-    static bool attr = false;
-    if (!attr) {
+    if (!(ws.attr_done & kAttrMortonSort)) {
         e = cudaFuncSetAttribute(morton_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kSortMax * sizeof(unsigned long long)));
         if (e != cudaSuccess) return e;
-        attr = true;
+        ws.attr_done |= kAttrMortonSort;
     }
     morton_sort_kernel<<<1, 1024, smem, st>>>(n_pad, m, ws.codes, ws.scodes, ws.perm);
     gather_recs_kernel<<<blocks, 256, 0, st>>>(n_pad, ws.perm, ws.recs_tmp, ws.recs, ws.recs32, ws.recs32s);
@@ -473,21 +683,37 @@ cudaError_t launch_axpy(int n, const double *a, double t, const double *b, doubl
     return cudaGetLastError();
 }
 
-// One block runs the whole recursion; its 2 hist + 1 reductions are the cost,
-// so small problems use a smaller block (fewer warps per reduction).
-static int lbfgs_threads(int n) { return n <= 2048 ? 256 : kRedThreads; }
+// The dot-product kernels take one block per 32 seeds, the p kernel one per 64,
+// each at most one block per SM (the workspace's partial-sum rows).
+static int lbfgs_blocks(int n, int per, const Workspace &ws) {
+    return std::max(1, std::min((n + per - 1) / per, ws.lb_rows));
+}
 
 cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double gamma, bool use_pair,
                                    int hist_acc, int newest_acc, Workspace &ws, cudaStream_t st) {
-    lbfgs_direction_kernel<<<1, lbfgs_threads(n), 0, st>>>(n, hist, newest, cap, gamma, use_pair ? 1 : 0,
-                                                           hist_acc, newest_acc, ws.S, ws.Y, ws.rho, ws.alpha,
-                                                           ws.gf, ws.p, ws.sc);
+    if (cap > kLbfgsMax || hist > cap || hist_acc > cap || !ws.lb_part || !ws.lb_coef || ws.lb_rows < 1)
+        return cudaErrorInvalidValue;
+    lbfgs_dots_kernel<<<lbfgs_blocks(n, kLbR, ws), kLbT, 0, st>>>(n, hist, newest, cap, gamma, use_pair ? 1 : 0,
+                                                                  hist_acc, newest_acc, ws.S, ws.Y, ws.rho, ws.gram,
+                                                                  ws.gf, ws.lb_part, ws.lb_coef, ws.sc);
+    return launch_lbfgs_pdir(n, ws, st);
+}
+
+cudaError_t launch_lbfgs_pdir(int n, Workspace &ws, cudaStream_t st) {
+    if (!ws.lb_part || !ws.lb_coef || ws.lb_rows < 1) return cudaErrorInvalidValue;
+    lbfgs_pdir_kernel<<<lbfgs_blocks(n, kLbP, ws), kLbP, 0, st>>>(n, ws.lb_coef, ws.S, ws.Y, ws.gf, ws.p,
+                                                                  ws.lb_part, ws.sc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbfgs_push(int n, int slot, Workspace &ws, cudaStream_t st) {
-    lbfgs_push_kernel<<<1, lbfgs_threads(n), 0, st>>>(n, slot, ws.W, ws.Wt, ws.gf, ws.gft, ws.S, ws.Y,
-                                                 ws.rho, ws.sc);
+cudaError_t launch_lbfgs_push(int n, int slot, int cap, int nprev, bool dir, int hist, int hist_acc, double gamma,
+                              Workspace &ws, cudaStream_t st) {
+    if (cap > kLbfgsMax || nprev >= cap || hist >= cap || hist_acc >= cap || !ws.lb_part || !ws.lb_coef ||
+        !ws.gram || ws.lb_rows < 1)
+        return cudaErrorInvalidValue;
+    lbfgs_push_kernel<<<lbfgs_blocks(n, kLbR, ws), kLbT, 0, st>>>(n, slot, cap, nprev, ws.W, ws.Wt, ws.gf, ws.gft,
+                                                                  ws.S, ws.Y, ws.rho, ws.gram, ws.lb_part, ws.sc,
+                                                                  dir ? 1 : 0, hist, hist_acc, gamma, ws.lb_coef);
     return cudaGetLastError();
 }
 

@@ -245,8 +245,7 @@ cudaError_t launch_masked_refine(const GridDev &gc, const GridDev &gf, int r, in
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&ws.sc->mask_count, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    static int sms = 0;
-    if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ws.device) != cudaSuccess) sms = 152;
+    const int sms = ws.sms;
     const int mblocks = (int)std::min<long long>((gc.J + kMaskThreads - 1) / kMaskThreads, (long long)sms * 8);
     if (gc.dim == 3)
         mask_kernel<3><<<mblocks, kMaskThreads, 0, st>>>(gc, (unsigned long long)r, n, coarse_labels, ws.flags,

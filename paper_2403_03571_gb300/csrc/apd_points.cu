@@ -130,8 +130,7 @@ cudaError_t launch_points_assign(int dim, long long count, const double *y, cons
     const int pb = (n + 255) / 256;
     if (dim == 3) points_prep_kernel<3><<<pb, 256, 0, st>>>(n, x, A, w, ws.recs32, ws.sc);
     else points_prep_kernel<2><<<pb, 256, 0, st>>>(n, x, A, w, ws.recs32, ws.sc);
-    static int sms = 0;
-    if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ws.device) != cudaSuccess) sms = 152;
+    const int sms = ws.sms;
     const long long want = (count + kPtThreads - 1) / kPtThreads;
     const int blocks = (int)std::min<long long>(want, (long long)sms * 8);
     if (dim == 3)

@@ -170,6 +170,11 @@ def test_argument_errors_before_cuda(lib):
     lib.apd_warmstart_destroy(None)
     assert lib.apd_tensor_core_check(0, 3, ctypes.byref(ctypes.c_int32()),
                                      ctypes.byref(ctypes.c_float())) == capi.APD_ERR_ARG
+    gp = ctypes.c_double()
+    assert lib.apd_lbfgs_check(4, 0, None, None, None, 0, None, ctypes.byref(gp)) == capi.APD_ERR_ARG
+    assert lib.apd_lbfgs_check(4, 32, None, None, None, 0, None, ctypes.byref(gp)) == capi.APD_ERR_ARG
+    assert lib.apd_lbfgs_check(0, 1, None, None, None, 1, None, ctypes.byref(gp)) == capi.APD_ERR_ARG
+    assert lib.apd_lbfgs_check(4, 1, None, None, None, 2, None, ctypes.byref(gp)) == capi.APD_ERR_ARG
 
 
 def test_masked_argument_errors_before_cuda(lib):
