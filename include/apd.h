@@ -111,6 +111,16 @@ void apd_workspace_destroy(apd_workspace *ws);
  * pruning.  Applies to every later scoring call on the workspace. */
 int apd_workspace_set_pruning(apd_workspace *ws, int32_t enable);
 
+/* Weight solves (Algorithm 2, and every solve inside the Lloyd, coarse-to-fine
+ * and refining entry points) replay each evaluation after a solve's first from
+ * a CUDA graph captured on first use: trial weights, scoring, rescoring,
+ * moments, the dual of eqs. (2.7)-(2.8) and the read-back of its scalars, with
+ * only the trial step changing between replays.  Results are the same with and
+ * without graphs; a sharded workspace never uses them.  enable = 0 switches
+ * them off for this workspace (default on).  Returns APD_ERR_ARG for a null
+ * workspace. */
+int apd_workspace_set_graphs(apd_workspace *ws, int32_t enable);
+
 /* Poll limit of the bounded shared-memory barrier waits of the FP32 scoring
  * kernel on this workspace (each poll sleeps at most ~20 us; default 65536,
  * about 1.3 s).  polls >= 0 sets the limit, polls < 0 restores the default.

@@ -46,6 +46,7 @@ EXPORTED = (
     "apd_points_moments", "apd_points_dual_value_grad", "apd_refine_next_grid",
     "apd_masked_moments", "apd_masked_dual_value_grad", "apd_workspace_set_wait_limit",
     "apd_shard_range", "apd_cell_moments_slab", "apd_workspace_set_shard", "apd_lbfgs_check",
+    "apd_workspace_set_graphs",
 )
 
 
@@ -127,6 +128,7 @@ def load(path: Optional[str] = None):
     L.apd_last_stats.argtypes = [_vp, _P(ApdEvalStats), _vp]
     L.apd_assign.argtypes = [_P(ApdGrid), _P(ApdSeeds), ctypes.c_int32, _vp, _vp, _vp, _vp]
     L.apd_workspace_set_wait_limit.argtypes = [_vp, ctypes.c_int64]
+    L.apd_workspace_set_graphs.argtypes = [_vp, ctypes.c_int32]
     L.apd_shard_range.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32),
                                   _P(ctypes.c_int32)]
     L.apd_cell_moments_slab.argtypes = [_P(ApdGrid), ctypes.c_int32, ctypes.c_int32, _P(ApdSeeds), ctypes.c_int32,
@@ -296,6 +298,10 @@ class Workspace:
     def set_wait_limit(self, polls: int = -1):
         """Poll limit of the FP32 scoring kernel's bounded waits (-1: the default)."""
         _check(load().apd_workspace_set_wait_limit(self.handle, int(polls)), "apd_workspace_set_wait_limit")
+
+    def set_graphs(self, enable: bool = True):
+        """Replay the weight solves' evaluations from captured CUDA graphs (default on)."""
+        _check(load().apd_workspace_set_graphs(self.handle, int(bool(enable))), "apd_workspace_set_graphs")
 
     def profile(self, enable: bool = True):
         _check(load().apd_profile_enable(self.handle, int(bool(enable))), "apd_profile_enable")

@@ -1359,6 +1359,22 @@ void tile_grid(const GridDev &g, int &ntx, int &nty, int &tlo, long long &ntiles
     }
 }
 
+template <int D>
+cudaError_t ensure_axis(const GridDev &g, int ntx, int nty, int ntz, int tlo, Workspace &ws, cudaStream_t st) {
+    const double key[12] = {(double)D,          (double)g.res[0], (double)g.res[1], (double)g.res[2],
+                            g.lo[0],            g.lo[1],          g.lo[2],          g.h[0],
+                            g.h[1],             g.h[2],           (double)tlo,      (double)win_hi(g)};
+    if (std::memcmp(key, ws.tc_axis_key, sizeof key) == 0) return cudaSuccess;
+    const int naxis = ntx + nty + ntz;
+    tc_axis_kernel<D><<<(naxis + 255) / 256, 256, 0, st>>>(g, ntx, nty, ntz, tlo, ws.tc_axis);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        std::memcpy(ws.tc_axis_key, key, sizeof key);
+        ++ws.kernel_launches;
+    }
+    return e;
+}
+
 template <int D, int KIND>
 cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels, unsigned long long *gmom,
                         cudaStream_t st) {
@@ -1372,15 +1388,11 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     const bool pruned = ws.prune;
     const SeedRec32 *rs = ws.sorted ? ws.recs32s : ws.recs32;
     const int ntz = D == 3 ? (int)(ntl / ((long long)ntx * nty)) : 0;
-    const int naxis = ntx + nty + ntz;
-    // the per-axis table depends on the grid and the tiling only: recomputed when they change
-    const double key[12] = {(double)D,          (double)g.res[0], (double)g.res[1], (double)g.res[2],
-                            g.lo[0],            g.lo[1],          g.lo[2],          g.h[0],
-                            g.h[1],             g.h[2],           (double)tlo,      (double)win_hi(g)};
-    if (std::memcmp(key, ws.tc_axis_key, sizeof key) != 0) {
-        tc_axis_kernel<D><<<(naxis + 255) / 256, 256, 0, st>>>(g, ntx, nty, ntz, tlo, ws.tc_axis);
-        std::memcpy(ws.tc_axis_key, key, sizeof key);
-        ++ws.kernel_launches;
+    // the per-axis table depends on the grid and the tiling only: recomputed when
+    // they change (a graph capture leaves it to the caller, before every replay)
+    if (!ws.capturing) {
+        const cudaError_t e = ensure_axis<D>(g, ntx, nty, ntz, tlo, ws, st);
+        if (e != cudaSuccess) return e;
     }
     if (pruned) {
         const SuperGeom sg{ntx, nty, ntz, tlo};
@@ -1456,6 +1468,19 @@ cudaError_t launch_assign_tc(const GridDev &g, int n, Workspace &ws, int32_t *la
                                      : launch_tc_t<3, tc::KIND_BF16>(g, n, ws, labels, moments, st);
     return kind == tc::KIND_TF32 ? launch_tc_t<2, tc::KIND_TF32>(g, n, ws, labels, moments, st)
                                  : launch_tc_t<2, tc::KIND_BF16>(g, n, ws, labels, moments, st);
+}
+
+cudaError_t launch_tc_axis(const GridDev &g, Workspace &ws, cudaStream_t st) {
+    int ntx = 0, nty = 0, tlo = 0;
+    long long ntl = 0;
+    if (g.dim == 3) {
+        tile_grid<3>(g, ntx, nty, tlo, ntl);
+        if (ntl > ws.tc_tile_cap) return cudaSuccess;  // scored by the FP32 kernel
+        return ensure_axis<3>(g, ntx, nty, (int)(ntl / ((long long)ntx * nty)), tlo, ws, st);
+    }
+    tile_grid<2>(g, ntx, nty, tlo, ntl);
+    if (ntl > ws.tc_tile_cap) return cudaSuccess;
+    return ensure_axis<2>(g, ntx, nty, 0, tlo, ws, st);
 }
 
 long long tc_tile_count(const GridDev &g) {

@@ -111,6 +111,16 @@ struct TrialStep {
     const double *p;
 };
 
+constexpr size_t kGraphCap = 16;  // evaluation graphs kept per workspace
+
+void destroy_graph(EvalGraph &e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    if (e.e0) cudaEventDestroy(e.e0);
+    if (e.e1) cudaEventDestroy(e.e1);
+    e = EvalGraph();
+}
+
 // Queues one pass of scoring + rescoring + moments at weights w.  With
 // weights_only the records of the previous pass (same x, A, n) are reused and
 // only the weights change; with a step, w (device, n) is first set to
@@ -141,7 +151,12 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
         APD_TRY(cuda_ok(launch_group_bounds(n, ws, st)));
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ws.profiling) {
+    if (ws.profiling && ws.capturing) {
+        // the graph's own events; the replay reads them after its synchronisation
+        e0 = ws.cap_e0;
+        e1 = ws.cap_e1;
+        APD_TRY(cuda_ok(cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal)));
+    } else if (ws.profiling) {
         while (ws.ev.size() < ws.ev_used + 2) {
             cudaEvent_t e;
             APD_TRY(cuda_ok(cudaEventCreate(&e)));
@@ -160,7 +175,8 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
         APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
     else
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
-    if (e1) APD_TRY(cuda_ok(cudaEventRecord(e1, st)));
+    if (e1) APD_TRY(cuda_ok(ws.capturing ? cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal)
+                                         : cudaEventRecord(e1, st)));
     if (!empty) APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
     if (sharded) {
         // every rank's slab moments, summed, before anything reads them
@@ -216,16 +232,141 @@ struct Solver {
 
     // Evaluate at Wp; gf_out receives grad f = -(v - |P| m); pdir (nullable) for <grad f, p>.
     // With a step, Wp (device, n) is first set to step->W + step->t step->p.
+    // The launches of one evaluation at weights Wp (a trial step when given),
+    // queued on stream s: scoring, rescoring, moments, dual, scalars read back.
+    int enqueue_eval(const double *Wp, double *gf_out, const double *pdir, const TrialStep *step,
+                     cudaStream_t s) {
+        // the records' positions and matrices are built once per solve
+        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, s, geometry_ready, step));
+        APD_TRY(cuda_ok(launch_dual(g, n, x, A, Wp, v, pdir, ws.moments, ws, nullptr, ws.grad, gf_out,
+                                    nullptr, s)));
+        ws.kernel_launches += 1;
+        return cuda_ok(cudaMemcpyAsync(ws.sc_host, ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    }
+
+    // A weights-only evaluation replayed from a captured graph (captured on
+    // first use of its arguments); eg stays null where the evaluation is not
+    // graphed (sharded workspaces, graphs switched off, a refused capture).
+    int graph_eval(const double *Wp, double *gf_out, const double *pdir, const TrialStep *step, EvalGraph *&eg) {
+        eg = nullptr;
+        if (!ws.graphs || !geometry_ready || ws.shard_world > 1) return APD_OK;
+        struct Key {
+            int dim, res[3], kz0, kz1, n, prec, prune, sorted, profiling, has_step;
+            uint32_t wait_limit, pad;
+            double lo[3], h[3];
+            const void *ptr[9];
+        } k;
+        std::memset(&k, 0, sizeof k);
+        k.dim = g.dim;
+        for (int a = 0; a < 3; ++a) {
+            k.res[a] = g.res[a];
+            k.lo[a] = g.lo[a];
+            k.h[a] = g.h[a];
+        }
+        k.kz0 = g.kz0;
+        k.kz1 = g.kz1;
+        k.n = n;
+        k.prec = (int)prec;
+        k.prune = ws.prune ? 1 : 0;
+        k.sorted = ws.sorted ? 1 : 0;
+        k.profiling = ws.profiling ? 1 : 0;
+        k.has_step = step ? 1 : 0;
+        k.wait_limit = ws.wait_limit;
+        const void *ptrs[9] = {x, A, v, Wp, gf_out, pdir, step ? step->W : nullptr, step ? step->p : nullptr,
+                               ws.moments};
+        std::memcpy(k.ptr, ptrs, sizeof ptrs);
+        const unsigned char *kb = reinterpret_cast<const unsigned char *>(&k);
+        for (EvalGraph &e : ws.graph_cache)
+            if (e.key.size() == sizeof k && std::memcmp(e.key.data(), kb, sizeof k) == 0) {
+                if (e.failed) return APD_OK;
+                eg = &e;
+                break;
+            }
+        if (!eg) {
+            EvalGraph e;
+            e.key.assign(kb, kb + sizeof k);
+            if (!ws.cap_stream && cudaStreamCreateWithFlags(&ws.cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return APD_ERR_CUDA;
+            if (ws.profiling &&
+                (cudaEventCreate(&e.e0) != cudaSuccess || cudaEventCreate(&e.e1) != cudaSuccess))
+                return APD_ERR_CUDA;
+            const int64_t kl0 = ws.kernel_launches;
+            ws.capturing = true;
+            ws.cap_e0 = e.e0;
+            ws.cap_e1 = e.e1;
+            int rc = cuda_ok(cudaStreamBeginCapture(ws.cap_stream, cudaStreamCaptureModeThreadLocal));
+            if (rc == APD_OK) {
+                rc = enqueue_eval(Wp, gf_out, pdir, step, ws.cap_stream);
+                cudaGraph_t gr = nullptr;
+                const cudaError_t ce = cudaStreamEndCapture(ws.cap_stream, &gr);
+                if (rc == APD_OK && ce == cudaSuccess && gr &&
+                    cudaGraphInstantiate(&e.exec, gr, 0ull) == cudaSuccess) {
+                    e.graph = gr;
+                } else {
+                    if (gr) cudaGraphDestroy(gr);
+                    e.failed = true;
+                }
+            } else {
+                e.failed = true;
+            }
+            ws.capturing = false;
+            cudaGetLastError();  // a refused capture leaves no error behind
+            e.launches = ws.kernel_launches - kl0;
+            ws.kernel_launches = kl0;
+            e.pixels = ws.last_pixels;
+            e.pairs = ws.last_pairs;
+            if (rc != APD_OK && rc != APD_ERR_CUDA) return rc;  // an argument error, as without a graph
+            if (!e.failed && step) {
+                size_t nn = 0;
+                cudaGraphGetNodes(e.graph, nullptr, &nn);
+                std::vector<cudaGraphNode_t> nodes(nn);
+                if (nn) cudaGraphGetNodes(e.graph, nodes.data(), &nn);
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType ty;
+                    cudaKernelNodeParams kp{};
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel &&
+                        cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess && kp.func == eval_begin_kernel_fn())
+                        e.begin = nd;
+                }
+                if (!e.begin) e.failed = true;
+            }
+            if (ws.graph_cache.size() >= kGraphCap) {  // the least recently used one goes
+                size_t old = 0;
+                for (size_t i = 1; i < ws.graph_cache.size(); ++i)
+                    if (ws.graph_cache[i].used < ws.graph_cache[old].used) old = i;
+                destroy_graph(ws.graph_cache[old]);
+                ws.graph_cache.erase(ws.graph_cache.begin() + (long)old);
+            }
+            ws.graph_cache.push_back(e);
+            if (ws.graph_cache.back().failed) return APD_OK;
+            eg = &ws.graph_cache.back();
+        }
+        eg->used = ++ws.graph_clock;
+        if (prec != APD_FP32) APD_TRY(cuda_ok(launch_tc_axis(g, ws, st)));
+        if (step)
+            APD_TRY(cuda_ok(set_eval_begin_node(eg->exec, eg->begin, n, step->W, step->t, step->p,
+                                                const_cast<double *>(Wp), ws.moments, ws)));
+        APD_TRY(cuda_ok(cudaGraphLaunch(eg->exec, st)));
+        ws.kernel_launches += eg->launches;
+        ws.last_pixels = eg->pixels;
+        ws.last_pairs = eg->pairs;
+        return APD_OK;
+    }
+
     int eval(const double *Wp, double *gf_out, const double *pdir, double &f, double &dphi,
              double &err, const TrialStep *step = nullptr) {
-        // the records' positions and matrices are built once per solve
-        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, st, geometry_ready, step));
+        EvalGraph *eg = nullptr;
+        APD_TRY(graph_eval(Wp, gf_out, pdir, step, eg));
+        if (!eg) APD_TRY(enqueue_eval(Wp, gf_out, pdir, step, st));
         geometry_ready = true;
-        APD_TRY(cuda_ok(launch_dual(g, n, x, A, Wp, v, pdir, ws.moments, ws, nullptr, ws.grad, gf_out,
-                                    nullptr, st)));
-        ws.kernel_launches += 1;
-        APD_TRY(cuda_ok(cudaMemcpyAsync(ws.sc_host, ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st)));
         APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+        if (eg && eg->e0 && ws.profiling) {
+            float ms = 0.f;
+            APD_TRY(cuda_ok(cudaEventElapsedTime(&ms, eg->e0, eg->e1)));
+            ws.prof_ms_graph += ms;
+            ws.prof_n_graph += 1;
+            ws.prof_pairs += eg->pairs;
+        }
         ++evals;
         const DevScalars &h = *ws.sc_host;
         rescored += h.flag_count;
@@ -659,6 +800,8 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (!ws) return;
     Workspace &w = ws->w;
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
+    for (EvalGraph &e : w.graph_cache) destroy_graph(e);
+    if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.tc_axis, w.tc_slist, w.tc_scount, w.tc_stex, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.gram, w.lb_part, w.lb_coef, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
     for (void *p : ptrs)
@@ -699,8 +842,10 @@ int apd_profile_read(apd_workspace *ws, double *assign_ms, int64_t *launches, in
         APD_TRY(cuda_ok(cudaEventElapsedTime(&ms, w.ev[k], w.ev[k + 1])));
         total += ms;
     }
-    *assign_ms = total;
-    *launches = (int64_t)(w.ev_used / 2);
+    *assign_ms = total + w.prof_ms_graph;
+    *launches = (int64_t)(w.ev_used / 2) + w.prof_n_graph;
+    w.prof_ms_graph = 0.0;
+    w.prof_n_graph = 0;
     *pairs = w.prof_pairs;
     *kernel_launches = w.kernel_launches;
     w.ev_used = 0;
@@ -801,6 +946,12 @@ int apd_lbfgs_check(int32_t n, int32_t hist, const double *S, const double *Y, c
     for (void *q : bufs) cudaFree(q);
     if (!ok) return APD_ERR_CUDA;
     *gp = h.gp0;
+    return APD_OK;
+}
+
+int apd_workspace_set_graphs(apd_workspace *ws, int32_t enable) {
+    if (!ws) return APD_ERR_ARG;
+    ws->w.graphs = enable != 0;
     return APD_OK;
 }
 

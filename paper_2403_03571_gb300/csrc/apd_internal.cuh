@@ -100,6 +100,20 @@ struct LbfgsCoef {
 constexpr unsigned kAttrFp32Score2 = 1u << 0, kAttrFp32Score3 = 1u << 1, kAttrMortonSort = 1u << 2;
 constexpr unsigned kAttrTcScore = 1u << 3;  // + 1 bit per (dimension, operand kind): 4 bits
 
+// One evaluation of a weight solve (trial weights, scoring, rescoring, dual,
+// read-back of the device scalars) captured as a CUDA graph and replayed with
+// a new trial step t.  The key holds every argument the captured launches take.
+struct EvalGraph {
+    std::vector<unsigned char> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t begin = nullptr;  // the eval_begin kernel node (null: no trial step)
+    int64_t launches = 0, pixels = 0, pairs = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;  // around the scoring stage (profiling)
+    uint64_t used = 0;
+    bool failed = false;  // capture refused: this key runs without a graph
+};
+
 // Workspace (host struct; device pointers inside).
 struct Workspace {
     int dim = 0;
@@ -167,6 +181,15 @@ struct Workspace {
     std::vector<cudaEvent_t> ev;  // 2 per recorded launch
     size_t ev_used = 0;
     int64_t prof_pairs = 0;
+    double prof_ms_graph = 0.0;   // scoring-stage time of replayed evaluation graphs
+    int64_t prof_n_graph = 0;
+    // evaluation graphs of the weight solve
+    bool graphs = true;
+    bool capturing = false;       // launches go into a stream capture
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t cap_e0 = nullptr, cap_e1 = nullptr;
+    std::vector<EvalGraph> graph_cache;
+    uint64_t graph_clock = 0;
     int64_t kernel_launches = 0;  // every kernel launched with this workspace
 };
 
@@ -378,5 +401,12 @@ cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double 
 cudaError_t launch_lbfgs_push(int n, int slot, int cap, int nprev, bool dir, int hist, int hist_acc, double gamma,
                               Workspace &ws, cudaStream_t st);
 cudaError_t launch_lbfgs_pdir(int n, Workspace &ws, cudaStream_t st);
+// graph support: the eval_begin kernel (to find its node), its launch written
+// into an instantiated graph's node, and the tensor-core per-axis table
+// brought up to date for a grid outside any capture
+const void *eval_begin_kernel_fn();
+cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int n, const double *W0, double t,
+                                const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws);
+cudaError_t launch_tc_axis(const GridDev &g, Workspace &ws, cudaStream_t st);
 
 }  // namespace apd

@@ -596,6 +596,32 @@ cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *p
     return cudaGetLastError();
 }
 
+const void *eval_begin_kernel_fn() { return reinterpret_cast<const void *>(eval_begin_kernel); }
+
+// The same launch as launch_eval_begin, written into a kernel node of an
+// instantiated graph (only the trial step t changes between replays).
+cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int n, const double *W0, double t,
+                                const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws) {
+    int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
+    long long n_mom = (long long)n * moment_width(ws.dim);
+    const int32_t *perm = ws.sorted ? ws.perm : nullptr;
+    SeedRec *recs = ws.recs;
+    SeedRec32 *recs32 = ws.recs32, *recs32s = ws.sorted ? ws.recs32s : nullptr;
+    GroupBound *groups = ws.groups;
+    double *part = ws.part;
+    DevScalars *sc = ws.sc;
+    void *args[] = {&n,    &n_pad,  &n_mom,   &W0,     &t,   &pdir, &Wt, &perm,
+                    &recs, &recs32, &recs32s, &groups, &mom, &part, &sc};
+    cudaKernelNodeParams p{};
+    p.func = reinterpret_cast<void *>(eval_begin_kernel);
+    p.gridDim = dim3(n_pad / 256);
+    p.blockDim = dim3(256);
+    p.sharedMemBytes = 0;
+    p.kernelParams = args;
+    p.extra = nullptr;
+    return cudaGraphExecKernelNodeSetParams(exec, node, &p);
+}
+
 cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const double *A,
                              const double *w, Workspace &ws, cudaStream_t st) {
     const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
