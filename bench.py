@@ -39,12 +39,16 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "3d_n1000_256cube_lloyd5"
 L2_FLUSH_BYTES = 512 << 20
+CARRY_HISTORY = False  # set from --carry-history
+
+
 def chosen_multires(capi):
     """Coarse-to-fine settings of the chosen forms: grid factor 2, coarse solves to
     1.5 % volume error or 200 evaluations (timed on both workloads: 3D coarse
     solves converge well before the cap; in 2D, where the smallest cells cannot
-    reach 1.5 % on the coarse grid, a cap of 80 cost 40 % more time)."""
-    return capi.multires_opts(factor=2, coarse_eps=0.015, coarse_max_evals=200)
+    reach 1.5 % on the coarse grid, a cap of 80 cost 40 % more time); with
+    CARRY_HISTORY the coarse solves of a Lloyd run continue one L-BFGS history."""
+    return capi.multires_opts(factor=2, coarse_eps=0.015, coarse_max_evals=200, carry_history=CARRY_HISTORY)
 
 
 def parse():
@@ -60,6 +64,9 @@ def parse():
     ap.add_argument("--precision", default="tc_tf32", choices=["fp32", "tc_tf32", "tc_bf16"],
                     help="scoring arithmetic of the chosen form (the same pipeline with the other "
                          "arithmetic, and the plain FP32 form, are always timed too)")
+    ap.add_argument("--carry-history", type=int, default=0,
+                    help="chosen form: the coarse solves of a Lloyd run continue one L-BFGS history (1) "
+                         "or start afresh (0)")
     ap.add_argument("--assign-res", type=int, default=0,
                     help="--mode assign: grid resolution per axis in place of the workload's")
     ap.add_argument("--assign-prune", action="store_true",
@@ -323,18 +330,19 @@ def kernel_source_hash(kind):
 
 
 def ncu_counters(kernel, workload, pruned, kind):
-    """Per-launch counters of one scoring launch (DRAM bytes read + written,
-    warp instructions executed) from the committed summary of an ncu capture,
-    or None when the kernel's code has changed since the capture."""
+    """Counters of one captured scoring launch (DRAM bytes read + written, warp
+    instructions executed, and the N x J pairs that launch covered) from the
+    committed summary of an ncu capture, or None when the kernel's code has
+    changed since the capture."""
     if not os.path.exists(COUNTERS_FILE):
         return None
     want = kernel_source_hash(kind)
     with open(COUNTERS_FILE) as f:
         for line in f:
             p = line.split()
-            if len(p) >= 6 and not line.startswith("#") and p[0] == kernel and p[1] == workload \
+            if len(p) >= 7 and not line.startswith("#") and p[0] == kernel and p[1] == workload \
                     and p[2] == ("pruned" if pruned else "dense") and p[3] == want:
-                return {"dram_bytes": int(p[4]), "warp_instructions": int(p[5])}
+                return {"dram_bytes": int(p[4]), "warp_instructions": int(p[5]), "pairs": int(p[6])}
     return None
 
 
@@ -461,9 +469,9 @@ def measure_form(args, ctx, precision, chosen_start=False):
 
 
 def roofline_block(form, dim, sms, workload):
-    """Roofline of the scoring stage (launch_ms: the stage's device time per
-    evaluation from the library's events; for the tensor-core form it includes the
-    candidate pre-pass).
+    """Roofline of the scoring kernel (launch_ms: its mean device time per launch
+    over the timed region, from the library's events around the kernel alone; the
+    tensor-core form's candidate pre-pass runs before it and is not included).
     FP32 form: bound = the FP32 pipe; achieved = executed FP32 flops of the
     evaluated pairs (the row-factored form, FLOPS_PER_PAIR each) per second.
     Tensor-core form: bound = the tensor pipe; achieved = the contraction's flops
@@ -471,8 +479,11 @@ def roofline_block(form, dim, sms, workload):
     peak of the operand type.  Both report beside it the algorithmic rate (2F flops
     per evaluated pair), the dense-equivalent rate (all N x J pairs of Algorithm 1
     per second: a rate, not a fraction -- pruned pairs are bounded away, not
-    computed) and, from the committed ncu counters, the instruction-issue fraction
-    (warp instructions per second against 4 schedulers x SMs x clock)."""
+    computed) and, from the committed ncu counters, the DRAM traffic and the
+    instruction-issue fraction (warp instructions per second against 4 schedulers
+    x SMs x clock).  The timed region mixes grid sizes (coarse and fine solves),
+    so the captured launch's counters are scaled to the region's mean launch by
+    its N x J pairs."""
     peaks, peak_src = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     F = 10 if dim == 3 else 6
@@ -485,13 +496,18 @@ def roofline_block(form, dim, sms, workload):
               "algorithmic_tflops_evaluated": sr * 2 * F / 1e12,
               "dense_equivalent_rate_tflops": pr * 2 * F / 1e12,
               "launch_ms": form["launch_ms"], "launches": form["launches"]}
+    pairs_per_launch = pr * launch_s  # N x J pairs of the mean launch
+
+    def scaled(cnt, key):
+        return int(round(cnt[key] * pairs_per_launch / cnt["pairs"])) if cnt else None
+
     if form["precision"] == "fp32":
         peak = fp32_peak_tflops(sm_mhz, sms)
         kern = "assign_fp32_kernel<%d>" % dim
         cnt = ncu_counters(kern, workload, pruned, "fp32")
         ach = sr * FLOPS_PER_PAIR[dim] / 1e12
         out = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-               "frac": ach / peak, "traffic": cnt["dram_bytes"] if cnt else None,
+               "frac": ach / peak, "traffic": scaled(cnt, "dram_bytes"),
                "achieved_is": "executed FP32 flops: FLOPS_PER_PAIR per evaluated pair (row-factored form)",
                "executed_flops_per_pair": FLOPS_PER_PAIR[dim],
                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
@@ -502,16 +518,16 @@ def roofline_block(form, dim, sms, workload):
         kern = "assign_tc_kernel<%d,%d>" % (dim, 0 if form["precision"] == "tc_tf32" else 1)
         cnt = ncu_counters(kern, workload, pruned, "tc")
         ach = sr * TC_FLOPS_PER_PAIR / 1e12
-        out = {"bound": "tensor", "kernel": kern + " (+ tc_tile_kernel pre-pass in the timed stage)",
-               "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-               "traffic": cnt["dram_bytes"] if cnt else None,
+        out = {"bound": "tensor", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+               "frac": ach / peak, "traffic": scaled(cnt, "dram_bytes"),
                "achieved_is": "tensor flops: 2 x 32 per scored pair (split operands, K = 32)",
                "peak_source": f"measured bf16 {bf16:.1f} TFLOP/s ({peak_src})"
                               + (" x 1.1/2.25 (nominal TF32/BF16)" if form["precision"] == "tc_tf32" else "")}
     if cnt:
-        out["issue_frac"] = cnt["warp_instructions"] / launch_s / issue_peak
-        out["warp_instructions_per_launch"] = cnt["warp_instructions"]
-        out["counters_source"] = "profiles/ncu_counters.txt (ncu capture of this kernel code)"
+        out["issue_frac"] = scaled(cnt, "warp_instructions") / launch_s / issue_peak
+        out["warp_instructions_per_launch"] = scaled(cnt, "warp_instructions")
+        out["counters_source"] = ("profiles/ncu_counters.txt (ncu capture of this kernel code at %d pairs, "
+                                  "scaled to the mean launch's %.3g pairs)" % (cnt["pairs"], pairs_per_launch))
     out.update(common)
     return out
 
@@ -1133,7 +1149,9 @@ def run_sweep(args):
 
 
 def main():
+    global CARRY_HISTORY
     args = parse()
+    CARRY_HISTORY = bool(args.carry_history)
     if args.mode == "assign":
         return run_assign_only(args)
     if args.mode == "sweep":

@@ -519,6 +519,10 @@ typedef struct {
     int32_t factor;           /* coarse grid: ceil(res_d / factor) pixels per axis (>= 4); factor >= 2 */
     double coarse_eps;        /* stop rule of the coarse solve */
     int32_t coarse_max_evals; /* evaluation cap of the coarse solve (its best iterate is used) */
+    int32_t carry_history;    /* apd_lloyd_multires: the coarse solves of successive rounds continue
+                                 one L-BFGS history (pairs and scaling) instead of starting afresh;
+                                 0 = off (default).  The history is kept in a second set of buffers
+                                 the workspace allocates on first use. */
 } apd_multires_opts;
 
 /* Fill *mo with the defaults: factor 2, coarse_eps 0.05, coarse_max_evals 60. */

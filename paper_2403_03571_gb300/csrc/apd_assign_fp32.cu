@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(256)
     const unsigned count = sc->flag_count;
     if (warp == 0 && (threadIdx.x & 31) == 0 && count)
         atomicAdd((unsigned long long *)&sc->rescored_total, (unsigned long long)count);
+    // warps without a queued pixel leave before any FP64 instruction (they issue slowly)
+    if ((unsigned)warp >= count) return;
     const double wref = dkey_inv(sc->wref_key);
     const float wrh = (float)wref;
     const float wrl = (float)(wref - (double)wrh);
@@ -134,6 +136,8 @@ cudaError_t launch_assign_fp32_t(const GridDev &g, int n, Workspace &ws, int32_t
     const TileSrc src{g,        n,     n_chunks,   R,      ws.recs, ws.sorted ? ws.scodes : nullptr,
                       ws.sorted ? ws.perm : nullptr, gmom, ws.flags, ws.flag_gi, labels, ws.sc,
                       ws.prune ? ws.groups : nullptr, ws.pairs_scored, ws.wait_limit};
+    const cudaError_t ep = record_scoring_start(ws, st);
+    if (ep != cudaSuccess) return ep;
     assign_fp32_kernel<D><<<grid, C::TX * C::TY * C::TZ, smem, st>>>(src, toff);
     return cudaGetLastError();
 }

@@ -221,6 +221,17 @@ __device__ __forceinline__ void split2(double v, float &h, float &l) {
     h = (float)v;
     l = (float)(v - (double)h);
 }
+// The reference weight's FP32 split, formed once per block (FP64 instructions
+// issue slowly; a per-warp conversion showed in the pre-pass kernels' time).
+// Every thread of the block calls it, before any early exit.
+__device__ __forceinline__ void block_wref(const DevScalars *__restrict__ sc, float &wrh, float &wrl) {
+    __shared__ float sw[2];
+    if (threadIdx.x == 0) split2(dkey_inv(sc->wref_key), sw[0], sw[1]);
+    __syncthreads();
+    wrh = sw[0];
+    wrl = sw[1];
+}
+
 __device__ __forceinline__ unsigned okey(float v) {  // order-preserving float -> unsigned
     const unsigned u = __float_as_uint(v);
     return u ^ ((u >> 31) ? 0xffffffffu : 0x80000000u);
@@ -301,6 +312,8 @@ __global__ void __launch_bounds__(256)
     using G = TcGeom<D>;
     const int lane = threadIdx.x & 31;
     const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    float wrh, wrl;
+    block_wref(sc, wrh, wrl);
     if (t >= ntiles) return;
     int kb[3];
     tile_origin<D>(t, ntx, nty, tlo, kb);
@@ -360,10 +373,6 @@ __global__ void __launch_bounds__(256)
         rlo[a] = ((float)(kb[a] - c) + 0.5f) * g.h32[a];
         rhi[a] = ((float)(khi[a] - c) + 0.5f) * g.h32[a];
     }
-    float wrh = 0.f, wrl = 0.f;
-    if (lane == 0) split2(dkey_inv(sc->wref_key), wrh, wrl);
-    wrh = __shfl_sync(0xffffffffu, wrh, 0);
-    wrl = __shfl_sync(0xffffffffu, wrl, 0);
     const float finf = __int_as_float(0x7f800000);
     const int n_groups = (n + 31) / 32;
     const int n_blocks = (n_groups + 31) / 32;
@@ -641,19 +650,14 @@ __global__ void __launch_bounds__(256)
     using G = TcGeom<D>;
     const int lane = threadIdx.x & 31;
     const int sup = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    float wrh, wrl;
+    block_wref(sc, wrh, wrl);
     if (sup >= nsup) return;
     const float finf = __int_as_float(0x7f800000);
     int c0[3], c1[3];
     super_range<D>(sg, sup, c0, c1);
     float ch[3], cl[3], rlo[3], rhi[3], alo[3], ahi[3];
     range_box<D>(g, sg, axis_tab, c0, c1, ch, cl, rlo, rhi, alo, ahi);
-    float wrh = 0.f, wrl = 0.f;
-    {
-        float h = 0.f, l = 0.f;
-        if (lane == 0) split2(dkey_inv(sc->wref_key), h, l);
-        wrh = __shfl_sync(0xffffffffu, h, 0);
-        wrl = __shfl_sync(0xffffffffu, l, 0);
-    }
     const int n_groups = (n + 31) / 32;
     const int n_blocks = (n_groups + 31) / 32;
     int bstart = 0;
@@ -782,6 +786,8 @@ __global__ void __launch_bounds__(256)
     using Fm = TcFmt<KIND>;
     const int lane = threadIdx.x & 31;
     const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    float wrh, wrl;
+    block_wref(sc, wrh, wrl);
     if (t >= ntiles) return;
     const float finf = __int_as_float(0x7f800000);
     const int tx = t % sg.ntx, rr = t / sg.ntx;
@@ -791,13 +797,6 @@ __global__ void __launch_bounds__(256)
     float ch[3], cl[3], rlo[3], rhi[3], alo[3], ahi[3];
     range_box<D>(g, sg, axis_tab, tc3, tc3, ch, cl, rlo, rhi, alo, ahi);
     if (lane < 6) centre[(size_t)t * 6 + lane] = lane < 3 ? ch[lane] : cl[lane - 3];
-    float wrh = 0.f, wrl = 0.f;
-    {
-        float h = 0.f, l = 0.f;
-        if (lane == 0) split2(dkey_inv(sc->wref_key), h, l);
-        wrh = __shfl_sync(0xffffffffu, h, 0);
-        wrl = __shfl_sync(0xffffffffu, l, 0);
-    }
     const int cntS = scount[sup];
     const int *sl = slist + (size_t)sup * kSuperCap;
     // the tile's bounds of the super-tile's candidates: at most 8 rounds of 32,
@@ -1455,6 +1454,8 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     args.pairs_scored = ws.pairs_scored;
     args.wide = (g.res[0] > 4096 || g.res[1] > 4096 || (D == 3 && g.res[2] > 4096)) ? 1 : 0;
     const int grid = (int)std::min<long long>(ntl, sms);
+    const cudaError_t ep = record_scoring_start(ws, st);
+    if (ep != cudaSuccess) return ep;
     assign_tc_kernel<D, KIND><<<grid, kThreads, smem, st>>>(args);
     return cudaGetLastError();
 }

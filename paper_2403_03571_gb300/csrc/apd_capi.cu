@@ -155,7 +155,6 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
         // the graph's own events; the replay reads them after its synchronisation
         e0 = ws.cap_e0;
         e1 = ws.cap_e1;
-        APD_TRY(cuda_ok(cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal)));
     } else if (ws.profiling) {
         while (ws.ev.size() < ws.ev_used + 2) {
             cudaEvent_t e;
@@ -166,8 +165,10 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
         e1 = ws.ev[ws.ev_used + 1];
         ws.ev_used += 2;
         ws.prof_pairs += win_pixels(g) * (long long)n;
-        APD_TRY(cuda_ok(cudaEventRecord(e0, st)));
     }
+    // recorded right before the scoring kernel itself (after the tensor-core
+    // form's candidate pre-pass), so the events time that kernel alone
+    ws.prof_e0 = e0;
     // the tensor-core tiling needs per-tile scratch; grids too thin for the
     // workspace's tile capacity are scored by the FP32 kernel (same labels)
     if (empty) {
@@ -175,6 +176,7 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
         APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
     else
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
+    APD_TRY(cuda_ok(record_scoring_start(ws, st)));  // nothing launched (an empty slab)
     if (e1) APD_TRY(cuda_ok(ws.capturing ? cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal)
                                          : cudaEventRecord(e1, st)));
     if (!empty) APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
@@ -569,6 +571,18 @@ struct Solver {
     int iterate(double f0, double *out, bool &converged) {
         int hist = 0, newest = kHistCap - 1;
         double gamma = 1.0;
+        if (ws.carry_on && ws.carry.valid) {  // continue the history of the previous solve
+            hist = std::min(ws.carry.hist, history);
+            newest = ws.carry.newest;
+            gamma = ws.carry.gamma;
+        }
+        auto keep = [&]() {
+            if (!ws.carry_on) return;
+            ws.carry.hist = hist;
+            ws.carry.newest = newest;
+            ws.carry.gamma = gamma;
+            ws.carry.valid = true;
+        };
         int fails = 0;
         bool pending = false;  // a pushed pair whose test result is not read yet
         int p_slot = 0;
@@ -612,6 +626,7 @@ struct Solver {
             if (res == LS_CONVERGED) {
                 converged = true;
                 ++iters;
+                keep();
                 return cuda_ok(cudaMemcpyAsync(out, ws.Wt, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
             }
             if (res == LS_BUDGET) break;
@@ -636,6 +651,7 @@ struct Solver {
             std::swap(ws.gf, ws.gft);
             f0 = f_acc;
         }
+        keep();
         return cuda_ok(cudaMemcpyAsync(out, ws.Wbest, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
 };
@@ -764,7 +780,8 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.tc_slist, (size_t)w.tc_tile_cap * tc_super_cap() * sizeof(int));
     alloc((void **)&w.tc_scount, (size_t)w.tc_tile_cap * sizeof(int));
     alloc((void **)&w.tc_stex, (size_t)w.tc_tile_cap * sizeof(float));
-    alloc((void **)&w.part, nb * 5 * sizeof(double));
+    w.part_rows = (int)nb;
+    alloc((void **)&w.part, nb * kPartStride * sizeof(double));
     alloc((void **)&w.grad, (size_t)max_n * sizeof(double));
     alloc((void **)&w.W, (size_t)max_n * sizeof(double));
     alloc((void **)&w.Wt, (size_t)max_n * sizeof(double));
@@ -803,7 +820,8 @@ void apd_workspace_destroy(apd_workspace *ws) {
     for (EvalGraph &e : w.graph_cache) destroy_graph(e);
     if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.tc_axis, w.tc_slist, w.tc_scount, w.tc_stex, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
-                    w.Wbest, w.S, w.Y, w.gram, w.lb_part, w.lb_coef, w.rho, w.X, w.vbuf, w.wfeat, w.wpred};
+                    w.Wbest, w.S, w.Y, w.gram, w.lb_part, w.lb_coef, w.rho, w.X, w.vbuf, w.wfeat, w.wpred,
+                    w.S2, w.Y2, w.gram2, w.rho2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.sc_host) cudaFreeHost(w.sc_host);
@@ -1258,6 +1276,7 @@ void apd_multires_opts_default(apd_multires_opts *mo) {
     mo->factor = 2;
     mo->coarse_eps = 0.05;
     mo->coarse_max_evals = 60;
+    mo->carry_history = 0;
 }
 
 // Coarse grid of a coarse-to-fine solve (same box, ceil(res / factor) >= 4 per axis).
@@ -1271,6 +1290,31 @@ static int coarse_grid(const apd_grid *grid, const apd_multires_opts &m, apd_gri
 // Solve on the coarse grid from w0 (judged against zero if asked), then on the
 // fine grid from the coarse weights; w_out receives both in turn.  The coarse
 // status (often NOT_CONVERGED at its cap) is not an error.
+// The second L-BFGS history of a Lloyd run's coarse solves: allocated on the
+// first use (the run asked for it with carry_history), exchanged with the main
+// one around each coarse solve.
+static bool carry_ready(const Workspace &ws) {
+    return ws.S2 && ws.Y2 && ws.gram2 && ws.rho2 && ws.carry_enabled;
+}
+static void swap_history(Workspace &ws) {
+    std::swap(ws.S, ws.S2);
+    std::swap(ws.Y, ws.Y2);
+    std::swap(ws.gram, ws.gram2);
+    std::swap(ws.rho, ws.rho2);
+}
+static int carry_begin(Workspace &ws) {
+    if (!ws.S2) {
+        bool ok = cudaMalloc((void **)&ws.S2, (size_t)kHistCap * ws.max_n * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc((void **)&ws.Y2, (size_t)kHistCap * ws.max_n * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc((void **)&ws.gram2, 2 * kHistCap * kHistCap * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc((void **)&ws.rho2, kHistCap * sizeof(double)) == cudaSuccess;
+        if (!ok) return APD_ERR_CUDA;
+    }
+    ws.carry.valid = false;
+    ws.carry_enabled = true;
+    return APD_OK;
+}
+
 static int c2f_solve(const GridDev &g, const apd_grid *grid, const GridDev &gc, const apd_grid *cg, int n,
                      const double *x, const double *A, const double *w0, const double *v, double *w_out,
                      const apd_solve_opts &o, const apd_multires_opts &m, apd_solve_info &inf,
@@ -1279,7 +1323,12 @@ static int c2f_solve(const GridDev &g, const apd_grid *grid, const GridDev &gc, 
     apd_solve_opts oc = o;
     oc.eps = m.coarse_eps;
     oc.max_evals = m.coarse_max_evals;
+    const bool carry = carry_ready(ws);  // the coarse solve runs on the second history
+    if (carry) swap_history(ws);
+    ws.carry_on = carry;
     const int crc = solve_impl(gc, cg, n, x, A, w0, v, w_out, oc, cinf, ws, st, false, judged, used);
+    ws.carry_on = false;
+    if (carry) swap_history(ws);
     if (crc < 0) return crc;
     return solve_impl(g, grid, n, x, A, w_out, v, w_out, o, inf, ws, st, need_moments_at_out);
 }
@@ -1351,6 +1400,7 @@ int apd_lloyd_multires(const apd_grid *grid, const apd_seeds *seeds, const doubl
         rc = cuda_ok(cudaMemcpyAsync(x_out, seeds->x, (size_t)n * g.dim * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (rc == APD_OK && w_out != seeds->w)
         rc = cuda_ok(cudaMemcpyAsync(w_out, seeds->w, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (rc == APD_OK && m.carry_history && rounds > 0) rc = carry_begin(ws->w);
     for (int k = 0; rc == APD_OK && k <= rounds; ++k) {
         const bool last = k == rounds;
         const int r = c2f_solve(g, grid, gc, &cg, n, x_out, seeds->A, k == 0 ? w0 : w_out, v, w_out, o, m, inf, cinf,
@@ -1365,6 +1415,10 @@ int apd_lloyd_multires(const apd_grid *grid, const apd_seeds *seeds, const doubl
             ws->w.kernel_launches += 1;
             rc = cuda_ok(launch_centroids(g, n, x_out, ws->w.moments, x_out, st));
         }
+    }
+    if (ws) {
+        ws->w.carry_enabled = false;
+        ws->w.carry.valid = false;
     }
     if (rc == APD_OK) rc = worst;
     if (rc >= 0) cudaStreamSynchronize(st);

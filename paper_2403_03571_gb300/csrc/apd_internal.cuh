@@ -85,6 +85,7 @@ struct DevScalars {
 // Partial sums per block row of the L-BFGS dot-product kernels: the push's
 // 3 + 3 (cap - 1) Gram products and 2 + 2 (cap - 1) direction products, cap = 32.
 constexpr int kLbfgsDots = 160;
+constexpr int kPartStride = 6;  // doubles per block row of Workspace::part
 
 // Coefficients of an L-BFGS direction p = -gamma g + sum_k (cy_k y_k + cs_k s_k)
 // over the pairs in slot[0..hist) (device; written by the direction's first kernel).
@@ -159,7 +160,8 @@ struct Workspace {
     GroupBound *groups = nullptr;       // [n_pad_max / 32] bounds of the scan-order seed groups
     DevScalars *sc = nullptr;           // device
     DevScalars *sc_host = nullptr;      // pinned host mirror
-    double *part = nullptr;             // [2 * max_blocks] dual partial sums
+    double *part = nullptr;             // [part_rows][kPartStride] per-block partials (dual, trial weights)
+    int part_rows = 0;
     double *grad = nullptr;             // [max_n] gradient of g~ of the last evaluation
     // L-BFGS / Lloyd state
     int hist_cap = 0;
@@ -171,6 +173,16 @@ struct Workspace {
     int lb_rows = 0;
     LbfgsCoef *lb_coef = nullptr;       // the last direction's coefficients
     double *rho = nullptr;              // [hist_cap]
+    // a second L-BFGS history (pairs, Gram entries, 1 / s.y) continued by the coarse
+    // solves of a Lloyd run (allocated on first use), and its host-side state
+    double *S2 = nullptr, *Y2 = nullptr, *gram2 = nullptr, *rho2 = nullptr;
+    bool carry_enabled = false;         // a Lloyd run with carry_history is in progress
+    bool carry_on = false;              // the running solve starts from `carry` and leaves its history there
+    struct {
+        int hist = 0, newest = 0;
+        double gamma = 1.0;
+        bool valid = false;
+    } carry;
     double *X = nullptr;                // [max_n * dim] seed positions for Lloyd
     double *vbuf = nullptr;             // [max_n]
     float *wfeat = nullptr;             // [max_n][kWarmFeatMax] warm-start features
@@ -181,7 +193,8 @@ struct Workspace {
     std::vector<cudaEvent_t> ev;  // 2 per recorded launch
     size_t ev_used = 0;
     int64_t prof_pairs = 0;
-    double prof_ms_graph = 0.0;   // scoring-stage time of replayed evaluation graphs
+    cudaEvent_t prof_e0 = nullptr;  // start event the next scoring kernel launch records
+    double prof_ms_graph = 0.0;   // scoring-kernel time of replayed evaluation graphs
     int64_t prof_n_graph = 0;
     // evaluation graphs of the weight solve
     bool graphs = true;
@@ -401,6 +414,14 @@ cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double 
 cudaError_t launch_lbfgs_push(int n, int slot, int cap, int nprev, bool dir, int hist, int hist_acc, double gamma,
                               Workspace &ws, cudaStream_t st);
 cudaError_t launch_lbfgs_pdir(int n, Workspace &ws, cudaStream_t st);
+// Records the pending profiling start event (if any) on st: called by the
+// scoring launchers right before the scoring kernel.
+inline cudaError_t record_scoring_start(Workspace &ws, cudaStream_t st) {
+    cudaEvent_t e = ws.prof_e0;
+    if (!e) return cudaSuccess;
+    ws.prof_e0 = nullptr;
+    return ws.capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+}
 // graph support: the eval_begin kernel (to find its node), its launch written
 // into an instantiated graph's node, and the tensor-core per-axis table
 // brought up to date for a grid outside any capture

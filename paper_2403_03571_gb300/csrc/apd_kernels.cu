@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) {
         double b = shw[0];
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) b = fmax(b, shw[k]);
-        part[(size_t)blockIdx.x * 5] = b;
+        part[(size_t)blockIdx.x * kPartStride] = b;
         __threadfence();
         last = atomicAdd(&sc->dual_done, 1u) == gridDim.x - 1;
     }
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256)
     // block maxima loaded in parallel (max is order-independent)
     double wref = -DBL_MAX;
     for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x)
-        wref = fmax(wref, *(volatile double *)&part[(size_t)k * 5]);
+        wref = fmax(wref, *(volatile double *)&part[(size_t)k * kPartStride]);
     wref = warp_max(wref);
     if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = wref;
     __syncthreads();
@@ -169,13 +169,88 @@ __global__ void gather_recs_kernel(const int n_pad, const int32_t *__restrict__ 
     }
 }
 
-// Per-cell dual terms from the integer moments (dual_terms), then a
-// deterministic two-phase reduction (block partials summed in block order by
-// the last block):  g_i = (v_i - m_i |P|) w_i + |P| Q_i,  grad_i = v_i - m_i |P|.
+// Pair p (of D (D + 1) / 2, a <= b in row order) of the upper triangle.
+template <int D>
+__device__ __forceinline__ void pair_ab(const int p, int &a, int &b) {
+    if (D == 3) {
+        a = p < 3 ? 0 : (p < 5 ? 1 : 2);
+        b = p < 3 ? p : (p < 5 ? p - 2 : 2);
+    } else {
+        a = p < 2 ? 0 : 1;
+        b = p < 2 ? p : 1;
+    }
+}
+__device__ __forceinline__ double sel3(const double (&v)[3], const int a) {
+    return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]);
+}
+
+// The pair terms of Q_i = sum_j (y_j - x_i)^T A_i (y_j - x_i) over cell i's
+// pixels (|P| Q_i is the integral term of eq. (2.7)) that lane q of the cell's
+// four lanes takes: pairs q and q + 4.  Q_ab = A_ab M_ab (A_ab + A_ba off the
+// diagonal) with M_ab = sum_j (y - x)_a (y - x)_b written through the integer
+// moments m, S1 = sum u, S2 = sum u u^T (u = 2k + 1, y = lo + h u / 2):
+// M_ab = h_a h_b / 4 (S2_ab - S1_a S1_b / m) + m e_a e_b, e = centroid - x.
+template <int D>
+__device__ __forceinline__ double dual_pair_terms(const GridDev &g, const unsigned long long *__restrict__ mo,
+                                                  const double *__restrict__ xi, const double *__restrict__ Ai,
+                                                  const int q) {
+    constexpr int NP = D * (D + 1) / 2;
+    if (mo[0] == 0ull) return 0.0;
+    const double m = (double)mo[0];
+    const double inv_m = 1.0 / m;  // one division; products with it differ from quotients by a few ulp
+    double Q = 0.0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int p = q + 4 * r;
+        if (p < NP) {
+            int a, b;
+            pair_ab<D>(p, a, b);
+            const double S1a = (double)mo[1 + a], S1b = (double)mo[1 + b];
+            const double ea = (sel3(g.lo, a) + 0.5 * sel3(g.h, a) * (S1a * inv_m)) - xi[a];
+            const double eb = (sel3(g.lo, b) + 0.5 * sel3(g.h, b) * (S1b * inv_m)) - xi[b];
+            const double Cab = (double)mo[1 + D + p] - S1a * S1b * inv_m;
+            const double Mab = 0.25 * sel3(g.h, a) * sel3(g.h, b) * Cab + m * ea * eb;
+            const double Aab = a == b ? Ai[a * D + a] : Ai[a * D + b] + Ai[b * D + a];
+            Q += Aab * Mab;
+        }
+    }
+    return Q;
+}
+
+// The same from FP64 element-measure moments (non-uniform discretisation):
+// m = sum |P_j|, S1 = sum |P_j| y_j, S2 = sum |P_j| y_j y_j^T, and
+// Q_ab = A_ab (S2_ab - S1_a x_b - x_a S1_b + m x_a x_b).
+template <int D>
+__device__ __forceinline__ double points_pair_terms(const double *__restrict__ mo, const double *__restrict__ xi,
+                                                    const double *__restrict__ Ai, const int q) {
+    constexpr int NP = D * (D + 1) / 2;
+    const double m = mo[0];
+    double Q = 0.0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int p = q + 4 * r;
+        if (p < NP) {
+            int a, b;
+            pair_ab<D>(p, a, b);
+            const double Cab = mo[1 + D + p] - mo[1 + a] * xi[b] - xi[a] * mo[1 + b] + m * xi[a] * xi[b];
+            const double Aab = a == b ? Ai[a * D + a] : Ai[a * D + b] + Ai[b * D + a];
+            Q += Aab * Cab;
+        }
+    }
+    return Q;
+}
+
+// Per-cell dual terms, four lanes per cell (FP64 issues slowly; the pair terms
+// are split over the lanes), then a deterministic reduction: block sums through
+// fixed shuffle trees, block partials reduced by the last block to finish.
+//   g_i = (v_i - m_i |P|) w_i + |P| Q_i,  grad_i = v_i - m_i |P|  (eqs. (2.7), (2.8))
 // kPoints: FP64 element-measure moments of a non-uniform discretisation
 // (mom_pts), g_i = (v_i - m_i) w_i + Q_i, grad_i = v_i - m_i.
+// The largest relative volume error max_i |grad_i| / v_i is tracked as the
+// pair (|grad_k|, v_k) of its cell and divided once at the end.
+constexpr int kDualThreads = 256;  // 64 cells per block round
 template <int D, bool kPoints = false>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kDualThreads)
     dual_kernel(const GridDev g, const int n, const double *__restrict__ x,
                 const double *__restrict__ A, const double *__restrict__ w,
                 const double *__restrict__ v, const double *__restrict__ p_dir,
@@ -183,80 +258,122 @@ __global__ void __launch_bounds__(256)
                 DevScalars *__restrict__ sc, double *g_out, double *grad_out, double *gf_out,
                 double *err_out, const double *__restrict__ mom_pts = nullptr) {
     constexpr int K = moment_width(D);
-    __shared__ double sh[33];
+    constexpr int NQ = kPartStride;  // g, <grad f, p>, sum v, max error (numerator, denominator), min v
+    __shared__ double shq[kDualThreads / 32][NQ];
     __shared__ bool last;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double gsum = 0.0, emax = 0.0, gp = 0.0, sv = 0.0, vmin = DBL_MAX;
-    if (i < n) {
-        const double vi = v[i], wi = w[i];
-        if (!(vi > 0.0) || !isfinite(vi)) atomicOr(&sc->status, ST_BAD_VOLUME);
-        double gr, Q;
-        if (kPoints) {
-            dual_terms_points<D>(mom_pts + (size_t)i * K, vi, x + (size_t)i * D, A + (size_t)i * D * D, gr, Q);
-            gsum = gr * wi + Q;
-        } else {
-            dual_terms<D>(g, mom + (size_t)i * K, vi, x + (size_t)i * D, A + (size_t)i * D * D, gr, Q);
-            gsum = gr * wi + g.cell * Q;
-        }
-        emax = __ddiv_rn(fabs(gr), vi);
-        if (grad_out) grad_out[i] = gr;
-        if (gf_out) gf_out[i] = -gr;
-        if (p_dir) gp = -gr * p_dir[i];
-        sv = vi;
-        vmin = vi;
-    }
-    const double bg = block_sum(gsum, sh);
-    const double bp = block_sum(gp, sh);
-    const double bs = block_sum(sv, sh);
-    // max / min through the same tree
-    double em = warp_max(emax), vm = warp_min(vmin);
-    __shared__ double shm[32], shn[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        shm[wid] = em;
-        shn[wid] = vm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = DBL_MAX;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            a = fmax(a, shm[k]);
-            b = fmin(b, shn[k]);
-        }
-        double *pp = part + (size_t)blockIdx.x * 5;
-        pp[0] = bg;
-        pp[1] = a;
-        pp[2] = bp;
-        pp[3] = bs;
-        pp[4] = b;
-        __threadfence();
-        const unsigned t = atomicAdd(&sc->dual_done, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // the partials are loaded in parallel, then summed in block order by one thread
-    __shared__ double pl[5 * 64];
-    const unsigned chunk = min(gridDim.x, 64u);
-    double G = 0.0, E = 0.0, GP = 0.0, SV = 0.0, VM = DBL_MAX;
-    for (unsigned k0 = 0; k0 < gridDim.x; k0 += chunk) {
-        const unsigned m = min(chunk, gridDim.x - k0);
-        for (unsigned e = threadIdx.x; e < 5 * m; e += blockDim.x)
-            pl[e] = *(const volatile double *)(part + (size_t)k0 * 5 + e);
-        __syncthreads();
-        if (threadIdx.x == 0)
-            for (unsigned k = 0; k < m; ++k) {
-                const double *pp = pl + (size_t)k * 5;
-                G += pp[0];
-                E = fmax(E, pp[1]);
-                GP += pp[2];
-                SV += pp[3];
-                VM = fmin(VM, pp[4]);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, q = lane & 3;
+    double gsum = 0.0, gp = 0.0, sv = 0.0, en = 0.0, ed = 1.0, vmin = DBL_MAX;
+    const int stride = gridDim.x * (kDualThreads / 4);
+    const int rounds = (n + stride - 1) / stride;  // the same for every lane (converged shuffles)
+    int i = (blockIdx.x * kDualThreads + threadIdx.x) >> 2;
+    for (int r = 0; r < rounds; ++r, i += stride) {
+        const bool real = i < n;
+        double Qp = 0.0;
+        if (real)
+            Qp = kPoints ? points_pair_terms<D>(mom_pts + (size_t)i * K, x + (size_t)i * D, A + (size_t)i * D * D, q)
+                         : dual_pair_terms<D>(g, mom + (size_t)i * K, x + (size_t)i * D, A + (size_t)i * D * D, q);
+        Qp += __shfl_xor_sync(0xffffffffu, Qp, 1);
+        Qp += __shfl_xor_sync(0xffffffffu, Qp, 2);
+        if (real && q == 0) {
+            const double vi = v[i], wi = w[i];
+            if (!(vi > 0.0) || !isfinite(vi)) atomicOr(&sc->status, ST_BAD_VOLUME);
+            const double gr = kPoints ? vi - mom_pts[(size_t)i * K] : __dsub_rn(vi, __dmul_rn((double)mom[(size_t)i * K], g.cell));
+            gsum += kPoints ? gr * wi + Qp : gr * wi + g.cell * Qp;
+            const double ag = fabs(gr);
+            if (ag * ed > en * vi) {
+                en = ag;
+                ed = vi;
             }
-        __syncthreads();
+            if (grad_out) grad_out[i] = gr;
+            if (gf_out) gf_out[i] = -gr;
+            if (p_dir) gp += -gr * p_dir[i];
+            sv += vi;
+            vmin = fmin(vmin, vi);
+        }
     }
-    if (threadIdx.x == 0) {
+    // warp: the cells' lanes q = 0 (lanes 0, 4, ..., 28) by a fixed tree
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+        gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
+        gp += __shfl_xor_sync(0xffffffffu, gp, off);
+        sv += __shfl_xor_sync(0xffffffffu, sv, off);
+        const double on = __shfl_xor_sync(0xffffffffu, en, off), od = __shfl_xor_sync(0xffffffffu, ed, off);
+        if (on * ed > en * od) {
+            en = on;
+            ed = od;
+        }
+        vmin = fmin(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+    }
+    if (lane == 0) {
+        shq[wid][0] = gsum;
+        shq[wid][1] = gp;
+        shq[wid][2] = sv;
+        shq[wid][3] = en;
+        shq[wid][4] = ed;
+        shq[wid][5] = vmin;
+    }
+    __syncthreads();
+    // block: warp 0 over the 8 warps' values by a fixed tree; lane 0 stores the partials
+    if (wid == 0) {
+        const int k = lane < kDualThreads / 32 ? lane : 0;
+        const bool own = lane < kDualThreads / 32;
+        double b0 = own ? shq[k][0] : 0.0, b1 = own ? shq[k][1] : 0.0, b2 = own ? shq[k][2] : 0.0;
+        double b3 = own ? shq[k][3] : 0.0, b4 = own ? shq[k][4] : 1.0, b5 = own ? shq[k][5] : DBL_MAX;
+#pragma unroll
+        for (int off = 1; off < kDualThreads / 32; off <<= 1) {
+            b0 += __shfl_xor_sync(0xffffffffu, b0, off);
+            b1 += __shfl_xor_sync(0xffffffffu, b1, off);
+            b2 += __shfl_xor_sync(0xffffffffu, b2, off);
+            const double on = __shfl_xor_sync(0xffffffffu, b3, off), od = __shfl_xor_sync(0xffffffffu, b4, off);
+            if (on * b4 > b3 * od) {
+                b3 = on;
+                b4 = od;
+            }
+            b5 = fmin(b5, __shfl_xor_sync(0xffffffffu, b5, off));
+        }
+        if (lane == 0) {
+            double *pp = part + (size_t)blockIdx.x * NQ;
+            pp[0] = b0;
+            pp[1] = b1;
+            pp[2] = b2;
+            pp[3] = b3;
+            pp[4] = b4;
+            pp[5] = b5;
+            __threadfence();
+            last = atomicAdd(&sc->dual_done, 1u) == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!last || wid != 0) return;
+    __threadfence();
+    // the last block: lanes take the blocks in order (lane, lane + 32, ...), then a fixed tree
+    double G = 0.0, GP = 0.0, SV = 0.0, EN = 0.0, ED = 1.0, VM = DBL_MAX;
+    for (unsigned b = lane; b < gridDim.x; b += 32) {
+        const volatile double *pp = part + (size_t)b * NQ;
+        G += pp[0];
+        GP += pp[1];
+        SV += pp[2];
+        const double on = pp[3], od = pp[4];
+        if (on * ED > EN * od) {
+            EN = on;
+            ED = od;
+        }
+        VM = fmin(VM, pp[5]);
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        G += __shfl_xor_sync(0xffffffffu, G, off);
+        GP += __shfl_xor_sync(0xffffffffu, GP, off);
+        SV += __shfl_xor_sync(0xffffffffu, SV, off);
+        const double on = __shfl_xor_sync(0xffffffffu, EN, off), od = __shfl_xor_sync(0xffffffffu, ED, off);
+        if (on * ED > EN * od) {
+            EN = on;
+            ED = od;
+        }
+        VM = fmin(VM, __shfl_xor_sync(0xffffffffu, VM, off));
+    }
+    if (lane == 0) {
+        const double E = __ddiv_rn(EN, ED);
         sc->g = G;
         sc->max_rel_err = E;
         sc->dot_gp = GP;
@@ -659,19 +776,21 @@ cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Blocks of the dual kernel: 64 cells each, at most the workspace's partial rows.
+static int dual_blocks(int n, const Workspace &ws) {
+    return std::max(1, std::min((n + kDualThreads / 4 - 1) / (kDualThreads / 4), ws.part_rows));
+}
+
 cudaError_t launch_dual(const GridDev &g, int n, const double *x, const double *A, const double *w,
                         const double *v, const double *p_dir, const unsigned long long *moments,
                         Workspace &ws, double *g_out, double *grad_out, double *gf_out,
                         double *err_out, cudaStream_t st) {
-    // one thread per cell, FP64: small problems spread over more SMs (at most 64
-    // blocks of 64, the workspace's minimum partials count)
-    const int threads = n <= 4096 ? 64 : 256;
-    const int blocks = (n + threads - 1) / threads;
+    const int blocks = dual_blocks(n, ws);
     if (g.dim == 3)
-        dual_kernel<3><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
+        dual_kernel<3><<<blocks, kDualThreads, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
                                                    grad_out, gf_out, err_out);
     else
-        dual_kernel<2><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
+        dual_kernel<2><<<blocks, kDualThreads, 0, st>>>(g, n, x, A, w, v, p_dir, moments, ws.part, ws.sc, g_out,
                                                    grad_out, gf_out, err_out);
     return cudaGetLastError();
 }
@@ -679,16 +798,15 @@ cudaError_t launch_dual(const GridDev &g, int n, const double *x, const double *
 cudaError_t launch_points_dual(int dim, int n, const double *x, const double *A, const double *w, const double *v,
                                const double *mom_pts, Workspace &ws, double *g_out, double *grad_out,
                                double *err_out, cudaStream_t st) {
-    const int threads = n <= 4096 ? 64 : 256;
-    const int blocks = (n + threads - 1) / threads;
+    const int blocks = dual_blocks(n, ws);
     GridDev g;
     memset(&g, 0, sizeof g);
     g.dim = dim;
     if (dim == 3)
-        dual_kernel<3, true><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, nullptr, nullptr, ws.part, ws.sc, g_out,
+        dual_kernel<3, true><<<blocks, kDualThreads, 0, st>>>(g, n, x, A, w, v, nullptr, nullptr, ws.part, ws.sc, g_out,
                                                          grad_out, nullptr, err_out, mom_pts);
     else
-        dual_kernel<2, true><<<blocks, threads, 0, st>>>(g, n, x, A, w, v, nullptr, nullptr, ws.part, ws.sc, g_out,
+        dual_kernel<2, true><<<blocks, kDualThreads, 0, st>>>(g, n, x, A, w, v, nullptr, nullptr, ws.part, ws.sc, g_out,
                                                          grad_out, nullptr, err_out, mom_pts);
     return cudaGetLastError();
 }

@@ -78,10 +78,18 @@ def test_counters_follow_the_kernel_code(tmp_path, monkeypatch):
     import bench
     f = tmp_path / "c.txt"
     h = bench.kernel_source_hash("tc")
-    f.write_text(f"# kernel workload form hash dram_bytes warp_instructions\n"
-                 f"assign_tc_kernel<3,0> 3d_n1000_256cube_lloyd5 pruned {h} 1000 2000\n"
-                 f"assign_tc_kernel<3,0> 3d_n1000_256cube_lloyd5 dense 0123456789abcdef 1 2\n")
+    f.write_text(f"# kernel workload form hash dram_bytes warp_instructions pairs\n"
+                 f"assign_tc_kernel<3,0> 3d_n1000_256cube_lloyd5 pruned {h} 1000 2000 4000\n"
+                 f"assign_tc_kernel<3,0> 3d_n1000_256cube_lloyd5 dense 0123456789abcdef 1 2 3\n")
     monkeypatch.setattr(bench, "COUNTERS_FILE", str(f))
     assert bench.ncu_counters("assign_tc_kernel<3,0>", "3d_n1000_256cube_lloyd5", True, "tc") == \
-        {"dram_bytes": 1000, "warp_instructions": 2000}
+        {"dram_bytes": 1000, "warp_instructions": 2000, "pairs": 4000}
     assert bench.ncu_counters("assign_tc_kernel<3,0>", "3d_n1000_256cube_lloyd5", False, "tc") is None
+    # scaled to the timed region's mean launch by its N x J pairs (here twice the captured launch's)
+    form = {"precision": "tc_tf32", "pair_rate": 8.0e6, "scored_pair_rate": 1.0e6, "pruned": True,
+            "launch_ms": 1.0, "launches": 3}
+    rb = bench.roofline_block(form, 3, 152, "3d_n1000_256cube_lloyd5")
+    assert rb["traffic"] == 2000 and rb["warp_instructions_per_launch"] == 4000
+    peaks, _ = bench.load_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    assert rb["issue_frac"] == pytest.approx(4000 / 1e-3 / (4 * 152 * mhz * 1e6))

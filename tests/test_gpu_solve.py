@@ -132,6 +132,39 @@ def test_lloyd_coarse_to_fine(capi):
     assert np.abs(X - inst.x).max() > 1e-3
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tc_tf32"])
+def test_lloyd_coarse_history_carried(capi, prec):
+    # the coarse solves of successive rounds continue one L-BFGS history: the
+    # result still solves the final positions to 1 % (oracle), the run is
+    # deterministic, and the main history is untouched by it (a plain solve
+    # afterwards on the same workspace matches one on a fresh workspace)
+    inst = synth.make_instance(3, 300, 48, 31)
+    x, A, w, v = instance_tensors(inst)
+    pc = capi.APD_FP32 if prec == "fp32" else capi.APD_TC_TF32
+    opts = capi.solve_opts(eps=0.01, precision=pc)
+    outs = []
+    for _ in range(2):
+        ws = capi.Workspace(3, inst.n, inst.grid.num_pixels)
+        ws.set_pruning(True)
+        x_out, w_out = torch.zeros_like(x), torch.zeros_like(w)
+        rc, info, _ = capi.apd_lloyd_multires(inst.grid, x, A, w, v, 4, x_out, w_out, ws, opts,
+                                              capi.multires_opts(2, 0.015, 200, carry_history=True))
+        assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+        assert info.solves == 10
+        outs.append((host(x_out), host(w_out), info.as_dict()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    X, W = outs[0][0], outs[0][1]
+    _, _, err = oracle.dual(inst.grid, X, inst.A, W, inst.v)
+    assert err < 0.01
+    w_a = torch.zeros_like(w)
+    capi.apd_solve_weights(inst.grid, x, A, w, v, w_a, ws, opts)
+    ws2 = capi.Workspace(3, inst.n, inst.grid.num_pixels)
+    ws2.set_pruning(True)
+    w_b = torch.zeros_like(w)
+    capi.apd_solve_weights(inst.grid, x, A, w, v, w_b, ws2, opts)
+    assert np.array_equal(host(w_a), host(w_b))
+
+
 def test_refining_solve_raises_the_resolution(capi):
     # Algorithm 2 with its step 4: on a 40^2 grid the smallest cell is a few
     # pixels, so 1 % is out of reach; the solve refines the grid of the same box,
