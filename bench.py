@@ -39,7 +39,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "3d_n1000_256cube_lloyd5"
 L2_FLUSH_BYTES = 512 << 20
-CARRY_HISTORY = False  # set from --carry-history
+CARRY_HISTORY = True  # set from --carry-history
 
 
 def chosen_multires(capi):
@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--precision", default="tc_tf32", choices=["fp32", "tc_tf32", "tc_bf16"],
                     help="scoring arithmetic of the chosen form (the same pipeline with the other "
                          "arithmetic, and the plain FP32 form, are always timed too)")
-    ap.add_argument("--carry-history", type=int, default=0,
+    ap.add_argument("--carry-history", type=int, default=1,
                     help="chosen form: the coarse solves of a Lloyd run continue one L-BFGS history (1) "
                          "or start afresh (0)")
     ap.add_argument("--assign-res", type=int, default=0,
@@ -627,7 +627,10 @@ def run_ours(args):
     out["chosen_" + forms["chosen_alt"]["precision"]] = side(forms["chosen_alt"])
     out["chosen_form"] = ("Algorithm 3 with every weight solve coarse-to-fine (grid factor 2, coarse eps "
                           "1.5 %, at most 200 coarse evaluations), the first started from the learned per-seed "
-                          f"prediction judged against W = 0; {args.precision} scoring"
+                          "prediction judged against W = 0"
+                          + ("; the coarse solves continue one L-BFGS history across the rounds"
+                             if args.carry_history else "")
+                          + f"; {args.precision} scoring"
                           + (" with seed pruning (tensor cores: per-tile candidate lists; FP32: group and "
                              "per-seed bounds)" if args.prune else ""))
     out["coarse_evaluations_per_apd"] = chosen["coarse_evaluations_per_apd"]
@@ -1060,11 +1063,12 @@ def run_masked(args):
 
 def run_sweep(args):
     """The paper's runtime tests (Section 3.2) on this GPU, one JSON line per point:
-    (a) Algorithm 1 for a fixed (X, W = 0, Lambda) in FP32 (labels), dense and
-        pruned, single-phase M of eq. (2.10) (v = 1/N);
+    (a) Algorithm 1 for a fixed (X, W = 0, Lambda) (labels): FP32 dense and
+        pruned, and the chosen scoring arithmetic (--precision) with pruning,
+        single-phase M of eq. (2.10) (v = 1/N);
     (b) Algorithm 2 to 1 % (single and multi phase, M of eq. (2.10) for the
-        smallest volume, capped), the plain form (W = 0, dense) and the chosen
-        form (coarse-to-fine, pruned).
+        smallest volume, capped), the plain form (W = 0, dense FP32) and the
+        chosen form (coarse-to-fine, pruned, the --precision arithmetic).
     Seeds by the sequential rejection C = 0.2, the alpha anisotropy laws,
     instance seeds 2403035710 + 7e6 + run; times are CUDA-event (a) or wall (b,
     synchronised) seconds.  Up to --sweep-runs random instances per point, fewer
@@ -1095,19 +1099,21 @@ def run_sweep(args):
                         ws = capi.Workspace(dim, n, inst.grid.num_pixels)
                         row = {"test": "a", "dim": dim, "n": n, "alpha": alpha, "run": run,
                                "m": inst.grid.res[0], "pixels": inst.grid.num_pixels}
-                        for prune in (False, True):
+                        for key, prune, prec in (("dense_s", False, capi.APD_FP32), ("pruned_s", True, capi.APD_FP32),
+                                                 ("chosen_s", True, precision_code(capi, args.precision))):
                             ws.set_pruning(prune)
                             for _ in range(2):
-                                capi.apd_assign(inst.grid, x, A, w, labels, ws)
+                                capi.apd_assign(inst.grid, x, A, w, labels, ws, precision=prec)
                             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                             torch.cuda.synchronize()
                             e0.record()
                             for _ in range(5):
-                                capi.apd_assign(inst.grid, x, A, w, labels, ws)
+                                capi.apd_assign(inst.grid, x, A, w, labels, ws, precision=prec)
                             e1.record()
                             torch.cuda.synchronize()
                             assert ws.status() == capi.APD_OK
-                            row["pruned_s" if prune else "dense_s"] = e0.elapsed_time(e1) / 5 / 1000.0
+                            row[key] = e0.elapsed_time(e1) / 5 / 1000.0
+                        row["chosen_precision"] = args.precision
                         print(json.dumps(row), flush=True)
                         del ws
     if "b" in args.sweep_test:
@@ -1127,6 +1133,9 @@ def run_sweep(args):
                                    "run": run, "m": inst.grid.res[0], "m_eq_2_10": synth.required_resolution(
                                        dim, float(inst.v.min()), 0.01)}
                             opts = capi.solve_opts(eps=0.01, max_evals=args.sweep_max_evals)
+                            opts_ch = capi.solve_opts(eps=0.01, max_evals=args.sweep_max_evals,
+                                                      precision=precision_code(capi, args.precision))
+                            row["chosen_precision"] = args.precision
                             for form in ("plain", "chosen"):
                                 w_out = torch.zeros_like(w)
                                 ws.set_pruning(form == "chosen")
@@ -1137,7 +1146,7 @@ def run_sweep(args):
                                     coarse = 0
                                 else:
                                     rc, info, _ = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws,
-                                                                                  opts=opts, mopts=mopts)
+                                                                                  opts=opts_ch, mopts=mopts)
                                     coarse = info.coarse_evaluations
                                 torch.cuda.synchronize()
                                 row[form] = {"s": time.perf_counter() - t0, "status": capi.status_string(rc),
