@@ -78,6 +78,13 @@ typedef enum {
                         K = 32), FP32 accumulate: ~1e-4 relative score error */
     APD_TC_TF32 = 2  /* the same with TF32 operands: ~3e-5 relative score error */
 } apd_precision;
+/* With APD_TC_BF16 / APD_TC_TF32, each seed preparation (the first pass of a
+ * call, or of a weight solve) reads the seeds' conditioning back once (a
+ * stream synchronisation): when max_i ||A_i||_F / min_i lambda_min(A_i) > 10
+ * the certificate and the candidate bounds of the tensor-core form are too
+ * loose to pay, and the pass scores with the FP32 kernel instead (same labels).
+ * Grids wider than the workspace's tile scratch are scored by the FP32 kernel
+ * too. */
 
 typedef struct apd_workspace apd_workspace;
 
@@ -523,6 +530,10 @@ typedef struct {
                                  one L-BFGS history (pairs and scaling) instead of starting afresh;
                                  0 = off (default).  The history is kept in a second set of buffers
                                  the workspace allocates on first use. */
+    int32_t min_cell_span;    /* the coarse solve runs only when the coarse grid has at least
+                                 min_cell_span^dim pixels per seed (default 8: cells about 8 pixels
+                                 across; coarser cells cannot reach coarse_eps and the coarse solve
+                                 would only burn its evaluation cap); 0 = always */
 } apd_multires_opts;
 
 /* Fill *mo with the defaults: factor 2, coarse_eps 0.05, coarse_max_evals 60. */

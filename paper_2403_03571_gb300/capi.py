@@ -89,7 +89,8 @@ REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, cty
 
 class ApdMultiresOpts(ctypes.Structure):
     _fields_ = [("factor", ctypes.c_int32), ("coarse_eps", ctypes.c_double),
-                ("coarse_max_evals", ctypes.c_int32), ("carry_history", ctypes.c_int32)]
+                ("coarse_max_evals", ctypes.c_int32), ("carry_history", ctypes.c_int32),
+                ("min_cell_span", ctypes.c_int32)]
 
 
 class ApdRefineOpts(ctypes.Structure):
@@ -632,11 +633,13 @@ def apd_solve_weights_warm(grid, x, A, v, w_out, ws: Workspace, net: WarmStart, 
     return rc, info, used.value
 
 
-def multires_opts(factor=2, coarse_eps=0.05, coarse_max_evals=60, carry_history=False):
+def multires_opts(factor=2, coarse_eps=0.05, coarse_max_evals=60, carry_history=False, min_cell_span=None):
     m = ApdMultiresOpts()
     load().apd_multires_opts_default(ctypes.byref(m))
     m.factor, m.coarse_eps, m.coarse_max_evals = int(factor), float(coarse_eps), int(coarse_max_evals)
     m.carry_history = int(bool(carry_history))
+    if min_cell_span is not None:
+        m.min_cell_span = int(min_cell_span)
     return m
 
 

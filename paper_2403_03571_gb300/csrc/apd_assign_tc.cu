@@ -536,12 +536,26 @@ __device__ __forceinline__ float group_lower(const GroupBound &gb, const float (
 }
 
 // Lower and upper bounds of seed r's costs (relative to w_ref) over the box
-// [rlo, rhi] of pixel centres given relative to the centre ch + cl.
+// [rlo, rhi] of pixel centres given relative to the centre ch + cl, the better
+// of two forms for each:
+//  - eigenvalue form: lambda_min dist(x, box)^2 and lambda_max maxdist(x, box)^2;
+//  - centre form: with d = c - x (c the box centre) and e = y - c, |e_a| <= r_a,
+//    (y - x)^T A (y - x) = d^T A d + 2 (A d).e + e^T A e lies within
+//    q -/+ 2 sum_a |(A d)_a| r_a (+ sum_ab |A_ab| r_a r_b above), q = d^T A d;
+//    tight for anisotropic A, where the eigenvalue form is off by up to the
+//    condition number.
+// The position slack widens r (it covers the FP32 offsets as in the eigenvalue
+// form); E = 1e-5 S, S = sum_ab |A_ab| (|d_a| + r_a)(|d_b| + r_b), covers the
+// FP32 rounding of q and of the linear term and the FP32 storage of A (about
+// 20 roundings of at most 2^-24 S each).  Only the lower bound decides
+// correctness (a seed left out costs at least its lower bound); the upper
+// bound only sets how short the lists are.
 template <int D>
 __device__ __forceinline__ void seed_bounds(const SeedRec32 &r, const float (&ch)[3], const float (&cl)[3],
                                             const float (&rlo)[3], const float (&rhi)[3], float wrh, float wrl,
                                             float &lb, float &ub) {
     float d2lo = 0.f, d2hi = 0.f;
+    float dv[3] = {0.f, 0.f, 0.f}, rr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const float xs = (r.xh[a] - ch[a]) + (r.xl[a] - cl[a]);
@@ -550,11 +564,49 @@ __device__ __forceinline__ void seed_bounds(const SeedRec32 &r, const float (&ch
         const float dh = fmaxf(fabsf(xs - rlo[a]), fabsf(xs - rhi[a])) + slack;
         d2lo = __fmaf_rd(dl, dl, d2lo);
         d2hi = __fmaf_ru(dh, dh, d2hi);
+        dv[a] = 0.5f * (rlo[a] + rhi[a]) - xs;
+        rr[a] = 0.5f * (rhi[a] - rlo[a]) + slack;
     }
     const float wn = -((r.wh - wrh) + (r.wl - wrl));  // w_ref - w_i, up to rounding
     const float wslack = 1e-6f * fabsf(wn) + 1e-30f;
-    lb = __fadd_rd(__fmul_rd(__fmul_rd(r.pad[0], d2lo), 1.f - 1e-5f), __fsub_rd(wn, wslack));
-    ub = __fadd_ru(__fmul_ru(__fmul_ru(r.pad[1], d2hi), 1.f + 1e-5f), __fadd_ru(wn, wslack));
+    const float lb1 = __fadd_rd(__fmul_rd(__fmul_rd(r.pad[0], d2lo), 1.f - 1e-5f), __fsub_rd(wn, wslack));
+    const float ub1 = __fadd_ru(__fmul_ru(__fmul_ru(r.pad[1], d2hi), 1.f + 1e-5f), __fadd_ru(wn, wslack));
+    // the symmetric matrix from the record (upper triangle, row order)
+    float M[3][3];
+    if (D == 3) {
+        M[0][0] = r.a[0];
+        M[0][1] = M[1][0] = r.a[1];
+        M[0][2] = M[2][0] = r.a[2];
+        M[1][1] = r.a[3];
+        M[1][2] = M[2][1] = r.a[4];
+        M[2][2] = r.a[5];
+    } else {
+        M[0][0] = r.a[0];
+        M[0][1] = M[1][0] = r.a[1];
+        M[1][1] = r.a[2];
+        M[0][2] = M[2][0] = M[1][2] = M[2][1] = M[2][2] = 0.f;
+    }
+    float q = 0.f, lin = 0.f, quad = 0.f, S = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        float ga = 0.f, qa = 0.f, sa = 0.f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            ga = fmaf(M[a][b], dv[b], ga);
+            qa = fmaf(fabsf(M[a][b]), rr[b], qa);
+            sa = fmaf(fabsf(M[a][b]), fabsf(dv[b]) + rr[b], sa);
+        }
+        q = fmaf(dv[a], ga, q);
+        lin = fmaf(fabsf(ga), rr[a], lin);
+        quad = fmaf(qa, rr[a], quad);
+        S = fmaf(sa, fabsf(dv[a]) + rr[a], S);
+    }
+    lin = 2.f * lin;
+    const float E = 1e-5f * S + 1e-30f;
+    const float lb2 = __fadd_rd(__fsub_rd(__fsub_rd(q, lin), E), __fsub_rd(wn, wslack));
+    const float ub2 = __fadd_ru(__fadd_ru(__fadd_ru(q, lin), __fadd_ru(quad, E)), __fadd_ru(wn, wslack));
+    lb = fmaxf(lb1, lb2);
+    ub = fminf(ub1, ub2);
 }
 
 // Merge the smallest four of the warp's 32 keys (one per lane) into the
@@ -589,10 +641,10 @@ __device__ __forceinline__ void merge_smallest4(unsigned ku, float &u0, float &u
     u3 = c3;
 }
 
-// Pruned form, step 1: one warp per super-tile of 2 x 2 (x 2) tiles finds the
-// candidates of the super-tile's box (groups visited by increasing bound; the
-// threshold is the fourth smallest upper bound, then the seeds with a lower
-// bound below it) and T_excl.  A seed left out there is left out of each tile
+// Pruned form, step 1: one block of eight warps per super-tile of 2 x 2 (x 2)
+// tiles finds the candidates of the super-tile's box (groups visited by
+// increasing bound, shared out among the warps; the threshold is the fourth
+// smallest upper bound, then the seeds with a lower bound below it) and T_excl.  A seed left out there is left out of each tile
 // too: its bound over a sub-box is at least its bound over the box.
 constexpr int kSuperCap = 256;
 
@@ -640,20 +692,30 @@ __device__ __forceinline__ void range_box(const GridDev &g, const SuperGeom &sg,
     }
 }
 
+constexpr int kSupWarps = 8;  // warps sharing one super-tile's scan
+
 template <int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSupWarps * 32)
     tc_super_kernel(const GridDev g, const SuperGeom sg, const int nsup, const int n,
                     const SeedRec32 *__restrict__ r32, const GroupBound *__restrict__ groups,
                     const uint32_t *__restrict__ scodes, const float4 *__restrict__ axis_tab,
                     int *__restrict__ slist, int *__restrict__ scount, float *__restrict__ stex,
                     const DevScalars *__restrict__ sc) {
     using G = TcGeom<D>;
-    const int lane = threadIdx.x & 31;
-    const int sup = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    constexpr int W = kSupWarps;
+    __shared__ unsigned s_T;                 // okey of the smallest threshold found so far
+    __shared__ float s_u[W][4];              // each warp's four smallest upper bounds
+    __shared__ int s_pos[W][kSuperCap];      // each warp's candidates (scan positions) ...
+    __shared__ float s_lb[W][kSuperCap];     // ... and their lower bounds
+    __shared__ int s_cnt[W];
+    __shared__ float s_tex[W], s_tex2[W];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int sup = (int)blockIdx.x;
     float wrh, wrl;
     block_wref(sc, wrh, wrl);
-    if (sup >= nsup) return;
+    if (sup >= nsup) return;  // uniform over the block
     const float finf = __int_as_float(0x7f800000);
+    if (threadIdx.x == 0) s_T = okey(finf);
     int c0[3], c1[3];
     super_range<D>(sg, sup, c0, c1);
     float ch[3], cl[3], rlo[3], rhi[3], alo[3], ahi[3];
@@ -684,89 +746,122 @@ __global__ void __launch_bounds__(256)
         if (blk < 0) blk += n_blocks;
         return blk;
     };
-    // pass 1: the threshold.  Groups are taken two at a time (their records
-    // loaded together); the second is taken only if its bound is below the
-    // current threshold, and extra seeds merged can only be ones a sequential
-    // visit would also have merged or ones with no smaller upper bound.
     const SeedRec32 zrec{};
+    __syncthreads();  // s_T set
+    // Pass 1: T = the fourth smallest upper bound of all seeds.  Per block of 32
+    // groups, warp w visits the groups of bound rank w, w + 8, ... (increasing
+    // bounds) and stops at the first whose bound exceeds its own fourth smallest
+    // upper bound or the block-wide smallest one (s_T): neither is below the
+    // final T, so every group left out has all its upper bounds above T.
     float u0 = finf, u1 = finf, u2 = finf, u3 = finf;
     for (int bi = 0; bi < n_blocks; ++bi) {
         const int blk = block_of(bi);
         const int grp = blk * 32 + lane;
-        const float lbg = grp < n_groups ? group_lower<D>(groups[grp], alo, ahi) : finf;
-        unsigned live = __ballot_sync(0xffffffffu, grp < n_groups);
-        while (live) {
-            const bool mine = (live >> lane) & 1u;
-            const unsigned key = mine ? okey(lbg) : 0xffffffffu;
-            const unsigned k1 = __reduce_min_sync(0xffffffffu, key);
-            const int g1 = __ffs(__ballot_sync(0xffffffffu, mine && key == k1)) - 1;
-            if (__shfl_sync(0xffffffffu, lbg, g1) > u3) break;
-            live &= ~(1u << g1);
-            const unsigned key2 = lane == g1 ? 0xffffffffu : key;
-            const unsigned k2 = __reduce_min_sync(0xffffffffu, key2);
-            int g2 = -1;
-            if (k2 != 0xffffffffu) {
-                g2 = __ffs(__ballot_sync(0xffffffffu, key2 == k2)) - 1;
-                if (__shfl_sync(0xffffffffu, lbg, g2) <= u3) live &= ~(1u << g2);
-                else g2 = -1;
-            }
-            const int p1 = (blk * 32 + g1) * 32 + lane;
-            const int p2 = g2 >= 0 ? (blk * 32 + g2) * 32 + lane : n;
-            const SeedRec32 q1 = p1 < n ? r32[p1] : zrec;
-            const SeedRec32 q2 = p2 < n ? r32[p2] : zrec;
-            float lb, ub1 = finf, ub2 = finf;
-            if (p1 < n) seed_bounds<D>(q1, ch, cl, rlo, rhi, wrh, wrl, lb, ub1);
-            if (p2 < n) seed_bounds<D>(q2, ch, cl, rlo, rhi, wrh, wrl, lb, ub2);
-            merge_smallest4(p1 < n ? okey(ub1) : 0xffffffffu, u0, u1, u2, u3);
-            if (g2 >= 0) merge_smallest4(p2 < n ? okey(ub2) : 0xffffffffu, u0, u1, u2, u3);
+        const bool valid = grp < n_groups;
+        const float lbg = valid ? group_lower<D>(groups[grp], alo, ahi) : finf;
+        const unsigned key = valid ? okey(lbg) : 0xffffffffu;
+        int rank = 0;  // position of this lane's group in increasing bound order (ties by lane)
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const unsigned kj = __shfl_sync(0xffffffffu, key, j);
+            rank += (kj < key || (kj == key && j < lane)) ? 1 : 0;
+        }
+        const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+        for (int r = wid; r < nvalid; r += W) {
+            const int gl = __ffs(__ballot_sync(0xffffffffu, valid && rank == r)) - 1;
+            const float bnd = __shfl_sync(0xffffffffu, lbg, gl);
+            if (bnd > fminf(u3, okey_inv(*(volatile unsigned *)&s_T))) break;
+            const int p = (blk * 32 + gl) * 32 + lane;
+            const SeedRec32 q = p < n ? r32[p] : zrec;
+            float lb, ub = finf;
+            if (p < n) seed_bounds<D>(q, ch, cl, rlo, rhi, wrh, wrl, lb, ub);
+            merge_smallest4(p < n ? okey(ub) : 0xffffffffu, u0, u1, u2, u3);
+            if (lane == 0) atomicMin(&s_T, okey(u3));
         }
     }
-    // pass 2: the list and T_excl (groups two at a time, records loaded together)
-    const float T = u3;
+    if (lane == 0) {
+        s_u[wid][0] = u0;
+        s_u[wid][1] = u1;
+        s_u[wid][2] = u2;
+        s_u[wid][3] = u3;
+    }
+    __syncthreads();
+    float T;
+    {  // the fourth smallest of the warps' four smallest (the same in every warp)
+        unsigned k = okey((&s_u[0][0])[lane]);
+        unsigned m = 0xffffffffu;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            m = __reduce_min_sync(0xffffffffu, k);
+            const int l = __ffs(__ballot_sync(0xffffffffu, k == m)) - 1;
+            if (lane == l) k = 0xffffffffu;
+        }
+        T = okey_inv(m);
+    }
+    // Pass 2: the candidates (lower bound <= T), the groups with a bound <= T
+    // shared out by rank as above, each warp's list kept in shared memory; then
+    // the lists are stored in warp order, and T_excl = the smallest bound of all
+    // that is left out (skipped groups by their bound, seeds by theirs).
     float tex = finf;
     int cnt = 0;
-    int *out = slist + (size_t)sup * kSuperCap;
-    auto take = [&](const SeedRec32 &q, int pos) {
-        float lb = finf, ub = finf;
-        if (pos < n) seed_bounds<D>(q, ch, cl, rlo, rhi, wrh, wrl, lb, ub);
-        const bool cand = pos < n && lb <= T;
-        const unsigned cm = __ballot_sync(0xffffffffu, cand);
-        const int rank = __popc(cm & ((1u << lane) - 1u));
-        if (cand) {
-            if (cnt + rank < kSuperCap) out[cnt + rank] = pos;
-            else tex = fminf(tex, lb);  // beyond the capacity: excluded
-        } else if (pos < n) {
-            tex = fminf(tex, lb);
-        }
-        cnt += __popc(cm);
-    };
     for (int bi = 0; bi < n_blocks; ++bi) {
         const int blk = block_of(bi);
         const int grp = blk * 32 + lane;
-        const float lbg = grp < n_groups ? group_lower<D>(groups[grp], alo, ahi) : finf;
-        const bool in = grp < n_groups && lbg <= T;
-        tex = fminf(tex, in ? finf : lbg);
-        unsigned todo = __ballot_sync(0xffffffffu, in);
-        while (todo) {
-            const int ga = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            int gb = -1;
-            if (todo) {
-                gb = __ffs(todo) - 1;
-                todo &= todo - 1u;
+        const bool valid = grp < n_groups;
+        const float lbg = valid ? group_lower<D>(groups[grp], alo, ahi) : finf;
+        const bool in = valid && lbg <= T;
+        tex = fminf(tex, (valid && !in) ? lbg : finf);
+        const unsigned inm = __ballot_sync(0xffffffffu, in);
+        const int rin = __popc(inm & ((1u << lane) - 1u));
+        for (int r = wid; r < __popc(inm); r += W) {
+            const int gl = __ffs(__ballot_sync(0xffffffffu, in && rin == r)) - 1;
+            const int p = (blk * 32 + gl) * 32 + lane;
+            const SeedRec32 q = p < n ? r32[p] : zrec;
+            float lb = finf, ub = finf;
+            if (p < n) seed_bounds<D>(q, ch, cl, rlo, rhi, wrh, wrl, lb, ub);
+            const bool cand = p < n && lb <= T;
+            const unsigned cm = __ballot_sync(0xffffffffu, cand);
+            const int e = cnt + __popc(cm & ((1u << lane) - 1u));
+            if (cand) {
+                if (e < kSuperCap) {
+                    s_pos[wid][e] = p;
+                    s_lb[wid][e] = lb;
+                } else {
+                    tex = fminf(tex, lb);  // beyond the capacity: excluded
+                }
+            } else if (p < n) {
+                tex = fminf(tex, lb);
             }
-            const int pa = (blk * 32 + ga) * 32 + lane;
-            const int pb = gb >= 0 ? (blk * 32 + gb) * 32 + lane : n;
-            const SeedRec32 qa = pa < n ? r32[pa] : zrec;
-            const SeedRec32 qb = pb < n ? r32[pb] : zrec;
-            take(qa, pa);
-            if (gb >= 0) take(qb, pb);
+            cnt += __popc(cm);
         }
     }
+    const int cnt_c = min(cnt, kSuperCap);
     tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
     if (lane == 0) {
-        scount[sup] = min(cnt, kSuperCap);
-        stex[sup] = tex;
+        s_cnt[wid] = cnt_c;
+        s_tex[wid] = tex;
+    }
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < wid; ++w) off += s_cnt[w];
+    float tex2 = finf;
+    int *out = slist + (size_t)sup * kSuperCap;
+    for (int e = lane; e < cnt_c; e += 32) {
+        if (off + e < kSuperCap) out[off + e] = s_pos[wid][e];
+        else tex2 = fminf(tex2, s_lb[wid][e]);  // beyond the capacity: excluded
+    }
+    tex2 = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex2)));
+    if (lane == 0) s_tex2[wid] = tex2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int total = 0;
+        float tx = finf;
+        for (int w = 0; w < W; ++w) {
+            total += s_cnt[w];
+            tx = fminf(tx, fminf(s_tex[w], s_tex2[w]));
+        }
+        scount[sup] = min(total, kSuperCap);
+        stex[sup] = tx;
     }
 }
 
@@ -1396,7 +1491,7 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     if (pruned) {
         const SuperGeom sg{ntx, nty, ntz, tlo};
         const int nsup = ((ntx + 1) / 2) * ((nty + 1) / 2) * (D == 3 ? (ntz + 1) / 2 : 1);
-        tc_super_kernel<D><<<(nsup * 32 + 255) / 256, 256, 0, st>>>(g, sg, nsup, n, rs, ws.groups,
+        tc_super_kernel<D><<<nsup, kSupWarps * 32, 0, st>>>(g, sg, nsup, n, rs, ws.groups,
                                                                     ws.sorted ? ws.scodes : nullptr, ws.tc_axis,
                                                                     ws.tc_slist, ws.tc_scount, ws.tc_stex, ws.sc);
         ws.kernel_launches += 2;

@@ -121,6 +121,33 @@ void destroy_graph(EvalGraph &e) {
     e = EvalGraph();
 }
 
+// Whether a pass scores with the tensor-core kernel: asked for, a grid the
+// workspace's tile scratch covers, and seeds conditioned well enough for its
+// certificate and candidate bounds (max ||A||_F / min lambda_min <= kTcMaxCond;
+// beyond that the FP32 kernel is faster and gives the same labels: measured on
+// the runtime tests' 3D alpha laws, the tensor-core form wins at ratios up to
+// 7.4 and loses 3.6x at 11.7).  The
+// conditioning comes from the seed preparation: read back once per preparation
+// (a stream synchronisation); passes that reuse the records reuse the value.
+constexpr double kTcMaxCond = 10.0;
+bool use_tensor_cores(const GridDev &g, apd_precision prec, Workspace &ws, bool weights_only, cudaStream_t st) {
+    if (prec == APD_FP32 || tc_tile_count(g) > ws.tc_tile_cap) return false;
+    if (!weights_only) {
+        unsigned long long bits[2] = {0ull, 0ull};  // lam_abs_bits, lam_min_bits
+        if (cudaMemcpyAsync(&ws.sc_host->lam_abs_bits, &ws.sc->lam_abs_bits, 2 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess) {
+            bits[0] = ws.sc_host->lam_abs_bits;
+            bits[1] = ws.sc_host->lam_min_bits;
+        }
+        double lam_abs = 0.0, lam_min = 0.0;
+        std::memcpy(&lam_abs, &bits[0], sizeof lam_abs);
+        std::memcpy(&lam_min, &bits[1], sizeof lam_min);
+        ws.tc_cond = lam_min > 0.0 ? lam_abs / lam_min : INFINITY;
+    }
+    return ws.tc_cond <= kTcMaxCond;
+}
+
 // Queues one pass of scoring + rescoring + moments at weights w.  With
 // weights_only the records of the previous pass (same x, A, n) are reused and
 // only the weights change; with a step, w (device, n) is first set to
@@ -172,7 +199,7 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
     // the tensor-core tiling needs per-tile scratch; grids too thin for the
     // workspace's tile capacity are scored by the FP32 kernel (same labels)
     if (empty) {
-    } else if (prec == APD_FP32 || tc_tile_count(g) > ws.tc_tile_cap)
+    } else if (!use_tensor_cores(g, prec, ws, weights_only, st))
         APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
     else
         APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
@@ -254,7 +281,7 @@ struct Solver {
         if (!ws.graphs || !geometry_ready || ws.shard_world > 1) return APD_OK;
         struct Key {
             int dim, res[3], kz0, kz1, n, prec, prune, sorted, profiling, has_step;
-            uint32_t wait_limit, pad;
+            uint32_t wait_limit, use_tc;
             double lo[3], h[3];
             const void *ptr[9];
         } k;
@@ -274,6 +301,9 @@ struct Solver {
         k.profiling = ws.profiling ? 1 : 0;
         k.has_step = step ? 1 : 0;
         k.wait_limit = ws.wait_limit;
+        // the scorer the captured pass takes (the seeds' conditioning can change it between solves)
+        const bool tc = use_tensor_cores(g, prec, ws, true, st);
+        k.use_tc = tc ? 1u : 0u;
         const void *ptrs[9] = {x, A, v, Wp, gf_out, pdir, step ? step->W : nullptr, step ? step->p : nullptr,
                                ws.moments};
         std::memcpy(k.ptr, ptrs, sizeof ptrs);
@@ -344,7 +374,7 @@ struct Solver {
             eg = &ws.graph_cache.back();
         }
         eg->used = ++ws.graph_clock;
-        if (prec != APD_FP32) APD_TRY(cuda_ok(launch_tc_axis(g, ws, st)));
+        if (tc) APD_TRY(cuda_ok(launch_tc_axis(g, ws, st)));
         if (step)
             APD_TRY(cuda_ok(set_eval_begin_node(eg->exec, eg->begin, n, step->W, step->t, step->p,
                                                 const_cast<double *>(Wp), ws.moments, ws)));
@@ -1277,11 +1307,12 @@ void apd_multires_opts_default(apd_multires_opts *mo) {
     mo->coarse_eps = 0.05;
     mo->coarse_max_evals = 60;
     mo->carry_history = 0;
+    mo->min_cell_span = 8;
 }
 
 // Coarse grid of a coarse-to-fine solve (same box, ceil(res / factor) >= 4 per axis).
 static int coarse_grid(const apd_grid *grid, const apd_multires_opts &m, apd_grid &cg, GridDev &gc) {
-    if (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1) return APD_ERR_ARG;
+    if (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1 || m.min_cell_span < 0) return APD_ERR_ARG;
     cg = *grid;
     for (int d = 0; d < grid->dim; ++d) cg.res[d] = std::max(4, (grid->res[d] + m.factor - 1) / m.factor);
     return validate_grid(&cg, gc);
@@ -1320,6 +1351,11 @@ static int c2f_solve(const GridDev &g, const apd_grid *grid, const GridDev &gc, 
                      const apd_solve_opts &o, const apd_multires_opts &m, apd_solve_info &inf,
                      apd_solve_info &cinf, Workspace &ws, cudaStream_t st, bool judged, int *used,
                      bool need_moments_at_out) {
+    // cells of fewer than min_cell_span^D coarse pixels on average cannot reach the
+    // coarse tolerance: the solve then runs on the fine grid alone
+    const double span_d = std::pow((double)m.min_cell_span, (double)g.dim);
+    if (m.min_cell_span > 0 && (double)gc.J < span_d * (double)n)
+        return solve_impl(g, grid, n, x, A, w0, v, w_out, o, inf, ws, st, need_moments_at_out, judged, used);
     apd_solve_opts oc = o;
     oc.eps = m.coarse_eps;
     oc.max_evals = m.coarse_max_evals;

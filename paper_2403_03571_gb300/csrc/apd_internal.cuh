@@ -141,6 +141,7 @@ struct Workspace {
     uint8_t *tc_bops = nullptr;         // [tc_tile_cap] x tc_bops_bytes_per_tile(): stored seed operands
     float4 *tc_axis = nullptr;          // [3 tc_tile_cap] per-axis tile centres and pixel boxes
     double tc_axis_key[12] = {};        // the grid and tiling tc_axis was computed for (all 0: none)
+    double tc_cond = 0.0;               // max ||A||_F / min lambda_min of the last prepared seeds
     int *tc_slist = nullptr;            // [tc_tile_cap][tc_super_cap()] candidates of the super-tiles
     int *tc_scount = nullptr;           // [tc_tile_cap] their counts
     float *tc_stex = nullptr;           // [tc_tile_cap] their bounds of the seeds left out
@@ -221,14 +222,17 @@ struct GridDev {
     long long J;  // pixels of the full grid
     int kz0, kz1;
 };
+// the last axis's resolution (a select, not a dynamic index: an indexed access
+// to a kernel's by-value GridDev makes the compiler copy it to the stack)
+__host__ __device__ inline int res_last(const GridDev &g) { return g.dim == 3 ? g.res[2] : g.res[1]; }
 __host__ __device__ inline int win_lo(const GridDev &g) { return g.kz0; }
-__host__ __device__ inline int win_hi(const GridDev &g) { return g.kz1 ? g.kz1 : g.res[g.dim - 1]; }
+__host__ __device__ inline int win_hi(const GridDev &g) { return g.kz1 ? g.kz1 : res_last(g); }
 // pixels of the window and the full-grid id of its first pixel
 __host__ __device__ inline long long win_pixels(const GridDev &g) {
-    return g.J / g.res[g.dim - 1] * (long long)(win_hi(g) - win_lo(g));
+    return g.J / res_last(g) * (long long)(win_hi(g) - win_lo(g));
 }
 __host__ __device__ inline long long win_first(const GridDev &g) {
-    return g.J / g.res[g.dim - 1] * (long long)win_lo(g);
+    return g.J / res_last(g) * (long long)win_lo(g);
 }
 
 // ----------------------------------------------------------------------------

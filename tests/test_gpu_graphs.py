@@ -46,11 +46,11 @@ def _run(capi, inst, kind, prec, prune, graphs, profile=False):
         x_out.copy_(x)
     elif kind == "multires":
         rc, info, _ = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws, opts,
-                                                      capi.multires_opts(2, 0.015, 200))
+                                                      capi.multires_opts(2, 0.015, 200, min_cell_span=0))
         x_out.copy_(x)
     else:
         rc, info, _ = capi.apd_lloyd_multires(inst.grid, x, A, w, v, 2, x_out, w_out, ws, opts,
-                                              capi.multires_opts(2, 0.015, 200))
+                                              capi.multires_opts(2, 0.015, 200, min_cell_span=0))
     prof = ws.profile_read() if profile else None
     return rc, info.as_dict(), host(x_out), host(w_out), prof
 

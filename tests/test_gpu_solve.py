@@ -102,7 +102,8 @@ def test_coarse_to_fine_solve(capi, dim, n, m, seed):
     x, A, w, v = instance_tensors(inst)
     ws = capi.Workspace(dim, n, inst.grid.num_pixels)
     w_out = torch.zeros_like(w)
-    rc, info, used = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws)
+    rc, info, used = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws,
+                                                     mopts=capi.multires_opts(min_cell_span=0))
     assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
     assert used == 0 and info.coarse_evaluations >= 1 and info.solves == 2
     _, _, err = oracle.dual(inst.grid, inst.x, inst.A, host(w_out), inst.v)
@@ -121,7 +122,8 @@ def test_lloyd_coarse_to_fine(capi):
     ws.set_pruning(True)
     x_out, w_out = torch.zeros_like(x), torch.zeros_like(w)
     rc, info, used = capi.apd_lloyd_multires(inst.grid, x, A, w, v, 3, x_out, w_out, ws,
-                                             mopts=capi.multires_opts(2, 0.02, 60), net=warmstart.load(3))
+                                             mopts=capi.multires_opts(2, 0.02, 60, min_cell_span=0),
+                                             net=warmstart.load(3))
     assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
     assert info.solves == 8 and info.coarse_evaluations >= 4
     X, W = host(x_out), host(w_out)
@@ -130,6 +132,23 @@ def test_lloyd_coarse_to_fine(capi):
     assert err < 0.01
     # ... and the positions moved: they are the discrete centroids of an earlier round
     assert np.abs(X - inst.x).max() > 1e-3
+
+
+def test_coarse_solve_skipped_for_small_cells(capi):
+    # 300 seeds on 64^3: the 32^3 coarse grid has ~109 pixels per seed (< 8^3), so
+    # the default options solve on the fine grid alone; min_cell_span = 0 forces
+    # the coarse solve; both results meet the stop rule (oracle)
+    inst = synth.make_instance(3, 300, 64, 12)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(3, inst.n, inst.grid.num_pixels)
+    for span, solves in ((None, 1), (0, 2)):
+        w_out = torch.zeros_like(w)
+        mo = capi.multires_opts() if span is None else capi.multires_opts(min_cell_span=span)
+        rc, info, _ = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws, mopts=mo)
+        assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+        assert info.solves == solves and (info.coarse_evaluations == 0) == (solves == 1)
+        _, _, err = oracle.dual(inst.grid, inst.x, inst.A, host(w_out), inst.v)
+        assert err < 0.01
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tc_tf32"])
@@ -148,7 +167,8 @@ def test_lloyd_coarse_history_carried(capi, prec):
         ws.set_pruning(True)
         x_out, w_out = torch.zeros_like(x), torch.zeros_like(w)
         rc, info, _ = capi.apd_lloyd_multires(inst.grid, x, A, w, v, 4, x_out, w_out, ws, opts,
-                                              capi.multires_opts(2, 0.015, 200, carry_history=True))
+                                              capi.multires_opts(2, 0.015, 200, carry_history=True,
+                                                                 min_cell_span=0))
         assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
         assert info.solves == 10
         outs.append((host(x_out), host(w_out), info.as_dict()))

@@ -15,12 +15,16 @@ costs C' = (y - x)^T A (y - x) + (w_ref - w):
   1. every packed score lies within err_unit * sum_k |f_k phi_k| of C';
   2. the candidate pre-pass's lower bound (lambda_min dist^2 + (w_ref - w),
      FP32 with its directed roundings and slacks, restated with exact
-     rounding) never exceeds C' at a pixel of the tile;
+     rounding) never exceeds C' at a pixel of the tile; nor does its second,
+     centre form (q - 2 sum |(A d)_a| r_a with d the box centre's offset), and
+     the centre form's upper bound is never below C' (boxes of one tile and of
+     a 2 x 2 (x 2) super-tile, conditioning up to 10^3);
   3. the certificate: whenever s1 + psi(s1) < min(s2 - psi(s2), T_excl), the
      best score's seed is the exact argmin over all seeds (those left out of
      the candidate list included).
-Planted mistakes: operands that are not split, and a lower bound built with
-the largest eigenvalue in place of the smallest, must fail."""
+Planted mistakes: operands that are not split, a lower bound built with the
+largest eigenvalue in place of the smallest, and a centre form without its
+linear term must fail."""
 from fractions import Fraction as Fr
 
 import numpy as np
@@ -251,3 +255,92 @@ def test_lower_bound_with_lambda_max_is_violated():
                 y = [(Fr(kb[a] + lk[a]) + Fr(1, 2)) * Fr(float(h[a])) for a in range(3)]
                 viol += Fr(float(lb)) > exact_cost(y, xs[i], As[i], ws[i], wref)
     assert viol > 0
+
+
+def ru32(x):
+    """Smallest float32 >= the rational x (exact directed rounding)."""
+    return -rd32(-x)
+
+
+def centre_bounds(D, xp, wp, A, lam_i, lmax_i, rlo, rhi, with_lin=True):
+    """The pre-pass's bounds with both forms, restated: FP32 round-to-nearest
+    where the kernel rounds to nearest, exact directed rounding where it rounds
+    up or down.  Returns (lower, upper) = (max of the forms, min of the forms)."""
+    a32 = [[f32(A[i][j]) for j in range(D)] for i in range(D)]
+    d2lo, d2hi = f32(0.0), f32(0.0)
+    dv, rr = [], []
+    for a in range(D):
+        xs = xp[a]
+        slack = f32(f32(f32(1e-6) * f32(f32(abs(rlo[a]) + abs(rhi[a])) + f32(2.0) * abs(xs))) + f32(1e-30))
+        dl = max(f32(max(f32(xs - rhi[a]), f32(rlo[a] - xs)) - slack), f32(0.0))
+        dh = f32(max(abs(f32(xs - rlo[a])), abs(f32(xs - rhi[a]))) + slack)
+        d2lo = rd32(Fr(float(dl)) * Fr(float(dl)) + Fr(float(d2lo)))
+        d2hi = ru32(Fr(float(dh)) * Fr(float(dh)) + Fr(float(d2hi)))
+        dv.append(f32(f32(f32(0.5) * f32(rlo[a] + rhi[a])) - xs))
+        rr.append(f32(f32(f32(0.5) * f32(rhi[a] - rlo[a])) + slack))
+    wn = f32(-wp)
+    wslack = f32(f32(f32(1e-6) * abs(wn)) + f32(1e-30))
+    lo_w, hi_w = rd32(Fr(float(wn)) - Fr(float(wslack))), ru32(Fr(float(wn)) + Fr(float(wslack)))
+    lb1 = rd32(Fr(float(rd32(Fr(float(rd32(Fr(float(lam_i)) * Fr(float(d2lo))))) * Fr(float(f32(1.0 - 1e-5))))))
+               + Fr(float(lo_w)))
+    ub1 = ru32(Fr(float(ru32(Fr(float(ru32(Fr(float(lmax_i)) * Fr(float(d2hi))))) * Fr(float(f32(1.0 + 1e-5))))))
+               + Fr(float(hi_w)))
+    q = lin = quad = S = f32(0.0)
+    for a in range(D):
+        ga = qa = sa = f32(0.0)
+        for b in range(D):
+            ga = fma32(a32[a][b], dv[b], ga)
+            qa = fma32(abs(a32[a][b]), rr[b], qa)
+            sa = fma32(abs(a32[a][b]), f32(abs(dv[b]) + rr[b]), sa)
+        q = fma32(dv[a], ga, q)
+        lin = fma32(abs(ga), rr[a], lin)
+        quad = fma32(qa, rr[a], quad)
+        S = fma32(sa, f32(abs(dv[a]) + rr[a]), S)
+    lin = f32(2.0) * lin if with_lin else f32(0.0)
+    E = f32(f32(f32(1e-5) * S) + f32(1e-30))
+    lb2 = rd32(Fr(float(rd32(Fr(float(rd32(Fr(float(q)) - Fr(float(lin))))) - Fr(float(E))))) + Fr(float(lo_w)))
+    ub2 = ru32(Fr(float(ru32(Fr(float(ru32(Fr(float(q)) + Fr(float(lin))))) + Fr(float(ru32(Fr(float(quad)) + Fr(float(E)))))))) + Fr(float(hi_w)))
+    return max(lb1, lb2), min(ub1, ub2), lb2 > lb1
+
+
+def centre_case(D, seed, super_box, with_lin=True, n=30, pixels=12):
+    """(lower-bound violations, upper-bound violations, seeds whose centre form is
+    the tighter lower bound) over random seeds and pixels of one box."""
+    g, h, td, kb, cen, R, xs, As, ws, wref = make_tile(D, seed, n)
+    xs = np.array(cen) + (xs - np.array(cen)) * g.uniform(1.0, 4.0, (n, 1))  # near and farther seeds
+    h32 = [f32(v) for v in h]
+    span = [2 * td[a] if super_box else td[a] for a in range(D)]
+    rlo = [f32(f32(f32(-(td[a] // 2)) + f32(0.5)) * h32[a]) for a in range(D)]
+    rhi = [f32(f32(f32(span[a] - 1 - td[a] // 2) + f32(0.5)) * h32[a]) for a in range(D)]
+    bad_lo = bad_hi = tighter = 0
+    for i in range(n):
+        A = As[i]
+        ev = np.linalg.eigvalsh(A)
+        lam_i = f32(ev.min() * (1 - 1e-6))
+        lmax_i = f32(ev.max() * (1 + 1e-6))
+        _, xp, wp = seed_features(D, xs[i], A, ws[i], cen, wref)
+        lb, ub, t = centre_bounds(D, xp, wp, A, lam_i, lmax_i, rlo, rhi, with_lin)
+        tighter += t
+        for _ in range(pixels):
+            lk = [int(g.integers(0, span[a])) for a in range(D)]
+            y = [(Fr(kb[a] + lk[a]) + Fr(1, 2)) * Fr(float(h[a])) for a in range(D)]
+            c = exact_cost(y, xs[i], A, ws[i], wref)
+            bad_lo += Fr(float(lb)) > c
+            bad_hi += Fr(float(ub)) < c
+    return bad_lo, bad_hi, tighter
+
+
+@pytest.mark.parametrize("D", [3, 2])
+@pytest.mark.parametrize("super_box", [False, True])
+def test_centre_form_bounds(D, super_box):
+    tighter = 0
+    for seed in range(6):  # conditioning 1, 10, 10^3 by seed
+        lo, hi, t = centre_case(D, seed, super_box)
+        assert (lo, hi) == (0, 0), seed
+        tighter += t
+    assert tighter > 0  # the centre form does improve on the eigenvalue form somewhere
+
+
+def test_centre_form_without_its_linear_term_is_violated():
+    # planted mistake: the lower bound q - E without -2 sum |(A d)_a| r_a
+    assert sum(centre_case(3, seed, False, with_lin=False)[0] for seed in range(3)) > 0
