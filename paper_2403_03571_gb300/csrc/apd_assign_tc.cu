@@ -16,19 +16,23 @@
 //
 // Candidate lists (pruned form).  A pre-pass gives every 512-pixel CTA tile
 // the seeds that can matter there: with rigorous FP32 bounds over the box of
-// the tile's pixel centres,
-//     LB_i = lambda_min,i dist(x_i, box)^2 + (w_ref - w_i) <= C'_i <= UB_i
-//          = lambda_max,i maxdist(x_i, box)^2 + (w_ref - w_i),
-// and T the fourth smallest UB_i, the list holds the seeds with LB_i <= T
-// (visited by 32-seed Morton groups in increasing order of their group bound).
-// T_excl = the smallest LB of every seed left out is a lower bound of every
-// excluded seed's cost at every pixel of the tile.  The dense form takes all
-// seeds, in 32-seed chunks zig-zagging out from the tile's Morton position.
+// the tile's pixel centres, LB_i <= C'_i <= UB_i (the better of an eigenvalue
+// form, lambda_min,i dist(x_i, box)^2 and lambda_max,i maxdist(x_i, box)^2,
+// and a centre form around the box centre; plus w_ref - w_i), and T the
+// fourth smallest UB_i, the list holds the seeds with LB_i <= T.  One kernel
+// does it per super-tile of 2 x 2 (x 2) tiles: eight warps visit the 32-seed
+// Morton groups in increasing order of their group bound for the super-tile's
+// box, then each warp narrows the super-tile's list for one tile and stores
+// the tile's list and split seed operands.  T_excl = the smallest LB of every
+// seed left out is a lower bound of every excluded seed's cost at every pixel
+// of the tile.  The dense form takes all seeds, in 32-seed chunks zig-zagging
+// out from the tile's Morton position.
 //
 // Pipeline (one persistent CTA per SM, warp-specialised).  A CTA tile is four
 // M = 128 tiles (one tensor-memory lane per pixel); a step scores 32 seeds of
-// the tile's list: two transform warps build the recentred, split seed
-// operand B (32 x 32) from the FP32 seed records, one thread issues the MMAs
+// the tile's list: the seed operand B (32 x 32, recentred and split) is the
+// stored one of the pruned form, brought in by a 1-D bulk copy, or built from
+// the FP32 seed records by two transform warps (dense form); one thread issues the MMAs
 // (4 M tiles x K = 32) into one of four accumulator stages (4 x 4 x 32 = 512
 // tensor-memory columns), and sixteen epilogue warps (thread = pixel) read the
 // stage with the min-reducing tensor-memory load, release it, and fold the 32
@@ -295,11 +299,9 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// Pre-pass: one warp per tile.  Tile centre (FP32 high/low split), and either
-// the Morton start chunk (dense form) or the candidate list with T_excl.
+// Dense-form pre-pass: one warp per tile writes the tile centre (FP32 high/low
+// split) and the Morton start chunk of the tile's zig-zag seed scan.
 // ---------------------------------------------------------------------------
-// Pruned form: the list ends as seed indices, and the split seed operand of
-// each step (32 list slots, core-matrix layout) is stored in bops[t][k].
 template <int D, int KIND>
 __global__ void __launch_bounds__(256)
     tc_tile_kernel(const GridDev g, const int ntx, const int nty, const int tlo, const int ntiles, const int n,
@@ -358,166 +360,9 @@ __global__ void __launch_bounds__(256)
         }
         spos = min(lo, n - 1);
     }
-    if (!list) {
-        if (lane == 0) {
-            start[t] = spos / kN;
-            meta[t] = make_int4(kb[0], kb[1], kb[2], 0);
-        }
-        return;
-    }
-    // pixel box relative to the centre (FP32, the kernel's offsets)
-    float rlo[3] = {0.f, 0.f, 0.f}, rhi[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        const int c = kb[a] + td[a] / 2;
-        rlo[a] = ((float)(kb[a] - c) + 0.5f) * g.h32[a];
-        rhi[a] = ((float)(khi[a] - c) + 0.5f) * g.h32[a];
-    }
-    const float finf = __int_as_float(0x7f800000);
-    const int n_groups = (n + 31) / 32;
-    const int n_blocks = (n_groups + 31) / 32;
-    const int bstart = min(spos / 1024, n_blocks - 1);
-    auto block_of = [&](int bi) {  // zig-zag out from the tile's block of 32 groups
-        const int off = (bi & 1) ? ((bi + 1) >> 1) : -(bi >> 1);
-        int blk = bstart + off;
-        if (blk >= n_blocks) blk -= n_blocks;
-        if (blk < 0) blk += n_blocks;
-        return blk;
-    };
-    auto group_lb = [&](int grp) {  // lower bound of the group's costs over the tile
-        float lbg = finf;
-        if (grp < n_groups) {
-            const GroupBound gb = groups[grp];
-            float d2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const float slack = 1e-6f * (fabsf(alo[a]) + fabsf(ahi[a]) + fabsf(gb.lo[a]) + fabsf(gb.hi[a]));
-                const float q = fmaxf(fmaxf(gb.lo[a] - ahi[a], alo[a] - gb.hi[a]) - slack, 0.f);
-                d2 = __fmaf_rd(q, q, d2);
-            }
-            lbg = __fadd_rd(__fmul_rd(__fmul_rd(gb.lam, d2), 1.f - 1e-5f), gb.wgap);
-        }
-        return lbg;
-    };
-    auto seed_bounds = [&](int pos, float &lb, float &ub) {  // bounds of one seed's costs over the tile
-        lb = finf;
-        ub = finf;
-        if (pos >= n) return;
-        const SeedRec32 r = r32[pos];
-        float d2lo = 0.f, d2hi = 0.f;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const float xs = (r.xh[a] - ch[a]) + (r.xl[a] - cl[a]);
-            const float slack = 1e-6f * (fabsf(rlo[a]) + fabsf(rhi[a]) + 2.f * fabsf(xs)) + 1e-30f;
-            const float dl = fmaxf(fmaxf(xs - rhi[a], rlo[a] - xs) - slack, 0.f);
-            const float dh = fmaxf(fabsf(xs - rlo[a]), fabsf(xs - rhi[a])) + slack;
-            d2lo = __fmaf_rd(dl, dl, d2lo);
-            d2hi = __fmaf_ru(dh, dh, d2hi);
-        }
-        const float wn = -((r.wh - wrh) + (r.wl - wrl));  // w_ref - w_i, up to rounding
-        const float wslack = 1e-6f * fabsf(wn) + 1e-30f;
-        lb = __fadd_rd(__fmul_rd(__fmul_rd(r.pad[0], d2lo), 1.f - 1e-5f), __fsub_rd(wn, wslack));
-        ub = __fadd_ru(__fmul_ru(__fmul_ru(r.pad[1], d2hi), 1.f + 1e-5f), __fadd_ru(wn, wslack));
-    };
-    // Pass 1: T = the fourth smallest upper bound.  Groups are visited in
-    // increasing order of their bound within each block; a group whose bound
-    // exceeds the current T holds no seed with a smaller upper bound, so T is the
-    // fourth smallest upper bound of all seeds.
-    float u0 = finf, u1 = finf, u2 = finf, u3 = finf;  // warp-uniform, ascending
-    for (int bi = 0; bi < n_blocks; ++bi) {
-        const int blk = block_of(bi);
-        const float lbg = group_lb(blk * 32 + lane);
-        unsigned live = __ballot_sync(0xffffffffu, blk * 32 + lane < n_groups);
-        while (live) {
-            const bool mine = (live >> lane) & 1u;
-            const unsigned key = mine ? okey(lbg) : 0xffffffffu;
-            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
-            const int kg = __ffs(__ballot_sync(0xffffffffu, mine && key == kmin)) - 1;
-            if (__shfl_sync(0xffffffffu, lbg, kg) > u3) break;
-            live &= ~(1u << kg);
-            float lb, ub;
-            seed_bounds((blk * 32 + kg) * 32 + lane, lb, ub);
-            unsigned ku = okey(ub);
-            if (__reduce_min_sync(0xffffffffu, ku) < okey(u3)) {
-                float b[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const unsigned m = __reduce_min_sync(0xffffffffu, ku);
-                    b[e] = okey_inv(m);
-                    const int l = __ffs(__ballot_sync(0xffffffffu, ku == m)) - 1;
-                    if (lane == l) ku = 0xffffffffu;
-                }
-                // the four smallest of two ascending lists of four: the elementwise
-                // minima of one list against the other reversed, then sorted
-                float c0 = fminf(u0, b[3]), c1 = fminf(u1, b[2]), c2 = fminf(u2, b[1]), c3 = fminf(u3, b[0]);
-                auto cswap = [](float &x, float &y) {
-                    const float lo = fminf(x, y), hi = fmaxf(x, y);
-                    x = lo;
-                    y = hi;
-                };
-                cswap(c0, c2);
-                cswap(c1, c3);
-                cswap(c0, c1);
-                cswap(c2, c3);
-                cswap(c1, c2);
-                u0 = c0;
-                u1 = c1;
-                u2 = c2;
-                u3 = c3;
-            }
-        }
-    }
-    // Pass 2: the list = the seeds with LB <= T (only groups with a bound <= T can
-    // hold them, and pass 1 visited exactly those); T_excl = the smallest bound of
-    // the rest (a group's bound stands for its seeds when the group is skipped).
-    const float T = u3;
-    float tex = finf;
-    int cnt = 0;
-    for (int bi = 0; bi < n_blocks; ++bi) {
-        const int blk = block_of(bi);
-        const float lbg = group_lb(blk * 32 + lane);
-        const bool in = blk * 32 + lane < n_groups && lbg <= T;
-        tex = fminf(tex, in ? finf : lbg);
-        unsigned todo = __ballot_sync(0xffffffffu, in);
-        while (todo) {
-            const int kg = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            const int pos = (blk * 32 + kg) * 32 + lane;
-            float lb, ub;
-            seed_bounds(pos, lb, ub);
-            const bool real = pos < n;
-            const bool cand = real && lb <= T;
-            const unsigned cm = __ballot_sync(0xffffffffu, cand);
-            const int rank = __popc(cm & ((1u << lane) - 1u));
-            float rej = finf;
-            if (cand) {
-                if (cnt + rank < kListCap) list[(size_t)t * kListCap + cnt + rank] = pos;
-                else rej = lb;  // beyond the list's capacity: treated as excluded
-            } else if (real) {
-                rej = lb;
-            }
-            cnt += __popc(cm);
-            tex = fminf(tex, rej);
-        }
-    }
-    tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
-    const int cnt_c = min(cnt, kListCap);
     if (lane == 0) {
-        meta[t] = make_int4(kb[0], kb[1], kb[2], cnt_c);
-        texcl[t] = tex;
-    }
-    __syncwarp();  // the list entries written by the other lanes
-    const int ns = max(1, (cnt_c + kN - 1) / kN);
-    for (int k = 0; k < ns; ++k) {
-        const int slot = k * kN + lane;
-        const int pos = slot < cnt_c ? list[(size_t)t * kListCap + slot] : -1;
-        float row[kK];
-        seed_row<D, KIND>(r32, pos, ch, cl, wrh, wrl, row);
-        uint8_t *dst = bops + ((size_t)t * kMaxSteps + k) * Fm::B_BYTES;
-#pragma unroll
-        for (int c = 0; c < kK / Fm::EPR; ++c)
-            put_row<KIND>(dst + tc::core_offset(lane, c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO), row + c * Fm::EPR);
-        if (pos >= 0) list[(size_t)t * kListCap + slot] = perm ? perm[pos] : pos;  // seed index for the labels
+        start[t] = spos / kN;
+        meta[t] = make_int4(kb[0], kb[1], kb[2], 0);
     }
 }
 
@@ -692,14 +537,99 @@ __device__ __forceinline__ void range_box(const GridDev &g, const SuperGeom &sg,
     }
 }
 
+// Pruned form, step 2 (in the same kernel, one warp per tile of the
+// super-tile): the warp narrows the super-tile's list with the tile's own
+// bounds (the fourth smallest upper bound over the tile), sets T_excl = min(the
+// super-tile's, the bounds of the seeds it drops), and stores its list (seed
+// indices) and split seed operands.  sl: the super-tile's list (shared memory).
+template <int D, int KIND>
+__device__ __forceinline__ void tile_list(const GridDev &g, const SuperGeom &sg, const int t, const int (&tc3)[3],
+                                          const SeedRec32 *__restrict__ r32, const int32_t *__restrict__ perm,
+                                          const float4 *__restrict__ axis_tab, const int *sl, const int cntS,
+                                          const float tex_sup, float *__restrict__ centre, int4 *__restrict__ meta,
+                                          float *__restrict__ texcl, int *__restrict__ list, uint8_t *__restrict__ bops,
+                                          const float wrh, const float wrl) {
+    using G = TcGeom<D>;
+    using Fm = TcFmt<KIND>;
+    const int lane = threadIdx.x & 31;
+    const float finf = __int_as_float(0x7f800000);
+    float ch[3], cl[3], rlo[3], rhi[3], alo[3], ahi[3];
+    range_box<D>(g, sg, axis_tab, tc3, tc3, ch, cl, rlo, rhi, alo, ahi);
+    if (lane < 6) centre[(size_t)t * 6 + lane] = lane < 3 ? ch[lane] : cl[lane - 3];
+    // the tile's bounds of the super-tile's candidates: at most 8 rounds of 32,
+    // taken two at a time (indices, then records, loaded together)
+    float lbv[kSuperCap / 32];
+    float u0 = finf, u1 = finf, u2 = finf, u3 = finf;
+    const SeedRec32 zrec{};
+#pragma unroll
+    for (int r = 0; r < kSuperCap / 32; r += 2) {
+        lbv[r] = lbv[r + 1] = finf;
+        if (r * 32 < cntS) {
+            const int e0 = r * 32 + lane, e1 = e0 + 32;
+            const int i0 = e0 < cntS ? sl[e0] : -1, i1 = e1 < cntS ? sl[e1] : -1;
+            const SeedRec32 q0 = i0 >= 0 ? r32[i0] : zrec;
+            const SeedRec32 q1 = i1 >= 0 ? r32[i1] : zrec;
+            float ub0 = finf, ub1 = finf;
+            if (i0 >= 0) seed_bounds<D>(q0, ch, cl, rlo, rhi, wrh, wrl, lbv[r], ub0);
+            if (i1 >= 0) seed_bounds<D>(q1, ch, cl, rlo, rhi, wrh, wrl, lbv[r + 1], ub1);
+            merge_smallest4(i0 >= 0 ? okey(ub0) : 0xffffffffu, u0, u1, u2, u3);
+            if ((r + 1) * 32 < cntS) merge_smallest4(i1 >= 0 ? okey(ub1) : 0xffffffffu, u0, u1, u2, u3);
+        }
+    }
+    const float T = u3;
+    float tex = tex_sup;
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kSuperCap / 32; ++r) {
+        if (r * 32 < cntS) {
+            const int e = r * 32 + lane;
+            const bool cand = e < cntS && lbv[r] <= T;
+            const unsigned cm = __ballot_sync(0xffffffffu, cand);
+            const int rank = __popc(cm & ((1u << lane) - 1u));
+            if (cand) {
+                if (cnt + rank < kListCap) list[(size_t)t * kListCap + cnt + rank] = sl[e];
+                else tex = fminf(tex, lbv[r]);
+            } else if (e < cntS) {
+                tex = fminf(tex, lbv[r]);
+            }
+            cnt += __popc(cm);
+        }
+    }
+    tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
+    const int cnt_c = min(cnt, kListCap);
+    if (lane == 0) {
+        const int td[3] = {G::TX, G::TY, G::TZ};
+        const int tl[3] = {0, D == 2 ? sg.tlo : 0, D == 3 ? sg.tlo : 0};
+        int kb[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) kb[a] = (tc3[a] + tl[a]) * td[a];
+        meta[t] = make_int4(kb[0], kb[1], kb[2], cnt_c);
+        texcl[t] = tex;
+    }
+    __syncwarp();  // the list entries written by the other lanes
+    const int ns = max(1, (cnt_c + kN - 1) / kN);
+    for (int k = 0; k < ns; ++k) {
+        const int slot = k * kN + lane;
+        const int pos = slot < cnt_c ? list[(size_t)t * kListCap + slot] : -1;
+        float row[kK];
+        seed_row<D, KIND>(r32, pos, ch, cl, wrh, wrl, row);
+        uint8_t *dst = bops + ((size_t)t * kMaxSteps + k) * Fm::B_BYTES;
+#pragma unroll
+        for (int c = 0; c < kK / Fm::EPR; ++c)
+            put_row<KIND>(dst + tc::core_offset(lane, c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO), row + c * Fm::EPR);
+        if (pos >= 0) list[(size_t)t * kListCap + slot] = perm ? perm[pos] : pos;  // seed index for the labels
+    }
+}
+
 constexpr int kSupWarps = 8;  // warps sharing one super-tile's scan
 
-template <int D>
+template <int D, int KIND>
 __global__ void __launch_bounds__(kSupWarps * 32)
-    tc_super_kernel(const GridDev g, const SuperGeom sg, const int nsup, const int n,
-                    const SeedRec32 *__restrict__ r32, const GroupBound *__restrict__ groups,
-                    const uint32_t *__restrict__ scodes, const float4 *__restrict__ axis_tab,
-                    int *__restrict__ slist, int *__restrict__ scount, float *__restrict__ stex,
+    tc_lists_kernel(const GridDev g, const SuperGeom sg, const int nsup, const int n,
+                    const SeedRec32 *__restrict__ r32, const int32_t *__restrict__ perm,
+                    const GroupBound *__restrict__ groups, const uint32_t *__restrict__ scodes,
+                    const float4 *__restrict__ axis_tab, float *__restrict__ centre, int4 *__restrict__ meta,
+                    float *__restrict__ texcl, int *__restrict__ list, uint8_t *__restrict__ bops,
                     const DevScalars *__restrict__ sc) {
     using G = TcGeom<D>;
     constexpr int W = kSupWarps;
@@ -709,6 +639,9 @@ __global__ void __launch_bounds__(kSupWarps * 32)
     __shared__ float s_lb[W][kSuperCap];     // ... and their lower bounds
     __shared__ int s_cnt[W];
     __shared__ float s_tex[W], s_tex2[W];
+    __shared__ int s_list[kSuperCap];        // the super-tile's list, warp order
+    __shared__ int s_total;
+    __shared__ float s_texs;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int sup = (int)blockIdx.x;
     float wrh, wrl;
@@ -845,9 +778,8 @@ __global__ void __launch_bounds__(kSupWarps * 32)
     int off = 0;
     for (int w = 0; w < wid; ++w) off += s_cnt[w];
     float tex2 = finf;
-    int *out = slist + (size_t)sup * kSuperCap;
     for (int e = lane; e < cnt_c; e += 32) {
-        if (off + e < kSuperCap) out[off + e] = s_pos[wid][e];
+        if (off + e < kSuperCap) s_list[off + e] = s_pos[wid][e];
         else tex2 = fminf(tex2, s_lb[wid][e]);  // beyond the capacity: excluded
     }
     tex2 = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex2)));
@@ -860,104 +792,18 @@ __global__ void __launch_bounds__(kSupWarps * 32)
             total += s_cnt[w];
             tx = fminf(tx, fminf(s_tex[w], s_tex2[w]));
         }
-        scount[sup] = min(total, kSuperCap);
-        stex[sup] = tx;
+        s_total = min(total, kSuperCap);
+        s_texs = tx;
     }
+    __syncthreads();
+    // step 2: warp w takes tile c0 + (w & 1, (w >> 1) & 1, w >> 2) of the super-tile
+    const int tc3[3] = {c0[0] + (wid & 1), c0[1] + ((wid >> 1) & 1), D == 3 ? c0[2] + (wid >> 2) : 0};
+    if ((D == 2 && wid >= 4) || tc3[0] > c1[0] || tc3[1] > c1[1] || (D == 3 && tc3[2] > c1[2])) return;
+    const int t = tc3[0] + sg.ntx * (tc3[1] + (D == 3 ? sg.nty * tc3[2] : 0));
+    tile_list<D, KIND>(g, sg, t, tc3, r32, perm, axis_tab, s_list, s_total, s_texs, centre, meta, texcl, list, bops,
+                       wrh, wrl);
 }
 
-// Pruned form, step 2: one warp per tile narrows its super-tile's list with
-// the tile's own bounds (the fourth smallest upper bound over the tile), sets
-// T_excl = min(the super-tile's, the bounds of the seeds it drops), and stores
-// its list (seed indices) and split seed operands.
-template <int D, int KIND>
-__global__ void __launch_bounds__(256)
-    tc_list_kernel(const GridDev g, const SuperGeom sg, const int ntiles, const int n,
-                   const SeedRec32 *__restrict__ r32, const int32_t *__restrict__ perm,
-                   const float4 *__restrict__ axis_tab, const int *__restrict__ slist, const int *__restrict__ scount,
-                   const float *__restrict__ stex, float *__restrict__ centre, int4 *__restrict__ meta,
-                   float *__restrict__ texcl, int *__restrict__ list, uint8_t *__restrict__ bops,
-                   const DevScalars *__restrict__ sc) {
-    using G = TcGeom<D>;
-    using Fm = TcFmt<KIND>;
-    const int lane = threadIdx.x & 31;
-    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    float wrh, wrl;
-    block_wref(sc, wrh, wrl);
-    if (t >= ntiles) return;
-    const float finf = __int_as_float(0x7f800000);
-    const int tx = t % sg.ntx, rr = t / sg.ntx;
-    const int tc3[3] = {tx, D == 3 ? rr % sg.nty : rr, D == 3 ? rr / sg.nty : 0};
-    const int nsx = (sg.ntx + 1) / 2, nsy = (sg.nty + 1) / 2;
-    const int sup = tc3[0] / 2 + nsx * (tc3[1] / 2 + nsy * (tc3[2] / 2));
-    float ch[3], cl[3], rlo[3], rhi[3], alo[3], ahi[3];
-    range_box<D>(g, sg, axis_tab, tc3, tc3, ch, cl, rlo, rhi, alo, ahi);
-    if (lane < 6) centre[(size_t)t * 6 + lane] = lane < 3 ? ch[lane] : cl[lane - 3];
-    const int cntS = scount[sup];
-    const int *sl = slist + (size_t)sup * kSuperCap;
-    // the tile's bounds of the super-tile's candidates: at most 8 rounds of 32,
-    // taken two at a time (indices, then records, loaded together)
-    float lbv[kSuperCap / 32];
-    float u0 = finf, u1 = finf, u2 = finf, u3 = finf;
-    const SeedRec32 zrec{};
-#pragma unroll
-    for (int r = 0; r < kSuperCap / 32; r += 2) {
-        lbv[r] = lbv[r + 1] = finf;
-        if (r * 32 < cntS) {
-            const int e0 = r * 32 + lane, e1 = e0 + 32;
-            const int i0 = e0 < cntS ? sl[e0] : -1, i1 = e1 < cntS ? sl[e1] : -1;
-            const SeedRec32 q0 = i0 >= 0 ? r32[i0] : zrec;
-            const SeedRec32 q1 = i1 >= 0 ? r32[i1] : zrec;
-            float ub0 = finf, ub1 = finf;
-            if (i0 >= 0) seed_bounds<D>(q0, ch, cl, rlo, rhi, wrh, wrl, lbv[r], ub0);
-            if (i1 >= 0) seed_bounds<D>(q1, ch, cl, rlo, rhi, wrh, wrl, lbv[r + 1], ub1);
-            merge_smallest4(i0 >= 0 ? okey(ub0) : 0xffffffffu, u0, u1, u2, u3);
-            if ((r + 1) * 32 < cntS) merge_smallest4(i1 >= 0 ? okey(ub1) : 0xffffffffu, u0, u1, u2, u3);
-        }
-    }
-    const float T = u3;
-    float tex = stex[sup];
-    int cnt = 0;
-#pragma unroll
-    for (int r = 0; r < kSuperCap / 32; ++r) {
-        if (r * 32 < cntS) {
-            const int e = r * 32 + lane;
-            const bool cand = e < cntS && lbv[r] <= T;
-            const unsigned cm = __ballot_sync(0xffffffffu, cand);
-            const int rank = __popc(cm & ((1u << lane) - 1u));
-            if (cand) {
-                if (cnt + rank < kListCap) list[(size_t)t * kListCap + cnt + rank] = sl[e];
-                else tex = fminf(tex, lbv[r]);
-            } else if (e < cntS) {
-                tex = fminf(tex, lbv[r]);
-            }
-            cnt += __popc(cm);
-        }
-    }
-    tex = okey_inv(__reduce_min_sync(0xffffffffu, okey(tex)));
-    const int cnt_c = min(cnt, kListCap);
-    if (lane == 0) {
-        const int td[3] = {G::TX, G::TY, G::TZ};
-        const int tl[3] = {0, D == 2 ? sg.tlo : 0, D == 3 ? sg.tlo : 0};
-        int kb[3] = {0, 0, 0};
-#pragma unroll
-        for (int a = 0; a < D; ++a) kb[a] = (tc3[a] + tl[a]) * td[a];
-        meta[t] = make_int4(kb[0], kb[1], kb[2], cnt_c);
-        texcl[t] = tex;
-    }
-    __syncwarp();  // the list entries written by the other lanes
-    const int ns = max(1, (cnt_c + kN - 1) / kN);
-    for (int k = 0; k < ns; ++k) {
-        const int slot = k * kN + lane;
-        const int pos = slot < cnt_c ? list[(size_t)t * kListCap + slot] : -1;
-        float row[kK];
-        seed_row<D, KIND>(r32, pos, ch, cl, wrh, wrl, row);
-        uint8_t *dst = bops + ((size_t)t * kMaxSteps + k) * Fm::B_BYTES;
-#pragma unroll
-        for (int c = 0; c < kK / Fm::EPR; ++c)
-            put_row<KIND>(dst + tc::core_offset(lane, c * Fm::EPR, Fm::EB, Fm::LBO, Fm::SBO), row + c * Fm::EPR);
-        if (pos >= 0) list[(size_t)t * kListCap + slot] = perm ? perm[pos] : pos;  // seed index for the labels
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Main kernel
@@ -1491,12 +1337,9 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     if (pruned) {
         const SuperGeom sg{ntx, nty, ntz, tlo};
         const int nsup = ((ntx + 1) / 2) * ((nty + 1) / 2) * (D == 3 ? (ntz + 1) / 2 : 1);
-        tc_super_kernel<D><<<nsup, kSupWarps * 32, 0, st>>>(g, sg, nsup, n, rs, ws.groups,
-                                                                    ws.sorted ? ws.scodes : nullptr, ws.tc_axis,
-                                                                    ws.tc_slist, ws.tc_scount, ws.tc_stex, ws.sc);
-        ws.kernel_launches += 2;
-        tc_list_kernel<D, KIND><<<(ntiles * 32 + 255) / 256, 256, 0, st>>>(
-            g, sg, ntiles, n, rs, ws.sorted ? ws.perm : nullptr, ws.tc_axis, ws.tc_slist, ws.tc_scount, ws.tc_stex,
+        ws.kernel_launches += 1;
+        tc_lists_kernel<D, KIND><<<nsup, kSupWarps * 32, 0, st>>>(
+            g, sg, nsup, n, rs, ws.sorted ? ws.perm : nullptr, ws.groups, ws.sorted ? ws.scodes : nullptr, ws.tc_axis,
             ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.tc_bops, ws.sc);
     } else {
         const int pblocks = (int)((ntl * 32 + 255) / 256);
@@ -1589,6 +1432,5 @@ long long tc_tile_count(const GridDev &g) {
 
 int tc_list_cap() { return kListCap; }
 size_t tc_bops_bytes_per_tile() { return (size_t)kMaxSteps * kBMax; }
-int tc_super_cap() { return kSuperCap; }
 
 }  // namespace apd

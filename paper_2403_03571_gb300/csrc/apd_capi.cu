@@ -168,8 +168,11 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
     const size_t K = (size_t)moment_width(g.dim);
     if (weights_only) {
         // one launch: moments and counters cleared, trial weights into the records
+        // the first trial of a new L-BFGS direction forms p too (see Solver::iterate)
+        const bool form_p = ws.p_pending && step && step->p == ws.p;
+        ws.p_pending = false;
         APD_TRY(cuda_ok(launch_eval_begin(n, step ? step->W : w, step ? step->t : 0.0, step ? step->p : nullptr,
-                                          const_cast<double *>(w), mom, ws, st)));
+                                          const_cast<double *>(w), mom, ws, st, form_p)));
     } else {
         if (step) APD_TRY(cuda_ok(launch_axpy(n, step->W, step->t, step->p, const_cast<double *>(w), st)));
         APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
@@ -280,7 +283,7 @@ struct Solver {
         eg = nullptr;
         if (!ws.graphs || !geometry_ready || ws.shard_world > 1) return APD_OK;
         struct Key {
-            int dim, res[3], kz0, kz1, n, prec, prune, sorted, profiling, has_step;
+            int dim, res[3], kz0, kz1, n, prec, prune, sorted, profiling, has_step, form_p, pad;
             uint32_t wait_limit, use_tc;
             double lo[3], h[3];
             const void *ptr[9];
@@ -300,6 +303,8 @@ struct Solver {
         k.sorted = ws.sorted ? 1 : 0;
         k.profiling = ws.profiling ? 1 : 0;
         k.has_step = step ? 1 : 0;
+        const bool form_p = ws.p_pending && step && step->p == ws.p;  // as enqueue_assign decides it
+        k.form_p = form_p ? 1 : 0;
         k.wait_limit = ws.wait_limit;
         // the scorer the captured pass takes (the seeds' conditioning can change it between solves)
         const bool tc = use_tensor_cores(g, prec, ws, true, st);
@@ -375,9 +380,10 @@ struct Solver {
         }
         eg->used = ++ws.graph_clock;
         if (tc) APD_TRY(cuda_ok(launch_tc_axis(g, ws, st)));
+        ws.p_pending = false;
         if (step)
             APD_TRY(cuda_ok(set_eval_begin_node(eg->exec, eg->begin, n, step->W, step->t, step->p,
-                                                const_cast<double *>(Wp), ws.moments, ws)));
+                                                const_cast<double *>(Wp), ws.moments, ws, form_p)));
         APD_TRY(cuda_ok(cudaGraphLaunch(eg->exec, st)));
         ws.kernel_launches += eg->launches;
         ws.last_pixels = eg->pixels;
@@ -555,6 +561,7 @@ struct Solver {
     // (or the converged point, copied to out) holds the weights.
     int run(const double *W0, double *out, bool &converged) {
         converged = false;
+        ws.p_pending = false;
         APD_TRY(cuda_ok(cudaMemcpyAsync(ws.W, W0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st)));
         double f0, d0, err0;
         APD_TRY(eval(ws.W, ws.gf, nullptr, f0, d0, err0));
@@ -569,6 +576,7 @@ struct Solver {
     // evaluated, so the gradient at the chosen start is already known.
     int run_judged(const double *Wpred, double *out, bool &converged, int &used) {
         converged = false;
+        ws.p_pending = false;
         used = 1;
         APD_TRY(cuda_ok(cudaMemcpyAsync(ws.W, Wpred, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st)));
         double fp, dp, ep;
@@ -619,14 +627,14 @@ struct Solver {
         bool dir_ready = false;  // the last push also formed this direction's coefficients
         while (evals < max_evals) {
             const int hist_acc = std::min(hist + 1, history);
-            if (dir_ready) {
-                APD_TRY(cuda_ok(launch_lbfgs_pdir(n, ws, st)));
+            // the coefficients of p come from the last push or from the dots kernel;
+            // the first trial's eval_begin forms p from them (and <grad f, p>)
+            if (!dir_ready) {
+                APD_TRY(cuda_ok(launch_lbfgs_coefficients(n, hist, newest, kHistCap, gamma, pending, hist_acc,
+                                                          p_slot, ws, st)));
                 ws.kernel_launches += 1;
-            } else {
-                APD_TRY(cuda_ok(launch_lbfgs_direction(n, hist, newest, kHistCap, gamma, pending, hist_acc, p_slot,
-                                                       ws, st)));
-                ws.kernel_launches += 2;
             }
+            ws.p_pending = true;
             dir_ready = false;
             double t0 = 1.0;
             if (!pending && hist == 0) {
@@ -807,9 +815,6 @@ int apd_workspace_create(apd_workspace **out, int32_t dim, int32_t max_n, int64_
     alloc((void **)&w.tc_bops, (size_t)w.tc_tile_cap * tc_bops_bytes_per_tile());
     alloc((void **)&w.tc_axis, (size_t)3 * w.tc_tile_cap * sizeof(float4));
     // super-tiles: at most one per tile
-    alloc((void **)&w.tc_slist, (size_t)w.tc_tile_cap * tc_super_cap() * sizeof(int));
-    alloc((void **)&w.tc_scount, (size_t)w.tc_tile_cap * sizeof(int));
-    alloc((void **)&w.tc_stex, (size_t)w.tc_tile_cap * sizeof(float));
     w.part_rows = (int)nb;
     alloc((void **)&w.part, nb * kPartStride * sizeof(double));
     alloc((void **)&w.grad, (size_t)max_n * sizeof(double));
@@ -849,7 +854,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     for (cudaEvent_t e : w.ev) cudaEventDestroy(e);
     for (EvalGraph &e : w.graph_cache) destroy_graph(e);
     if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
-    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.tc_axis, w.tc_slist, w.tc_scount, w.tc_stex, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
+    void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.tc_axis, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.gram, w.lb_part, w.lb_coef, w.rho, w.X, w.vbuf, w.wfeat, w.wpred,
                     w.S2, w.Y2, w.gram2, w.rho2};
     for (void *p : ptrs)

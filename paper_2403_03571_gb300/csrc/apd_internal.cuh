@@ -142,9 +142,6 @@ struct Workspace {
     float4 *tc_axis = nullptr;          // [3 tc_tile_cap] per-axis tile centres and pixel boxes
     double tc_axis_key[12] = {};        // the grid and tiling tc_axis was computed for (all 0: none)
     double tc_cond = 0.0;               // max ||A||_F / min lambda_min of the last prepared seeds
-    int *tc_slist = nullptr;            // [tc_tile_cap][tc_super_cap()] candidates of the super-tiles
-    int *tc_scount = nullptr;           // [tc_tile_cap] their counts
-    float *tc_stex = nullptr;           // [tc_tile_cap] their bounds of the seeds left out
     long long tc_tile_cap = 0;
     bool sorted = false;                // set by launch_seed_prep for the current pass
     bool prune = false;                 // FP32 scoring skips seed groups by their bounds
@@ -173,6 +170,7 @@ struct Workspace {
     double *lb_part = nullptr;          // [lb_rows][kLbfgsDots] per-block partial sums of the L-BFGS kernels
     int lb_rows = 0;
     LbfgsCoef *lb_coef = nullptr;       // the last direction's coefficients
+    bool p_pending = false;             // lb_coef holds a direction that ws.p does not yet hold
     double *rho = nullptr;              // [hist_cap]
     // a second L-BFGS history (pairs, Gram entries, 1 / s.y) continued by the coarse
     // solves of a Lloyd run (allocated on first use), and its host-side state
@@ -368,8 +366,10 @@ cudaError_t launch_masked_refine(const GridDev &gc, const GridDev &gf, int r, in
 // start of an evaluation with the records of the last launch_seed_prep (same x,
 // A, n): zeroed moments and counters, weights W0 + t pdir (into Wt; pdir null:
 // W0 itself) in the records, wref and the group weight gaps
+// form_p: pdir is first formed from the last direction coefficients (ws.lb_coef,
+// gradient ws.gf) and <gf, p> goes to sc->gp0.
 cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *pdir, double *Wt,
-                              unsigned long long *mom, Workspace &ws, cudaStream_t st);
+                              unsigned long long *mom, Workspace &ws, cudaStream_t st, bool form_p = false);
 // seed records (FP64 x, w; FP32 symmetric A) + stats (max w, max ||A||_F, min lambda bound)
 cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const double *A,
                              const double *w, Workspace &ws, cudaStream_t st);
@@ -385,7 +385,6 @@ cudaError_t launch_assign_tc(const GridDev &g, int n, Workspace &ws, int32_t *la
 long long tc_tile_count(const GridDev &g);
 int tc_list_cap();
 size_t tc_bops_bytes_per_tile();
-int tc_super_cap();
 // bounds of the 32-seed groups of the scan-order records (ws.groups)
 cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st);
 // FP64 rescoring of the queued pixels (labels optional, moments updated).
@@ -431,7 +430,11 @@ inline cudaError_t record_scoring_start(Workspace &ws, cudaStream_t st) {
 // brought up to date for a grid outside any capture
 const void *eval_begin_kernel_fn();
 cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int n, const double *W0, double t,
-                                const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws);
+                                const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws,
+                                bool form_p);
+// the direction's coefficients only (p is then formed by the next trial's eval_begin)
+cudaError_t launch_lbfgs_coefficients(int n, int hist, int newest, int cap, double gamma, bool use_pair,
+                                      int hist_acc, int newest_acc, Workspace &ws, cudaStream_t st);
 cudaError_t launch_tc_axis(const GridDev &g, Workspace &ws, cudaStream_t st);
 
 }  // namespace apd

@@ -29,16 +29,36 @@ __global__ void eval_reset_kernel(DevScalars *sc, const int keep_geometry) {
 // the reference weight wref = max w (per-block maxima reduced by the last block
 // to finish), and each 32-seed group's largest weight and gap wref - wmax.  One
 // thread per scan position; a warp covers one group.
+// With coef (the first trial of a new L-BFGS direction), the direction itself
+// is formed first, p = -gamma gf + sum_k (cy_k y_k + cs_k s_k) from the
+// coefficients the direction kernels left (written to pdir), with <gf, p>
+// reduced by the last block into sc->gp0: one launch instead of two.
 __global__ void __launch_bounds__(256)
     eval_begin_kernel(const int n, const int n_pad, const long long n_mom, const double *__restrict__ W0,
-                      const double t, const double *__restrict__ pdir, double *__restrict__ Wt,
+                      const double t, double *__restrict__ pdir, double *__restrict__ Wt,
                       const int32_t *__restrict__ perm, SeedRec *__restrict__ recs,
                       SeedRec32 *__restrict__ recs32, SeedRec32 *__restrict__ recs32s,
                       GroupBound *__restrict__ groups, unsigned long long *__restrict__ mom,
-                      double *__restrict__ part, DevScalars *__restrict__ sc) {
-    __shared__ double shw[8];
+                      double *__restrict__ part, DevScalars *__restrict__ sc, const LbfgsCoef *__restrict__ coef,
+                      const double *__restrict__ S, const double *__restrict__ Y, const double *__restrict__ gfv) {
+    __shared__ double shw[8], shg[8];
+    __shared__ double ccy[32], ccs[32];
+    __shared__ int cslot[32];
     __shared__ bool last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int hist = 0;
+    double gam = 0.0;
+    if (coef) {
+        hist = min(coef->hist, 31);
+        gam = coef->gamma;
+        for (int k = threadIdx.x; k < hist; k += blockDim.x) {
+            ccy[k] = coef->cy[k];
+            ccs[k] = coef->cs[k];
+            cslot[k] = coef->slot[k];
+        }
+        __syncthreads();
+    }
+    double gp = 0.0;
     for (long long e = i; e < n_mom; e += (long long)gridDim.x * blockDim.x) mom[e] = 0ull;
     if (i == 0) sc->flag_count = 0u;
     const int src = i < n_pad ? (perm ? perm[i] : i) : n;
@@ -47,7 +67,21 @@ __global__ void __launch_bounds__(256)
     if (real) {
         double wi;
         if (pdir) {
-            wi = fma(t, pdir[src], W0[src]);
+            double pv;
+            if (coef) {
+                const double g = gfv[src];
+                pv = -gam * g;
+#pragma unroll 4
+                for (int k = 0; k < hist; ++k) {
+                    const size_t o = (size_t)cslot[k] * n + src;
+                    pv += ccy[k] * Y[o] + ccs[k] * S[o];
+                }
+                pdir[src] = pv;
+                gp = g * pv;
+            } else {
+                pv = pdir[src];
+            }
+            wi = fma(t, pv, W0[src]);
             Wt[src] = wi;
         } else {
             wi = W0[src];
@@ -67,6 +101,10 @@ __global__ void __launch_bounds__(256)
     }
     const double wmax = warp_max(wkey);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (coef) {
+        gp = warp_sum(gp);
+        if (lane == 0) shg[wid] = gp;
+    }
     if (lane == 0) {
         shw[wid] = wmax;
         if (groups && i < n_pad && (i & ~31) < n) groups[i >> 5].wmax = wmax;
@@ -77,6 +115,11 @@ __global__ void __launch_bounds__(256)
         double b = shw[0];
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) b = fmax(b, shw[k]);
         part[(size_t)blockIdx.x * kPartStride] = b;
+        if (coef) {
+            double s = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += shg[k];
+            part[(size_t)blockIdx.x * kPartStride + 1] = s;
+        }
         __threadfence();
         last = atomicAdd(&sc->dual_done, 1u) == gridDim.x - 1;
     }
@@ -97,6 +140,12 @@ __global__ void __launch_bounds__(256)
             const double wm = *(volatile double *)&groups[gidx].wmax;
             groups[gidx].wgap = __double2float_rd(wref - wm);
         }
+    if (coef && threadIdx.x < 32) {  // <gf, p>: the blocks' sums, lane-strided, then a fixed tree
+        double s = 0.0;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += 32) s += *(volatile double *)&part[(size_t)k * kPartStride + 1];
+        s = warp_sum(s);
+        if (threadIdx.x == 0) sc->gp0 = s;
+    }
     if (threadIdx.x == 0) {
         sc->wref_key = dkey(wref);
         sc->dual_done = 0u;
@@ -195,8 +244,10 @@ __device__ __forceinline__ double dual_pair_terms(const GridDev &g, const unsign
                                                   const double *__restrict__ xi, const double *__restrict__ Ai,
                                                   const int q) {
     constexpr int NP = D * (D + 1) / 2;
-    if (mo[0] == 0ull) return 0.0;
-    const double m = (double)mo[0];
+    // no early exit on an empty cell: every load is issued before the first result
+    // is needed (one memory round trip), and an empty cell's terms are dropped at the end
+    const unsigned long long m0 = mo[0];
+    const double m = (double)m0;
     const double inv_m = 1.0 / m;  // one division; products with it differ from quotients by a few ulp
     double Q = 0.0;
 #pragma unroll
@@ -214,7 +265,7 @@ __device__ __forceinline__ double dual_pair_terms(const GridDev &g, const unsign
             Q += Aab * Mab;
         }
     }
-    return Q;
+    return m0 == 0ull ? 0.0 : Q;
 }
 
 // The same from FP64 element-measure moments (non-uniform discretisation):
@@ -268,14 +319,18 @@ __global__ void __launch_bounds__(kDualThreads)
     int i = (blockIdx.x * kDualThreads + threadIdx.x) >> 2;
     for (int r = 0; r < rounds; ++r, i += stride) {
         const bool real = i < n;
-        double Qp = 0.0;
+        double Qp = 0.0, vi = 1.0, wi = 0.0, pd = 0.0;
+        if (real) {  // the cell's scalars too, before the pair terms' arithmetic
+            vi = v[i];
+            wi = w[i];
+            if (p_dir) pd = p_dir[i];
+        }
         if (real)
             Qp = kPoints ? points_pair_terms<D>(mom_pts + (size_t)i * K, x + (size_t)i * D, A + (size_t)i * D * D, q)
                          : dual_pair_terms<D>(g, mom + (size_t)i * K, x + (size_t)i * D, A + (size_t)i * D * D, q);
         Qp += __shfl_xor_sync(0xffffffffu, Qp, 1);
         Qp += __shfl_xor_sync(0xffffffffu, Qp, 2);
         if (real && q == 0) {
-            const double vi = v[i], wi = w[i];
             if (!(vi > 0.0) || !isfinite(vi)) atomicOr(&sc->status, ST_BAD_VOLUME);
             const double gr = kPoints ? vi - mom_pts[(size_t)i * K] : __dsub_rn(vi, __dmul_rn((double)mom[(size_t)i * K], g.cell));
             gsum += kPoints ? gr * wi + Qp : gr * wi + g.cell * Qp;
@@ -286,7 +341,7 @@ __global__ void __launch_bounds__(kDualThreads)
             }
             if (grad_out) grad_out[i] = gr;
             if (gf_out) gf_out[i] = -gr;
-            if (p_dir) gp += -gr * p_dir[i];
+            if (p_dir) gp += -gr * pd;
             sv += vi;
             vmin = fmin(vmin, vi);
         }
@@ -703,13 +758,15 @@ cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry
 }
 
 cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *pdir, double *Wt,
-                              unsigned long long *mom, Workspace &ws, cudaStream_t st) {
+                              unsigned long long *mom, Workspace &ws, cudaStream_t st, bool form_p) {
     const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
     const long long n_mom = (long long)n * moment_width(ws.dim);
     if (n_pad == 0) return cudaSuccess;
-    eval_begin_kernel<<<n_pad / 256, 256, 0, st>>>(n, n_pad, n_mom, W0, t, pdir, Wt, ws.sorted ? ws.perm : nullptr,
-                                                   ws.recs, ws.recs32, ws.sorted ? ws.recs32s : nullptr, ws.groups,
-                                                   mom, ws.part, ws.sc);
+    const bool fp = form_p && pdir;
+    eval_begin_kernel<<<n_pad / 256, 256, 0, st>>>(n, n_pad, n_mom, W0, t, const_cast<double *>(pdir), Wt,
+                                                   ws.sorted ? ws.perm : nullptr, ws.recs, ws.recs32,
+                                                   ws.sorted ? ws.recs32s : nullptr, ws.groups, mom, ws.part, ws.sc,
+                                                   fp ? ws.lb_coef : nullptr, ws.S, ws.Y, ws.gf);
     return cudaGetLastError();
 }
 
@@ -718,7 +775,8 @@ const void *eval_begin_kernel_fn() { return reinterpret_cast<const void *>(eval_
 // The same launch as launch_eval_begin, written into a kernel node of an
 // instantiated graph (only the trial step t changes between replays).
 cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int n, const double *W0, double t,
-                                const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws) {
+                                const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws,
+                                bool form_p) {
     int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
     long long n_mom = (long long)n * moment_width(ws.dim);
     const int32_t *perm = ws.sorted ? ws.perm : nullptr;
@@ -727,8 +785,11 @@ cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int 
     GroupBound *groups = ws.groups;
     double *part = ws.part;
     DevScalars *sc = ws.sc;
-    void *args[] = {&n,    &n_pad,  &n_mom,   &W0,     &t,   &pdir, &Wt, &perm,
-                    &recs, &recs32, &recs32s, &groups, &mom, &part, &sc};
+    double *pd = const_cast<double *>(pdir);
+    const LbfgsCoef *coef = form_p && pdir ? ws.lb_coef : nullptr;
+    const double *S = ws.S, *Y = ws.Y, *gfv = ws.gf;
+    void *args[] = {&n,      &n_pad, &n_mom, &W0,   &t,    &pd, &Wt, &perm, &recs,
+                    &recs32, &recs32s, &groups, &mom, &part, &sc, &coef, &S,  &Y,  &gfv};
     cudaKernelNodeParams p{};
     p.func = reinterpret_cast<void *>(eval_begin_kernel);
     p.gridDim = dim3(n_pad / 256);
@@ -837,10 +898,18 @@ cudaError_t launch_lbfgs_direction(int n, int hist, int newest, int cap, double 
                                    int hist_acc, int newest_acc, Workspace &ws, cudaStream_t st) {
     if (cap > kLbfgsMax || hist > cap || hist_acc > cap || !ws.lb_part || !ws.lb_coef || ws.lb_rows < 1)
         return cudaErrorInvalidValue;
+    const cudaError_t e = launch_lbfgs_coefficients(n, hist, newest, cap, gamma, use_pair, hist_acc, newest_acc, ws, st);
+    return e != cudaSuccess ? e : launch_lbfgs_pdir(n, ws, st);
+}
+
+cudaError_t launch_lbfgs_coefficients(int n, int hist, int newest, int cap, double gamma, bool use_pair,
+                                      int hist_acc, int newest_acc, Workspace &ws, cudaStream_t st) {
+    if (cap > kLbfgsMax || hist > cap || hist_acc > cap || !ws.lb_part || !ws.lb_coef || ws.lb_rows < 1)
+        return cudaErrorInvalidValue;
     lbfgs_dots_kernel<<<lbfgs_blocks(n, kLbR, ws), kLbT, 0, st>>>(n, hist, newest, cap, gamma, use_pair ? 1 : 0,
                                                                   hist_acc, newest_acc, ws.S, ws.Y, ws.rho, ws.gram,
                                                                   ws.gf, ws.lb_part, ws.lb_coef, ws.sc);
-    return launch_lbfgs_pdir(n, ws, st);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lbfgs_pdir(int n, Workspace &ws, cudaStream_t st) {
