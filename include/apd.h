@@ -534,6 +534,13 @@ typedef struct {
                                  min_cell_span^dim pixels per seed (default 8: cells about 8 pixels
                                  across; coarser cells cannot reach coarse_eps and the coarse solve
                                  would only burn its evaluation cap); 0 = always */
+    int32_t coarse_stall_evals; /* the coarse solve stops (its best iterate is used) after this many
+                                   evaluations without a 2 % better max relative volume error: a coarse
+                                   grid whose discretisation keeps it above coarse_eps has stalled
+                                   (0 = off, the default: on the runtime tests' 2D points, 30 helped
+                                   single-phase solves by up to 25 % and slowed multi-phase ones by up
+                                   to 50 %, whose coarse stage keeps improving the smooth part of W
+                                   while the largest error stands still) */
 } apd_multires_opts;
 
 /* Fill *mo with the defaults: factor 2, coarse_eps 0.05, coarse_max_evals 60. */

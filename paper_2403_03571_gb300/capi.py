@@ -90,7 +90,7 @@ REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, cty
 class ApdMultiresOpts(ctypes.Structure):
     _fields_ = [("factor", ctypes.c_int32), ("coarse_eps", ctypes.c_double),
                 ("coarse_max_evals", ctypes.c_int32), ("carry_history", ctypes.c_int32),
-                ("min_cell_span", ctypes.c_int32)]
+                ("min_cell_span", ctypes.c_int32), ("coarse_stall_evals", ctypes.c_int32)]
 
 
 class ApdRefineOpts(ctypes.Structure):
@@ -633,13 +633,16 @@ def apd_solve_weights_warm(grid, x, A, v, w_out, ws: Workspace, net: WarmStart, 
     return rc, info, used.value
 
 
-def multires_opts(factor=2, coarse_eps=0.05, coarse_max_evals=60, carry_history=False, min_cell_span=None):
+def multires_opts(factor=2, coarse_eps=0.05, coarse_max_evals=60, carry_history=False, min_cell_span=None,
+                  coarse_stall_evals=None):
     m = ApdMultiresOpts()
     load().apd_multires_opts_default(ctypes.byref(m))
     m.factor, m.coarse_eps, m.coarse_max_evals = int(factor), float(coarse_eps), int(coarse_max_evals)
     m.carry_history = int(bool(carry_history))
     if min_cell_span is not None:
         m.min_cell_span = int(min_cell_span)
+    if coarse_stall_evals is not None:
+        m.coarse_stall_evals = int(coarse_stall_evals)
     return m
 
 

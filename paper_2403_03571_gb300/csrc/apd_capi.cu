@@ -254,6 +254,8 @@ struct Solver {
     int evals = 0, iters = 0;
     long long rescored = 0;
     double best_err = INFINITY, best_g = 0.0;
+    int stall_evals = 0;  // > 0: stop after this many evaluations without a 2 % better error
+    int last_gain = 0;    // evaluation count at the last such improvement
     double last_g = 0.0, last_err = INFINITY;
     const double *last_point = nullptr;  // device pointer evaluated last
     bool last_is_best = false;
@@ -426,6 +428,7 @@ struct Solver {
         last_err = err;
         last_point = Wp;
         last_is_best = false;
+        if (err < 0.98 * best_err) last_gain = evals;
         if (err < best_err) {
             best_err = err;
             best_g = h.g;
@@ -625,7 +628,7 @@ struct Solver {
         bool pending = false;  // a pushed pair whose test result is not read yet
         int p_slot = 0;
         bool dir_ready = false;  // the last push also formed this direction's coefficients
-        while (evals < max_evals) {
+        while (evals < max_evals && !(stall_evals > 0 && evals - last_gain >= stall_evals)) {
             const int hist_acc = std::min(hist + 1, history);
             // the coefficients of p come from the last push or from the dots kernel;
             // the first trial's eval_begin forms p from them (and <grad f, p>)
@@ -711,6 +714,7 @@ int solve_impl(const GridDev &g, const apd_grid *grid, int n, const double *x, c
     s.history = std::max(1, std::min(o.history, kHistCap - 1));  // the slot written next is never in use
     s.check_volumes = o.check_volumes != 0;
     s.measure = domain_measure(grid);
+    s.stall_evals = ws.solve_stall;
     bool conv = false;
     int used_pred = 0;
     int rc = judged ? s.run_judged(w0, w_out, conv, used_pred) : s.run(w0, w_out, conv);
@@ -1313,11 +1317,14 @@ void apd_multires_opts_default(apd_multires_opts *mo) {
     mo->coarse_max_evals = 60;
     mo->carry_history = 0;
     mo->min_cell_span = 8;
+    mo->coarse_stall_evals = 0;
 }
 
 // Coarse grid of a coarse-to-fine solve (same box, ceil(res / factor) >= 4 per axis).
 static int coarse_grid(const apd_grid *grid, const apd_multires_opts &m, apd_grid &cg, GridDev &gc) {
-    if (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1 || m.min_cell_span < 0) return APD_ERR_ARG;
+    if (m.factor < 2 || !(m.coarse_eps > 0.0) || m.coarse_max_evals < 1 || m.min_cell_span < 0 ||
+        m.coarse_stall_evals < 0)
+        return APD_ERR_ARG;
     cg = *grid;
     for (int d = 0; d < grid->dim; ++d) cg.res[d] = std::max(4, (grid->res[d] + m.factor - 1) / m.factor);
     return validate_grid(&cg, gc);
@@ -1367,7 +1374,9 @@ static int c2f_solve(const GridDev &g, const apd_grid *grid, const GridDev &gc, 
     const bool carry = carry_ready(ws);  // the coarse solve runs on the second history
     if (carry) swap_history(ws);
     ws.carry_on = carry;
+    ws.solve_stall = m.coarse_stall_evals;
     const int crc = solve_impl(gc, cg, n, x, A, w0, v, w_out, oc, cinf, ws, st, false, judged, used);
+    ws.solve_stall = 0;
     ws.carry_on = false;
     if (carry) swap_history(ws);
     if (crc < 0) return crc;

@@ -175,6 +175,7 @@ struct Workspace {
     // a second L-BFGS history (pairs, Gram entries, 1 / s.y) continued by the coarse
     // solves of a Lloyd run (allocated on first use), and its host-side state
     double *S2 = nullptr, *Y2 = nullptr, *gram2 = nullptr, *rho2 = nullptr;
+    int solve_stall = 0;                // the running solve's stall limit (coarse solves), 0: none
     bool carry_enabled = false;         // a Lloyd run with carry_history is in progress
     bool carry_on = false;              // the running solve starts from `carry` and leaves its history there
     struct {

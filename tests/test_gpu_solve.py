@@ -151,6 +151,23 @@ def test_coarse_solve_skipped_for_small_cells(capi):
         assert err < 0.01
 
 
+def test_coarse_solve_stops_when_it_stalls(capi):
+    # a coarse tolerance no coarse grid can reach: with coarse_stall_evals = 30 the
+    # coarse solve stops after 30 evaluations without a 2 % better error instead of
+    # running to its cap of 300,
+    # and the fine solve still meets the stop rule (oracle)
+    inst = synth.make_instance(2, 400, 384, 13)
+    x, A, w, v = instance_tensors(inst)
+    ws = capi.Workspace(2, inst.n, inst.grid.num_pixels)
+    w_out = torch.zeros_like(w)
+    rc, info, _ = capi.apd_solve_weights_multires(inst.grid, x, A, w, v, w_out, ws,
+                                                  mopts=capi.multires_opts(2, 1e-6, 300, coarse_stall_evals=30))
+    assert rc in (capi.APD_OK, capi.APD_WARN_TOL_INFEASIBLE), info.as_dict()
+    assert info.solves == 2 and 30 <= info.coarse_evaluations < 300
+    _, _, err = oracle.dual(inst.grid, inst.x, inst.A, host(w_out), inst.v)
+    assert err < 0.01
+
+
 @pytest.mark.parametrize("prec", ["fp32", "tc_tf32"])
 def test_lloyd_coarse_history_carried(capi, prec):
     # the coarse solves of successive rounds continue one L-BFGS history: the
