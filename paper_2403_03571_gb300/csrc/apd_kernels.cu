@@ -757,13 +757,19 @@ cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry
     return cudaGetLastError();
 }
 
+// Threads per block of eval_begin_kernel: 64 (two warps, spreading the FP64
+// work of forming p and the trial weights over more SMs) while the blocks fit
+// the workspace's partial-sum rows, else 256.
+static int eval_begin_threads(int n_pad, const Workspace &ws) { return n_pad / 64 <= ws.part_rows ? 64 : 256; }
+
 cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *pdir, double *Wt,
                               unsigned long long *mom, Workspace &ws, cudaStream_t st, bool form_p) {
     const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
     const long long n_mom = (long long)n * moment_width(ws.dim);
     if (n_pad == 0) return cudaSuccess;
     const bool fp = form_p && pdir;
-    eval_begin_kernel<<<n_pad / 256, 256, 0, st>>>(n, n_pad, n_mom, W0, t, const_cast<double *>(pdir), Wt,
+    const int tpb = eval_begin_threads(n_pad, ws);
+    eval_begin_kernel<<<n_pad / tpb, tpb, 0, st>>>(n, n_pad, n_mom, W0, t, const_cast<double *>(pdir), Wt,
                                                    ws.sorted ? ws.perm : nullptr, ws.recs, ws.recs32,
                                                    ws.sorted ? ws.recs32s : nullptr, ws.groups, mom, ws.part, ws.sc,
                                                    fp ? ws.lb_coef : nullptr, ws.S, ws.Y, ws.gf);
@@ -792,8 +798,9 @@ cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int 
                     &recs32, &recs32s, &groups, &mom, &part, &sc, &coef, &S,  &Y,  &gfv};
     cudaKernelNodeParams p{};
     p.func = reinterpret_cast<void *>(eval_begin_kernel);
-    p.gridDim = dim3(n_pad / 256);
-    p.blockDim = dim3(256);
+    const int tpb = eval_begin_threads(n_pad, ws);
+    p.gridDim = dim3(n_pad / tpb);
+    p.blockDim = dim3(tpb);
     p.sharedMemBytes = 0;
     p.kernelParams = args;
     p.extra = nullptr;
