@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--carry-history", type=int, default=1,
                     help="chosen form: the coarse solves of a Lloyd run continue one L-BFGS history (1) "
                          "or start afresh (0)")
+    ap.add_argument("--incremental", type=int, default=1,
+                    help="weight solves re-decide only the pixels within the weights' drift of their "
+                         "recorded cost gap (1) or score every pixel in every evaluation (0)")
     ap.add_argument("--assign-res", type=int, default=0,
                     help="--mode assign: grid resolution per axis in place of the workload's")
     ap.add_argument("--assign-prune", action="store_true",
@@ -556,6 +559,7 @@ def run_ours(args):
     ctx["x_out"] = torch.empty_like(ctx["x0"])
     ctx["w_out"] = torch.empty_like(ctx["w0"])
     ctx["ws"] = capi.Workspace(dim, n, J)
+    ctx["ws"].set_incremental(bool(args.incremental))
     if world > 1:
         from paper_2403_03571_gb300 import shard
         shard.shard_workspace(ctx["ws"], rank, world)
@@ -566,6 +570,7 @@ def run_ours(args):
     forms["chosen"] = measure_form(args, ctx, args.precision, chosen_start=True)
     forms["chosen"]["precision"] = args.precision
     forms["chosen"]["pruned"] = bool(args.prune)
+    forms["chosen"]["incremental"] = bool(args.incremental)
     # the chosen form's final generators and its labels there (for the accuracy report)
     x_fin = (ctx["x_out"] if rounds > 0 else ctx["x0"]).clone()
     w_fin = ctx["w_out"].clone()

@@ -128,6 +128,24 @@ int apd_workspace_set_pruning(apd_workspace *ws, int32_t enable);
  * workspace. */
 int apd_workspace_set_graphs(apd_workspace *ws, int32_t enable);
 
+/* Incremental evaluations inside weight solves (tensor-core scorers with
+ * pruning on, one rank; default on).  The weights enter every cost
+ * C_ij = |y_j - x_i|_A^2 - w_i (eq. (2.1)) linearly: between weights w0 and w,
+ * C_k - C_a changes by exactly -(D_k - D_a), D = w - w0.  A full pass at w0
+ * records, per pixel, its label a, its runner-up b and certified bounds
+ * gl <= C_b - C_a <= gu and g3 <= C_k - C_a for every other seed k.  A later
+ * pass at w keeps a where min(gl, g3) > max D - min D; where g3 > max D - D_a
+ * the label is a or b, decided by the sign of [gl, gu] - (D_b - D_a) (or by
+ * the two costs in FP32 when that interval holds 0); the remaining pixels are
+ * re-decided in FP32 over their tile's recorded candidate list, and in FP64
+ * where that cannot decide.  The moments are the recorded ones plus the
+ * changes.  The device chooses each pass's kind from the drift: it records
+ * afresh when more than 8 % of the pixels have a recorded g3 within
+ * max D - min D.  Labels and moments are the same as with full passes.
+ * enable = 0 makes every pass a full one.  Returns APD_ERR_ARG for a null
+ * workspace. */
+int apd_workspace_set_incremental(apd_workspace *ws, int32_t enable);
+
 /* Poll limit of the bounded shared-memory barrier waits of the FP32 scoring
  * kernel on this workspace (each poll sleeps at most ~20 us; default 65536,
  * about 1.3 s).  polls >= 0 sets the limit, polls < 0 restores the default.

@@ -47,6 +47,7 @@ EXPORTED = (
     "apd_masked_moments", "apd_masked_dual_value_grad", "apd_workspace_set_wait_limit",
     "apd_shard_range", "apd_cell_moments_slab", "apd_workspace_set_shard", "apd_lbfgs_check",
     "apd_workspace_set_graphs",
+    "apd_workspace_set_incremental",
 )
 
 
@@ -130,6 +131,7 @@ def load(path: Optional[str] = None):
     L.apd_assign.argtypes = [_P(ApdGrid), _P(ApdSeeds), ctypes.c_int32, _vp, _vp, _vp, _vp]
     L.apd_workspace_set_wait_limit.argtypes = [_vp, ctypes.c_int64]
     L.apd_workspace_set_graphs.argtypes = [_vp, ctypes.c_int32]
+    L.apd_workspace_set_incremental.argtypes = [_vp, ctypes.c_int32]
     L.apd_shard_range.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32),
                                   _P(ctypes.c_int32)]
     L.apd_cell_moments_slab.argtypes = [_P(ApdGrid), ctypes.c_int32, ctypes.c_int32, _P(ApdSeeds), ctypes.c_int32,
@@ -303,6 +305,12 @@ class Workspace:
     def set_graphs(self, enable: bool = True):
         """Replay the weight solves' evaluations from captured CUDA graphs (default on)."""
         _check(load().apd_workspace_set_graphs(self.handle, int(bool(enable))), "apd_workspace_set_graphs")
+
+    def set_incremental(self, enable: bool = True):
+        """Re-decide only the pixels within the weights' drift of their recorded
+        cost gap in the weight solves' evaluations (default on)."""
+        _check(load().apd_workspace_set_incremental(self.handle, int(bool(enable))),
+               "apd_workspace_set_incremental")
 
     def profile(self, enable: bool = True):
         _check(load().apd_profile_enable(self.handle, int(bool(enable))), "apd_profile_enable")

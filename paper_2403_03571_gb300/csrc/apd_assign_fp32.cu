@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(256)
                    const SeedRec32 *__restrict__ r32, const uint32_t *__restrict__ flags,
                    const int32_t *__restrict__ flag_gi, const RescorePrune pr,
                    DevScalars *__restrict__ sc, unsigned long long *__restrict__ gmom,
-                   int32_t *__restrict__ labels) {
+                   int32_t *__restrict__ labels, const int32_t *__restrict__ old_labels,
+                   const int *__restrict__ go) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const unsigned count = sc->flag_count;
@@ -90,8 +91,14 @@ __global__ void __launch_bounds__(256)
     const double wref = dkey_inv(sc->wref_key);
     const float wrh = (float)wref;
     const float wrl = (float)(wref - (double)wrh);
+    // an incremental pass: a re-decision moves words from the recorded labels'
+    // cells and keeps the record; a recording writes the labels
+    const bool delta = go ? *go != 0 : old_labels != nullptr;
+    int32_t *lab = delta && go ? nullptr : labels;
+    const int32_t *old = delta ? old_labels : nullptr;
     for (unsigned it = warp; it < count; it += nwarps)
-        rescore_pixel<D>(g, n, x, A, w, r32, flags[it], flag_gi ? flag_gi[it] : -1, wrh, wrl, pr, sc, gmom, labels);
+        rescore_pixel<D>(g, n, x, A, w, r32, flags[it], flag_gi ? flag_gi[it] : -1, wrh, wrl, pr, sc, gmom, lab,
+                         old);
 }
 
 // One warp per pixel: the relative gap of its two smallest FP64 costs.
@@ -163,7 +170,8 @@ cudaError_t launch_tie_gap(const GridDev &g, int n, const double *x, const doubl
 
 cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,
                                 const double *w, Workspace &ws, int32_t *labels,
-                                unsigned long long *moments, cudaStream_t st) {
+                                unsigned long long *moments, cudaStream_t st, const int32_t *old_labels,
+                                const int *go) {
     // one warp per queued pixel, latency-bound (dependent record loads): as many
     // resident warps as the registers allow
     int &bps = ws.rescore_bps[g.dim == 3 ? 1 : 0];
@@ -183,10 +191,10 @@ cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const 
     }
     if (g.dim == 3)
         rescore_kernel<3><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.flag_gi, pr, ws.sc, moments,
-                                                  labels);
+                                                  labels, old_labels, go);
     else
         rescore_kernel<2><<<blocks, 256, 0, st>>>(g, n, x, A, w, ws.recs32, ws.flags, ws.flag_gi, pr, ws.sc, moments,
-                                                  labels);
+                                                  labels, old_labels, go);
     return cudaGetLastError();
 }
 

@@ -630,9 +630,10 @@ __global__ void __launch_bounds__(kSupWarps * 32)
                     const GroupBound *__restrict__ groups, const uint32_t *__restrict__ scodes,
                     const float4 *__restrict__ axis_tab, float *__restrict__ centre, int4 *__restrict__ meta,
                     float *__restrict__ texcl, int *__restrict__ list, uint8_t *__restrict__ bops,
-                    const DevScalars *__restrict__ sc) {
+                    const DevScalars *__restrict__ sc, const int *__restrict__ skip) {
     using G = TcGeom<D>;
     constexpr int W = kSupWarps;
+    if (skip && *(volatile const int *)skip) return;  // an incremental re-decision keeps the lists
     __shared__ unsigned s_T;                 // okey of the smallest threshold found so far
     __shared__ float s_u[W][4];              // each warp's four smallest upper bounds
     __shared__ int s_pos[W][kSuperCap];      // each warp's candidates (scan positions) ...
@@ -826,12 +827,20 @@ struct TcArgs {
     uint32_t *flags;
     int32_t *flag_gi;
     int32_t *labels;
+    // recording pass (REC) only, per pixel: gap0 = a certified lower bound of every
+    // other seed's cost minus the label's (0: none); rec = {gl, gu, g3, b}: the
+    // runner-up seed b (-1: none), certified bounds gl <= C_b - C_a <= gu and
+    // g3 <= C_k - C_a for every other seed k (all 0: none)
+    float *gap0;
+    float4 *rec;
     DevScalars *sc;
     unsigned long long *pairs_scored;
     int wide;  // some axis has more than 4096 pixels: 64-bit moment sums across the warp
+    const int *skip;  // incremental pass: nothing to do when *skip (a re-decision)
+    unsigned *hist;   // REC: recorded pixels by the float exponent of their g3 margin
 };
 
-template <int D, int KIND>
+template <int D, int KIND, bool REC>
 __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_constant__ TcArgs a) {
     using G = TcGeom<D>;
     using Fm = TcFmt<KIND>;
@@ -842,6 +851,10 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GridDev &g = a.g;
+    if (a.skip && *(volatile const int *)a.skip) return;  // the whole block, before any setup
+    __shared__ unsigned s_hist[REC ? kIncBins : 1];
+    if constexpr (REC)
+        for (int i = tid; i < kIncBins; i += blockDim.x) s_hist[i] = 0u;
     const bool pruned = a.pruned != 0;
     const int my_tiles = (int)blockIdx.x < a.ntiles ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto tile_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
@@ -1070,7 +1083,8 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
             for (int k = 0; k < kMaxSteps; ++k)
                 lv[k] = (pruned && k * kN + lane < cnt) ? a.list[(size_t)t * kListCap + k * kN + lane] : -1;
             float k1 = FLT_MAX, k2 = FLT_MAX;  // two smallest packed scores
-            int bstep = 0;
+            float k3 = FLT_MAX;                // REC: the third smallest
+            int bstep = 0, bstep2 = 0;         // steps of k1 and (REC) k2
             bool ok = true;
             for (int k = 0; k < ns; ++k, ++q) {
                 const int s = q & (kStages - 1);
@@ -1086,11 +1100,49 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.bar_aempty[s]);
-                // a slice whose smallest score lies above the second-best by more than
-                // the packing (< 32 ulp) cannot change the two smallest keys
-                if (got && !(mn > fmaf(fabsf(k2), 0x1p-16f, k2))) {
+                // a slice whose smallest score lies above the second-best (REC: third)
+                // by more than the packing (< 32 ulp) cannot change the kept keys
+                const float kq = REC ? k3 : k2;
+                if (got && !(mn > fmaf(fabsf(kq), 0x1p-16f, kq))) {
 #pragma unroll
                     for (int e = 0; e < 32; ++e) v[e] = __uint_as_float((__float_as_uint(v[e]) & ~31u) | (unsigned)e);
+                  if constexpr (REC) {
+                    // the three smallest: sorted pairs, then sorted triples merged (the
+                    // m-th smallest of two sorted lists A, B is min over i + j = m of
+                    // max(A_i, B_j), A_0 = B_0 = -inf)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const float lo = fminf(v[2 * e], v[2 * e + 1]), hi = fmaxf(v[2 * e], v[2 * e + 1]);
+                        v[2 * e] = lo;
+                        v[2 * e + 1] = hi;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 32; e += 4) {
+                        const float a1 = v[e], a2 = v[e + 1], b1 = v[e + 2], b2 = v[e + 3];
+                        v[e] = fminf(a1, b1);
+                        v[e + 1] = fminf(fmaxf(a1, b1), fminf(a2, b2));
+                        v[e + 2] = fminf(fmaxf(a1, b2), fmaxf(a2, b1));
+                    }
+#pragma unroll
+                    for (int w = 8; w <= 32; w <<= 1) {
+#pragma unroll
+                        for (int e = 0; e < 32; e += w) {
+                            const float a1 = v[e], a2 = v[e + 1], a3 = v[e + 2];
+                            const float b1 = v[e + w / 2], b2 = v[e + w / 2 + 1], b3 = v[e + w / 2 + 2];
+                            v[e] = fminf(a1, b1);
+                            v[e + 1] = fmin3_f(a2, b2, fmaxf(a1, b1));
+                            v[e + 2] = fminf(fmin3_f(a3, b3, fmaxf(a2, b1)), fmaxf(a1, b2));
+                        }
+                    }
+                    const float o1 = k1, o2 = k2;
+                    const bool better = v[0] < o1;
+                    k1 = fminf(o1, v[0]);
+                    k2 = fmin3_f(o2, v[1], fmaxf(o1, v[0]));
+                    k3 = fminf(fmin3_f(k3, v[2], fmaxf(o2, v[0])), fmaxf(o1, v[1]));
+                    // k2 is the old best, the old second or one of this step's scores
+                    bstep2 = k2 == o1 ? bstep : (k2 == o2 ? bstep2 : k);
+                    bstep = better ? k : bstep;
+                  } else {
                     // tournament: pairs (lo, hi), then merge pairs of pairs
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
@@ -1111,6 +1163,7 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                     k2 = fmin3_f(fmaxf(k1, v[0]), k2, v[1]);
                     k1 = fminf(k1, v[0]);
                     bstep = better ? k : bstep;
+                  }
                 }
             }
             // ---- end of tile: certificate, label, FP64 queue, moments ----
@@ -1125,13 +1178,22 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
             // the best seed: list slot bstep * 32 + idx (pruned) or scan position (dense)
             const int idx = (int)(__float_as_uint(k1) & 31u);
             int seed = -1;
+            int seed_b = -1;  // REC: the seed of k2
             if (pruned) {
+                const int idx2 = (int)(__float_as_uint(k2) & 31u);
 #pragma unroll
                 for (int kk = 0; kk < kMaxSteps; ++kk) {
                     const int v = __shfl_sync(0xffffffffu, lv[kk], idx);
                     if (kk == bstep) seed = v;
+                    if constexpr (REC) {
+                        const int v2 = __shfl_sync(0xffffffffu, lv[kk], idx2);
+                        if (kk == bstep2) seed_b = v2;
+                    }
                 }
             }
+            // REC: this pixel's record (all 0: re-decided in full by a later pass)
+            float r_gl = 0.f, r_gu = 0.f, r_g3 = 0.f;
+            int r_b = -1;
             if (valid) {
                 j = (long long)kk[0] + (long long)g.res[0] * ((long long)kk[1] + (long long)g.res[1] * (long long)kk[2]);
                 if (!pruned) {
@@ -1143,6 +1205,26 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 const bool cert = seed >= 0 && k1 < 1e29f && U < k2 - psi(k2) && U < tex;
                 if (cert) label = seed;
                 else queue = true;
+                if constexpr (REC) {
+                    // margins of the certificate: C_b - C_a lies within [s2 - psi(s2) - U,
+                    // s2 + psi(s2) - (s1 - psi(s1))]; every seed but a and b costs at least
+                    // min(s3 - psi(s3), T_excl) (s - psi(s) grows with s), every listed
+                    // seed at least its score less psi
+                    if (cert) {
+                        const float Uu = __fadd_ru(k1, psi(k1)), Ld = __fsub_rd(k1, psi(k1));
+                        const float l2 = k2 < 1e29f ? __fsub_rd(k2, psi(k2)) : finf;
+                        const float l3 = k3 < 1e29f ? __fsub_rd(k3, psi(k3)) : finf;
+                        if (k2 < 1e29f && seed_b >= 0 && seed_b != seed) {
+                            r_b = seed_b;
+                            r_gl = __fsub_rd(l2, Uu);
+                            r_gu = __fsub_ru(__fadd_ru(k2, psi(k2)), Ld);
+                            r_g3 = __fsub_rd(fminf(l3, tex), Uu);
+                        } else {  // no runner-up identified: one bound for every other seed
+                            r_gl = r_gu = finf;
+                            r_g3 = __fsub_rd(fminf(l2, tex), Uu);
+                        }
+                    }
+                }
             }
             // Pruned form: the pixels the scores leave undecided are settled in FP32
             // direct form by the warp (lane l takes list slots l, l + 32, ..): the label
@@ -1189,6 +1271,49 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                         for (int kk2 = 0; kk2 < kMaxSteps; ++kk2)
                             if (kk2 < ns && lv[kk2] >= 0 && lv[kk2] != smin && !(cv[kk2] - ev[kk2] > Ub)) other = true;
                         const bool ok2 = !__any_sync(0xffffffffu, other) && Ub < tex && smin < a.n;
+                        if constexpr (REC) {
+                            if (ok2) {
+                                // the runner-up: smallest lower bound among the other candidates;
+                                // then its upper bound, the label's lower bound and the rest's
+                                float lb2 = finf;
+                                int sb2 = 0x7fffffff;
+#pragma unroll
+                                for (int kk2 = 0; kk2 < kMaxSteps; ++kk2)
+                                    if (kk2 < ns && lv[kk2] >= 0 && lv[kk2] != smin) {
+                                        const float l = __fsub_rd(cv[kk2], ev[kk2]);
+                                        if (l < lb2 || (l == lb2 && lv[kk2] < sb2)) {
+                                            lb2 = l;
+                                            sb2 = lv[kk2];
+                                        }
+                                    }
+                                const unsigned kl2 = __reduce_min_sync(0xffffffffu, okey(lb2));
+                                const int sb = (int)__reduce_min_sync(0xffffffffu, okey(lb2) == kl2 ? (unsigned)sb2 : 0x7fffffffu);
+                                float hb = finf, la = finf, l3 = finf;
+#pragma unroll
+                                for (int kk2 = 0; kk2 < kMaxSteps; ++kk2)
+                                    if (kk2 < ns && lv[kk2] >= 0) {
+                                        if (lv[kk2] == sb) hb = __fadd_ru(cv[kk2], ev[kk2]);
+                                        else if (lv[kk2] == smin) la = __fsub_rd(cv[kk2], ev[kk2]);
+                                        else l3 = fminf(l3, __fsub_rd(cv[kk2], ev[kk2]));
+                                    }
+                                const float HB = okey_inv(__reduce_min_sync(0xffffffffu, okey(hb)));
+                                const float LA = okey_inv(__reduce_min_sync(0xffffffffu, okey(la)));
+                                const float L3 = okey_inv(__reduce_min_sync(0xffffffffu, okey(l3)));
+                                const float LB2 = okey_inv(kl2);
+                                if (lane == p) {
+                                    if (sb < a.n && LB2 < finf) {
+                                        r_b = sb;
+                                        r_gl = __fsub_rd(LB2, Ub);
+                                        r_gu = __fsub_ru(HB, LA);
+                                        r_g3 = __fsub_rd(fminf(L3, tex), Ub);
+                                    } else {
+                                        r_b = -1;
+                                        r_gl = r_gu = finf;
+                                        r_g3 = __fsub_rd(fminf(LB2, tex), Ub);
+                                    }
+                                }
+                            }
+                        }
                         if (lane == p) {
                             if (ok2) {
                                 label = smin;
@@ -1213,6 +1338,13 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
                 }
             }
             if (label >= 0 && a.labels) a.labels[j] = label;
+            if constexpr (REC) {
+                if (valid) {
+                    a.rec[j] = make_float4(r_gl, r_gu, r_g3, __int_as_float(r_b));
+                    a.gap0[j] = label >= 0 ? fmaxf(fminf(r_gl, r_g3), 0.f) : 0.f;
+                    atomicAdd(&s_hist[r_g3 > 0.f ? min(__float_as_uint(r_g3) >> 21, (unsigned)kIncBins - 1u) : 0u], 1u);
+                }
+            }
             // Moments of the certified pixels.  The lanes holding the same label sum
             // their words across the warp; the last axis's coordinate is the same for
             // the whole warp (3D: one z of an 8 x 4 block, 2D: one row), so the words
@@ -1280,6 +1412,9 @@ __global__ void __launch_bounds__(kThreads, 1) assign_tc_kernel(const __grid_con
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(taddr, kCols);
+    if constexpr (REC)
+        for (int i = tid; i < kIncBins; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
 }
 
 template <int D>
@@ -1340,7 +1475,8 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
         ws.kernel_launches += 1;
         tc_lists_kernel<D, KIND><<<nsup, kSupWarps * 32, 0, st>>>(
             g, sg, nsup, n, rs, ws.sorted ? ws.perm : nullptr, ws.groups, ws.sorted ? ws.scodes : nullptr, ws.tc_axis,
-            ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.tc_bops, ws.sc);
+            ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.tc_bops, ws.sc,
+            ws.inc_auto ? &ws.sc->inc_go : nullptr);
     } else {
         const int pblocks = (int)((ntl * 32 + 255) / 256);
         ws.kernel_launches += 1;
@@ -1351,9 +1487,12 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     }
     // more than 114 KB of shared memory keeps one CTA (512 tensor-memory columns) per SM
     const size_t smem = std::max<size_t>(sizeof(TcShared<D, KIND>), 120 * 1024);
-    const unsigned bit = kAttrTcScore << ((D == 3 ? 2 : 0) + (KIND == tc::KIND_BF16 ? 1 : 0));
+    // the recording variant (incremental passes) also keeps each pixel's runner-up and margins
+    const bool rec = ws.rec_gap != nullptr;
+    if (rec && (!pruned || !ws.inc_rec || !ws.inc_hist)) return cudaErrorInvalidValue;
+    const unsigned bit = (rec ? kAttrTcScoreRec : kAttrTcScore) << ((D == 3 ? 2 : 0) + (KIND == tc::KIND_BF16 ? 1 : 0));
     if (!(ws.attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(assign_tc_kernel<D, KIND>,
+        const cudaError_t e = cudaFuncSetAttribute(rec ? assign_tc_kernel<D, KIND, true> : assign_tc_kernel<D, KIND, false>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         ws.attr_done |= bit;
@@ -1388,13 +1527,256 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
     args.flags = ws.flags;
     args.flag_gi = ws.flag_gi;
     args.labels = labels;
+    args.gap0 = ws.rec_gap;
+    args.rec = rec ? ws.inc_rec : nullptr;
+    args.hist = rec ? ws.inc_hist : nullptr;
+    args.skip = ws.inc_auto ? &ws.sc->inc_go : nullptr;
     args.sc = ws.sc;
     args.pairs_scored = ws.pairs_scored;
     args.wide = (g.res[0] > 4096 || g.res[1] > 4096 || (D == 3 && g.res[2] > 4096)) ? 1 : 0;
     const int grid = (int)std::min<long long>(ntl, sms);
     const cudaError_t ep = record_scoring_start(ws, st);
     if (ep != cudaSuccess) return ep;
-    assign_tc_kernel<D, KIND><<<grid, kThreads, smem, st>>>(args);
+    if (rec) assign_tc_kernel<D, KIND, true><<<grid, kThreads, smem, st>>>(args);
+    else assign_tc_kernel<D, KIND, false><<<grid, kThreads, smem, st>>>(args);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Incremental pass.  The weights enter every cost linearly: at weights w the
+// cost of seed k differs from the recorded pass's (weights w0) by -(w_k - w0_k),
+// so C_k - C_a moves by -(Delta_k - Delta_a), Delta = w - w0.  Per pixel, with
+// a its recorded label:
+//  * gap0 > D = max Delta - min Delta: a stays (no other seed gained enough);
+//  * else, from the record {gl, gu, g3, b}: when g3 > max Delta - Delta_a no
+//    seed but a and b can be the argmin, and the sign of C_b - C_a, within
+//    [gl, gu] - (Delta_b - Delta_a), decides between them; an interval that
+//    holds 0 is settled by both costs in FP32 direct form (cost32_bound_rel's
+//    rigorous bound), or else by the FP64 rescoring;
+//  * else the pixel is re-decided in full: the warp scores the tile's recorded
+//    candidate list in FP32 direct form against the recorded bound of the
+//    excluded seeds, moved by the largest weight rise and re-expressed
+//    relative to the current w_ref; what that cannot settle goes to the FP64
+//    rescoring queue.
+// A pixel whose label changed moves its moment words from a's cell to the new
+// one (lanes with the same pair of cells summed first); the pass starts from
+// the recorded moments.  One warp per 32 pixels of a tile.  D, max Delta and
+// Delta per seed (float intervals, rounded outwards) and the shift of the
+// excluded bound (rounded down) come from the trial-weights kernel.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256)
+    tc_band_kernel(const GridDev g, const int ntiles, const int n, const SeedRec32 *__restrict__ recs_nat,
+                   const float *__restrict__ centre, const int4 *__restrict__ meta, const float *__restrict__ texcl,
+                   const int *__restrict__ list, const int32_t *__restrict__ lab0, const float *__restrict__ gap0,
+                   const float4 *__restrict__ rec0, const float2 *__restrict__ drift,
+                   unsigned long long *__restrict__ gmom, uint32_t *__restrict__ flags,
+                   int32_t *__restrict__ flag_gi, DevScalars *__restrict__ sc) {
+    using G = TcGeom<D>;
+    constexpr int KM = moment_width(D);
+    constexpr int kPix = G::TX * G::TY * G::TZ;
+    constexpr int kRows = kPix / 32;
+    const unsigned full_mask = 0xffffffffu;
+    if (!*(volatile const int *)&sc->inc_go) return;  // a recording pass: the scorer did it all
+    __shared__ unsigned s_full;  // this block's full re-decisions
+    if (threadIdx.x == 0) s_full = 0u;
+    const int lane = threadIdx.x & 31;
+    float wrh, wrl;
+    block_wref(sc, wrh, wrl);  // (its barrier also orders the counters' clearing)
+    const float finf = __int_as_float(0x7f800000);
+    const float bandD = sc->band_D, drift_hi = sc->drift_hi;
+    const long long nwarps = (long long)ntiles * kRows;
+    const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+    // one warp per 32 pixels (a row group) of a tile, grid-strided
+    for (long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nwarps; wi += wstride) {
+        const int t = (int)(wi / kRows), r = (int)(wi % kRows);
+        const int4 mt = meta[t];
+        const int lt = r * 32 + lane;
+        const int lk[3] = {lt % G::TX, (lt / G::TX) % G::TY, lt / (G::TX * G::TY)};
+        const int kk[3] = {mt.x + lk[0], mt.y + lk[1], D == 3 ? mt.z + lk[2] : 0};
+        const int klast = D == 3 ? kk[2] : kk[1];
+        const bool valid = kk[0] < g.res[0] && kk[1] < g.res[1] && (D == 2 || kk[2] < g.res[2]) &&
+                           klast >= win_lo(g) && klast < win_hi(g);
+        long long j = 0;
+        bool cand = false;
+        if (valid) {
+            j = (long long)kk[0] + (long long)g.res[0] * ((long long)kk[1] + (long long)g.res[1] * (long long)kk[2]);
+            cand = !(gap0[j] > bandD);
+        }
+        if (!__any_sync(full_mask, cand)) continue;
+        int a0 = -1, nl = -1, hint = -1, b = -1;
+        bool full = false, pair = false, flag = false;
+        if (cand) {
+            a0 = lab0[j];
+            if (a0 < 0 || a0 >= n) {  // no valid record (its pass failed): leave the pixel alone
+                atomicOr(&sc->status, ST_BAD_LABEL);
+                cand = false;
+                a0 = -1;
+            }
+        }
+        if (cand) {
+            const float4 rc = rec0[j];
+            b = __float_as_int(rc.w);
+            const float2 da = drift[a0];
+            // every seed but a and b: C_k - C_a >= g3 - (Delta_k - Delta_a) >= g3 - (max Delta - Delta_a)
+            const float thr = __fsub_ru(drift_hi, da.x);
+            if (!(rc.z > thr)) {
+                full = true;
+            } else if (b < 0 || b >= n) {
+                nl = a0;
+            } else {
+                const float2 db = drift[b];
+                const float lo = __fsub_rd(rc.x, __fsub_ru(db.y, da.x));  // C_b - C_a, rounded outwards
+                const float hi = __fsub_ru(rc.y, __fsub_rd(db.x, da.y));
+                if (lo > 0.f) nl = a0;
+                else if (hi < 0.f) nl = b;
+                else pair = true;
+            }
+        }
+        const unsigned fm = __ballot_sync(full_mask, full);
+        if (fm || __any_sync(full_mask, pair)) {
+            const int tdim[3] = {G::TX, G::TY, G::TZ};
+            float ypx[3] = {0.f, 0.f, 0.f};  // this lane's pixel relative to the tile centre
+#pragma unroll
+            for (int d = 0; d < D; ++d) ypx[d] = ((float)(lk[d] - tdim[d] / 2) + 0.5f) * g.h32[d];
+            float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                ch[d] = centre[(size_t)t * 6 + d];
+                cl[d] = centre[(size_t)t * 6 + 3 + d];
+            }
+            if (pair) {  // a against b in FP32 direct form, each lane its own pixel
+                float ca, ea, cb, eb;
+                cost32_bound_rel<D>(recs_nat[a0], ch, cl, ypx, wrh, wrl, ca, ea);
+                cost32_bound_rel<D>(recs_nat[b], ch, cl, ypx, wrh, wrl, cb, eb);
+                if (__fadd_ru(ca, ea) < __fsub_rd(cb, eb)) nl = a0;
+                else if (__fadd_ru(cb, eb) < __fsub_rd(ca, ea)) nl = b;
+                else {
+                    flag = true;
+                    hint = a0;
+                }
+            }
+            if (fm) {  // full re-decisions over the tile's list, one pixel at a time
+                const int cnt = mt.w;
+                const int ns = (cnt + kN - 1) / kN;
+                int lv[kMaxSteps];
+#pragma unroll
+                for (int k = 0; k < kMaxSteps; ++k)
+                    lv[k] = k * kN + lane < cnt ? list[(size_t)t * kListCap + k * kN + lane] : -1;
+                const float t0 = texcl[t];
+                const float tex = t0 < finf ? __fadd_rd(t0, sc->band_shift) : finf;
+                if (lane == 0) atomicAdd(&s_full, (unsigned)__popc(fm));
+                unsigned pending = fm;
+                while (pending) {
+                    const int p = __ffs(pending) - 1;
+                    pending &= pending - 1u;
+                    float yp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int d = 0; d < D; ++d) yp[d] = __shfl_sync(full_mask, ypx[d], p);
+                    float cv[kMaxSteps], ev[kMaxSteps];
+                    float ub = finf;
+                    int us = 0x7fffffff;
+#pragma unroll
+                    for (int k = 0; k < kMaxSteps; ++k) {
+                        cv[k] = finf;
+                        ev[k] = 0.f;
+                        if (k < ns && lv[k] >= 0) {
+                            cost32_bound_rel<D>(recs_nat[lv[k]], ch, cl, yp, wrh, wrl, cv[k], ev[k]);
+                            const float u1 = __fadd_ru(cv[k], ev[k]);
+                            if (u1 < ub || (u1 == ub && lv[k] < us)) {
+                                ub = u1;
+                                us = lv[k];
+                            }
+                        }
+                    }
+                    const unsigned kub = okey(ub);
+                    const unsigned kmin = __reduce_min_sync(full_mask, kub);
+                    const int smin = (int)__reduce_min_sync(full_mask, kub == kmin ? (unsigned)us : 0x7fffffffu);
+                    const float Ub = okey_inv(kmin);
+                    bool other = false;
+#pragma unroll
+                    for (int k = 0; k < kMaxSteps; ++k)
+                        if (k < ns && lv[k] >= 0 && lv[k] != smin && !(__fsub_rd(cv[k], ev[k]) > Ub)) other = true;
+                    const bool ok2 = !__any_sync(full_mask, other) && Ub < tex && smin < n;
+                    if (lane == p) {
+                        if (ok2) {
+                            nl = smin;
+                        } else {
+                            flag = true;
+                            hint = smin < n ? smin : -1;
+                        }
+                    }
+                }
+            }
+        }
+        // near ties to the FP64 rescoring (which moves their words from a's cell)
+        const unsigned qm = __ballot_sync(full_mask, flag);
+        if (qm) {
+            unsigned base = 0u;
+            if (lane == __ffs(qm) - 1) base = atomicAdd(&sc->flag_count, (unsigned)__popc(qm));
+            base = __shfl_sync(full_mask, base, __ffs(qm) - 1);
+            if (flag) {
+                const unsigned slot = base + (unsigned)__popc(qm & ((1u << lane) - 1u));
+                flags[slot] = (uint32_t)j;
+                if (flag_gi) flag_gi[slot] = hint;
+            }
+        }
+        // moved pixels: their words leave a's cell for the new one, summed per pair of cells
+        const bool moved = nl >= 0 && nl != a0;
+        unsigned todo = __ballot_sync(full_mask, moved);
+        while (todo) {
+            const int leader = __ffs(todo) - 1;
+            const int A0 = __shfl_sync(full_mask, a0, leader), NL = __shfl_sync(full_mask, nl, leader);
+            const bool mine = moved && a0 == A0 && nl == NL;
+            const unsigned grp = __ballot_sync(full_mask, mine);
+            unsigned long long u[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+            for (int d = 0; d < D; ++d) u[d] = mine ? 2ull * (unsigned long long)kk[d] + 1ull : 0ull;
+            unsigned long long word = 0ull;
+            int e = 0;
+            auto fold = [&](unsigned long long x) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(full_mask, x, off);
+                if (lane == e) word = x;
+                ++e;
+            };
+            fold(mine ? 1ull : 0ull);
+#pragma unroll
+            for (int d = 0; d < D; ++d) fold(u[d]);
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+#pragma unroll
+                for (int d2 = d; d2 < D; ++d2) fold(u[d] * u[d2]);
+            if (lane < KM && word) {
+                atomicAdd(&gmom[(size_t)NL * KM + lane], word);
+                atomicAdd(&gmom[(size_t)A0 * KM + lane], 0ull - word);
+            }
+            todo &= ~grp;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_full) atomicAdd(&sc->band_count, s_full);
+    }
+}
+
+template <int D>
+cudaError_t launch_band_t(const GridDev &g, int n, const double *w, Workspace &ws, cudaStream_t st) {
+    using G = TcGeom<D>;
+    (void)w;
+    int ntx = 0, nty = 0, tlo = 0;
+    long long ntl = 0;
+    tile_grid<D>(g, ntx, nty, tlo, ntl);
+    if (ntl > ws.tc_tile_cap || !ws.inc_labels || !ws.inc_gap || !ws.inc_rec || !ws.inc_drift)
+        return cudaErrorInvalidValue;
+    const int ntiles = (int)ntl;
+    // one warp per 32 pixels of a tile, grid-strided: a few resident blocks per SM
+    // (a recording pass launches it for nothing)
+    const long long warps = ntl * (G::TX * G::TY * G::TZ / 32);
+    const long long blocks = std::max<long long>(1, std::min<long long>((warps * 32 + 255) / 256, (long long)ws.sms * 8));
+    tc_band_kernel<D><<<(unsigned)blocks, 256, 0, st>>>(
+        g, ntiles, n, ws.recs32, ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.inc_labels, ws.inc_gap,
+        ws.inc_rec, ws.inc_drift, ws.moments, ws.flags, ws.flag_gi, ws.sc);
     return cudaGetLastError();
 }
 
@@ -1420,6 +1802,10 @@ cudaError_t launch_tc_axis(const GridDev &g, Workspace &ws, cudaStream_t st) {
     tile_grid<2>(g, ntx, nty, tlo, ntl);
     if (ntl > ws.tc_tile_cap) return cudaSuccess;
     return ensure_axis<2>(g, ntx, nty, 0, tlo, ws, st);
+}
+
+cudaError_t launch_tc_band(const GridDev &g, int n, const double *w, Workspace &ws, cudaStream_t st) {
+    return g.dim == 3 ? launch_band_t<3>(g, n, w, ws, st) : launch_band_t<2>(g, n, w, ws, st);
 }
 
 long long tc_tile_count(const GridDev &g) {

@@ -148,13 +148,40 @@ bool use_tensor_cores(const GridDev &g, apd_precision prec, Workspace &ws, bool 
     return ws.tc_cond <= kTcMaxCond;
 }
 
+// Incremental passes (weight solves, pruned tensor-core scorer, one rank).  A
+// pass queued with kIncAuto either re-decides from the solve's record or
+// records afresh; the trial-weights kernel chooses on the device (sc->inc_go):
+// a re-decision when a record exists and at most kIncFullMax of the pixels can
+// need a full one (see tc_band_kernel).  The first pass of a solve records.
+constexpr int kIncNone = 0, kIncAuto = 1;
+constexpr double kIncFullMax = 0.08;
+
+// The buffers of the incremental passes, allocated on first use (never inside a
+// graph capture).
+static int inc_alloc(Workspace &ws) {
+    if (ws.inc_labels) return APD_OK;
+    const size_t K = (size_t)moment_width(ws.dim);
+    bool ok = cudaMalloc((void **)&ws.inc_labels, (size_t)ws.max_j * sizeof(int32_t)) == cudaSuccess &&
+              cudaMalloc((void **)&ws.inc_gap, (size_t)ws.max_j * sizeof(float)) == cudaSuccess &&
+              cudaMalloc((void **)&ws.inc_rec, (size_t)ws.max_j * sizeof(float4)) == cudaSuccess &&
+              cudaMalloc((void **)&ws.inc_hist, kIncBins * sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc((void **)&ws.inc_drift, (size_t)ws.max_n * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc((void **)&ws.inc_mom0, (size_t)ws.max_n * K * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc((void **)&ws.inc_w0, (size_t)ws.max_n * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&ws.inc_aux, 2 * sizeof(unsigned long long)) == cudaSuccess;
+    return ok ? APD_OK : APD_ERR_CUDA;
+}
+
 // Queues one pass of scoring + rescoring + moments at weights w.  With
 // weights_only the records of the previous pass (same x, A, n) are reused and
 // only the weights change; with a step, w (device, n) is first set to
-// step->W + step->t step->p.
+// step->W + step->t step->p.  inc = kIncAuto makes it an incremental pass where
+// the form allows (ws.inc_recorded says whether it was queued as one).
 int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A, const double *w,
                    apd_precision prec, Workspace &ws, int32_t *labels, unsigned long long *mom,
-                   cudaStream_t st, bool weights_only = false, const TrialStep *step = nullptr) {
+                   cudaStream_t st, bool weights_only = false, const TrialStep *step = nullptr,
+                   int inc = kIncNone) {
+    ws.inc_recorded = false;
     if (prec != APD_FP32 && prec != APD_TC_TF32 && prec != APD_TC_BF16) return APD_ERR_UNSUPPORTED;
     GridDev g = g_in;
     const bool sharded = ws.shard_world > 1 && !g.kz1;
@@ -166,20 +193,32 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
     }
     const bool empty = g.kz1 && g.kz1 <= g.kz0;  // an empty slab: moments stay zero
     const size_t K = (size_t)moment_width(g.dim);
+    // an incremental pass needs the pruned tensor-core scorer on one rank (its
+    // buffers are allocated by the caller, outside any graph capture)
+    const bool inc_form = inc == kIncAuto && !sharded && !empty && ws.prune && ws.inc_labels &&
+                          prec != APD_FP32;
+    bool tc = false, inc_on = false;
     if (weights_only) {
+        tc = !empty && use_tensor_cores(g, prec, ws, true, st);
+        inc_on = inc_form && tc;
         // one launch: moments and counters cleared, trial weights into the records
         // the first trial of a new L-BFGS direction forms p too (see Solver::iterate)
         const bool form_p = ws.p_pending && step && step->p == ws.p;
         ws.p_pending = false;
+        const unsigned full_max = (unsigned)(kIncFullMax * (double)win_pixels(g));
         APD_TRY(cuda_ok(launch_eval_begin(n, step ? step->W : w, step ? step->t : 0.0, step ? step->p : nullptr,
-                                          const_cast<double *>(w), mom, ws, st, form_p)));
+                                          const_cast<double *>(w), mom, ws, st, form_p,
+                                          inc_on ? ws.inc_w0 : nullptr, full_max)));
     } else {
         if (step) APD_TRY(cuda_ok(launch_axpy(n, step->W, step->t, step->p, const_cast<double *>(w), st)));
         APD_TRY(cuda_ok(cudaMemsetAsync(mom, 0, (size_t)n * K * sizeof(unsigned long long), st)));
-        APD_TRY(cuda_ok(launch_eval_reset(ws, st, false)));
+        APD_TRY(cuda_ok(launch_eval_reset(ws, st, false)));  // also: no record, this pass records
         APD_TRY(cuda_ok(launch_seed_prep(g, n, x, A, w, ws, st)));
         APD_TRY(cuda_ok(launch_group_bounds(n, ws, st)));
+        tc = !empty && use_tensor_cores(g, prec, ws, false, st);
+        inc_on = inc_form && tc;
     }
+    if (inc_on) APD_TRY(cuda_ok(launch_inc_prepare(n, mom, ws, st)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ws.profiling && ws.capturing) {
         // the graph's own events; the replay reads them after its synchronisation
@@ -202,14 +241,32 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
     // the tensor-core tiling needs per-tile scratch; grids too thin for the
     // workspace's tile capacity are scored by the FP32 kernel (same labels)
     if (empty) {
-    } else if (!use_tensor_cores(g, prec, ws, weights_only, st))
+    } else if (!tc)
         APD_TRY(cuda_ok(launch_assign_fp32(g, n, ws, labels, mom, st)));
-    else
-        APD_TRY(cuda_ok(launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st)));
+    else {
+        // an incremental pass: the pre-pass and the scorer (recording variant, the
+        // labels into the record) do nothing when the device chose a re-decision
+        if (inc_on) {
+            labels = ws.inc_labels;
+            ws.rec_gap = ws.inc_gap;
+            ws.inc_auto = true;
+        }
+        const cudaError_t e = launch_assign_tc(g, n, ws, labels, mom, prec == APD_TC_TF32 ? 0 : 1, st);
+        ws.rec_gap = nullptr;
+        ws.inc_auto = false;
+        APD_TRY(cuda_ok(e));
+        ws.inc_recorded = inc_on;
+    }
     APD_TRY(cuda_ok(record_scoring_start(ws, st)));  // nothing launched (an empty slab)
     if (e1) APD_TRY(cuda_ok(ws.capturing ? cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal)
                                          : cudaEventRecord(e1, st)));
-    if (!empty) APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st)));
+    // the re-decision (nothing when the pass records), the rescoring in the mode
+    // the device chose, and a recording's moments, weights and w_ref kept
+    if (inc_on) APD_TRY(cuda_ok(launch_tc_band(g, n, w, ws, st)));
+    if (!empty)
+        APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st, inc_on ? ws.inc_labels : nullptr,
+                                            inc_on ? &ws.sc->inc_go : nullptr)));
+    if (inc_on) APD_TRY(cuda_ok(launch_inc_commit(n, mom, w, ws, st)));
     if (sharded) {
         // every rank's slab moments, summed, before anything reads them
         const apd_seeds cur{n, x, A, w};
@@ -219,7 +276,8 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
     }
     // the tensor-core launcher counts its pre-pass launches itself
     ws.kernel_launches += (weights_only ? 3 : (ws.sorted ? 6 : 4) + (ws.groups ? 1 : 0) + (step ? 1 : 0)) -
-                          (empty ? 2 : 0);  // an empty slab launches neither scoring nor rescoring
+                          (empty ? 2 : 0) +  // an empty slab launches neither scoring nor rescoring
+                          (inc_on ? 3 : 0);  // the incremental pass's prepare, re-decision and commit
     ws.last_pixels = win_pixels(g);
     ws.last_pairs = win_pixels(g) * (long long)n;
     return APD_OK;
@@ -261,6 +319,8 @@ struct Solver {
     bool last_is_best = false;
     bool first = true;
     bool geometry_ready = false;  // records of x, A built (they are fixed for the solve)
+    int inc_mode = kIncNone;  // kIncAuto: every pass incremental (see enqueue_assign)
+    int64_t inc_redecided = 0;  // passes the device made re-decisions
 
     Solver(Workspace &w) : ws(w) {}
 
@@ -271,7 +331,7 @@ struct Solver {
     int enqueue_eval(const double *Wp, double *gf_out, const double *pdir, const TrialStep *step,
                      cudaStream_t s) {
         // the records' positions and matrices are built once per solve
-        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, s, geometry_ready, step));
+        APD_TRY(enqueue_assign(g, n, x, A, Wp, prec, ws, nullptr, ws.moments, s, geometry_ready, step, inc_mode));
         APD_TRY(cuda_ok(launch_dual(g, n, x, A, Wp, v, pdir, ws.moments, ws, nullptr, ws.grad, gf_out,
                                     nullptr, s)));
         ws.kernel_launches += 1;
@@ -285,7 +345,7 @@ struct Solver {
         eg = nullptr;
         if (!ws.graphs || !geometry_ready || ws.shard_world > 1) return APD_OK;
         struct Key {
-            int dim, res[3], kz0, kz1, n, prec, prune, sorted, profiling, has_step, form_p, pad;
+            int dim, res[3], kz0, kz1, n, prec, prune, sorted, profiling, has_step, form_p, inc;
             uint32_t wait_limit, use_tc;
             double lo[3], h[3];
             const void *ptr[9];
@@ -307,6 +367,7 @@ struct Solver {
         k.has_step = step ? 1 : 0;
         const bool form_p = ws.p_pending && step && step->p == ws.p;  // as enqueue_assign decides it
         k.form_p = form_p ? 1 : 0;
+        k.inc = inc_mode;
         k.wait_limit = ws.wait_limit;
         // the scorer the captured pass takes (the seeds' conditioning can change it between solves)
         const bool tc = use_tensor_cores(g, prec, ws, true, st);
@@ -354,6 +415,7 @@ struct Solver {
             ws.kernel_launches = kl0;
             e.pixels = ws.last_pixels;
             e.pairs = ws.last_pairs;
+            e.recorded = ws.inc_recorded;
             if (rc != APD_OK && rc != APD_ERR_CUDA) return rc;  // an argument error, as without a graph
             if (!e.failed && step) {
                 size_t nn = 0;
@@ -385,22 +447,39 @@ struct Solver {
         ws.p_pending = false;
         if (step)
             APD_TRY(cuda_ok(set_eval_begin_node(eg->exec, eg->begin, n, step->W, step->t, step->p,
-                                                const_cast<double *>(Wp), ws.moments, ws, form_p)));
+                                                const_cast<double *>(Wp), ws.moments, ws, form_p,
+                                                eg->recorded ? ws.inc_w0 : nullptr,
+                                                (unsigned)(kIncFullMax * (double)win_pixels(g)))));
         APD_TRY(cuda_ok(cudaGraphLaunch(eg->exec, st)));
         ws.kernel_launches += eg->launches;
         ws.last_pixels = eg->pixels;
         ws.last_pairs = eg->pairs;
+        ws.inc_recorded = eg->recorded;
         return APD_OK;
     }
 
     int eval(const double *Wp, double *gf_out, const double *pdir, double &f, double &dphi,
              double &err, const TrialStep *step = nullptr) {
+        inc_mode = kIncNone;
+        if (ws.incremental && ws.prune && ws.shard_world <= 1 && prec != APD_FP32) {
+            APD_TRY(inc_alloc(ws));  // never inside a graph capture
+            inc_mode = kIncAuto;
+        }
         EvalGraph *eg = nullptr;
         APD_TRY(graph_eval(Wp, gf_out, pdir, step, eg));
         if (!eg) APD_TRY(enqueue_eval(Wp, gf_out, pdir, step, st));
         geometry_ready = true;
         APD_TRY(cuda_ok(cudaStreamSynchronize(st)));
-        if (eg && eg->e0 && ws.profiling) {
+        // a re-decision ran no scoring kernel: its (empty) launch is not timed
+        const bool redecided = ws.inc_recorded && ws.sc_host->inc_go;
+        if (redecided) {
+            ++inc_redecided;
+            if (!eg && ws.profiling && ws.ev_used >= 2) {
+                ws.ev_used -= 2;
+                ws.prof_pairs -= ws.last_pairs;
+            }
+        }
+        if (eg && eg->e0 && ws.profiling && !redecided) {
             float ms = 0.f;
             APD_TRY(cuda_ok(cudaEventElapsedTime(&ms, eg->e0, eg->e1)));
             ws.prof_ms_graph += ms;
@@ -860,7 +939,7 @@ void apd_workspace_destroy(apd_workspace *ws) {
     if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     void *ptrs[] = {w.recs, w.recs32, w.recs_tmp, w.codes, w.scodes, w.perm, w.recs32s, w.tc_centre, w.tc_start, w.tc_meta, w.tc_texcl, w.tc_list, w.tc_bops, w.tc_axis, w.moments, w.flags, w.flag_gi, w.pairs_scored, w.groups, w.sc, w.part, w.grad, w.W, w.Wt, w.p, w.gf, w.gft,
                     w.Wbest, w.S, w.Y, w.gram, w.lb_part, w.lb_coef, w.rho, w.X, w.vbuf, w.wfeat, w.wpred,
-                    w.S2, w.Y2, w.gram2, w.rho2};
+                    w.S2, w.Y2, w.gram2, w.rho2, w.inc_labels, w.inc_gap, w.inc_rec, w.inc_hist, w.inc_drift, w.inc_mom0, w.inc_w0, w.inc_aux};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.sc_host) cudaFreeHost(w.sc_host);
@@ -1003,6 +1082,12 @@ int apd_lbfgs_check(int32_t n, int32_t hist, const double *S, const double *Y, c
     for (void *q : bufs) cudaFree(q);
     if (!ok) return APD_ERR_CUDA;
     *gp = h.gp0;
+    return APD_OK;
+}
+
+int apd_workspace_set_incremental(apd_workspace *ws, int32_t enable) {
+    if (!ws) return APD_ERR_ARG;
+    ws->w.incremental = enable != 0;
     return APD_OK;
 }
 

@@ -167,7 +167,8 @@ __device__ __forceinline__ void cost32_bound_rel(const SeedRec32 &r, const float
 template <int D>
 __device__ __forceinline__ void rescore_finish(const GridDev &g, const int n, const long long j, const int (&k)[3],
                                                double best, int bi, DevScalars *__restrict__ sc,
-                                               unsigned long long *__restrict__ gmom, int32_t *__restrict__ labels) {
+                                               unsigned long long *__restrict__ gmom, int32_t *__restrict__ labels,
+                                               const int32_t *__restrict__ old_labels = nullptr) {
     constexpr int K = moment_width(D);
     const int lane = threadIdx.x & 31;
     // smallest (cost, index) over the few lanes holding a candidate (FP64 compares
@@ -192,18 +193,33 @@ __device__ __forceinline__ void rescore_finish(const GridDev &g, const int n, co
             atomicOr(&sc->status, ST_BAD_LABEL);
         } else {
             if (labels) labels[j] = bi;
-            unsigned long long u[3];
+            // with old_labels the moments hold another labelling's sums: move the
+            // pixel's words from its old cell to its new one (two's-complement
+            // subtraction; nothing when the label is unchanged)
+            int old = old_labels ? old_labels[j] : -1;
+            if (old >= n) old = -1;
+            if (old != bi) {
+                unsigned long long u[3];
 #pragma unroll
-            for (int a = 0; a < D; ++a) u[a] = 2ull * (unsigned long long)k[a] + 1ull;
-            unsigned long long *o = gmom + (size_t)bi * K;
-            atomicAdd(&o[0], 1ull);
+                for (int a = 0; a < D; ++a) u[a] = 2ull * (unsigned long long)k[a] + 1ull;
+                unsigned long long words[K];
+                words[0] = 1ull;
 #pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(&o[1 + a], u[a]);
-            int e = 1 + D;
+                for (int a = 0; a < D; ++a) words[1 + a] = u[a];
+                int e = 1 + D;
 #pragma unroll
-            for (int a = 0; a < D; ++a)
+                for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int b = a; b < D; ++b) atomicAdd(&o[e++], u[a] * u[b]);
+                    for (int b = a; b < D; ++b) words[e++] = u[a] * u[b];
+                unsigned long long *o = gmom + (size_t)bi * K;
+#pragma unroll
+                for (int v = 0; v < K; ++v) atomicAdd(&o[v], words[v]);
+                if (old >= 0) {
+                    unsigned long long *q = gmom + (size_t)old * K;
+#pragma unroll
+                    for (int v = 0; v < K; ++v) atomicAdd(&q[v], 0ull - words[v]);
+                }
+            }
         }
     }
 }
@@ -222,7 +238,8 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
                                               const SeedRec32 *__restrict__ r32, const uint32_t fj, const int gi,
                                               const float wrh, const float wrl, const RescorePrune &pr,
                                               DevScalars *__restrict__ sc, unsigned long long *__restrict__ gmom,
-                                              int32_t *__restrict__ labels) {
+                                              int32_t *__restrict__ labels,
+                                              const int32_t *__restrict__ old_labels = nullptr) {
     const int lane = threadIdx.x & 31;
     const long long j = (long long)fj;
     int k[3] = {0, 0, 0};
@@ -273,7 +290,7 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
                 }
             }
         }
-        rescore_finish<D>(g, n, j, k, best, bi, sc, gmom, labels);
+        rescore_finish<D>(g, n, j, k, best, bi, sc, gmom, labels, old_labels);
         return;
     }
     // full scan: pass 1, threshold = min over seeds of (C + E)
@@ -295,7 +312,7 @@ __device__ __forceinline__ void rescore_pixel(const GridDev &g, const int n, con
             bi = s;
         }
     }
-    rescore_finish<D>(g, n, j, k, best, bi, sc, gmom, labels);
+    rescore_finish<D>(g, n, j, k, best, bi, sc, gmom, labels, old_labels);
 }
 
 // Relative gap of the two smallest costs at pixel j (one warp), the quantity

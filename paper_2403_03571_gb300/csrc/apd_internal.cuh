@@ -80,12 +80,22 @@ struct DevScalars {
     long long rescored_total;
     unsigned int mask_count;            // boundary coarse pixels listed by the masked discretisation
     unsigned int lbfgs_done;            // block counter of the L-BFGS kernels' last-block reductions
+    unsigned int band_count;            // pixels re-decided by the last incremental pass
+    double drift_max, drift_min;        // max and min of w - w0 (incremental passes)
+    float band_D;                       // drift_max - drift_min rounded up
+    float band_shift;                   // w_ref - w_ref0 - drift_max rounded down
+    float drift_hi;                     // drift_max rounded up to a float
+    int inc_go;                         // this incremental pass re-decides from the record (else records)
+    int inc_valid;                      // a record of this solve exists
 };
 
 // Partial sums per block row of the L-BFGS dot-product kernels: the push's
 // 3 + 3 (cap - 1) Gram products and 2 + 2 (cap - 1) direction products, cap = 32.
 constexpr int kLbfgsDots = 160;
 constexpr int kPartStride = 6;  // doubles per block row of Workspace::part
+// Bins of the incremental record's margin histogram: a positive float margin
+// falls in bin (its bits >> 21), four bins per octave (bin 0: no margin).
+constexpr int kIncBins = 1024;
 
 // Coefficients of an L-BFGS direction p = -gamma g + sum_k (cy_k y_k + cs_k s_k)
 // over the pairs in slot[0..hist) (device; written by the direction's first kernel).
@@ -99,7 +109,8 @@ struct LbfgsCoef {
 // Bits of Workspace::attr_done: the dynamic shared-memory limit of these
 // kernels is raised once per workspace (a workspace lives on one device).
 constexpr unsigned kAttrFp32Score2 = 1u << 0, kAttrFp32Score3 = 1u << 1, kAttrMortonSort = 1u << 2;
-constexpr unsigned kAttrTcScore = 1u << 3;  // + 1 bit per (dimension, operand kind): 4 bits
+constexpr unsigned kAttrTcScore = 1u << 3;     // + 1 bit per (dimension, operand kind): 4 bits
+constexpr unsigned kAttrTcScoreRec = 1u << 7;  // the recording variant: 4 bits
 
 // One evaluation of a weight solve (trial weights, scoring, rescoring, dual,
 // read-back of the device scalars) captured as a CUDA graph and replayed with
@@ -113,6 +124,7 @@ struct EvalGraph {
     cudaEvent_t e0 = nullptr, e1 = nullptr;  // around the scoring stage (profiling)
     uint64_t used = 0;
     bool failed = false;  // capture refused: this key runs without a graph
+    bool recorded = false;  // queued as an incremental pass (the device chooses its kind)
 };
 
 // Workspace (host struct; device pointers inside).
@@ -171,6 +183,23 @@ struct Workspace {
     int lb_rows = 0;
     LbfgsCoef *lb_coef = nullptr;       // the last direction's coefficients
     bool p_pending = false;             // lb_coef holds a direction that ws.p does not yet hold
+    // incremental evaluation (weight solves with the pruned tensor-core scorer): a
+    // full pass records each pixel's label, runner-up and certified cost margins,
+    // the moments and the weights; a later pass at weights w re-decides only the
+    // pixels whose margins the drift w - w0 can close.  Which of the two a pass
+    // is, the trial-weights kernel decides on the device (sc->inc_go).
+    int32_t *inc_labels = nullptr;      // [max_j] labels of the recorded pass
+    float *inc_gap = nullptr;           // [max_j] certified gaps of the recorded pass
+    float4 *inc_rec = nullptr;          // [max_j] runner-up and margins of the recorded pass
+    unsigned *inc_hist = nullptr;       // [kIncBins] recorded pixels by their g3 margin (see kIncBins)
+    float2 *inc_drift = nullptr;        // [max_n] w - w0 per seed as a float interval (lo, hi)
+    bool inc_auto = false;              // set while an incremental pass is queued (kernels test sc->inc_go)
+    unsigned long long *inc_mom0 = nullptr;  // [max_n * K] moments of the recorded pass
+    double *inc_w0 = nullptr;           // [max_n] weights of the recorded pass
+    unsigned long long *inc_aux = nullptr;  // [2] ordered key of the recorded pass's w_ref, spare
+    float *rec_gap = nullptr;           // set while a recording pass is queued (the scorer's gap output)
+    bool incremental = true;            // apd_workspace_set_incremental
+    bool inc_recorded = false;          // the last queued pass recorded its state
     double *rho = nullptr;              // [hist_cap]
     // a second L-BFGS history (pairs, Gram entries, 1 / s.y) continued by the coarse
     // solves of a Lloyd run (allocated on first use), and its host-side state
@@ -369,8 +398,13 @@ cudaError_t launch_masked_refine(const GridDev &gc, const GridDev &gf, int r, in
 // W0 itself) in the records, wref and the group weight gaps
 // form_p: pdir is first formed from the last direction coefficients (ws.lb_coef,
 // gradient ws.gf) and <gf, p> goes to sc->gp0.
+// w0 (nullable): the drift range max/min of w - w0 goes to sc->drift_max / drift_min.
+// With w0 (incremental passes) also the drift range of w - w0 and the choice of
+// the pass: re-decide from the record when one exists and at most full_max
+// recorded pixels have a g3 margin within the drift (sc->inc_go), else record.
 cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *pdir, double *Wt,
-                              unsigned long long *mom, Workspace &ws, cudaStream_t st, bool form_p = false);
+                              unsigned long long *mom, Workspace &ws, cudaStream_t st, bool form_p = false,
+                              const double *w0 = nullptr, unsigned full_max = 0u);
 // seed records (FP64 x, w; FP32 symmetric A) + stats (max w, max ||A||_F, min lambda bound)
 cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const double *A,
                              const double *w, Workspace &ws, cudaStream_t st);
@@ -391,7 +425,8 @@ cudaError_t launch_group_bounds(int n, Workspace &ws, cudaStream_t st);
 // FP64 rescoring of the queued pixels (labels optional, moments updated).
 cudaError_t launch_rescore_fp64(const GridDev &g, int n, const double *x, const double *A,
                                 const double *w, Workspace &ws, int32_t *labels,
-                                unsigned long long *moments, cudaStream_t st);
+                                unsigned long long *moments, cudaStream_t st,
+                                const int32_t *old_labels = nullptr, const int *go = nullptr);
 // relative gap of the two smallest FP64 costs of every pixel (after a scoring
 // pass on the same seeds: uses its records, group bounds and w_ref)
 cudaError_t launch_tie_gap(const GridDev &g, int n, const double *x, const double *A, const double *w,
@@ -432,10 +467,18 @@ inline cudaError_t record_scoring_start(Workspace &ws, cudaStream_t st) {
 const void *eval_begin_kernel_fn();
 cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int n, const double *W0, double t,
                                 const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws,
-                                bool form_p);
+                                bool form_p, const double *w0, unsigned full_max);
 // the direction's coefficients only (p is then formed by the next trial's eval_begin)
 cudaError_t launch_lbfgs_coefficients(int n, int hist, int newest, int cap, double gamma, bool use_pair,
                                       int hist_acc, int newest_acc, Workspace &ws, cudaStream_t st);
 cudaError_t launch_tc_axis(const GridDev &g, Workspace &ws, cudaStream_t st);
+// the incremental pass's re-decision of the pixels within the drift of their recorded gap
+cudaError_t launch_tc_band(const GridDev &g, int n, const double *w, Workspace &ws, cudaStream_t st);
+// incremental pass, before scoring: the recorded moments copied in (re-decision)
+// or the margin histogram cleared (recording); after rescoring: the record's
+// moments, weights and w_ref kept (recording)
+cudaError_t launch_inc_prepare(int n, unsigned long long *mom, Workspace &ws, cudaStream_t st);
+cudaError_t launch_inc_commit(int n, const unsigned long long *mom, const double *w, Workspace &ws,
+                              cudaStream_t st);
 
 }  // namespace apd

@@ -16,6 +16,8 @@ __global__ void eval_reset_kernel(DevScalars *sc, const int keep_geometry) {
     sc->flag_count = 0u;
     sc->wref_key = 0ull;
     sc->dual_done = 0u;
+    sc->inc_go = 0;     // a full pass: it records (incremental solves) ...
+    sc->inc_valid = 0;  // ... and no earlier record holds for its records
     if (!keep_geometry) {
         sc->lam_abs_bits = 0ull;
         sc->lam_min_bits = 0x7ff0000000000000ull;
@@ -40,8 +42,11 @@ __global__ void __launch_bounds__(256)
                       SeedRec32 *__restrict__ recs32, SeedRec32 *__restrict__ recs32s,
                       GroupBound *__restrict__ groups, unsigned long long *__restrict__ mom,
                       double *__restrict__ part, DevScalars *__restrict__ sc, const LbfgsCoef *__restrict__ coef,
-                      const double *__restrict__ S, const double *__restrict__ Y, const double *__restrict__ gfv) {
-    __shared__ double shw[8], shg[8];
+                      const double *__restrict__ S, const double *__restrict__ Y, const double *__restrict__ gfv,
+                      const double *__restrict__ w0, const unsigned long long *__restrict__ wref0,
+                      const unsigned *__restrict__ g3_hist, const unsigned full_max,
+                      float2 *__restrict__ drift) {
+    __shared__ double shw[8], shg[8], shdx[8], shdn[8];
     __shared__ double ccy[32], ccs[32];
     __shared__ int cslot[32];
     __shared__ bool last;
@@ -59,8 +64,12 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
     }
     double gp = 0.0;
+    double dhi = -DBL_MAX, dlo = DBL_MAX;  // range of w - w0 (with w0)
     for (long long e = i; e < n_mom; e += (long long)gridDim.x * blockDim.x) mom[e] = 0ull;
-    if (i == 0) sc->flag_count = 0u;
+    if (i == 0) {
+        sc->flag_count = 0u;
+        sc->band_count = 0u;
+    }
     const int src = i < n_pad ? (perm ? perm[i] : i) : n;
     const bool real = src < n;
     double wkey = -DBL_MAX;
@@ -98,12 +107,25 @@ __global__ void __launch_bounds__(256)
             recs32s[i].wl = wl;
         }
         wkey = finite ? wi : -DBL_MAX;
+        if (w0) {  // rounded outwards, so that the range covers the exact drift
+            dhi = __dsub_ru(wi, w0[src]);
+            dlo = __dsub_rd(wi, w0[src]);
+            if (drift) drift[src] = make_float2(__double2float_rd(dlo), __double2float_ru(dhi));
+        }
     }
     const double wmax = warp_max(wkey);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (coef) {
         gp = warp_sum(gp);
         if (lane == 0) shg[wid] = gp;
+    }
+    if (w0) {
+        dhi = warp_max(dhi);
+        dlo = warp_min(dlo);
+        if (lane == 0) {
+            shdx[wid] = dhi;
+            shdn[wid] = dlo;
+        }
     }
     if (lane == 0) {
         shw[wid] = wmax;
@@ -119,6 +141,15 @@ __global__ void __launch_bounds__(256)
             double s = 0.0;
             for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += shg[k];
             part[(size_t)blockIdx.x * kPartStride + 1] = s;
+        }
+        if (w0) {
+            double x = -DBL_MAX, m = DBL_MAX;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                x = fmax(x, shdx[k]);
+                m = fmin(m, shdn[k]);
+            }
+            part[(size_t)blockIdx.x * kPartStride + 2] = x;
+            part[(size_t)blockIdx.x * kPartStride + 3] = m;
         }
         __threadfence();
         last = atomicAdd(&sc->dual_done, 1u) == gridDim.x - 1;
@@ -140,6 +171,37 @@ __global__ void __launch_bounds__(256)
             const double wm = *(volatile double *)&groups[gidx].wmax;
             groups[gidx].wgap = __double2float_rd(wref - wm);
         }
+    if (w0 && threadIdx.x < 32) {  // the drift range (max and min are order-independent)
+        double x = -DBL_MAX, m = DBL_MAX;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += 32) {
+            x = fmax(x, *(volatile double *)&part[(size_t)k * kPartStride + 2]);
+            m = fmin(m, *(volatile double *)&part[(size_t)k * kPartStride + 3]);
+        }
+        x = warp_max(x);
+        m = warp_min(m);
+        // the pixels a re-decision would settle in full have g3 <= D: bound their
+        // count by the record's histogram (every bin up to D's); bin 0 (no
+        // certified margin: FP64 near ties) costs a recording as much
+        const float bD = __double2float_ru(__dsub_ru(x, m));
+        const unsigned eD = bD > 0.f ? min(__float_as_uint(bD) >> 21, (unsigned)kIncBins - 1u) : 0u;
+        unsigned cnt = 0u;
+        if (g3_hist)
+            for (unsigned e = threadIdx.x; e < (unsigned)kIncBins; e += 32u)
+                cnt += (e > 0u && e <= eD) ? g3_hist[e] : 0u;
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (threadIdx.x == 0) {
+            sc->drift_max = x;
+            sc->drift_min = m;
+            sc->drift_hi = __double2float_ru(x);
+            sc->inc_go = (sc->inc_valid && g3_hist && cnt <= full_max) ? 1 : 0;
+            // the incremental pass's band width and excluded-seed shift, rounded outwards
+            sc->band_D = bD;
+            // (less 2^-40 (|w_ref| + |w_ref0|): the scorers take w_ref as a float pair)
+            const double wr0 = wref0 ? dkey_inv(*wref0) : wref;
+            const double slack = ldexp(fabs(wref) + fabs(wr0), -40);
+            sc->band_shift = __double2float_rd(__dsub_rd(__dsub_rd(__dsub_rd(wref, wr0), x), slack));
+        }
+    }
     if (coef && threadIdx.x < 32) {  // <gf, p>: the blocks' sums, lane-strided, then a fixed tree
         double s = 0.0;
         for (unsigned k = threadIdx.x; k < gridDim.x; k += 32) s += *(volatile double *)&part[(size_t)k * kPartStride + 1];
@@ -763,7 +825,10 @@ cudaError_t launch_eval_reset(Workspace &ws, cudaStream_t st, bool keep_geometry
 static int eval_begin_threads(int n_pad, const Workspace &ws) { return n_pad / 64 <= ws.part_rows ? 64 : 256; }
 
 cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *pdir, double *Wt,
-                              unsigned long long *mom, Workspace &ws, cudaStream_t st, bool form_p) {
+                              unsigned long long *mom, Workspace &ws, cudaStream_t st, bool form_p,
+                              const double *w0, unsigned full_max) {
+    const unsigned long long *wref0 = w0 ? ws.inc_aux : nullptr;
+    const unsigned *hist = w0 ? ws.inc_hist : nullptr;
     const int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
     const long long n_mom = (long long)n * moment_width(ws.dim);
     if (n_pad == 0) return cudaSuccess;
@@ -772,7 +837,8 @@ cudaError_t launch_eval_begin(int n, const double *W0, double t, const double *p
     eval_begin_kernel<<<n_pad / tpb, tpb, 0, st>>>(n, n_pad, n_mom, W0, t, const_cast<double *>(pdir), Wt,
                                                    ws.sorted ? ws.perm : nullptr, ws.recs, ws.recs32,
                                                    ws.sorted ? ws.recs32s : nullptr, ws.groups, mom, ws.part, ws.sc,
-                                                   fp ? ws.lb_coef : nullptr, ws.S, ws.Y, ws.gf);
+                                                   fp ? ws.lb_coef : nullptr, ws.S, ws.Y, ws.gf, w0, wref0,
+                                                   hist, full_max, w0 ? ws.inc_drift : nullptr);
     return cudaGetLastError();
 }
 
@@ -782,7 +848,10 @@ const void *eval_begin_kernel_fn() { return reinterpret_cast<const void *>(eval_
 // instantiated graph (only the trial step t changes between replays).
 cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int n, const double *W0, double t,
                                 const double *pdir, double *Wt, unsigned long long *mom, Workspace &ws,
-                                bool form_p) {
+                                bool form_p, const double *w0, unsigned full_max) {
+    const unsigned long long *wref0 = w0 ? ws.inc_aux : nullptr;
+    const unsigned *hist = w0 ? ws.inc_hist : nullptr;
+    float2 *drift = w0 ? ws.inc_drift : nullptr;
     int n_pad = ((n + kChunk - 1) / kChunk) * kChunk;
     long long n_mom = (long long)n * moment_width(ws.dim);
     const int32_t *perm = ws.sorted ? ws.perm : nullptr;
@@ -794,8 +863,9 @@ cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int 
     double *pd = const_cast<double *>(pdir);
     const LbfgsCoef *coef = form_p && pdir ? ws.lb_coef : nullptr;
     const double *S = ws.S, *Y = ws.Y, *gfv = ws.gf;
-    void *args[] = {&n,      &n_pad, &n_mom, &W0,   &t,    &pd, &Wt, &perm, &recs,
-                    &recs32, &recs32s, &groups, &mom, &part, &sc, &coef, &S,  &Y,  &gfv};
+    void *args[] = {&n,      &n_pad,   &n_mom,  &W0,  &t,    &pd, &Wt,   &perm, &recs, &recs32,
+                    &recs32s, &groups, &mom, &part, &sc, &coef, &S, &Y, &gfv, &w0, &wref0, &hist, &full_max,
+                    &drift};
     cudaKernelNodeParams p{};
     p.func = reinterpret_cast<void *>(eval_begin_kernel);
     const int tpb = eval_begin_threads(n_pad, ws);
@@ -805,6 +875,51 @@ cudaError_t set_eval_begin_node(cudaGraphExec_t exec, cudaGraphNode_t node, int 
     p.kernelParams = args;
     p.extra = nullptr;
     return cudaGraphExecKernelNodeSetParams(exec, node, &p);
+}
+
+// Incremental pass, before scoring: a re-decision starts from the recorded
+// moments; a recording clears the margin histogram its scorer fills.
+__global__ void inc_prepare_kernel(const long long n_mom, unsigned long long *__restrict__ mom,
+                                   const unsigned long long *__restrict__ mom0, unsigned *__restrict__ hist,
+                                   const DevScalars *__restrict__ sc) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (sc->inc_go) {
+        for (long long e = i; e < n_mom; e += stride) mom[e] = mom0[e];
+    } else {
+        for (long long e = i; e < kIncBins; e += stride) hist[e] = 0u;
+    }
+}
+
+// Incremental pass, after rescoring: a recording keeps its moments, weights and
+// w_ref for the re-decisions that follow.
+__global__ void inc_commit_kernel(const int n, const long long n_mom, const unsigned long long *__restrict__ mom,
+                                  const double *__restrict__ w, unsigned long long *__restrict__ mom0,
+                                  double *__restrict__ w0, unsigned long long *__restrict__ aux,
+                                  DevScalars *__restrict__ sc) {
+    if (sc->inc_go) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long e = i; e < n_mom; e += (long long)gridDim.x * blockDim.x) mom0[e] = mom[e];
+    for (long long e = i; e < n; e += (long long)gridDim.x * blockDim.x) w0[e] = w[e];
+    if (i == 0) {
+        aux[0] = sc->wref_key;
+        sc->inc_valid = 1;
+    }
+}
+
+cudaError_t launch_inc_prepare(int n, unsigned long long *mom, Workspace &ws, cudaStream_t st) {
+    const long long n_mom = (long long)n * moment_width(ws.dim);
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n_mom + 255) / 256, 4 * ws.sms));
+    inc_prepare_kernel<<<blocks, 256, 0, st>>>(n_mom, mom, ws.inc_mom0, ws.inc_hist, ws.sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inc_commit(int n, const unsigned long long *mom, const double *w, Workspace &ws,
+                              cudaStream_t st) {
+    const long long n_mom = (long long)n * moment_width(ws.dim);
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n_mom + 255) / 256, 4 * ws.sms));
+    inc_commit_kernel<<<blocks, 256, 0, st>>>(n, n_mom, mom, w, ws.inc_mom0, ws.inc_w0, ws.inc_aux, ws.sc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_seed_prep(const GridDev &g, int n, const double *x, const double *A,

@@ -176,6 +176,7 @@ def test_argument_errors_before_cuda(lib):
     assert lib.apd_lbfgs_check(0, 1, None, None, None, 1, None, ctypes.byref(gp)) == capi.APD_ERR_ARG
     assert lib.apd_lbfgs_check(4, 1, None, None, None, 2, None, ctypes.byref(gp)) == capi.APD_ERR_ARG
     assert lib.apd_workspace_set_graphs(None, 1) == capi.APD_ERR_ARG
+    assert lib.apd_workspace_set_incremental(None, 1) == capi.APD_ERR_ARG
 
 
 def test_masked_argument_errors_before_cuda(lib):
