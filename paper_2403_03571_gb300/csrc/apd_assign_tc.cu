@@ -1565,8 +1565,9 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
 // excluded bound (rounded down) come from the trial-weights kernel.
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(256)
-    tc_band_kernel(const GridDev g, const int ntiles, const int n, const SeedRec32 *__restrict__ recs_nat,
+__global__ void __launch_bounds__(256, 4)
+    tc_band_kernel(const GridDev g, const int ntx, const int nty, const int tlo, const int ntiles, const int n,
+                   const SeedRec32 *__restrict__ recs_nat,
                    const float *__restrict__ centre, const int4 *__restrict__ meta, const float *__restrict__ texcl,
                    const int *__restrict__ list, const int32_t *__restrict__ lab0, const float *__restrict__ gap0,
                    const float4 *__restrict__ rec0, const float2 *__restrict__ drift,
@@ -1578,8 +1579,11 @@ __global__ void __launch_bounds__(256)
     constexpr int kRows = kPix / 32;
     const unsigned full_mask = 0xffffffffu;
     if (!*(volatile const int *)&sc->inc_go) return;  // a recording pass: the scorer did it all
-    __shared__ unsigned s_full;  // this block's full re-decisions
-    if (threadIdx.x == 0) s_full = 0u;
+    __shared__ unsigned s_full, s_done;  // this block's full re-decisions; its warps done
+    if (threadIdx.x == 0) {
+        s_full = 0u;
+        s_done = 0u;
+    }
     const int lane = threadIdx.x & 31;
     float wrh, wrl;
     block_wref(sc, wrh, wrl);  // (its barrier also orders the counters' clearing)
@@ -1587,22 +1591,45 @@ __global__ void __launch_bounds__(256)
     const float bandD = sc->band_D, drift_hi = sc->drift_hi;
     const long long nwarps = (long long)ntiles * kRows;
     const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
-    // one warp per 32 pixels (a row group) of a tile, grid-strided
-    for (long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nwarps; wi += wstride) {
+    // row group wi -> this lane's pixel (index j, -1 outside the grid or window)
+    auto locate = [&](long long wi, int (&kk)[3], int (&lk)[3]) -> long long {
         const int t = (int)(wi / kRows), r = (int)(wi % kRows);
-        const int4 mt = meta[t];
+        int kb[3];
+        tile_origin<D>(t, ntx, nty, tlo, kb);
         const int lt = r * 32 + lane;
-        const int lk[3] = {lt % G::TX, (lt / G::TX) % G::TY, lt / (G::TX * G::TY)};
-        const int kk[3] = {mt.x + lk[0], mt.y + lk[1], D == 3 ? mt.z + lk[2] : 0};
+        lk[0] = lt % G::TX;
+        lk[1] = (lt / G::TX) % G::TY;
+        lk[2] = lt / (G::TX * G::TY);
+        kk[0] = kb[0] + lk[0];
+        kk[1] = kb[1] + lk[1];
+        kk[2] = D == 3 ? kb[2] + lk[2] : 0;
         const int klast = D == 3 ? kk[2] : kk[1];
         const bool valid = kk[0] < g.res[0] && kk[1] < g.res[1] && (D == 2 || kk[2] < g.res[2]) &&
                            klast >= win_lo(g) && klast < win_hi(g);
-        long long j = 0;
-        bool cand = false;
-        if (valid) {
-            j = (long long)kk[0] + (long long)g.res[0] * ((long long)kk[1] + (long long)g.res[1] * (long long)kk[2]);
-            cand = !(gap0[j] > bandD);
+        return valid ? (long long)kk[0] + (long long)g.res[0] * ((long long)kk[1] + (long long)g.res[1] * (long long)kk[2])
+                     : -1ll;
+    };
+    // one warp per 32 pixels (a row group) of a tile, grid-strided; the next row
+    // group's margin is loaded while this one is settled
+    long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    float g_next = finf;
+    if (wi < nwarps) {
+        int kk[3], lk[3];
+        const long long j = locate(wi, kk, lk);
+        if (j >= 0) g_next = gap0[j];
+    }
+    for (; wi < nwarps; wi += wstride) {
+        const float g_this = g_next;
+        if (wi + wstride < nwarps) {
+            int kn[3], ln[3];
+            const long long jn = locate(wi + wstride, kn, ln);
+            g_next = jn >= 0 ? gap0[jn] : finf;
         }
+        const int t = (int)(wi / kRows);
+        int kk[3], lk[3];
+        const long long jl = locate(wi, kk, lk);
+        const long long j = jl >= 0 ? jl : 0;
+        bool cand = jl >= 0 && !(g_this > bandD);
         if (!__any_sync(full_mask, cand)) continue;
         int a0 = -1, nl = -1, hint = -1, b = -1;
         bool full = false, pair = false, flag = false;
@@ -1657,7 +1684,7 @@ __global__ void __launch_bounds__(256)
                 }
             }
             if (fm) {  // full re-decisions over the tile's list, one pixel at a time
-                const int cnt = mt.w;
+                const int cnt = meta[t].w;
                 const int ns = (cnt + kN - 1) / kN;
                 int lv[kMaxSteps];
 #pragma unroll
@@ -1754,9 +1781,14 @@ __global__ void __launch_bounds__(256)
             todo &= ~grp;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_full) atomicAdd(&sc->band_count, s_full);
+    // the block's count, added by its last warp to finish (no barrier: a warp that
+    // is done does not wait for the others)
+    if (lane == 0) {
+        __threadfence_block();
+        if (atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1u) {
+            const unsigned f = atomicAdd(&s_full, 0u);
+            if (f) atomicAdd(&sc->band_count, f);
+        }
     }
 }
 
@@ -1775,7 +1807,7 @@ cudaError_t launch_band_t(const GridDev &g, int n, const double *w, Workspace &w
     const long long warps = ntl * (G::TX * G::TY * G::TZ / 32);
     const long long blocks = std::max<long long>(1, std::min<long long>((warps * 32 + 255) / 256, (long long)ws.sms * 8));
     tc_band_kernel<D><<<(unsigned)blocks, 256, 0, st>>>(
-        g, ntiles, n, ws.recs32, ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.inc_labels, ws.inc_gap,
+        g, ntx, nty, tlo, ntiles, n, ws.recs32, ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.inc_labels, ws.inc_gap,
         ws.inc_rec, ws.inc_drift, ws.moments, ws.flags, ws.flag_gi, ws.sc);
     return cudaGetLastError();
 }
