@@ -1572,7 +1572,7 @@ __global__ void __launch_bounds__(256, 4)
                    const int *__restrict__ list, const int32_t *__restrict__ lab0, const float *__restrict__ gap0,
                    const float4 *__restrict__ rec0, const float2 *__restrict__ drift,
                    unsigned long long *__restrict__ gmom, uint32_t *__restrict__ flags,
-                   int32_t *__restrict__ flag_gi, DevScalars *__restrict__ sc) {
+                   int32_t *__restrict__ flag_gi, DevScalars *__restrict__ sc, const int wide) {
     using G = TcGeom<D>;
     constexpr int KM = moment_width(D);
     constexpr int kPix = G::TX * G::TY * G::TZ;
@@ -1762,8 +1762,13 @@ __global__ void __launch_bounds__(256, 4)
             unsigned long long word = 0ull;
             int e = 0;
             auto fold = [&](unsigned long long x) {
+                if (!wide) {
+                    // u < 2^13: every product is below 2^26 and 32 of them below 2^31
+                    x = __reduce_add_sync(full_mask, (unsigned)x);
+                } else {
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(full_mask, x, off);
+                    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(full_mask, x, off);
+                }
                 if (lane == e) word = x;
                 ++e;
             };
@@ -1802,13 +1807,20 @@ cudaError_t launch_band_t(const GridDev &g, int n, const double *w, Workspace &w
     if (ntl > ws.tc_tile_cap || !ws.inc_labels || !ws.inc_gap || !ws.inc_rec || !ws.inc_drift)
         return cudaErrorInvalidValue;
     const int ntiles = (int)ntl;
-    // one warp per 32 pixels of a tile, grid-strided: a few resident blocks per SM
-    // (a recording pass launches it for nothing)
+    // one warp per 32 pixels of a tile, grid-strided over as many blocks as stay
+    // resident together (a recording pass launches it for nothing)
+    int &bps = ws.band_bps[D == 3 ? 1 : 0];
+    if (!bps) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tc_band_kernel<D>, 256, 0) != cudaSuccess || bps < 1)
+            bps = 2;
+        cudaGetLastError();
+    }
     const long long warps = ntl * (G::TX * G::TY * G::TZ / 32);
-    const long long blocks = std::max<long long>(1, std::min<long long>((warps * 32 + 255) / 256, (long long)ws.sms * 8));
+    const long long blocks = std::max<long long>(1, std::min<long long>((warps * 32 + 255) / 256, (long long)ws.sms * bps));
+    const int wide = (g.res[0] > 4096 || g.res[1] > 4096 || (D == 3 && g.res[2] > 4096)) ? 1 : 0;
     tc_band_kernel<D><<<(unsigned)blocks, 256, 0, st>>>(
         g, ntx, nty, tlo, ntiles, n, ws.recs32, ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.inc_labels, ws.inc_gap,
-        ws.inc_rec, ws.inc_drift, ws.moments, ws.flags, ws.flag_gi, ws.sc);
+        ws.inc_rec, ws.inc_drift, ws.moments, ws.flags, ws.flag_gi, ws.sc, wide);
     return cudaGetLastError();
 }
 

@@ -193,6 +193,7 @@ struct Workspace {
     float4 *inc_rec = nullptr;          // [max_j] runner-up and margins of the recorded pass
     unsigned *inc_hist = nullptr;       // [kIncBins] recorded pixels by their g3 margin (see kIncBins)
     float2 *inc_drift = nullptr;        // [max_n] w - w0 per seed as a float interval (lo, hi)
+    int band_bps[2] = {0, 0};           // resident blocks per SM of the re-decision kernel (2D, 3D)
     bool inc_auto = false;              // set while an incremental pass is queued (kernels test sc->inc_go)
     unsigned long long *inc_mom0 = nullptr;  // [max_n * K] moments of the recorded pass
     double *inc_w0 = nullptr;           // [max_n] weights of the recorded pass
