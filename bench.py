@@ -68,8 +68,8 @@ def parse():
                     help="chosen form: the coarse solves of a Lloyd run continue one L-BFGS history (1) "
                          "or start afresh (0)")
     ap.add_argument("--incremental", type=int, default=1,
-                    help="weight solves re-decide only the pixels within the weights' drift of their "
-                         "recorded cost gap (1) or score every pixel in every evaluation (0)")
+                    help="incremental evaluations in weight solves: 1 on grids of at least 2^20 pixels "
+                         "(default), 2 on every grid, 0 every evaluation scores every pixel")
     ap.add_argument("--assign-res", type=int, default=0,
                     help="--mode assign: grid resolution per axis in place of the workload's")
     ap.add_argument("--assign-prune", action="store_true",
@@ -561,7 +561,7 @@ def run_ours(args):
     ctx["x_out"] = torch.empty_like(ctx["x0"])
     ctx["w_out"] = torch.empty_like(ctx["w0"])
     ctx["ws"] = capi.Workspace(dim, n, J)
-    ctx["ws"].set_incremental(bool(args.incremental))
+    ctx["ws"].set_incremental(int(args.incremental))
     if world > 1:
         from paper_2403_03571_gb300 import shard
         shard.shard_workspace(ctx["ws"], rank, world)

@@ -142,8 +142,10 @@ int apd_workspace_set_graphs(apd_workspace *ws, int32_t enable);
  * changes.  The device chooses each pass's kind from the drift: it records
  * afresh when more than 8 % of the pixels have a recorded g3 within
  * max D - min D.  Labels and moments are the same as with full passes.
- * enable = 0 makes every pass a full one.  Returns APD_ERR_ARG for a null
- * workspace. */
+ * enable: 0 every pass a full one; 1 (default) incremental passes on grids of
+ * at least 2^20 pixels (below that a full pass costs about as much as the
+ * incremental pass's extra launches); 2 incremental passes on every grid.
+ * Returns APD_ERR_ARG for a null workspace or another enable value. */
 int apd_workspace_set_incremental(apd_workspace *ws, int32_t enable);
 
 /* Poll limit of the bounded shared-memory barrier waits of the FP32 scoring

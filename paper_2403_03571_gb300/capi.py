@@ -306,10 +306,10 @@ class Workspace:
         """Replay the weight solves' evaluations from captured CUDA graphs (default on)."""
         _check(load().apd_workspace_set_graphs(self.handle, int(bool(enable))), "apd_workspace_set_graphs")
 
-    def set_incremental(self, enable: bool = True):
-        """Re-decide only the pixels within the weights' drift of their recorded
-        cost gap in the weight solves' evaluations (default on)."""
-        _check(load().apd_workspace_set_incremental(self.handle, int(bool(enable))),
+    def set_incremental(self, mode=1):
+        """Incremental evaluations in weight solves: 0 (or False) off, 1 (or True,
+        the default) on grids of at least 2^20 pixels, 2 on every grid."""
+        _check(load().apd_workspace_set_incremental(self.handle, int(mode)),
                "apd_workspace_set_incremental")
 
     def profile(self, enable: bool = True):

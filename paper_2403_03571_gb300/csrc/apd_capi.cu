@@ -155,6 +155,9 @@ bool use_tensor_cores(const GridDev &g, apd_precision prec, Workspace &ws, bool 
 // need a full one (see tc_band_kernel).  The first pass of a solve records.
 constexpr int kIncNone = 0, kIncAuto = 1;
 constexpr double kIncFullMax = 0.08;
+// Below this many pixels a full pass costs about as much as the three extra
+// launches of an incremental one (apd_workspace_set_incremental mode 1).
+constexpr long long kIncMinPixels = 1ll << 20;
 
 // The buffers of the incremental passes, allocated on first use (never inside a
 // graph capture).
@@ -461,7 +464,8 @@ struct Solver {
     int eval(const double *Wp, double *gf_out, const double *pdir, double &f, double &dphi,
              double &err, const TrialStep *step = nullptr) {
         inc_mode = kIncNone;
-        if (ws.incremental && ws.prune && ws.shard_world <= 1 && prec != APD_FP32) {
+        if (ws.incremental && ws.prune && ws.shard_world <= 1 && prec != APD_FP32 &&
+            (ws.incremental > 1 || win_pixels(g) >= kIncMinPixels)) {
             APD_TRY(inc_alloc(ws));  // never inside a graph capture
             inc_mode = kIncAuto;
         }
@@ -1087,7 +1091,8 @@ int apd_lbfgs_check(int32_t n, int32_t hist, const double *S, const double *Y, c
 
 int apd_workspace_set_incremental(apd_workspace *ws, int32_t enable) {
     if (!ws) return APD_ERR_ARG;
-    ws->w.incremental = enable != 0;
+    if (enable < 0 || enable > 2) return APD_ERR_ARG;
+    ws->w.incremental = enable;
     return APD_OK;
 }
 

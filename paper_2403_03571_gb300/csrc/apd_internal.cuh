@@ -199,7 +199,7 @@ struct Workspace {
     double *inc_w0 = nullptr;           // [max_n] weights of the recorded pass
     unsigned long long *inc_aux = nullptr;  // [2] ordered key of the recorded pass's w_ref, spare
     float *rec_gap = nullptr;           // set while a recording pass is queued (the scorer's gap output)
-    bool incremental = true;            // apd_workspace_set_incremental
+    int incremental = 1;                // apd_workspace_set_incremental mode (0 off, 1 large grids, 2 all)
     bool inc_recorded = false;          // the last queued pass recorded its state
     double *rho = nullptr;              // [hist_cap]
     // a second L-BFGS history (pairs, Gram entries, 1 / s.y) continued by the coarse
