@@ -81,6 +81,7 @@ constexpr int kXfWarps = 2;
 constexpr int kThreads = (kEpiWarps + 1 + kXfWarps) * 32;  // 608
 constexpr int kListCap = 128;                // candidate seeds stored per tile
 constexpr int kMaxSteps = kListCap / kN;     // steps of a pruned tile (B operands stored per tile)
+constexpr int kBandChunk = 2048;             // pixels per block step of the re-decision kernel
 constexpr int kAhead = 2;                    // pruned form: bulk copies issued ahead of the MMAs
 constexpr int kBMax = kN * kK * 4;           // bytes of one stored B operand (TF32; BF16 uses half)
 
@@ -1565,261 +1566,274 @@ cudaError_t launch_tc_t(const GridDev &g, int n, Workspace &ws, int32_t *labels,
 // excluded bound (rounded down) come from the trial-weights kernel.
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(256, 4)
-    tc_band_kernel(const GridDev g, const int ntx, const int nty, const int tlo, const int ntiles, const int n,
-                   const SeedRec32 *__restrict__ recs_nat,
-                   const float *__restrict__ centre, const int4 *__restrict__ meta, const float *__restrict__ texcl,
-                   const int *__restrict__ list, const int32_t *__restrict__ lab0, const float *__restrict__ gap0,
+__global__ void __launch_bounds__(256)
+    tc_band_kernel(const GridDev g, const int ntx, const int nty, const int tlo, const int n,
+                   const SeedRec32 *__restrict__ recs_nat, const float *__restrict__ centre,
+                   const int4 *__restrict__ meta, const float *__restrict__ texcl, const int *__restrict__ list,
+                   const int32_t *__restrict__ lab0, const float *__restrict__ gap0,
                    const float4 *__restrict__ rec0, const float2 *__restrict__ drift,
                    unsigned long long *__restrict__ gmom, uint32_t *__restrict__ flags,
                    int32_t *__restrict__ flag_gi, DevScalars *__restrict__ sc, const int wide) {
     using G = TcGeom<D>;
     constexpr int KM = moment_width(D);
-    constexpr int kPix = G::TX * G::TY * G::TZ;
-    constexpr int kRows = kPix / 32;
+    constexpr int kPer = kBandChunk / 256;  // margins per thread and chunk
     const unsigned full_mask = 0xffffffffu;
     if (!*(volatile const int *)&sc->inc_go) return;  // a recording pass: the scorer did it all
-    __shared__ unsigned s_full, s_done;  // this block's full re-decisions; its warps done
-    if (threadIdx.x == 0) {
-        s_full = 0u;
-        s_done = 0u;
-    }
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t s_q[kBandChunk];  // the chunk's candidate pixels ...
+    __shared__ uint32_t s_f[kBandChunk];  // ... and those left for a full re-decision
+    __shared__ unsigned s_nq, s_nf, s_full;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_full = 0u;
     float wrh, wrl;
-    block_wref(sc, wrh, wrl);  // (its barrier also orders the counters' clearing)
+    block_wref(sc, wrh, wrl);  // (its barrier also orders the counter's clearing)
     const float finf = __int_as_float(0x7f800000);
     const float bandD = sc->band_D, drift_hi = sc->drift_hi;
-    const long long nwarps = (long long)ntiles * kRows;
-    const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
-    // row group wi -> this lane's pixel (index j, -1 outside the grid or window)
-    auto locate = [&](long long wi, int (&kk)[3], int (&lk)[3]) -> long long {
-        const int t = (int)(wi / kRows), r = (int)(wi % kRows);
-        int kb[3];
-        tile_origin<D>(t, ntx, nty, tlo, kb);
-        const int lt = r * 32 + lane;
-        lk[0] = lt % G::TX;
-        lk[1] = (lt / G::TX) % G::TY;
-        lk[2] = lt / (G::TX * G::TY);
-        kk[0] = kb[0] + lk[0];
-        kk[1] = kb[1] + lk[1];
-        kk[2] = D == 3 ? kb[2] + lk[2] : 0;
-        const int klast = D == 3 ? kk[2] : kk[1];
-        const bool valid = kk[0] < g.res[0] && kk[1] < g.res[1] && (D == 2 || kk[2] < g.res[2]) &&
-                           klast >= win_lo(g) && klast < win_hi(g);
-        return valid ? (long long)kk[0] + (long long)g.res[0] * ((long long)kk[1] + (long long)g.res[1] * (long long)kk[2])
-                     : -1ll;
-    };
-    // one warp per 32 pixels (a row group) of a tile, grid-strided; the next row
-    // group's margin is loaded while this one is settled
-    long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    float g_next = finf;
-    if (wi < nwarps) {
-        int kk[3], lk[3];
-        const long long j = locate(wi, kk, lk);
-        if (j >= 0) g_next = gap0[j];
-    }
-    for (; wi < nwarps; wi += wstride) {
-        const float g_this = g_next;
-        if (wi + wstride < nwarps) {
-            int kn[3], ln[3];
-            const long long jn = locate(wi + wstride, kn, ln);
-            g_next = jn >= 0 ? gap0[jn] : finf;
-        }
-        const int t = (int)(wi / kRows);
-        int kk[3], lk[3];
-        const long long jl = locate(wi, kk, lk);
-        const long long j = jl >= 0 ? jl : 0;
-        bool cand = jl >= 0 && !(g_this > bandD);
-        if (!__any_sync(full_mask, cand)) continue;
-        int a0 = -1, nl = -1, hint = -1, b = -1;
-        bool full = false, pair = false, flag = false;
-        if (cand) {
-            a0 = lab0[j];
-            if (a0 < 0 || a0 >= n) {  // no valid record (its pass failed): leave the pixel alone
-                atomicOr(&sc->status, ST_BAD_LABEL);
-                cand = false;
-                a0 = -1;
-            }
-        }
-        if (cand) {
-            const float4 rc = rec0[j];
-            b = __float_as_int(rc.w);
-            const float2 da = drift[a0];
-            // every seed but a and b: C_k - C_a >= g3 - (Delta_k - Delta_a) >= g3 - (max Delta - Delta_a)
-            const float thr = __fsub_ru(drift_hi, da.x);
-            if (!(rc.z > thr)) {
-                full = true;
-            } else if (b < 0 || b >= n) {
-                nl = a0;
-            } else {
-                const float2 db = drift[b];
-                const float lo = __fsub_rd(rc.x, __fsub_ru(db.y, da.x));  // C_b - C_a, rounded outwards
-                const float hi = __fsub_ru(rc.y, __fsub_rd(db.x, da.y));
-                if (lo > 0.f) nl = a0;
-                else if (hi < 0.f) nl = b;
-                else pair = true;
-            }
-        }
-        const unsigned fm = __ballot_sync(full_mask, full);
-        if (fm || __any_sync(full_mask, pair)) {
-            const int tdim[3] = {G::TX, G::TY, G::TZ};
-            float ypx[3] = {0.f, 0.f, 0.f};  // this lane's pixel relative to the tile centre
+    const long long plane = (long long)g.res[0] * (D == 3 ? g.res[1] : 1);
+    const long long jlo = (long long)win_lo(g) * plane, jhi = (long long)win_hi(g) * plane;
+    const int tdim[3] = {G::TX, G::TY, G::TZ};
+    // pixel j -> grid coordinates, its tile and its position relative to the tile centre
+    auto place = [&](long long j, int (&kk)[3], int &t, float (&yp)[3]) {
+        kk[0] = (int)(j % g.res[0]);
+        const long long r = j / g.res[0];
+        kk[1] = D == 3 ? (int)(r % g.res[1]) : (int)r;
+        kk[2] = D == 3 ? (int)(r / g.res[1]) : 0;
+        const int tx = kk[0] / G::TX, ty = kk[1] / G::TY, tz = D == 3 ? kk[2] / G::TZ : 0;
+        t = D == 3 ? tx + ntx * (ty + nty * (tz - tlo)) : tx + ntx * (ty - tlo);
+        const int tc[3] = {tx, ty, tz};
 #pragma unroll
-            for (int d = 0; d < D; ++d) ypx[d] = ((float)(lk[d] - tdim[d] / 2) + 0.5f) * g.h32[d];
+        for (int d = 0; d < 3; ++d)
+            yp[d] = d < D ? ((float)(kk[d] - tc[d] * tdim[d] - tdim[d] / 2) + 0.5f) * g.h32[d] : 0.f;
+    };
+    for (long long base = jlo + (long long)blockIdx.x * kBandChunk; base < jhi;
+         base += (long long)gridDim.x * kBandChunk) {
+        if (tid == 0) {
+            s_nq = 0u;
+            s_nf = 0u;
+        }
+        __syncthreads();
+        // 1. the chunk's margins (coalesced, kPer loads in flight per thread) -> candidates
+        float gv[kPer];
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+            const long long j = base + e * 256 + tid;
+            gv[e] = j < jhi ? gap0[j] : finf;
+        }
+#pragma unroll
+        for (int e = 0; e < kPer; ++e)
+            if (!(gv[e] > bandD)) s_q[atomicAdd(&s_nq, 1u)] = (uint32_t)(base + e * 256 + tid);
+        __syncthreads();
+        const unsigned nq = s_nq;
+        // 2. one thread per candidate: keep a, or decide between a and b
+        for (unsigned i0 = 0; i0 < nq; i0 += 256) {
+            const unsigned i = i0 + (unsigned)tid;
+            const bool act = i < nq;
+            long long j = 0;
+            int kk[3] = {0, 0, 0}, t = 0;
+            float yp[3] = {0.f, 0.f, 0.f};
+            int a0 = -1, nl = -1, b = -1, hint = -1;
+            bool flag = false;
+            if (act) {
+                j = s_q[i];
+                a0 = lab0[j];
+                if (a0 < 0 || a0 >= n) {  // no valid record (its pass failed): leave the pixel alone
+                    atomicOr(&sc->status, ST_BAD_LABEL);
+                    a0 = -1;
+                }
+            }
+            if (a0 >= 0) {
+                const float4 rc = rec0[j];
+                b = __float_as_int(rc.w);
+                const float2 da = drift[a0];
+                // every seed but a and b: C_k - C_a >= g3 - (Delta_k - Delta_a) >= g3 - (max Delta - Delta_a)
+                const float thr = __fsub_ru(drift_hi, da.x);
+                if (!(rc.z > thr)) {
+                    s_f[atomicAdd(&s_nf, 1u)] = (uint32_t)j;  // a full re-decision
+                } else if (b < 0 || b >= n) {
+                    nl = a0;
+                } else {
+                    const float2 db = drift[b];
+                    const float lo = __fsub_rd(rc.x, __fsub_ru(db.y, da.x));  // C_b - C_a, rounded outwards
+                    const float hi = __fsub_ru(rc.y, __fsub_rd(db.x, da.y));
+                    if (lo > 0.f) {
+                        nl = a0;
+                    } else if (hi < 0.f) {
+                        nl = b;
+                    } else {  // a against b in FP32 direct form
+                        place(j, kk, t, yp);
+                        float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int d = 0; d < D; ++d) {
+                            ch[d] = centre[(size_t)t * 6 + d];
+                            cl[d] = centre[(size_t)t * 6 + 3 + d];
+                        }
+                        float ca, ea, cb, eb;
+                        cost32_bound_rel<D>(recs_nat[a0], ch, cl, yp, wrh, wrl, ca, ea);
+                        cost32_bound_rel<D>(recs_nat[b], ch, cl, yp, wrh, wrl, cb, eb);
+                        if (__fadd_ru(ca, ea) < __fsub_rd(cb, eb)) nl = a0;
+                        else if (__fadd_ru(cb, eb) < __fsub_rd(ca, ea)) nl = b;
+                        else {
+                            flag = true;
+                            hint = a0;
+                        }
+                    }
+                }
+            }
+            // near ties to the FP64 rescoring (which moves their words from a's cell)
+            const unsigned qm = __ballot_sync(full_mask, flag);
+            if (qm) {
+                unsigned qb = 0u;
+                if (lane == __ffs(qm) - 1) qb = atomicAdd(&sc->flag_count, (unsigned)__popc(qm));
+                qb = __shfl_sync(full_mask, qb, __ffs(qm) - 1);
+                if (flag) {
+                    const unsigned slot = qb + (unsigned)__popc(qm & ((1u << lane) - 1u));
+                    flags[slot] = (uint32_t)j;
+                    if (flag_gi) flag_gi[slot] = hint;
+                }
+            }
+            // moved pixels: their words leave a's cell for the new one, summed per
+            // pair of cells across the warp (neighbouring candidates share pairs)
+            const bool moved = nl >= 0 && nl != a0;
+            if (moved) place(j, kk, t, yp);
+            unsigned todo = __ballot_sync(full_mask, moved);
+            while (todo) {
+                const int leader = __ffs(todo) - 1;
+                const int A0 = __shfl_sync(full_mask, a0, leader), NL = __shfl_sync(full_mask, nl, leader);
+                const bool mine = moved && a0 == A0 && nl == NL;
+                const unsigned grp = __ballot_sync(full_mask, mine);
+                unsigned long long u[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+                for (int d = 0; d < D; ++d) u[d] = mine ? 2ull * (unsigned long long)kk[d] + 1ull : 0ull;
+                unsigned long long word = 0ull;
+                int e = 0;
+                auto fold = [&](unsigned long long x) {
+                    if (!wide) {
+                        // u < 2^13: every product is below 2^26 and 32 of them below 2^31
+                        x = __reduce_add_sync(full_mask, (unsigned)x);
+                    } else {
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(full_mask, x, off);
+                    }
+                    if (lane == e) word = x;
+                    ++e;
+                };
+                fold(mine ? 1ull : 0ull);
+#pragma unroll
+                for (int d = 0; d < D; ++d) fold(u[d]);
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+#pragma unroll
+                    for (int d2 = d; d2 < D; ++d2) fold(u[d] * u[d2]);
+                if (lane < KM && word) {
+                    atomicAdd(&gmom[(size_t)NL * KM + lane], word);
+                    atomicAdd(&gmom[(size_t)A0 * KM + lane], 0ull - word);
+                }
+                todo &= ~grp;
+            }
+        }
+        __syncthreads();
+        // 3. full re-decisions, one warp per pixel: lanes over its tile's recorded
+        // candidate list, against the excluded seeds' bound moved by the drift
+        const unsigned nf = s_nf;
+        if (tid == 0) s_full += nf;
+        for (unsigned f = (unsigned)wid; f < nf; f += 8u) {
+            const long long j = s_f[f];
+            int kk[3], t;
+            float yp[3];
+            place(j, kk, t, yp);
+            const int a0 = lab0[j];
+            const int cnt = meta[t].w;
+            const int ns = (cnt + kN - 1) / kN;
             float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 ch[d] = centre[(size_t)t * 6 + d];
                 cl[d] = centre[(size_t)t * 6 + 3 + d];
             }
-            if (pair) {  // a against b in FP32 direct form, each lane its own pixel
-                float ca, ea, cb, eb;
-                cost32_bound_rel<D>(recs_nat[a0], ch, cl, ypx, wrh, wrl, ca, ea);
-                cost32_bound_rel<D>(recs_nat[b], ch, cl, ypx, wrh, wrl, cb, eb);
-                if (__fadd_ru(ca, ea) < __fsub_rd(cb, eb)) nl = a0;
-                else if (__fadd_ru(cb, eb) < __fsub_rd(ca, ea)) nl = b;
-                else {
-                    flag = true;
-                    hint = a0;
-                }
-            }
-            if (fm) {  // full re-decisions over the tile's list, one pixel at a time
-                const int cnt = meta[t].w;
-                const int ns = (cnt + kN - 1) / kN;
-                int lv[kMaxSteps];
+            const float t0 = texcl[t];
+            const float tex = t0 < finf ? __fadd_rd(t0, sc->band_shift) : finf;
+            float cv[kMaxSteps], ev[kMaxSteps];
+            int lv[kMaxSteps];
+            float ub = finf;
+            int us = 0x7fffffff;
 #pragma unroll
-                for (int k = 0; k < kMaxSteps; ++k)
-                    lv[k] = k * kN + lane < cnt ? list[(size_t)t * kListCap + k * kN + lane] : -1;
-                const float t0 = texcl[t];
-                const float tex = t0 < finf ? __fadd_rd(t0, sc->band_shift) : finf;
-                if (lane == 0) atomicAdd(&s_full, (unsigned)__popc(fm));
-                unsigned pending = fm;
-                while (pending) {
-                    const int p = __ffs(pending) - 1;
-                    pending &= pending - 1u;
-                    float yp[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int d = 0; d < D; ++d) yp[d] = __shfl_sync(full_mask, ypx[d], p);
-                    float cv[kMaxSteps], ev[kMaxSteps];
-                    float ub = finf;
-                    int us = 0x7fffffff;
-#pragma unroll
-                    for (int k = 0; k < kMaxSteps; ++k) {
-                        cv[k] = finf;
-                        ev[k] = 0.f;
-                        if (k < ns && lv[k] >= 0) {
-                            cost32_bound_rel<D>(recs_nat[lv[k]], ch, cl, yp, wrh, wrl, cv[k], ev[k]);
-                            const float u1 = __fadd_ru(cv[k], ev[k]);
-                            if (u1 < ub || (u1 == ub && lv[k] < us)) {
-                                ub = u1;
-                                us = lv[k];
-                            }
-                        }
-                    }
-                    const unsigned kub = okey(ub);
-                    const unsigned kmin = __reduce_min_sync(full_mask, kub);
-                    const int smin = (int)__reduce_min_sync(full_mask, kub == kmin ? (unsigned)us : 0x7fffffffu);
-                    const float Ub = okey_inv(kmin);
-                    bool other = false;
-#pragma unroll
-                    for (int k = 0; k < kMaxSteps; ++k)
-                        if (k < ns && lv[k] >= 0 && lv[k] != smin && !(__fsub_rd(cv[k], ev[k]) > Ub)) other = true;
-                    const bool ok2 = !__any_sync(full_mask, other) && Ub < tex && smin < n;
-                    if (lane == p) {
-                        if (ok2) {
-                            nl = smin;
-                        } else {
-                            flag = true;
-                            hint = smin < n ? smin : -1;
-                        }
+            for (int k = 0; k < kMaxSteps; ++k) {
+                lv[k] = k * kN + lane < cnt ? list[(size_t)t * kListCap + k * kN + lane] : -1;
+                cv[k] = finf;
+                ev[k] = 0.f;
+                if (k < ns && lv[k] >= 0) {
+                    cost32_bound_rel<D>(recs_nat[lv[k]], ch, cl, yp, wrh, wrl, cv[k], ev[k]);
+                    const float u1 = __fadd_ru(cv[k], ev[k]);
+                    if (u1 < ub || (u1 == ub && lv[k] < us)) {
+                        ub = u1;
+                        us = lv[k];
                     }
                 }
             }
-        }
-        // near ties to the FP64 rescoring (which moves their words from a's cell)
-        const unsigned qm = __ballot_sync(full_mask, flag);
-        if (qm) {
-            unsigned base = 0u;
-            if (lane == __ffs(qm) - 1) base = atomicAdd(&sc->flag_count, (unsigned)__popc(qm));
-            base = __shfl_sync(full_mask, base, __ffs(qm) - 1);
-            if (flag) {
-                const unsigned slot = base + (unsigned)__popc(qm & ((1u << lane) - 1u));
-                flags[slot] = (uint32_t)j;
-                if (flag_gi) flag_gi[slot] = hint;
-            }
-        }
-        // moved pixels: their words leave a's cell for the new one, summed per pair of cells
-        const bool moved = nl >= 0 && nl != a0;
-        unsigned todo = __ballot_sync(full_mask, moved);
-        while (todo) {
-            const int leader = __ffs(todo) - 1;
-            const int A0 = __shfl_sync(full_mask, a0, leader), NL = __shfl_sync(full_mask, nl, leader);
-            const bool mine = moved && a0 == A0 && nl == NL;
-            const unsigned grp = __ballot_sync(full_mask, mine);
-            unsigned long long u[3] = {0ull, 0ull, 0ull};
+            const unsigned kub = okey(ub);
+            const unsigned kmin = __reduce_min_sync(full_mask, kub);
+            const int smin = (int)__reduce_min_sync(full_mask, kub == kmin ? (unsigned)us : 0x7fffffffu);
+            const float Ub = okey_inv(kmin);
+            bool other = false;
 #pragma unroll
-            for (int d = 0; d < D; ++d) u[d] = mine ? 2ull * (unsigned long long)kk[d] + 1ull : 0ull;
-            unsigned long long word = 0ull;
-            int e = 0;
-            auto fold = [&](unsigned long long x) {
-                if (!wide) {
-                    // u < 2^13: every product is below 2^26 and 32 of them below 2^31
-                    x = __reduce_add_sync(full_mask, (unsigned)x);
-                } else {
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(full_mask, x, off);
+            for (int k = 0; k < kMaxSteps; ++k)
+                if (k < ns && lv[k] >= 0 && lv[k] != smin && !(__fsub_rd(cv[k], ev[k]) > Ub)) other = true;
+            const bool ok2 = !__any_sync(full_mask, other) && Ub < tex && smin < n;
+            if (!ok2) {
+                if (lane == 0) {
+                    const unsigned slot = atomicAdd(&sc->flag_count, 1u);
+                    flags[slot] = (uint32_t)j;
+                    if (flag_gi) flag_gi[slot] = smin < n ? smin : -1;
                 }
-                if (lane == e) word = x;
-                ++e;
-            };
-            fold(mine ? 1ull : 0ull);
+            } else if (smin != a0 && lane < KM) {
+                // this pixel's words from a's cell to smin's
+                unsigned long long u[3] = {0ull, 0ull, 0ull};
 #pragma unroll
-            for (int d = 0; d < D; ++d) fold(u[d]);
+                for (int d = 0; d < D; ++d) u[d] = 2ull * (unsigned long long)kk[d] + 1ull;
+                unsigned long long word = 0ull;
+                int e = 0;
+                auto put = [&](unsigned long long x) {
+                    if (lane == e) word = x;
+                    ++e;
+                };
+                put(1ull);
 #pragma unroll
-            for (int d = 0; d < D; ++d)
+                for (int d = 0; d < D; ++d) put(u[d]);
 #pragma unroll
-                for (int d2 = d; d2 < D; ++d2) fold(u[d] * u[d2]);
-            if (lane < KM && word) {
-                atomicAdd(&gmom[(size_t)NL * KM + lane], word);
-                atomicAdd(&gmom[(size_t)A0 * KM + lane], 0ull - word);
+                for (int d = 0; d < D; ++d)
+#pragma unroll
+                    for (int d2 = d; d2 < D; ++d2) put(u[d] * u[d2]);
+                atomicAdd(&gmom[(size_t)smin * KM + lane], word);
+                atomicAdd(&gmom[(size_t)a0 * KM + lane], 0ull - word);
             }
-            todo &= ~grp;
         }
+        __syncthreads();  // the queues are refilled by the next chunk
     }
-    // the block's count, added by its last warp to finish (no barrier: a warp that
-    // is done does not wait for the others)
-    if (lane == 0) {
-        __threadfence_block();
-        if (atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1u) {
-            const unsigned f = atomicAdd(&s_full, 0u);
-            if (f) atomicAdd(&sc->band_count, f);
-        }
-    }
+    if (tid == 0 && s_full) atomicAdd(&sc->band_count, s_full);
 }
 
 template <int D>
 cudaError_t launch_band_t(const GridDev &g, int n, const double *w, Workspace &ws, cudaStream_t st) {
-    using G = TcGeom<D>;
     (void)w;
     int ntx = 0, nty = 0, tlo = 0;
     long long ntl = 0;
     tile_grid<D>(g, ntx, nty, tlo, ntl);
     if (ntl > ws.tc_tile_cap || !ws.inc_labels || !ws.inc_gap || !ws.inc_rec || !ws.inc_drift)
         return cudaErrorInvalidValue;
-    const int ntiles = (int)ntl;
-    // one warp per 32 pixels of a tile, grid-strided over as many blocks as stay
-    // resident together (a recording pass launches it for nothing)
+    // chunks of kBandChunk pixels, grid-strided over as many blocks as stay resident
+    // together (a recording pass launches it for nothing)
     int &bps = ws.band_bps[D == 3 ? 1 : 0];
     if (!bps) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tc_band_kernel<D>, 256, 0) != cudaSuccess || bps < 1)
             bps = 2;
         cudaGetLastError();
     }
-    const long long warps = ntl * (G::TX * G::TY * G::TZ / 32);
-    const long long blocks = std::max<long long>(1, std::min<long long>((warps * 32 + 255) / 256, (long long)ws.sms * bps));
+    const long long plane = (long long)g.res[0] * (D == 3 ? g.res[1] : 1);
+    const long long pix = (long long)(win_hi(g) - win_lo(g)) * plane;
+    const long long blocks =
+        std::max<long long>(1, std::min<long long>((pix + kBandChunk - 1) / kBandChunk, (long long)ws.sms * bps));
     const int wide = (g.res[0] > 4096 || g.res[1] > 4096 || (D == 3 && g.res[2] > 4096)) ? 1 : 0;
     tc_band_kernel<D><<<(unsigned)blocks, 256, 0, st>>>(
-        g, ntx, nty, tlo, ntiles, n, ws.recs32, ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.inc_labels, ws.inc_gap,
+        g, ntx, nty, tlo, n, ws.recs32, ws.tc_centre, ws.tc_meta, ws.tc_texcl, ws.tc_list, ws.inc_labels, ws.inc_gap,
         ws.inc_rec, ws.inc_drift, ws.moments, ws.flags, ws.flag_gi, ws.sc, wide);
     return cudaGetLastError();
 }
