@@ -1812,8 +1812,7 @@ __global__ void __launch_bounds__(256)
 }
 
 template <int D>
-cudaError_t launch_band_t(const GridDev &g, int n, const double *w, Workspace &ws, cudaStream_t st) {
-    (void)w;
+cudaError_t launch_band_t(const GridDev &g, int n, Workspace &ws, cudaStream_t st) {
     int ntx = 0, nty = 0, tlo = 0;
     long long ntl = 0;
     tile_grid<D>(g, ntx, nty, tlo, ntl);
@@ -1862,8 +1861,8 @@ cudaError_t launch_tc_axis(const GridDev &g, Workspace &ws, cudaStream_t st) {
     return ensure_axis<2>(g, ntx, nty, 0, tlo, ws, st);
 }
 
-cudaError_t launch_tc_band(const GridDev &g, int n, const double *w, Workspace &ws, cudaStream_t st) {
-    return g.dim == 3 ? launch_band_t<3>(g, n, w, ws, st) : launch_band_t<2>(g, n, w, ws, st);
+cudaError_t launch_tc_band(const GridDev &g, int n, Workspace &ws, cudaStream_t st) {
+    return g.dim == 3 ? launch_band_t<3>(g, n, ws, st) : launch_band_t<2>(g, n, ws, st);
 }
 
 long long tc_tile_count(const GridDev &g) {

@@ -265,7 +265,7 @@ int enqueue_assign(const GridDev &g_in, int n, const double *x, const double *A,
                                          : cudaEventRecord(e1, st)));
     // the re-decision (nothing when the pass records), the rescoring in the mode
     // the device chose, and a recording's moments, weights and w_ref kept
-    if (inc_on) APD_TRY(cuda_ok(launch_tc_band(g, n, w, ws, st)));
+    if (inc_on) APD_TRY(cuda_ok(launch_tc_band(g, n, ws, st)));
     if (!empty)
         APD_TRY(cuda_ok(launch_rescore_fp64(g, n, x, A, w, ws, labels, mom, st, inc_on ? ws.inc_labels : nullptr,
                                             inc_on ? &ws.sc->inc_go : nullptr)));

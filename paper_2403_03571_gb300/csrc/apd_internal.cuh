@@ -474,7 +474,7 @@ cudaError_t launch_lbfgs_coefficients(int n, int hist, int newest, int cap, doub
                                       int hist_acc, int newest_acc, Workspace &ws, cudaStream_t st);
 cudaError_t launch_tc_axis(const GridDev &g, Workspace &ws, cudaStream_t st);
 // the incremental pass's re-decision of the pixels within the drift of their recorded gap
-cudaError_t launch_tc_band(const GridDev &g, int n, const double *w, Workspace &ws, cudaStream_t st);
+cudaError_t launch_tc_band(const GridDev &g, int n, Workspace &ws, cudaStream_t st);
 // incremental pass, before scoring: the recorded moments copied in (re-decision)
 // or the margin histogram cleared (recording); after rescoring: the record's
 // moments, weights and w_ref kept (recording)
